@@ -1,0 +1,314 @@
+"""Seeded synthetic scattering problems (inputs only).
+
+This module builds the *inputs* of a close-coupling Hamiltonian build: orbital
+integrals, target determinant lists with CI vectors, continuum-orbital ranges and
+L2 determinant lists.  It holds none of the method's arithmetic (no Slater-Condon
+rules, no contraction, no expansion): both the CPU oracle and the CUDA path read
+what it produces.  The paper's own workloads (UKRMol H3PO4 and UKRMol+ BeH
+integrals) are not available, so these seeded inputs stand in for them with the
+shapes of the paper's problems: a CI-expanded target (Eq. 2) coupled to a set of
+continuum orbitals, plus L2 configurations (Eq. 1).
+
+Conventions shared by every consumer (they define the *input format*):
+
+* spatial orbitals: target orbitals 0..n_to-1, continuum orbitals n_to..n_orb-1
+  (continuum index j in 0..n_co-1 is global orbital n_to+j);
+* a determinant is 2*W uint64 words: words 0..W-1 hold the alpha string, words
+  W..2W-1 the beta string; bit p of a string is target orbital p;
+* one-electron integrals h[p, q] over all n_orb orbitals (symmetric);
+* two-electron integrals in chemists' notation (pq|rs), real, 8-fold symmetric,
+  stored in four class arrays (at most two continuum indices ever occur in an
+  (N+1)-electron function with a single continuum electron):
+    eri_tttt[pair(p,q), pair(r,s)]          all four target
+    eri_tttc[pair(p,q), r*n_co + j]         (pq|r j)
+    eri_ttcc[pair(p,q), j*n_co + k]         (pq|j k), full square in (j, k)
+    eri_tctc[r*n_co + j, s*n_co + k]        (r j|s k), full square
+  where pair(p,q) = p(p+1)/2 + q for p >= q.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ALPHA, BETA = 0, 1
+
+
+def pair_index(p: int, q: int) -> int:
+    if p < q:
+        p, q = q, p
+    return p * (p + 1) // 2 + q
+
+
+@dataclass
+class Group:
+    """One target symmetry: determinants, CI vectors and its continuum range."""
+    dets: np.ndarray        # (n_det, 2W) uint64
+    ci: np.ndarray          # (n_det, n_state) float64, row-major c[m, n]
+    cont_first: int         # first continuum orbital (0-based within continuum)
+    cont_count: int         # number of continuum orbitals coupled to this group
+
+
+@dataclass
+class Problem:
+    name: str
+    n_to: int
+    n_co: int
+    n_elec: int             # N, electrons of the target
+    n_words: int            # W, uint64 words per spin string
+    cont_spin: int          # spin of the continuum electron (0 alpha, 1 beta)
+    h: np.ndarray
+    eri_tttt: np.ndarray
+    eri_tttc: np.ndarray
+    eri_ttcc: np.ndarray
+    eri_tctc: np.ndarray
+    groups: list
+    l2_dets: np.ndarray     # (n_l2, 2W) uint64
+    e_core: float = 0.0
+    chol: np.ndarray | None = None   # packed-pair Cholesky factor (small problems)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_orb(self) -> int:
+        return self.n_to + self.n_co
+
+    @property
+    def n_l2(self) -> int:
+        return int(self.l2_dets.shape[0])
+
+    @property
+    def contracted_dim(self) -> int:
+        return int(sum(g.ci.shape[1] * g.cont_count for g in self.groups))
+
+    @property
+    def dim(self) -> int:
+        return self.contracted_dim + self.n_l2
+
+    def full_eri(self) -> np.ndarray:
+        """Full (pq|rs) tensor over all orbitals from the Cholesky factor (small only)."""
+        assert self.chol is not None and self.n_orb <= 40
+        n = self.n_orb
+        P = np.zeros((n, n, self.chol.shape[1]))
+        for p in range(n):
+            for q in range(p + 1):
+                P[p, q] = P[q, p] = self.chol[pair_index(p, q)]
+        return np.einsum("pqk,rsk->pqrs", P, P)
+
+
+# --------------------------------------------------------------------------
+# determinant pools
+# --------------------------------------------------------------------------
+
+def occ_to_words(alpha_occ, beta_occ, W: int) -> np.ndarray:
+    w = np.zeros(2 * W, dtype=np.uint64)
+    for p in alpha_occ:
+        w[p // 64] |= np.uint64(1) << np.uint64(p % 64)
+    for p in beta_occ:
+        w[W + p // 64] |= np.uint64(1) << np.uint64(p % 64)
+    return w
+
+
+def _excite(occ, n_orb, k):
+    """All strings reached from `occ` by exactly k substitutions within 0..n_orb-1."""
+    occ = tuple(occ)
+    virt = tuple(sorted(set(range(n_orb)) - set(occ)))
+    out = []
+    for holes in itertools.combinations(occ, k):
+        keep = [o for o in occ if o not in holes]
+        for parts in itertools.combinations(virt, k):
+            out.append(tuple(sorted(keep + list(parts))))
+    return out
+
+
+def sd_pool(n_alpha: int, n_beta: int, n_orb: int):
+    """Reference (lowest orbitals filled) plus all singles and doubles, as (a, b)."""
+    ra, rb = tuple(range(n_alpha)), tuple(range(n_beta))
+    pool = [(ra, rb)]
+    sa, sb = _excite(ra, n_orb, 1), _excite(rb, n_orb, 1)
+    pool += [(a, rb) for a in sa] + [(ra, b) for b in sb]
+    pool += [(a, rb) for a in _excite(ra, n_orb, 2)]
+    pool += [(ra, b) for b in _excite(rb, n_orb, 2)]
+    pool += [(a, b) for a in sa for b in sb]
+    return pool
+
+
+def sample_dets(rng, pool, n, W, include_reference=True):
+    if n > len(pool):
+        raise ValueError(f"asked for {n} determinants from a pool of {len(pool)}")
+    if include_reference:
+        idx = np.concatenate([[0], 1 + rng.choice(len(pool) - 1, n - 1, replace=False)])
+    else:
+        idx = rng.choice(len(pool), n, replace=False)
+    return np.stack([occ_to_words(*pool[i], W) for i in idx]), idx
+
+
+# --------------------------------------------------------------------------
+# integrals
+# --------------------------------------------------------------------------
+
+def make_h(rng, n_to, n_co, cont_diag=(-3.0, -0.5), offdiag_sd=0.05, orb_irrep=None):
+    n = n_to + n_co
+    h = rng.normal(0.0, offdiag_sd, size=(n, n))
+    h = np.tril(h, -1)
+    h = h + h.T
+    h[np.arange(n_to), np.arange(n_to)] = rng.uniform(-3.0, -0.5, size=n_to)
+    h[np.arange(n_to, n), np.arange(n_to, n)] = rng.uniform(*cont_diag, size=n_co)
+    if orb_irrep is not None:
+        ir = np.asarray(orb_irrep)
+        h[(ir[:, None] ^ ir[None, :]) != 0] = 0.0
+    return h
+
+
+def make_chol(rng, n_orb, rank, orb_irrep=None):
+    """Packed-pair Cholesky-like factor L[pair(p,q), k] ~ N(0, 0.5/rank)."""
+    npair = n_orb * (n_orb + 1) // 2
+    L = rng.normal(0.0, np.sqrt(0.5 / rank), size=(npair, rank))
+    if orb_irrep is not None:
+        ir = np.asarray(orb_irrep)
+        vec_irrep = rng.integers(0, 8, size=rank)
+        vec_irrep[: max(1, rank // 8)] = 0   # keep totally symmetric vectors present
+        pi = np.empty(npair, dtype=np.int64)
+        for p in range(n_orb):
+            for q in range(p + 1):
+                pi[pair_index(p, q)] = ir[p] ^ ir[q]
+        L[pi[:, None] != vec_irrep[None, :]] = 0.0
+    return L
+
+
+def eri_classes(L, n_to, n_co):
+    """The four class arrays of (pq|rs) = sum_k L[pq,k] L[rs,k]."""
+    Pt = n_to * (n_to + 1) // 2
+    Ltt = L[:Pt]
+    tc = np.empty(n_to * n_co, dtype=np.int64)
+    for r in range(n_to):
+        for j in range(n_co):
+            tc[r * n_co + j] = pair_index(n_to + j, r)
+    cc = np.empty(n_co * n_co, dtype=np.int64)
+    for j in range(n_co):
+        for k in range(n_co):
+            cc[j * n_co + k] = pair_index(n_to + j, n_to + k)
+    Ltc = L[tc]
+    eri_tttt = Ltt @ Ltt.T
+    eri_tttc = Ltt @ Ltc.T
+    eri_ttcc = Ltt @ L[cc].T
+    eri_tctc = Ltc @ Ltc.T
+    return eri_tttt, eri_tttc, eri_ttcc, eri_tctc
+
+
+def orthonormal_ci(rng, n_det, n_state):
+    g = rng.standard_normal((n_det, n_state))
+    q, _ = np.linalg.qr(g)
+    return np.ascontiguousarray(q)
+
+
+# --------------------------------------------------------------------------
+# problem families
+# --------------------------------------------------------------------------
+
+def make_problem(name, seed, n_to, n_co, n_elec, n_det, n_state, n_l2, rank,
+                 cont_diag=(-3.0, -0.5), n_words=None, cont_spin=ALPHA,
+                 n_groups=1, cont_ranges=None, keep_chol=None):
+    """Single-spin-coupling problem: all groups share Ms and the continuum spin.
+
+    cont_spin=ALPHA: targets have Ms=0 (N/2 alpha, N/2 beta), continuum alpha.
+    cont_spin=BETA:  targets have Ms=+1 (N/2+1 alpha, N/2-1 beta), continuum beta.
+    L2 determinants always carry N/2+1 alpha and N/2 beta electrons (Ms=+1/2).
+    With several groups, target determinants are split disjointly among them.
+    """
+    rng = np.random.default_rng(seed)
+    W = n_words or max(1, (n_to + 63) // 64)
+    half = n_elec // 2
+    if cont_spin == ALPHA:
+        na, nb = half, n_elec - half
+    else:
+        na, nb = half + 1, n_elec - half - 1
+    h = make_h(rng, n_to, n_co, cont_diag)
+    L = make_chol(rng, n_to + n_co, rank)
+    eri = eri_classes(L, n_to, n_co)
+
+    pool = sd_pool(na, nb, n_to)
+    total = n_det * n_groups
+    dets, _ = sample_dets(rng, pool, total, W)
+    groups = []
+    for g in range(n_groups):
+        d = dets[g * n_det:(g + 1) * n_det]
+        ns = n_state[g] if isinstance(n_state, (list, tuple)) else n_state
+        ci = orthonormal_ci(rng, n_det, ns)
+        if cont_ranges is None:
+            cf, cn = 0, n_co
+        else:
+            cf, cn = cont_ranges[g]
+            if cf < 0 or cn < 1 or cf + cn > n_co:
+                raise ValueError(f"continuum range {cf}+{cn} outside 0..{n_co}")
+        groups.append(Group(np.ascontiguousarray(d), ci, cf, cn))
+
+    l2pool = sd_pool(half + 1, n_elec - half, n_to)
+    l2, _ = sample_dets(rng, l2pool, n_l2, W) if n_l2 > 0 else (np.zeros((0, 2 * W), np.uint64), None)
+    keep = keep_chol if keep_chol is not None else (n_to + n_co) <= 40
+    return Problem(name=name, n_to=n_to, n_co=n_co, n_elec=n_elec, n_words=W,
+                   cont_spin=cont_spin, h=h, eri_tttt=eri[0], eri_tttc=eri[1],
+                   eri_ttcc=eri[2], eri_tctc=eri[3], groups=groups,
+                   l2_dets=np.ascontiguousarray(l2), chol=L if keep else None,
+                   meta=dict(seed=seed, rank=rank))
+
+
+# The five workloads.  Sizes follow the problem statement of each workload:
+# C1 tiny FP64 build, C2 medium build + Davidson, C3 precision, C5 learned
+# preconditioner (C3 family, more L2).  C4 (batched symmetry blocks) is built by
+# make_batched_family below.
+CONFIGS = {
+    "c1": dict(name="c1_tiny", seed=1, n_to=10, n_co=20, n_elec=6, n_det=40, n_state=3,
+               n_l2=50, rank=20),
+    "c2": dict(name="c2_medium", seed=2, n_to=30, n_co=150, n_elec=10, n_det=2000,
+               n_state=20, n_l2=5000, rank=60),
+    "c3": dict(name="c3_precision", seed=3, n_to=40, n_co=400, n_elec=14, n_det=20000,
+               n_state=50, n_l2=30000, rank=60, cont_diag=(0.0, 50.0)),
+    "c5": dict(name="c5_learned", seed=5, n_to=40, n_co=400, n_elec=14, n_det=20000,
+               n_state=50, n_l2=40000, rank=60, cont_diag=(0.0, 50.0)),
+    # a mid-size case that spans several GPU tiles with ragged tails and that the
+    # oracle builds in full within seconds
+    "mid": dict(name="mid_ragged", seed=11, n_to=12, n_co=37, n_elec=6, n_det=300,
+                n_state=7, n_l2=700, rank=24),
+}
+
+
+def make_config(key: str, **overrides) -> Problem:
+    kw = dict(CONFIGS[key])
+    kw.update(overrides)
+    return make_problem(**kw)
+
+
+def make_tiny(seed, n_to=5, n_co=3, n_elec=4, n_det=6, n_state=2, n_l2=5, rank=6,
+              n_groups=1, cont_spin=ALPHA, cont_ranges=None, n_words=None):
+    """Tiny random problems for brute-force pinning (all integrals kept)."""
+    return make_problem(f"tiny{seed}", seed, n_to, n_co, n_elec, n_det, n_state, n_l2,
+                        rank, n_words=n_words, cont_spin=cont_spin, n_groups=n_groups,
+                        cont_ranges=cont_ranges, keep_chol=True)
+
+
+def random_det_pairs(rng, n_orb, n_alpha, n_beta, W, count, max_exc=3, orbitals=None):
+    """Random determinant pairs (bra, ket) within `max_exc` substitutions.
+
+    `orbitals`, if given, is the list of spatial orbitals the strings may use
+    (e.g. orbitals straddling the 64-bit word boundaries).
+    """
+    orbs = np.arange(n_orb) if orbitals is None else np.asarray(orbitals)
+    out = []
+    for _ in range(count):
+        a = rng.choice(orbs, n_alpha, replace=False)
+        b = rng.choice(orbs, n_beta, replace=False)
+        a2, b2 = set(a.tolist()), set(b.tolist())
+        k = rng.integers(0, max_exc + 1)
+        for _ in range(k):
+            if rng.random() < 0.5 and len(set(orbs.tolist()) - a2) > 0:
+                s = rng.choice(sorted(a2)); t = rng.choice(sorted(set(orbs.tolist()) - a2))
+                a2.remove(s); a2.add(t)
+            elif len(set(orbs.tolist()) - b2) > 0:
+                s = rng.choice(sorted(b2)); t = rng.choice(sorted(set(orbs.tolist()) - b2))
+                b2.remove(s); b2.add(t)
+        out.append((occ_to_words(sorted(a.tolist()), sorted(b.tolist()), W),
+                    occ_to_words(sorted(a2), sorted(b2), W)))
+    bra = np.stack([o[0] for o in out])
+    ket = np.stack([o[1] for o in out])
+    return bra, ket
