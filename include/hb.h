@@ -1,0 +1,223 @@
+/*
+ * hb.h -- C ABI of the GB300 close-coupling Hamiltonian build.
+ *
+ * The library builds the contracted (N+1)-electron scattering Hamiltonian of
+ * the close-coupling expansion (Eq. 1 of Al-Refaie & Tennyson, "A parallel
+ * algorithm for Hamiltonian matrix construction in electron-molecule
+ * collision calculations: MPI-SCATCI") with Tennyson's structured algorithm
+ * (Section 2.1: bitstring Slater-Condon rules, prototype symbols, contraction
+ * with the target CI coefficients, Eq. 6-8, and expansion over continuum
+ * orbitals), and finds its lowest eigenpairs (Section 3.2.2, Davidson).
+ *
+ * Conventions
+ * -----------
+ * Orbitals: spatial orbitals 0..n_to-1 are target orbitals, n_to..n_to+n_co-1
+ *   continuum orbitals.  Continuum index j (0..n_co-1) is orbital n_to+j.
+ * Determinants: 2*n_words uint64 words, words [0, W) the alpha string and
+ *   [W, 2W) the beta string; bit p of a string is target orbital p.  The
+ *   (N+1)-electron determinant of a target determinant D and continuum orbital
+ *   j is the canonically ordered product of creation operators over all alpha
+ *   spin orbitals (target, then continuum) followed by all beta ones, so the
+ *   continuum spin orbital sits above every target orbital of its spin and
+ *   every phase and integral label is independent of j (prototyping).
+ * Integrals (chemists' notation, real, 8-fold symmetric; pair(p,q) =
+ *   p(p+1)/2+q for p >= q, Pt = n_to(n_to+1)/2):
+ *     h[(n_to+n_co)^2]                 one-electron, row-major, symmetric
+ *     eri_tttt[Pt][Pt]                 (pq|rs), four target indices
+ *     eri_tttc[Pt][n_to*n_co]          (pq|r j) at [pair(p,q)][r*n_co + j]
+ *     eri_ttcc[Pt][n_co*n_co]          (pq|j k) at [pair(p,q)][j*n_co + k]
+ *     eri_tctc[n_to*n_co][n_to*n_co]   (r j|s k) at [r*n_co + j][s*n_co + k]
+ *   No other class is needed: an (N+1)-electron function holds at most one
+ *   continuum electron, so at most two continuum indices occur (Section 2.1).
+ * Basis order of the result: for each target group g (a target symmetry),
+ *   for each state n, for each continuum orbital j of its range (n-major);
+ *   then the L2 functions.  Group g starts at row group_offset(g).
+ *
+ * Results (hb_blocks, all caller-owned device memory):
+ *   Hcc  [Dc][Dc]      continuum-continuum classes 1,3,5,6,7, full symmetric
+ *   Hlc  [n_l2][Dc]    class 4, L2 row l against contracted column (g,n,j);
+ *                      this is the lower-triangle block of the matrix
+ *   CSR  row_ptr[n_l2+1] (int64), col[nnz] (int32), val[nnz] (double):
+ *                      classes 2 and 8, the full symmetric L2 x L2 block with
+ *                      one entry per pair within a double excitation
+ *   Dc = contracted dimension, dim = Dc + n_l2.
+ *
+ * Errors: every call returns an int status (HB_OK = 0); no exception crosses
+ * the ABI and nothing aborts.  hb_last_error(ctx) (or hb_last_error(NULL)
+ * for calls without a context) returns a message for the last failure.
+ * Streams: `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ * default stream.  Work is enqueued on it; calls that must read a device
+ * result (counts, convergence) synchronise that stream before returning.
+ */
+#ifndef HB_H
+#define HB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HB_OK = 0,
+    HB_ERR_INVALID_ARG = 1,
+    HB_ERR_CUDA = 2,
+    HB_ERR_OOM = 3,
+    HB_ERR_TIMEOUT = 4,
+    HB_ERR_NOT_CONVERGED = 5,
+    HB_ERR_UNSUPPORTED = 6
+};
+
+enum { HB_FP64 = 0, HB_MIXED = 1 };
+enum { HB_PRECOND_DIAG = 0, HB_PRECOND_MLP = 1 };
+enum { HB_SPIN_ALPHA = 0, HB_SPIN_BETA = 1 };
+
+typedef struct hb_ctx hb_ctx;
+
+/* One target symmetry (Eq. 2): phi_n = sum_m c[m][n] D_m, coupled to the
+   contiguous continuum range [cont_first, cont_first + cont_count). */
+typedef struct {
+    int32_t n_det;
+    int32_t n_state;
+    const uint64_t *dets;   /* host, [n_det][2*n_words] */
+    const double *ci;       /* host, [n_det][n_state], row-major */
+    int32_t cont_first;
+    int32_t cont_count;
+} hb_group;
+
+/* The problem of Eq. 1: orbitals, integrals, target groups, L2 functions.
+   All pointers are host pointers; hb_init copies what it needs. */
+typedef struct {
+    int32_t n_to, n_co;     /* target and continuum spatial orbitals */
+    int32_t n_elec;         /* N, target electrons (the system has N+1) */
+    int32_t n_words;        /* W, uint64 words per spin string (1..4) */
+    int32_t cont_spin;      /* spin of the continuum electron, HB_SPIN_* */
+    const double *h;
+    const double *eri_tttt, *eri_tttc, *eri_ttcc, *eri_tctc;
+    int32_t n_groups;
+    const hb_group *groups;
+    int32_t n_l2;
+    const uint64_t *l2_dets;  /* host, [n_l2][2*n_words], N+1 electrons */
+    double e_core;            /* constant added to the Hamiltonian (0 if none) */
+} hb_problem;
+
+typedef struct {
+    int32_t split_slices;     /* mixed path: bf16 slices per operand, 0 = default (5) */
+    int32_t validate;         /* 0 = skip the O(n^2) input checks */
+    int32_t reserved[14];
+} hb_options;
+
+typedef struct {
+    int64_t dim, contracted_dim, n_l2, l2_nnz;
+    int64_t tt_pairs;         /* target x target pairs within a double excitation */
+    int64_t tl2_pairs;        /* target x L2 pairs within a double excitation */
+    int64_t n_labels;         /* K: labels of the expansion contraction */
+    int64_t device_bytes;     /* device memory held by the context */
+    int32_t n_groups;
+    int32_t n_words;
+} hb_layout;
+
+typedef struct {
+    double *Hcc;
+    double *Hlc;
+    int64_t *l2_row_ptr;
+    int32_t *l2_col;
+    double *l2_val;
+} hb_blocks;
+
+typedef struct {
+    float ms_total;           /* build: enqueue to completion on the stream */
+    float ms_target;          /* classification + target-side contraction */
+    float ms_expand;          /* continuum-continuum expansion */
+    float ms_class4;
+    float ms_l2;
+    float ms_expand_gemm;     /* dominant kernel alone (expansion contraction) */
+    int32_t expand_launches;
+    int32_t kernel_launches;  /* kernels launched by the call */
+    double expand_flops;      /* algorithmic flops of the expansion */
+    int32_t iterations;       /* hb_diag */
+    int32_t mlp_fallbacks;
+    double max_residual;
+    float ms_matvec;
+    float ms_rr;
+    int32_t reserved[8];
+} hb_stats;
+
+/* Excitation record of one determinant pair (row, col), see hb_classify. */
+typedef struct {
+    int32_t row, col;
+    int16_t hole[2];          /* bit positions (spin*64*W + orbital) in col only */
+    int16_t part[2];          /* bit positions in row only; -1 if unused */
+    int8_t degree;
+    int8_t phase;             /* +1 / -1 */
+    int16_t pad[3];
+} hb_pair;
+
+/* Validate and copy a problem (Eq. 1-2), stage it on the current device and
+   build the continuum-continuum integral panels.  Allocates the device memory
+   the context needs (reported by hb_query).  Errors: HB_ERR_INVALID_ARG for
+   inconsistent input (electron counts, spins, duplicate determinants, ranges,
+   non-finite integrals, orbital counts beyond 16-bit labels), HB_ERR_OOM,
+   HB_ERR_CUDA, HB_ERR_UNSUPPORTED (n_words > 4). */
+int hb_init(hb_ctx **ctx, const hb_problem *p, const hb_options *o, void *stream);
+
+/* Sizes of the result and of the context (Section 2.2 classes). */
+int hb_query(const hb_ctx *ctx, hb_layout *out);
+
+/* First row of target group g in the contracted basis. */
+int64_t hb_group_offset(const hb_ctx *ctx, int32_t g);
+
+/* Build every class (1-8) into the caller's device buffers.  precision:
+   HB_FP64 (double arithmetic throughout) or HB_MIXED (the continuum-continuum
+   contraction on bf16 tensor cores with split operands, FP32 accumulation and
+   double-float recovery; everything else double).  `st` may be NULL. */
+int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *out, hb_stats *st,
+                    void *stream);
+
+/* Lowest k eigenpairs of the built matrix by block Davidson (Section 3.2.2)
+   to ||H x - lambda x||_2 <= tol for each pair.  evals: host [k]; evecs:
+   device [dim][k] row-major or NULL; v0: device [dim][k] start vectors or
+   NULL (unit vectors at the smallest diagonal entries).  precond:
+   HB_PRECOND_DIAG, or HB_PRECOND_MLP after hb_mlp_set.  Returns
+   HB_ERR_NOT_CONVERGED after max_iter iterations (evals then hold the current
+   Ritz values). */
+int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, int32_t max_iter,
+            int32_t precond, const double *v0, double *evals, double *evecs, hb_stats *st,
+            void *stream);
+
+/* Excitation classification (Section 2.1) of every pair (a, b) of two
+   determinant lists on the device.  mode 0: equal electron counts, degree =
+   popcount(a ^ b) / 2; mode 1: b holds N-electron target determinants and a
+   holds (N+1)-electron ones, the pair being (b + continuum electron of spin
+   cont_spin, a), degree = popcount(b & ~a) + 1.  Pairs with degree <= max_degree
+   (and b <= a when lower != 0) are written to pairs[] ordered by (a, b), with
+   row = a, col = b.  row_ptr (device, n_a + 1) receives the CSR offsets.  The
+   total goes to *total; if it exceeds cap nothing is written to pairs and
+   HB_ERR_INVALID_ARG is returned.  Phase = <row| a+_p1 a+_p2 a_h2 a_h1 |col>
+   (or a+_p a_h) with holes in col only and particles in row only, ascending
+   in the canonical order; for mode 1 the continuum electron is a particle
+   and is not listed. */
+int hb_classify(const uint64_t *a, int32_t n_a, const uint64_t *b, int32_t n_b,
+                int32_t n_words, int32_t mode, int32_t cont_spin, int32_t max_degree,
+                int32_t lower, int64_t *row_ptr, hb_pair *pairs, int64_t cap,
+                int64_t *total, void *stream);
+
+/* ---- learned Davidson preconditioner (a small MLP, not in the paper) ---- */
+
+typedef struct {
+    int32_t n_in, width;      /* input features, hidden width */
+    const float *w1, *b1;     /* host [width][n_in], [width] */
+    const float *w2, *b2;     /* host [width][width], [width] */
+    const float *w3, *b3;     /* host [1][width], [1] */
+} hb_mlp_weights;
+
+int hb_mlp_set(hb_ctx *ctx, const hb_mlp_weights *w);
+
+const char *hb_last_error(const hb_ctx *ctx);
+void hb_destroy(hb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HB_H */

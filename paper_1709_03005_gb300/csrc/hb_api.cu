@@ -1,0 +1,494 @@
+// C ABI of the Hamiltonian build: validation, staging, orchestration.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "hb_api_internal.cuh"
+
+using namespace hb;
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(hb_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(hb_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? HB_ERR_OOM : HB_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct DetHash {
+    size_t operator()(const std::vector<uint64_t> &v) const {
+        uint64_t x = 0x9e3779b97f4a7c15ull;
+        for (uint64_t w : v) x = (x ^ w) * 0xff51afd7ed558ccdull, x ^= x >> 29;
+        return (size_t)x;
+    }
+};
+
+int popcount_words(const uint64_t *w, int n) {
+    int c = 0;
+    for (int i = 0; i < n; ++i) c += __builtin_popcountll(w[i]);
+    return c;
+}
+
+bool all_finite(const double *x, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+}  // namespace
+
+#define CK(call)                                                         \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call);         \
+    } while (0)
+
+template <class T>
+static int dalloc(hb_ctx *ctx, T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * n);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    ctx->allocs.push_back(*p);
+    ctx->dev_bytes += sizeof(T) * n;
+    return HB_OK;
+}
+
+#define DALLOC(ptr, n)                                   \
+    do {                                                 \
+        int _r = dalloc(ctx, &(ptr), (size_t)(n));       \
+        if (_r != HB_OK) return _r;                      \
+    } while (0)
+
+static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o) {
+    if (!p) return fail(ctx, HB_ERR_INVALID_ARG, "problem is NULL");
+    if (p->n_words < 1 || p->n_words > HB_MAXW)
+        return fail(ctx, HB_ERR_UNSUPPORTED, "n_words must be 1..4 (up to 256 target orbitals)");
+    if (p->n_to < 1 || p->n_to > 64 * p->n_words)
+        return fail(ctx, HB_ERR_INVALID_ARG, "n_to must be 1..64*n_words");
+    if (p->n_co < 0 || p->n_to + p->n_co >= 65535)
+        return fail(ctx, HB_ERR_INVALID_ARG, "orbital count exceeds the 16-bit integral labels");
+    if (p->cont_spin != HB_SPIN_ALPHA && p->cont_spin != HB_SPIN_BETA)
+        return fail(ctx, HB_ERR_INVALID_ARG, "cont_spin must be HB_SPIN_ALPHA or HB_SPIN_BETA");
+    if (p->n_groups < 0 || p->n_l2 < 0) return fail(ctx, HB_ERR_INVALID_ARG, "negative counts");
+    if (p->n_groups > 0 && (!p->groups || p->n_co < 1))
+        return fail(ctx, HB_ERR_INVALID_ARG, "groups need a continuum");
+    if (p->n_elec < 1 || p->n_elec > 2 * p->n_to)
+        return fail(ctx, HB_ERR_INVALID_ARG, "n_elec out of range");
+    if (!p->h || !p->eri_tttt) return fail(ctx, HB_ERR_INVALID_ARG, "h or eri_tttt is NULL");
+    if (p->n_groups > 0 && (!p->eri_tttc || !p->eri_ttcc || !p->eri_tctc))
+        return fail(ctx, HB_ERR_INVALID_ARG, "continuum integral arrays are NULL");
+    if (p->n_l2 > 0 && !p->l2_dets) return fail(ctx, HB_ERR_INVALID_ARG, "l2_dets is NULL");
+    if (p->n_groups > 0 && p->n_l2 > 0 && !p->eri_tttc)
+        return fail(ctx, HB_ERR_INVALID_ARG, "eri_tttc is NULL");
+    if (!std::isfinite(p->e_core)) return fail(ctx, HB_ERR_INVALID_ARG, "e_core is not finite");
+    const int W = p->n_words, nw = 2 * W;
+    // electron counts: every target determinant has the same alpha/beta split,
+    // the continuum electron sets the L2 split
+    int na = -1, nb = -1;
+    std::unordered_set<std::vector<uint64_t>, DetHash> seen;
+    const uint64_t hi_mask = p->n_to % 64 ? ((1ull << (p->n_to % 64)) - 1ull) : ~0ull;
+    auto check_bits = [&](const uint64_t *d) {
+        for (int s = 0; s < 2; ++s)
+            for (int w = 0; w < W; ++w) {
+                const int first = 64 * w;
+                uint64_t allowed = first + 64 <= p->n_to ? ~0ull : (first < p->n_to ? hi_mask : 0ull);
+                if (d[s * W + w] & ~allowed) return false;
+            }
+        return true;
+    };
+    for (int g = 0; g < p->n_groups; ++g) {
+        const hb_group &G = p->groups[g];
+        if (G.n_det < 1 || G.n_state < 1 || !G.dets || !G.ci)
+            return fail(ctx, HB_ERR_INVALID_ARG, "group " + std::to_string(g) + ": empty or NULL");
+        if (G.n_state > 1024)
+            return fail(ctx, HB_ERR_UNSUPPORTED, "more than 1024 target states in a group");
+        if (G.cont_first < 0 || G.cont_count < 1 || G.cont_first + G.cont_count > p->n_co)
+            return fail(ctx, HB_ERR_INVALID_ARG, "group " + std::to_string(g) + ": continuum range");
+        if (!all_finite(G.ci, (size_t)G.n_det * G.n_state))
+            return fail(ctx, HB_ERR_INVALID_ARG, "group " + std::to_string(g) + ": non-finite CI");
+        for (int m = 0; m < G.n_det; ++m) {
+            const uint64_t *d = G.dets + (size_t)m * nw;
+            if (!check_bits(d)) return fail(ctx, HB_ERR_INVALID_ARG, "determinant uses a non-target orbital");
+            const int a = popcount_words(d, W), b = popcount_words(d + W, W);
+            if (a + b != p->n_elec)
+                return fail(ctx, HB_ERR_INVALID_ARG, "group " + std::to_string(g) + ": wrong electron count");
+            if (na < 0) { na = a; nb = b; }
+            if (a != na || b != nb)
+                return fail(ctx, HB_ERR_INVALID_ARG, "target determinants differ in Ms (one spin coupling per problem)");
+            if (!seen.insert(std::vector<uint64_t>(d, d + nw)).second)
+                return fail(ctx, HB_ERR_INVALID_ARG, "duplicate target determinant (groups must be disjoint)");
+        }
+    }
+    seen.clear();
+    for (int l = 0; l < p->n_l2; ++l) {
+        const uint64_t *d = p->l2_dets + (size_t)l * nw;
+        if (!check_bits(d)) return fail(ctx, HB_ERR_INVALID_ARG, "L2 determinant uses a non-target orbital");
+        const int a = popcount_words(d, W), b = popcount_words(d + W, W);
+        if (a + b != p->n_elec + 1) return fail(ctx, HB_ERR_INVALID_ARG, "L2 determinant with wrong electron count");
+        if (na >= 0) {
+            const int ea = na + (p->cont_spin == HB_SPIN_ALPHA), eb = nb + (p->cont_spin == HB_SPIN_BETA);
+            if (a != ea || b != eb) return fail(ctx, HB_ERR_INVALID_ARG, "L2 determinant with a different Ms");
+        }
+        if (!seen.insert(std::vector<uint64_t>(d, d + nw)).second)
+            return fail(ctx, HB_ERR_INVALID_ARG, "duplicate L2 determinant");
+    }
+    const size_t no = (size_t)(p->n_to + p->n_co);
+    const size_t Pt = (size_t)p->n_to * (p->n_to + 1) / 2, ntc = (size_t)p->n_to * p->n_co;
+    if (!all_finite(p->h, no * no) || !all_finite(p->eri_tttt, Pt * Pt))
+        return fail(ctx, HB_ERR_INVALID_ARG, "non-finite integrals");
+    for (size_t i = 0; i < no; ++i)
+        for (size_t j = 0; j < i; ++j)
+            if (p->h[i * no + j] != p->h[j * no + i]) return fail(ctx, HB_ERR_INVALID_ARG, "h is not symmetric");
+    for (size_t i = 0; i < Pt; ++i)
+        for (size_t j = 0; j < i; ++j)
+            if (p->eri_tttt[i * Pt + j] != p->eri_tttt[j * Pt + i])
+                return fail(ctx, HB_ERR_INVALID_ARG, "eri_tttt breaks the (pq|rs) = (rs|pq) symmetry");
+    const bool deep = !o || o->validate != 0;
+    if (p->n_groups > 0 || p->n_l2 > 0) {
+        if (p->eri_tttc && !all_finite(p->eri_tttc, Pt * ntc)) return fail(ctx, HB_ERR_INVALID_ARG, "non-finite eri_tttc");
+    }
+    if (p->n_groups > 0 && deep) {
+        if (!all_finite(p->eri_ttcc, Pt * (size_t)p->n_co * p->n_co) || !all_finite(p->eri_tctc, ntc * ntc))
+            return fail(ctx, HB_ERR_INVALID_ARG, "non-finite continuum integrals");
+        for (size_t i = 0; i < ntc; ++i)
+            for (size_t j = 0; j < i; ++j)
+                if (p->eri_tctc[i * ntc + j] != p->eri_tctc[j * ntc + i])
+                    return fail(ctx, HB_ERR_INVALID_ARG, "eri_tctc breaks the (pq|rs) = (rs|pq) symmetry");
+        const size_t nc = p->n_co;
+        for (size_t k = 0; k < Pt; ++k)
+            for (size_t j = 0; j < nc; ++j)
+                for (size_t i = 0; i < j; ++i)
+                    if (p->eri_ttcc[k * nc * nc + j * nc + i] != p->eri_ttcc[k * nc * nc + i * nc + j])
+                        return fail(ctx, HB_ERR_INVALID_ARG, "eri_ttcc breaks the (pq|rs) = (pq|sr) symmetry");
+    }
+    return HB_OK;
+}
+
+extern "C" int hb_init(hb_ctx **out, const hb_problem *p, const hb_options *o, void *stream) {
+    if (!out) return fail(nullptr, HB_ERR_INVALID_ARG, "ctx pointer is NULL");
+    *out = nullptr;
+    hb_ctx *ctx = new hb_ctx();
+    int rc = validate_problem(ctx, p, o);
+    if (rc != HB_OK) { g_last_error = ctx->err; delete ctx; return rc; }
+    rc = stage_problem(ctx, p, o, (cudaStream_t)stream);
+    if (rc != HB_OK) { g_last_error = ctx->err; hb_destroy(ctx); return rc; }
+    *out = ctx;
+    return HB_OK;
+}
+
+int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStream_t s) {
+    CK(cudaGetDevice(&ctx->device));
+    ctx->n_to = p->n_to; ctx->n_co = p->n_co; ctx->n_orb = p->n_to + p->n_co;
+    ctx->n_elec = p->n_elec; ctx->W = p->n_words; ctx->cont_spin = p->cont_spin;
+    ctx->n_groups = p->n_groups; ctx->n_l2 = p->n_l2; ctx->e_core = p->e_core;
+    ctx->split_slices = (o && o->split_slices > 0) ? o->split_slices : 5;
+    ctx->Pt = (int64_t)p->n_to * (p->n_to + 1) / 2;
+    ctx->K = (int)(ctx->Pt + (int64_t)p->n_to * p->n_to + 2);
+    ctx->Kpad = (ctx->K + 63) / 64 * 64;
+    const int W = ctx->W, nw = 2 * W;
+    // groups and offsets
+    int64_t det_off = 0, ci_off = 0, row_off = 0;
+    for (int g = 0; g < p->n_groups; ++g) {
+        const hb_group &G = p->groups[g];
+        GroupInfo gi;
+        gi.ndet = G.n_det; gi.ns = G.n_state; gi.cf = G.cont_first; gi.cn = G.cont_count;
+        gi.det_off = det_off; gi.ci_off = ci_off; gi.row_off = row_off;
+        ctx->groups.push_back(gi);
+        det_off += (int64_t)G.n_det * nw;
+        ci_off += (int64_t)G.n_det * G.n_state;
+        row_off += (int64_t)G.n_state * G.cont_count;
+    }
+    ctx->Dc = row_off;
+    ctx->dim = row_off + p->n_l2;
+    const size_t no = ctx->n_orb, Pt = ctx->Pt, ntc = (size_t)p->n_to * p->n_co, ncc = (size_t)p->n_co * p->n_co;
+    // --- stage integrals, determinants, CI
+    DALLOC(ctx->h, no * no);
+    DALLOC(ctx->tttt, Pt * Pt);
+    DALLOC(ctx->jk, 2 * (size_t)p->n_to * p->n_to);
+    CK(cudaMemcpyAsync(ctx->h, p->h, sizeof(double) * no * no, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->tttt, p->eri_tttt, sizeof(double) * Pt * Pt, cudaMemcpyHostToDevice, s));
+    if (p->eri_tttc && ntc > 0) {
+        DALLOC(ctx->tttc, Pt * ntc);
+        CK(cudaMemcpyAsync(ctx->tttc, p->eri_tttc, sizeof(double) * Pt * ntc, cudaMemcpyHostToDevice, s));
+    }
+    DALLOC(ctx->dets, std::max<int64_t>(det_off, 1));
+    DALLOC(ctx->ci, std::max<int64_t>(ci_off, 1));
+    for (int g = 0; g < p->n_groups; ++g) {
+        const hb_group &G = p->groups[g];
+        const GroupInfo &gi = ctx->groups[g];
+        CK(cudaMemcpyAsync(ctx->dets + gi.det_off, G.dets, sizeof(uint64_t) * G.n_det * nw, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->ci + gi.ci_off, G.ci, sizeof(double) * G.n_det * G.n_state, cudaMemcpyHostToDevice, s));
+    }
+    DALLOC(ctx->l2, std::max(p->n_l2, 1) * nw);
+    if (p->n_l2 > 0)
+        CK(cudaMemcpyAsync(ctx->l2, p->l2_dets, sizeof(uint64_t) * p->n_l2 * nw, cudaMemcpyHostToDevice, s));
+    Ints I = ctx->ints();
+    build_jk(I, ctx->jk, s);
+    // --- the expansion panel (classes 1,3,5,6,7)
+    if (p->n_groups > 0) {
+        DALLOC(ctx->panel, ncc * ctx->Kpad);
+        double *t_ttcc = nullptr, *t_tctc = nullptr;
+        CK(cudaMalloc(&t_ttcc, sizeof(double) * Pt * ncc));
+        cudaError_t e2 = cudaMalloc(&t_tctc, sizeof(double) * ntc * ntc);
+        if (e2 != cudaSuccess) { cudaFree(t_ttcc); return cuda_fail(ctx, e2, "cudaMalloc"); }
+        cudaError_t e3 = cudaMemcpyAsync(t_ttcc, p->eri_ttcc, sizeof(double) * Pt * ncc, cudaMemcpyHostToDevice, s);
+        if (e3 == cudaSuccess)
+            e3 = cudaMemcpyAsync(t_tctc, p->eri_tctc, sizeof(double) * ntc * ntc, cudaMemcpyHostToDevice, s);
+        if (e3 == cudaSuccess) {
+            build_panel(t_ttcc, t_tctc, ctx->h, p->n_to, p->n_co, ctx->Kpad, ctx->panel, s);
+            e3 = cudaStreamSynchronize(s);
+        }
+        cudaFree(t_ttcc);
+        cudaFree(t_tctc);
+        if (e3 != cudaSuccess) return cuda_fail(ctx, e3, "panel staging");
+    }
+    // --- classification counts (structure of every class)
+    for (int g = 0; g < p->n_groups; ++g)
+        for (int gp = 0; gp <= g; ++gp) {
+            GroupPair P;
+            P.g = g; P.gp = gp; P.same = (g == gp);
+            DALLOC(P.rowptr, ctx->groups[g].ndet + 1);
+            ctx->gps.push_back(P);
+        }
+    for (auto &P : ctx->gps) {
+        const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
+        CK(cudaMemsetAsync(P.rowptr, 0, sizeof(int64_t), s));
+        k1_count(ctx->dets + A.det_off, A.ndet, ctx->dets + B.det_off, B.ndet, W, 0, 2, 0, P.rowptr, s);
+        exclusive_scan_inplace(P.rowptr, A.ndet, s);
+    }
+    for (int g = 0; g < p->n_groups; ++g) {
+        GroupL2 L;
+        DALLOC(L.rowptr, p->n_l2 + 1);
+        CK(cudaMemsetAsync(L.rowptr, 0, sizeof(int64_t), s));
+        k1_count(ctx->l2, p->n_l2, ctx->dets + ctx->groups[g].det_off, ctx->groups[g].ndet, W, 1, 2, 0, L.rowptr, s);
+        exclusive_scan_inplace(L.rowptr, p->n_l2, s);
+        ctx->gl2.push_back(L);
+    }
+    DALLOC(ctx->l2_rowptr, p->n_l2 + 1);
+    CK(cudaMemsetAsync(ctx->l2_rowptr, 0, sizeof(int64_t), s));
+    k1_count(ctx->l2, p->n_l2, ctx->l2, p->n_l2, W, 0, 2, 0, ctx->l2_rowptr, s);
+    exclusive_scan_inplace(ctx->l2_rowptr, p->n_l2, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    ctx->tt_pairs = 0;
+    for (auto &P : ctx->gps) {
+        CK(cudaMemcpy(&P.n_pairs, P.rowptr + ctx->groups[P.g].ndet, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        ctx->tt_pairs += P.n_pairs;
+    }
+    ctx->tl2_pairs = 0;
+    for (auto &L : ctx->gl2) {
+        CK(cudaMemcpy(&L.n_pairs, L.rowptr + p->n_l2, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        ctx->tl2_pairs += L.n_pairs;
+    }
+    CK(cudaMemcpy(&ctx->l2_nnz, ctx->l2_rowptr + p->n_l2, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    // --- per group pair scratch; the gamma item count needs the records
+    const int n_keys = 2 * p->n_to * p->n_to;
+    for (auto &P : ctx->gps) {
+        const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
+        DALLOC(P.pairs, P.n_pairs);
+        DALLOC(P.val, P.n_pairs);
+        DALLOC(P.item_ptr, A.ndet + 1);
+        k1_fill_pairs(ctx->dets + A.det_off, A.ndet, ctx->dets + B.det_off, B.ndet, W, 0, ctx->cont_spin, 2, 0,
+                      P.rowptr, P.pairs, s);
+        CK(cudaMemsetAsync(P.item_ptr, 0, sizeof(int64_t), s));
+        gamma_item_counts(P.pairs, P.rowptr, A.ndet, ctx->n_elec, P.item_ptr, s);
+        exclusive_scan_inplace(P.item_ptr, A.ndet, s);
+        CK(cudaMemcpyAsync(&P.n_items, P.item_ptr + A.ndet, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        P.n_chunks = sort_chunks(P.n_items);
+        DALLOC(P.items, P.n_items);
+        DALLOC(P.order, P.n_items);
+        DALLOC(P.sort_off, (int64_t)n_keys * P.n_chunks + 1);
+        DALLOC(P.sort_cur, (int64_t)n_keys * P.n_chunks + 1);
+        const int64_t nout = (int64_t)A.ns * B.ns;
+        DALLOC(P.gamma, n_keys * nout);
+        DALLOC(P.W, (int64_t)A.ndet * B.ns);
+        DALLOC(P.partial, (int64_t)tn_chunks(A.ndet) * nout);
+        DALLOC(P.S, nout);
+        DALLOC(P.E, nout);
+        std::vector<int32_t> nn;
+        for (int a = 0; a < A.ns; ++a)
+            for (int b = 0; b < B.ns; ++b)
+                if (!P.same || b <= a) { nn.push_back(a); nn.push_back(b); }
+        P.n_nn = (int)(nn.size() / 2);
+        DALLOC(P.nn, nn.size());
+        CK(cudaMemcpyAsync(P.nn, nn.data(), sizeof(int32_t) * nn.size(), cudaMemcpyHostToDevice, s));
+        DALLOC(P.A, (int64_t)P.n_nn * ctx->Kpad);
+        CK(cudaStreamSynchronize(s));
+    }
+    for (auto &L : ctx->gl2) DALLOC(L.pairs, L.n_pairs);
+    for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ctx->ev[i]));
+    CK(cudaStreamSynchronize(s));
+    return HB_OK;
+}
+
+extern "C" int hb_query(const hb_ctx *ctx, hb_layout *out) {
+    if (!ctx || !out) return fail(nullptr, HB_ERR_INVALID_ARG, "NULL argument");
+    out->dim = ctx->dim;
+    out->contracted_dim = ctx->Dc;
+    out->n_l2 = ctx->n_l2;
+    out->l2_nnz = ctx->l2_nnz;
+    out->tt_pairs = ctx->tt_pairs;
+    out->tl2_pairs = ctx->tl2_pairs;
+    out->n_labels = ctx->K;
+    out->device_bytes = (int64_t)ctx->dev_bytes;
+    out->n_groups = ctx->n_groups;
+    out->n_words = ctx->W;
+    return HB_OK;
+}
+
+extern "C" int64_t hb_group_offset(const hb_ctx *ctx, int32_t g) {
+    if (!ctx || g < 0 || g > ctx->n_groups) return -1;
+    return g == ctx->n_groups ? ctx->Dc : ctx->groups[g].row_off;
+}
+
+// Target side of one group pair: classification, H^N, S, E, gamma, coefficients.
+static int target_side(hb_ctx *ctx, GroupPair &P, cudaStream_t s, int *launches) {
+    const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
+    const int W = ctx->W;
+    const uint64_t *da = ctx->dets + A.det_off, *db = ctx->dets + B.det_off;
+    const double *Ca = ctx->ci + A.ci_off, *Cb = ctx->ci + B.ci_off;
+    Ints I = ctx->ints();
+    const int n_keys = 2 * ctx->n_to * ctx->n_to;
+    k1_fill_pairs(da, A.ndet, db, B.ndet, W, 0, ctx->cont_spin, 2, 0, P.rowptr, P.pairs, s);
+    pair_values(I, da, db, W, P.pairs, P.n_pairs, P.val, s);
+    sandwich_rows(P.pairs, P.rowptr, P.val, 0, A.ndet, Cb, B.ns, P.W, s);
+    gemm_tn_reduce(Ca, P.W, A.ndet, A.ns, B.ns, P.partial, P.E, s);
+    sandwich_rows(P.pairs, P.rowptr, nullptr, 1, A.ndet, Cb, B.ns, P.W, s);
+    gemm_tn_reduce(Ca, P.W, A.ndet, A.ns, B.ns, P.partial, P.S, s);
+    gamma_item_fill(P.pairs, P.rowptr, A.ndet, da, W, ctx->n_to, ctx->n_elec, P.item_ptr, P.items, s);
+    gamma_sort(P.items, P.n_items, n_keys, P.sort_off, P.sort_cur, P.order, s);
+    gamma_bins(P.items, P.order, P.sort_off, n_keys, P.n_items, Ca, A.ns, Cb, B.ns, P.gamma, s);
+    assemble_coefficients(P.gamma, P.S, P.E, P.nn, P.n_nn, A.ns, B.ns, ctx->n_to, ctx->cont_spin, ctx->e_core,
+                          ctx->Kpad, P.A, s);
+    *launches += 14;
+    return HB_OK;
+}
+
+extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *out, hb_stats *st,
+                               void *stream) {
+    if (!ctx || !out) return fail(ctx, HB_ERR_INVALID_ARG, "NULL argument");
+    if (precision != HB_FP64 && precision != HB_MIXED)
+        return fail(ctx, HB_ERR_INVALID_ARG, "precision must be HB_FP64 or HB_MIXED");
+    if (ctx->Dc > 0 && !out->Hcc) return fail(ctx, HB_ERR_INVALID_ARG, "Hcc is NULL");
+    if (ctx->Dc > 0 && ctx->n_l2 > 0 && !out->Hlc) return fail(ctx, HB_ERR_INVALID_ARG, "Hlc is NULL");
+    if (ctx->n_l2 > 0 && (!out->l2_row_ptr || !out->l2_col || !out->l2_val))
+        return fail(ctx, HB_ERR_INVALID_ARG, "L2 CSR arrays are NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    int launches = 0;
+    CK(cudaEventRecord(ctx->ev[0], s));
+    for (auto &P : ctx->gps) {
+        int rc = target_side(ctx, P, s, &launches);
+        if (rc != HB_OK) return rc;
+    }
+    CK(cudaEventRecord(ctx->ev[1], s));
+    float ms_gemm = 0.0f;
+    int n_expand = 0;
+    double flops = 0.0;
+    for (auto &P : ctx->gps) {
+        const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
+        if (precision == HB_MIXED) {
+            int rc = expand_mixed(ctx, P, out->Hcc, s);
+            if (rc != HB_OK) return rc;
+        } else {
+            expand_fp64(ctx->panel, P.A, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, A.cf, A.cn, B.cf, B.cn, A.row_off,
+                        B.row_off, P.same, ctx->Dc, out->Hcc, s);
+        }
+        ++n_expand;
+        flops += 2.0 * (double)A.cn * B.cn * P.n_nn * ctx->K;
+    }
+    launches += n_expand;
+    CK(cudaEventRecord(ctx->ev[2], s));
+    Ints I = ctx->ints();
+    for (int g = 0; g < ctx->n_groups; ++g) {
+        const GroupInfo &G = ctx->groups[g];
+        GroupL2 &L = ctx->gl2[g];
+        k1_fill_pairs(ctx->l2, ctx->n_l2, ctx->dets + G.det_off, G.ndet, ctx->W, 1, ctx->cont_spin, 2, 0, L.rowptr,
+                      L.pairs, s);
+        class4_fp64(I, L.pairs, L.rowptr, ctx->n_l2, ctx->dets + G.det_off, ctx->ci + G.ci_off, G.ns, G.cf, G.cn,
+                    ctx->W, ctx->cont_spin, G.row_off, ctx->Dc, out->Hlc, s);
+        launches += 2;
+    }
+    CK(cudaEventRecord(ctx->ev[3], s));
+    if (ctx->n_l2 > 0) {
+        CK(cudaMemcpyAsync(out->l2_row_ptr, ctx->l2_rowptr, sizeof(int64_t) * (ctx->n_l2 + 1),
+                           cudaMemcpyDeviceToDevice, s));
+        l2_csr_fill(I, ctx->l2, ctx->n_l2, ctx->W, ctx->l2_rowptr, out->l2_col, out->l2_val, ctx->e_core, s);
+        launches += 1;
+    }
+    CK(cudaGetLastError());
+    if (st) {
+        cudaEvent_t end;
+        CK(cudaEventCreate(&end));
+        CK(cudaEventRecord(end, s));
+        CK(cudaEventSynchronize(end));
+        float t01, t12, t23, t3e, t0e;
+        cudaEventElapsedTime(&t01, ctx->ev[0], ctx->ev[1]);
+        cudaEventElapsedTime(&t12, ctx->ev[1], ctx->ev[2]);
+        cudaEventElapsedTime(&t23, ctx->ev[2], ctx->ev[3]);
+        cudaEventElapsedTime(&t3e, ctx->ev[3], end);
+        cudaEventElapsedTime(&t0e, ctx->ev[0], end);
+        cudaEventDestroy(end);
+        memset(st, 0, sizeof(*st));
+        st->ms_total = t0e;
+        st->ms_target = t01;
+        st->ms_expand = t12;
+        st->ms_class4 = t23;
+        st->ms_l2 = t3e;
+        st->ms_expand_gemm = t12 + ms_gemm;
+        st->expand_launches = n_expand;
+        st->kernel_launches = launches;
+        st->expand_flops = flops;
+    }
+    return HB_OK;
+}
+
+extern "C" int hb_classify(const uint64_t *a, int32_t n_a, const uint64_t *b, int32_t n_b, int32_t n_words,
+                           int32_t mode, int32_t cont_spin, int32_t max_degree, int32_t lower, int64_t *row_ptr,
+                           hb_pair *pairs, int64_t cap, int64_t *total, void *stream) {
+    hb_ctx *ctx = nullptr;
+    if (n_words < 1 || n_words > HB_MAXW) return fail(ctx, HB_ERR_UNSUPPORTED, "n_words must be 1..4");
+    if (n_a < 0 || n_b < 0 || !row_ptr || !total || (mode != 0 && mode != 1) || max_degree < 0)
+        return fail(ctx, HB_ERR_INVALID_ARG, "bad classify arguments");
+    if ((n_a > 0 && !a) || (n_b > 0 && !b)) return fail(ctx, HB_ERR_INVALID_ARG, "NULL determinant list");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s));
+    if (n_a > 0) {
+        k1_count(a, n_a, b, n_b, n_words, mode, max_degree, lower, row_ptr, s);
+        exclusive_scan_inplace(row_ptr, n_a, s);
+    }
+    int64_t t = 0;
+    CK(cudaMemcpyAsync(&t, row_ptr + n_a, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *total = t;
+    if (t > cap) return fail(ctx, HB_ERR_INVALID_ARG, "pair capacity too small");
+    if (t > 0) {
+        if (!pairs) return fail(ctx, HB_ERR_INVALID_ARG, "pairs is NULL");
+        k1_fill_pairs(a, n_a, b, n_b, n_words, mode, cont_spin, max_degree, lower, row_ptr, pairs, s);
+    }
+    CK(cudaGetLastError());
+    return HB_OK;
+}
+
+extern "C" const char *hb_last_error(const hb_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+extern "C" void hb_destroy(hb_ctx *ctx) {
+    if (!ctx) return;
+    for (void *p : ctx->allocs) cudaFree(p);
+    for (int i = 0; i < 4; ++i)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    release_mixed(ctx);
+    delete ctx;
+}

@@ -1,0 +1,78 @@
+// The context behind the C ABI (host side).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "hb_internal.cuh"
+
+namespace hb {
+
+struct GroupInfo {
+    int ndet = 0, ns = 0, cf = 0, cn = 0;
+    int64_t det_off = 0, ci_off = 0, row_off = 0;
+};
+
+// Scratch of one target-group pair (g >= g'), classes 1, 3, 5, 6, 7.
+struct GroupPair {
+    int g = 0, gp = 0, same = 0;
+    int64_t n_pairs = 0, n_items = 0;
+    int n_chunks = 0, n_nn = 0;
+    int64_t *rowptr = nullptr;
+    hb_pair *pairs = nullptr;
+    double *val = nullptr;
+    int64_t *item_ptr = nullptr;
+    GammaItem *items = nullptr;
+    int32_t *order = nullptr;
+    int64_t *sort_off = nullptr, *sort_cur = nullptr;
+    double *gamma = nullptr, *W = nullptr, *partial = nullptr, *S = nullptr, *E = nullptr;
+    int32_t *nn = nullptr;
+    double *A = nullptr;        // [n_nn][Kpad] contracted coefficients
+};
+
+// Scratch of one target group against the L2 functions (class 4).
+struct GroupL2 {
+    int64_t *rowptr = nullptr;
+    hb_pair *pairs = nullptr;
+    int64_t n_pairs = 0;
+};
+
+struct MixedState;   // split-precision operands (k_split.cu)
+
+}  // namespace hb
+
+struct hb_ctx {
+    std::string err;
+    int device = 0;
+    int n_to = 0, n_co = 0, n_orb = 0, n_elec = 0, W = 1, cont_spin = 0, n_groups = 0, n_l2 = 0;
+    double e_core = 0.0;
+    int split_slices = 5;
+    int64_t Pt = 0;
+    int K = 0, Kpad = 0;
+    int64_t Dc = 0, dim = 0;
+    std::vector<hb::GroupInfo> groups;
+    std::vector<hb::GroupPair> gps;
+    std::vector<hb::GroupL2> gl2;
+    std::vector<void *> allocs;
+    size_t dev_bytes = 0;
+    double *h = nullptr, *tttt = nullptr, *tttc = nullptr, *jk = nullptr, *panel = nullptr;
+    uint64_t *dets = nullptr, *l2 = nullptr;
+    double *ci = nullptr;
+    int64_t *l2_rowptr = nullptr;
+    int64_t l2_nnz = 0, tt_pairs = 0, tl2_pairs = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    hb::MixedState *mixed = nullptr;
+    void *diag = nullptr;   // Davidson workspace (k_davidson.cu)
+    void *mlp = nullptr;    // learned preconditioner weights (k_mlp.cu)
+
+    hb::Ints ints() const {
+        hb::Ints I;
+        I.h = h; I.tttt = tttt; I.tttc = tttc; I.jk = jk;
+        I.n_to = n_to; I.n_co = n_co; I.n_orb = n_orb; I.Pt = Pt;
+        return I;
+    }
+};
+
+int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStream_t s);
+int expand_mixed(hb_ctx *ctx, hb::GroupPair &P, double *Hcc, cudaStream_t s);
+void release_mixed(hb_ctx *ctx);

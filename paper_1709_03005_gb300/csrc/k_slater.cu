@@ -1,0 +1,226 @@
+// K5: numeric Slater-Condon elements between target-orbital determinants
+// (classes 2 and 8, the L2 x L2 block, Section 2.2; and the target Hamiltonian
+// H^N used by the contraction of classes 1, 3, 5, 6, 7).
+//
+// diagonal : sum_i h_ii + sum_{i<k} [(ii|kk) - delta_spin (ik|ki)]
+// single   : phase * [h_ph + sum_{k common} ((ph|kk) - delta_spin (pk|kh))]
+// double   : phase * [(p1 h1|p2 h2) - (p1 h2|p2 h1)], with spin deltas
+// (the standard rules for an orthonormal spin-orbital basis; the paper
+// evaluates them symbolically, Eq. 6).  (pp|qq) and (pq|qp) come from a small
+// n_to x n_to table that stays in L1/L2; other (tt|tt) integrals are gathered.
+#include "hb_internal.cuh"
+
+namespace hb {
+
+namespace {
+
+__device__ __forceinline__ double eri4(const Ints &I, int p, int q, int r, int s) {
+    return __ldg(I.tttt + pair_idx(p, q) * I.Pt + pair_idx(r, s));
+}
+
+template <int W>
+__device__ double diag_value(const Ints &I, const uint64_t (&d)[2 * W]) {
+    const double *J = I.jk, *K = I.jk + I.n_to * I.n_to;
+    const int n = I.n_to, no = I.n_orb;
+    double e = 0.0;
+    // one-electron and same-spin / opposite-spin pair sums
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint64_t x = d[s * W + w];
+            while (x) {
+                const int p = 64 * w + __ffsll((long long)x) - 1;
+                x &= x - 1;
+                e += __ldg(I.h + (int64_t)p * no + p);
+                // pairs (p, q) with q after p in canonical order
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    if (s2 < s) continue;
+#pragma unroll
+                    for (int w2 = 0; w2 < W; ++w2) {
+                        uint64_t y = d[s2 * W + w2];
+                        if (s2 == s) {
+                            if (w2 < w) continue;
+                            if (w2 == w) y &= x;  // bits above p in the same word (x already cleared p)
+                        }
+                        while (y) {
+                            const int q = 64 * w2 + __ffsll((long long)y) - 1;
+                            y &= y - 1;
+                            e += __ldg(J + p * n + q);
+                            if (s2 == s) e -= __ldg(K + p * n + q);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    return e;
+}
+
+template <int W>
+__device__ double single_value(const Ints &I, const uint64_t (&bra)[2 * W], const uint64_t (&ket)[2 * W],
+                               int hpos, int ppos) {
+    const int sb = 64 * W;
+    const int hs = hpos / sb, h = hpos % sb, p = ppos % sb;
+    double v = __ldg(I.h + (int64_t)p * I.n_orb + h);
+    const int64_t ph = pair_idx(p, h) * I.Pt;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint64_t x = bra[s * W + w] & ket[s * W + w];
+            while (x) {
+                const int k = 64 * w + __ffsll((long long)x) - 1;
+                x &= x - 1;
+                v += __ldg(I.tttt + ph + pair_idx(k, k));
+                if (s == hs) v -= eri4(I, p, k, k, h);
+            }
+        }
+    }
+    return v;
+}
+
+__device__ __forceinline__ double double_value(const Ints &I, int W, int h1, int h2, int p1, int p2) {
+    const int sb = 64 * W;
+    double v = 0.0;
+    if (p1 / sb == h1 / sb && p2 / sb == h2 / sb) v += eri4(I, p1 % sb, h1 % sb, p2 % sb, h2 % sb);
+    if (p1 / sb == h2 / sb && p2 / sb == h1 / sb) v -= eri4(I, p1 % sb, h2 % sb, p2 % sb, h1 % sb);
+    return v;
+}
+
+template <int W>
+__device__ __forceinline__ void load_det(const uint64_t *p, uint64_t (&x)[2 * W]) {
+#pragma unroll
+    for (int i = 0; i < 2 * W; ++i) x[i] = __ldg(p + i);
+}
+
+template <int W>
+__device__ __forceinline__ int diff_bits(const uint64_t (&x)[2 * W], const uint64_t (&y)[2 * W], int (&pos)[2]) {
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < 2 * W; ++i) {
+        uint64_t m = x[i] & ~y[i];
+        while (m && n < 2) {
+            pos[n++] = 64 * i + (__ffsll((long long)m) - 1);
+            m &= m - 1;
+        }
+    }
+    return n;
+}
+
+// Full element <bra|H|ket> (same electron count), classification inline.
+template <int W>
+__device__ double element(const Ints &I, const uint64_t (&a)[2 * W], const uint64_t (&b)[2 * W], int deg) {
+    if (deg == 0) return diag_value<W>(I, a);
+    int h[2], p[2];
+    diff_bits<W>(b, a, h);
+    diff_bits<W>(a, b, p);
+    if (deg == 1) {
+        const int e = prefix_count(b, 2 * W, h[0]) + prefix_count(b, 2 * W, p[0]) - (h[0] < p[0]);
+        const double v = single_value<W>(I, a, b, h[0], p[0]);
+        return (e & 1) ? -v : v;
+    }
+    const int e = prefix_count(b, 2 * W, h[0]) + prefix_count(b, 2 * W, h[1]) - 1 + prefix_count(b, 2 * W, p[1]) -
+                  (h[0] < p[1]) - (h[1] < p[1]) + prefix_count(b, 2 * W, p[0]) - (h[0] < p[0]) - (h[1] < p[0]);
+    const double v = double_value(I, W, h[0], h[1], p[0], p[1]);
+    return (e & 1) ? -v : v;
+}
+
+constexpr int kWarps = 8;
+
+template <int W>
+__global__ void __launch_bounds__(32 * kWarps)
+l2_csr_kernel(Ints I, const uint64_t *__restrict__ D, int n, const int64_t *__restrict__ row_ptr,
+              int32_t *__restrict__ col, double *__restrict__ val, double e_core) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    if (row >= n) return;
+    uint64_t a[2 * W];
+    load_det<W>(D + (int64_t)row * 2 * W, a);
+    int64_t pos = row_ptr[row];
+    const int64_t end = row_ptr[row + 1];
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int c = c0 + lane;
+        int deg = 99;
+        uint64_t b[2 * W];
+        if (c < n) {
+            load_det<W>(D + (int64_t)c * 2 * W, b);
+            int x = 0;
+#pragma unroll
+            for (int i = 0; i < 2 * W; ++i) x += __popcll(a[i] ^ b[i]);
+            deg = x >> 1;
+        }
+        const bool ok = deg <= 2;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const int64_t at = pos + __popc(m & ((1u << lane) - 1u));
+            if (at < end) {
+                double v = element<W>(I, a, b, deg);
+                if (deg == 0) v += e_core;
+                col[at] = c;
+                val[at] = v;
+            }
+        }
+        pos += __popc(m);
+    }
+}
+
+// <A[row]|H|B[col]> for classified pairs (mode 0 records).
+template <int W>
+__global__ void pair_values_kernel(Ints I, const uint64_t *__restrict__ A, const uint64_t *__restrict__ B,
+                                   const hb_pair *__restrict__ pairs, int64_t n_pairs, double *__restrict__ val) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_pairs) return;
+    const hb_pair r = pairs[k];
+    uint64_t a[2 * W], b[2 * W];
+    load_det<W>(A + (int64_t)r.row * 2 * W, a);
+    load_det<W>(B + (int64_t)r.col * 2 * W, b);
+    double v;
+    if (r.degree == 0) v = diag_value<W>(I, a);
+    else if (r.degree == 1) v = r.phase * single_value<W>(I, a, b, r.hole[0], r.part[0]);
+    else v = r.phase * double_value(I, W, r.hole[0], r.hole[1], r.part[0], r.part[1]);
+    val[k] = v;
+}
+
+__global__ void jk_kernel(Ints I, double *jk) {
+    const int n = I.n_to;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * n) return;
+    const int p = t / n, q = t % n;
+    jk[t] = eri4(I, p, p, q, q);
+    jk[n * n + t] = eri4(I, p, q, q, p);
+}
+
+}  // namespace
+
+void build_jk(const Ints &I, double *jk, cudaStream_t s) {
+    const int n = I.n_to * I.n_to;
+    jk_kernel<<<(n + 255) / 256, 256, 0, s>>>(I, jk);
+}
+
+void l2_csr_fill(const Ints &I, const uint64_t *dets, int n, int W, const int64_t *row_ptr, int32_t *col,
+                 double *val, double e_core, cudaStream_t s) {
+    if (n <= 0) return;
+    const dim3 grid((n + kWarps - 1) / kWarps), block(32 * kWarps);
+    switch (W) {
+        case 1: l2_csr_kernel<1><<<grid, block, 0, s>>>(I, dets, n, row_ptr, col, val, e_core); break;
+        case 2: l2_csr_kernel<2><<<grid, block, 0, s>>>(I, dets, n, row_ptr, col, val, e_core); break;
+        case 3: l2_csr_kernel<3><<<grid, block, 0, s>>>(I, dets, n, row_ptr, col, val, e_core); break;
+        default: l2_csr_kernel<4><<<grid, block, 0, s>>>(I, dets, n, row_ptr, col, val, e_core); break;
+    }
+}
+
+void pair_values(const Ints &I, const uint64_t *A, const uint64_t *B, int W, const hb_pair *pairs,
+                 int64_t n_pairs, double *val, cudaStream_t s) {
+    if (n_pairs <= 0) return;
+    const int grid = (int)((n_pairs + 255) / 256);
+    switch (W) {
+        case 1: pair_values_kernel<1><<<grid, 256, 0, s>>>(I, A, B, pairs, n_pairs, val); break;
+        case 2: pair_values_kernel<2><<<grid, 256, 0, s>>>(I, A, B, pairs, n_pairs, val); break;
+        case 3: pair_values_kernel<3><<<grid, 256, 0, s>>>(I, A, B, pairs, n_pairs, val); break;
+        default: pair_values_kernel<4><<<grid, 256, 0, s>>>(I, A, B, pairs, n_pairs, val); break;
+    }
+}
+
+}  // namespace hb

@@ -1,0 +1,279 @@
+"""Python binding of the C ABI in include/hb.h (argument marshalling only).
+
+Every function here forwards to libhb.so; there is no CPU fallback.  If the
+library has not been built, `load()` raises.  Device memory for results comes
+from PyTorch tensors; streams are PyTorch CUDA streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HB_OK, HB_ERR_INVALID_ARG, HB_ERR_CUDA, HB_ERR_OOM, HB_ERR_TIMEOUT, HB_ERR_NOT_CONVERGED, \
+    HB_ERR_UNSUPPORTED = range(7)
+HB_FP64, HB_MIXED = 0, 1
+HB_PRECOND_DIAG, HB_PRECOND_MLP = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhb.so")
+
+
+class hb_group(C.Structure):
+    _fields_ = [("n_det", C.c_int32), ("n_state", C.c_int32), ("dets", C.c_void_p), ("ci", C.c_void_p),
+                ("cont_first", C.c_int32), ("cont_count", C.c_int32)]
+
+
+class hb_problem(C.Structure):
+    _fields_ = [("n_to", C.c_int32), ("n_co", C.c_int32), ("n_elec", C.c_int32), ("n_words", C.c_int32),
+                ("cont_spin", C.c_int32), ("h", C.c_void_p), ("eri_tttt", C.c_void_p),
+                ("eri_tttc", C.c_void_p), ("eri_ttcc", C.c_void_p), ("eri_tctc", C.c_void_p),
+                ("n_groups", C.c_int32), ("groups", C.c_void_p), ("n_l2", C.c_int32),
+                ("l2_dets", C.c_void_p), ("e_core", C.c_double)]
+
+
+class hb_options(C.Structure):
+    _fields_ = [("split_slices", C.c_int32), ("validate", C.c_int32), ("reserved", C.c_int32 * 14)]
+
+
+class hb_layout(C.Structure):
+    _fields_ = [("dim", C.c_int64), ("contracted_dim", C.c_int64), ("n_l2", C.c_int64), ("l2_nnz", C.c_int64),
+                ("tt_pairs", C.c_int64), ("tl2_pairs", C.c_int64), ("n_labels", C.c_int64),
+                ("device_bytes", C.c_int64), ("n_groups", C.c_int32), ("n_words", C.c_int32)]
+
+
+class hb_blocks(C.Structure):
+    _fields_ = [("Hcc", C.c_void_p), ("Hlc", C.c_void_p), ("l2_row_ptr", C.c_void_p), ("l2_col", C.c_void_p),
+                ("l2_val", C.c_void_p)]
+
+
+class hb_stats(C.Structure):
+    _fields_ = [("ms_total", C.c_float), ("ms_target", C.c_float), ("ms_expand", C.c_float),
+                ("ms_class4", C.c_float), ("ms_l2", C.c_float), ("ms_expand_gemm", C.c_float),
+                ("expand_launches", C.c_int32), ("kernel_launches", C.c_int32), ("expand_flops", C.c_double),
+                ("iterations", C.c_int32), ("mlp_fallbacks", C.c_int32), ("max_residual", C.c_double),
+                ("ms_matvec", C.c_float), ("ms_rr", C.c_float), ("reserved", C.c_int32 * 8)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class hb_mlp_weights(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("width", C.c_int32), ("w1", C.c_void_p), ("b1", C.c_void_p),
+                ("w2", C.c_void_p), ("b2", C.c_void_p), ("w3", C.c_void_p), ("b3", C.c_void_p)]
+
+
+PAIR_DTYPE = np.dtype([("row", "<i4"), ("col", "<i4"), ("hole", "<i2", (2,)), ("part", "<i2", (2,)),
+                       ("degree", "i1"), ("phase", "i1"), ("pad", "<i2", (3,))])
+assert PAIR_DTYPE.itemsize == 24
+
+EXPORTS = ["hb_init", "hb_query", "hb_group_offset", "hb_build_blocks", "hb_diag", "hb_classify",
+           "hb_mlp_set", "hb_last_error", "hb_destroy"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1709_03005_gb300.build_ext.build()")
+    lib = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    P = C.POINTER
+    lib.hb_init.argtypes = [P(vp), P(hb_problem), P(hb_options), vp]
+    lib.hb_query.argtypes = [vp, P(hb_layout)]
+    lib.hb_group_offset.argtypes = [vp, i32]
+    lib.hb_group_offset.restype = i64
+    lib.hb_build_blocks.argtypes = [vp, i32, P(hb_blocks), P(hb_stats), vp]
+    lib.hb_diag.argtypes = [vp, P(hb_blocks), i32, C.c_double, i32, i32, vp, vp, vp, P(hb_stats), vp]
+    lib.hb_classify.argtypes = [vp, i32, vp, i32, i32, i32, i32, i32, i32, vp, vp, i64, P(i64), vp]
+    lib.hb_mlp_set.argtypes = [vp, P(hb_mlp_weights)]
+    lib.hb_last_error.argtypes = [vp]
+    lib.hb_last_error.restype = C.c_char_p
+    lib.hb_destroy.argtypes = [vp]
+    lib.hb_destroy.restype = None
+    for name in ["hb_init", "hb_query", "hb_build_blocks", "hb_diag", "hb_classify", "hb_mlp_set"]:
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class HBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hb error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc, ctx=None):
+    if rc != HB_OK:
+        msg = load().hb_last_error(ctx)
+        raise HBError(rc, msg.decode() if msg else "")
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+# --------------------------------------------------------------------------
+# the build
+# --------------------------------------------------------------------------
+
+class Hamiltonian:
+    """A staged problem (hb_init) whose blocks can be built and diagonalised.
+
+    `problem` is any object with the fields of hb_problem (synth.Problem fits):
+    n_to, n_co, n_elec, n_words, cont_spin, h, eri_*, groups (dets, ci,
+    cont_first, cont_count), l2_dets, e_core.
+    """
+
+    def __init__(self, problem, split_slices=0, validate=True, stream=None):
+        import torch
+        self.lib = load()
+        p = problem
+        keep = []
+
+        def arr(x, dt):
+            a = np.ascontiguousarray(x, dtype=dt)
+            keep.append(a)
+            return a
+
+        gs = (hb_group * max(1, len(p.groups)))()
+        for i, g in enumerate(p.groups):
+            d = arr(g.dets, np.uint64)
+            c = arr(g.ci, np.float64)
+            gs[i] = hb_group(d.shape[0], c.shape[1], d.ctypes.data, c.ctypes.data, g.cont_first, g.cont_count)
+        ptr = lambda a: a.ctypes.data
+        l2 = arr(p.l2_dets, np.uint64) if p.l2_dets.shape[0] else None
+        self._problem = hb_problem(p.n_to, p.n_co, p.n_elec, p.n_words, p.cont_spin,
+                                   ptr(arr(p.h, np.float64)), ptr(arr(p.eri_tttt, np.float64)),
+                                   ptr(arr(p.eri_tttc, np.float64)), ptr(arr(p.eri_ttcc, np.float64)),
+                                   ptr(arr(p.eri_tctc, np.float64)), len(p.groups), C.addressof(gs),
+                                   p.l2_dets.shape[0], ptr(l2) if l2 is not None else None, float(p.e_core))
+        opts = hb_options(split_slices, 1 if validate else 0)
+        self.ctx = C.c_void_p()
+        torch.cuda.init()
+        rc = self.lib.hb_init(C.byref(self.ctx), C.byref(self._problem), C.byref(opts), _stream_handle(stream))
+        del keep, gs
+        if rc != HB_OK:
+            msg = self.lib.hb_last_error(None)
+            raise HBError(rc, msg.decode() if msg else "")
+        self.layout = hb_layout()
+        _check(self.lib.hb_query(self.ctx, C.byref(self.layout)), self.ctx)
+        self.group_offsets = [self.lib.hb_group_offset(self.ctx, g) for g in range(len(p.groups) + 1)]
+
+    # sizes
+    @property
+    def dim(self):
+        return self.layout.dim
+
+    @property
+    def contracted_dim(self):
+        return self.layout.contracted_dim
+
+    def allocate(self, device="cuda"):
+        import torch
+        L = self.layout
+        Dc, nl = L.contracted_dim, L.n_l2
+        return dict(
+            Hcc=torch.zeros((Dc, Dc), dtype=torch.float64, device=device),
+            Hlc=torch.zeros((nl, Dc), dtype=torch.float64, device=device),
+            row_ptr=torch.zeros(nl + 1, dtype=torch.int64, device=device),
+            col=torch.zeros(max(L.l2_nnz, 1), dtype=torch.int32, device=device),
+            val=torch.zeros(max(L.l2_nnz, 1), dtype=torch.float64, device=device),
+        )
+
+    @staticmethod
+    def blocks_struct(b):
+        return hb_blocks(b["Hcc"].data_ptr(), b["Hlc"].data_ptr(), b["row_ptr"].data_ptr(),
+                         b["col"].data_ptr(), b["val"].data_ptr())
+
+    def build(self, precision=HB_FP64, blocks=None, stream=None, stats=True):
+        b = blocks if blocks is not None else self.allocate()
+        bs = self.blocks_struct(b)
+        st = hb_stats()
+        _check(self.lib.hb_build_blocks(self.ctx, precision, C.byref(bs), C.byref(st) if stats else None,
+                                        _stream_handle(stream)), self.ctx)
+        return b, st
+
+    def diag(self, blocks, k, tol=1e-8, max_iter=200, precond=HB_PRECOND_DIAG, v0=None, evecs=None,
+             stream=None, allow_not_converged=False):
+        evals = np.zeros(k)
+        bs = self.blocks_struct(blocks)
+        st = hb_stats()
+        rc = self.lib.hb_diag(self.ctx, C.byref(bs), k, tol, max_iter, precond, _ptr(v0),
+                              evals.ctypes.data, _ptr(evecs), C.byref(st), _stream_handle(stream))
+        if rc == HB_ERR_NOT_CONVERGED and allow_not_converged:
+            return evals, st, False
+        _check(rc, self.ctx)
+        return evals, st, True
+
+    def set_mlp(self, w1, b1, w2, b2, w3, b3):
+        arrs = [np.ascontiguousarray(a, np.float32) for a in (w1, b1, w2, b2, w3, b3)]
+        w = hb_mlp_weights(arrs[0].shape[1], arrs[0].shape[0], *[a.ctypes.data for a in arrs])
+        _check(self.lib.hb_mlp_set(self.ctx, C.byref(w)), self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            self.lib.hb_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dense_from_blocks(b, dim=None):
+    """Assemble the full symmetric matrix from the blocks (torch, on device)."""
+    import torch
+    Hcc, Hlc = b["Hcc"], b["Hlc"]
+    Dc, nl = Hcc.shape[0], Hlc.shape[0]
+    H = torch.zeros((Dc + nl, Dc + nl), dtype=torch.float64, device=Hcc.device)
+    H[:Dc, :Dc] = Hcc
+    H[Dc:, :Dc] = Hlc
+    H[:Dc, Dc:] = Hlc.T
+    if nl:
+        rp = b["row_ptr"].to(torch.int64)
+        counts = rp[1:] - rp[:-1]
+        rows = torch.repeat_interleave(torch.arange(nl, device=Hcc.device), counts)
+        nnz = int(rp[-1])
+        H[Dc + rows, Dc + b["col"][:nnz].to(torch.int64)] = b["val"][:nnz]
+    return H
+
+
+# --------------------------------------------------------------------------
+# excitation classification
+# --------------------------------------------------------------------------
+
+def classify(a, b, n_words, mode=0, cont_spin=0, max_degree=2, lower=False, cap=None, stream=None):
+    """hb_classify on device uint64 tensors a [n_a, 2W], b [n_b, 2W].
+
+    Returns (row_ptr [n_a+1] int64 tensor, records as a numpy structured array).
+    """
+    import torch
+    lib = load()
+    n_a, n_b = a.shape[0], b.shape[0]
+    row_ptr = torch.zeros(n_a + 1, dtype=torch.int64, device=a.device)
+    total = C.c_int64()
+    rc = lib.hb_classify(_ptr(a), n_a, _ptr(b), n_b, n_words, mode, cont_spin, max_degree, 1 if lower else 0,
+                         _ptr(row_ptr), None, 0, C.byref(total), _stream_handle(stream))
+    if rc not in (HB_OK, HB_ERR_INVALID_ARG) or (rc == HB_ERR_INVALID_ARG and total.value == 0):
+        _check(rc)
+    n = total.value if cap is None else cap
+    pairs = torch.zeros(max(n, 1) * PAIR_DTYPE.itemsize, dtype=torch.uint8, device=a.device)
+    _check(lib.hb_classify(_ptr(a), n_a, _ptr(b), n_b, n_words, mode, cont_spin, max_degree, 1 if lower else 0,
+                           _ptr(row_ptr), _ptr(pairs), n, C.byref(total), _stream_handle(stream)))
+    torch.cuda.synchronize()
+    rec = np.frombuffer(pairs.cpu().numpy().tobytes(), dtype=PAIR_DTYPE)[: total.value]
+    return row_ptr, rec
