@@ -1,0 +1,288 @@
+"""Benchmark of the Hamiltonian build (and Davidson) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config c2] [--precision mixed|fp64]
+
+One step is one build of every class of the close-coupling Hamiltonian
+(hb_build_blocks) for the medium workload (30 target + 150 continuum orbitals,
+N = 10 + 1 electrons, 2000 target determinants, 20 target states, 5000 L2
+functions, dimension 8000), with the integrals already resident on the device.
+The metric is H elements per second: dim(dim+1)/2 lower-triangle positions per
+build (the positions the paper's whole-matrix timings cover).  Davidson (lowest
+20 eigenpairs to a residual of 1e-8) is timed after the build steps and
+reported under "davidson".
+
+Prints one JSON line (rank 0).  Under torchrun every rank builds its own
+replica (independent problem, no data-path collective) and the time is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIG_TEXT = {
+    "c1": "c1_tiny: 10 target + 20 continuum orbitals, N=6+1, 40 target dets, 3 states, 50 L2, dim 110",
+    "c2": "c2_medium: 30 target + 150 continuum orbitals, N=10+1, 2000 target dets, 20 states, 5000 L2, dim 8000",
+    "c3": "c3_precision: 40 target + 400 continuum orbitals, N=14+1, 20000 target dets, 50 states, 30000 L2, "
+          "dim 50000",
+}
+
+
+def positions(dim):
+    return dim * (dim + 1) / 2
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[0])); mx.append(float(f[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp64_alu_peak_tflops():
+    # GB300 nominal FP64 1.25 TFLOP/s = 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+    return 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def cpu_baseline(problem, budget_s=30.0):
+    """Time the oracle (as it stands) on this host's cores on the same workload."""
+    from oracle import coracle
+    o = coracle.Oracle(problem)
+    t0 = time.perf_counter()
+    covered = 0.0
+    off = o.offsets
+    for g in range(len(problem.groups)):
+        for gp in range(g + 1):
+            o.cc_block(g, gp)
+            covered += (off[g + 1] - off[g]) * (off[gp + 1] - off[gp]) if g != gp else \
+                positions(off[g + 1] - off[g])
+            if time.perf_counter() - t0 > budget_s:
+                break
+    nl = problem.n_l2
+    if nl:
+        o.class4_rows(0, nl)
+        covered += nl * o.Dc
+        o.l2_csr()
+        covered += positions(nl)
+    dt = time.perf_counter() - t0
+    return {"value": covered / dt, "unit": "H elements/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"whole workload: every block of the {problem.name} matrix once "
+                      f"({covered:.3e} positions, {dt:.2f} s)"}
+
+
+def run_reference(args, rank, world):
+    from paper_1709_03005_gb300 import synth
+    if rank != 0:
+        return
+    P = synth.make_config(args.config)
+    for _ in range(args.warmup):
+        cpu_baseline(P)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(P))
+    dt = time.perf_counter() - t0
+    v = float(np.mean([x["value"] for x in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    print(json.dumps({"metric": "H elements/sec", "value": v, "unit": "H elements/s", "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1),
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "impl": "reference",
+                      "config": {"workload": CONFIG_TEXT.get(args.config, args.config)},
+                      "cpu_baseline": cb, "e2e": {"value": v, "unit": "H elements/s", "h2d_bytes_per_step": 0,
+                                                  "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1709_03005_gb300 import build_ext, hb, synth
+    torch.cuda.set_device(local_rank)
+    build_ext.build()
+    precision = hb.HB_MIXED if args.precision == "mixed" else hb.HB_FP64
+    P = synth.make_config(args.config)
+    dim = P.dim
+    H = hb.Hamiltonian(P)
+    blocks = H.allocate()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    for _ in range(args.warmup):
+        H.build(precision, blocks)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    times, exp_ms, launches, flops_exp = [], [], 0, 0.0
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = H.build(precision, blocks)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            exp_ms.append(st.ms_expand)
+            launches += st.kernel_launches
+            flops_exp = st.expand_flops
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = float(np.sum(times))
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * args.steps * positions(dim) / (total_ms / 1000.0)
+
+    # end to end through the public API with host buffers: staging (H2D of the
+    # problem), build, and the D2H read of every block, each step
+    e2e_steps = max(1, min(args.steps, 3))
+    h2d = sum(np.asarray(a).nbytes for a in (P.h, P.eri_tttt, P.eri_tttc, P.eri_ttcc, P.eri_tctc, P.l2_dets)) + \
+        sum(g.dets.nbytes + g.ci.nbytes for g in P.groups)
+    d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        H2 = hb.Hamiltonian(P, validate=False)
+        b2, _ = H2.build(precision)
+        host = {k: v.cpu() for k, v in b2.items()}
+        d2h = sum(v.numel() * v.element_size() for v in host.values())
+        H2.close()
+        del b2
+    torch.cuda.synchronize()
+    e2e_value = world * e2e_steps * positions(dim) / (time.perf_counter() - t0)
+
+    # Davidson after the timed build steps
+    davidson = None
+    if args.davidson_k > 0:
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev, dst, ok = H.diag(blocks, args.davidson_k, 1e-8, 400, allow_not_converged=True)
+            torch.cuda.synchronize()
+            davidson = {"k": args.davidson_k, "tol": 1e-8, "seconds": time.perf_counter() - t0,
+                        "iterations": dst.iterations, "converged": ok, "max_residual": dst.max_residual}
+        except hb.HBError as e:
+            davidson = {"unavailable": str(e)}
+
+    peaks = measured_peaks()
+    avg_exp_ms = float(np.mean(exp_ms)) if exp_ms else None
+    if precision == hb.HB_MIXED:
+        peak = peaks.get("bf16_tflops")
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak, "peak_source": "measured bf16 burst"}
+    else:
+        peak = fp64_alu_peak_tflops()
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                "peak_source": "derived FP64 peak: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"}
+    achieved = flops_exp / (avg_exp_ms / 1000.0) / 1e12 if avg_exp_ms else None
+    roof.update({"kernel": "expansion contraction (Eq. 7)", "achieved": achieved,
+                 "frac": achieved / roof["peak"] if achieved and roof["peak"] else None,
+                 "traffic": None, "flops_per_launch": flops_exp})
+
+    if rank == 0:
+        cb = cpu_baseline(P) if args.cpu_baseline else None
+        out = {"metric": "H elements/sec", "value": value, "unit": "H elements/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "mixed-bf16x5/f32->f64" if precision == hb.HB_MIXED else "f64", "data": "synthetic",
+               "config": {"workload": CONFIG_TEXT.get(args.config, args.config), "dim": dim,
+                          "positions": positions(dim), "l2_flush": "256 MB write between timed steps",
+                          "parallelism": f"replicas x{world}", "precision": args.precision},
+               "roofline": roof, "cpu_baseline": cb,
+               "e2e": {"value": e2e_value, "unit": "H elements/s", "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h)},
+               "gpu_launches": launches, "clocks": clk.summary(), "davidson": davidson,
+               "stages_ms": {"target": st.ms_target, "expand": st.ms_expand, "class4": st.ms_class4,
+                             "l2": st.ms_l2}}
+        print(json.dumps(out), flush=True)
+    H.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--davidson-k", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -67,6 +67,8 @@ def load():
         lib.orc_contracted_dim.argtypes = [vp]
         lib.orc_build_dense.argtypes = [vp, vp]
         lib.orc_l2_csr.argtypes = [vp, vp, vp, vp]
+        lib.orc_l2_rows.argtypes = [vp, C.c_int, C.c_int, vp]
+        lib.orc_class4_rows.argtypes = [vp, C.c_int, C.c_int, vp]
         _lib = lib
     return _lib
 
@@ -152,6 +154,27 @@ class Oracle:
 
     def l2_element(self, a, b) -> float:
         return self.lib.orc_l2_element(self.sp, int(a), int(b))
+
+    def l2_rows(self, a0, a1) -> np.ndarray:
+        out = np.zeros((max(a1 - a0, 1), max(self.problem.n_l2, 1)))
+        self.lib.orc_l2_rows(self.sp, int(a0), int(a1), _ptr(out))
+        return out[: a1 - a0, : self.problem.n_l2]
+
+    def class4_rows(self, l0, l1) -> np.ndarray:
+        out = np.zeros((max(l1 - l0, 1), max(self.Dc, 1)))
+        self.lib.orc_class4_rows(self.sp, int(l0), int(l1), _ptr(out))
+        return out[: l1 - l0, : self.Dc]
+
+    def cc_block(self, g, gp) -> np.ndarray:
+        """Contract and expand one group-pair block (Eq. 8 then Eq. 7)."""
+        rows = int(self.g_nstate[g] * self.g_ccount[g])
+        cols = int(self.g_nstate[gp] * self.g_ccount[gp])
+        n = rows + cols
+        H = np.zeros((n, n))
+        cc = self.lib.orc_cc_contract(self.sp, int(g), int(gp))
+        self.lib.orc_cc_expand(cc, _ptr(H), n, 0, rows if g != gp else 0)
+        self.lib.orc_cc_free(cc)
+        return H[:rows, rows:] if g != gp else H[:rows, :rows]
 
     def l2_csr(self):
         nl = self.problem.n_l2

@@ -642,3 +642,24 @@ void orc_l2_csr(const orc_problem *P, int64_t *row_ptr, int32_t *cols, double *v
         }
     }
 }
+
+/* Dense rows [a0, a1) of the L2 x L2 block (row-major, n_l2 columns). */
+void orc_l2_rows(const orc_problem *P, int a0, int a1, double *out) {
+    const int nl = P->n_l2;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int a = a0; a < a1; ++a) {
+        const int W = P->W;
+        for (int b = 0; b < nl; ++b) {
+            int nd = 0;
+            for (int w = 0; w < 2 * W; ++w) nd += popc64(P->l2[(int64_t)a * 2 * W + w] ^ P->l2[(int64_t)b * 2 * W + w]);
+            out[(int64_t)(a - a0) * nl + b] = nd <= 4 ? orc_l2_element(P, a, b) : 0.0;
+        }
+    }
+}
+
+/* Class-4 rows [l0, l1) into out[(l - l0) * Dc + c]. */
+void orc_class4_rows(const orc_problem *P, int l0, int l1, double *out) {
+    const int64_t Dc = orc_contracted_dim(P);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int l = l0; l < l1; ++l) orc_class4_row(P, l, out + (int64_t)(l - l0) * Dc);
+}
