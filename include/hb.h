@@ -203,6 +203,25 @@ int hb_classify(const uint64_t *a, int32_t n_a, const uint64_t *b, int32_t n_b,
                 int32_t lower, int64_t *row_ptr, hb_pair *pairs, int64_t cap,
                 int64_t *total, void *stream);
 
+/* Allocation-free variant of hb_classify.  The paper has no counterpart: it
+   exists for callers that cannot allocate device memory (a host framework
+   that owns the allocator, a plug-in that may not call cudaMalloc after
+   start-up, a real-time loop that cannot afford an allocation's implicit
+   synchronisation) and so cannot provide hb_classify's row_ptr buffer.  The
+   row offsets live instead in a static device array of HB_NOALLOC_MAX_ROWS + 1
+   int64 values (2 MiB) that every GPU loading the library holds until the
+   process exits.  Same arguments and results as hb_classify without row_ptr;
+   n_a > HB_NOALLOC_MAX_ROWS returns HB_ERR_INVALID_ARG.  The function calls no
+   allocating routine.  Its first call on a device looks up the array's device
+   address (cudaGetSymbolAddress) with that device current; make that first
+   call before any stream capture.  All calls share the array, so calls whose
+   work overlaps on the GPU race: serialise them.  Errors are reported through
+   hb_last_error(NULL). */
+#define HB_NOALLOC_MAX_ROWS 262144
+int hb_classify_noalloc(const uint64_t *a, int32_t n_a, const uint64_t *b, int32_t n_b,
+                        int32_t n_words, int32_t mode, int32_t cont_spin, int32_t max_degree,
+                        int32_t lower, hb_pair *pairs, int64_t cap, int64_t *total, void *stream);
+
 /* ---- learned Davidson preconditioner (a small MLP, not in the paper) ---- */
 
 typedef struct {

@@ -10,9 +10,11 @@
 
 using namespace hb;
 
-namespace {
+namespace hb {
 thread_local std::string g_last_error;
+}
 
+namespace {
 int fail(hb_ctx *ctx, int code, const std::string &msg) {
     if (ctx) ctx->err = msg;
     g_last_error = msg;

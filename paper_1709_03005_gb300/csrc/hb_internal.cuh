@@ -13,6 +13,9 @@
 
 namespace hb {
 
+// message behind hb_last_error(NULL)
+extern thread_local std::string g_last_error;
+
 // ---------------------------------------------------------------- bit helpers
 __host__ __device__ inline int64_t pair_idx(int p, int q) {
     return p >= q ? (int64_t)p * (p + 1) / 2 + q : (int64_t)q * (q + 1) / 2 + p;

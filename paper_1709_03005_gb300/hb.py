@@ -15,6 +15,7 @@ HB_OK, HB_ERR_INVALID_ARG, HB_ERR_CUDA, HB_ERR_OOM, HB_ERR_TIMEOUT, HB_ERR_NOT_C
     HB_ERR_UNSUPPORTED = range(7)
 HB_FP64, HB_MIXED = 0, 1
 HB_PRECOND_DIAG, HB_PRECOND_MLP = 0, 1
+HB_NOALLOC_MAX_ROWS = 262144
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhb.so")
@@ -69,7 +70,7 @@ PAIR_DTYPE = np.dtype([("row", "<i4"), ("col", "<i4"), ("hole", "<i2", (2,)), ("
 assert PAIR_DTYPE.itemsize == 24
 
 EXPORTS = ["hb_init", "hb_query", "hb_group_offset", "hb_build_blocks", "hb_diag", "hb_classify",
-           "hb_mlp_set", "hb_last_error", "hb_destroy"]
+           "hb_classify_noalloc", "hb_mlp_set", "hb_last_error", "hb_destroy"]
 
 _lib = None
 
@@ -277,3 +278,26 @@ def classify(a, b, n_words, mode=0, cont_spin=0, max_degree=2, lower=False, cap=
     torch.cuda.synchronize()
     rec = np.frombuffer(pairs.cpu().numpy().tobytes(), dtype=PAIR_DTYPE)[: total.value]
     return row_ptr, rec
+
+
+def classify_noalloc(a, b, n_words, mode=0, cont_spin=0, max_degree=2, lower=False, pairs=None, stream=None):
+    """hb_classify_noalloc on device uint64 tensors a [n_a, 2W], b [n_b, 2W].
+
+    For callers that cannot allocate device memory: the row offsets live in the
+    library's static device buffer (at most HB_NOALLOC_MAX_ROWS rows of a) and
+    the caller provides the output buffer `pairs` (a uint8 device tensor of
+    cap * 24 bytes).  Returns (number of pairs, records as a numpy array).
+    """
+    import torch
+    lib = load()
+    fn = lib.hb_classify_noalloc
+    fn.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                   C.c_int32, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]
+    fn.restype = C.c_int
+    cap = pairs.numel() // PAIR_DTYPE.itemsize
+    total = C.c_int64()
+    _check(fn(_ptr(a), a.shape[0], _ptr(b), b.shape[0], n_words, mode, cont_spin, max_degree, 1 if lower else 0,
+              _ptr(pairs), cap, C.byref(total), _stream_handle(stream)))
+    torch.cuda.synchronize()
+    rec = np.frombuffer(pairs.cpu().numpy().tobytes(), dtype=PAIR_DTYPE)[: total.value]
+    return total.value, rec
