@@ -103,7 +103,7 @@ typedef struct {
 } hb_problem;
 
 typedef struct {
-    int32_t split_slices;     /* mixed path: bf16 slices per operand, 0 = default (5) */
+    int32_t split_slices;     /* mixed path: bf16 slices per operand (2..6), 0 = default (6) */
     int32_t validate;         /* 0 = skip the O(n^2) input checks */
     int32_t reserved[14];
 } hb_options;

@@ -68,6 +68,9 @@ def load():
         lib.orc_build_dense.argtypes = [vp, vp]
         lib.orc_l2_csr.argtypes = [vp, vp, vp, vp]
         lib.orc_l2_rows.argtypes = [vp, C.c_int, C.c_int, vp]
+        lib.orc_cc_element_abs.restype = dbl
+        lib.orc_cc_element_abs.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+        lib.orc_cc_expand_abs.argtypes = [vp, vp, i64, i64, i64]
         lib.orc_class4_rows.argtypes = [vp, C.c_int, C.c_int, vp]
         _lib = lib
     return _lib
@@ -165,6 +168,16 @@ class Oracle:
         self.lib.orc_class4_rows(self.sp, int(l0), int(l1), _ptr(out))
         return out[: l1 - l0, : self.Dc]
 
+    def cc_condition(self) -> np.ndarray:
+        """Dc x Dc matrix of sum_b |D^b X(I^b)| for every continuum element."""
+        H = np.zeros((self.Dc, self.Dc))
+        for g in range(len(self.problem.groups)):
+            for gp in range(g + 1):
+                cc = self.lib.orc_cc_contract(self.sp, g, gp)
+                self.lib.orc_cc_expand_abs(cc, _ptr(H), self.Dc, int(self.offsets[g]), int(self.offsets[gp]))
+                self.lib.orc_cc_free(cc)
+        return H
+
     def cc_block(self, g, gp) -> np.ndarray:
         """Contract and expand one group-pair block (Eq. 8 then Eq. 7)."""
         rows = int(self.g_nstate[g] * self.g_ccount[g])
@@ -194,6 +207,9 @@ class _CC:
     def element(self, n, j, np_, jp) -> float:
         """Continuum indices j, jp are 0-based within the continuum."""
         return self.orc.lib.orc_cc_element(self.h, n, j, np_, jp)
+
+    def element_abs(self, n, j, np_, jp) -> float:
+        return self.orc.lib.orc_cc_element_abs(self.h, n, j, np_, jp)
 
     def nlabels(self, which=0):
         return self.orc.lib.orc_cc_nlabels(self.h, which)

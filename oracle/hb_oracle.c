@@ -663,3 +663,46 @@ void orc_class4_rows(const orc_problem *P, int l0, int l1, double *out) {
 #pragma omp parallel for schedule(dynamic, 4)
     for (int l = l0; l < l1; ++l) orc_class4_row(P, l, out + (int64_t)(l - l0) * Dc);
 }
+
+/* Condition scale of a contracted continuum element: sum over labels of
+   |D^b X(I^b)| (Eq. 7 with absolute values).  This is the natural size of the
+   rounding error of any finite-precision evaluation of the sum. */
+double orc_cc_element_abs(const orc_cc *c, int n, int j, int np, int jp) {
+    const orc_problem *P = c->P;
+    const int ph = P->n_to, phk = P->n_to + 1, t = n * c->nsp + np;
+    const int jg = P->n_to + j, jpg = P->n_to + jp;
+    double v = 0.0;
+    if (j == jp) {
+        v = fabs(c->K0[t]);
+        for (int64_t i = 0; i < c->same.cap; ++i) {
+            int s = c->same.slot[i];
+            if (s < 0) continue;
+            v += fabs(c->same.blocks[(int64_t)s * c->same.bsz + t] * orc_X(P, c->same.keys[i], ph, jg, -1, 0));
+        }
+    } else {
+        for (int64_t i = 0; i < c->diff.cap; ++i) {
+            int s = c->diff.slot[i];
+            if (s < 0) continue;
+            v += fabs(c->diff.blocks[(int64_t)s * c->diff.bsz + t] * orc_X(P, c->diff.keys[i], ph, jg, phk, jpg));
+        }
+    }
+    return v;
+}
+
+/* The same for a whole group-pair block, written like orc_cc_expand. */
+void orc_cc_expand_abs(const orc_cc *c, double *H, int64_t ld, int64_t row0, int64_t col0) {
+    const orc_problem *P = c->P;
+    const int cfg = P->g_cfirst[c->g], cng = P->g_ccount[c->g];
+    const int cfp = P->g_cfirst[c->gp], cnp = P->g_ccount[c->gp];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int jj = 0; jj < cng; ++jj)
+        for (int jjp = 0; jjp < cnp; ++jjp)
+            for (int n = 0; n < c->ns; ++n)
+                for (int np = 0; np < c->nsp; ++np) {
+                    int64_t r = row0 + (int64_t)n * cng + jj, cl = col0 + (int64_t)np * cnp + jjp;
+                    if (c->g == c->gp && r < cl) continue;
+                    double v = orc_cc_element_abs(c, n, cfg + jj, np, cfp + jjp);
+                    H[r * ld + cl] = v;
+                    H[cl * ld + r] = v;
+                }
+}

@@ -192,7 +192,7 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
     ctx->n_to = p->n_to; ctx->n_co = p->n_co; ctx->n_orb = p->n_to + p->n_co;
     ctx->n_elec = p->n_elec; ctx->W = p->n_words; ctx->cont_spin = p->cont_spin;
     ctx->n_groups = p->n_groups; ctx->n_l2 = p->n_l2; ctx->e_core = p->e_core;
-    ctx->split_slices = (o && o->split_slices > 0) ? o->split_slices : 5;
+    ctx->split_slices = (o && o->split_slices > 0) ? o->split_slices : 6;
     ctx->Pt = (int64_t)p->n_to * (p->n_to + 1) / 2;
     ctx->K = (int)(ctx->Pt + (int64_t)p->n_to * p->n_to + 2);
     ctx->Kpad = (ctx->K + 63) / 64 * 64;
@@ -429,6 +429,14 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         launches += 1;
     }
     CK(cudaGetLastError());
+    if (precision == HB_MIXED) {
+        // the tensor-core kernel reports a bounded-wait timeout in a device word
+        int word = 0;
+        CK(cudaStreamSynchronize(s));
+        if (mixed_error_word(ctx, &word) != HB_OK) return fail(ctx, HB_ERR_CUDA, "reading the mixed error word");
+        if (word != 0)
+            return fail(ctx, HB_ERR_TIMEOUT, "split expansion kernel gave up waiting (code " + std::to_string(word) + ")");
+    }
     if (st) {
         cudaEvent_t end;
         CK(cudaEventCreate(&end));

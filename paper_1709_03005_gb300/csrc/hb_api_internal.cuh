@@ -76,3 +76,4 @@ struct hb_ctx {
 int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStream_t s);
 int expand_mixed(hb_ctx *ctx, hb::GroupPair &P, double *Hcc, cudaStream_t s);
 void release_mixed(hb_ctx *ctx);
+int mixed_error_word(hb_ctx *ctx, int *out);

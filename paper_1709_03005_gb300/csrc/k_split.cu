@@ -1,9 +1,660 @@
-// Split-precision expansion (placeholder until the tensor-core kernel lands).
+// Split-precision expansion (Eq. 7) on the 5th-generation tensor cores.
+//
+//   out[(j,j'), (n,n')] = sum_k P[(j,j')][k] * A[(n,n')][k]
+//
+// Both FP64 operands are split row by row into S bf16 slices (an error-free
+// splitting in the manner of Ozaki, Ogita, Oishi & Rump 2012): with 2^e the
+// smallest power of two above the row's largest magnitude,
+//   slice 0 = rint(x 2^{7-e}) 2^{e-7},  |integer| <= 128,
+//   slice i = rint(r_i 2^{7+7i-e}) 2^{e-7-7i}, |integer| <= 64  (i >= 1),
+// with r_i the remainder after slices 0..i-1, so S slices carry 7S bits.  The
+// row exponent is folded into the slice values, so every product of slice i of
+// a panel row with slice l of a coefficient row is an integer multiple of the
+// same unit 2^{e_row + e_col - 14 - 7(i+l)}.  The products with the same
+// s = i + l are summed by tcgen05.mma (kind::f16, bf16 inputs, FP32
+// accumulation in tensor memory) in K-chunks of 512: there every partial sum
+// stays below 2^24 units, so the FP32 accumulation is exact.  Separate TMEM
+// accumulators hold s = 0, 1, 2 and one holds s >= 3 (its rounding is below
+// 2^-45 of the result).  The epilogue drains the accumulators after each
+// chunk; the MMAs of the next chunk wait for that drain.  After each chunk the epilogue warps fold the four
+// accumulators into a double-float running sum (TwoSum), and at the end write
+// it as FP64.  Pairs with i + l >= S are dropped (below 2^-7S relative).
+//
+// Kernel structure (one CTA per 128 x 128 output tile, 10 warps):
+//   warp 0  TMA producer: per 64-wide K block and slice, one panel tile
+//           (128 x 64) and one coefficient tile (128 x 64), 128-byte swizzle,
+//           each slice in its own shared-memory slot with full/empty mbarriers
+//           so the MMAs start as slices land and slots refill as they free
+//   warp 1  MMA issuer (one elected thread), TMEM allocation owner
+//   warps 2-9 epilogue: TMEM -> registers, double-float accumulation, FP64 out
+//           (two warps per TMEM lane quadrant, 64 columns each)
+// Every mbarrier wait is bounded; on a timeout the kernel records an error,
+// drains its own copies and MMAs, frees TMEM and returns.
+//
+// Rows with j == j' carry h_jj and the delta_jj' E term and so have a wide
+// dynamic range; the mixed kernel skips them and an FP64 kernel computes them.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
 #include "hb_api_internal.cuh"
 
-int expand_mixed(hb_ctx *ctx, hb::GroupPair &, double *, cudaStream_t) {
-    ctx->err = "HB_MIXED is not available in this build";
-    return HB_ERR_UNSUPPORTED;
+namespace hb {
+
+struct MixedState {
+    int slices = 5;
+    int64_t panel_rows = 0;
+    __nv_bfloat16 *panel_slices = nullptr;   // [S][Kpad/64][n_co*n_co][64]
+    __nv_bfloat16 *coef_slices = nullptr;    // [S][Kpad/64][n_nn][64]
+    int64_t coef_rows = 0;
+    int *err = nullptr;                       // device error word
+    bool panel_ready = false;
+    CUtensorMap tm_panel;
+};
+
+}  // namespace hb
+
+using namespace hb;
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BKB = 64;  // tile rows, tile cols, K per block (one 128-B swizzle row)
+constexpr int KCHUNK = 512;                  // exact FP32 accumulation span
+constexpr int MAXS = 6;
+constexpr int A_TILE = BM * BKB * 2;         // 16 KB
+constexpr int B_TILE = BN * BKB * 2;         // 16 KB
+constexpr int SLOT = A_TILE + B_TILE;        // one slice of one K block (S slots in shared memory)
+constexpr int TMEM_COLS = 512;               // 4 accumulators x 128 columns
+constexpr int EPI_WARPS = 8;                 // 2 per TMEM lane quadrant
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int EPI_COLS = BN / 2;             // columns per epilogue thread
+constexpr int NTHREADS = 64 + EPI_THREADS;
+constexpr long long kSpinLimit = 1ll << 26;  // bounded waits (~seconds with backoff)
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-void release_mixed(hb_ctx *) {}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: returns false (and records `code`) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+    for (long long i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 256) __nanosleep(32);
+        // another role gave up: stop waiting (checked rarely, it is a global load)
+        if ((i & 4095) == 4095 && *(volatile int *)err != 0) return false;
+    }
+    atomicCAS(err, 0, code);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tm, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)tm), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, uint64_t *bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)tm), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+// K-major operand, 128-byte swizzle: rows of 128 B, 8-row atoms of 1024 B.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)0 << 16;                          // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;     // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
+    d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
+    return d;
+}
+
+// Slot of slice t in a K block of parity P.  Slice i of a block is last read
+// at step max(i, S-1-i) (steps follow the slices as they arrive), so in odd
+// blocks the first-needed slices go to the slots that the even block frees
+// first, and the loads of a block overlap the last steps of the one before.
+template <int S>
+__host__ __device__ constexpr int release_step(int i) { return i > S - 1 - i ? i : S - 1 - i; }
+
+template <int S>
+__host__ __device__ constexpr int slot_of(int P, int t) {
+    if (P == 0) return t;
+    // the slot whose release rank (release step, then index) is t
+    for (int i = 0; i < S; ++i) {
+        int r = 0;
+        for (int j = 0; j < S; ++j)
+            r += (release_step<S>(j) < release_step<S>(i)) || (release_step<S>(j) == release_step<S>(i) && j < i);
+        if (r == t) return i;
+    }
+    return 0;
+}
+
+// kind::f16 instruction descriptor: bf16 x bf16 -> f32, K-major A and B.
+__host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
+    return (1u << 4)                    // D format f32
+           | (1u << 7)                  // A format bf16
+           | (1u << 10)                 // B format bf16
+           | ((uint32_t)(N >> 3) << 17) // N / 8
+           | ((uint32_t)(M >> 4) << 24);// M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// double-float accumulation: (hi, lo) += x, exact TwoSum on the high part
+__device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// hi + lo as a double, with integer operations only (the FP64 pipe of this
+// part is slow).  Both are aligned into a 64-bit integer with 38 bits of
+// headroom below the larger exponent, added exactly, and the result is
+// truncated to 53 bits (relative error below 2^-52).  FP32 subnormals are
+// treated as zero.
+__device__ __forceinline__ double df_to_double(float hi, float lo) {
+    const uint32_t bh = __float_as_uint(hi), bl = __float_as_uint(lo);
+    const int eh = (int)((bh >> 23) & 0xFF), el = (int)((bl >> 23) & 0xFF);
+    long long mh = eh ? (long long)((bh & 0x7FFFFFu) | 0x800000u) : 0;
+    long long ml = el ? (long long)((bl & 0x7FFFFFu) | 0x800000u) : 0;
+    if (bh >> 31) mh = -mh;
+    if (bl >> 31) ml = -ml;
+    const int base = eh > el ? eh : el;
+    // value = (mh 2^(eh-base) + ml 2^(el-base)) * 2^(base - 150)
+    const int sh_h = 38 - (base - eh), sh_l = 38 - (base - el);
+    long long acc = 0;
+    if (mh) acc += sh_h >= 0 ? (mh << sh_h) : (sh_h > -63 ? (mh >> -sh_h) : 0);
+    if (ml) acc += sh_l >= 0 ? (ml << sh_l) : (sh_l > -63 ? (ml >> -sh_l) : 0);
+    if (acc == 0) return 0.0;
+    const unsigned long long neg = acc < 0 ? 1ull : 0ull;
+    unsigned long long u = neg ? (unsigned long long)(-acc) : (unsigned long long)acc;
+    const int lz = __clzll((long long)u);            // leading zeros, u > 0
+    const int top = 63 - lz;                          // position of the leading one
+    // normalise to 53 bits: leading one at bit 52
+    if (top > 52) u >>= (top - 52);
+    else u <<= (52 - top);
+    // exponent: value = u * 2^(top - 52) * 2^(base - 150 - 38), u in [2^52, 2^53)
+    const int e2 = top + base - 150 - 38;             // unbiased exponent of the leading one
+    const long long be = (long long)e2 + 1023;
+    if (be <= 0) return 0.0;                          // below the FP64 normal range
+    const unsigned long long bits = (neg << 63) | ((unsigned long long)be << 52) | (u & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+}
+
+struct SplitArgs {
+    int n_co, cf, cn, cfp, cnp;       // panel geometry and group ranges
+    int jpt_tiles;                     // tiles along jjp (16 each)
+    int n_nn, kblocks, slices;
+    int64_t row_off, col_off, ld;
+    int same_group;
+    const int32_t *nn;
+    double *H;
+    int *err;
+};
+
+// One K block of MMAs, fully unrolled for slot parity P: for each arriving
+// slice t, the pairs (i, l) with max(i, l) = t and i + l < S, then the commits
+// that free the slots read for the last time.
+template <int S, int P>
+__device__ __forceinline__ bool mma_block(uint64_t *full_bar, uint64_t *empty_bar, uint32_t par, uint32_t tmem,
+                                          uint64_t desc0, uint32_t idesc, uint32_t &fresh, int *err) {
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        if (!mbar_wait(&full_bar[slot_of<S>(P, t)], par, err, 4)) return false;
+        tc_fence_after();
+#pragma unroll
+        for (int i = 0; i <= t; ++i) {
+#pragma unroll
+            for (int l = 0; l <= t; ++l) {
+                if ((i == t || l == t) && i + l < S) {
+                    const int s = i + l < 3 ? i + l : 3;
+                    const uint32_t offA = (uint32_t)(slot_of<S>(P, i) * SLOT);
+                    const uint32_t offB = (uint32_t)(slot_of<S>(P, l) * SLOT + A_TILE);
+#pragma unroll
+                    for (int k = 0; k < BKB / 16; ++k) {
+                        const uint32_t acc = (fresh >> s) & 1u ? 0u : 1u;
+                        mma_bf16(tmem + s * BN, desc0 + ((offA + k * 32) >> 4), desc0 + ((offB + k * 32) >> 4), idesc,
+                                 acc);
+                        fresh &= ~(1u << s);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+            if (release_step<S>(i) == t) mma_commit(&empty_bar[slot_of<S>(P, i)]);
+    }
+    return true;
+}
+
+template <int S>
+__global__ void __launch_bounds__(NTHREADS, 1)
+split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_constant__ CUtensorMap tm_coef,
+                    SplitArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *slots = base;                                  // [S][SLOT]
+    uint64_t *full_bar = (uint64_t *)(base + S * SLOT);    // [MAXS]
+    uint64_t *empty_bar = full_bar + MAXS;                  // [MAXS]
+    uint64_t *acc_full = empty_bar + MAXS;                  // [1]
+    uint64_t *acc_empty = acc_full + 1;                     // [1]
+    uint64_t *final_bar = acc_empty + 1;                    // [1]
+    uint32_t *tmem_slot = (uint32_t *)(final_bar + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile_n = blockIdx.x, tile_m = blockIdx.y;     // N fastest: CTAs sharing a panel tile run together
+    const int jt = tile_m / a.jpt_tiles, jpt = tile_m % a.jpt_tiles;
+    const int jj0 = jt * 8, jjp0 = jpt * 16;                // within the group ranges
+    const int n0 = tile_n * BN;
+    const int kb_per_chunk = KCHUNK / BKB;
+    const int nchunks = (a.kblocks + kb_per_chunk - 1) / kb_per_chunk;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < MAXS; ++i) { mbar_init(&full_bar[i], 1); mbar_init(&empty_bar[i], 1); }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, EPI_THREADS);
+        mbar_init(final_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int kb = 0;
+            bool ok = true;
+            for (; kb < a.kblocks && ok; ++kb) {
+                for (int t = 0; t < S && ok; ++t) {
+                    const int sl = (kb & 1) ? slot_of<S>(1, t) : t;
+                    // each slot is filled once per K block: wait for its release in block kb-1
+                    if (kb > 0) ok = mbar_wait(&empty_bar[sl], (kb - 1) & 1, a.err, 1);
+                    if (!ok) break;
+                    uint8_t *sA = slots + sl * SLOT;
+                    mbar_expect_tx(&full_bar[sl], (uint32_t)SLOT);
+                    const int plane = t * a.kblocks + kb;
+                    tma_load_4d(sA, &tm_panel, &full_bar[sl], 0, a.cfp + jjp0, a.cf + jj0, plane);
+                    tma_load_3d(sA + A_TILE, &tm_coef, &full_bar[sl], 0, n0, plane);
+                }
+            }
+            // wait until this producer's copies of the last block have landed
+            if (kb > 0)
+                for (int sl = 0; sl < S; ++sl) mbar_wait(&full_bar[sl], (kb - 1) & 1, a.err, 2);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc_bf16(BM, BN);
+            const uint64_t desc0 = smem_desc_sw128(smem_u32(slots));   // + (offset >> 4) per operand tile
+            bool ok = true;
+            int kb = 0;
+            for (int c = 0; c < nchunks && ok; ++c) {
+                if (c > 0) ok = mbar_wait(acc_empty, (c - 1) & 1, a.err, 3);
+                if (!ok) break;
+                tc_fence_after();
+                const int kb_end = min(a.kblocks, (c + 1) * kb_per_chunk);
+                uint32_t fresh = 0xFu;           // accumulators not yet written in this chunk
+                for (; kb < kb_end && ok; ++kb) {
+                    if (kb & 1) ok = mma_block<S, 1>(full_bar, empty_bar, 1u, tmem, desc0, idesc, fresh, a.err);
+                    else ok = mma_block<S, 0>(full_bar, empty_bar, 0u, tmem, desc0, idesc, fresh, a.err);
+                }
+                if (ok) mma_commit(acc_full);             // accumulators of chunk c complete
+            }
+            mma_commit(final_bar);
+            mbar_wait(final_bar, 0, a.err, 5);
+        }
+    } else {
+        // ------------------------------------------------------ epilogue
+        const int ew = warp - 2;
+        const int q = warp & 3;                  // TMEM lane quadrant this warp may access
+        const int col0 = (ew >> 2) * EPI_COLS;
+        const int row = q * 32 + lane;           // tile row = TMEM lane
+        float hi[EPI_COLS], lo[EPI_COLS];
+#pragma unroll
+        for (int c = 0; c < EPI_COLS; ++c) { hi[c] = 0.0f; lo[c] = 0.0f; }
+        bool ok = true;
+        const int n_acc = S < 4 ? S : 4;         // accumulators written by the MMAs
+        for (int c = 0; c < nchunks && ok; ++c) {
+            ok = mbar_wait(acc_full, c & 1, a.err, 6);
+            if (!ok) break;
+            tc_fence_after();
+            // s = 0 and s = 1 need the exact TwoSum; s = 2 and s >= 3 are 2^-14
+            // and 2^-21 of the result, so their FP32 sum joins the low word
+#pragma unroll
+            for (int c0 = 0; c0 < EPI_COLS; c0 += 16) {
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + col0 + c0;
+                float v[16], w[16];
+                tmem_ld16(tbase, v);
+                if (n_acc > 1) tmem_ld16(tbase + BN, w);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    df_add(hi[c0 + i], lo[c0 + i], v[i]);
+                    if (n_acc > 1) df_add(hi[c0 + i], lo[c0 + i], w[i]);
+                }
+                if (n_acc > 2) {
+                    tmem_ld16(tbase + 2 * BN, v);
+                    if (n_acc > 3) tmem_ld16(tbase + 3 * BN, w);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) lo[c0 + i] = __fadd_rn(lo[c0 + i], n_acc > 3 ? __fadd_rn(v[i], w[i]) : v[i]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty);
+        }
+        if (ok) {
+            const int jj = jj0 + row / 16, jjp = jjp0 + row % 16;
+            if (jj < a.cn && jjp < a.cnp && (a.cf + jj) != (a.cfp + jjp)) {
+#pragma unroll
+                for (int c = 0; c < EPI_COLS; ++c) {
+                    const int t = n0 + col0 + c;
+                    if (t < a.n_nn) {
+                        const int na = __ldg(a.nn + 2 * t), nb = __ldg(a.nn + 2 * t + 1);
+                        const int64_t r = a.row_off + (int64_t)na * a.cn + jj;
+                        const int64_t cc = a.col_off + (int64_t)nb * a.cnp + jjp;
+                        if (!a.same_group || r >= cc) {
+                            const double v = df_to_double(hi[c], lo[c]);
+                            a.H[r * a.ld + cc] = v;
+                            if (r != cc) a.H[cc * a.ld + r] = v;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ------------------------------------------------------------- slicing
+// One warp per row.  Row maximum |x|, e with max < 2^e; each element becomes
+// the 64-bit fixed-point integer F = round(x 2^{7S-e}) (|F| < 2^{7S}, built
+// from the FP64 bit pattern with integer operations), whose balanced base-128
+// digits d_0 .. d_{S-1} (d_0 in [-128, 128], the rest in [-64, 64]) are the
+// slices: slice i = d_i 2^{e-7-7i}.  Output layout [S][K/64][rows][64], so a
+// 64-wide K block of consecutive rows is contiguous.  Column skip_col is zero.
+__global__ void slice_rows_kernel(const double *__restrict__ X, int64_t rows, int Kpad, int S, int skip_col,
+                                  __nv_bfloat16 *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    const double *x = X + row * Kpad;
+    const int KB = Kpad / BKB;
+    // exponent of the row maximum from the bit patterns (no FP64 arithmetic)
+    int emax = -2000;
+    for (int k = lane; k < Kpad; k += 32) {
+        if (k == skip_col) continue;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(x[k]);
+        const int be = (int)((b >> 52) & 0x7FF);
+        if (be == 0) continue;                 // zero (FP64 subnormals ignored)
+        const int e = be - 1022;               // |x| in [2^(e-1), 2^e)
+        emax = e > emax ? e : emax;
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const int o = __shfl_xor_sync(0xffffffffu, emax, off);
+        emax = o > emax ? o : emax;
+    }
+    for (int k = lane; k < Kpad; k += 32) {
+        long long F = 0;
+        if (k != skip_col && emax > -2000) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(x[k]);
+            const int be = (int)((b >> 52) & 0x7FF);
+            if (be != 0) {
+                const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));   // x = m 2^(be-1075)
+                const int sh = (be - 1075) + 7 * S - emax;      // F = m 2^sh, rounded to nearest
+                long long f;
+                if (sh >= 0) f = m << sh;                       // sh <= 7S - 53 < 0 in practice
+                else if (sh > -63) f = (m + (1ll << (-sh - 1))) >> (-sh);
+                else f = 0;
+                F = (b >> 63) ? -f : f;
+            }
+        }
+        const int kb = k / BKB, kk = k % BKB;
+        for (int i = 0; i < S; ++i) {
+            const int sh = 7 * (S - 1 - i);
+            long long d = sh > 0 ? ((F + (1ll << (sh - 1))) >> sh) : F;   // nearest digit (floor of F/2^sh + 1/2)
+            F -= d << sh;
+            const float v = ldexpf((float)d, emax - 7 - 7 * i);            // exact: |d| <= 128
+            out[(((int64_t)i * KB + kb) * rows + row) * BKB + kk] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+// FP64 rows with j == j' (both ranges): H[(n,j),(n',j)] over all K, incl. delta.
+// One block per (j, 32 state pairs); the threads of a warp split K.
+__global__ void diag_rows_fp64_kernel(const double *__restrict__ P, const double *__restrict__ A,
+                                      const int32_t *__restrict__ nn, int n_nn, int Kpad, int n_co, int j_lo,
+                                      int j_hi, int cf, int cn, int cfp, int cnp, int64_t row_off, int64_t col_off,
+                                      int same_group, int64_t ld, double *__restrict__ H) {
+    const int j = j_lo + blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= j_hi || t >= n_nn) return;
+    const double *prow = P + ((int64_t)j * n_co + j) * Kpad;
+    const double *arow = A + (int64_t)t * Kpad;
+    double acc = 0.0;
+    for (int k = lane; k < Kpad; k += 32) acc = fma(prow[k], arow[k], acc);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane) return;
+    const int na = nn[2 * t], nb = nn[2 * t + 1];
+    const int64_t r = row_off + (int64_t)na * cn + (j - cf);
+    const int64_t c = col_off + (int64_t)nb * cnp + (j - cfp);
+    if (same_group && r < c) return;
+    H[r * ld + c] = acc;
+    if (r != c) H[c * ld + r] = acc;
+}
+
+// ------------------------------------------------------ tensor maps (host)
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiled)p;
+    });
+    return fn;
+}
+
+}  // namespace
+
+static cudaError_t set_smem_attr(int S) {
+    const int bytes = S * SLOT + 2048;
+    switch (S) {
+        case 2: return cudaFuncSetAttribute(split_expand_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        case 3: return cudaFuncSetAttribute(split_expand_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        case 4: return cudaFuncSetAttribute(split_expand_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        case 5: return cudaFuncSetAttribute(split_expand_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        default: return cudaFuncSetAttribute(split_expand_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
+}
+
+static int mixed_fail(hb_ctx *ctx, int code, const std::string &m) {
+    ctx->err = m;
+    return code;
+}
+
+// Panel slices once per context (the integrals do not change between builds).
+static int ensure_mixed(hb_ctx *ctx, cudaStream_t s) {
+    if (!ctx->mixed) ctx->mixed = new MixedState();
+    MixedState &M = *ctx->mixed;
+    if (M.panel_ready) return HB_OK;
+    M.slices = ctx->split_slices;
+    if (M.slices < 2 || M.slices > MAXS) return mixed_fail(ctx, HB_ERR_INVALID_ARG, "split_slices must be 2..6");
+    if (!encode_fn()) return mixed_fail(ctx, HB_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    const int64_t rows = (int64_t)ctx->n_co * ctx->n_co;
+    M.panel_rows = rows;
+    int64_t max_nn = 1;
+    for (auto &P : ctx->gps) max_nn = std::max<int64_t>(max_nn, P.n_nn);
+    M.coef_rows = max_nn;
+    cudaError_t e = cudaMalloc(&M.panel_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * rows * ctx->Kpad);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&M.coef_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * max_nn * ctx->Kpad);
+    if (e == cudaSuccess) e = cudaMalloc(&M.err, sizeof(int));
+    if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("mixed operands: ") + cudaGetErrorString(e));
+    ctx->dev_bytes += sizeof(__nv_bfloat16) * (size_t)M.slices * (rows + max_nn) * ctx->Kpad + sizeof(int);
+    const int delta_col = (int)(ctx->Pt + (int64_t)ctx->n_to * ctx->n_to + 1);
+    slice_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(ctx->panel, rows, ctx->Kpad, M.slices, delta_col,
+                                                                 M.panel_slices);
+    // 4D map over the panel slices [S*KB][j][j'][32]: coordinates (kk, j', j, plane)
+    const int KB = ctx->Kpad / BKB;
+    cuuint64_t dims[4] = {(cuuint64_t)BKB, (cuuint64_t)ctx->n_co, (cuuint64_t)ctx->n_co,
+                          (cuuint64_t)M.slices * KB};
+    cuuint64_t strides[3] = {(cuuint64_t)BKB * 2, (cuuint64_t)ctx->n_co * BKB * 2, (cuuint64_t)rows * BKB * 2};
+    cuuint32_t box[4] = {BKB, 16, 8, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode_fn()(&M.tm_panel, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, M.panel_slices, dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return mixed_fail(ctx, HB_ERR_CUDA, "panel tensor map: error " + std::to_string((int)r));
+    e = set_smem_attr(M.slices);
+    if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
+    M.panel_ready = true;
+    return HB_OK;
+}
+
+int expand_mixed(hb_ctx *ctx, GroupPair &P, double *Hcc, cudaStream_t s) {
+    int rc = ensure_mixed(ctx, s);
+    if (rc != HB_OK) return rc;
+    MixedState &M = *ctx->mixed;
+    const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
+    const int delta_col = (int)(ctx->Pt + (int64_t)ctx->n_to * ctx->n_to + 1);
+    // coefficient slices of this group pair
+    slice_rows_kernel<<<(P.n_nn + 7) / 8, 256, 0, s>>>(P.A, P.n_nn, ctx->Kpad, M.slices, delta_col, M.coef_slices);
+    const int KB = ctx->Kpad / BKB;
+    CUtensorMap tm_coef;
+    cuuint64_t dims[3] = {(cuuint64_t)BKB, (cuuint64_t)P.n_nn, (cuuint64_t)M.slices * KB};
+    cuuint64_t strides[2] = {(cuuint64_t)BKB * 2, (cuuint64_t)P.n_nn * BKB * 2};
+    cuuint32_t box[3] = {BKB, BN, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&tm_coef, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, M.coef_slices, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return mixed_fail(ctx, HB_ERR_CUDA, "coefficient tensor map: error " + std::to_string((int)r));
+    SplitArgs a;
+    a.n_co = ctx->n_co; a.cf = A.cf; a.cn = A.cn; a.cfp = B.cf; a.cnp = B.cn;
+    a.jpt_tiles = (B.cn + 15) / 16;
+    a.n_nn = P.n_nn; a.kblocks = KB; a.slices = M.slices;
+    a.row_off = A.row_off; a.col_off = B.row_off; a.ld = ctx->Dc; a.same_group = P.same;
+    a.nn = P.nn; a.H = Hcc; a.err = M.err;
+    cudaMemsetAsync(M.err, 0, sizeof(int), s);
+    const dim3 grid((P.n_nn + BN - 1) / BN, ((A.cn + 7) / 8) * a.jpt_tiles);
+    const size_t smem = M.slices * SLOT + 2048;
+    switch (M.slices) {
+        case 2: split_expand_kernel<2><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
+        case 3: split_expand_kernel<3><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
+        case 4: split_expand_kernel<4><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
+        case 5: split_expand_kernel<5><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
+        default: split_expand_kernel<6><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
+    }
+    // rows with j == j' in FP64
+    const int j_lo = std::max(A.cf, B.cf), j_hi = std::min(A.cf + A.cn, B.cf + B.cn);
+    if (j_hi > j_lo)
+        diag_rows_fp64_kernel<<<dim3(j_hi - j_lo, (P.n_nn + 7) / 8), 256, 0, s>>>(ctx->panel, P.A, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, j_lo,
+                                                          j_hi, A.cf, A.cn, B.cf, B.cn, A.row_off, B.row_off, P.same,
+                                                          ctx->Dc, Hcc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_CUDA, std::string("split expansion: ") + cudaGetErrorString(e));
+    return HB_OK;
+}
+
+int mixed_error_word(hb_ctx *ctx, int *out) {
+    *out = 0;
+    if (!ctx->mixed || !ctx->mixed->err) return HB_OK;
+    cudaError_t e = cudaMemcpy(out, ctx->mixed->err, sizeof(int), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+void release_mixed(hb_ctx *ctx) {
+    if (!ctx->mixed) return;
+    cudaFree(ctx->mixed->panel_slices);
+    cudaFree(ctx->mixed->coef_slices);
+    cudaFree(ctx->mixed->err);
+    delete ctx->mixed;
+    ctx->mixed = nullptr;
+}
