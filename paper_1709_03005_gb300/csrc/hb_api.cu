@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "hb_api_internal.cuh"
+#include "hb_davidson.cuh"
 
 using namespace hb;
 
@@ -500,5 +501,7 @@ extern "C" void hb_destroy(hb_ctx *ctx) {
     for (int i = 0; i < 4; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     release_mixed(ctx);
+    hb::release_diag(ctx);
+    hb::release_mlp(ctx);
     delete ctx;
 }

@@ -1,0 +1,32 @@
+// Davidson solver and learned-preconditioner internals.
+#pragma once
+
+#include <vector>
+
+#include "hb_api_internal.cuh"
+
+namespace hb {
+
+// Device workspace of hb_diag (vectors stored as rows of length dim).
+struct DiagWork {
+    int mmax = 0;
+    int64_t n = 0;
+    double *V = nullptr, *AV = nullptr, *X = nullptr, *AX = nullptr;
+    double *d = nullptr;          // diagonal of H
+    double *partial = nullptr, *small = nullptr, *theta = nullptr;
+    int32_t *idx = nullptr;
+    double *HlcT = nullptr;       // class-4 block transposed (Dc x n_l2)
+    const double *HlcT_src = nullptr;
+};
+
+void jacobi_eig(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V);
+int ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t s);
+void release_diag(hb_ctx *ctx);
+
+// Learned preconditioner (k_mlp.cu): per-row factors w[j][i] for the Ritz
+// values theta[0..nr) of this iteration; *out points at device memory owned
+// by the context.
+int mlp_weights_for(hb_ctx *ctx, DiagWork *w, const double *theta, int nr, float **out, cudaStream_t s);
+void release_mlp(hb_ctx *ctx);
+
+}  // namespace hb
