@@ -231,7 +231,38 @@ typedef struct {
     const float *w3, *b3;     /* host [1][width], [1] */
 } hb_mlp_weights;
 
+/* Weights of the network used by hb_diag with HB_PRECOND_MLP: 8 inputs,
+   width 64 (w1 [64][8], b1 [64], w2 [64][64], b2 [64], w3 [64], b3 [1]);
+   stored as FP16, biases FP32.  The factor for row i and Ritz value theta is
+   w = 4^tanh(o), o = w3 . relu(w2 relu(w1 f + b1) + b2) + b3, applied as
+   t_i = w r_i / (H_ii - theta).  A non-finite factor falls back to 1. */
 int hb_mlp_set(hb_ctx *ctx, const hb_mlp_weights *w);
+
+/* Number of packed parameters (w1, b1, w2, b2, w3, b3 in that order) for
+   n_in = 8, width = 64 (4801); -1 for any other shape. */
+int hb_mlp_param_count(int32_t n_in, int32_t width);
+
+/* Device scratch needed by hb_mlp_loss_grad for n samples. */
+int64_t hb_mlp_workspace_bytes(int64_t n);
+
+/* Training step pieces, all device pointers.  For samples i with features
+   feats[i][8] and targets a_i, b_i: loss = mean_i (w(f_i) a_i - b_i)^2 and its
+   gradient with respect to the packed parameters (weights rounded to FP16 in
+   the forward pass, FP32 accumulation, fixed-order sums). */
+int hb_mlp_loss_grad(const float *params, const float *feats, const float *a, const float *b, int64_t n,
+                     float *grads, float *loss, void *work, void *stream);
+
+/* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8) of n_param parameters. */
+int hb_mlp_adam(int64_t n_param, float *params, const float *grads, float *m, float *v, int32_t step,
+                float lr, void *stream);
+
+/* Factors w(f_i) for n feature rows (device). */
+int hb_mlp_predict(const float *params, const float *feats, int64_t n, float *out, void *stream);
+
+/* Features of every row of the built matrix for q Ritz values theta (host):
+   feats (device) [q][dim][8], as hb_diag computes them. */
+int hb_diag_features(hb_ctx *ctx, const hb_blocks *H, const double *theta, int32_t q, float *feats,
+                     void *stream);
 
 const char *hb_last_error(const hb_ctx *ctx);
 void hb_destroy(hb_ctx *ctx);

@@ -11,7 +11,7 @@ namespace hb {
 struct DiagWork {
     int mmax = 0;
     int64_t n = 0;
-    double *V = nullptr, *AV = nullptr, *X = nullptr, *AX = nullptr;
+    double *V = nullptr, *AV = nullptr, *X = nullptr, *AX = nullptr, *W2 = nullptr;
     double *d = nullptr;          // diagonal of H
     double *partial = nullptr, *small = nullptr, *theta = nullptr;
     int32_t *idx = nullptr;
@@ -19,9 +19,10 @@ struct DiagWork {
     const double *HlcT_src = nullptr;
 };
 
-void jacobi_eig(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V);
+void small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V);
 int ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t s);
 void release_diag(hb_ctx *ctx);
+void fill_diag(hb_ctx *ctx, const hb_blocks *H, DiagWork *w, cudaStream_t s);
 
 // Learned preconditioner (k_mlp.cu): per-row factors w[j][i] for the Ritz
 // values theta[0..nr) of this iteration; *out points at device memory owned

@@ -6,11 +6,11 @@
 //   residuals r = Ax - theta x; stop when ||r_i|| <= tol for i < k
 //   correction t_i = r_i / (H_ii - theta_i) (optionally times a learned factor)
 //   t orthogonalised against V twice, then among itself (SVQB), appended
-//   restart to the current Ritz vectors when the basis is full.
+//   thick restart to the 2b lowest Ritz vectors when the basis is full.
 // The products H V, the projection V^T AV, the Ritz combinations, residuals
 // and the orthogonalisation run on the GPU in FP64 with fixed-order sums; only
 // the small projected eigenproblem (at most a few hundred) is solved on the
-// host by cyclic Jacobi rotations.
+// host (Householder tridiagonalisation and implicit QL).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -224,64 +224,135 @@ __global__ void import_kernel(const double *__restrict__ E, int k, int64_t n, do
 
 }  // namespace
 
+// The diagonal of H from the built blocks into w->d.
+void hb::fill_diag(hb_ctx *ctx, const hb_blocks *H, DiagWork *w, cudaStream_t s) {
+    diag_kernel<<<(unsigned)((ctx->dim + 255) / 256), 256, 0, s>>>(H->Hcc, ctx->Dc, H->l2_row_ptr, H->l2_col,
+                                                                    H->l2_val, ctx->n_l2, w->d);
+}
+
 // ------------------------------------------------------------ host solver
-// Cyclic Jacobi eigensolver for a small symmetric matrix (Golub & Van Loan,
-// the cyclic-by-row method with the stable rotation formulas).  A is n x n
-// row-major; on return w holds the eigenvalues ascending and column j of V
-// (V[i*n + j]) the eigenvector of w[j].
-void hb::jacobi_eig(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V) {
+// Symmetric eigensolver for the small projected matrix: Householder reduction
+// to tridiagonal form, then the implicit-shift QL iteration on the tridiagonal
+// matrix with the transformations accumulated (the classical two-phase method,
+// as in Golub & Van Loan and Wilkinson & Reinsch).  A is n x n row-major; on
+// return w holds the eigenvalues ascending and column j of V (V[i*n + j]) the
+// eigenvector of w[j].
+void hb::small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V) {
+    w.assign(n, 0.0);
     V.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int p = 0; p < n; ++p)
-            for (int q = 0; q < n; ++q) {
-                const double a = A[(size_t)p * n + q];
-                tot += a * a;
-                if (p != q) off += a * a;
+    if (n == 0) return;
+    if (n == 1) { w[0] = A[0]; V[0] = 1.0; return; }
+    // z holds the accumulated orthogonal transformation, row-major z[i][j]
+    std::vector<double> z(A), d(n), e(n);
+    auto Z = [&](int i, int j) -> double & { return z[(size_t)i * n + j]; };
+    // --- Householder tridiagonalisation (rows from the bottom up)
+    for (int i = n - 1; i > 0; --i) {
+        const int l = i - 1;
+        double h = 0.0, scale = 0.0;
+        if (l > 0) {
+            for (int k = 0; k <= l; ++k) scale += std::fabs(Z(i, k));
+            if (scale == 0.0) {
+                e[i] = Z(i, l);
+            } else {
+                for (int k = 0; k <= l; ++k) { Z(i, k) /= scale; h += Z(i, k) * Z(i, k); }
+                double f = Z(i, l);
+                double g = f >= 0.0 ? -std::sqrt(h) : std::sqrt(h);
+                e[i] = scale * g;
+                h -= f * g;
+                Z(i, l) = f - g;
+                f = 0.0;
+                for (int j = 0; j <= l; ++j) {
+                    Z(j, i) = Z(i, j) / h;
+                    g = 0.0;
+                    for (int k = 0; k <= j; ++k) g += Z(j, k) * Z(i, k);
+                    for (int k = j + 1; k <= l; ++k) g += Z(k, j) * Z(i, k);
+                    e[j] = g / h;
+                    f += e[j] * Z(i, j);
+                }
+                const double hh = f / (h + h);
+                for (int j = 0; j <= l; ++j) {
+                    f = Z(i, j);
+                    e[j] = g = e[j] - hh * f;
+                    for (int k = 0; k <= j; ++k) Z(j, k) -= (f * e[k] + g * Z(i, k));
+                }
             }
-        if (off <= 1e-30 * tot || off == 0.0) break;
-        for (int p = 0; p < n - 1; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = A[(size_t)p * n + q];
-                if (apq == 0.0) continue;
-                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
-                const double theta = (aqq - app) / (2.0 * apq);
-                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-                for (int r = 0; r < n; ++r) {   // columns p, q
-                    const double arp = A[(size_t)r * n + p], arq = A[(size_t)r * n + q];
-                    A[(size_t)r * n + p] = c * arp - s * arq;
-                    A[(size_t)r * n + q] = s * arp + c * arq;
-                }
-                for (int r = 0; r < n; ++r) {   // rows p, q
-                    const double apr = A[(size_t)p * n + r], aqr = A[(size_t)q * n + r];
-                    A[(size_t)p * n + r] = c * apr - s * aqr;
-                    A[(size_t)q * n + r] = s * apr + c * aqr;
-                }
-                for (int r = 0; r < n; ++r) {
-                    const double vrp = V[(size_t)r * n + p], vrq = V[(size_t)r * n + q];
-                    V[(size_t)r * n + p] = c * vrp - s * vrq;
-                    V[(size_t)r * n + q] = s * vrp + c * vrq;
-                }
+        } else {
+            e[i] = Z(i, l);
+        }
+        d[i] = h;
+    }
+    d[0] = 0.0;
+    e[0] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int l = i - 1;
+        if (d[i] != 0.0) {
+            for (int j = 0; j <= l; ++j) {
+                double g = 0.0;
+                for (int k = 0; k <= l; ++k) g += Z(i, k) * Z(k, j);
+                for (int k = 0; k <= l; ++k) Z(k, j) -= g * Z(k, i);
             }
+        }
+        d[i] = Z(i, i);
+        Z(i, i) = 1.0;
+        for (int j = 0; j <= l; ++j) Z(j, i) = Z(i, j) = 0.0;
+    }
+    // --- implicit QL on (d, e) with accumulation into z
+    for (int i = 1; i < n; ++i) e[i - 1] = e[i];
+    e[n - 1] = 0.0;
+    for (int l = 0; l < n; ++l) {
+        int iter = 0;
+        int m;
+        do {
+            for (m = l; m < n - 1; ++m) {
+                const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+                if (std::fabs(e[m]) <= 1e-16 * dd) break;
+            }
+            if (m != l) {
+                if (++iter > 60) break;
+                double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+                double r = std::hypot(g, 1.0);
+                g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? std::fabs(r) : -std::fabs(r)));
+                double s = 1.0, c = 1.0, p = 0.0;
+                int i;
+                for (i = m - 1; i >= l; --i) {
+                    double f = s * e[i], b = c * e[i];
+                    e[i + 1] = (r = std::hypot(f, g));
+                    if (r == 0.0) {
+                        d[i + 1] -= p;
+                        e[m] = 0.0;
+                        break;
+                    }
+                    s = f / r;
+                    c = g / r;
+                    g = d[i + 1] - p;
+                    r = (d[i] - g) * s + 2.0 * c * b;
+                    d[i + 1] = g + (p = s * r);
+                    g = c * r - b;
+                    for (int k = 0; k < n; ++k) {
+                        f = Z(k, i + 1);
+                        Z(k, i + 1) = s * Z(k, i) + c * f;
+                        Z(k, i) = c * Z(k, i) - s * f;
+                    }
+                }
+                if (r == 0.0 && i >= l) continue;
+                d[l] -= p;
+                e[l] = g;
+                e[m] = 0.0;
+            }
+        } while (m != l);
     }
     std::vector<int> ord(n);
     std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(),
-                     [&](int a, int b) { return A[(size_t)a * n + a] < A[(size_t)b * n + b]; });
-    w.resize(n);
-    std::vector<double> V2((size_t)n * n);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return d[a] < d[b]; });
     for (int j = 0; j < n; ++j) {
-        w[j] = A[(size_t)ord[j] * n + ord[j]];
-        for (int i = 0; i < n; ++i) V2[(size_t)i * n + j] = V[(size_t)i * n + ord[j]];
+        w[j] = d[ord[j]];
+        for (int i = 0; i < n; ++i) V[(size_t)i * n + j] = Z(i, ord[j]);
     }
-    V.swap(V2);
 }
 
 extern "C" int hb_test_symeig(int n, const double *A, double *w, double *V) {
     std::vector<double> a(A, A + (size_t)n * n), ww, vv;
-    hb::jacobi_eig(n, a, ww, vv);
+    hb::small_eigh(n, a, ww, vv);
     std::memcpy(w, ww.data(), sizeof(double) * n);
     std::memcpy(V, vv.data(), sizeof(double) * (size_t)n * n);
     return 0;
@@ -362,15 +433,16 @@ int hb::ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t
     }
     if (w->mmax < mmax || w->n != n) {
         auto fr = [](void *p) { if (p) cudaFree(p); };
-        fr(w->V); fr(w->AV); fr(w->X); fr(w->AX); fr(w->d); fr(w->partial); fr(w->small); fr(w->theta);
+        fr(w->V); fr(w->AV); fr(w->X); fr(w->AX); fr(w->W2); fr(w->d); fr(w->partial); fr(w->small); fr(w->theta);
         fr(w->idx);
-        w->V = w->AV = w->X = w->AX = w->d = w->partial = w->small = w->theta = nullptr;
+        w->V = w->AV = w->X = w->AX = w->W2 = w->d = w->partial = w->small = w->theta = nullptr;
         w->idx = nullptr;
         const size_t vec = sizeof(double) * (size_t)mmax * n;
         cudaError_t e = cudaMalloc(&w->V, vec);
         if (e == cudaSuccess) e = cudaMalloc(&w->AV, vec);
         if (e == cudaSuccess) e = cudaMalloc(&w->X, vec);
         if (e == cudaSuccess) e = cudaMalloc(&w->AX, vec);
+        if (e == cudaSuccess) e = cudaMalloc(&w->W2, vec);
         if (e == cudaSuccess) e = cudaMalloc(&w->d, sizeof(double) * n);
         const int chunks = (int)((n + kGramChunk - 1) / kGramChunk);
         if (e == cudaSuccess) e = cudaMalloc(&w->partial, sizeof(double) * (size_t)chunks * mmax * mmax);
@@ -403,7 +475,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         return diag_fail(ctx, HB_ERR_INVALID_ARG, "HB_PRECOND_MLP without weights (hb_mlp_set)");
     cudaStream_t s = (cudaStream_t)stream;
     const int b = (int)std::min<int64_t>(n, k + std::max(4, std::min(16, k / 2)));
-    const int mmax = (int)std::min<int64_t>(n, std::max(3 * b, k + 2 * b));
+    const int mmax = (int)std::min<int64_t>(n, std::max(5 * b, k + 4 * b));
     int rc = ensure_diag_work(ctx, H, mmax, s);
     if (rc != HB_OK) return rc;
     DiagWork *w = (DiagWork *)ctx->diag;
@@ -447,7 +519,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         ops.gram(blk, q, blk, q, ld, G);
         for (int a = 0; a < q; ++a)
             for (int c = 0; c < a; ++c) G[(size_t)a * q + c] = G[(size_t)c * q + a] = 0.5 * (G[(size_t)a * q + c] + G[(size_t)c * q + a]);
-        jacobi_eig(q, G, lam, U);
+        small_eigh(q, G, lam, U);
         const double lmax = lam.empty() ? 0.0 : lam.back();
         std::vector<int> keep;
         for (int a = 0; a < q; ++a)
@@ -479,7 +551,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         ops.gram(w->V, m, w->AV, m, ld, T);
         for (int a = 0; a < m; ++a)
             for (int c = 0; c < a; ++c) T[(size_t)a * m + c] = T[(size_t)c * m + a] = 0.5 * (T[(size_t)a * m + c] + T[(size_t)c * m + a]);
-        jacobi_eig(m, T, theta, S);
+        small_eigh(m, T, theta, S);
         const int nr = std::min(m, b);
         std::vector<double> Sk((size_t)m * nr);
         for (int a = 0; a < m; ++a)
@@ -510,18 +582,18 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         // corrections for the unconverged Ritz pairs (lowest first, at most b)
         if ((int)which.size() > b) which.resize(b);
         int q = (int)which.size();
-        // restart when the basis would overflow: keep the current Ritz vectors
+        // thick restart when the basis would overflow: keep the 2b lowest Ritz
+        // vectors (the residuals of the first nr stay in AX)
         if (m + q > mmax) {
-            cudaMemcpyAsync(w->V, w->X, sizeof(double) * (size_t)nr * ld, cudaMemcpyDeviceToDevice, s);
-            // AX now holds residuals: AV of the Ritz vectors = residual + theta X
-            ops.combine(w->AV, m, Sk, nr, w->AX, ld, 0.0);
-            cudaMemcpyAsync(w->AV, w->AX, sizeof(double) * (size_t)nr * ld, cudaMemcpyDeviceToDevice, s);
-            {
-                dim3 g((unsigned)((n + 255) / 256), nr);
-                residual_kernel<<<g, 256, 0, s>>>(w->AX, w->X, ld, w->theta, nr, n, w->AX);
-                ++ops.launches;
-            }
-            m = nr;
+            const int keep = std::min(m, std::min(2 * b, mmax - q));
+            std::vector<double> Sr((size_t)m * keep);
+            for (int a2 = 0; a2 < m; ++a2)
+                for (int c = 0; c < keep; ++c) Sr[(size_t)a2 * keep + c] = S[(size_t)a2 * m + c];
+            ops.combine(w->V, m, Sr, keep, w->W2, ld, 0.0);
+            cudaMemcpyAsync(w->V, w->W2, sizeof(double) * (size_t)keep * ld, cudaMemcpyDeviceToDevice, s);
+            ops.combine(w->AV, m, Sr, keep, w->W2, ld, 0.0);
+            cudaMemcpyAsync(w->AV, w->W2, sizeof(double) * (size_t)keep * ld, cudaMemcpyDeviceToDevice, s);
+            m = keep;
         }
         if (m + q > mmax) q = mmax - m;
         if (q <= 0) break;
@@ -599,7 +671,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
 void hb::release_diag(hb_ctx *ctx) {
     DiagWork *w = (DiagWork *)ctx->diag;
     if (!w) return;
-    for (void *p : {(void *)w->V, (void *)w->AV, (void *)w->X, (void *)w->AX, (void *)w->d, (void *)w->partial,
+    for (void *p : {(void *)w->V, (void *)w->AV, (void *)w->X, (void *)w->AX, (void *)w->W2, (void *)w->d, (void *)w->partial,
                     (void *)w->small, (void *)w->theta, (void *)w->idx, (void *)w->HlcT})
         if (p) cudaFree(p);
     delete w;

@@ -70,7 +70,8 @@ PAIR_DTYPE = np.dtype([("row", "<i4"), ("col", "<i4"), ("hole", "<i2", (2,)), ("
 assert PAIR_DTYPE.itemsize == 24
 
 EXPORTS = ["hb_init", "hb_query", "hb_group_offset", "hb_build_blocks", "hb_diag", "hb_classify",
-           "hb_classify_noalloc", "hb_mlp_set", "hb_last_error", "hb_destroy"]
+           "hb_classify_noalloc", "hb_mlp_set", "hb_mlp_param_count", "hb_mlp_workspace_bytes", "hb_mlp_loss_grad",
+           "hb_mlp_adam", "hb_mlp_predict", "hb_diag_features", "hb_last_error", "hb_destroy"]
 
 _lib = None
 
@@ -223,6 +224,10 @@ class Hamiltonian:
         w = hb_mlp_weights(arrs[0].shape[1], arrs[0].shape[0], *[a.ctypes.data for a in arrs])
         _check(self.lib.hb_mlp_set(self.ctx, C.byref(w)), self.ctx)
 
+    def set_mlp_params(self, packed):
+        """Load a packed parameter vector (see unpack_mlp) for HB_PRECOND_MLP."""
+        self.set_mlp(*unpack_mlp(packed))
+
     def close(self):
         if getattr(self, "ctx", None) and self.ctx.value:
             self.lib.hb_destroy(self.ctx)
@@ -301,3 +306,82 @@ def classify_noalloc(a, b, n_words, mode=0, cont_spin=0, max_degree=2, lower=Fal
     torch.cuda.synchronize()
     rec = np.frombuffer(pairs.cpu().numpy().tobytes(), dtype=PAIR_DTYPE)[: total.value]
     return total.value, rec
+
+
+# --------------------------------------------------------------------------
+# learned preconditioner
+# --------------------------------------------------------------------------
+
+MLP_IN, MLP_WIDTH = 8, 64
+
+
+def _mlp_fns():
+    lib = load()
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    lib.hb_mlp_param_count.argtypes = [i32, i32]
+    lib.hb_mlp_param_count.restype = C.c_int
+    lib.hb_mlp_workspace_bytes.argtypes = [i64]
+    lib.hb_mlp_workspace_bytes.restype = i64
+    lib.hb_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.hb_mlp_loss_grad.restype = C.c_int
+    lib.hb_mlp_adam.argtypes = [i64, vp, vp, vp, vp, i32, C.c_float, vp]
+    lib.hb_mlp_adam.restype = C.c_int
+    lib.hb_mlp_predict.argtypes = [vp, vp, i64, vp, vp]
+    lib.hb_mlp_predict.restype = C.c_int
+    lib.hb_diag_features.argtypes = [vp, C.POINTER(hb_blocks), vp, i32, vp, vp]
+    lib.hb_diag_features.restype = C.c_int
+    return lib
+
+
+def mlp_param_count():
+    return _mlp_fns().hb_mlp_param_count(MLP_IN, MLP_WIDTH)
+
+
+def mlp_loss_grad(params, feats, a, b, work=None, stream=None):
+    """(loss, grads) of mean (w(f) a - b)^2 on the device (float32 tensors)."""
+    import torch
+    lib = _mlp_fns()
+    n = feats.shape[0]
+    if work is None:
+        work = torch.empty(lib.hb_mlp_workspace_bytes(n), dtype=torch.uint8, device=feats.device)
+    grads = torch.empty_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device=feats.device)
+    _check(lib.hb_mlp_loss_grad(_ptr(params), _ptr(feats), _ptr(a), _ptr(b), n, _ptr(grads), _ptr(loss),
+                                _ptr(work), _stream_handle(stream)))
+    return loss, grads
+
+
+def mlp_adam(params, grads, m, v, step, lr, stream=None):
+    _check(_mlp_fns().hb_mlp_adam(params.numel(), _ptr(params), _ptr(grads), _ptr(m), _ptr(v), step, lr,
+                                  _stream_handle(stream)))
+
+
+def mlp_predict(params, feats, stream=None):
+    import torch
+    out = torch.empty(feats.shape[0], dtype=torch.float32, device=feats.device)
+    _check(_mlp_fns().hb_mlp_predict(_ptr(params), _ptr(feats), feats.shape[0], _ptr(out), _stream_handle(stream)))
+    return out
+
+
+def unpack_mlp(params):
+    """Packed parameter vector -> (w1, b1, w2, b2, w3, b3) numpy arrays."""
+    p = np.asarray(params, dtype=np.float32)
+    W, I = MLP_WIDTH, MLP_IN
+    o = 0
+    out = []
+    for shape in [(W, I), (W,), (W, W), (W,), (W,), (1,)]:
+        sz = int(np.prod(shape))
+        out.append(p[o:o + sz].reshape(shape))
+        o += sz
+    return out
+
+
+def diag_features(H, blocks, theta, stream=None):
+    """Features [q, dim, 8] (device float32) of every row for Ritz values theta."""
+    import torch
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    out = torch.empty((len(th), H.dim, MLP_IN), dtype=torch.float32, device="cuda")
+    bs = H.blocks_struct(blocks)
+    _check(_mlp_fns().hb_diag_features(H.ctx, C.byref(bs), th.ctypes.data, len(th), _ptr(out),
+                                       _stream_handle(stream)), H.ctx)
+    return out

@@ -1,11 +1,11 @@
 """The small dense eigensolver used for the Davidson Rayleigh-Ritz step
-(cyclic Jacobi, host code of the library) against numpy's eigh."""
+(Householder tridiagonalisation + implicit QL, host code of the library) against numpy's eigh."""
 import ctypes
 
 import numpy as np
 
 
-def test_jacobi_matches_eigh():
+def test_small_eigensolver_matches_eigh():
     from paper_1709_03005_gb300 import build_ext, hb
     lib = ctypes.CDLL(build_ext.build())
     fn = lib.hb_test_symeig

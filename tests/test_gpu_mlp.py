@@ -1,0 +1,75 @@
+"""The preconditioner network's CUDA kernels against the FP64 reference
+(forward, loss, gradient, Adam), and its use inside hb_diag."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_1709_03005_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1709_03005_gb300 import build_ext
+    build_ext.build()
+
+
+def _random(seed, n=3000, scale=0.2):
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0, scale, 4801).astype(np.float32)
+    f = rng.normal(0, 1, (n, 8)).astype(np.float32)
+    a = rng.normal(0, 1, n).astype(np.float32)
+    b = rng.normal(0, 1, n).astype(np.float32)
+    return p, f, a, b
+
+
+def test_forward_and_gradient_match_reference():
+    import torch
+    from paper_1709_03005_gb300 import hb
+    p, f, a, b = _random(0)
+    t = lambda x: torch.from_numpy(x).cuda()
+    loss, g = hb.mlp_loss_grad(t(p), t(f), t(a), t(b))
+    w = hb.mlp_predict(t(p), t(f))
+    torch.cuda.synchronize()
+    ref_loss, ref_g = mlp.loss_grad(p.astype(np.float64), f.astype(np.float64), a.astype(np.float64),
+                                    b.astype(np.float64))
+    ref_w = mlp.factor(p.astype(np.float64), f.astype(np.float64))
+    np.testing.assert_allclose(w.cpu().numpy(), ref_w, rtol=2e-5, atol=1e-6)
+    assert abs(float(loss) - ref_loss) <= 1e-5 * abs(ref_loss)
+    g = g.cpu().numpy()
+    scale = np.abs(ref_g).max()
+    np.testing.assert_allclose(g, ref_g, rtol=1e-3, atol=1e-4 * scale)
+
+
+def test_adam_step():
+    import torch
+    from paper_1709_03005_gb300 import hb
+    rng = np.random.default_rng(1)
+    p = rng.normal(0, 1, 4801).astype(np.float32)
+    g = rng.normal(0, 1, 4801).astype(np.float32)
+    m = rng.normal(0, 0.1, 4801).astype(np.float32)
+    v = np.abs(rng.normal(0, 0.1, 4801)).astype(np.float32)
+    tp, tg, tm, tv = (torch.from_numpy(x.copy()).cuda() for x in (p, g, m, v))
+    hb.mlp_adam(tp, tg, tm, tv, 3, 1e-2)
+    torch.cuda.synchronize()
+    m2 = 0.9 * m + 0.1 * g
+    v2 = 0.999 * v + 0.001 * g * g
+    ref = p - 1e-2 * (m2 / (1 - 0.9 ** 3)) / (np.sqrt(v2 / (1 - 0.999 ** 3)) + 1e-8)
+    np.testing.assert_allclose(tp.cpu().numpy(), ref, rtol=1e-5, atol=1e-6)
+
+
+def test_unit_network_reproduces_plain_davidson():
+    """A network whose output is 0 gives w = 1 everywhere: HB_PRECOND_MLP must
+    then take exactly the iterations of HB_PRECOND_DIAG."""
+    import torch
+    from paper_1709_03005_gb300 import hb
+    P = synth.make_config("mid")
+    H = hb.Hamiltonian(P)
+    b, _ = H.build()
+    w0, s0, _ = H.diag(b, 8, 1e-8, 300)
+    H.set_mlp_params(np.zeros(4801, np.float32))
+    w1, s1, _ = H.diag(b, 8, 1e-8, 300, precond=hb.HB_PRECOND_MLP)
+    assert s0.iterations == s1.iterations
+    np.testing.assert_allclose(w0, w1, atol=1e-9)
+    H.close()
