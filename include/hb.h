@@ -186,6 +186,25 @@ int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, int32_t max_
             int32_t precond, const double *v0, double *evals, double *evecs, hb_stats *st,
             void *stream);
 
+/* Stage a problem whose orbitals and integrals are those of `base` (for
+   instance another spatial-symmetry or spin-coupling block of the same
+   molecule): the integrals, the expansion panel and its tensor-core slices are
+   borrowed from `base`, which must outlive this context.  The caller
+   guarantees that p's integral arrays equal base's (only their shapes are
+   checked). */
+int hb_init_shared(hb_ctx **ctx, const hb_problem *p, const hb_options *o, hb_ctx *base, void *stream);
+
+/* Batched build of n staged contexts into outs[0..n) (Section 2.2 classes for
+   every block): one eager build, then the whole set is captured as a CUDA graph
+   that hb_batch_launch replays with a single launch.  The blocks in outs are
+   baked into the graph and must stay allocated. */
+typedef struct hb_batch hb_batch;
+int hb_batch_create(hb_batch **b, hb_ctx *const *ctxs, int32_t n, int32_t precision, const hb_blocks *outs,
+                    void *stream);
+int hb_batch_launch(hb_batch *b, hb_stats *st, void *stream);
+int hb_batch_nodes(const hb_batch *b);
+void hb_batch_destroy(hb_batch *b);
+
 /* Excitation classification (Section 2.1) of every pair (a, b) of two
    determinant lists on the device.  mode 0: equal electron counts, degree =
    popcount(a ^ b) / 2; mode 1: b holds N-electron target determinants and a

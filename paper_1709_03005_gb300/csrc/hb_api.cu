@@ -188,6 +188,22 @@ extern "C" int hb_init(hb_ctx **out, const hb_problem *p, const hb_options *o, v
     return HB_OK;
 }
 
+extern "C" int hb_init_shared(hb_ctx **out, const hb_problem *p, const hb_options *o, hb_ctx *base, void *stream) {
+    if (!out || !base) return fail(nullptr, HB_ERR_INVALID_ARG, "ctx pointer or base is NULL");
+    *out = nullptr;
+    if (base->base) return fail(nullptr, HB_ERR_INVALID_ARG, "the base context borrows its integrals itself");
+    if (!p || p->n_to != base->n_to || p->n_co != base->n_co || p->n_words != base->W)
+        return fail(nullptr, HB_ERR_INVALID_ARG, "problem orbitals differ from the base context");
+    hb_ctx *ctx = new hb_ctx();
+    ctx->base = base;
+    int rc = validate_problem(ctx, p, o);
+    if (rc != HB_OK) { g_last_error = ctx->err; delete ctx; return rc; }
+    rc = stage_problem(ctx, p, o, (cudaStream_t)stream);
+    if (rc != HB_OK) { g_last_error = ctx->err; hb_destroy(ctx); return rc; }
+    *out = ctx;
+    return HB_OK;
+}
+
 int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStream_t s) {
     CK(cudaGetDevice(&ctx->device));
     ctx->n_to = p->n_to; ctx->n_co = p->n_co; ctx->n_orb = p->n_to + p->n_co;
@@ -214,14 +230,21 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
     ctx->dim = row_off + p->n_l2;
     const size_t no = ctx->n_orb, Pt = ctx->Pt, ntc = (size_t)p->n_to * p->n_co, ncc = (size_t)p->n_co * p->n_co;
     // --- stage integrals, determinants, CI
-    DALLOC(ctx->h, no * no);
-    DALLOC(ctx->tttt, Pt * Pt);
-    DALLOC(ctx->jk, 2 * (size_t)p->n_to * p->n_to);
-    CK(cudaMemcpyAsync(ctx->h, p->h, sizeof(double) * no * no, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->tttt, p->eri_tttt, sizeof(double) * Pt * Pt, cudaMemcpyHostToDevice, s));
-    if (p->eri_tttc && ntc > 0) {
-        DALLOC(ctx->tttc, Pt * ntc);
-        CK(cudaMemcpyAsync(ctx->tttc, p->eri_tttc, sizeof(double) * Pt * ntc, cudaMemcpyHostToDevice, s));
+    const bool shared = ctx->base != nullptr;
+    if (shared) {
+        // integrals, their tables and the expansion panel belong to the base context
+        ctx->h = ctx->base->h; ctx->tttt = ctx->base->tttt; ctx->tttc = ctx->base->tttc;
+        ctx->jk = ctx->base->jk; ctx->panel = ctx->base->panel;
+    } else {
+        DALLOC(ctx->h, no * no);
+        DALLOC(ctx->tttt, Pt * Pt);
+        DALLOC(ctx->jk, 2 * (size_t)p->n_to * p->n_to);
+        CK(cudaMemcpyAsync(ctx->h, p->h, sizeof(double) * no * no, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->tttt, p->eri_tttt, sizeof(double) * Pt * Pt, cudaMemcpyHostToDevice, s));
+        if (p->eri_tttc && ntc > 0) {
+            DALLOC(ctx->tttc, Pt * ntc);
+            CK(cudaMemcpyAsync(ctx->tttc, p->eri_tttc, sizeof(double) * Pt * ntc, cudaMemcpyHostToDevice, s));
+        }
     }
     DALLOC(ctx->dets, std::max<int64_t>(det_off, 1));
     DALLOC(ctx->ci, std::max<int64_t>(ci_off, 1));
@@ -235,9 +258,9 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
     if (p->n_l2 > 0)
         CK(cudaMemcpyAsync(ctx->l2, p->l2_dets, sizeof(uint64_t) * p->n_l2 * nw, cudaMemcpyHostToDevice, s));
     Ints I = ctx->ints();
-    build_jk(I, ctx->jk, s);
+    if (!shared) build_jk(I, ctx->jk, s);
     // --- the expansion panel (classes 1,3,5,6,7)
-    if (p->n_groups > 0) {
+    if (p->n_groups > 0 && !shared) {
         DALLOC(ctx->panel, ncc * ctx->Kpad);
         double *t_ttcc = nullptr, *t_tctc = nullptr;
         CK(cudaMalloc(&t_ttcc, sizeof(double) * Pt * ncc));
@@ -389,12 +412,12 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
     int launches = 0;
-    CK(cudaEventRecord(ctx->ev[0], s));
+    if (!ctx->capturing) CK(cudaEventRecord(ctx->ev[0], s));
     for (auto &P : ctx->gps) {
         int rc = target_side(ctx, P, s, &launches);
         if (rc != HB_OK) return rc;
     }
-    CK(cudaEventRecord(ctx->ev[1], s));
+    if (!ctx->capturing) CK(cudaEventRecord(ctx->ev[1], s));
     float ms_gemm = 0.0f;
     int n_expand = 0;
     double flops = 0.0;
@@ -411,7 +434,7 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         flops += 2.0 * (double)A.cn * B.cn * P.n_nn * ctx->K;
     }
     launches += n_expand;
-    CK(cudaEventRecord(ctx->ev[2], s));
+    if (!ctx->capturing) CK(cudaEventRecord(ctx->ev[2], s));
     Ints I = ctx->ints();
     for (int g = 0; g < ctx->n_groups; ++g) {
         const GroupInfo &G = ctx->groups[g];
@@ -422,7 +445,7 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
                     ctx->W, ctx->cont_spin, G.row_off, ctx->Dc, out->Hlc, s);
         launches += 2;
     }
-    CK(cudaEventRecord(ctx->ev[3], s));
+    if (!ctx->capturing) CK(cudaEventRecord(ctx->ev[3], s));
     if (ctx->n_l2 > 0) {
         CK(cudaMemcpyAsync(out->l2_row_ptr, ctx->l2_rowptr, sizeof(int64_t) * (ctx->n_l2 + 1),
                            cudaMemcpyDeviceToDevice, s));
@@ -430,7 +453,7 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         launches += 1;
     }
     CK(cudaGetLastError());
-    if (precision == HB_MIXED) {
+    if (precision == HB_MIXED && !ctx->capturing) {
         // the tensor-core kernel reports a bounded-wait timeout in a device word
         int word = 0;
         CK(cudaStreamSynchronize(s));
@@ -438,7 +461,7 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         if (word != 0)
             return fail(ctx, HB_ERR_TIMEOUT, "split expansion kernel gave up waiting (code " + std::to_string(word) + ")");
     }
-    if (st) {
+    if (st && !ctx->capturing) {
         cudaEvent_t end;
         CK(cudaEventCreate(&end));
         CK(cudaEventRecord(end, s));

@@ -62,6 +62,8 @@ struct hb_ctx {
     int64_t l2_nnz = 0, tt_pairs = 0, tl2_pairs = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     hb::MixedState *mixed = nullptr;
+    hb_ctx *base = nullptr;  // context whose staged integrals this one borrows (or null)
+    bool capturing = false;  // inside a CUDA-graph capture: no host synchronisation
     void *diag = nullptr;   // Davidson workspace (k_davidson.cu)
     void *mlp = nullptr;    // learned preconditioner weights (k_mlp.cu)
 

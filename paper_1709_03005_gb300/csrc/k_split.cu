@@ -50,6 +50,7 @@ struct MixedState {
     int64_t coef_rows = 0;
     int *err = nullptr;                       // device error word
     bool panel_ready = false;
+    bool borrowed_panel = false;
     CUtensorMap tm_panel;
 };
 
@@ -564,6 +565,25 @@ static int ensure_mixed(hb_ctx *ctx, cudaStream_t s) {
     if (!ctx->mixed) ctx->mixed = new MixedState();
     MixedState &M = *ctx->mixed;
     if (M.panel_ready) return HB_OK;
+    if (ctx->base) {
+        // panel slices and their tensor map come from the base context
+        int rc = ensure_mixed(ctx->base, s);
+        if (rc != HB_OK) return mixed_fail(ctx, rc, ctx->base->err);
+        const MixedState &B = *ctx->base->mixed;
+        M.slices = B.slices;
+        M.panel_rows = B.panel_rows;
+        M.panel_slices = B.panel_slices;
+        M.tm_panel = B.tm_panel;
+        M.borrowed_panel = true;
+        int64_t max_nn = 1;
+        for (auto &P : ctx->gps) max_nn = std::max<int64_t>(max_nn, P.n_nn);
+        M.coef_rows = max_nn;
+        cudaError_t e = cudaMalloc(&M.coef_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * max_nn * ctx->Kpad);
+        if (e == cudaSuccess) e = cudaMalloc(&M.err, sizeof(int));
+        if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("mixed operands: ") + cudaGetErrorString(e));
+        M.panel_ready = true;
+        return HB_OK;
+    }
     M.slices = ctx->split_slices;
     if (M.slices < 2 || M.slices > MAXS) return mixed_fail(ctx, HB_ERR_INVALID_ARG, "split_slices must be 2..6");
     if (!encode_fn()) return mixed_fail(ctx, HB_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
@@ -652,7 +672,7 @@ int mixed_error_word(hb_ctx *ctx, int *out) {
 
 void release_mixed(hb_ctx *ctx) {
     if (!ctx->mixed) return;
-    cudaFree(ctx->mixed->panel_slices);
+    if (!ctx->mixed->borrowed_panel) cudaFree(ctx->mixed->panel_slices);
     cudaFree(ctx->mixed->coef_slices);
     cudaFree(ctx->mixed->err);
     delete ctx->mixed;

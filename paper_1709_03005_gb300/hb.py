@@ -69,7 +69,8 @@ PAIR_DTYPE = np.dtype([("row", "<i4"), ("col", "<i4"), ("hole", "<i2", (2,)), ("
                        ("degree", "i1"), ("phase", "i1"), ("pad", "<i2", (3,))])
 assert PAIR_DTYPE.itemsize == 24
 
-EXPORTS = ["hb_init", "hb_query", "hb_group_offset", "hb_build_blocks", "hb_diag", "hb_classify",
+EXPORTS = ["hb_init", "hb_init_shared", "hb_batch_create", "hb_batch_launch", "hb_batch_nodes",
+           "hb_batch_destroy", "hb_query", "hb_group_offset", "hb_build_blocks", "hb_diag", "hb_classify",
            "hb_classify_noalloc", "hb_mlp_set", "hb_mlp_param_count", "hb_mlp_workspace_bytes", "hb_mlp_loss_grad",
            "hb_mlp_adam", "hb_mlp_predict", "hb_diag_features", "hb_last_error", "hb_destroy"]
 
@@ -138,9 +139,10 @@ class Hamiltonian:
     cont_first, cont_count), l2_dets, e_core.
     """
 
-    def __init__(self, problem, split_slices=0, validate=True, stream=None):
+    def __init__(self, problem, split_slices=0, validate=True, stream=None, base=None):
         import torch
         self.lib = load()
+        self.base = base        # keeps a borrowed-integral base context alive
         p = problem
         keep = []
 
@@ -164,7 +166,14 @@ class Hamiltonian:
         opts = hb_options(split_slices, 1 if validate else 0)
         self.ctx = C.c_void_p()
         torch.cuda.init()
-        rc = self.lib.hb_init(C.byref(self.ctx), C.byref(self._problem), C.byref(opts), _stream_handle(stream))
+        if base is None:
+            rc = self.lib.hb_init(C.byref(self.ctx), C.byref(self._problem), C.byref(opts), _stream_handle(stream))
+        else:
+            self.lib.hb_init_shared.argtypes = [C.POINTER(C.c_void_p), C.POINTER(hb_problem), C.POINTER(hb_options),
+                                                C.c_void_p, C.c_void_p]
+            self.lib.hb_init_shared.restype = C.c_int
+            rc = self.lib.hb_init_shared(C.byref(self.ctx), C.byref(self._problem), C.byref(opts), base.ctx,
+                                         _stream_handle(stream))
         del keep, gs
         if rc != HB_OK:
             msg = self.lib.hb_last_error(None)
@@ -385,3 +394,59 @@ def diag_features(H, blocks, theta, stream=None):
     _check(_mlp_fns().hb_diag_features(H.ctx, C.byref(bs), th.ctypes.data, len(th), _ptr(out),
                                        _stream_handle(stream)), H.ctx)
     return out
+
+
+
+# --------------------------------------------------------------------------
+# batched build (CUDA graph over many staged Hamiltonians)
+# --------------------------------------------------------------------------
+
+class Batch:
+    """Stage several problems that share orbitals and integrals (the first one
+    owns the staged integrals) and build them all with one graph launch."""
+
+    def __init__(self, problems, precision=HB_MIXED, stream=None):
+        lib = load()
+        lib.hb_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                        C.c_void_p]
+        lib.hb_batch_create.restype = C.c_int
+        lib.hb_batch_launch.argtypes = [C.c_void_p, C.POINTER(hb_stats), C.c_void_p]
+        lib.hb_batch_launch.restype = C.c_int
+        lib.hb_batch_nodes.argtypes = [C.c_void_p]
+        lib.hb_batch_nodes.restype = C.c_int
+        lib.hb_batch_destroy.argtypes = [C.c_void_p]
+        lib.hb_batch_destroy.restype = None
+        self.lib = lib
+        self.hams = [Hamiltonian(problems[0], stream=stream)]
+        for p in problems[1:]:
+            self.hams.append(Hamiltonian(p, validate=False, stream=stream, base=self.hams[0]))
+        self.blocks = [h.allocate() for h in self.hams]
+        n = len(self.hams)
+        ctxs = (C.c_void_p * n)(*[h.ctx.value for h in self.hams])
+        outs = (hb_blocks * n)(*[Hamiltonian.blocks_struct(b) for b in self.blocks])
+        self._keep = (ctxs, outs)
+        self.handle = C.c_void_p()
+        _check(lib.hb_batch_create(C.byref(self.handle), ctxs, n, precision, outs, _stream_handle(stream)))
+        self.positions = sum(h.dim * (h.dim + 1) / 2 for h in self.hams)
+
+    @property
+    def nodes(self):
+        return self.lib.hb_batch_nodes(self.handle)
+
+    def launch(self, stream=None, stats=True):
+        st = hb_stats()
+        _check(self.lib.hb_batch_launch(self.handle, C.byref(st) if stats else None, _stream_handle(stream)))
+        return st
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self.lib.hb_batch_destroy(self.handle)
+            self.handle = C.c_void_p()
+        for h in reversed(getattr(self, "hams", [])):
+            h.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -312,3 +312,93 @@ def random_det_pairs(rng, n_orb, n_alpha, n_beta, W, count, max_exc=3, orbitals=
     bra = np.stack([o[0] for o in out])
     ket = np.stack([o[1] for o in out])
     return bra, ket
+
+
+# --------------------------------------------------------------------------
+# batched workload: 8 spatial symmetries x 2 spin couplings
+# --------------------------------------------------------------------------
+
+def _irrep_of(occ_a, occ_b, orb_irrep):
+    x = 0
+    for p in list(occ_a) + list(occ_b):
+        x ^= int(orb_irrep[p])
+    return x
+
+
+def make_batched_family(seed=4, n_hams=16, n_to=40, cont_per_irrep=(20, 60), n_elec=8, rank=32,
+                        dim_range=(500, 20000), max_det=600):
+    """16 Hamiltonians of one D2h-like molecule: total symmetry Gamma in 0..7
+    times two spin couplings (Ms = 0 targets + alpha continuum electron, and
+    Ms = +1 targets + beta continuum electron).  Orbitals carry irreps (XOR is
+    the group product); h and (pq|rs) vanish unless symmetry-allowed, so every
+    Hamiltonian shares the same integrals.  Target group i holds determinants
+    of irrep i and couples to the continuum orbitals of irrep i ^ Gamma (a
+    contiguous range, orbitals ordered by irrep); two extra groups repeat an
+    irrep with disjoint determinants (classes 5 and 6).  The target dimension of
+    each Hamiltonian is log-uniform in dim_range, about 40 % contracted and
+    60 % L2."""
+    rng = np.random.default_rng(seed)
+    n_irrep = 8
+    t_irrep = np.repeat(np.arange(n_irrep), n_to // n_irrep)
+    cont_counts = rng.integers(cont_per_irrep[0], cont_per_irrep[1] + 1, size=n_irrep)
+    c_irrep = np.repeat(np.arange(n_irrep), cont_counts)
+    cont_first = np.concatenate([[0], np.cumsum(cont_counts)[:-1]])
+    n_co = int(cont_counts.sum())
+    orb_irrep = np.concatenate([t_irrep, c_irrep])
+    h = make_h(rng, n_to, n_co, orb_irrep=orb_irrep)
+    L = make_chol(rng, n_to + n_co, rank, orb_irrep=orb_irrep)
+    eri = eri_classes(L, n_to, n_co)
+    W = max(1, (n_to + 63) // 64)
+    half = n_elec // 2
+    pools = {}
+    for spin in (ALPHA, BETA):
+        na, nb = (half, half) if spin == ALPHA else (half + 1, half - 1)
+        pool = sd_pool(na, nb, n_to)
+        by_irrep = {i: [] for i in range(n_irrep)}
+        for a, b in pool:
+            by_irrep[_irrep_of(a, b, orb_irrep)].append((a, b))
+        pools[spin] = by_irrep
+    l2pool = sd_pool(half + 1, half, n_to)
+    l2_by = {i: [] for i in range(n_irrep)}
+    for a, b in l2pool:
+        l2_by[_irrep_of(a, b, orb_irrep)].append((a, b))
+    dims = np.exp(rng.uniform(np.log(dim_range[0]), np.log(dim_range[1]), size=n_hams)).astype(int)
+    problems = []
+    for hidx in range(n_hams):
+        gam, spin = hidx % n_irrep, hidx // n_irrep
+        target = int(dims[hidx])
+        n_l2 = min(int(0.6 * target), len(l2_by[gam]))
+        contracted = target - n_l2
+        # groups: every target irrep, plus two repeats of irreps 0 and 1
+        irreps = list(range(n_irrep)) + [0, 1]
+        ns = rng.integers(1, 7, size=len(irreps))
+        cdim = sum(int(ns[g]) * int(cont_counts[irreps[g] ^ gam]) for g in range(len(irreps)))
+        # scale the state counts towards the contracted share
+        if cdim > 0:
+            f = max(0.2, contracted / cdim)
+            ns = np.maximum(1, np.minimum(6, np.round(ns * f))).astype(int)
+        used = {i: 0 for i in range(n_irrep)}
+        groups = []
+        for g, ir in enumerate(irreps):
+            avail = pools[spin][ir]
+            nd = min(max_det, max(int(ns[g]) + 2, len(avail) // 3))
+            start = used[ir]
+            if start + nd > len(avail):
+                nd = len(avail) - start
+            if nd < int(ns[g]) or nd <= 0:
+                continue
+            sel = avail[start:start + nd]
+            used[ir] += nd
+            perm = rng.permutation(len(sel))
+            dets = np.stack([occ_to_words(*sel[i], W) for i in perm])
+            ci = orthonormal_ci(rng, nd, int(min(ns[g], nd)))
+            cir = ir ^ gam
+            groups.append(Group(dets, ci, int(cont_first[cir]), int(cont_counts[cir])))
+        l2sel = [l2_by[gam][i] for i in rng.choice(len(l2_by[gam]), n_l2, replace=False)] if n_l2 else []
+        l2 = np.stack([occ_to_words(*x, W) for x in l2sel]) if l2sel else np.zeros((0, 2 * W), np.uint64)
+        problems.append(Problem(name=f"batch_G{gam}_s{spin}", n_to=n_to, n_co=n_co, n_elec=n_elec, n_words=W,
+                                cont_spin=spin, h=h, eri_tttt=eri[0], eri_tttc=eri[1], eri_ttcc=eri[2],
+                                eri_tctc=eri[3], groups=groups, l2_dets=np.ascontiguousarray(l2),
+                                meta=dict(seed=seed, gamma=gam, spin=spin, target_dim=target,
+                                          orb_irrep=orb_irrep)))
+    return problems
