@@ -141,7 +141,8 @@ typedef struct {
     double max_residual;
     float ms_matvec;
     float ms_rr;
-    int32_t reserved[8];
+    double expand_tensor_flops;  /* mixed: bf16 tensor flops of the split products */
+    int32_t reserved[6];
 } hb_stats;
 
 /* Excitation record of one determinant pair (row, col), see hb_classify. */

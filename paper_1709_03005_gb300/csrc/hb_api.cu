@@ -411,6 +411,7 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         return fail(ctx, HB_ERR_INVALID_ARG, "L2 CSR arrays are NULL");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
+    if (!ctx->capturing) mixed_reset_timers(ctx);
     int launches = 0;
     if (!ctx->capturing) CK(cudaEventRecord(ctx->ev[0], s));
     for (auto &P : ctx->gps) {
@@ -479,10 +480,18 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         st->ms_expand = t12;
         st->ms_class4 = t23;
         st->ms_l2 = t3e;
-        st->ms_expand_gemm = t12 + ms_gemm;
         st->expand_launches = n_expand;
         st->kernel_launches = launches;
         st->expand_flops = flops;
+        if (precision == HB_MIXED) {
+            int nl = 0;
+            st->ms_expand_gemm = mixed_kernel_ms(ctx, &nl);
+            const int S = mixed_slices(ctx);
+            st->expand_tensor_flops = flops * (double)(S * (S + 1) / 2);
+        } else {
+            st->ms_expand_gemm = t12 + ms_gemm;
+            st->expand_tensor_flops = 0.0;
+        }
     }
     return HB_OK;
 }

@@ -79,3 +79,6 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
 int expand_mixed(hb_ctx *ctx, hb::GroupPair &P, double *Hcc, cudaStream_t s);
 void release_mixed(hb_ctx *ctx);
 int mixed_error_word(hb_ctx *ctx, int *out);
+float mixed_kernel_ms(hb_ctx *ctx, int *launches);
+void mixed_reset_timers(hb_ctx *ctx);
+int mixed_slices(hb_ctx *ctx);

@@ -2,8 +2,9 @@
 // and spin-coupling blocks of one molecule, which share integrals through
 // hb_init_shared) built by one CUDA-graph launch.  The graph is captured once
 // from the ordinary build of every context (after one eager build that sets up
-// the tensor-core operands) and replayed by hb_batch_launch, so the host issues
-// a single launch for the whole set of uneven blocks.
+// the tensor-core operands), each context on its own branch so that their
+// kernels overlap, and replayed by hb_batch_launch: the host issues a single
+// launch for the whole set of uneven blocks.
 #include <cstring>
 #include <string>
 #include <vector>
@@ -44,23 +45,42 @@ extern "C" int hb_batch_create(hb_batch **out, hb_ctx *const *ctxs, int32_t n, i
     }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { delete b; return bfail(HB_ERR_CUDA, cudaGetErrorString(e)); }
-    // capture on a private stream (the legacy default stream cannot be captured)
+    // capture on a private stream (the legacy default stream cannot be captured);
+    // every context is its own branch of the graph (fork / join through events),
+    // so the small kernels of different Hamiltonians run concurrently
     cudaStream_t cs;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete b; return bfail(HB_ERR_CUDA, cudaGetErrorString(e)); }
+    std::vector<cudaStream_t> br(n, nullptr);
+    std::vector<cudaEvent_t> done(n, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < n; ++i) {
+        cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+    }
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     int rc = HB_OK;
     if (e == cudaSuccess) {
+        cudaEventRecord(fork, cs);
         for (int i = 0; i < n && rc == HB_OK; ++i) {
+            cudaStreamWaitEvent(br[i], fork, 0);
             ctxs[i]->capturing = true;
-            rc = hb_build_blocks(ctxs[i], precision, &outs[i], nullptr, cs);
+            rc = hb_build_blocks(ctxs[i], precision, &outs[i], nullptr, br[i]);
             ctxs[i]->capturing = false;
+            cudaEventRecord(done[i], br[i]);
+            cudaStreamWaitEvent(cs, done[i], 0);
         }
         cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
         if (e2 != cudaSuccess && rc == HB_OK) rc = bfail(HB_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e2));
     } else {
         rc = bfail(HB_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
     }
+    for (int i = 0; i < n; ++i) {
+        cudaStreamDestroy(br[i]);
+        cudaEventDestroy(done[i]);
+    }
+    cudaEventDestroy(fork);
     cudaStreamDestroy(cs);
     if (rc == HB_OK) {
         e = cudaGraphInstantiate(&b->exec, b->graph, 0);

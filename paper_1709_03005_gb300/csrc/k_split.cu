@@ -51,6 +51,8 @@ struct MixedState {
     int *err = nullptr;                       // device error word
     bool panel_ready = false;
     bool borrowed_panel = false;
+    std::vector<cudaEvent_t> ev;              // [2 * launches] around the split kernels of one build
+    int n_ev = 0;
     CUtensorMap tm_panel;
 };
 
@@ -645,12 +647,26 @@ int expand_mixed(hb_ctx *ctx, GroupPair &P, double *Hcc, cudaStream_t s) {
     cudaMemsetAsync(M.err, 0, sizeof(int), s);
     const dim3 grid((P.n_nn + BN - 1) / BN, ((A.cn + 7) / 8) * a.jpt_tiles);
     const size_t smem = M.slices * SLOT + 2048;
+    if (!ctx->capturing) {
+        if ((int)M.ev.size() < M.n_ev + 2) {
+            cudaEvent_t a0, a1;
+            cudaEventCreate(&a0);
+            cudaEventCreate(&a1);
+            M.ev.push_back(a0);
+            M.ev.push_back(a1);
+        }
+        cudaEventRecord(M.ev[M.n_ev], s);
+    }
     switch (M.slices) {
         case 2: split_expand_kernel<2><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
         case 3: split_expand_kernel<3><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
         case 4: split_expand_kernel<4><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
         case 5: split_expand_kernel<5><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
         default: split_expand_kernel<6><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
+    }
+    if (!ctx->capturing) {
+        cudaEventRecord(M.ev[M.n_ev + 1], s);
+        M.n_ev += 2;
     }
     // rows with j == j' in FP64
     const int j_lo = std::max(A.cf, B.cf), j_hi = std::min(A.cf + A.cn, B.cf + B.cn);
@@ -663,6 +679,28 @@ int expand_mixed(hb_ctx *ctx, GroupPair &P, double *Hcc, cudaStream_t s) {
     return HB_OK;
 }
 
+// Time of the split kernels of the last build (after its stream has finished),
+// and resets the counter for the next build.
+float mixed_kernel_ms(hb_ctx *ctx, int *launches) {
+    *launches = 0;
+    if (!ctx->mixed) return 0.0f;
+    MixedState &M = *ctx->mixed;
+    float total = 0.0f;
+    for (int i = 0; i + 1 < M.n_ev; i += 2) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, M.ev[i], M.ev[i + 1]) == cudaSuccess) total += t;
+        ++*launches;
+    }
+    M.n_ev = 0;
+    return total;
+}
+
+void mixed_reset_timers(hb_ctx *ctx) {
+    if (ctx->mixed) ctx->mixed->n_ev = 0;
+}
+
+int mixed_slices(hb_ctx *ctx) { return ctx->mixed ? ctx->mixed->slices : ctx->split_slices; }
+
 int mixed_error_word(hb_ctx *ctx, int *out) {
     *out = 0;
     if (!ctx->mixed || !ctx->mixed->err) return HB_OK;
@@ -674,6 +712,7 @@ void release_mixed(hb_ctx *ctx) {
     if (!ctx->mixed) return;
     if (!ctx->mixed->borrowed_panel) cudaFree(ctx->mixed->panel_slices);
     cudaFree(ctx->mixed->coef_slices);
+    for (cudaEvent_t e : ctx->mixed->ev) cudaEventDestroy(e);
     cudaFree(ctx->mixed->err);
     delete ctx->mixed;
     ctx->mixed = nullptr;

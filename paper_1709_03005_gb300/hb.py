@@ -54,7 +54,8 @@ class hb_stats(C.Structure):
                 ("ms_class4", C.c_float), ("ms_l2", C.c_float), ("ms_expand_gemm", C.c_float),
                 ("expand_launches", C.c_int32), ("kernel_launches", C.c_int32), ("expand_flops", C.c_double),
                 ("iterations", C.c_int32), ("mlp_fallbacks", C.c_int32), ("max_residual", C.c_double),
-                ("ms_matvec", C.c_float), ("ms_rr", C.c_float), ("reserved", C.c_int32 * 8)]
+                ("ms_matvec", C.c_float), ("ms_rr", C.c_float), ("expand_tensor_flops", C.c_double),
+                ("reserved", C.c_int32 * 6)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
