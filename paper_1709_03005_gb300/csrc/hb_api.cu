@@ -379,6 +379,7 @@ extern "C" int64_t hb_group_offset(const hb_ctx *ctx, int32_t g) {
 
 // Target side of one group pair: classification, H^N, S, E, gamma, coefficients.
 static int target_side(hb_ctx *ctx, GroupPair &P, cudaStream_t s, int *launches) {
+    if (!ctx) return HB_ERR_INVALID_ARG;
     const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
     const int W = ctx->W;
     const uint64_t *da = ctx->dets + A.det_off, *db = ctx->dets + B.det_off;
@@ -387,10 +388,16 @@ static int target_side(hb_ctx *ctx, GroupPair &P, cudaStream_t s, int *launches)
     const int n_keys = 2 * ctx->n_to * ctx->n_to;
     k1_fill_pairs(da, A.ndet, db, B.ndet, W, 0, ctx->cont_spin, 2, 0, P.rowptr, P.pairs, s);
     pair_values(I, da, db, W, P.pairs, P.n_pairs, P.val, s);
-    sandwich_rows(P.pairs, P.rowptr, P.val, 0, A.ndet, Cb, B.ns, P.W, s);
+    sandwich_rows(P.pairs, P.rowptr, P.val, A.ndet, Cb, B.ns, P.W, s);
     gemm_tn_reduce(Ca, P.W, A.ndet, A.ns, B.ns, P.partial, P.E, s);
-    sandwich_rows(P.pairs, P.rowptr, nullptr, 1, A.ndet, Cb, B.ns, P.W, s);
-    gemm_tn_reduce(Ca, P.W, A.ndet, A.ns, B.ns, P.partial, P.S, s);
+    // S = sum over identical determinants of c c'.  hb_init rejects repeated
+    // determinants, so within a group the identical pairs are (m, m) and
+    // S = C^T C, and between different groups S = 0.
+    if (P.same) {
+        gemm_tn_reduce(Ca, Ca, A.ndet, A.ns, B.ns, P.partial, P.S, s);
+    } else {
+        CK(cudaMemsetAsync(P.S, 0, sizeof(double) * (size_t)A.ns * B.ns, s));
+    }
     gamma_item_fill(P.pairs, P.rowptr, A.ndet, da, W, ctx->n_to, ctx->n_elec, P.item_ptr, P.items, s);
     gamma_sort(P.items, P.n_items, n_keys, P.sort_off, P.sort_cur, P.order, s);
     gamma_bins(P.items, P.order, P.sort_off, n_keys, P.n_items, Ca, A.ns, Cb, B.ns, P.gamma, s);
@@ -442,8 +449,8 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         GroupL2 &L = ctx->gl2[g];
         k1_fill_pairs(ctx->l2, ctx->n_l2, ctx->dets + G.det_off, G.ndet, ctx->W, 1, ctx->cont_spin, 2, 0, L.rowptr,
                       L.pairs, s);
-        class4_fp64(I, L.pairs, L.rowptr, ctx->n_l2, ctx->dets + G.det_off, ctx->ci + G.ci_off, G.ns, G.cf, G.cn,
-                    ctx->W, ctx->cont_spin, G.row_off, ctx->Dc, out->Hlc, s);
+        class4_build(I, L.pairs, L.rowptr, ctx->n_l2, ctx->dets + G.det_off, ctx->ci + G.ci_off, G.ns, G.cf, G.cn,
+                     ctx->W, ctx->cont_spin, G.row_off, ctx->Dc, out->Hlc, precision == HB_MIXED ? 1 : 0, s);
         launches += 2;
     }
     if (!ctx->capturing) CK(cudaEventRecord(ctx->ev[3], s));

@@ -67,8 +67,8 @@ void pair_values(const Ints &I, const uint64_t *A, const uint64_t *B, int W, con
                  int64_t n_pairs, double *val, cudaStream_t s);
 
 // K2 target side (k_target.cu)
-void sandwich_rows(const hb_pair *pairs, const int64_t *row_ptr, const double *val, int only_deg0, int n_rows,
-                   const double *Cp, int nsp, double *Wout, cudaStream_t s);
+void sandwich_rows(const hb_pair *pairs, const int64_t *row_ptr, const double *val, int n_rows, const double *Cp,
+                   int nsp, double *Wout, cudaStream_t s);
 int tn_chunks(int n_rows);
 void gemm_tn_reduce(const double *C, const double *Wm, int n_rows, int ns, int nsp, double *partials,
                     double *out, cudaStream_t s);
@@ -94,8 +94,9 @@ void expand_fp64(const double *P, const double *A, const int32_t *nn, int n_nn, 
                  double *H, cudaStream_t s);
 
 // K4 class 4 (k_class4.cu)
-void class4_fp64(const Ints &I, const hb_pair *pairs, const int64_t *row_ptr, int n_l2, const uint64_t *dets,
-                 const double *C, int ns, int cf, int cn, int W, int cont_spin, int64_t col_off, int64_t ld,
-                 double *Hlc, cudaStream_t s);
+// dfloat = 0: FP64 accumulation; 1: FP32 double-float accumulation (mixed path)
+void class4_build(const Ints &I, const hb_pair *pairs, const int64_t *row_ptr, int n_l2, const uint64_t *dets,
+                  const double *C, int ns, int cf, int cn, int W, int cont_spin, int64_t col_off, int64_t ld,
+                  double *Hlc, int dfloat, cudaStream_t s);
 
 }  // namespace hb

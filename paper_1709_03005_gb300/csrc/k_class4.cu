@@ -9,7 +9,11 @@
 // (tt|tc) class array, so the 128 threads of a block read them coalesced.
 // A block owns one L2 row and 128 continuum orbitals and keeps up to 32
 // target states in registers; the CI rows of a batch of partners are staged
-// in shared memory.
+// in shared memory.  The prototype values are always evaluated in FP64; the
+// rank-1 accumulation over partners is FP64 (plain build) or, in the mixed
+// build, double-float FP32 (exact products by FMA, TwoSum accumulation, about
+// 44 significant bits), which runs on the FP32 pipes instead of the much
+// slower FP64 pipe of this part.
 #include "hb_internal.cuh"
 
 namespace hb {
@@ -64,12 +68,19 @@ __device__ double prototype_value(const Ints &I, const hb_pair &r, const uint64_
     return r.phase * (dir - exc);
 }
 
-template <int W>
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+template <int W, int DF>
 __global__ void __launch_bounds__(kJ)
 class4_kernel(Ints I, const hb_pair *__restrict__ pairs, const int64_t *__restrict__ row_ptr,
               const uint64_t *__restrict__ dets, const double *__restrict__ C, int ns, int cf, int cn,
               int cont_spin, int64_t col_off, int64_t ld, double *__restrict__ Hlc) {
     __shared__ double cs[kBatch][kNS];
+    __shared__ float ch[kBatch][kNS], cl[kBatch][kNS];
     __shared__ hb_pair rs[kBatch];
     const int l = blockIdx.x;
     const int jl = blockIdx.y * kJ + threadIdx.x;
@@ -79,8 +90,9 @@ class4_kernel(Ints I, const hb_pair *__restrict__ pairs, const int64_t *__restri
     for (int n0 = 0; n0 < ns; n0 += kNS) {
         const int nc = min(kNS, ns - n0);
         double acc[kNS];
+        float ahi[kNS], alo[kNS];
 #pragma unroll
-        for (int n = 0; n < kNS; ++n) acc[n] = 0.0;
+        for (int n = 0; n < kNS; ++n) { acc[n] = 0.0; ahi[n] = 0.0f; alo[n] = 0.0f; }
         for (int64_t p0 = b; p0 < e; p0 += kBatch) {
             const int cnt = (int)(e - p0 < kBatch ? e - p0 : kBatch);
             __syncthreads();
@@ -88,38 +100,70 @@ class4_kernel(Ints I, const hb_pair *__restrict__ pairs, const int64_t *__restri
             __syncthreads();
             for (int t = threadIdx.x; t < cnt * kNS; t += kJ) {
                 const int i = t / kNS, n = t % kNS;
-                cs[i][n] = n < nc ? C[(int64_t)rs[i].col * ns + n0 + n] : 0.0;
+                const double c = n < nc ? C[(int64_t)rs[i].col * ns + n0 + n] : 0.0;
+                if (DF) {
+                    const float h = (float)c;
+                    ch[i][n] = h;
+                    cl[i][n] = (float)(c - (double)h);
+                } else {
+                    cs[i][n] = c;
+                }
             }
             __syncthreads();
             for (int i = 0; i < cnt; ++i) {
                 const hb_pair r = rs[i];
                 const double y = prototype_value<W>(I, r, dets + (int64_t)r.col * 2 * W, j, cont_spin);
+                if (DF) {
+                    const float yh = (float)y, yl = (float)(y - (double)yh);
 #pragma unroll
-                for (int n = 0; n < kNS; ++n) acc[n] = fma(cs[i][n], y, acc[n]);
+                    for (int n = 0; n < kNS; ++n) {
+                        const float ph = ch[i][n] * yh;
+                        const float pe = fmaf(ch[i][n], yh, -ph);             // exact error of ph
+                        const float pl = fmaf(ch[i][n], yl, fmaf(cl[i][n], yh, pe));
+                        float sum, err;
+                        two_sum(ahi[n], ph, sum, err);
+                        ahi[n] = sum;
+                        alo[n] = __fadd_rn(alo[n], __fadd_rn(err, pl));
+                    }
+                } else {
+#pragma unroll
+                    for (int n = 0; n < kNS; ++n) acc[n] = fma(cs[i][n], y, acc[n]);
+                }
             }
         }
         if (jv) {
             double *out = Hlc + (int64_t)l * ld + col_off + jl;
 #pragma unroll
             for (int n = 0; n < kNS; ++n)
-                if (n < nc) out[(int64_t)(n0 + n) * cn] = acc[n];
+                if (n < nc) out[(int64_t)(n0 + n) * cn] = DF ? (double)ahi[n] + (double)alo[n] : acc[n];
         }
     }
 }
 
 }  // namespace
 
-void class4_fp64(const Ints &I, const hb_pair *pairs, const int64_t *row_ptr, int n_l2, const uint64_t *dets,
-                 const double *C, int ns, int cf, int cn, int W, int cont_spin, int64_t col_off, int64_t ld,
-                 double *Hlc, cudaStream_t s) {
+void class4_build(const Ints &I, const hb_pair *pairs, const int64_t *row_ptr, int n_l2, const uint64_t *dets,
+                  const double *C, int ns, int cf, int cn, int W, int cont_spin, int64_t col_off, int64_t ld,
+                  double *Hlc, int dfloat, cudaStream_t s) {
     if (n_l2 <= 0 || cn <= 0) return;
     const dim3 grid(n_l2, (cn + kJ - 1) / kJ);
-    switch (W) {
-        case 1: class4_kernel<1><<<grid, kJ, 0, s>>>(I, pairs, row_ptr, dets, C, ns, cf, cn, cont_spin, col_off, ld, Hlc); break;
-        case 2: class4_kernel<2><<<grid, kJ, 0, s>>>(I, pairs, row_ptr, dets, C, ns, cf, cn, cont_spin, col_off, ld, Hlc); break;
-        case 3: class4_kernel<3><<<grid, kJ, 0, s>>>(I, pairs, row_ptr, dets, C, ns, cf, cn, cont_spin, col_off, ld, Hlc); break;
-        default: class4_kernel<4><<<grid, kJ, 0, s>>>(I, pairs, row_ptr, dets, C, ns, cf, cn, cont_spin, col_off, ld, Hlc); break;
+#define HB_C4(WW, DD) class4_kernel<WW, DD><<<grid, kJ, 0, s>>>(I, pairs, row_ptr, dets, C, ns, cf, cn, cont_spin, col_off, ld, Hlc)
+    if (dfloat) {
+        switch (W) {
+            case 1: HB_C4(1, 1); break;
+            case 2: HB_C4(2, 1); break;
+            case 3: HB_C4(3, 1); break;
+            default: HB_C4(4, 1); break;
+        }
+    } else {
+        switch (W) {
+            case 1: HB_C4(1, 0); break;
+            case 2: HB_C4(2, 0); break;
+            case 3: HB_C4(3, 0); break;
+            default: HB_C4(4, 0); break;
+        }
     }
+#undef HB_C4
 }
 
 }  // namespace hb

@@ -17,29 +17,40 @@ namespace hb {
 namespace {
 
 // ---------------------------------------------------------------- sandwich
-// Wout[m][n'] = sum over records k of row m (in order) of v_k * Cp[col_k][n']
+// Wout[m][n'] = sum over records k of row m of v_k * Cp[col_k][n'].  One warp
+// per row: lane l takes records l, l+32, ... (fixed order), 16 columns at a
+// time, then a butterfly reduction over the lanes (fixed order as well).
 __global__ void sandwich_kernel(const hb_pair *__restrict__ pairs, const int64_t *__restrict__ row_ptr,
-                                const double *__restrict__ val, int only_deg0, int n_rows,
-                                const double *__restrict__ Cp, int nsp, double *__restrict__ Wout) {
+                                const double *__restrict__ val, int n_rows, const double *__restrict__ Cp, int nsp,
+                                double *__restrict__ Wout) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= n_rows) return;
     const int64_t b = row_ptr[row], e = row_ptr[row + 1];
-    for (int n0 = 0; n0 < nsp; n0 += 32) {
-        const int n = n0 + lane;
-        double acc = 0.0;
-        for (int64_t k = b; k < e; ++k) {
-            const hb_pair r = pairs[k];
-            double v;
-            if (only_deg0) {
-                if (r.degree != 0) continue;
-                v = 1.0;
-            } else {
-                v = val[k];
-            }
-            if (n < nsp) acc = fma(v, __ldg(Cp + (int64_t)r.col * nsp + n), acc);
+    for (int n0 = 0; n0 < nsp; n0 += 16) {
+        double acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int col = pairs[k].col;
+            const double v = val[k];
+            const double *crow = Cp + (int64_t)col * nsp + n0;
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (n0 + c < nsp) acc[c] = fma(v, __ldg(crow + c), acc[c]);
         }
-        if (n < nsp) Wout[(int64_t)row * nsp + n] = acc;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+#pragma unroll
+            for (int off = 16; off; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+        }
+        if (lane < 16 && n0 + lane < nsp) {
+            double mine = 0.0;
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c == lane) mine = acc[c];
+            Wout[(int64_t)row * nsp + n0 + lane] = mine;
+        }
     }
 }
 
@@ -291,10 +302,10 @@ __global__ void assemble_kernel(const double *__restrict__ gamma, const double *
 
 }  // namespace
 
-void sandwich_rows(const hb_pair *pairs, const int64_t *row_ptr, const double *val, int only_deg0, int n_rows,
-                   const double *Cp, int nsp, double *Wout, cudaStream_t s) {
+void sandwich_rows(const hb_pair *pairs, const int64_t *row_ptr, const double *val, int n_rows, const double *Cp,
+                   int nsp, double *Wout, cudaStream_t s) {
     if (n_rows <= 0) return;
-    sandwich_kernel<<<(n_rows + 7) / 8, 256, 0, s>>>(pairs, row_ptr, val, only_deg0, n_rows, Cp, nsp, Wout);
+    sandwich_kernel<<<(n_rows + 7) / 8, 256, 0, s>>>(pairs, row_ptr, val, n_rows, Cp, nsp, Wout);
 }
 
 int tn_chunks(int n_rows) { return (n_rows + kRowsPerChunk - 1) / kRowsPerChunk; }
