@@ -71,6 +71,7 @@ def load():
         lib.orc_cc_element_abs.restype = dbl
         lib.orc_cc_element_abs.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         lib.orc_cc_expand_abs.argtypes = [vp, vp, i64, i64, i64]
+        lib.orc_cc_expand_rows.argtypes = [vp, vp, C.c_int, C.c_int]
         lib.orc_class4_rows.argtypes = [vp, C.c_int, C.c_int, vp]
         _lib = lib
     return _lib
@@ -210,6 +211,15 @@ class _CC:
 
     def element_abs(self, n, j, np_, jp) -> float:
         return self.orc.lib.orc_cc_element_abs(self.h, n, j, np_, jp)
+
+    def expand_rows(self, jj0, jj1):
+        """Elements [(jj, jj', n, n')] for rows jj0 <= jj < jj1 of this block."""
+        P = self.orc.problem
+        cnp = P.groups[self.gp].cont_count
+        ns, nsp = P.groups[self.g].ci.shape[1], P.groups[self.gp].ci.shape[1]
+        out = np.zeros((jj1 - jj0, cnp, ns, nsp))
+        self.orc.lib.orc_cc_expand_rows(self.h, _ptr(out), int(jj0), int(jj1))
+        return out
 
     def nlabels(self, which=0):
         return self.orc.lib.orc_cc_nlabels(self.h, which)

@@ -35,6 +35,7 @@
  * beyond the order stated above.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -377,6 +378,17 @@ typedef struct {
     double *K0;     /* j-independent part of the same-orbital prototype [n][n'] */
 } orc_cc;
 
+/* Merge map b into map a (blocks added label by label). */
+static void map_merge(orc_map *a, const orc_map *b) {
+    for (int64_t i = 0; i < b->cap; ++i) {
+        const int s = b->slot[i];
+        if (s < 0) continue;
+        double *dst = map_get(a, b->keys[i]);
+        const double *src = b->blocks + (int64_t)s * b->bsz;
+        for (int64_t t = 0; t < a->bsz; ++t) dst[t] += src[t];
+    }
+}
+
 orc_cc *orc_cc_contract(const orc_problem *P, int g, int gp) {
     orc_cc *c = (orc_cc *)calloc(1, sizeof(orc_cc));
     c->P = P; c->g = g; c->gp = gp;
@@ -388,50 +400,73 @@ orc_cc *orc_cc_contract(const orc_problem *P, int g, int gp) {
     const int W = P->W, We = ext_words(P), ph = P->n_to, phk = P->n_to + 1, sc = P->cont_spin;
     const uint64_t *Dg = P->g_dets[g], *Dgp = P->g_dets[gp];
     const double *Cg = P->g_ci[g], *Cgp = P->g_ci[gp];
-    orc_sym *buf = (orc_sym *)malloc(sizeof(orc_sym) * 8192);
-    double *cc = (double *)malloc(sizeof(double) * bsz);
-    uint64_t I[2 * ORC_MAXW], J[2 * ORC_MAXW];
-    for (int m = 0; m < P->g_ndet[g]; ++m) {
-        const uint64_t *Dm = Dg + (int64_t)m * 2 * W;
-        for (int mp = 0; mp < P->g_ndet[gp]; ++mp) {
-            const uint64_t *Dmp = Dgp + (int64_t)mp * 2 * W;
-            int nd = 0;
-            for (int w = 0; w < 2 * W; ++w) nd += popc64(Dm[w] ^ Dmp[w]);
-            if (nd > 4) continue;
-            for (int a = 0; a < ns; ++a)
-                for (int b = 0; b < nsp; ++b)
-                    cc[a * nsp + b] = Cg[(int64_t)m * ns + a] * Cgp[(int64_t)mp * nsp + b];
-            /* prototype 1: the same continuum orbital in bra and ket */
-            extend(P, Dm, ph, sc, I);
-            extend(P, Dmp, ph, sc, J);
-            int n = orc_symbols(We, I, J, buf, 8192);
-            for (int k = 0; k < n; ++k) {
-                uint64_t L = buf[k].label;
-                int has = 0;
-                for (int s = 0; s < 4; ++s) has |= (int)(((L >> (16 * s)) & 0xFFFFu) == (uint64_t)ph);
-                if (!has) {
-                    double x = buf[k].coef * orc_X(P, L, -1, 0, -1, 0);
-                    for (int t = 0; t < bsz; ++t) c->K0[t] += cc[t] * x;
-                } else {
-                    double *blk = map_get(&c->same, L);
-                    for (int t = 0; t < bsz; ++t) blk[t] += cc[t] * buf[k].coef;
-                }
-            }
-            if (nd == 0 && P->e_core != 0.0)
-                for (int t = 0; t < bsz; ++t) c->K0[t] += cc[t] * P->e_core;
-            /* prototype 2: different continuum orbitals (j in bra, j' in ket) */
-            if (nd <= 2) {
+    /* bra determinants are split over threads; every thread contracts into its
+       own maps (Eq. 8 sums), merged in thread order at the end */
+#pragma omp parallel
+    {
+        orc_map same, diff;
+        map_init(&same, bsz);
+        map_init(&diff, bsz);
+        double *K0 = (double *)calloc((size_t)bsz, sizeof(double));
+        orc_sym *buf = (orc_sym *)malloc(sizeof(orc_sym) * 8192);
+        double *cc = (double *)malloc(sizeof(double) * bsz);
+        uint64_t I[2 * ORC_MAXW], J[2 * ORC_MAXW];
+#pragma omp for schedule(static)
+        for (int m = 0; m < P->g_ndet[g]; ++m) {
+            const uint64_t *Dm = Dg + (int64_t)m * 2 * W;
+            for (int mp = 0; mp < P->g_ndet[gp]; ++mp) {
+                const uint64_t *Dmp = Dgp + (int64_t)mp * 2 * W;
+                int nd = 0;
+                for (int w = 0; w < 2 * W; ++w) nd += popc64(Dm[w] ^ Dmp[w]);
+                if (nd > 4) continue;
+                for (int a = 0; a < ns; ++a)
+                    for (int b = 0; b < nsp; ++b)
+                        cc[a * nsp + b] = Cg[(int64_t)m * ns + a] * Cgp[(int64_t)mp * nsp + b];
+                /* prototype 1: the same continuum orbital in bra and ket */
                 extend(P, Dm, ph, sc, I);
-                extend(P, Dmp, phk, sc, J);
-                n = orc_symbols(We, I, J, buf, 8192);
+                extend(P, Dmp, ph, sc, J);
+                int n = orc_symbols(We, I, J, buf, 8192);
                 for (int k = 0; k < n; ++k) {
-                    double *blk = map_get(&c->diff, buf[k].label);
-                    for (int t = 0; t < bsz; ++t) blk[t] += cc[t] * buf[k].coef;
+                    uint64_t L = buf[k].label;
+                    int has = 0;
+                    for (int s2 = 0; s2 < 4; ++s2) has |= (int)(((L >> (16 * s2)) & 0xFFFFu) == (uint64_t)ph);
+                    if (!has) {
+                        double x = buf[k].coef * orc_X(P, L, -1, 0, -1, 0);
+                        for (int t = 0; t < bsz; ++t) K0[t] += cc[t] * x;
+                    } else {
+                        double *blk = map_get(&same, L);
+                        for (int t = 0; t < bsz; ++t) blk[t] += cc[t] * buf[k].coef;
+                    }
+                }
+                if (nd == 0 && P->e_core != 0.0)
+                    for (int t = 0; t < bsz; ++t) K0[t] += cc[t] * P->e_core;
+                /* prototype 2: different continuum orbitals (j in bra, j' in ket) */
+                if (nd <= 2) {
+                    extend(P, Dm, ph, sc, I);
+                    extend(P, Dmp, phk, sc, J);
+                    n = orc_symbols(We, I, J, buf, 8192);
+                    for (int k = 0; k < n; ++k) {
+                        double *blk = map_get(&diff, buf[k].label);
+                        for (int t = 0; t < bsz; ++t) blk[t] += cc[t] * buf[k].coef;
+                    }
                 }
             }
         }
+#pragma omp for ordered schedule(static, 1)
+        for (int th = 0; th < omp_get_num_threads(); ++th) {
+#pragma omp ordered
+            {
+                map_merge(&c->same, &same);
+                map_merge(&c->diff, &diff);
+                for (int t = 0; t < bsz; ++t) c->K0[t] += K0[t];
+            }
+        }
+        map_free(&same);
+        map_free(&diff);
+        free(K0);
+        free(buf);
+        free(cc);
     }
-    free(buf); free(cc);
     return c;
 }
 
@@ -705,4 +740,48 @@ void orc_cc_expand_abs(const orc_cc *c, double *H, int64_t ld, int64_t row0, int
                     H[r * ld + cl] = v;
                     H[cl * ld + r] = v;
                 }
+}
+
+/* Expansion (Eq. 7) of the rows jj in [jj0, jj1) of a group-pair block only,
+   for every state pair (a bounded sample of orc_cc_expand): the integrals of
+   every label are looked up once per (j, j'), then used for all (n, n'). */
+void orc_cc_expand_rows(const orc_cc *c, double *out, int jj0, int jj1) {
+    const orc_problem *P = c->P;
+    const int cfg = P->g_cfirst[c->g];
+    const int cfp = P->g_cfirst[c->gp], cnp = P->g_ccount[c->gp];
+    const int nr = jj1 - jj0, bsz = c->ns * c->nsp;
+    const int64_t ns_ = c->same.n, nd_ = c->diff.n;
+    uint64_t *ks = (uint64_t *)malloc(sizeof(uint64_t) * (ns_ + 1));
+    uint64_t *kd = (uint64_t *)malloc(sizeof(uint64_t) * (nd_ + 1));
+    for (int64_t i = 0; i < c->same.cap; ++i) if (c->same.slot[i] >= 0) ks[c->same.slot[i]] = c->same.keys[i];
+    for (int64_t i = 0; i < c->diff.cap; ++i) if (c->diff.slot[i] >= 0) kd[c->diff.slot[i]] = c->diff.keys[i];
+    const int ph = P->n_to, phk = P->n_to + 1;
+#pragma omp parallel
+    {
+        double *xs = (double *)malloc(sizeof(double) * (ns_ + 1));
+        double *xd = (double *)malloc(sizeof(double) * (nd_ + 1));
+#pragma omp for collapse(2) schedule(dynamic, 4)
+        for (int r = 0; r < nr; ++r)
+            for (int jjp = 0; jjp < cnp; ++jjp) {
+                const int j = cfg + jj0 + r, jp = cfp + jjp;
+                const int same = (j == jp);
+                if (same) for (int64_t i = 0; i < ns_; ++i) xs[i] = orc_X(P, ks[i], ph, P->n_to + j, -1, 0);
+                else for (int64_t i = 0; i < nd_; ++i) xd[i] = orc_X(P, kd[i], ph, P->n_to + j, phk, P->n_to + jp);
+                double *o = out + ((int64_t)r * cnp + jjp) * bsz;
+                for (int t = 0; t < bsz; ++t) {
+                    double v = 0.0;
+                    if (same) {
+                        v = c->K0[t];
+                        for (int64_t i = 0; i < ns_; ++i) v += c->same.blocks[i * bsz + t] * xs[i];
+                    } else {
+                        for (int64_t i = 0; i < nd_; ++i) v += c->diff.blocks[i * bsz + t] * xd[i];
+                    }
+                    o[t] = v;
+                }
+            }
+        free(xs);
+        free(xd);
+    }
+    free(ks);
+    free(kd);
 }
