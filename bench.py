@@ -165,6 +165,20 @@ def cpu_baseline(problem, budget_s=20.0):
             "sample": f"{what} of {problem.name} ({covered:.3e} positions, {dt:.2f} s)"}
 
 
+def replica_throughput(local_ms, steps, dim, world, device):
+    """Whole-job throughput of `world` independent replicas (weak scaling: every
+    rank builds the same workload).  After a barrier the slowest rank's time
+    decides: value = world x steps x positions / max over ranks of the time.
+    Returns (max_ms, value)."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return max_ms, world * steps * positions(dim) / (max_ms / 1000.0)
+
+
 def run_reference(args, rank, world):
     from paper_1709_03005_gb300 import synth
     if rank != 0:
@@ -222,14 +236,7 @@ def run_ours(args, rank, world, local_rank):
             launches += st.kernel_launches
             flops_exp = st.expand_flops
         torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    total_ms = float(np.sum(times))
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * args.steps * positions(dim) / (total_ms / 1000.0)
+    total_ms, value = replica_throughput(float(np.sum(times)), args.steps, dim, world, "cuda")
 
     # end to end through the public API with host buffers: staging (H2D of the
     # problem), build, and the D2H read of every block, each step
