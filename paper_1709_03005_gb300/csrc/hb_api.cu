@@ -8,6 +8,7 @@
 
 #include "hb_api_internal.cuh"
 #include "hb_davidson.cuh"
+#include "hb_plan.cuh"
 
 using namespace hb;
 
@@ -339,6 +340,7 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         DALLOC(P.gamma, n_keys * nout);
         DALLOC(P.W, (int64_t)A.ndet * B.ns);
         DALLOC(P.partial, (int64_t)tn_chunks(A.ndet) * nout);
+        DALLOC(P.partial_s, P.same ? (int64_t)tn_chunks(A.ndet) * nout : 1);
         DALLOC(P.S, nout);
         DALLOC(P.E, nout);
         std::vector<int32_t> nn;
@@ -352,7 +354,6 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         CK(cudaStreamSynchronize(s));
     }
     for (auto &L : ctx->gl2) DALLOC(L.pairs, L.n_pairs);
-    for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ctx->ev[i]));
     CK(cudaStreamSynchronize(s));
     return HB_OK;
 }
@@ -377,36 +378,6 @@ extern "C" int64_t hb_group_offset(const hb_ctx *ctx, int32_t g) {
     return g == ctx->n_groups ? ctx->Dc : ctx->groups[g].row_off;
 }
 
-// Target side of one group pair: classification, H^N, S, E, gamma, coefficients.
-static int target_side(hb_ctx *ctx, GroupPair &P, cudaStream_t s, int *launches) {
-    if (!ctx) return HB_ERR_INVALID_ARG;
-    const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
-    const int W = ctx->W;
-    const uint64_t *da = ctx->dets + A.det_off, *db = ctx->dets + B.det_off;
-    const double *Ca = ctx->ci + A.ci_off, *Cb = ctx->ci + B.ci_off;
-    Ints I = ctx->ints();
-    const int n_keys = 2 * ctx->n_to * ctx->n_to;
-    k1_fill_pairs(da, A.ndet, db, B.ndet, W, 0, ctx->cont_spin, 2, 0, P.rowptr, P.pairs, s);
-    pair_values(I, da, db, W, P.pairs, P.n_pairs, P.val, s);
-    sandwich_rows(P.pairs, P.rowptr, P.val, A.ndet, Cb, B.ns, P.W, s);
-    gemm_tn_reduce(Ca, P.W, A.ndet, A.ns, B.ns, P.partial, P.E, s);
-    // S = sum over identical determinants of c c'.  hb_init rejects repeated
-    // determinants, so within a group the identical pairs are (m, m) and
-    // S = C^T C, and between different groups S = 0.
-    if (P.same) {
-        gemm_tn_reduce(Ca, Ca, A.ndet, A.ns, B.ns, P.partial, P.S, s);
-    } else {
-        CK(cudaMemsetAsync(P.S, 0, sizeof(double) * (size_t)A.ns * B.ns, s));
-    }
-    gamma_item_fill(P.pairs, P.rowptr, A.ndet, da, W, ctx->n_to, ctx->n_elec, P.item_ptr, P.items, s);
-    gamma_sort(P.items, P.n_items, n_keys, P.sort_off, P.sort_cur, P.order, s);
-    gamma_bins(P.items, P.order, P.sort_off, n_keys, P.n_items, Ca, A.ns, Cb, B.ns, P.gamma, s);
-    assemble_coefficients(P.gamma, P.S, P.E, P.nn, P.n_nn, A.ns, B.ns, ctx->n_to, ctx->cont_spin, ctx->e_core,
-                          ctx->Kpad, P.A, s);
-    *launches += 14;
-    return HB_OK;
-}
-
 extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *out, hb_stats *st,
                                void *stream) {
     if (!ctx || !out) return fail(ctx, HB_ERR_INVALID_ARG, "NULL argument");
@@ -418,88 +389,38 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         return fail(ctx, HB_ERR_INVALID_ARG, "L2 CSR arrays are NULL");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
-    if (!ctx->capturing) mixed_reset_timers(ctx);
+    // the build as a plan of grouped launches over this context's group pairs,
+    // kept between builds (made again for another precision, re-pointed for
+    // other output blocks)
+    hb::Plan *plan = (hb::Plan *)ctx->plan;
+    std::string err;
+    if (plan && plan_precision(plan) != precision) {
+        cudaStreamSynchronize(s);
+        plan_destroy(plan);
+        plan = nullptr;
+        ctx->plan = nullptr;
+    }
+    if (!plan) {
+        hb_ctx *one[1] = {ctx};
+        int rc = plan_create(one, 1, out, precision, &plan, &err, s);
+        if (rc != HB_OK) return fail(ctx, rc, err);
+        ctx->plan = plan;
+    } else if (!plan_outputs_equal(plan, out)) {
+        int rc = plan_set_outputs(plan, out, &err, s);
+        if (rc != HB_OK) return fail(ctx, rc, err);
+    }
     int launches = 0;
-    if (!ctx->capturing) CK(cudaEventRecord(ctx->ev[0], s));
-    for (auto &P : ctx->gps) {
-        int rc = target_side(ctx, P, s, &launches);
-        if (rc != HB_OK) return rc;
-    }
-    if (!ctx->capturing) CK(cudaEventRecord(ctx->ev[1], s));
-    float ms_gemm = 0.0f;
-    int n_expand = 0;
-    double flops = 0.0;
-    for (auto &P : ctx->gps) {
-        const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
-        if (precision == HB_MIXED) {
-            int rc = expand_mixed(ctx, P, out->Hcc, s);
-            if (rc != HB_OK) return rc;
-        } else {
-            expand_fp64(ctx->panel, P.A, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, A.cf, A.cn, B.cf, B.cn, A.row_off,
-                        B.row_off, P.same, ctx->Dc, out->Hcc, s);
-        }
-        ++n_expand;
-        flops += 2.0 * (double)A.cn * B.cn * P.n_nn * ctx->K;
-    }
-    launches += n_expand;
-    if (!ctx->capturing) CK(cudaEventRecord(ctx->ev[2], s));
-    Ints I = ctx->ints();
-    for (int g = 0; g < ctx->n_groups; ++g) {
-        const GroupInfo &G = ctx->groups[g];
-        GroupL2 &L = ctx->gl2[g];
-        k1_fill_pairs(ctx->l2, ctx->n_l2, ctx->dets + G.det_off, G.ndet, ctx->W, 1, ctx->cont_spin, 2, 0, L.rowptr,
-                      L.pairs, s);
-        class4_build(I, L.pairs, L.rowptr, ctx->n_l2, ctx->dets + G.det_off, ctx->ci + G.ci_off, G.ns, G.cf, G.cn,
-                     ctx->W, ctx->cont_spin, G.row_off, ctx->Dc, out->Hlc, precision == HB_MIXED ? 1 : 0, s);
-        launches += 2;
-    }
-    if (!ctx->capturing) CK(cudaEventRecord(ctx->ev[3], s));
-    if (ctx->n_l2 > 0) {
-        CK(cudaMemcpyAsync(out->l2_row_ptr, ctx->l2_rowptr, sizeof(int64_t) * (ctx->n_l2 + 1),
-                           cudaMemcpyDeviceToDevice, s));
-        l2_csr_fill(I, ctx->l2, ctx->n_l2, ctx->W, ctx->l2_rowptr, out->l2_col, out->l2_val, ctx->e_core, s);
-        launches += 1;
-    }
-    CK(cudaGetLastError());
-    if (precision == HB_MIXED && !ctx->capturing) {
+    int rc = plan_run(plan, s, true, &launches, &err);
+    if (rc != HB_OK) return fail(ctx, rc, err);
+    if (precision == HB_MIXED) {
         // the tensor-core kernel reports a bounded-wait timeout in a device word
         int word = 0;
         CK(cudaStreamSynchronize(s));
-        if (mixed_error_word(ctx, &word) != HB_OK) return fail(ctx, HB_ERR_CUDA, "reading the mixed error word");
+        if (plan_error_word(plan, &word) != HB_OK) return fail(ctx, HB_ERR_CUDA, "reading the mixed error word");
         if (word != 0)
             return fail(ctx, HB_ERR_TIMEOUT, "split expansion kernel gave up waiting (code " + std::to_string(word) + ")");
     }
-    if (st && !ctx->capturing) {
-        cudaEvent_t end;
-        CK(cudaEventCreate(&end));
-        CK(cudaEventRecord(end, s));
-        CK(cudaEventSynchronize(end));
-        float t01, t12, t23, t3e, t0e;
-        cudaEventElapsedTime(&t01, ctx->ev[0], ctx->ev[1]);
-        cudaEventElapsedTime(&t12, ctx->ev[1], ctx->ev[2]);
-        cudaEventElapsedTime(&t23, ctx->ev[2], ctx->ev[3]);
-        cudaEventElapsedTime(&t3e, ctx->ev[3], end);
-        cudaEventElapsedTime(&t0e, ctx->ev[0], end);
-        cudaEventDestroy(end);
-        memset(st, 0, sizeof(*st));
-        st->ms_total = t0e;
-        st->ms_target = t01;
-        st->ms_expand = t12;
-        st->ms_class4 = t23;
-        st->ms_l2 = t3e;
-        st->expand_launches = n_expand;
-        st->kernel_launches = launches;
-        st->expand_flops = flops;
-        if (precision == HB_MIXED) {
-            int nl = 0;
-            st->ms_expand_gemm = mixed_kernel_ms(ctx, &nl);
-            const int S = mixed_slices(ctx);
-            st->expand_tensor_flops = flops * (double)(S * (S + 1) / 2);
-        } else {
-            st->ms_expand_gemm = t12 + ms_gemm;
-            st->expand_tensor_flops = 0.0;
-        }
-    }
+    if (st) plan_stats(plan, st);
     return HB_OK;
 }
 
@@ -537,8 +458,11 @@ extern "C" const char *hb_last_error(const hb_ctx *ctx) {
 extern "C" void hb_destroy(hb_ctx *ctx) {
     if (!ctx) return;
     for (void *p : ctx->allocs) cudaFree(p);
-    for (int i = 0; i < 4; ++i)
-        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->plan) {
+        cudaDeviceSynchronize();
+        plan_destroy((hb::Plan *)ctx->plan);
+        ctx->plan = nullptr;
+    }
     release_mixed(ctx);
     hb::release_diag(ctx);
     hb::release_mlp(ctx);

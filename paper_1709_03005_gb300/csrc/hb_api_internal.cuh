@@ -25,7 +25,7 @@ struct GroupPair {
     GammaItem *items = nullptr;
     int32_t *order = nullptr;
     int64_t *sort_off = nullptr, *sort_cur = nullptr;
-    double *gamma = nullptr, *W = nullptr, *partial = nullptr, *S = nullptr, *E = nullptr;
+    double *gamma = nullptr, *W = nullptr, *partial = nullptr, *partial_s = nullptr, *S = nullptr, *E = nullptr;
     int32_t *nn = nullptr;
     double *A = nullptr;        // [n_nn][Kpad] contracted coefficients
 };
@@ -60,10 +60,9 @@ struct hb_ctx {
     double *ci = nullptr;
     int64_t *l2_rowptr = nullptr;
     int64_t l2_nnz = 0, tt_pairs = 0, tl2_pairs = 0;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     hb::MixedState *mixed = nullptr;
     hb_ctx *base = nullptr;  // context whose staged integrals this one borrows (or null)
-    bool capturing = false;  // inside a CUDA-graph capture: no host synchronisation
+    void *plan = nullptr;    // cached grouped-launch plan of this context's own builds (k_plan.cu)
     void *diag = nullptr;   // Davidson workspace (k_davidson.cu)
     void *mlp = nullptr;    // learned preconditioner weights (k_mlp.cu)
 
@@ -76,9 +75,4 @@ struct hb_ctx {
 };
 
 int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStream_t s);
-int expand_mixed(hb_ctx *ctx, hb::GroupPair &P, double *Hcc, cudaStream_t s);
 void release_mixed(hb_ctx *ctx);
-int mixed_error_word(hb_ctx *ctx, int *out);
-float mixed_kernel_ms(hb_ctx *ctx, int *launches);
-void mixed_reset_timers(hb_ctx *ctx);
-int mixed_slices(hb_ctx *ctx);

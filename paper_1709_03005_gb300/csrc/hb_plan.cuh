@@ -1,0 +1,30 @@
+// Build plan: every stage of the Hamiltonian build as one grouped launch over
+// all target-group pairs, target groups and L2 sets of one or many staged
+// Hamiltonians (k_plan.cu).
+#pragma once
+
+#include <vector>
+
+#include "hb_api_internal.cuh"
+
+namespace hb {
+struct Plan;
+}
+
+// Plan over n contexts (same orbital space: equal n_words, n_to and label
+// count) writing into outs[i].  Prepares the tensor-core operands when
+// precision is HB_MIXED.  Returns HB_OK or an error with *err set.
+int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision, hb::Plan **out, std::string *err,
+                cudaStream_t s);
+// Point the plan's tasks at new output blocks (re-uploads the task tables).
+int plan_set_outputs(hb::Plan *p, const hb_blocks *outs, std::string *err, cudaStream_t s);
+bool plan_outputs_equal(const hb::Plan *p, const hb_blocks *outs);
+int plan_precision(const hb::Plan *p);
+// Issue every stage on stream s.  timing: record stage events (not inside a
+// graph capture).  *launches: kernels launched.
+int plan_run(hb::Plan *p, cudaStream_t s, bool timing, int *launches, std::string *err);
+// After the stream has finished a timed run: per-stage times and counters.
+void plan_stats(hb::Plan *p, hb_stats *st);
+// Bounded-wait status word of the tensor-core kernel (0: fine).
+int plan_error_word(hb::Plan *p, int *word);
+void plan_destroy(hb::Plan *p);

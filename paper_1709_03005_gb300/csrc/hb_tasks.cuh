@@ -1,0 +1,201 @@
+// Grouped launches: one kernel launch runs one stage of the build for many
+// independent tasks (the target-group pairs, target groups or L2 sets of one
+// or many Hamiltonians).  Every task owns a contiguous range of the grid's
+// blocks; blk[t] is the first block of task t and blk[n] the grid size, so a
+// block finds its task by binary search and runs the stage's body on that
+// task's arguments with its block index inside the task.
+#pragma once
+
+#include "hb_internal.cuh"
+
+namespace hb {
+
+// Last task t with blk[t] <= b (tasks with no blocks are skipped over).
+__device__ __forceinline__ int task_of(const int64_t *__restrict__ blk, int n, int64_t b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(blk + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// A stage as launched: its task table and block ranges on the device.
+template <class T>
+struct Grouped {
+    const T *tasks = nullptr;
+    const int64_t *blk = nullptr;
+    int n = 0;
+    int64_t blocks = 0;
+};
+
+// ----------------------------------------------------------------- tasks
+struct ClsTask {        // K1: classify rows of a against b into records
+    const uint64_t *a, *b;
+    int n_a, n_b, cont_spin, max_degree, lower;
+    const int64_t *row_ptr;
+    hb_pair *out;
+};
+
+struct PVTask {         // <D_m|H^N|D'_m'> for the records of a group pair
+    Ints I;
+    const uint64_t *a, *b;
+    const hb_pair *pairs;
+    int64_t n_pairs;
+    double *val;
+};
+
+struct SWTask {         // W = V C' row by row
+    const hb_pair *pairs;
+    const int64_t *row_ptr;
+    const double *val;
+    int n_rows;
+    const double *Cp;
+    int nsp;
+    double *Wout;
+};
+
+struct TNTask {         // out = C^T W by chunked partials (n_rows = 0 gives zeros)
+    const double *C, *Wm;
+    int n_rows, ns, nsp, ny;
+    double *partial, *out;
+};
+
+struct IFTask {         // gamma items of the records of a group pair
+    const hb_pair *pairs;
+    const int64_t *row_ptr;
+    int n_rows;
+    const uint64_t *bra;
+    int W, n_to, n_elec;
+    const int64_t *item_ptr;
+    GammaItem *items;
+};
+
+struct ZTask {          // zero n 8-byte words
+    int64_t *p;
+    int64_t n;
+};
+
+struct SortTask {       // stable counting sort of the gamma items by key
+    const GammaItem *items;
+    int64_t n_items;
+    int nc, n_keys;
+    int64_t *off, *cur;
+    int32_t *order;
+};
+
+struct ScanTask {       // x[0] = 0, x[1..n] inclusive scan; copy[0..n-1] = result
+    int64_t *x;
+    int64_t n;
+    int64_t *copy;
+};
+
+struct GTask {          // gamma[key][n][n'] over the sorted items
+    const GammaItem *items;
+    const int32_t *order;
+    const int64_t *off;
+    int nc, n_keys;
+    const double *C;
+    int ns;
+    const double *Cp;
+    int nsp, ny;
+    double *gamma;
+};
+
+struct ATask {          // contracted coefficient rows A[(n,n')][k]
+    const double *gamma, *S, *E;
+    const int32_t *nn;
+    int n_nn, ns, nsp, n_to, cont_spin, Kpad;
+    double e_core;
+    double *A;
+};
+
+struct XTask {          // FP64 expansion of one group pair (Eq. 7)
+    const double *P, *A;
+    const int32_t *nn;
+    int n_nn, Kpad, n_co, cf, cn, cfp, cnp, same, mtiles;
+    int64_t row_off, col_off, ld;
+    double *H;
+};
+
+struct SliceTask {      // rows of X into bf16 slices at destination rows [row0, row0 + rows)
+    const double *X;
+    int64_t rows, row0;
+};
+
+struct SplitTask {      // one group pair on the tensor cores
+    int cf, cn, cfp, cnp;     // continuum ranges of the two groups
+    int jpt_tiles, ntn;       // tiles along j' (16 each), tiles along the state pairs
+    int n_nn, same;
+    int64_t coef_row0;        // first row of this pair in the coefficient slices
+    int64_t row_off, col_off, ld;
+    const int32_t *nn;
+    double *H;
+};
+
+struct DRTask {         // FP64 rows with j == j' of one group pair
+    const double *P, *A;
+    const int32_t *nn;
+    int n_nn, Kpad, n_co, j_lo, j_hi, cf, cn, cfp, cnp, same, ny;
+    int64_t row_off, col_off, ld;
+    double *H;
+};
+
+struct C4Task {         // class 4 of one target group against the L2 functions
+    Ints I;
+    const hb_pair *pairs;
+    const int64_t *row_ptr;
+    int n_l2;
+    const uint64_t *dets;
+    const double *C;
+    int ns, cf, cn, cont_spin, ny;
+    int64_t col_off, ld;
+    double *Hlc;
+};
+
+struct L2Task {         // classes 2 and 8: L2-L2 CSR of one Hamiltonian
+    Ints I;
+    const uint64_t *dets;
+    int n;
+    const int64_t *row_ptr;
+    int64_t *row_ptr_out;
+    int32_t *col;
+    double *val;
+    double e_core;
+};
+
+// ------------------------------------------------------------ launchers
+// Each returns the number of kernel launches it made (0 for an empty stage).
+int g_classify(const Grouped<ClsTask> &g, int W, int mode, cudaStream_t s);
+int g_pair_values(const Grouped<PVTask> &g, int W, cudaStream_t s);
+int g_l2_csr(const Grouped<L2Task> &g, int W, cudaStream_t s);
+int g_sandwich(const Grouped<SWTask> &g, cudaStream_t s);
+int g_tn_partial(const Grouped<TNTask> &g, size_t smem, cudaStream_t s);
+int g_tn_reduce(const Grouped<TNTask> &g, cudaStream_t s);
+int g_item_fill(const Grouped<IFTask> &g, cudaStream_t s);
+int g_zero(const Grouped<ZTask> &g, cudaStream_t s);
+int g_sort_hist(const Grouped<SortTask> &g, cudaStream_t s);
+int g_scan(const Grouped<ScanTask> &g, cudaStream_t s);
+int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s);
+int g_gamma(const Grouped<GTask> &g, size_t smem, cudaStream_t s);
+int g_assemble(const Grouped<ATask> &g, cudaStream_t s);
+int g_expand_fp64(const Grouped<XTask> &g, cudaStream_t s);
+int g_class4(const Grouped<C4Task> &g, int W, int dfloat, cudaStream_t s);
+
+// block counts of one task of each stage (host side)
+int64_t blocks_rows8(int64_t rows);                 // one warp per row, 8 warps a block
+int64_t blocks_pair_values(int64_t n_pairs);
+int64_t blocks_tn_partial(int n_rows, int ns, int nsp);
+int64_t blocks_tn_reduce(int ns, int nsp);
+int64_t blocks_zero(int64_t n);
+int64_t blocks_sort(int64_t n_items);
+int64_t blocks_gamma(int n_keys, int ns, int nsp);
+int64_t blocks_expand_fp64(int cn, int cnp, int n_nn);
+int64_t blocks_class4(int n_l2, int cn);
+int tn_ny(int ns, int nsp);
+int class4_ny(int cn);
+int expand_fp64_mtiles(int cn, int cnp);
+size_t smem_stage(int ns, int nsp);                 // dynamic shared memory of tn_partial / gamma
+
+}  // namespace hb

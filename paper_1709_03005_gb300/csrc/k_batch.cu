@@ -1,23 +1,26 @@
 // Batched build: many staged Hamiltonians (for instance the spatial-symmetry
 // and spin-coupling blocks of one molecule, which share integrals through
-// hb_init_shared) built by one CUDA-graph launch.  The graph is captured once
-// from the ordinary build of every context (after one eager build that sets up
-// the tensor-core operands), each context on its own branch so that their
-// kernels overlap, and replayed by hb_batch_launch: the host issues a single
-// launch for the whole set of uneven blocks.
+// hb_init_shared) built by one CUDA-graph launch.  The build of all of them
+// is one plan (k_plan.cu): every stage is a single grouped launch over the
+// group pairs of all Hamiltonians, so blocks of very different size fill the
+// GPU together, and the short fixed sequence of launches is captured once and
+// replayed by hb_batch_launch: the host issues one launch for the whole set.
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "hb_api_internal.cuh"
+#include "hb_plan.cuh"
 
 struct hb_batch {
     std::vector<hb_ctx *> ctxs;
     std::vector<hb_blocks> outs;
     int precision = HB_FP64;
+    hb::Plan *plan = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t nodes = 0;
+    int launches = 0;
 };
 
 namespace {
@@ -27,69 +30,57 @@ int bfail(int code, const std::string &m) {
     hb::g_last_error = m;
     return code;
 }
+
+void batch_free(hb_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->plan) {
+        cudaDeviceSynchronize();
+        plan_destroy(b->plan);
+    }
+    delete b;
+}
 }  // namespace
 
 extern "C" int hb_batch_create(hb_batch **out, hb_ctx *const *ctxs, int32_t n, int32_t precision,
                                const hb_blocks *outs, void *stream) {
     if (!out || !ctxs || !outs || n < 1) return bfail(HB_ERR_INVALID_ARG, "bad batch arguments");
+    if (precision != HB_FP64 && precision != HB_MIXED) return bfail(HB_ERR_INVALID_ARG, "bad precision");
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return bfail(HB_ERR_INVALID_ARG, "NULL context");
     *out = nullptr;
     hb_batch *b = new hb_batch();
     b->precision = precision;
     b->ctxs.assign(ctxs, ctxs + n);
     b->outs.assign(outs, outs + n);
     cudaStream_t s = (cudaStream_t)stream;
-    // eager build: allocates and slices the tensor-core operands, sets kernel attributes
-    for (int i = 0; i < n; ++i) {
-        int rc = hb_build_blocks(ctxs[i], precision, &outs[i], nullptr, s);
-        if (rc != HB_OK) { delete b; return bfail(rc, std::string("eager build: ") + hb_last_error(ctxs[i])); }
-    }
+    std::string err;
+    // the plan prepares the tensor-core operands and uploads its task tables
+    int rc = plan_create(ctxs, n, outs, precision, &b->plan, &err, s);
+    if (rc != HB_OK) { delete b; return bfail(rc, err); }
     cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { delete b; return bfail(HB_ERR_CUDA, cudaGetErrorString(e)); }
-    // capture on a private stream (the legacy default stream cannot be captured);
-    // every context is its own branch of the graph (fork / join through events),
-    // so the small kernels of different Hamiltonians run concurrently
+    if (e != cudaSuccess) { batch_free(b); return bfail(HB_ERR_CUDA, cudaGetErrorString(e)); }
+    // capture on a private stream (the legacy default stream cannot be captured)
     cudaStream_t cs;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { delete b; return bfail(HB_ERR_CUDA, cudaGetErrorString(e)); }
-    std::vector<cudaStream_t> br(n, nullptr);
-    std::vector<cudaEvent_t> done(n, nullptr);
-    cudaEvent_t fork = nullptr;
-    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    for (int i = 0; i < n; ++i) {
-        cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
-        cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
-    }
+    if (e != cudaSuccess) { batch_free(b); return bfail(HB_ERR_CUDA, cudaGetErrorString(e)); }
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    int rc = HB_OK;
     if (e == cudaSuccess) {
-        cudaEventRecord(fork, cs);
-        for (int i = 0; i < n && rc == HB_OK; ++i) {
-            cudaStreamWaitEvent(br[i], fork, 0);
-            ctxs[i]->capturing = true;
-            rc = hb_build_blocks(ctxs[i], precision, &outs[i], nullptr, br[i]);
-            ctxs[i]->capturing = false;
-            cudaEventRecord(done[i], br[i]);
-            cudaStreamWaitEvent(cs, done[i], 0);
-        }
+        rc = plan_run(b->plan, cs, false, &b->launches, &err);
         cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
-        if (e2 != cudaSuccess && rc == HB_OK) rc = bfail(HB_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e2));
+        if (rc != HB_OK) rc = bfail(rc, err);
+        else if (e2 != cudaSuccess) rc = bfail(HB_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e2));
     } else {
         rc = bfail(HB_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
     }
-    for (int i = 0; i < n; ++i) {
-        cudaStreamDestroy(br[i]);
-        cudaEventDestroy(done[i]);
-    }
-    cudaEventDestroy(fork);
     cudaStreamDestroy(cs);
     if (rc == HB_OK) {
         e = cudaGraphInstantiate(&b->exec, b->graph, 0);
         if (e != cudaSuccess) rc = bfail(HB_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
-        cudaGraphGetNodes(b->graph, nullptr, &b->nodes);
+        else cudaGraphGetNodes(b->graph, nullptr, &b->nodes);
     }
     if (rc != HB_OK) {
-        if (b->graph) cudaGraphDestroy(b->graph);
-        delete b;
+        batch_free(b);
         return rc;
     }
     *out = b;
@@ -116,16 +107,14 @@ extern "C" int hb_batch_launch(hb_batch *b, hb_stats *st, void *stream) {
         cudaEventDestroy(e1);
         memset(st, 0, sizeof(*st));
         st->ms_total = ms;
-        st->kernel_launches = (int32_t)b->nodes;
+        st->kernel_launches = b->launches;
     }
     if (b->precision == HB_MIXED) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return bfail(HB_ERR_CUDA, cudaGetErrorString(e));
-        for (hb_ctx *c : b->ctxs) {
-            int word = 0;
-            if (mixed_error_word(c, &word) != HB_OK) return bfail(HB_ERR_CUDA, "reading the mixed error word");
-            if (word) return bfail(HB_ERR_TIMEOUT, "split expansion kernel gave up waiting");
-        }
+        int word = 0;
+        if (plan_error_word(b->plan, &word) != HB_OK) return bfail(HB_ERR_CUDA, "reading the mixed error word");
+        if (word) return bfail(HB_ERR_TIMEOUT, "split expansion kernel gave up waiting");
     }
     return HB_OK;
 }
@@ -134,7 +123,5 @@ extern "C" int hb_batch_nodes(const hb_batch *b) { return b ? (int)b->nodes : -1
 
 extern "C" void hb_batch_destroy(hb_batch *b) {
     if (!b) return;
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    delete b;
+    batch_free(b);
 }

@@ -14,7 +14,7 @@
 // build, double-float FP32 (exact products by FMA, TwoSum accumulation, about
 // 44 significant bits), which runs on the FP32 pipes instead of the much
 // slower FP64 pipe of this part.
-#include "hb_internal.cuh"
+#include "hb_tasks.cuh"
 
 namespace hb {
 
@@ -76,17 +76,23 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 
 template <int W, int DF>
 __global__ void __launch_bounds__(kJ)
-class4_kernel(Ints I, const hb_pair *__restrict__ pairs, const int64_t *__restrict__ row_ptr,
-              const uint64_t *__restrict__ dets, const double *__restrict__ C, int ns, int cf, int cn,
-              int cont_spin, int64_t col_off, int64_t ld, double *__restrict__ Hlc) {
+class4_kernel(const C4Task *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     __shared__ double cs[kBatch][kNS];
     __shared__ float ch[kBatch][kNS], cl[kBatch][kNS];
     __shared__ hb_pair rs[kBatch];
-    const int l = blockIdx.x;
-    const int jl = blockIdx.y * kJ + threadIdx.x;
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const C4Task &T = tasks[ti];
+    const Ints I = T.I;
+    const hb_pair *__restrict__ pairs = T.pairs;
+    const uint64_t *__restrict__ dets = T.dets;
+    const double *__restrict__ C = T.C;
+    const int ns = T.ns, cf = T.cf, cn = T.cn, cont_spin = T.cont_spin;
+    const int lb = (int)(blockIdx.x - blk[ti]);
+    const int l = lb / T.ny;
+    const int jl = (lb % T.ny) * kJ + threadIdx.x;
     const bool jv = jl < cn;
     const int j = cf + (jv ? jl : 0);
-    const int64_t b = row_ptr[l], e = row_ptr[l + 1];
+    const int64_t b = T.row_ptr[l], e = T.row_ptr[l + 1];
     for (int n0 = 0; n0 < ns; n0 += kNS) {
         const int nc = min(kNS, ns - n0);
         double acc[kNS];
@@ -132,7 +138,7 @@ class4_kernel(Ints I, const hb_pair *__restrict__ pairs, const int64_t *__restri
             }
         }
         if (jv) {
-            double *out = Hlc + (int64_t)l * ld + col_off + jl;
+            double *out = T.Hlc + (int64_t)l * T.ld + T.col_off + jl;
 #pragma unroll
             for (int n = 0; n < kNS; ++n)
                 if (n < nc) out[(int64_t)(n0 + n) * cn] = DF ? (double)ahi[n] + (double)alo[n] : acc[n];
@@ -142,12 +148,13 @@ class4_kernel(Ints I, const hb_pair *__restrict__ pairs, const int64_t *__restri
 
 }  // namespace
 
-void class4_build(const Ints &I, const hb_pair *pairs, const int64_t *row_ptr, int n_l2, const uint64_t *dets,
-                  const double *C, int ns, int cf, int cn, int W, int cont_spin, int64_t col_off, int64_t ld,
-                  double *Hlc, int dfloat, cudaStream_t s) {
-    if (n_l2 <= 0 || cn <= 0) return;
-    const dim3 grid(n_l2, (cn + kJ - 1) / kJ);
-#define HB_C4(WW, DD) class4_kernel<WW, DD><<<grid, kJ, 0, s>>>(I, pairs, row_ptr, dets, C, ns, cf, cn, cont_spin, col_off, ld, Hlc)
+int class4_ny(int cn) { return (cn + kJ - 1) / kJ; }
+int64_t blocks_class4(int n_l2, int cn) { return cn > 0 ? (int64_t)n_l2 * class4_ny(cn) : 0; }
+
+int g_class4(const Grouped<C4Task> &g, int W, int dfloat, cudaStream_t s) {
+    if (g.blocks <= 0) return 0;
+    const unsigned grid = (unsigned)g.blocks;
+#define HB_C4(WW, DD) class4_kernel<WW, DD><<<grid, kJ, 0, s>>>(g.tasks, g.blk, g.n)
     if (dfloat) {
         switch (W) {
             case 1: HB_C4(1, 1); break;
@@ -164,6 +171,7 @@ void class4_build(const Ints &I, const hb_pair *pairs, const int64_t *row_ptr, i
         }
     }
 #undef HB_C4
+    return 1;
 }
 
 }  // namespace hb

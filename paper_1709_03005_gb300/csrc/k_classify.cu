@@ -7,7 +7,7 @@
 // Holes and particles come from the set bits of (ket & ~bra) and (bra & ~ket);
 // the phase comes from prefix popcounts of the ket string (the sign of applying
 // the annihilation and creation operators one after the other).
-#include "hb_internal.cuh"
+#include "hb_tasks.cuh"
 
 namespace hb {
 
@@ -133,13 +133,10 @@ k1_count_kernel(const uint64_t *__restrict__ A, int n_a, const uint64_t *__restr
 }
 
 template <int W, int MODE>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock)
-k1_fill_kernel(const uint64_t *__restrict__ A, int n_a, const uint64_t *__restrict__ B, int n_b,
-               int cont_spin, int max_degree, int lower, const int64_t *__restrict__ row_ptr,
-               hb_pair *__restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (row >= n_a) return;
+__device__ __forceinline__ void fill_row(const uint64_t *__restrict__ A, const uint64_t *__restrict__ B, int n_b,
+                                         int cont_spin, int max_degree, int lower,
+                                         const int64_t *__restrict__ row_ptr, hb_pair *__restrict__ out, int row,
+                                         int lane) {
     uint64_t a[2 * W];
     load_det<W>(A + (int64_t)row * 2 * W, a);
     const int limit = lower ? min(n_b, row + 1) : n_b;
@@ -166,6 +163,28 @@ k1_fill_kernel(const uint64_t *__restrict__ A, int n_a, const uint64_t *__restri
         }
         pos += __popc(m);
     }
+}
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+k1_fill_kernel(const uint64_t *__restrict__ A, int n_a, const uint64_t *__restrict__ B, int n_b,
+               int cont_spin, int max_degree, int lower, const int64_t *__restrict__ row_ptr,
+               hb_pair *__restrict__ out) {
+    const int row = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (row >= n_a) return;
+    fill_row<W, MODE>(A, B, n_b, cont_spin, max_degree, lower, row_ptr, out, row, threadIdx.x & 31);
+}
+
+// The same over many (a, b) tasks in one launch.
+template <int W, int MODE>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+k1_fill_grouped(const ClsTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const ClsTask &T = tasks[ti];
+    const int row = (int)(blockIdx.x - blk[ti]) * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (row >= T.n_a) return;
+    fill_row<W, MODE>(T.a, T.b, T.n_b, T.cont_spin, T.max_degree, T.lower, T.row_ptr, T.out, row,
+                      threadIdx.x & 31);
 }
 
 // Inclusive scan of x[1..n] in place (x[0] = 0 is set), single block.
@@ -252,6 +271,21 @@ void k1_fill_pairs(const uint64_t *a, int n_a, const uint64_t *b, int n_b, int W
 
 void exclusive_scan_inplace(int64_t *x, int n, cudaStream_t s) {
     scan_kernel<<<1, 1024, 0, s>>>(x, n);
+}
+
+int g_classify(const Grouped<ClsTask> &g, int W, int mode, cudaStream_t s) {
+    if (g.blocks <= 0) return 0;
+    const dim3 grid((unsigned)g.blocks), block(32 * kWarpsPerBlock);
+#define HB_K1G(WW) (mode == 0 ? k1_fill_grouped<WW, 0><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n) \
+                              : k1_fill_grouped<WW, 1><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n))
+    switch (W) {
+        case 1: HB_K1G(1); break;
+        case 2: HB_K1G(2); break;
+        case 3: HB_K1G(3); break;
+        default: HB_K1G(4); break;
+    }
+#undef HB_K1G
+    return 1;
 }
 
 }  // namespace hb

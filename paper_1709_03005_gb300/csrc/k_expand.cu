@@ -7,7 +7,7 @@
 // labels k: (jj'|rs) for r >= s, (jq|pj') for all (p, q), h_jj', delta_jj'.
 // This file builds the panel (once, at staging) and runs the FP64 contraction
 // with a scatter epilogue into the full symmetric continuum block.
-#include "hb_internal.cuh"
+#include "hb_tasks.cuh"
 
 namespace hb {
 
@@ -52,16 +52,24 @@ __global__ void panel_kernel(const double *__restrict__ ttcc, const double *__re
 constexpr int BM = 64, BN = 64, BK = 16;
 
 __global__ void __launch_bounds__(256)
-expand_fp64_kernel(const double *__restrict__ P, const double *__restrict__ A, const int32_t *__restrict__ nn,
-                   int n_nn, int Kpad, int n_co, int cf, int cn, int cfp, int cnp, int64_t row_off,
-                   int64_t col_off, int same_group, int64_t ld, double *__restrict__ H) {
+expand_fp64_kernel(const XTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const XTask &T = tasks[ti];
+    const double *__restrict__ P = T.P;
+    const double *__restrict__ A = T.A;
+    const int32_t *__restrict__ nn = T.nn;
+    const int n_nn = T.n_nn, Kpad = T.Kpad, n_co = T.n_co, cf = T.cf, cn = T.cn, cfp = T.cfp, cnp = T.cnp;
+    const int64_t row_off = T.row_off, col_off = T.col_off, ld = T.ld;
+    const int same_group = T.same;
+    double *__restrict__ H = T.H;
+    const int lb = (int)(blockIdx.x - blk[ti]);
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
     const int64_t M = (int64_t)cn * cnp;
-    const int64_t m0 = (int64_t)blockIdx.x * BM;
-    const int n0 = blockIdx.y * BN;
+    const int64_t m0 = (int64_t)(lb % T.mtiles) * BM;
+    const int n0 = (lb / T.mtiles) * BN;
     // loader: 64 rows x 16 k per operand, 4 doubles per thread
     const int lrow = tid / 4, lk = (tid % 4) * 4;
     const int64_t lm = m0 + lrow;
@@ -126,14 +134,17 @@ void build_panel(const double *ttcc, const double *tctc, const double *h, int n_
     panel_kernel<<<grid, block, 0, s>>>(ttcc, tctc, h, n_to, n_co, Kpad, P);
 }
 
-void expand_fp64(const double *P, const double *A, const int32_t *nn, int n_nn, int Kpad, int n_co, int cf,
-                 int cn, int cfp, int cnp, int64_t row_off, int64_t col_off, int same_group, int64_t ld,
-                 double *H, cudaStream_t s) {
-    const int64_t M = (int64_t)cn * cnp;
-    if (M == 0 || n_nn == 0) return;
-    const dim3 grid((unsigned)((M + BM - 1) / BM), (n_nn + BN - 1) / BN);
-    expand_fp64_kernel<<<grid, 256, 0, s>>>(P, A, nn, n_nn, Kpad, n_co, cf, cn, cfp, cnp, row_off, col_off,
-                                            same_group, ld, H);
+int expand_fp64_mtiles(int cn, int cnp) { return (int)(((int64_t)cn * cnp + BM - 1) / BM); }
+
+int64_t blocks_expand_fp64(int cn, int cnp, int n_nn) {
+    if ((int64_t)cn * cnp == 0 || n_nn == 0) return 0;
+    return (int64_t)expand_fp64_mtiles(cn, cnp) * ((n_nn + BN - 1) / BN);
+}
+
+int g_expand_fp64(const Grouped<XTask> &g, cudaStream_t s) {
+    if (g.blocks <= 0) return 0;
+    expand_fp64_kernel<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n);
+    return 1;
 }
 
 }  // namespace hb

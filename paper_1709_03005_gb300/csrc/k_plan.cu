@@ -1,0 +1,443 @@
+// Build plan: the whole build of one or many staged Hamiltonians as a short,
+// fixed sequence of grouped launches.
+//
+// Every stage of the path (K1 classification, the H^N values, the S / E
+// sandwiches, the gamma items, their counting sort and bins, the coefficient
+// rows, the Eq. 7 expansion, class 4, the L2 CSR) is launched once for all
+// target-group pairs (or groups, or L2 sets) of all Hamiltonians of the plan:
+// each task owns a block range of the grid (hb_tasks.cuh), so uneven blocks
+// of different size share the GPU within one launch instead of queueing as
+// thousands of small launches.  The task tables live in one device buffer,
+// uploaded when the plan is made (and again only when the output blocks
+// change).  A plan over many contexts is what a batch captures in a CUDA graph.
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "hb_plan.cuh"
+#include "hb_split.cuh"
+#include "hb_tasks.cuh"
+
+namespace hb {
+
+template <class T>
+struct Stage {
+    std::vector<T> tasks;
+    std::vector<int64_t> blk{0};
+    size_t off_t = 0, off_b = 0;
+    Grouped<T> g;
+    void add(const T &t, int64_t blocks) {
+        tasks.push_back(t);
+        blk.push_back(blk.back() + (blocks > 0 ? blocks : 0));
+    }
+    void clear() {
+        tasks.clear();
+        blk.assign(1, 0);
+    }
+};
+
+struct SplitGroup {
+    const hb_ctx *panel_ctx = nullptr;
+    Stage<SplitTask> st;
+};
+
+struct Plan {
+    std::vector<hb_ctx *> ctxs;
+    std::vector<hb_blocks> outs;
+    int precision = HB_FP64;
+    int W = 1, Kpad = 0, n_to = 0, S = 0, delta_col = 0;
+    Stage<ClsTask> cls_tt, cls_tl2;
+    Stage<PVTask> pv;
+    Stage<SWTask> sw;
+    Stage<TNTask> tn, tnr;
+    Stage<IFTask> itf;
+    Stage<ZTask> zero;
+    Stage<SortTask> sort;
+    Stage<ScanTask> scan;
+    Stage<GTask> gam;
+    Stage<ATask> asmb;
+    Stage<XTask> x64;
+    Stage<SliceTask> slc;
+    std::vector<SplitGroup> split;
+    Stage<DRTask> drows;
+    Stage<C4Task> c4;
+    Stage<L2Task> l2;
+    size_t smem_tn = 0, smem_gamma = 0;
+    double flops = 0.0;
+    int n_expand_tasks = 0;
+    // device copies of the task tables
+    std::vector<uint8_t> host;
+    uint8_t *dev = nullptr, *pinned = nullptr;
+    size_t dev_size = 0;
+    cudaEvent_t uploaded = nullptr;
+    bool upload_pending = false;
+    // tensor-core operands
+    void *coef = nullptr;
+    CUtensorMap tm_coef;
+    int64_t coef_rows = 0;
+    int *err = nullptr;
+    // timers: target, expansion, class 4, L2 boundaries; split kernels
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> ev_split;
+    int launches = 0, expand_launches = 0;
+    bool timed = false;
+};
+
+}  // namespace hb
+
+using namespace hb;
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <class T>
+void stage_pack(Stage<T> &st, std::vector<uint8_t> &host) {
+    st.off_t = align256(host.size());
+    host.resize(st.off_t + sizeof(T) * st.tasks.size());
+    if (!st.tasks.empty()) memcpy(host.data() + st.off_t, st.tasks.data(), sizeof(T) * st.tasks.size());
+    st.off_b = align256(host.size());
+    host.resize(st.off_b + sizeof(int64_t) * st.blk.size());
+    memcpy(host.data() + st.off_b, st.blk.data(), sizeof(int64_t) * st.blk.size());
+}
+
+template <class T>
+void stage_bind(Stage<T> &st, uint8_t *dev) {
+    st.g.tasks = (const T *)(dev + st.off_t);
+    st.g.blk = (const int64_t *)(dev + st.off_b);
+    st.g.n = (int)st.tasks.size();
+    st.g.blocks = st.blk.back();
+}
+
+// Task tables of every stage from the contexts and the output blocks.
+void fill_tasks(Plan &p) {
+    p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.sw.clear(); p.tn.clear(); p.tnr.clear();
+    p.itf.clear(); p.zero.clear(); p.sort.clear(); p.scan.clear(); p.gam.clear(); p.asmb.clear();
+    p.x64.clear(); p.slc.clear(); p.drows.clear(); p.c4.clear(); p.l2.clear();
+    for (auto &sg : p.split) sg.st.clear();
+    p.smem_tn = p.smem_gamma = 0;
+    p.flops = 0.0;
+    p.n_expand_tasks = 0;
+    int64_t coef_row = 0;
+    for (size_t ci = 0; ci < p.ctxs.size(); ++ci) {
+        hb_ctx *ctx = p.ctxs[ci];
+        const hb_blocks &out = p.outs[ci];
+        const Ints I = ctx->ints();
+        const int n_keys = 2 * ctx->n_to * ctx->n_to;
+        const int W = ctx->W;
+        SplitGroup *sg = nullptr;
+        if (p.precision == HB_MIXED && !ctx->gps.empty()) {
+            const void *key = mixed_panel_key(ctx);
+            for (auto &g : p.split)
+                if (mixed_panel_key(g.panel_ctx) == key) sg = &g;
+            if (!sg) {
+                p.split.emplace_back();
+                sg = &p.split.back();
+                sg->panel_ctx = ctx;
+            }
+        }
+        for (auto &P : ctx->gps) {
+            const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
+            const uint64_t *da = ctx->dets + A.det_off, *db = ctx->dets + B.det_off;
+            const double *Ca = ctx->ci + A.ci_off, *Cb = ctx->ci + B.ci_off;
+            p.cls_tt.add(ClsTask{da, db, A.ndet, B.ndet, ctx->cont_spin, 2, 0, P.rowptr, P.pairs},
+                         blocks_rows8(A.ndet));
+            p.pv.add(PVTask{I, da, db, P.pairs, P.n_pairs, P.val}, blocks_pair_values(P.n_pairs));
+            p.sw.add(SWTask{P.pairs, P.rowptr, P.val, A.ndet, Cb, B.ns, P.W}, blocks_rows8(A.ndet));
+            const int ny = tn_ny(A.ns, B.ns);
+            // E = C^T (H^N C'); S = C^T C within a group (identical determinants
+            // only, hb_init rejects repeats) and zero between groups
+            const TNTask te{Ca, P.W, A.ndet, A.ns, B.ns, ny, P.partial, P.E};
+            const TNTask ts{Ca, Ca, P.same ? A.ndet : 0, A.ns, B.ns, ny, P.partial_s, P.S};
+            p.tn.add(te, blocks_tn_partial(te.n_rows, A.ns, B.ns));
+            p.tn.add(ts, blocks_tn_partial(ts.n_rows, A.ns, B.ns));
+            p.tnr.add(te, blocks_tn_reduce(A.ns, B.ns));
+            p.tnr.add(ts, blocks_tn_reduce(A.ns, B.ns));
+            p.smem_tn = std::max(p.smem_tn, smem_stage(A.ns, B.ns));
+            p.itf.add(IFTask{P.pairs, P.rowptr, A.ndet, da, W, ctx->n_to, ctx->n_elec, P.item_ptr, P.items},
+                      blocks_rows8(A.ndet));
+            const int nc = P.n_chunks;
+            const int64_t n_off = (int64_t)n_keys * nc;
+            p.zero.add(ZTask{P.sort_off, n_off + 1}, blocks_zero(n_off + 1));
+            p.sort.add(SortTask{P.items, P.n_items, nc, n_keys, P.sort_off, P.sort_cur, P.order}, blocks_sort(P.n_items));
+            p.scan.add(ScanTask{P.sort_off, n_off, P.sort_cur}, 1);
+            p.gam.add(GTask{P.items, P.order, P.sort_off, nc, n_keys, Ca, A.ns, Cb, B.ns, ny, P.gamma},
+                      blocks_gamma(n_keys, A.ns, B.ns));
+            p.smem_gamma = std::max(p.smem_gamma, smem_stage(A.ns, B.ns));
+            p.asmb.add(ATask{P.gamma, P.S, P.E, P.nn, P.n_nn, A.ns, B.ns, ctx->n_to, ctx->cont_spin, ctx->Kpad,
+                             ctx->e_core, P.A},
+                       P.n_nn);
+            p.flops += 2.0 * (double)A.cn * B.cn * P.n_nn * ctx->K;
+            ++p.n_expand_tasks;
+            if (p.precision == HB_MIXED) {
+                p.slc.add(SliceTask{P.A, P.n_nn, coef_row}, blocks_rows8(P.n_nn));
+                SplitTask t;
+                t.cf = A.cf; t.cn = A.cn; t.cfp = B.cf; t.cnp = B.cn;
+                t.jpt_tiles = split_jpt(B.cn);
+                t.ntn = split_ntn(P.n_nn);
+                t.n_nn = P.n_nn; t.same = P.same;
+                t.coef_row0 = coef_row;
+                t.row_off = A.row_off; t.col_off = B.row_off; t.ld = ctx->Dc;
+                t.nn = P.nn; t.H = out.Hcc;
+                sg->st.add(t, blocks_split(A.cn, B.cn, P.n_nn));
+                coef_row += P.n_nn;
+                const int j_lo = std::max(A.cf, B.cf), j_hi = std::min(A.cf + A.cn, B.cf + B.cn);
+                p.drows.add(DRTask{ctx->panel, P.A, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, j_lo, j_hi, A.cf, A.cn,
+                                   B.cf, B.cn, P.same, diag_rows_ny(P.n_nn), A.row_off, B.row_off, ctx->Dc, out.Hcc},
+                            blocks_diag_rows(j_lo, j_hi, P.n_nn));
+            } else {
+                p.x64.add(XTask{ctx->panel, P.A, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, A.cf, A.cn, B.cf, B.cn, P.same,
+                                expand_fp64_mtiles(A.cn, B.cn), A.row_off, B.row_off, ctx->Dc, out.Hcc},
+                          blocks_expand_fp64(A.cn, B.cn, P.n_nn));
+            }
+        }
+        for (int g = 0; g < ctx->n_groups; ++g) {
+            const GroupInfo &G = ctx->groups[g];
+            GroupL2 &L = ctx->gl2[g];
+            const uint64_t *dg = ctx->dets + G.det_off;
+            p.cls_tl2.add(ClsTask{ctx->l2, dg, ctx->n_l2, G.ndet, ctx->cont_spin, 2, 0, L.rowptr, L.pairs},
+                          blocks_rows8(ctx->n_l2));
+            p.c4.add(C4Task{I, L.pairs, L.rowptr, ctx->n_l2, dg, ctx->ci + G.ci_off, G.ns, G.cf, G.cn, ctx->cont_spin,
+                            class4_ny(G.cn), G.row_off, ctx->Dc, out.Hlc},
+                     blocks_class4(ctx->n_l2, G.cn));
+        }
+        if (ctx->n_l2 > 0)
+            p.l2.add(L2Task{I, ctx->l2, ctx->n_l2, ctx->l2_rowptr, out.l2_row_ptr, out.l2_col, out.l2_val, ctx->e_core},
+                     blocks_rows8(ctx->n_l2));
+    }
+    p.coef_rows = coef_row;
+}
+
+void pack_all(Plan &p) {
+    p.host.clear();
+    stage_pack(p.cls_tt, p.host); stage_pack(p.cls_tl2, p.host); stage_pack(p.pv, p.host);
+    stage_pack(p.sw, p.host); stage_pack(p.tn, p.host); stage_pack(p.tnr, p.host); stage_pack(p.itf, p.host);
+    stage_pack(p.zero, p.host); stage_pack(p.sort, p.host); stage_pack(p.scan, p.host); stage_pack(p.gam, p.host);
+    stage_pack(p.asmb, p.host); stage_pack(p.x64, p.host); stage_pack(p.slc, p.host);
+    for (auto &sg : p.split) stage_pack(sg.st, p.host);
+    stage_pack(p.drows, p.host); stage_pack(p.c4, p.host); stage_pack(p.l2, p.host);
+}
+
+void bind_all(Plan &p) {
+    stage_bind(p.cls_tt, p.dev); stage_bind(p.cls_tl2, p.dev); stage_bind(p.pv, p.dev);
+    stage_bind(p.sw, p.dev); stage_bind(p.tn, p.dev); stage_bind(p.tnr, p.dev); stage_bind(p.itf, p.dev);
+    stage_bind(p.zero, p.dev); stage_bind(p.sort, p.dev); stage_bind(p.scan, p.dev); stage_bind(p.gam, p.dev);
+    stage_bind(p.asmb, p.dev); stage_bind(p.x64, p.dev); stage_bind(p.slc, p.dev);
+    for (auto &sg : p.split) stage_bind(sg.st, p.dev);
+    stage_bind(p.drows, p.dev); stage_bind(p.c4, p.dev); stage_bind(p.l2, p.dev);
+    p.scan.g.blocks = p.scan.g.n;     // one block per task
+}
+
+// Copy the packed tables through the pinned staging buffer (which is reused
+// only after the previous copy from it has finished).
+int upload(Plan &p, std::string *err, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (p.upload_pending) e = cudaEventSynchronize(p.uploaded);
+    p.upload_pending = false;
+    if (e == cudaSuccess && p.host.size() > p.dev_size) {
+        if (p.dev) cudaFree(p.dev);
+        if (p.pinned) cudaFreeHost(p.pinned);
+        p.dev = nullptr;
+        p.pinned = nullptr;
+        p.dev_size = 0;
+        e = cudaMalloc((void **)&p.dev, p.host.size());
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&p.pinned, p.host.size());
+        if (e == cudaSuccess) p.dev_size = p.host.size();
+    }
+    if (e == cudaSuccess && !p.host.empty()) {
+        memcpy(p.pinned, p.host.data(), p.host.size());
+        e = cudaMemcpyAsync(p.dev, p.pinned, p.host.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(p.uploaded, s);
+        if (e == cudaSuccess) p.upload_pending = true;
+    }
+    if (e != cudaSuccess) {
+        *err = std::string("plan upload: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? HB_ERR_OOM : HB_ERR_CUDA;
+    }
+    bind_all(p);
+    return HB_OK;
+}
+
+}  // namespace
+
+int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision, Plan **out, std::string *err,
+                cudaStream_t s) {
+    *out = nullptr;
+    if (n < 1) { *err = "empty plan"; return HB_ERR_INVALID_ARG; }
+    Plan *p = new Plan();
+    p->ctxs.assign(ctxs, ctxs + n);
+    p->outs.assign(outs, outs + n);
+    p->precision = precision;
+    p->W = ctxs[0]->W;
+    p->Kpad = ctxs[0]->Kpad;
+    p->n_to = ctxs[0]->n_to;
+    for (int i = 1; i < n; ++i)
+        if (ctxs[i]->W != p->W || ctxs[i]->Kpad != p->Kpad || ctxs[i]->n_to != p->n_to) {
+            delete p;
+            *err = "contexts of one plan must share the target orbital space (n_words, n_to)";
+            return HB_ERR_INVALID_ARG;
+        }
+    int rc = HB_OK;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&p->ev[i]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->uploaded, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&p->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, sizeof(int), s);
+    if (e != cudaSuccess) {
+        *err = std::string("plan: ") + cudaGetErrorString(e);
+        plan_destroy(p);
+        return HB_ERR_CUDA;
+    }
+    bool any_pairs = false;
+    for (int i = 0; i < n; ++i) any_pairs = any_pairs || !ctxs[i]->gps.empty();
+    if (precision == HB_MIXED && any_pairs) {
+        for (int i = 0; i < n && rc == HB_OK; ++i) {
+            if (ctxs[i]->gps.empty()) continue;
+            rc = mixed_prepare(ctxs[i], s);
+            if (rc != HB_OK) { *err = ctxs[i]->err; break; }
+            const int S = mixed_slices(ctxs[i]);
+            if (p->S == 0) p->S = S;
+            else if (S != p->S) { rc = HB_ERR_INVALID_ARG; *err = "contexts of one plan use different split_slices"; }
+        }
+        if (rc != HB_OK) { plan_destroy(p); return rc; }
+        p->delta_col = (int)(ctxs[0]->Pt + (int64_t)ctxs[0]->n_to * ctxs[0]->n_to + 1);
+    }
+    fill_tasks(*p);
+    if (precision == HB_MIXED && p->coef_rows > 0) {
+        rc = split_coef_alloc(p->S, p->coef_rows, p->Kpad, &p->coef, &p->tm_coef, err);
+        if (rc != HB_OK) { plan_destroy(p); return rc; }
+        for (auto &sg : p->split) {
+            (void)sg;
+            cudaEvent_t a = nullptr, b = nullptr;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            p->ev_split.push_back(a);
+            p->ev_split.push_back(b);
+        }
+    }
+    pack_all(*p);
+    rc = upload(*p, err, s);
+    if (rc != HB_OK) { plan_destroy(p); return rc; }
+    *out = p;
+    return HB_OK;
+}
+
+bool plan_outputs_equal(const Plan *p, const hb_blocks *outs) {
+    for (size_t i = 0; i < p->outs.size(); ++i) {
+        const hb_blocks &a = p->outs[i], &b = outs[i];
+        if (a.Hcc != b.Hcc || a.Hlc != b.Hlc || a.l2_row_ptr != b.l2_row_ptr || a.l2_col != b.l2_col ||
+            a.l2_val != b.l2_val)
+            return false;
+    }
+    return true;
+}
+
+int plan_precision(const Plan *p) { return p->precision; }
+
+int plan_set_outputs(Plan *p, const hb_blocks *outs, std::string *err, cudaStream_t s) {
+    p->outs.assign(outs, outs + p->outs.size());
+    fill_tasks(*p);
+    pack_all(*p);
+    return upload(*p, err, s);
+}
+
+int plan_run(Plan *p, cudaStream_t s, bool timing, int *launches, std::string *err) {
+    int L = 0, LX = 0;
+    const int W = p->W;
+    p->timed = timing;
+    if (timing) cudaEventRecord(p->ev[0], s);
+    // target side (Eq. 8): classes, H^N, S, E, gamma, coefficient rows
+    L += g_classify(p->cls_tt.g, W, 0, s);
+    L += g_pair_values(p->pv.g, W, s);
+    L += g_sandwich(p->sw.g, s);
+    L += g_tn_partial(p->tn.g, p->smem_tn, s);
+    L += g_tn_reduce(p->tnr.g, s);
+    L += g_item_fill(p->itf.g, s);
+    L += g_zero(p->zero.g, s);
+    L += g_sort_hist(p->sort.g, s);
+    L += g_scan(p->scan.g, s);
+    L += g_sort_scatter(p->sort.g, s);
+    L += g_gamma(p->gam.g, p->smem_gamma, s);
+    L += g_assemble(p->asmb.g, s);
+    if (timing) cudaEventRecord(p->ev[1], s);
+    // expansion (Eq. 7): classes 1, 3, 5, 6, 7
+    if (p->precision == HB_MIXED) {
+        if (p->coef_rows > 0) {
+            cudaMemsetAsync(p->err, 0, sizeof(int), s);
+            L += g_slice(p->slc.g, p->coef_rows, p->Kpad, p->S, p->delta_col, p->coef, s);
+            for (size_t i = 0; i < p->split.size(); ++i) {
+                if (timing) cudaEventRecord(p->ev_split[2 * i], s);
+                LX += g_split(p->split[i].panel_ctx, &p->tm_coef, p->split[i].st.g, p->Kpad / 64, p->err, s);
+                if (timing) cudaEventRecord(p->ev_split[2 * i + 1], s);
+            }
+            L += g_diag_rows(p->drows.g, s);
+        }
+    } else {
+        LX += g_expand_fp64(p->x64.g, s);
+    }
+    L += LX;
+    if (timing) cudaEventRecord(p->ev[2], s);
+    // class 4 (Eq. 5)
+    L += g_classify(p->cls_tl2.g, W, 1, s);
+    L += g_class4(p->c4.g, W, p->precision == HB_MIXED ? 1 : 0, s);
+    if (timing) cudaEventRecord(p->ev[3], s);
+    // classes 2 and 8
+    L += g_l2_csr(p->l2.g, W, s);
+    if (timing) cudaEventRecord(p->ev[4], s);
+    cudaError_t e = cudaGetLastError();
+    p->launches = L;
+    p->expand_launches = LX;
+    if (launches) *launches = L;
+    if (e != cudaSuccess) {
+        *err = std::string("build launch: ") + cudaGetErrorString(e);
+        return HB_ERR_CUDA;
+    }
+    return HB_OK;
+}
+
+void plan_stats(Plan *p, hb_stats *st) {
+    memset(st, 0, sizeof(*st));
+    st->kernel_launches = p->launches;
+    st->expand_launches = p->expand_launches;
+    st->expand_flops = p->flops;
+    if (!p->timed) return;
+    cudaEventSynchronize(p->ev[4]);
+    cudaEventElapsedTime(&st->ms_total, p->ev[0], p->ev[4]);
+    cudaEventElapsedTime(&st->ms_target, p->ev[0], p->ev[1]);
+    cudaEventElapsedTime(&st->ms_expand, p->ev[1], p->ev[2]);
+    cudaEventElapsedTime(&st->ms_class4, p->ev[2], p->ev[3]);
+    cudaEventElapsedTime(&st->ms_l2, p->ev[3], p->ev[4]);
+    if (p->precision == HB_MIXED) {
+        float total = 0.0f;
+        for (size_t i = 0; i + 1 < p->ev_split.size(); i += 2) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, p->ev_split[i], p->ev_split[i + 1]) == cudaSuccess) total += t;
+        }
+        st->ms_expand_gemm = total;
+        st->expand_tensor_flops = p->flops * (double)(p->S * (p->S + 1) / 2);
+    } else {
+        st->ms_expand_gemm = st->ms_expand;
+    }
+}
+
+int plan_error_word(Plan *p, int *word) {
+    *word = 0;
+    if (!p->err) return HB_OK;
+    return cudaMemcpy(word, p->err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+void plan_destroy(Plan *p) {
+    if (!p) return;
+    if (p->upload_pending) cudaEventSynchronize(p->uploaded);
+    for (cudaEvent_t e : p->ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->ev_split)
+        if (e) cudaEventDestroy(e);
+    if (p->uploaded) cudaEventDestroy(p->uploaded);
+    if (p->dev) cudaFree(p->dev);
+    if (p->pinned) cudaFreeHost(p->pinned);
+    if (p->coef) cudaFree(p->coef);
+    if (p->err) cudaFree(p->err);
+    delete p;
+}

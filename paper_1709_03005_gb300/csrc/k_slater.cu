@@ -8,7 +8,7 @@
 // (the standard rules for an orthonormal spin-orbital basis; the paper
 // evaluates them symbolically, Eq. 6).  (pp|qq) and (pq|qp) come from a small
 // n_to x n_to table that stays in L1/L2; other (tt|tt) integrals are gathered.
-#include "hb_internal.cuh"
+#include "hb_tasks.cuh"
 
 namespace hb {
 
@@ -131,15 +131,23 @@ constexpr int kWarps = 8;
 
 template <int W>
 __global__ void __launch_bounds__(32 * kWarps)
-l2_csr_kernel(Ints I, const uint64_t *__restrict__ D, int n, const int64_t *__restrict__ row_ptr,
-              int32_t *__restrict__ col, double *__restrict__ val, double e_core) {
+l2_csr_kernel(const L2Task *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const L2Task &T = tasks[ti];
+    const Ints I = T.I;
+    const uint64_t *__restrict__ D = T.dets;
+    const int n = T.n;
     const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int row = (int)(blockIdx.x - blk[ti]) * kWarps + (threadIdx.x >> 5);
     if (row >= n) return;
     uint64_t a[2 * W];
     load_det<W>(D + (int64_t)row * 2 * W, a);
-    int64_t pos = row_ptr[row];
-    const int64_t end = row_ptr[row + 1];
+    int64_t pos = T.row_ptr[row];
+    const int64_t end = T.row_ptr[row + 1];
+    if (lane == 0) {
+        T.row_ptr_out[row] = pos;
+        if (row == n - 1) T.row_ptr_out[n] = end;
+    }
     for (int c0 = 0; c0 < n; c0 += 32) {
         const int c = c0 + lane;
         int deg = 99;
@@ -157,9 +165,9 @@ l2_csr_kernel(Ints I, const uint64_t *__restrict__ D, int n, const int64_t *__re
             const int64_t at = pos + __popc(m & ((1u << lane) - 1u));
             if (at < end) {
                 double v = element<W>(I, a, b, deg);
-                if (deg == 0) v += e_core;
-                col[at] = c;
-                val[at] = v;
+                if (deg == 0) v += T.e_core;
+                T.col[at] = c;
+                T.val[at] = v;
             }
         }
         pos += __popc(m);
@@ -168,19 +176,21 @@ l2_csr_kernel(Ints I, const uint64_t *__restrict__ D, int n, const int64_t *__re
 
 // <A[row]|H|B[col]> for classified pairs (mode 0 records).
 template <int W>
-__global__ void pair_values_kernel(Ints I, const uint64_t *__restrict__ A, const uint64_t *__restrict__ B,
-                                   const hb_pair *__restrict__ pairs, int64_t n_pairs, double *__restrict__ val) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_pairs) return;
-    const hb_pair r = pairs[k];
+__global__ void pair_values_kernel(const PVTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const PVTask &T = tasks[ti];
+    const int64_t k = (blockIdx.x - blk[ti]) * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= T.n_pairs) return;
+    const Ints I = T.I;
+    const hb_pair r = T.pairs[k];
     uint64_t a[2 * W], b[2 * W];
-    load_det<W>(A + (int64_t)r.row * 2 * W, a);
-    load_det<W>(B + (int64_t)r.col * 2 * W, b);
+    load_det<W>(T.a + (int64_t)r.row * 2 * W, a);
+    load_det<W>(T.b + (int64_t)r.col * 2 * W, b);
     double v;
     if (r.degree == 0) v = diag_value<W>(I, a);
     else if (r.degree == 1) v = r.phase * single_value<W>(I, a, b, r.hole[0], r.part[0]);
     else v = r.phase * double_value(I, W, r.hole[0], r.hole[1], r.part[0], r.part[1]);
-    val[k] = v;
+    T.val[k] = v;
 }
 
 __global__ void jk_kernel(Ints I, double *jk) {
@@ -199,28 +209,29 @@ void build_jk(const Ints &I, double *jk, cudaStream_t s) {
     jk_kernel<<<(n + 255) / 256, 256, 0, s>>>(I, jk);
 }
 
-void l2_csr_fill(const Ints &I, const uint64_t *dets, int n, int W, const int64_t *row_ptr, int32_t *col,
-                 double *val, double e_core, cudaStream_t s) {
-    if (n <= 0) return;
-    const dim3 grid((n + kWarps - 1) / kWarps), block(32 * kWarps);
+int64_t blocks_pair_values(int64_t n_pairs) { return (n_pairs + 255) / 256; }
+
+int g_l2_csr(const Grouped<L2Task> &g, int W, cudaStream_t s) {
+    if (g.blocks <= 0) return 0;
+    const dim3 grid((unsigned)g.blocks), block(32 * kWarps);
     switch (W) {
-        case 1: l2_csr_kernel<1><<<grid, block, 0, s>>>(I, dets, n, row_ptr, col, val, e_core); break;
-        case 2: l2_csr_kernel<2><<<grid, block, 0, s>>>(I, dets, n, row_ptr, col, val, e_core); break;
-        case 3: l2_csr_kernel<3><<<grid, block, 0, s>>>(I, dets, n, row_ptr, col, val, e_core); break;
-        default: l2_csr_kernel<4><<<grid, block, 0, s>>>(I, dets, n, row_ptr, col, val, e_core); break;
+        case 1: l2_csr_kernel<1><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n); break;
+        case 2: l2_csr_kernel<2><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n); break;
+        case 3: l2_csr_kernel<3><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n); break;
+        default: l2_csr_kernel<4><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n); break;
     }
+    return 1;
 }
 
-void pair_values(const Ints &I, const uint64_t *A, const uint64_t *B, int W, const hb_pair *pairs,
-                 int64_t n_pairs, double *val, cudaStream_t s) {
-    if (n_pairs <= 0) return;
-    const int grid = (int)((n_pairs + 255) / 256);
+int g_pair_values(const Grouped<PVTask> &g, int W, cudaStream_t s) {
+    if (g.blocks <= 0) return 0;
     switch (W) {
-        case 1: pair_values_kernel<1><<<grid, 256, 0, s>>>(I, A, B, pairs, n_pairs, val); break;
-        case 2: pair_values_kernel<2><<<grid, 256, 0, s>>>(I, A, B, pairs, n_pairs, val); break;
-        case 3: pair_values_kernel<3><<<grid, 256, 0, s>>>(I, A, B, pairs, n_pairs, val); break;
-        default: pair_values_kernel<4><<<grid, 256, 0, s>>>(I, A, B, pairs, n_pairs, val); break;
+        case 1: pair_values_kernel<1><<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n); break;
+        case 2: pair_values_kernel<2><<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n); break;
+        case 3: pair_values_kernel<3><<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n); break;
+        default: pair_values_kernel<4><<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n); break;
     }
+    return 1;
 }
 
 }  // namespace hb

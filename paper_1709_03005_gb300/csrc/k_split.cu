@@ -39,20 +39,16 @@
 #include <mutex>
 
 #include "hb_api_internal.cuh"
+#include "hb_split.cuh"
 
 namespace hb {
 
 struct MixedState {
-    int slices = 5;
+    int slices = 6;
     int64_t panel_rows = 0;
     __nv_bfloat16 *panel_slices = nullptr;   // [S][Kpad/64][n_co*n_co][64]
-    __nv_bfloat16 *coef_slices = nullptr;    // [S][Kpad/64][n_nn][64]
-    int64_t coef_rows = 0;
-    int *err = nullptr;                       // device error word
     bool panel_ready = false;
     bool borrowed_panel = false;
-    std::vector<cudaEvent_t> ev;              // [2 * launches] around the split kernels of one build
-    int n_ev = 0;
     CUtensorMap tm_panel;
 };
 
@@ -249,17 +245,6 @@ __device__ __forceinline__ double df_to_double(float hi, float lo) {
     return __longlong_as_double((long long)bits);
 }
 
-struct SplitArgs {
-    int n_co, cf, cn, cfp, cnp;       // panel geometry and group ranges
-    int jpt_tiles;                     // tiles along jjp (16 each)
-    int n_nn, kblocks, slices;
-    int64_t row_off, col_off, ld;
-    int same_group;
-    const int32_t *nn;
-    double *H;
-    int *err;
-};
-
 // One K block of MMAs, fully unrolled for slot parity P: for each arriving
 // slice t, the pairs (i, l) with max(i, l) = t and i + l < S, then the commits
 // that free the slots read for the last time.
@@ -298,7 +283,8 @@ __device__ __forceinline__ bool mma_block(uint64_t *full_bar, uint64_t *empty_ba
 template <int S>
 __global__ void __launch_bounds__(NTHREADS, 1)
 split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_constant__ CUtensorMap tm_coef,
-                    SplitArgs a) {
+                    const SplitTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks, int kblocks,
+                    int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *slots = base;                                  // [S][SLOT]
@@ -310,12 +296,22 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     uint32_t *tmem_slot = (uint32_t *)(final_bar + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile_n = blockIdx.x, tile_m = blockIdx.y;     // N fastest: CTAs sharing a panel tile run together
+    // the task's arguments in shared memory: read where needed, not held in registers
+    __shared__ SplitTask a;
+    __shared__ int lb_s;
+    if (threadIdx.x == 0) {
+        const int ti = task_of(blk, n_tasks, blockIdx.x);
+        a = tasks[ti];
+        lb_s = (int)(blockIdx.x - blk[ti]);
+    }
+    __syncthreads();
+    const int lb = lb_s;
+    const int tile_n = lb % a.ntn, tile_m = lb / a.ntn;     // N fastest: CTAs sharing a panel tile run together
     const int jt = tile_m / a.jpt_tiles, jpt = tile_m % a.jpt_tiles;
     const int jj0 = jt * 8, jjp0 = jpt * 16;                // within the group ranges
     const int n0 = tile_n * BN;
     const int kb_per_chunk = KCHUNK / BKB;
-    const int nchunks = (a.kblocks + kb_per_chunk - 1) / kb_per_chunk;
+    const int nchunks = (kblocks + kb_per_chunk - 1) / kb_per_chunk;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < MAXS; ++i) { mbar_init(&full_bar[i], 1); mbar_init(&empty_bar[i], 1); }
@@ -340,22 +336,22 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
         if (lane == 0) {
             int kb = 0;
             bool ok = true;
-            for (; kb < a.kblocks && ok; ++kb) {
+            for (; kb < kblocks && ok; ++kb) {
                 for (int t = 0; t < S && ok; ++t) {
                     const int sl = (kb & 1) ? slot_of<S>(1, t) : t;
                     // each slot is filled once per K block: wait for its release in block kb-1
-                    if (kb > 0) ok = mbar_wait(&empty_bar[sl], (kb - 1) & 1, a.err, 1);
+                    if (kb > 0) ok = mbar_wait(&empty_bar[sl], (kb - 1) & 1, err, 1);
                     if (!ok) break;
                     uint8_t *sA = slots + sl * SLOT;
                     mbar_expect_tx(&full_bar[sl], (uint32_t)SLOT);
-                    const int plane = t * a.kblocks + kb;
+                    const int plane = t * kblocks + kb;
                     tma_load_4d(sA, &tm_panel, &full_bar[sl], 0, a.cfp + jjp0, a.cf + jj0, plane);
-                    tma_load_3d(sA + A_TILE, &tm_coef, &full_bar[sl], 0, n0, plane);
+                    tma_load_3d(sA + A_TILE, &tm_coef, &full_bar[sl], 0, (int)(a.coef_row0 + n0), plane);
                 }
             }
             // wait until this producer's copies of the last block have landed
             if (kb > 0)
-                for (int sl = 0; sl < S; ++sl) mbar_wait(&full_bar[sl], (kb - 1) & 1, a.err, 2);
+                for (int sl = 0; sl < S; ++sl) mbar_wait(&full_bar[sl], (kb - 1) & 1, err, 2);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
@@ -365,19 +361,19 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
             bool ok = true;
             int kb = 0;
             for (int c = 0; c < nchunks && ok; ++c) {
-                if (c > 0) ok = mbar_wait(acc_empty, (c - 1) & 1, a.err, 3);
+                if (c > 0) ok = mbar_wait(acc_empty, (c - 1) & 1, err, 3);
                 if (!ok) break;
                 tc_fence_after();
-                const int kb_end = min(a.kblocks, (c + 1) * kb_per_chunk);
+                const int kb_end = min(kblocks, (c + 1) * kb_per_chunk);
                 uint32_t fresh = 0xFu;           // accumulators not yet written in this chunk
                 for (; kb < kb_end && ok; ++kb) {
-                    if (kb & 1) ok = mma_block<S, 1>(full_bar, empty_bar, 1u, tmem, desc0, idesc, fresh, a.err);
-                    else ok = mma_block<S, 0>(full_bar, empty_bar, 0u, tmem, desc0, idesc, fresh, a.err);
+                    if (kb & 1) ok = mma_block<S, 1>(full_bar, empty_bar, 1u, tmem, desc0, idesc, fresh, err);
+                    else ok = mma_block<S, 0>(full_bar, empty_bar, 0u, tmem, desc0, idesc, fresh, err);
                 }
                 if (ok) mma_commit(acc_full);             // accumulators of chunk c complete
             }
             mma_commit(final_bar);
-            mbar_wait(final_bar, 0, a.err, 5);
+            mbar_wait(final_bar, 0, err, 5);
         }
     } else {
         // ------------------------------------------------------ epilogue
@@ -391,7 +387,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
         bool ok = true;
         const int n_acc = S < 4 ? S : 4;         // accumulators written by the MMAs
         for (int c = 0; c < nchunks && ok; ++c) {
-            ok = mbar_wait(acc_full, c & 1, a.err, 6);
+            ok = mbar_wait(acc_full, c & 1, err, 6);
             if (!ok) break;
             tc_fence_after();
             // s = 0 and s = 1 need the exact TwoSum; s = 2 and s >= 3 are 2^-14
@@ -427,7 +423,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
                         const int na = __ldg(a.nn + 2 * t), nb = __ldg(a.nn + 2 * t + 1);
                         const int64_t r = a.row_off + (int64_t)na * a.cn + jj;
                         const int64_t cc = a.col_off + (int64_t)nb * a.cnp + jjp;
-                        if (!a.same_group || r >= cc) {
+                        if (!a.same || r >= cc) {
                             const double v = df_to_double(hi[c], lo[c]);
                             a.H[r * a.ld + cc] = v;
                             if (r != cc) a.H[cc * a.ld + r] = v;
@@ -450,14 +446,11 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
 // the 64-bit fixed-point integer F = round(x 2^{7S-e}) (|F| < 2^{7S}, built
 // from the FP64 bit pattern with integer operations), whose balanced base-128
 // digits d_0 .. d_{S-1} (d_0 in [-128, 128], the rest in [-64, 64]) are the
-// slices: slice i = d_i 2^{e-7-7i}.  Output layout [S][K/64][rows][64], so a
-// 64-wide K block of consecutive rows is contiguous.  Column skip_col is zero.
-__global__ void slice_rows_kernel(const double *__restrict__ X, int64_t rows, int Kpad, int S, int skip_col,
-                                  __nv_bfloat16 *__restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= rows) return;
-    const double *x = X + row * Kpad;
+// slices: slice i = d_i 2^{e-7-7i}.  Output layout [S][K/64][R][64] (R rows in
+// all), so a 64-wide K block of consecutive rows is contiguous.  Column
+// skip_col is zero.
+__device__ __forceinline__ void slice_row(const double *__restrict__ x, int64_t dest, int64_t R, int Kpad, int S,
+                                          int skip_col, __nv_bfloat16 *__restrict__ out, int lane) {
     const int KB = Kpad / BKB;
     // exponent of the row maximum from the bit patterns (no FP64 arithmetic)
     int emax = -2000;
@@ -495,34 +488,52 @@ __global__ void slice_rows_kernel(const double *__restrict__ X, int64_t rows, in
             long long d = sh > 0 ? ((F + (1ll << (sh - 1))) >> sh) : F;   // nearest digit (floor of F/2^sh + 1/2)
             F -= d << sh;
             const float v = ldexpf((float)d, emax - 7 - 7 * i);            // exact: |d| <= 128
-            out[(((int64_t)i * KB + kb) * rows + row) * BKB + kk] = __float2bfloat16_rn(v);
+            out[(((int64_t)i * KB + kb) * R + dest) * BKB + kk] = __float2bfloat16_rn(v);
         }
     }
 }
 
+__global__ void slice_rows_kernel(const double *__restrict__ X, int64_t rows, int Kpad, int S, int skip_col,
+                                  __nv_bfloat16 *__restrict__ out) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    slice_row(X + row * Kpad, row, rows, Kpad, S, skip_col, out, threadIdx.x & 31);
+}
+
+__global__ void slice_rows_grouped(const SliceTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks,
+                                   int64_t R, int Kpad, int S, int skip_col, __nv_bfloat16 *__restrict__ out) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const SliceTask &T = tasks[ti];
+    const int64_t row = (blockIdx.x - blk[ti]) * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= T.rows) return;
+    slice_row(T.X + row * Kpad, T.row0 + row, R, Kpad, S, skip_col, out, threadIdx.x & 31);
+}
+
 // FP64 rows with j == j' (both ranges): H[(n,j),(n',j)] over all K, incl. delta.
-// One block per (j, 32 state pairs); the threads of a warp split K.
-__global__ void diag_rows_fp64_kernel(const double *__restrict__ P, const double *__restrict__ A,
-                                      const int32_t *__restrict__ nn, int n_nn, int Kpad, int n_co, int j_lo,
-                                      int j_hi, int cf, int cn, int cfp, int cnp, int64_t row_off, int64_t col_off,
-                                      int same_group, int64_t ld, double *__restrict__ H) {
-    const int j = j_lo + blockIdx.x;
+// Per task one block per (j, 8 state pairs); the lanes of a warp split K.
+__global__ void diag_rows_fp64_kernel(const DRTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                      int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const DRTask &T = tasks[ti];
+    const int lb = (int)(blockIdx.x - blk[ti]);
+    const int j = T.j_lo + lb / T.ny;
     const int lane = threadIdx.x & 31;
-    const int t = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= j_hi || t >= n_nn) return;
-    const double *prow = P + ((int64_t)j * n_co + j) * Kpad;
-    const double *arow = A + (int64_t)t * Kpad;
+    const int t = (lb % T.ny) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= T.j_hi || t >= T.n_nn) return;
+    const int Kpad = T.Kpad;
+    const double *prow = T.P + ((int64_t)j * T.n_co + j) * Kpad;
+    const double *arow = T.A + (int64_t)t * Kpad;
     double acc = 0.0;
     for (int k = lane; k < Kpad; k += 32) acc = fma(prow[k], arow[k], acc);
 #pragma unroll
     for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if (lane) return;
-    const int na = nn[2 * t], nb = nn[2 * t + 1];
-    const int64_t r = row_off + (int64_t)na * cn + (j - cf);
-    const int64_t c = col_off + (int64_t)nb * cnp + (j - cfp);
-    if (same_group && r < c) return;
-    H[r * ld + c] = acc;
-    if (r != c) H[c * ld + r] = acc;
+    const int na = T.nn[2 * t], nb = T.nn[2 * t + 1];
+    const int64_t r = T.row_off + (int64_t)na * T.cn + (j - T.cf);
+    const int64_t c = T.col_off + (int64_t)nb * T.cnp + (j - T.cfp);
+    if (T.same && r < c) return;
+    T.H[r * T.ld + c] = acc;
+    if (r != c) T.H[c * T.ld + r] = acc;
 }
 
 // ------------------------------------------------------ tensor maps (host)
@@ -562,14 +573,14 @@ static int mixed_fail(hb_ctx *ctx, int code, const std::string &m) {
     return code;
 }
 
-// Panel slices once per context (the integrals do not change between builds).
-static int ensure_mixed(hb_ctx *ctx, cudaStream_t s) {
+// Panel slices and their tensor map, once per context (the integrals do not
+// change between builds); a context that borrows its integrals borrows these.
+int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
     if (!ctx->mixed) ctx->mixed = new MixedState();
     MixedState &M = *ctx->mixed;
     if (M.panel_ready) return HB_OK;
     if (ctx->base) {
-        // panel slices and their tensor map come from the base context
-        int rc = ensure_mixed(ctx->base, s);
+        int rc = mixed_prepare(ctx->base, s);
         if (rc != HB_OK) return mixed_fail(ctx, rc, ctx->base->err);
         const MixedState &B = *ctx->base->mixed;
         M.slices = B.slices;
@@ -577,12 +588,6 @@ static int ensure_mixed(hb_ctx *ctx, cudaStream_t s) {
         M.panel_slices = B.panel_slices;
         M.tm_panel = B.tm_panel;
         M.borrowed_panel = true;
-        int64_t max_nn = 1;
-        for (auto &P : ctx->gps) max_nn = std::max<int64_t>(max_nn, P.n_nn);
-        M.coef_rows = max_nn;
-        cudaError_t e = cudaMalloc(&M.coef_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * max_nn * ctx->Kpad);
-        if (e == cudaSuccess) e = cudaMalloc(&M.err, sizeof(int));
-        if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("mixed operands: ") + cudaGetErrorString(e));
         M.panel_ready = true;
         return HB_OK;
     }
@@ -591,19 +596,13 @@ static int ensure_mixed(hb_ctx *ctx, cudaStream_t s) {
     if (!encode_fn()) return mixed_fail(ctx, HB_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     const int64_t rows = (int64_t)ctx->n_co * ctx->n_co;
     M.panel_rows = rows;
-    int64_t max_nn = 1;
-    for (auto &P : ctx->gps) max_nn = std::max<int64_t>(max_nn, P.n_nn);
-    M.coef_rows = max_nn;
     cudaError_t e = cudaMalloc(&M.panel_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * rows * ctx->Kpad);
-    if (e == cudaSuccess)
-        e = cudaMalloc(&M.coef_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * max_nn * ctx->Kpad);
-    if (e == cudaSuccess) e = cudaMalloc(&M.err, sizeof(int));
-    if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("mixed operands: ") + cudaGetErrorString(e));
-    ctx->dev_bytes += sizeof(__nv_bfloat16) * (size_t)M.slices * (rows + max_nn) * ctx->Kpad + sizeof(int);
+    if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("panel slices: ") + cudaGetErrorString(e));
+    ctx->dev_bytes += sizeof(__nv_bfloat16) * (size_t)M.slices * rows * ctx->Kpad;
     const int delta_col = (int)(ctx->Pt + (int64_t)ctx->n_to * ctx->n_to + 1);
     slice_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(ctx->panel, rows, ctx->Kpad, M.slices, delta_col,
                                                                  M.panel_slices);
-    // 4D map over the panel slices [S*KB][j][j'][32]: coordinates (kk, j', j, plane)
+    // 4D map over the panel slices [S*KB][j][j'][64]: coordinates (kk, j', j, plane)
     const int KB = ctx->Kpad / BKB;
     cuuint64_t dims[4] = {(cuuint64_t)BKB, (cuuint64_t)ctx->n_co, (cuuint64_t)ctx->n_co,
                           (cuuint64_t)M.slices * KB};
@@ -620,100 +619,79 @@ static int ensure_mixed(hb_ctx *ctx, cudaStream_t s) {
     return HB_OK;
 }
 
-int expand_mixed(hb_ctx *ctx, GroupPair &P, double *Hcc, cudaStream_t s) {
-    int rc = ensure_mixed(ctx, s);
-    if (rc != HB_OK) return rc;
-    MixedState &M = *ctx->mixed;
-    const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
-    const int delta_col = (int)(ctx->Pt + (int64_t)ctx->n_to * ctx->n_to + 1);
-    // coefficient slices of this group pair
-    slice_rows_kernel<<<(P.n_nn + 7) / 8, 256, 0, s>>>(P.A, P.n_nn, ctx->Kpad, M.slices, delta_col, M.coef_slices);
-    const int KB = ctx->Kpad / BKB;
-    CUtensorMap tm_coef;
-    cuuint64_t dims[3] = {(cuuint64_t)BKB, (cuuint64_t)P.n_nn, (cuuint64_t)M.slices * KB};
-    cuuint64_t strides[2] = {(cuuint64_t)BKB * 2, (cuuint64_t)P.n_nn * BKB * 2};
+const void *mixed_panel_key(const hb_ctx *ctx) { return ctx->mixed ? ctx->mixed->panel_slices : nullptr; }
+int mixed_slices(const hb_ctx *ctx) { return ctx->mixed ? ctx->mixed->slices : ctx->split_slices; }
+
+// Coefficient slices of `rows` rows in all: [S][Kpad/64][rows][64] bf16 and
+// the 3D map whose box is one 128 x 64 tile of one slice plane.
+int split_coef_alloc(int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err) {
+    *buf = nullptr;
+    if (!encode_fn()) { *err = "cuTensorMapEncodeTiled is not available"; return HB_ERR_CUDA; }
+    if (rows < 1) rows = 1;
+    cudaError_t e = cudaMalloc(buf, sizeof(__nv_bfloat16) * (size_t)S * rows * Kpad);
+    if (e != cudaSuccess) { *err = std::string("coefficient slices: ") + cudaGetErrorString(e); return HB_ERR_OOM; }
+    const int KB = Kpad / BKB;
+    cuuint64_t dims[3] = {(cuuint64_t)BKB, (cuuint64_t)rows, (cuuint64_t)S * KB};
+    cuuint64_t strides[2] = {(cuuint64_t)BKB * 2, (cuuint64_t)rows * BKB * 2};
     cuuint32_t box[3] = {BKB, BN, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode_fn()(&tm_coef, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, M.coef_slices, dims, strides, box, estr,
+    CUresult r = encode_fn()(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, *buf, dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return mixed_fail(ctx, HB_ERR_CUDA, "coefficient tensor map: error " + std::to_string((int)r));
-    SplitArgs a;
-    a.n_co = ctx->n_co; a.cf = A.cf; a.cn = A.cn; a.cfp = B.cf; a.cnp = B.cn;
-    a.jpt_tiles = (B.cn + 15) / 16;
-    a.n_nn = P.n_nn; a.kblocks = KB; a.slices = M.slices;
-    a.row_off = A.row_off; a.col_off = B.row_off; a.ld = ctx->Dc; a.same_group = P.same;
-    a.nn = P.nn; a.H = Hcc; a.err = M.err;
-    cudaMemsetAsync(M.err, 0, sizeof(int), s);
-    const dim3 grid((P.n_nn + BN - 1) / BN, ((A.cn + 7) / 8) * a.jpt_tiles);
-    const size_t smem = M.slices * SLOT + 2048;
-    if (!ctx->capturing) {
-        if ((int)M.ev.size() < M.n_ev + 2) {
-            cudaEvent_t a0, a1;
-            cudaEventCreate(&a0);
-            cudaEventCreate(&a1);
-            M.ev.push_back(a0);
-            M.ev.push_back(a1);
-        }
-        cudaEventRecord(M.ev[M.n_ev], s);
+    if (r != CUDA_SUCCESS) {
+        cudaFree(*buf);
+        *buf = nullptr;
+        *err = "coefficient tensor map: error " + std::to_string((int)r);
+        return HB_ERR_CUDA;
     }
-    switch (M.slices) {
-        case 2: split_expand_kernel<2><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
-        case 3: split_expand_kernel<3><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
-        case 4: split_expand_kernel<4><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
-        case 5: split_expand_kernel<5><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
-        default: split_expand_kernel<6><<<grid, NTHREADS, smem, s>>>(M.tm_panel, tm_coef, a); break;
-    }
-    if (!ctx->capturing) {
-        cudaEventRecord(M.ev[M.n_ev + 1], s);
-        M.n_ev += 2;
-    }
-    // rows with j == j' in FP64
-    const int j_lo = std::max(A.cf, B.cf), j_hi = std::min(A.cf + A.cn, B.cf + B.cn);
-    if (j_hi > j_lo)
-        diag_rows_fp64_kernel<<<dim3(j_hi - j_lo, (P.n_nn + 7) / 8), 256, 0, s>>>(ctx->panel, P.A, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, j_lo,
-                                                          j_hi, A.cf, A.cn, B.cf, B.cn, A.row_off, B.row_off, P.same,
-                                                          ctx->Dc, Hcc);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_CUDA, std::string("split expansion: ") + cudaGetErrorString(e));
     return HB_OK;
 }
 
-// Time of the split kernels of the last build (after its stream has finished),
-// and resets the counter for the next build.
-float mixed_kernel_ms(hb_ctx *ctx, int *launches) {
-    *launches = 0;
-    if (!ctx->mixed) return 0.0f;
-    MixedState &M = *ctx->mixed;
-    float total = 0.0f;
-    for (int i = 0; i + 1 < M.n_ev; i += 2) {
-        float t = 0.0f;
-        if (cudaEventElapsedTime(&t, M.ev[i], M.ev[i + 1]) == cudaSuccess) total += t;
-        ++*launches;
+int64_t blocks_split(int cn, int cnp, int n_nn) {
+    if (cn <= 0 || cnp <= 0 || n_nn <= 0) return 0;
+    return (int64_t)((n_nn + BN - 1) / BN) * ((cn + 7) / 8) * ((cnp + 15) / 16);
+}
+int split_ntn(int n_nn) { return (n_nn + BN - 1) / BN; }
+int split_jpt(int cnp) { return (cnp + 15) / 16; }
+
+int g_slice(const Grouped<SliceTask> &g, int64_t R, int Kpad, int S, int skip_col, void *out, cudaStream_t s) {
+    if (g.blocks <= 0) return 0;
+    slice_rows_grouped<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n, R, Kpad, S, skip_col,
+                                                          (__nv_bfloat16 *)out);
+    return 1;
+}
+
+int g_split(const hb_ctx *panel_ctx, const CUtensorMap *tm_coef, const Grouped<SplitTask> &g, int kblocks, int *err,
+            cudaStream_t s) {
+    if (g.blocks <= 0) return 0;
+    const MixedState &M = *panel_ctx->mixed;
+    const size_t smem = M.slices * SLOT + 2048;
+    const unsigned grid = (unsigned)g.blocks;
+    switch (M.slices) {
+        case 2: split_expand_kernel<2><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, err); break;
+        case 3: split_expand_kernel<3><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, err); break;
+        case 4: split_expand_kernel<4><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, err); break;
+        case 5: split_expand_kernel<5><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, err); break;
+        default: split_expand_kernel<6><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, err); break;
     }
-    M.n_ev = 0;
-    return total;
+    return 1;
 }
 
-void mixed_reset_timers(hb_ctx *ctx) {
-    if (ctx->mixed) ctx->mixed->n_ev = 0;
+int64_t blocks_diag_rows(int j_lo, int j_hi, int n_nn) {
+    if (j_hi <= j_lo || n_nn <= 0) return 0;
+    return (int64_t)(j_hi - j_lo) * ((n_nn + 7) / 8);
 }
+int diag_rows_ny(int n_nn) { return (n_nn + 7) / 8; }
 
-int mixed_slices(hb_ctx *ctx) { return ctx->mixed ? ctx->mixed->slices : ctx->split_slices; }
-
-int mixed_error_word(hb_ctx *ctx, int *out) {
-    *out = 0;
-    if (!ctx->mixed || !ctx->mixed->err) return HB_OK;
-    cudaError_t e = cudaMemcpy(out, ctx->mixed->err, sizeof(int), cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+int g_diag_rows(const Grouped<DRTask> &g, cudaStream_t s) {
+    if (g.blocks <= 0) return 0;
+    diag_rows_fp64_kernel<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n);
+    return 1;
 }
 
 void release_mixed(hb_ctx *ctx) {
     if (!ctx->mixed) return;
     if (!ctx->mixed->borrowed_panel) cudaFree(ctx->mixed->panel_slices);
-    cudaFree(ctx->mixed->coef_slices);
-    for (cudaEvent_t e : ctx->mixed->ev) cudaEventDestroy(e);
-    cudaFree(ctx->mixed->err);
     delete ctx->mixed;
     ctx->mixed = nullptr;
 }

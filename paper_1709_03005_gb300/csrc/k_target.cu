@@ -9,8 +9,9 @@
 // then C^T W by chunked partial sums.  gamma is a sum of phase-weighted outer
 // products per key (s, r, q); the contributions are put in key order by a
 // stable counting sort so that every sum runs in a fixed order (no floating
-// point atomics anywhere).
-#include "hb_internal.cuh"
+// point atomics anywhere).  Every stage is a grouped launch over the group
+// pairs of one or many Hamiltonians (one task per group pair).
+#include "hb_tasks.cuh"
 
 namespace hb {
 
@@ -20,21 +21,22 @@ namespace {
 // Wout[m][n'] = sum over records k of row m of v_k * Cp[col_k][n'].  One warp
 // per row: lane l takes records l, l+32, ... (fixed order), 16 columns at a
 // time, then a butterfly reduction over the lanes (fixed order as well).
-__global__ void sandwich_kernel(const hb_pair *__restrict__ pairs, const int64_t *__restrict__ row_ptr,
-                                const double *__restrict__ val, int n_rows, const double *__restrict__ Cp, int nsp,
-                                double *__restrict__ Wout) {
+__global__ void sandwich_kernel(const SWTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const SWTask T = tasks[ti];
     const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= n_rows) return;
-    const int64_t b = row_ptr[row], e = row_ptr[row + 1];
+    const int row = (int)(blockIdx.x - blk[ti]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= T.n_rows) return;
+    const int nsp = T.nsp;
+    const int64_t b = T.row_ptr[row], e = T.row_ptr[row + 1];
     for (int n0 = 0; n0 < nsp; n0 += 16) {
         double acc[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) acc[c] = 0.0;
         for (int64_t k = b + lane; k < e; k += 32) {
-            const int col = pairs[k].col;
-            const double v = val[k];
-            const double *crow = Cp + (int64_t)col * nsp + n0;
+            const int col = T.pairs[k].col;
+            const double v = T.val[k];
+            const double *crow = T.Cp + (int64_t)col * nsp + n0;
 #pragma unroll
             for (int c = 0; c < 16; ++c)
                 if (n0 + c < nsp) acc[c] = fma(v, __ldg(crow + c), acc[c]);
@@ -49,39 +51,43 @@ __global__ void sandwich_kernel(const hb_pair *__restrict__ pairs, const int64_t
 #pragma unroll
             for (int c = 0; c < 16; ++c)
                 if (c == lane) mine = acc[c];
-            Wout[(int64_t)row * nsp + n0 + lane] = mine;
+            T.Wout[(int64_t)row * nsp + n0 + lane] = mine;
         }
     }
 }
 
 // partial[c][n][n'] = sum_{m in chunk c} C[m][n] * Wm[m][n']; rows staged in
-// batches of 32, each thread keeps 4 outputs, grid.y covers the outputs.
+// batches, each thread keeps 4 outputs; the task's blocks are (chunk, y) with
+// y covering the outputs in steps of 1024.
 constexpr int kRowsPerChunk = 256;
 // rows (or items) staged per batch so that the staging buffer stays <= 48 KB
 __host__ __device__ inline int stage_batch(int ns, int nsp) {
     const int b = 6144 / (ns + nsp);
     return b < 1 ? 1 : (b > 32 ? 32 : b);
 }
-__global__ void tn_partial_kernel(const double *__restrict__ C, const double *__restrict__ Wm, int n_rows,
-                                  int ns, int nsp, double *__restrict__ partial) {
+__global__ void tn_partial_kernel(const TNTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     extern __shared__ double sh[];
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const TNTask T = tasks[ti];
+    const int lb = (int)(blockIdx.x - blk[ti]);
+    const int c = lb / T.ny, by = lb % T.ny;
+    const int ns = T.ns, nsp = T.nsp;
     const int kRowBatch = stage_batch(ns, nsp);
     double *cs = sh;                      // [kRowBatch][ns]
     double *ws = sh + kRowBatch * ns;     // [kRowBatch][nsp]
-    const int c = blockIdx.x;
     const int m0 = c * kRowsPerChunk;
-    const int rows = min(kRowsPerChunk, n_rows - m0);
+    const int rows = min(kRowsPerChunk, T.n_rows - m0);
     const int nout = ns * nsp;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int r0 = 0; r0 < rows; r0 += kRowBatch) {
         const int nr = min(kRowBatch, rows - r0);
         __syncthreads();
-        for (int i = threadIdx.x; i < nr * ns; i += blockDim.x) cs[i] = C[(int64_t)(m0 + r0) * ns + i];
-        for (int i = threadIdx.x; i < nr * nsp; i += blockDim.x) ws[i] = Wm[(int64_t)(m0 + r0) * nsp + i];
+        for (int i = threadIdx.x; i < nr * ns; i += blockDim.x) cs[i] = T.C[(int64_t)(m0 + r0) * ns + i];
+        for (int i = threadIdx.x; i < nr * nsp; i += blockDim.x) ws[i] = T.Wm[(int64_t)(m0 + r0) * nsp + i];
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int t = blockIdx.y * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
+            const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
             if (t < nout) {
                 const int a = t / nsp, b = t % nsp;
                 double s = acc[u];
@@ -92,18 +98,22 @@ __global__ void tn_partial_kernel(const double *__restrict__ C, const double *__
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int t = blockIdx.y * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
-        if (t < nout) partial[(int64_t)c * nout + t] = acc[u];
+        const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
+        if (t < nout) T.partial[(int64_t)c * nout + t] = acc[u];
     }
 }
 
-__global__ void reduce_partials_kernel(const double *__restrict__ partial, int n_chunks, int n_out,
-                                       double *__restrict__ out) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void reduce_partials_kernel(const TNTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                       int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const TNTask T = tasks[ti];
+    const int t = (int)(blockIdx.x - blk[ti]) * blockDim.x + threadIdx.x;
+    const int n_out = T.ns * T.nsp;
     if (t >= n_out) return;
+    const int n_chunks = (T.n_rows + kRowsPerChunk - 1) / kRowsPerChunk;
     double acc = 0.0;
-    for (int c = 0; c < n_chunks; ++c) acc += partial[(int64_t)c * n_out + t];
-    out[t] = acc;
+    for (int c = 0; c < n_chunks; ++c) acc += T.partial[(int64_t)c * n_out + t];
+    T.out[t] = acc;
 }
 
 // ------------------------------------------------------------ gamma items
@@ -126,21 +136,22 @@ __global__ void item_count_kernel(const hb_pair *__restrict__ pairs, const int64
 
 // Items in record order; a deg-0 record emits its occupied spin orbitals in
 // canonical order.  key = spin * n_to^2 + r * n_to + q.
-__global__ void item_fill_kernel(const hb_pair *__restrict__ pairs, const int64_t *__restrict__ row_ptr,
-                                 int n_rows, const uint64_t *__restrict__ bra_dets, int W, int n_to, int n_elec,
-                                 const int64_t *__restrict__ item_ptr, GammaItem *__restrict__ items) {
+__global__ void item_fill_kernel(const IFTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const IFTask T = tasks[ti];
     const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= n_rows) return;
-    const int64_t b = row_ptr[row], e = row_ptr[row + 1];
-    int64_t pos = item_ptr[row];
+    const int row = (int)(blockIdx.x - blk[ti]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= T.n_rows) return;
+    const int64_t b = T.row_ptr[row], e = T.row_ptr[row + 1];
+    int64_t pos = T.item_ptr[row];
+    const int W = T.W, n_to = T.n_to, n_elec = T.n_elec;
     const int sb = 64 * W;
     for (int64_t k0 = b; k0 < e; k0 += 32) {
         const int64_t k = k0 + lane;
         int cnt = 0;
         hb_pair r;
         if (k < e) {
-            r = pairs[k];
+            r = T.pairs[k];
             cnt = r.degree == 0 ? n_elec : (r.degree == 1 ? 1 : 0);
         }
         int incl = cnt;
@@ -157,9 +168,9 @@ __global__ void item_fill_kernel(const hb_pair *__restrict__ pairs, const int64_
                 GammaItem it;
                 it.key = s * n_to * n_to + p * n_to + q;
                 it.m = r.row; it.mp = r.col; it.phase = r.phase;
-                items[at] = it;
+                T.items[at] = it;
             } else {
-                const uint64_t *d = bra_dets + (int64_t)r.row * 2 * W;
+                const uint64_t *d = T.bra + (int64_t)r.row * 2 * W;
                 for (int w = 0; w < 2 * W; ++w) {
                     uint64_t x = d[w];
                     while (x) {
@@ -169,7 +180,7 @@ __global__ void item_fill_kernel(const hb_pair *__restrict__ pairs, const int64_
                         GammaItem it;
                         it.key = s * n_to * n_to + p * n_to + p;
                         it.m = r.row; it.mp = r.col; it.phase = 1;
-                        items[at++] = it;
+                        T.items[at++] = it;
                     }
                 }
             }
@@ -181,50 +192,118 @@ __global__ void item_fill_kernel(const hb_pair *__restrict__ pairs, const int64_
 // ------------------------------------------------- stable counting sort by key
 constexpr int kSortChunk = 4096;
 
-__global__ void sort_hist_kernel(const GammaItem *__restrict__ items, int64_t n_items, int n_chunks,
-                                 unsigned long long *__restrict__ hist_plus1) {
-    const int64_t base = (int64_t)blockIdx.x * kSortChunk;
+__global__ void zero_kernel(const ZTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const ZTask T = tasks[ti];
+    const int64_t i0 = (blockIdx.x - blk[ti]) * (int64_t)blockDim.x * 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + u * blockDim.x + threadIdx.x;
+        if (i < T.n) T.p[i] = 0;
+    }
+}
+
+// histogram per (key, chunk) in off[1 + key * nc + chunk] (integer atomics: exact)
+__global__ void sort_hist_kernel(const SortTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const SortTask T = tasks[ti];
+    const int chunk = (int)(blockIdx.x - blk[ti]);
+    const int64_t base = (int64_t)chunk * kSortChunk;
+    unsigned long long *hist = (unsigned long long *)T.off;
     for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
         const int64_t k = base + i;
-        if (k < n_items) atomicAdd(hist_plus1 + 1 + (int64_t)items[k].key * n_chunks + blockIdx.x, 1ull);
+        if (k < T.n_items) atomicAdd(hist + 1 + (int64_t)T.items[k].key * T.nc + chunk, 1ull);
+    }
+}
+
+// One block per task: x[0] = 0, x[1..n] := inclusive scan of x[1..n], and
+// copy[0..n-1] := x[0..n-1] (the exclusive offsets).
+__global__ void __launch_bounds__(1024) scan_kernel(const ScanTask *__restrict__ tasks, int n_tasks) {
+    __shared__ int64_t warp_sums[32];
+    __shared__ int64_t carry;
+    const ScanTask T = tasks[blockIdx.x];
+    const int64_t n = T.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) { carry = 0; T.x[0] = 0; if (T.copy && n > 0) T.copy[0] = 0; }
+    __syncthreads();
+    int64_t *y = T.x + 1;
+    for (int64_t base = 0; base < n; base += 1024 * 4) {
+        int64_t v[4];
+        const int64_t i0 = base + tid * 4;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = (i0 + k < n) ? y[i0 + k] : 0;
+        v[1] += v[0]; v[2] += v[1]; v[3] += v[2];
+        int64_t t = v[3];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int64_t u = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += u;
+        }
+        if (lane == 31) warp_sums[warp] = t;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t s = warp_sums[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                int64_t u = __shfl_up_sync(0xffffffffu, s, off);
+                if (lane >= off) s += u;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int64_t prefix = carry + (warp > 0 ? warp_sums[warp - 1] : 0) + (t - v[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (i0 + k < n) {
+                y[i0 + k] = v[k] + prefix;
+                if (T.copy && i0 + k + 1 < n) T.copy[i0 + k + 1] = v[k] + prefix;
+            }
+        __syncthreads();
+        if (tid == 0) carry += warp_sums[31];
+        __syncthreads();
     }
 }
 
 // One warp per chunk walks its items in order, so equal keys keep their order.
-// cursors: a copy of the exclusive offsets [key][chunk], advanced in place.
-__global__ void sort_scatter_kernel(const GammaItem *__restrict__ items, int64_t n_items, int n_chunks,
-                                    int64_t *__restrict__ cursors, int32_t *__restrict__ order) {
+// cur: a copy of the exclusive offsets [key][chunk], advanced in place.
+__global__ void sort_scatter_kernel(const SortTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                    int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const SortTask T = tasks[ti];
+    const int chunk = (int)(blockIdx.x - blk[ti]);
     const int lane = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * kSortChunk;
+    const int64_t base = (int64_t)chunk * kSortChunk;
     for (int i0 = 0; i0 < kSortChunk; i0 += 32) {
         const int64_t k = base + i0 + lane;
-        const bool valid = k < n_items;
-        const int key = valid ? items[k].key : -1 - lane;
+        const bool valid = k < T.n_items;
+        const int key = valid ? T.items[k].key : -1 - lane;
         const unsigned peers = __match_any_sync(0xffffffffu, key);
         const int rank = __popc(peers & ((1u << lane) - 1u));
         const int leader = __ffs(peers) - 1;
-        int64_t *cur = valid ? cursors + (int64_t)key * n_chunks + blockIdx.x : nullptr;
+        int64_t *cur = valid ? T.cur + (int64_t)key * T.nc + chunk : nullptr;
         int64_t at = 0;
         if (valid) at = *cur + rank;
         __syncwarp();
         if (valid && lane == leader) *cur += __popc(peers);
         __syncwarp();
-        if (valid) order[at] = (int32_t)k;
+        if (valid) T.order[at] = (int32_t)k;
     }
 }
 
 // gamma[key][n][n'] = sum over the key's items of phase * C[m][n] * Cp[m'][n']
-__global__ void gamma_kernel(const GammaItem *__restrict__ items, const int32_t *__restrict__ order,
-                             const int64_t *__restrict__ offsets, int n_chunks, int64_t n_items,
-                             const double *__restrict__ C, int ns, const double *__restrict__ Cp, int nsp,
-                             double *__restrict__ gamma) {
+__global__ void gamma_kernel(const GTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     extern __shared__ double sm[];
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const GTask T = tasks[ti];
+    const int lb = (int)(blockIdx.x - blk[ti]);
+    const int key = lb / T.ny, by = lb % T.ny;
+    const int ns = T.ns, nsp = T.nsp;
     const int kItemBatch = stage_batch(ns, nsp);
     double *ca = sm;                          // [kItemBatch][ns]
     double *cb = sm + kItemBatch * ns;        // [kItemBatch][nsp]
-    const int key = blockIdx.x;
-    const int64_t b = offsets[(int64_t)key * n_chunks];
-    const int64_t e = offsets[(int64_t)(key + 1) * n_chunks];
+    // with no items (nc == 0) both ends are off[0] = 0 and gamma is zero
+    const int64_t b = T.off[(int64_t)key * T.nc];
+    const int64_t e = T.off[(int64_t)(key + 1) * T.nc];
     const int nout = ns * nsp;
     // each thread keeps up to 4 outputs in registers
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -233,18 +312,18 @@ __global__ void gamma_kernel(const GammaItem *__restrict__ items, const int32_t 
         __syncthreads();
         for (int t = threadIdx.x; t < cnt * ns; t += blockDim.x) {
             const int i = t / ns, a = t % ns;
-            const GammaItem it = items[order[i0 + i]];
-            ca[i * ns + a] = it.phase * C[(int64_t)it.m * ns + a];
+            const GammaItem it = T.items[T.order[i0 + i]];
+            ca[i * ns + a] = it.phase * T.C[(int64_t)it.m * ns + a];
         }
         for (int t = threadIdx.x; t < cnt * nsp; t += blockDim.x) {
             const int i = t / nsp, a = t % nsp;
-            const GammaItem it = items[order[i0 + i]];
-            cb[i * nsp + a] = Cp[(int64_t)it.mp * nsp + a];
+            const GammaItem it = T.items[T.order[i0 + i]];
+            cb[i * nsp + a] = T.Cp[(int64_t)it.mp * nsp + a];
         }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int t = blockIdx.y * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
+            const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
             if (t < nout) {
                 const int a = t / nsp, c = t % nsp;
                 double s = acc[u];
@@ -255,8 +334,8 @@ __global__ void gamma_kernel(const GammaItem *__restrict__ items, const int32_t 
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int t = blockIdx.y * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
-        if (t < nout) gamma[(int64_t)key * nout + t] = acc[u];
+        const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
+        if (t < nout) T.gamma[(int64_t)key * nout + t] = acc[u];
     }
 }
 
@@ -267,13 +346,13 @@ __global__ void gamma_kernel(const GammaItem *__restrict__ items, const int32_t 
 //   k == Pt+n_to^2     : S            (multiplies h_jj')
 //   k == Pt+n_to^2+1   : E + e_core S (multiplies delta_jj')
 //   k >= K             : 0
-__global__ void assemble_kernel(const double *__restrict__ gamma, const double *__restrict__ S,
-                                const double *__restrict__ E, const int32_t *__restrict__ nn, int n_nn, int ns,
-                                int nsp, int n_to, int cont_spin, double e_core, int Kpad,
-                                double *__restrict__ A) {
-    const int t = blockIdx.x;
-    if (t >= n_nn) return;
-    const int n = nn[2 * t], np = nn[2 * t + 1];
+__global__ void assemble_kernel(const ATask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const ATask T = tasks[ti];
+    const int t = (int)(blockIdx.x - blk[ti]);
+    if (t >= T.n_nn) return;
+    const int n = T.nn[2 * t], np = T.nn[2 * t + 1];
+    const int ns = T.ns, nsp = T.nsp, n_to = T.n_to, Kpad = T.Kpad;
     const int nout = ns * nsp, sidx = n * nsp + np;
     const int Pt = n_to * (n_to + 1) / 2, nt2 = n_to * n_to;
     for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
@@ -285,42 +364,33 @@ __global__ void assemble_kernel(const double *__restrict__ gamma, const double *
             while (r * (r + 1) / 2 > k) --r;
             const int s = k - r * (r + 1) / 2;
             for (int sp = 0; sp < 2; ++sp) {
-                v += gamma[((int64_t)sp * nt2 + r * n_to + s) * nout + sidx];
-                if (r != s) v += gamma[((int64_t)sp * nt2 + s * n_to + r) * nout + sidx];
+                v += T.gamma[((int64_t)sp * nt2 + r * n_to + s) * nout + sidx];
+                if (r != s) v += T.gamma[((int64_t)sp * nt2 + s * n_to + r) * nout + sidx];
             }
         } else if (k < Pt + nt2) {
             const int pq = k - Pt;
-            v = -gamma[((int64_t)cont_spin * nt2 + pq) * nout + sidx];
+            v = -T.gamma[((int64_t)T.cont_spin * nt2 + pq) * nout + sidx];
         } else if (k == Pt + nt2) {
-            v = S[sidx];
+            v = T.S[sidx];
         } else if (k == Pt + nt2 + 1) {
-            v = E[sidx] + e_core * S[sidx];
+            v = T.E[sidx] + T.e_core * T.S[sidx];
         }
-        A[(int64_t)t * Kpad + k] = v;
+        T.A[(int64_t)t * Kpad + k] = v;
     }
 }
 
 }  // namespace
 
-void sandwich_rows(const hb_pair *pairs, const int64_t *row_ptr, const double *val, int n_rows, const double *Cp,
-                   int nsp, double *Wout, cudaStream_t s) {
-    if (n_rows <= 0) return;
-    sandwich_kernel<<<(n_rows + 7) / 8, 256, 0, s>>>(pairs, row_ptr, val, n_rows, Cp, nsp, Wout);
-}
-
+int64_t blocks_rows8(int64_t rows) { return (rows + 7) / 8; }
 int tn_chunks(int n_rows) { return (n_rows + kRowsPerChunk - 1) / kRowsPerChunk; }
-
-void gemm_tn_reduce(const double *C, const double *Wm, int n_rows, int ns, int nsp, double *partials,
-                    double *out, cudaStream_t s) {
-    const int nc = tn_chunks(n_rows);
-    if (nc > 0) {
-        const size_t sh = sizeof(double) * stage_batch(ns, nsp) * (ns + nsp);
-        const dim3 grid(nc, (ns * nsp + 1023) / 1024);
-        tn_partial_kernel<<<grid, 256, sh, s>>>(C, Wm, n_rows, ns, nsp, partials);
-    }
-    const int n_out = ns * nsp;
-    reduce_partials_kernel<<<(n_out + 255) / 256, 256, 0, s>>>(partials, nc, n_out, out);
-}
+int tn_ny(int ns, int nsp) { return (ns * nsp + 1023) / 1024; }
+int64_t blocks_tn_partial(int n_rows, int ns, int nsp) { return (int64_t)tn_chunks(n_rows) * tn_ny(ns, nsp); }
+int64_t blocks_tn_reduce(int ns, int nsp) { return (ns * nsp + 255) / 256; }
+int64_t blocks_zero(int64_t n) { return (n + 1023) / 1024; }
+int sort_chunks(int64_t n_items) { return (int)((n_items + kSortChunk - 1) / kSortChunk); }
+int64_t blocks_sort(int64_t n_items) { return sort_chunks(n_items); }
+int64_t blocks_gamma(int n_keys, int ns, int nsp) { return (int64_t)n_keys * tn_ny(ns, nsp); }
+size_t smem_stage(int ns, int nsp) { return sizeof(double) * stage_batch(ns, nsp) * (ns + nsp); }
 
 void gamma_item_counts(const hb_pair *pairs, const int64_t *row_ptr, int n_rows, int n_elec,
                        int64_t *counts_plus1, cudaStream_t s) {
@@ -328,47 +398,29 @@ void gamma_item_counts(const hb_pair *pairs, const int64_t *row_ptr, int n_rows,
     item_count_kernel<<<(n_rows + 7) / 8, 256, 0, s>>>(pairs, row_ptr, n_rows, n_elec, counts_plus1);
 }
 
-void gamma_item_fill(const hb_pair *pairs, const int64_t *row_ptr, int n_rows, const uint64_t *bra_dets, int W,
-                     int n_to, int n_elec, const int64_t *item_ptr, GammaItem *items, cudaStream_t s) {
-    if (n_rows <= 0) return;
-    item_fill_kernel<<<(n_rows + 7) / 8, 256, 0, s>>>(pairs, row_ptr, n_rows, bra_dets, W, n_to, n_elec, item_ptr,
-                                                      items);
+#define HB_GROUPED(kernel, g, threads, smem, s)                                                     \
+    do {                                                                                            \
+        if ((g).blocks <= 0) return 0;                                                              \
+        kernel<<<(unsigned)(g).blocks, threads, smem, s>>>((g).tasks, (g).blk, (g).n);              \
+        return 1;                                                                                   \
+    } while (0)
+
+int g_sandwich(const Grouped<SWTask> &g, cudaStream_t s) { HB_GROUPED(sandwich_kernel, g, 256, 0, s); }
+int g_tn_partial(const Grouped<TNTask> &g, size_t smem, cudaStream_t s) {
+    HB_GROUPED(tn_partial_kernel, g, 256, smem, s);
 }
+int g_tn_reduce(const Grouped<TNTask> &g, cudaStream_t s) { HB_GROUPED(reduce_partials_kernel, g, 256, 0, s); }
+int g_item_fill(const Grouped<IFTask> &g, cudaStream_t s) { HB_GROUPED(item_fill_kernel, g, 256, 0, s); }
+int g_zero(const Grouped<ZTask> &g, cudaStream_t s) { HB_GROUPED(zero_kernel, g, 256, 0, s); }
+int g_sort_hist(const Grouped<SortTask> &g, cudaStream_t s) { HB_GROUPED(sort_hist_kernel, g, 256, 0, s); }
+int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s) { HB_GROUPED(sort_scatter_kernel, g, 32, 0, s); }
+int g_gamma(const Grouped<GTask> &g, size_t smem, cudaStream_t s) { HB_GROUPED(gamma_kernel, g, 256, smem, s); }
+int g_assemble(const Grouped<ATask> &g, cudaStream_t s) { HB_GROUPED(assemble_kernel, g, 256, 0, s); }
 
-int sort_chunks(int64_t n_items) { return (int)((n_items + kSortChunk - 1) / kSortChunk); }
-
-void gamma_sort(const GammaItem *items, int64_t n_items, int n_keys, int64_t *offsets_plus1, int64_t *cursors,
-                int32_t *order, cudaStream_t s) {
-    const int nc = sort_chunks(n_items);
-    const int64_t n_off = (int64_t)n_keys * nc;
-    // zero the histogram (also covers the n_items == 0 case)
-    cudaMemsetAsync(offsets_plus1, 0, sizeof(int64_t) * (n_off + 1), s);
-    if (nc > 0) {
-        sort_hist_kernel<<<nc, 256, 0, s>>>(items, n_items, nc, (unsigned long long *)offsets_plus1);
-        exclusive_scan_inplace(offsets_plus1, (int)n_off, s);
-        cudaMemcpyAsync(cursors, offsets_plus1, sizeof(int64_t) * n_off, cudaMemcpyDeviceToDevice, s);
-        sort_scatter_kernel<<<nc, 32, 0, s>>>(items, n_items, nc, cursors, order);
-    }
-}
-
-void gamma_bins(const GammaItem *items, const int32_t *order, const int64_t *offsets, int n_keys, int64_t n_items,
-                const double *C, int ns, const double *Cp, int nsp, double *gamma, cudaStream_t s) {
-    const int nc = sort_chunks(n_items);
-    if (nc == 0) {
-        cudaMemsetAsync(gamma, 0, sizeof(double) * (size_t)n_keys * ns * nsp, s);
-        return;
-    }
-    // each thread holds 4 outputs, grid.y covers ns * nsp in steps of 1024
-    const size_t sh = sizeof(double) * stage_batch(ns, nsp) * (ns + nsp);
-    const dim3 grid(n_keys, (ns * nsp + 1023) / 1024);
-    gamma_kernel<<<grid, 256, sh, s>>>(items, order, offsets, nc, n_items, C, ns, Cp, nsp, gamma);
-}
-
-void assemble_coefficients(const double *gamma, const double *S, const double *E, const int32_t *nn, int n_nn,
-                           int ns, int nsp, int n_to, int cont_spin, double e_core, int Kpad, double *A,
-                           cudaStream_t s) {
-    if (n_nn <= 0) return;
-    assemble_kernel<<<n_nn, 256, 0, s>>>(gamma, S, E, nn, n_nn, ns, nsp, n_to, cont_spin, e_core, Kpad, A);
+int g_scan(const Grouped<ScanTask> &g, cudaStream_t s) {
+    if (g.n <= 0) return 0;
+    scan_kernel<<<g.n, 1024, 0, s>>>(g.tasks, g.n);
+    return 1;
 }
 
 }  // namespace hb
