@@ -308,7 +308,10 @@ def run_ours(args, rank, world, local_rank):
             batched = {"workload": "16 Hamiltonians (8 irreps x 2 spin couplings), dims " +
                        f"{min(h.dim for h in B.hams)}-{max(h.dim for h in B.hams)}, shared integrals",
                        "value": B.positions / (float(np.mean(bt)) / 1e3), "unit": "H elements/s",
-                       "ms_per_launch": float(np.mean(bt)), "graph_nodes": B.nodes, "graph_launches_per_step": 1}
+                       "ms_per_launch": float(np.mean(bt)), "graph_nodes": B.nodes, "graph_launches_per_step": 1,
+                       "kernel_launches_per_graph": stb.kernel_launches,
+                       "stages_ms": {"target": stb.ms_target, "expand": stb.ms_expand, "class4": stb.ms_class4,
+                                     "l2": stb.ms_l2, "expand_gemm": stb.ms_expand_gemm}}
             B.close()
         except hb.HBError as e:
             batched = {"unavailable": str(e)}

@@ -9,6 +9,7 @@
 #include "hb_api_internal.cuh"
 #include "hb_davidson.cuh"
 #include "hb_plan.cuh"
+#include "hb_df.cuh"
 
 using namespace hb;
 
@@ -358,6 +359,30 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
     return HB_OK;
 }
 
+int ensure_df(hb_ctx *ctx, cudaStream_t s) {
+    if (ctx->ci_df) return HB_OK;
+    const size_t no = ctx->n_orb, ntc = (size_t)ctx->n_to * ctx->n_co;
+    if (ctx->base) {
+        int rc = ensure_df(ctx->base, s);
+        if (rc != HB_OK) return fail(ctx, rc, ctx->base->err);
+        ctx->tttc_df = ctx->base->tttc_df;
+        ctx->h_df = ctx->base->h_df;
+    } else {
+        DALLOC(ctx->h_df, no * no);
+        split_df(ctx->h, (int64_t)(no * no), ctx->h_df, s);
+        if (ctx->tttc && ntc > 0) {
+            DALLOC(ctx->tttc_df, (size_t)ctx->Pt * ntc);
+            split_df(ctx->tttc, (int64_t)((size_t)ctx->Pt * ntc), ctx->tttc_df, s);
+        }
+    }
+    int64_t nci = 0;
+    for (auto &g : ctx->groups) nci += (int64_t)g.ndet * g.ns;
+    DALLOC(ctx->ci_df, std::max<int64_t>(nci, 1));
+    split_df(ctx->ci, nci, ctx->ci_df, s);
+    CK(cudaGetLastError());
+    return HB_OK;
+}
+
 extern "C" int hb_query(const hb_ctx *ctx, hb_layout *out) {
     if (!ctx || !out) return fail(nullptr, HB_ERR_INVALID_ARG, "NULL argument");
     out->dim = ctx->dim;
@@ -410,7 +435,7 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         if (rc != HB_OK) return fail(ctx, rc, err);
     }
     int launches = 0;
-    int rc = plan_run(plan, s, true, &launches, &err);
+    int rc = plan_run(plan, s, true, false, &launches, &err);
     if (rc != HB_OK) return fail(ctx, rc, err);
     if (precision == HB_MIXED) {
         // the tensor-core kernel reports a bounded-wait timeout in a device word

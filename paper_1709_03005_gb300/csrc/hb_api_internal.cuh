@@ -58,6 +58,8 @@ struct hb_ctx {
     double *h = nullptr, *tttt = nullptr, *tttc = nullptr, *jk = nullptr, *panel = nullptr;
     uint64_t *dets = nullptr, *l2 = nullptr;
     double *ci = nullptr;
+    // double-float (hi, lo) copies for the mixed class-4 kernel, made on first use
+    float2 *tttc_df = nullptr, *h_df = nullptr, *ci_df = nullptr;
     int64_t *l2_rowptr = nullptr;
     int64_t l2_nnz = 0, tt_pairs = 0, tl2_pairs = 0;
     hb::MixedState *mixed = nullptr;
@@ -76,3 +78,6 @@ struct hb_ctx {
 
 int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStream_t s);
 void release_mixed(hb_ctx *ctx);
+// Make the double-float copies of (tt|tc), h and the CI vectors (borrowing the
+// integrals' copies from the base context).
+int ensure_df(hb_ctx *ctx, cudaStream_t s);

@@ -20,9 +20,9 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
 int plan_set_outputs(hb::Plan *p, const hb_blocks *outs, std::string *err, cudaStream_t s);
 bool plan_outputs_equal(const hb::Plan *p, const hb_blocks *outs);
 int plan_precision(const hb::Plan *p);
-// Issue every stage on stream s.  timing: record stage events (not inside a
-// graph capture).  *launches: kernels launched.
-int plan_run(hb::Plan *p, cudaStream_t s, bool timing, int *launches, std::string *err);
+// Issue every stage on stream s.  timing: record the stage events (as graph
+// event nodes when capture is set).  *launches: kernels launched.
+int plan_run(hb::Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, std::string *err);
 // After the stream has finished a timed run: per-stage times and counters.
 void plan_stats(hb::Plan *p, hb_stats *st);
 // Bounded-wait status word of the tensor-core kernel (0: fine).

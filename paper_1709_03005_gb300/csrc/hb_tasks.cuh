@@ -111,12 +111,22 @@ struct ATask {          // contracted coefficient rows A[(n,n')][k]
     double *A;
 };
 
-struct XTask {          // FP64 expansion of one group pair (Eq. 7)
-    const double *P, *A;
-    const int32_t *nn;
-    int n_nn, Kpad, n_co, cf, cn, cfp, cnp, same, mtiles;
-    int64_t row_off, col_off, ld;
-    double *H;
+// One column of a merged expansion block: a state pair (n, n') of one group
+// pair of one Hamiltonian.  The Eq. 7 GEMMs of all group pairs that read the
+// same continuum rectangle of the panel are merged into one, whose columns are
+// the state pairs of all of them; each column scatters to its own matrix.
+struct ExpCol {
+    const double *arow;       // contracted coefficient row A[(n,n')][0..Kpad)
+    double *H;                // continuum block of its Hamiltonian (ld x ld)
+    int64_t rbase, cbase;     // row_off + n cn, col_off + n' cn'
+    int64_t ld;
+    int32_t same, pad;        // same target group: write the lower triangle and mirror
+};
+
+struct XTask {          // FP64 expansion of one merged block (Eq. 7)
+    const double *P;
+    int Kpad, n_co, cf, cn, cfp, cnp, mtiles, N;
+    int64_t col0;             // first column in the ExpCol table
 };
 
 struct SliceTask {      // rows of X into bf16 slices at destination rows [row0, row0 + rows)
@@ -124,14 +134,11 @@ struct SliceTask {      // rows of X into bf16 slices at destination rows [row0,
     int64_t rows, row0;
 };
 
-struct SplitTask {      // one group pair on the tensor cores
-    int cf, cn, cfp, cnp;     // continuum ranges of the two groups
-    int jpt_tiles, ntn;       // tiles along j' (16 each), tiles along the state pairs
-    int n_nn, same;
-    int64_t coef_row0;        // first row of this pair in the coefficient slices
-    int64_t row_off, col_off, ld;
-    const int32_t *nn;
-    double *H;
+struct SplitTask {      // one merged block on the tensor cores
+    int cf, cn, cfp, cnp;     // the continuum rectangle (same for every column)
+    int jpt_tiles, ntn, N;    // tiles along j' (16 each), tiles along the columns, columns
+    int64_t coef_row0;        // first row of the block in the coefficient slices
+    int64_t col0;             // first column in the ExpCol table
 };
 
 struct DRTask {         // FP64 rows with j == j' of one group pair
@@ -149,6 +156,7 @@ struct C4Task {         // class 4 of one target group against the L2 functions
     int n_l2;
     const uint64_t *dets;
     const double *C;
+    const float2 *C_df, *tttc_df, *h_df;   // double-float copies (mixed build)
     int ns, cf, cn, cont_spin, ny;
     int64_t col_off, ld;
     double *Hlc;
@@ -180,8 +188,11 @@ int g_scan(const Grouped<ScanTask> &g, cudaStream_t s);
 int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s);
 int g_gamma(const Grouped<GTask> &g, size_t smem, cudaStream_t s);
 int g_assemble(const Grouped<ATask> &g, cudaStream_t s);
-int g_expand_fp64(const Grouped<XTask> &g, cudaStream_t s);
-int g_class4(const Grouped<C4Task> &g, int W, int dfloat, cudaStream_t s);
+int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s);
+// dfloat = 0: FP64 (128 threads, 32 states a pass); 1: double-float with
+// ns_tile states a pass (8, 16 or 32) and jt threads a block (32, 64 or 128)
+int g_class4(const Grouped<C4Task> &g, int W, int dfloat, int ns_tile, int jt, cudaStream_t s);
+void class4_shape(int ns, int cn, int *ns_tile, int *jt);
 
 // block counts of one task of each stage (host side)
 int64_t blocks_rows8(int64_t rows);                 // one warp per row, 8 warps a block
@@ -191,10 +202,10 @@ int64_t blocks_tn_reduce(int ns, int nsp);
 int64_t blocks_zero(int64_t n);
 int64_t blocks_sort(int64_t n_items);
 int64_t blocks_gamma(int n_keys, int ns, int nsp);
-int64_t blocks_expand_fp64(int cn, int cnp, int n_nn);
-int64_t blocks_class4(int n_l2, int cn);
+int64_t blocks_expand_fp64(int cn, int cnp, int N);
+int64_t blocks_class4(int n_l2, int cn, int jt);
 int tn_ny(int ns, int nsp);
-int class4_ny(int cn);
+int class4_ny(int cn, int jt);
 int expand_fp64_mtiles(int cn, int cnp);
 size_t smem_stage(int ns, int nsp);                 // dynamic shared memory of tn_partial / gamma
 

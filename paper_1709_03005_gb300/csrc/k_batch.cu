@@ -66,7 +66,9 @@ extern "C" int hb_batch_create(hb_batch **out, hb_ctx *const *ctxs, int32_t n, i
     if (e != cudaSuccess) { batch_free(b); return bfail(HB_ERR_CUDA, cudaGetErrorString(e)); }
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = plan_run(b->plan, cs, false, &b->launches, &err);
+        // the stage events are captured as event-record nodes, so every replay
+        // leaves its per-stage times behind
+        rc = plan_run(b->plan, cs, true, true, &b->launches, &err);
         cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
         if (rc != HB_OK) rc = bfail(rc, err);
         else if (e2 != cudaSuccess) rc = bfail(HB_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e2));
@@ -105,7 +107,7 @@ extern "C" int hb_batch_launch(hb_batch *b, hb_stats *st, void *stream) {
         cudaEventElapsedTime(&ms, e0, e1);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        memset(st, 0, sizeof(*st));
+        plan_stats(b->plan, st);
         st->ms_total = ms;
         st->kernel_launches = b->launches;
     }

@@ -47,23 +47,21 @@ __global__ void panel_kernel(const double *__restrict__ ttcc, const double *__re
     }
 }
 
-// FP64 TN GEMM with scatter: rows m = (jj, jjp) of the group pair's continuum
-// block, columns t = state pair (n, n') from nn[], K = Kpad labels.
+// FP64 TN GEMM with scatter: rows m = (jj, jjp) of a continuum rectangle,
+// columns = the state pairs of every group pair merged into the block (each
+// with its coefficient row and its own destination), K = Kpad labels.
 constexpr int BM = 64, BN = 64, BK = 16;
 
 __global__ void __launch_bounds__(256)
-expand_fp64_kernel(const XTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+expand_fp64_kernel(const XTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks,
+                   const ExpCol *__restrict__ cols) {
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const XTask &T = tasks[ti];
     const double *__restrict__ P = T.P;
-    const double *__restrict__ A = T.A;
-    const int32_t *__restrict__ nn = T.nn;
-    const int n_nn = T.n_nn, Kpad = T.Kpad, n_co = T.n_co, cf = T.cf, cn = T.cn, cfp = T.cfp, cnp = T.cnp;
-    const int64_t row_off = T.row_off, col_off = T.col_off, ld = T.ld;
-    const int same_group = T.same;
-    double *__restrict__ H = T.H;
+    const int Kpad = T.Kpad, n_co = T.n_co, cf = T.cf, cn = T.cn, cfp = T.cfp, cnp = T.cnp, N = T.N;
+    const ExpCol *__restrict__ bc = cols + T.col0;
     const int lb = (int)(blockIdx.x - blk[ti]);
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
@@ -79,7 +77,7 @@ expand_fp64_kernel(const XTask *__restrict__ tasks, const int64_t *__restrict__ 
         prow = P + ((int64_t)(cf + jj) * n_co + (cfp + jjp)) * Kpad;
     }
     const int ln = n0 + lrow;
-    const double *arow = ln < n_nn ? A + (int64_t)ln * Kpad : nullptr;
+    const double *arow = ln < N ? bc[ln].arow : nullptr;
     double acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -106,22 +104,22 @@ expand_fp64_kernel(const XTask *__restrict__ tasks, const int64_t *__restrict__ 
         }
         __syncthreads();
     }
-    // epilogue: H[(n, jj)][(n', jjp)] and its mirror
+    // epilogue: H[(n, jj)][(n', jjp)] of the column's own matrix, and its mirror
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t m = m0 + ty * 4 + i;
-        if (m >= M) continue;
-        const int jj = (int)(m / cnp), jjp = (int)(m % cnp);
+    for (int j = 0; j < 4; ++j) {
+        const int t = n0 + tx * 4 + j;
+        if (t >= N) continue;
+        const ExpCol c = bc[t];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int t = n0 + tx * 4 + j;
-            if (t >= n_nn) continue;
-            const int na = nn[2 * t], nb = nn[2 * t + 1];
-            const int64_t r = row_off + (int64_t)na * cn + jj;
-            const int64_t c = col_off + (int64_t)nb * cnp + jjp;
-            if (same_group && r < c) continue;
-            H[r * ld + c] = acc[i][j];
-            if (r != c) H[c * ld + r] = acc[i][j];
+        for (int i = 0; i < 4; ++i) {
+            const int64_t m = m0 + ty * 4 + i;
+            if (m >= M) continue;
+            const int jj = (int)(m / cnp), jjp = (int)(m % cnp);
+            const int64_t r = c.rbase + jj;
+            const int64_t cc = c.cbase + jjp;
+            if (c.same && r < cc) continue;
+            c.H[r * c.ld + cc] = acc[i][j];
+            if (r != cc) c.H[cc * c.ld + r] = acc[i][j];
         }
     }
 }
@@ -136,14 +134,14 @@ void build_panel(const double *ttcc, const double *tctc, const double *h, int n_
 
 int expand_fp64_mtiles(int cn, int cnp) { return (int)(((int64_t)cn * cnp + BM - 1) / BM); }
 
-int64_t blocks_expand_fp64(int cn, int cnp, int n_nn) {
-    if ((int64_t)cn * cnp == 0 || n_nn == 0) return 0;
-    return (int64_t)expand_fp64_mtiles(cn, cnp) * ((n_nn + BN - 1) / BN);
+int64_t blocks_expand_fp64(int cn, int cnp, int N) {
+    if ((int64_t)cn * cnp == 0 || N == 0) return 0;
+    return (int64_t)expand_fp64_mtiles(cn, cnp) * ((N + BN - 1) / BN);
 }
 
-int g_expand_fp64(const Grouped<XTask> &g, cudaStream_t s) {
+int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
-    expand_fp64_kernel<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n);
+    expand_fp64_kernel<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n, cols);
     return 1;
 }
 

@@ -61,8 +61,15 @@ struct Plan {
     Stage<SliceTask> slc;
     std::vector<SplitGroup> split;
     Stage<DRTask> drows;
-    Stage<C4Task> c4;
+    struct C4Var {
+        int ns_tile, jt;
+        Stage<C4Task> st;
+    };
+    std::vector<C4Var> c4v;            // class-4 launch shapes (one grouped launch each)
     Stage<L2Task> l2;
+    std::vector<ExpCol> cols;          // columns of the merged expansion blocks
+    size_t off_cols = 0;
+    const ExpCol *d_cols = nullptr;
     size_t smem_tn = 0, smem_gamma = 0;
     double flops = 0.0;
     int n_expand_tasks = 0;
@@ -114,27 +121,55 @@ void stage_bind(Stage<T> &st, uint8_t *dev) {
 void fill_tasks(Plan &p) {
     p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.sw.clear(); p.tn.clear(); p.tnr.clear();
     p.itf.clear(); p.zero.clear(); p.sort.clear(); p.scan.clear(); p.gam.clear(); p.asmb.clear();
-    p.x64.clear(); p.slc.clear(); p.drows.clear(); p.c4.clear(); p.l2.clear();
+    p.x64.clear(); p.slc.clear(); p.drows.clear(); p.l2.clear();
+    for (auto &v : p.c4v) v.st.clear();
     for (auto &sg : p.split) sg.st.clear();
+    p.cols.clear();
     p.smem_tn = p.smem_gamma = 0;
     p.flops = 0.0;
     p.n_expand_tasks = 0;
     int64_t coef_row = 0;
+    // expansion blocks: the group pairs (of any context) that read the same
+    // continuum rectangle of the same panel share one GEMM
+    struct BlockKey {
+        const void *panel;
+        int cf, cn, cfp, cnp;
+        bool operator<(const BlockKey &o) const {
+            if (panel != o.panel) return panel < o.panel;
+            if (cf != o.cf) return cf < o.cf;
+            if (cn != o.cn) return cn < o.cn;
+            if (cfp != o.cfp) return cfp < o.cfp;
+            return cnp < o.cnp;
+        }
+    };
+    struct Member {
+        hb_ctx *ctx;
+        const GroupPair *P;
+        const hb_blocks *out;
+    };
+    struct Block {
+        BlockKey key;
+        hb_ctx *ctx = nullptr;
+        int sg = -1;
+        std::vector<Member> members;
+    };
+    std::map<BlockKey, int> block_of;
+    std::vector<Block> blocks;
     for (size_t ci = 0; ci < p.ctxs.size(); ++ci) {
         hb_ctx *ctx = p.ctxs[ci];
         const hb_blocks &out = p.outs[ci];
         const Ints I = ctx->ints();
         const int n_keys = 2 * ctx->n_to * ctx->n_to;
         const int W = ctx->W;
-        SplitGroup *sg = nullptr;
+        int sg = -1;
         if (p.precision == HB_MIXED && !ctx->gps.empty()) {
             const void *key = mixed_panel_key(ctx);
-            for (auto &g : p.split)
-                if (mixed_panel_key(g.panel_ctx) == key) sg = &g;
-            if (!sg) {
+            for (size_t i = 0; i < p.split.size(); ++i)
+                if (mixed_panel_key(p.split[i].panel_ctx) == key) sg = (int)i;
+            if (sg < 0) {
                 p.split.emplace_back();
-                sg = &p.split.back();
-                sg->panel_ctx = ctx;
+                p.split.back().panel_ctx = ctx;
+                sg = (int)p.split.size() - 1;
             }
         }
         for (auto &P : ctx->gps) {
@@ -170,26 +205,22 @@ void fill_tasks(Plan &p) {
                        P.n_nn);
             p.flops += 2.0 * (double)A.cn * B.cn * P.n_nn * ctx->K;
             ++p.n_expand_tasks;
+            // the pair joins the expansion block of its continuum rectangle
+            const BlockKey key{(const void *)ctx->panel, A.cf, A.cn, B.cf, B.cn};
+            auto it = block_of.find(key);
+            if (it == block_of.end()) {
+                it = block_of.emplace(key, (int)blocks.size()).first;
+                blocks.emplace_back();
+                blocks.back().key = key;
+                blocks.back().ctx = ctx;
+                blocks.back().sg = sg;
+            }
+            blocks[it->second].members.push_back(Member{ctx, &P, &out});
             if (p.precision == HB_MIXED) {
-                p.slc.add(SliceTask{P.A, P.n_nn, coef_row}, blocks_rows8(P.n_nn));
-                SplitTask t;
-                t.cf = A.cf; t.cn = A.cn; t.cfp = B.cf; t.cnp = B.cn;
-                t.jpt_tiles = split_jpt(B.cn);
-                t.ntn = split_ntn(P.n_nn);
-                t.n_nn = P.n_nn; t.same = P.same;
-                t.coef_row0 = coef_row;
-                t.row_off = A.row_off; t.col_off = B.row_off; t.ld = ctx->Dc;
-                t.nn = P.nn; t.H = out.Hcc;
-                sg->st.add(t, blocks_split(A.cn, B.cn, P.n_nn));
-                coef_row += P.n_nn;
                 const int j_lo = std::max(A.cf, B.cf), j_hi = std::min(A.cf + A.cn, B.cf + B.cn);
                 p.drows.add(DRTask{ctx->panel, P.A, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, j_lo, j_hi, A.cf, A.cn,
                                    B.cf, B.cn, P.same, diag_rows_ny(P.n_nn), A.row_off, B.row_off, ctx->Dc, out.Hcc},
                             blocks_diag_rows(j_lo, j_hi, P.n_nn));
-            } else {
-                p.x64.add(XTask{ctx->panel, P.A, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, A.cf, A.cn, B.cf, B.cn, P.same,
-                                expand_fp64_mtiles(A.cn, B.cn), A.row_off, B.row_off, ctx->Dc, out.Hcc},
-                          blocks_expand_fp64(A.cn, B.cn, P.n_nn));
             }
         }
         for (int g = 0; g < ctx->n_groups; ++g) {
@@ -198,13 +229,66 @@ void fill_tasks(Plan &p) {
             const uint64_t *dg = ctx->dets + G.det_off;
             p.cls_tl2.add(ClsTask{ctx->l2, dg, ctx->n_l2, G.ndet, ctx->cont_spin, 2, 0, L.rowptr, L.pairs},
                           blocks_rows8(ctx->n_l2));
-            p.c4.add(C4Task{I, L.pairs, L.rowptr, ctx->n_l2, dg, ctx->ci + G.ci_off, G.ns, G.cf, G.cn, ctx->cont_spin,
-                            class4_ny(G.cn), G.row_off, ctx->Dc, out.Hlc},
-                     blocks_class4(ctx->n_l2, G.cn));
+            int ns_tile = 32, jt = 128;
+            if (p.precision == HB_MIXED) class4_shape(G.ns, G.cn, &ns_tile, &jt);
+            Plan::C4Var *var = nullptr;
+            for (auto &v : p.c4v)
+                if (v.ns_tile == ns_tile && v.jt == jt) var = &v;
+            if (!var) {
+                p.c4v.push_back(Plan::C4Var{ns_tile, jt, Stage<C4Task>()});
+                var = &p.c4v.back();
+            }
+            var->st.add(C4Task{I, L.pairs, L.rowptr, ctx->n_l2, dg, ctx->ci + G.ci_off,
+                               ctx->ci_df ? ctx->ci_df + G.ci_off : nullptr, ctx->tttc_df, ctx->h_df, G.ns, G.cf, G.cn,
+                               ctx->cont_spin, class4_ny(G.cn, jt), G.row_off, ctx->Dc, out.Hlc},
+                        blocks_class4(ctx->n_l2, G.cn, jt));
         }
         if (ctx->n_l2 > 0)
             p.l2.add(L2Task{I, ctx->l2, ctx->n_l2, ctx->l2_rowptr, out.l2_row_ptr, out.l2_col, out.l2_val, ctx->e_core},
                      blocks_rows8(ctx->n_l2));
+    }
+    // merged expansion blocks: columns member by member, state pairs in order
+    for (auto &B : blocks) {
+        const int64_t col0 = (int64_t)p.cols.size();
+        for (const Member &m : B.members) {
+            const GroupPair &P = *m.P;
+            const int64_t mstart = (int64_t)p.cols.size();
+            const GroupInfo &A = m.ctx->groups[P.g], &Bg = m.ctx->groups[P.gp];
+            int t = 0;
+            for (int a = 0; a < A.ns; ++a)
+                for (int b = 0; b < Bg.ns; ++b) {
+                    if (P.same && b > a) continue;
+                    ExpCol c;
+                    c.arow = P.A + (int64_t)t * m.ctx->Kpad;
+                    c.H = m.out->Hcc;
+                    c.rbase = A.row_off + (int64_t)a * A.cn;
+                    c.cbase = Bg.row_off + (int64_t)b * Bg.cn;
+                    c.ld = m.ctx->Dc;
+                    c.same = P.same;
+                    c.pad = 0;
+                    p.cols.push_back(c);
+                    ++t;
+                }
+            if (p.precision == HB_MIXED)
+                p.slc.add(SliceTask{P.A, P.n_nn, coef_row + (mstart - col0)}, blocks_rows8(P.n_nn));
+        }
+        const int N = (int)((int64_t)p.cols.size() - col0);
+        const BlockKey &k = B.key;
+        if (p.precision == HB_MIXED) {
+            SplitTask t;
+            t.cf = k.cf; t.cn = k.cn; t.cfp = k.cfp; t.cnp = k.cnp;
+            t.jpt_tiles = split_jpt(k.cnp);
+            t.ntn = split_ntn(N);
+            t.N = N;
+            t.coef_row0 = coef_row;
+            t.col0 = col0;
+            p.split[B.sg].st.add(t, blocks_split(k.cn, k.cnp, N));
+            coef_row += N;
+        } else {
+            p.x64.add(XTask{B.ctx->panel, B.ctx->Kpad, B.ctx->n_co, k.cf, k.cn, k.cfp, k.cnp,
+                            expand_fp64_mtiles(k.cn, k.cnp), N, col0},
+                      blocks_expand_fp64(k.cn, k.cnp, N));
+        }
     }
     p.coef_rows = coef_row;
 }
@@ -216,7 +300,11 @@ void pack_all(Plan &p) {
     stage_pack(p.zero, p.host); stage_pack(p.sort, p.host); stage_pack(p.scan, p.host); stage_pack(p.gam, p.host);
     stage_pack(p.asmb, p.host); stage_pack(p.x64, p.host); stage_pack(p.slc, p.host);
     for (auto &sg : p.split) stage_pack(sg.st, p.host);
-    stage_pack(p.drows, p.host); stage_pack(p.c4, p.host); stage_pack(p.l2, p.host);
+    stage_pack(p.drows, p.host); stage_pack(p.l2, p.host);
+    for (auto &v : p.c4v) stage_pack(v.st, p.host);
+    p.off_cols = align256(p.host.size());
+    p.host.resize(p.off_cols + sizeof(ExpCol) * p.cols.size());
+    if (!p.cols.empty()) memcpy(p.host.data() + p.off_cols, p.cols.data(), sizeof(ExpCol) * p.cols.size());
 }
 
 void bind_all(Plan &p) {
@@ -225,7 +313,9 @@ void bind_all(Plan &p) {
     stage_bind(p.zero, p.dev); stage_bind(p.sort, p.dev); stage_bind(p.scan, p.dev); stage_bind(p.gam, p.dev);
     stage_bind(p.asmb, p.dev); stage_bind(p.x64, p.dev); stage_bind(p.slc, p.dev);
     for (auto &sg : p.split) stage_bind(sg.st, p.dev);
-    stage_bind(p.drows, p.dev); stage_bind(p.c4, p.dev); stage_bind(p.l2, p.dev);
+    stage_bind(p.drows, p.dev); stage_bind(p.l2, p.dev);
+    for (auto &v : p.c4v) stage_bind(v.st, p.dev);
+    p.d_cols = (const ExpCol *)(p.dev + p.off_cols);
     p.scan.g.blocks = p.scan.g.n;     // one block per task
 }
 
@@ -303,6 +393,13 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
         if (rc != HB_OK) { plan_destroy(p); return rc; }
         p->delta_col = (int)(ctxs[0]->Pt + (int64_t)ctxs[0]->n_to * ctxs[0]->n_to + 1);
     }
+    if (precision == HB_MIXED)
+        for (int i = 0; i < n && rc == HB_OK; ++i)
+            if (ctxs[i]->n_groups > 0 && ctxs[i]->n_l2 > 0) {
+                rc = ensure_df(ctxs[i], s);
+                if (rc != HB_OK) *err = ctxs[i]->err;
+            }
+    if (rc != HB_OK) { plan_destroy(p); return rc; }
     fill_tasks(*p);
     if (precision == HB_MIXED && p->coef_rows > 0) {
         rc = split_coef_alloc(p->S, p->coef_rows, p->Kpad, &p->coef, &p->tm_coef, err);
@@ -342,11 +439,17 @@ int plan_set_outputs(Plan *p, const hb_blocks *outs, std::string *err, cudaStrea
     return upload(*p, err, s);
 }
 
-int plan_run(Plan *p, cudaStream_t s, bool timing, int *launches, std::string *err) {
+int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, std::string *err) {
     int L = 0, LX = 0;
     const int W = p->W;
     p->timed = timing;
-    if (timing) cudaEventRecord(p->ev[0], s);
+    // inside a capture an event record becomes a graph node only when external
+    auto rec = [&](cudaEvent_t e) {
+        if (!timing) return;
+        if (capture) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else cudaEventRecord(e, s);
+    };
+    rec(p->ev[0]);
     // target side (Eq. 8): classes, H^N, S, E, gamma, coefficient rows
     L += g_classify(p->cls_tt.g, W, 0, s);
     L += g_pair_values(p->pv.g, W, s);
@@ -360,31 +463,31 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, int *launches, std::string *e
     L += g_sort_scatter(p->sort.g, s);
     L += g_gamma(p->gam.g, p->smem_gamma, s);
     L += g_assemble(p->asmb.g, s);
-    if (timing) cudaEventRecord(p->ev[1], s);
+    rec(p->ev[1]);
     // expansion (Eq. 7): classes 1, 3, 5, 6, 7
     if (p->precision == HB_MIXED) {
         if (p->coef_rows > 0) {
             cudaMemsetAsync(p->err, 0, sizeof(int), s);
             L += g_slice(p->slc.g, p->coef_rows, p->Kpad, p->S, p->delta_col, p->coef, s);
             for (size_t i = 0; i < p->split.size(); ++i) {
-                if (timing) cudaEventRecord(p->ev_split[2 * i], s);
-                LX += g_split(p->split[i].panel_ctx, &p->tm_coef, p->split[i].st.g, p->Kpad / 64, p->err, s);
-                if (timing) cudaEventRecord(p->ev_split[2 * i + 1], s);
+                rec(p->ev_split[2 * i]);
+                LX += g_split(p->split[i].panel_ctx, &p->tm_coef, p->split[i].st.g, p->Kpad / 64, p->d_cols, p->err, s);
+                rec(p->ev_split[2 * i + 1]);
             }
             L += g_diag_rows(p->drows.g, s);
         }
     } else {
-        LX += g_expand_fp64(p->x64.g, s);
+        LX += g_expand_fp64(p->x64.g, p->d_cols, s);
     }
     L += LX;
-    if (timing) cudaEventRecord(p->ev[2], s);
+    rec(p->ev[2]);
     // class 4 (Eq. 5)
     L += g_classify(p->cls_tl2.g, W, 1, s);
-    L += g_class4(p->c4.g, W, p->precision == HB_MIXED ? 1 : 0, s);
-    if (timing) cudaEventRecord(p->ev[3], s);
+    for (auto &v : p->c4v) L += g_class4(v.st.g, W, p->precision == HB_MIXED ? 1 : 0, v.ns_tile, v.jt, s);
+    rec(p->ev[3]);
     // classes 2 and 8
     L += g_l2_csr(p->l2.g, W, s);
-    if (timing) cudaEventRecord(p->ev[4], s);
+    rec(p->ev[4]);
     cudaError_t e = cudaGetLastError();
     p->launches = L;
     p->expand_launches = LX;

@@ -40,6 +40,7 @@
 
 #include "hb_api_internal.cuh"
 #include "hb_split.cuh"
+#include "hb_df.cuh"
 
 namespace hb {
 
@@ -211,40 +212,6 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
     lo = __fadd_rn(lo, e);
 }
 
-// hi + lo as a double, with integer operations only (the FP64 pipe of this
-// part is slow).  Both are aligned into a 64-bit integer with 38 bits of
-// headroom below the larger exponent, added exactly, and the result is
-// truncated to 53 bits (relative error below 2^-52).  FP32 subnormals are
-// treated as zero.
-__device__ __forceinline__ double df_to_double(float hi, float lo) {
-    const uint32_t bh = __float_as_uint(hi), bl = __float_as_uint(lo);
-    const int eh = (int)((bh >> 23) & 0xFF), el = (int)((bl >> 23) & 0xFF);
-    long long mh = eh ? (long long)((bh & 0x7FFFFFu) | 0x800000u) : 0;
-    long long ml = el ? (long long)((bl & 0x7FFFFFu) | 0x800000u) : 0;
-    if (bh >> 31) mh = -mh;
-    if (bl >> 31) ml = -ml;
-    const int base = eh > el ? eh : el;
-    // value = (mh 2^(eh-base) + ml 2^(el-base)) * 2^(base - 150)
-    const int sh_h = 38 - (base - eh), sh_l = 38 - (base - el);
-    long long acc = 0;
-    if (mh) acc += sh_h >= 0 ? (mh << sh_h) : (sh_h > -63 ? (mh >> -sh_h) : 0);
-    if (ml) acc += sh_l >= 0 ? (ml << sh_l) : (sh_l > -63 ? (ml >> -sh_l) : 0);
-    if (acc == 0) return 0.0;
-    const unsigned long long neg = acc < 0 ? 1ull : 0ull;
-    unsigned long long u = neg ? (unsigned long long)(-acc) : (unsigned long long)acc;
-    const int lz = __clzll((long long)u);            // leading zeros, u > 0
-    const int top = 63 - lz;                          // position of the leading one
-    // normalise to 53 bits: leading one at bit 52
-    if (top > 52) u >>= (top - 52);
-    else u <<= (52 - top);
-    // exponent: value = u * 2^(top - 52) * 2^(base - 150 - 38), u in [2^52, 2^53)
-    const int e2 = top + base - 150 - 38;             // unbiased exponent of the leading one
-    const long long be = (long long)e2 + 1023;
-    if (be <= 0) return 0.0;                          // below the FP64 normal range
-    const unsigned long long bits = (neg << 63) | ((unsigned long long)be << 52) | (u & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double((long long)bits);
-}
-
 // One K block of MMAs, fully unrolled for slot parity P: for each arriving
 // slice t, the pairs (i, l) with max(i, l) = t and i + l < S, then the commits
 // that free the slots read for the last time.
@@ -284,7 +251,7 @@ template <int S>
 __global__ void __launch_bounds__(NTHREADS, 1)
 split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_constant__ CUtensorMap tm_coef,
                     const SplitTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks, int kblocks,
-                    int *err) {
+                    const ExpCol *__restrict__ cols, int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *slots = base;                                  // [S][SLOT]
@@ -312,6 +279,15 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     const int n0 = tile_n * BN;
     const int kb_per_chunk = KCHUNK / BKB;
     const int nchunks = (kblocks + kb_per_chunk - 1) / kb_per_chunk;
+    // destinations of this tile's 128 columns (ExpCol with H == null: no column)
+    __shared__ ExpCol colmeta[BN];
+    if (threadIdx.x < BN) {
+        const int t = n0 + threadIdx.x;
+        ExpCol c;
+        if (t < a.N) c = cols[a.col0 + t];
+        else c.H = nullptr;
+        colmeta[threadIdx.x] = c;
+    }
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < MAXS; ++i) { mbar_init(&full_bar[i], 1); mbar_init(&empty_bar[i], 1); }
@@ -418,15 +394,14 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
             if (jj < a.cn && jjp < a.cnp && (a.cf + jj) != (a.cfp + jjp)) {
 #pragma unroll
                 for (int c = 0; c < EPI_COLS; ++c) {
-                    const int t = n0 + col0 + c;
-                    if (t < a.n_nn) {
-                        const int na = __ldg(a.nn + 2 * t), nb = __ldg(a.nn + 2 * t + 1);
-                        const int64_t r = a.row_off + (int64_t)na * a.cn + jj;
-                        const int64_t cc = a.col_off + (int64_t)nb * a.cnp + jjp;
-                        if (!a.same || r >= cc) {
+                    const ExpCol &m = colmeta[col0 + c];
+                    if (m.H) {
+                        const int64_t r = m.rbase + jj;
+                        const int64_t cc = m.cbase + jjp;
+                        if (!m.same || r >= cc) {
                             const double v = df_to_double(hi[c], lo[c]);
-                            a.H[r * a.ld + cc] = v;
-                            if (r != cc) a.H[cc * a.ld + r] = v;
+                            m.H[r * m.ld + cc] = v;
+                            if (r != cc) m.H[cc * m.ld + r] = v;
                         }
                     }
                 }
@@ -647,11 +622,11 @@ int split_coef_alloc(int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm,
     return HB_OK;
 }
 
-int64_t blocks_split(int cn, int cnp, int n_nn) {
-    if (cn <= 0 || cnp <= 0 || n_nn <= 0) return 0;
-    return (int64_t)((n_nn + BN - 1) / BN) * ((cn + 7) / 8) * ((cnp + 15) / 16);
+int64_t blocks_split(int cn, int cnp, int N) {
+    if (cn <= 0 || cnp <= 0 || N <= 0) return 0;
+    return (int64_t)((N + BN - 1) / BN) * ((cn + 7) / 8) * ((cnp + 15) / 16);
 }
-int split_ntn(int n_nn) { return (n_nn + BN - 1) / BN; }
+int split_ntn(int N) { return (N + BN - 1) / BN; }
 int split_jpt(int cnp) { return (cnp + 15) / 16; }
 
 int g_slice(const Grouped<SliceTask> &g, int64_t R, int Kpad, int S, int skip_col, void *out, cudaStream_t s) {
@@ -661,18 +636,18 @@ int g_slice(const Grouped<SliceTask> &g, int64_t R, int Kpad, int S, int skip_co
     return 1;
 }
 
-int g_split(const hb_ctx *panel_ctx, const CUtensorMap *tm_coef, const Grouped<SplitTask> &g, int kblocks, int *err,
-            cudaStream_t s) {
+int g_split(const hb_ctx *panel_ctx, const CUtensorMap *tm_coef, const Grouped<SplitTask> &g, int kblocks,
+            const ExpCol *cols, int *err, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
     const MixedState &M = *panel_ctx->mixed;
     const size_t smem = M.slices * SLOT + 2048;
     const unsigned grid = (unsigned)g.blocks;
     switch (M.slices) {
-        case 2: split_expand_kernel<2><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, err); break;
-        case 3: split_expand_kernel<3><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, err); break;
-        case 4: split_expand_kernel<4><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, err); break;
-        case 5: split_expand_kernel<5><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, err); break;
-        default: split_expand_kernel<6><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, err); break;
+        case 2: split_expand_kernel<2><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
+        case 3: split_expand_kernel<3><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
+        case 4: split_expand_kernel<4><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
+        case 5: split_expand_kernel<5><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
+        default: split_expand_kernel<6><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
     }
     return 1;
 }

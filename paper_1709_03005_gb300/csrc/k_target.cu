@@ -218,7 +218,7 @@ __global__ void sort_hist_kernel(const SortTask *__restrict__ tasks, const int64
 
 // One block per task: x[0] = 0, x[1..n] := inclusive scan of x[1..n], and
 // copy[0..n-1] := x[0..n-1] (the exclusive offsets).
-__global__ void __launch_bounds__(1024) scan_kernel(const ScanTask *__restrict__ tasks, int n_tasks) {
+__global__ void __launch_bounds__(1024) scan_grouped_kernel(const ScanTask *__restrict__ tasks, int n_tasks) {
     __shared__ int64_t warp_sums[32];
     __shared__ int64_t carry;
     const ScanTask T = tasks[blockIdx.x];
@@ -419,7 +419,7 @@ int g_assemble(const Grouped<ATask> &g, cudaStream_t s) { HB_GROUPED(assemble_ke
 
 int g_scan(const Grouped<ScanTask> &g, cudaStream_t s) {
     if (g.n <= 0) return 0;
-    scan_kernel<<<g.n, 1024, 0, s>>>(g.tasks, g.n);
+    scan_grouped_kernel<<<g.n, 1024, 0, s>>>(g.tasks, g.n);
     return 1;
 }
 
