@@ -105,7 +105,12 @@ typedef struct {
 typedef struct {
     int32_t split_slices;     /* mixed path: bf16 slices per operand (2..6), 0 = default (6) */
     int32_t validate;         /* 0 = skip the O(n^2) input checks */
-    int32_t reserved[14];
+    int32_t autotune;         /* 1 = time the launch-shape candidates on the first build
+                                 (results are bit-identical for every candidate) */
+    int32_t split_tile;       /* 0 = chosen; 3, 4, 5: tensor-core tiles of (128 >> v) j x (1 << v) j' */
+    int32_t class4_states;    /* 0 = chosen; 8, 16, 32: target states per pass of the mixed class-4 kernel */
+    int32_t class4_threads;   /* 0 = chosen; 32, 64, 128: continuum orbitals per class-4 block */
+    int32_t reserved[10];
 } hb_options;
 
 typedef struct {
@@ -196,15 +201,27 @@ int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, int32_t max_
 int hb_init_shared(hb_ctx **ctx, const hb_problem *p, const hb_options *o, hb_ctx *base, void *stream);
 
 /* Batched build of n staged contexts into outs[0..n) (Section 2.2 classes for
-   every block): one eager build, then the whole set is captured as a CUDA graph
-   that hb_batch_launch replays with a single launch.  The blocks in outs are
-   baked into the graph and must stay allocated. */
+   every block).  The contexts must share the target orbital space (n_words,
+   n_to).  Every stage of the build is one grouped launch over the group pairs
+   of all contexts; the group pairs of any context that read the same
+   continuum rectangle of the same panel share one expansion GEMM (Eq. 7).
+   Creation times the launch-shape candidates once on the batch's own tasks
+   (results are bit-identical for every candidate), then captures the whole
+   set as a CUDA graph that hb_batch_launch replays with a single launch.  The
+   blocks in outs are baked into the graph and must stay allocated.  st of
+   hb_batch_launch (or NULL) receives the per-stage times of the replay. */
 typedef struct hb_batch hb_batch;
 int hb_batch_create(hb_batch **b, hb_ctx *const *ctxs, int32_t n, int32_t precision, const hb_blocks *outs,
                     void *stream);
 int hb_batch_launch(hb_batch *b, hb_stats *st, void *stream);
 int hb_batch_nodes(const hb_batch *b);
 void hb_batch_destroy(hb_batch *b);
+
+/* The launch shapes a batch (or a context's own build plan) uses, as text
+   into buf (NUL-terminated, truncated to len).  Returns the full length, -1
+   on a NULL argument.  No counterpart in the paper: reports the autotuner. */
+int32_t hb_batch_report(const hb_batch *b, char *buf, int32_t len);
+int32_t hb_tuning_report(const hb_ctx *ctx, char *buf, int32_t len);
 
 /* Excitation classification (Section 2.1) of every pair (a, b) of two
    determinant lists on the device.  mode 0: equal electron counts, degree =

@@ -95,6 +95,12 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
     if (p->n_groups > 0 && p->n_l2 > 0 && !p->eri_tttc)
         return fail(ctx, HB_ERR_INVALID_ARG, "eri_tttc is NULL");
     if (!std::isfinite(p->e_core)) return fail(ctx, HB_ERR_INVALID_ARG, "e_core is not finite");
+    if (o && o->split_tile != 0 && (o->split_tile < 3 || o->split_tile > 5))
+        return fail(ctx, HB_ERR_INVALID_ARG, "split_tile must be 0, 3, 4 or 5");
+    if (o && o->class4_states != 0 && o->class4_states != 8 && o->class4_states != 16 && o->class4_states != 32)
+        return fail(ctx, HB_ERR_INVALID_ARG, "class4_states must be 0, 8, 16 or 32");
+    if (o && o->class4_threads != 0 && o->class4_threads != 32 && o->class4_threads != 64 && o->class4_threads != 128)
+        return fail(ctx, HB_ERR_INVALID_ARG, "class4_threads must be 0, 32, 64 or 128");
     const int W = p->n_words, nw = 2 * W;
     // electron counts: every target determinant has the same alpha/beta split,
     // the continuum electron sets the L2 split
@@ -212,6 +218,12 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
     ctx->n_elec = p->n_elec; ctx->W = p->n_words; ctx->cont_spin = p->cont_spin;
     ctx->n_groups = p->n_groups; ctx->n_l2 = p->n_l2; ctx->e_core = p->e_core;
     ctx->split_slices = (o && o->split_slices > 0) ? o->split_slices : 6;
+    ctx->autotune = (o && o->autotune) ? 1 : 0;
+    if (o) {
+        ctx->force_tile = o->split_tile;
+        ctx->force_c4_states = o->class4_states;
+        ctx->force_c4_threads = o->class4_threads;
+    }
     ctx->Pt = (int64_t)p->n_to * (p->n_to + 1) / 2;
     ctx->K = (int)(ctx->Pt + (int64_t)p->n_to * p->n_to + 2);
     ctx->Kpad = (ctx->K + 63) / 64 * 64;
@@ -430,6 +442,10 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         int rc = plan_create(one, 1, out, precision, &plan, &err, s);
         if (rc != HB_OK) return fail(ctx, rc, err);
         ctx->plan = plan;
+        if (ctx->autotune) {
+            rc = plan_autotune(plan, s, &err);
+            if (rc != HB_OK) return fail(ctx, rc, err);
+        }
     } else if (!plan_outputs_equal(plan, out)) {
         int rc = plan_set_outputs(plan, out, &err, s);
         if (rc != HB_OK) return fail(ctx, rc, err);
@@ -474,6 +490,15 @@ extern "C" int hb_classify(const uint64_t *a, int32_t n_a, const uint64_t *b, in
     }
     CK(cudaGetLastError());
     return HB_OK;
+}
+
+extern "C" int32_t hb_tuning_report(const hb_ctx *ctx, char *buf, int32_t len) {
+    if (!ctx || !buf || len < 1) return -1;
+    const std::string r = ctx->plan ? plan_report((const hb::Plan *)ctx->plan) : std::string("no build yet");
+    const int32_t n = (int32_t)std::min<size_t>(r.size(), (size_t)len - 1);
+    memcpy(buf, r.data(), n);
+    buf[n] = 0;
+    return (int32_t)r.size();
 }
 
 extern "C" const char *hb_last_error(const hb_ctx *ctx) {

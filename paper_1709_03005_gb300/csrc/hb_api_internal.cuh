@@ -47,6 +47,8 @@ struct hb_ctx {
     int n_to = 0, n_co = 0, n_orb = 0, n_elec = 0, W = 1, cont_spin = 0, n_groups = 0, n_l2 = 0;
     double e_core = 0.0;
     int split_slices = 5;
+    int autotune = 0;
+    int force_tile = 0, force_c4_states = 0, force_c4_threads = 0;   // 0: chosen by the plan
     int64_t Pt = 0;
     int K = 0, Kpad = 0;
     int64_t Dc = 0, dim = 0;

@@ -25,6 +25,13 @@ int plan_precision(const hb::Plan *p);
 int plan_run(hb::Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, std::string *err);
 // After the stream has finished a timed run: per-stage times and counters.
 void plan_stats(hb::Plan *p, hb_stats *st);
+// Time the result-identical launch-shape candidates of every tunable stage
+// (split tile arrangement, class-4 state tile and threads, gamma warp or block
+// per key) on this plan's own tasks, keep the fastest, re-upload the tables.
+int plan_autotune(hb::Plan *p, cudaStream_t s, std::string *err);
+bool plan_tuned(const hb::Plan *p);
+// The launch shapes in use, as text.
+std::string plan_report(const hb::Plan *p);
 // Bounded-wait status word of the tensor-core kernel (0: fine).
 int plan_error_word(hb::Plan *p, int *word);
 void plan_destroy(hb::Plan *p);

@@ -136,7 +136,8 @@ struct SliceTask {      // rows of X into bf16 slices at destination rows [row0,
 
 struct SplitTask {      // one merged block on the tensor cores
     int cf, cn, cfp, cnp;     // the continuum rectangle (same for every column)
-    int jpt_tiles, ntn, N;    // tiles along j' (16 each), tiles along the columns, columns
+    int jpt_tiles, ntn, N;    // tiles along j', tiles along the columns, columns
+    int bjp_log2;             // tile of (128 >> bjp_log2) j x (1 << bjp_log2) j' continuum pairs (3..5)
     int64_t coef_row0;        // first row of the block in the coefficient slices
     int64_t col0;             // first column in the ExpCol table
 };
@@ -179,6 +180,7 @@ int g_classify(const Grouped<ClsTask> &g, int W, int mode, cudaStream_t s);
 int g_pair_values(const Grouped<PVTask> &g, int W, cudaStream_t s);
 int g_l2_csr(const Grouped<L2Task> &g, int W, cudaStream_t s);
 int g_sandwich(const Grouped<SWTask> &g, cudaStream_t s);
+int g_sandwich_small(const Grouped<SWTask> &g, cudaStream_t s);    // nsp <= 32 (used for nsp <= 16)
 int g_tn_partial(const Grouped<TNTask> &g, size_t smem, cudaStream_t s);
 int g_tn_reduce(const Grouped<TNTask> &g, cudaStream_t s);
 int g_item_fill(const Grouped<IFTask> &g, cudaStream_t s);
@@ -187,6 +189,7 @@ int g_sort_hist(const Grouped<SortTask> &g, cudaStream_t s);
 int g_scan(const Grouped<ScanTask> &g, cudaStream_t s);
 int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s);
 int g_gamma(const Grouped<GTask> &g, size_t smem, cudaStream_t s);
+int g_gamma_warp(const Grouped<GTask> &g, cudaStream_t s);         // ns * nsp <= 64
 int g_assemble(const Grouped<ATask> &g, cudaStream_t s);
 int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s);
 // dfloat = 0: FP64 (128 threads, 32 states a pass); 1: double-float with
@@ -202,6 +205,7 @@ int64_t blocks_tn_reduce(int ns, int nsp);
 int64_t blocks_zero(int64_t n);
 int64_t blocks_sort(int64_t n_items);
 int64_t blocks_gamma(int n_keys, int ns, int nsp);
+int64_t blocks_gamma_warp(int n_keys);
 int64_t blocks_expand_fp64(int cn, int cnp, int N);
 int64_t blocks_class4(int n_l2, int cn, int jt);
 int tn_ny(int ns, int nsp);

@@ -5,6 +5,7 @@
 // group pairs of all Hamiltonians, so blocks of very different size fill the
 // GPU together, and the short fixed sequence of launches is captured once and
 // replayed by hb_batch_launch: the host issues one launch for the whole set.
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -58,6 +59,9 @@ extern "C" int hb_batch_create(hb_batch **out, hb_ctx *const *ctxs, int32_t n, i
     // the plan prepares the tensor-core operands and uploads its task tables
     int rc = plan_create(ctxs, n, outs, precision, &b->plan, &err, s);
     if (rc != HB_OK) { delete b; return bfail(rc, err); }
+    // pick the launch shapes by timing them on this batch's own tasks
+    rc = plan_autotune(b->plan, s, &err);
+    if (rc != HB_OK) { batch_free(b); return bfail(rc, err); }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { batch_free(b); return bfail(HB_ERR_CUDA, cudaGetErrorString(e)); }
     // capture on a private stream (the legacy default stream cannot be captured)
@@ -122,6 +126,15 @@ extern "C" int hb_batch_launch(hb_batch *b, hb_stats *st, void *stream) {
 }
 
 extern "C" int hb_batch_nodes(const hb_batch *b) { return b ? (int)b->nodes : -1; }
+
+extern "C" int32_t hb_batch_report(const hb_batch *b, char *buf, int32_t len) {
+    if (!b || !buf || len < 1) return -1;
+    const std::string r = plan_report(b->plan);
+    const int32_t n = (int32_t)std::min<size_t>(r.size(), (size_t)len - 1);
+    memcpy(buf, r.data(), n);
+    buf[n] = 0;
+    return (int32_t)r.size();
+}
 
 extern "C" void hb_batch_destroy(hb_batch *b) {
     if (!b) return;

@@ -10,8 +10,11 @@
 // thousands of small launches.  The task tables live in one device buffer,
 // uploaded when the plan is made (and again only when the output blocks
 // change).  A plan over many contexts is what a batch captures in a CUDA graph.
+#include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -39,7 +42,29 @@ struct Stage {
 
 struct SplitGroup {
     const hb_ctx *panel_ctx = nullptr;
+    int lg = 4;                        // tile arrangement of every task of the launch
     Stage<SplitTask> st;
+};
+
+// Tunable launch shapes.  Every candidate of a choice computes bit-identical
+// results (only the partition of the work over blocks and threads changes),
+// so tuning never changes the output.
+struct Choices {
+    std::map<std::pair<int, int>, int> tile;                   // (cn, cn') -> split tile arrangement
+    std::map<std::pair<int, int>, std::pair<int, int>> c4;     // (ns, cn) -> (state tile, threads)
+    std::map<int, int> gamma_warp;                             // ns * ns' (<= 64) -> 1 warp / 0 block per key
+};
+
+// What the tuner needs of each tunable task.
+struct TuneSplit {
+    const hb_ctx *panel_ctx;
+    SplitTask t;
+};
+struct TuneC4 {
+    C4Task t;
+};
+struct TuneGamma {
+    GTask t;
 };
 
 struct Plan {
@@ -49,13 +74,13 @@ struct Plan {
     int W = 1, Kpad = 0, n_to = 0, S = 0, delta_col = 0;
     Stage<ClsTask> cls_tt, cls_tl2;
     Stage<PVTask> pv;
-    Stage<SWTask> sw;
+    Stage<SWTask> sw, sws;             // sandwich: wide / narrow (nsp <= 16) states
     Stage<TNTask> tn, tnr;
     Stage<IFTask> itf;
     Stage<ZTask> zero;
     Stage<SortTask> sort;
     Stage<ScanTask> scan;
-    Stage<GTask> gam;
+    Stage<GTask> gam, gamw;            // gamma bins: block / warp (ns * nsp <= 64) per key
     Stage<ATask> asmb;
     Stage<XTask> x64;
     Stage<SliceTask> slc;
@@ -89,6 +114,11 @@ struct Plan {
     std::vector<cudaEvent_t> ev_split;
     int launches = 0, expand_launches = 0;
     bool timed = false;
+    Choices choice;
+    bool tuned = false;
+    std::vector<TuneSplit> tune_split;
+    std::vector<TuneC4> tune_c4;
+    std::vector<TuneGamma> tune_gamma;
 };
 
 }  // namespace hb
@@ -119,12 +149,13 @@ void stage_bind(Stage<T> &st, uint8_t *dev) {
 
 // Task tables of every stage from the contexts and the output blocks.
 void fill_tasks(Plan &p) {
-    p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.sw.clear(); p.tn.clear(); p.tnr.clear();
+    p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.sw.clear(); p.sws.clear(); p.gamw.clear(); p.tn.clear(); p.tnr.clear();
     p.itf.clear(); p.zero.clear(); p.sort.clear(); p.scan.clear(); p.gam.clear(); p.asmb.clear();
     p.x64.clear(); p.slc.clear(); p.drows.clear(); p.l2.clear();
     for (auto &v : p.c4v) v.st.clear();
     for (auto &sg : p.split) sg.st.clear();
     p.cols.clear();
+    p.tune_split.clear(); p.tune_c4.clear(); p.tune_gamma.clear();
     p.smem_tn = p.smem_gamma = 0;
     p.flops = 0.0;
     p.n_expand_tasks = 0;
@@ -150,7 +181,6 @@ void fill_tasks(Plan &p) {
     struct Block {
         BlockKey key;
         hb_ctx *ctx = nullptr;
-        int sg = -1;
         std::vector<Member> members;
     };
     std::map<BlockKey, int> block_of;
@@ -161,17 +191,6 @@ void fill_tasks(Plan &p) {
         const Ints I = ctx->ints();
         const int n_keys = 2 * ctx->n_to * ctx->n_to;
         const int W = ctx->W;
-        int sg = -1;
-        if (p.precision == HB_MIXED && !ctx->gps.empty()) {
-            const void *key = mixed_panel_key(ctx);
-            for (size_t i = 0; i < p.split.size(); ++i)
-                if (mixed_panel_key(p.split[i].panel_ctx) == key) sg = (int)i;
-            if (sg < 0) {
-                p.split.emplace_back();
-                p.split.back().panel_ctx = ctx;
-                sg = (int)p.split.size() - 1;
-            }
-        }
         for (auto &P : ctx->gps) {
             const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
             const uint64_t *da = ctx->dets + A.det_off, *db = ctx->dets + B.det_off;
@@ -179,7 +198,8 @@ void fill_tasks(Plan &p) {
             p.cls_tt.add(ClsTask{da, db, A.ndet, B.ndet, ctx->cont_spin, 2, 0, P.rowptr, P.pairs},
                          blocks_rows8(A.ndet));
             p.pv.add(PVTask{I, da, db, P.pairs, P.n_pairs, P.val}, blocks_pair_values(P.n_pairs));
-            p.sw.add(SWTask{P.pairs, P.rowptr, P.val, A.ndet, Cb, B.ns, P.W}, blocks_rows8(A.ndet));
+            (B.ns <= 16 ? p.sws : p.sw).add(SWTask{P.pairs, P.rowptr, P.val, A.ndet, Cb, B.ns, P.W},
+                                            blocks_rows8(A.ndet));
             const int ny = tn_ny(A.ns, B.ns);
             // E = C^T (H^N C'); S = C^T C within a group (identical determinants
             // only, hb_init rejects repeats) and zero between groups
@@ -197,9 +217,20 @@ void fill_tasks(Plan &p) {
             p.zero.add(ZTask{P.sort_off, n_off + 1}, blocks_zero(n_off + 1));
             p.sort.add(SortTask{P.items, P.n_items, nc, n_keys, P.sort_off, P.sort_cur, P.order}, blocks_sort(P.n_items));
             p.scan.add(ScanTask{P.sort_off, n_off, P.sort_cur}, 1);
-            p.gam.add(GTask{P.items, P.order, P.sort_off, nc, n_keys, Ca, A.ns, Cb, B.ns, ny, P.gamma},
-                      blocks_gamma(n_keys, A.ns, B.ns));
-            p.smem_gamma = std::max(p.smem_gamma, smem_stage(A.ns, B.ns));
+            const GTask gt{P.items, P.order, P.sort_off, nc, n_keys, Ca, A.ns, Cb, B.ns, ny, P.gamma};
+            const int nout = A.ns * B.ns;
+            bool warp = nout <= 64;
+            if (warp) {
+                auto gc = p.choice.gamma_warp.find(nout);
+                if (gc != p.choice.gamma_warp.end()) warp = gc->second != 0;
+                p.tune_gamma.push_back(TuneGamma{gt});
+            }
+            if (warp) {
+                p.gamw.add(gt, blocks_gamma_warp(n_keys));
+            } else {
+                p.gam.add(gt, blocks_gamma(n_keys, A.ns, B.ns));
+                p.smem_gamma = std::max(p.smem_gamma, smem_stage(A.ns, B.ns));
+            }
             p.asmb.add(ATask{P.gamma, P.S, P.E, P.nn, P.n_nn, A.ns, B.ns, ctx->n_to, ctx->cont_spin, ctx->Kpad,
                              ctx->e_core, P.A},
                        P.n_nn);
@@ -213,7 +244,6 @@ void fill_tasks(Plan &p) {
                 blocks.emplace_back();
                 blocks.back().key = key;
                 blocks.back().ctx = ctx;
-                blocks.back().sg = sg;
             }
             blocks[it->second].members.push_back(Member{ctx, &P, &out});
             if (p.precision == HB_MIXED) {
@@ -230,7 +260,13 @@ void fill_tasks(Plan &p) {
             p.cls_tl2.add(ClsTask{ctx->l2, dg, ctx->n_l2, G.ndet, ctx->cont_spin, 2, 0, L.rowptr, L.pairs},
                           blocks_rows8(ctx->n_l2));
             int ns_tile = 32, jt = 128;
-            if (p.precision == HB_MIXED) class4_shape(G.ns, G.cn, &ns_tile, &jt);
+            if (p.precision == HB_MIXED) {
+                class4_shape(G.ns, G.cn, &ns_tile, &jt);
+                auto cc = p.choice.c4.find({G.ns, G.cn});
+                if (cc != p.choice.c4.end()) { ns_tile = cc->second.first; jt = cc->second.second; }
+                if (ctx->force_c4_states) ns_tile = ctx->force_c4_states;
+                if (ctx->force_c4_threads) jt = ctx->force_c4_threads;
+            }
             Plan::C4Var *var = nullptr;
             for (auto &v : p.c4v)
                 if (v.ns_tile == ns_tile && v.jt == jt) var = &v;
@@ -238,10 +274,11 @@ void fill_tasks(Plan &p) {
                 p.c4v.push_back(Plan::C4Var{ns_tile, jt, Stage<C4Task>()});
                 var = &p.c4v.back();
             }
-            var->st.add(C4Task{I, L.pairs, L.rowptr, ctx->n_l2, dg, ctx->ci + G.ci_off,
-                               ctx->ci_df ? ctx->ci_df + G.ci_off : nullptr, ctx->tttc_df, ctx->h_df, G.ns, G.cf, G.cn,
-                               ctx->cont_spin, class4_ny(G.cn, jt), G.row_off, ctx->Dc, out.Hlc},
-                        blocks_class4(ctx->n_l2, G.cn, jt));
+            const C4Task c4t{I, L.pairs, L.rowptr, ctx->n_l2, dg, ctx->ci + G.ci_off,
+                             ctx->ci_df ? ctx->ci_df + G.ci_off : nullptr, ctx->tttc_df, ctx->h_df, G.ns, G.cf, G.cn,
+                             ctx->cont_spin, class4_ny(G.cn, jt), G.row_off, ctx->Dc, out.Hlc};
+            var->st.add(c4t, blocks_class4(ctx->n_l2, G.cn, jt));
+            if (p.precision == HB_MIXED) p.tune_c4.push_back(TuneC4{c4t});
         }
         if (ctx->n_l2 > 0)
             p.l2.add(L2Task{I, ctx->l2, ctx->n_l2, ctx->l2_rowptr, out.l2_row_ptr, out.l2_col, out.l2_val, ctx->e_core},
@@ -275,14 +312,30 @@ void fill_tasks(Plan &p) {
         const int N = (int)((int64_t)p.cols.size() - col0);
         const BlockKey &k = B.key;
         if (p.precision == HB_MIXED) {
+            int lg = split_tile_heuristic(k.cn, k.cnp);
+            auto tc = p.choice.tile.find({k.cn, k.cnp});
+            if (tc != p.choice.tile.end()) lg = tc->second;
+            if (B.ctx->force_tile) lg = B.ctx->force_tile;
+            const void *pkey = mixed_panel_key(B.ctx);
+            int gi = -1;
+            for (size_t i = 0; i < p.split.size(); ++i)
+                if (mixed_panel_key(p.split[i].panel_ctx) == pkey && p.split[i].lg == lg) gi = (int)i;
+            if (gi < 0) {
+                p.split.emplace_back();
+                p.split.back().panel_ctx = B.ctx;
+                p.split.back().lg = lg;
+                gi = (int)p.split.size() - 1;
+            }
             SplitTask t;
             t.cf = k.cf; t.cn = k.cn; t.cfp = k.cfp; t.cnp = k.cnp;
-            t.jpt_tiles = split_jpt(k.cnp);
+            t.bjp_log2 = lg;
+            t.jpt_tiles = split_jpt(k.cnp, lg);
             t.ntn = split_ntn(N);
             t.N = N;
             t.coef_row0 = coef_row;
             t.col0 = col0;
-            p.split[B.sg].st.add(t, blocks_split(k.cn, k.cnp, N));
+            p.split[gi].st.add(t, blocks_split(k.cn, k.cnp, N, lg));
+            p.tune_split.push_back(TuneSplit{B.ctx, t});
             coef_row += N;
         } else {
             p.x64.add(XTask{B.ctx->panel, B.ctx->Kpad, B.ctx->n_co, k.cf, k.cn, k.cfp, k.cnp,
@@ -293,10 +346,18 @@ void fill_tasks(Plan &p) {
     p.coef_rows = coef_row;
 }
 
+void ensure_split_events(Plan &p) {
+    while (p.ev_split.size() < 2 * p.split.size()) {
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        p.ev_split.push_back(e);
+    }
+}
+
 void pack_all(Plan &p) {
     p.host.clear();
     stage_pack(p.cls_tt, p.host); stage_pack(p.cls_tl2, p.host); stage_pack(p.pv, p.host);
-    stage_pack(p.sw, p.host); stage_pack(p.tn, p.host); stage_pack(p.tnr, p.host); stage_pack(p.itf, p.host);
+    stage_pack(p.sw, p.host); stage_pack(p.sws, p.host); stage_pack(p.gamw, p.host); stage_pack(p.tn, p.host); stage_pack(p.tnr, p.host); stage_pack(p.itf, p.host);
     stage_pack(p.zero, p.host); stage_pack(p.sort, p.host); stage_pack(p.scan, p.host); stage_pack(p.gam, p.host);
     stage_pack(p.asmb, p.host); stage_pack(p.x64, p.host); stage_pack(p.slc, p.host);
     for (auto &sg : p.split) stage_pack(sg.st, p.host);
@@ -309,7 +370,7 @@ void pack_all(Plan &p) {
 
 void bind_all(Plan &p) {
     stage_bind(p.cls_tt, p.dev); stage_bind(p.cls_tl2, p.dev); stage_bind(p.pv, p.dev);
-    stage_bind(p.sw, p.dev); stage_bind(p.tn, p.dev); stage_bind(p.tnr, p.dev); stage_bind(p.itf, p.dev);
+    stage_bind(p.sw, p.dev); stage_bind(p.sws, p.dev); stage_bind(p.gamw, p.dev); stage_bind(p.tn, p.dev); stage_bind(p.tnr, p.dev); stage_bind(p.itf, p.dev);
     stage_bind(p.zero, p.dev); stage_bind(p.sort, p.dev); stage_bind(p.scan, p.dev); stage_bind(p.gam, p.dev);
     stage_bind(p.asmb, p.dev); stage_bind(p.x64, p.dev); stage_bind(p.slc, p.dev);
     for (auto &sg : p.split) stage_bind(sg.st, p.dev);
@@ -404,14 +465,7 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
     if (precision == HB_MIXED && p->coef_rows > 0) {
         rc = split_coef_alloc(p->S, p->coef_rows, p->Kpad, &p->coef, &p->tm_coef, err);
         if (rc != HB_OK) { plan_destroy(p); return rc; }
-        for (auto &sg : p->split) {
-            (void)sg;
-            cudaEvent_t a = nullptr, b = nullptr;
-            cudaEventCreate(&a);
-            cudaEventCreate(&b);
-            p->ev_split.push_back(a);
-            p->ev_split.push_back(b);
-        }
+        ensure_split_events(*p);
     }
     pack_all(*p);
     rc = upload(*p, err, s);
@@ -435,8 +489,180 @@ int plan_precision(const Plan *p) { return p->precision; }
 int plan_set_outputs(Plan *p, const hb_blocks *outs, std::string *err, cudaStream_t s) {
     p->outs.assign(outs, outs + p->outs.size());
     fill_tasks(*p);
+    ensure_split_events(*p);
     pack_all(*p);
     return upload(*p, err, s);
+}
+
+namespace {
+
+// Mean time of `launch` over a private copy of the given tasks (one warm-up
+// launch, then `reps` timed launches on stream s).
+template <class T, class F>
+float time_tasks(const std::vector<T> &tasks, const std::vector<int64_t> &nblocks, F launch, cudaStream_t s,
+                 int reps = 2) {
+    std::vector<int64_t> blk(1, 0);
+    for (int64_t b : nblocks) blk.push_back(blk.back() + b);
+    if (tasks.empty() || blk.back() == 0) return 0.0f;
+    const size_t bt = sizeof(T) * tasks.size(), ob = align256(bt), total = ob + sizeof(int64_t) * blk.size();
+    uint8_t *d = nullptr;
+    if (cudaMalloc(&d, total) != cudaSuccess) return 1e30f;
+    cudaMemcpyAsync(d, tasks.data(), bt, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d + ob, blk.data(), sizeof(int64_t) * blk.size(), cudaMemcpyHostToDevice, s);
+    Grouped<T> g;
+    g.tasks = (const T *)d;
+    g.blk = (const int64_t *)(d + ob);
+    g.n = (int)tasks.size();
+    g.blocks = blk.back();
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    launch(g);
+    cudaEventRecord(a, s);
+    for (int r = 0; r < reps; ++r) launch(g);
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamSynchronize(s);
+    cudaFree(d);
+    return ms / reps;
+}
+
+}  // namespace
+
+// A candidate replaces the heuristic default only if it is this much faster
+// (short launches time noisily; a stage's tasks also share the GPU when the
+// whole plan runs, which a timing of one class alone does not see).
+constexpr float kGain = 0.95f;
+
+int plan_autotune(Plan *p, cudaStream_t s, std::string *err) {
+    // one build makes every stage's inputs (records, coefficient rows and their
+    // slices) current; the candidates then rerun single stages on them
+    int rc = plan_run(p, s, false, false, nullptr, err);
+    if (rc != HB_OK) return rc;
+    if (cudaStreamSynchronize(s) != cudaSuccess) { *err = "autotune: build failed"; return HB_ERR_CUDA; }
+    const int W = p->W;
+    Choices ch;
+    // split expansion: tile arrangement per continuum rectangle (and panel)
+    {
+        std::map<std::tuple<const void *, int, int>, std::vector<const TuneSplit *>> cls;
+        for (auto &t : p->tune_split) cls[{mixed_panel_key(t.panel_ctx), t.t.cn, t.t.cnp}].push_back(&t);
+        for (auto &kv : cls) {
+            const int cn = std::get<1>(kv.first), cnp = std::get<2>(kv.first);
+            const hb_ctx *pc = kv.second.front()->panel_ctx;
+            // the least-padding arrangement stays unless another is clearly faster
+            const int def_lg = split_tile_heuristic(cn, cnp);
+            float best = 0.0f, def_ms = 0.0f;
+            int best_lg = -1;
+            for (int lg : {def_lg, 3, 4, 5}) {
+                if (best_lg >= 0 && lg == def_lg) continue;
+                std::vector<SplitTask> ts;
+                std::vector<int64_t> nb;
+                for (auto *t : kv.second) {
+                    SplitTask u = t->t;
+                    u.bjp_log2 = lg;
+                    u.jpt_tiles = split_jpt(cnp, lg);
+                    ts.push_back(u);
+                    nb.push_back(blocks_split(cn, cnp, u.N, lg));
+                }
+                const float ms = time_tasks(ts, nb, [&](const Grouped<SplitTask> &g) {
+                    g_split(pc, lg, &p->tm_coef, g, p->Kpad / 64, p->d_cols, p->err, s);
+                }, s);
+                if (best_lg < 0) { best = def_ms = ms; best_lg = lg; }
+                else if (ms < best && ms < kGain * def_ms) { best = ms; best_lg = lg; }
+            }
+            // a rectangle seen with several panels keeps the first panel's choice
+            ch.tile.emplace(std::make_pair(cn, cnp), best_lg);
+        }
+    }
+    // class 4: state tile and thread count per (states, continuum count)
+    {
+        std::map<std::pair<int, int>, std::vector<const TuneC4 *>> cls;
+        for (auto &t : p->tune_c4) cls[{t.t.ns, t.t.cn}].push_back(&t);
+        for (auto &kv : cls) {
+            const int cn = kv.first.second;
+            int dnt = 32, djt = 128;
+            class4_shape(kv.first.first, cn, &dnt, &djt);
+            float best = 0.0f, def_ms = 0.0f;
+            std::pair<int, int> arg(-1, -1);
+            std::vector<std::pair<int, int>> cand{{dnt, djt}};
+            for (int nt : {8, 16, 32})
+                for (int jt : {32, 64, 128})
+                    if (nt != dnt || jt != djt) cand.push_back({nt, jt});
+            for (auto &c : cand) {
+                const int nt = c.first, jt = c.second;
+                std::vector<C4Task> ts;
+                std::vector<int64_t> nb;
+                for (auto *t : kv.second) {
+                    C4Task u = t->t;
+                    u.ny = class4_ny(cn, jt);
+                    ts.push_back(u);
+                    nb.push_back(blocks_class4(u.n_l2, cn, jt));
+                }
+                const float ms = time_tasks(ts, nb, [&](const Grouped<C4Task> &g) {
+                    g_class4(g, W, 1, nt, jt, s);
+                }, s);
+                if (arg.first < 0) { best = def_ms = ms; arg = c; }
+                else if (ms < best && ms < kGain * def_ms) { best = ms; arg = c; }
+            }
+            ch.c4[kv.first] = arg;
+        }
+    }
+    // gamma bins of small state blocks: one warp or one block per key
+    {
+        std::map<int, std::vector<const TuneGamma *>> cls;
+        for (auto &t : p->tune_gamma) cls[t.t.ns * t.t.nsp].push_back(&t);
+        for (auto &kv : cls) {
+            std::vector<GTask> ts;
+            std::vector<int64_t> nbw, nbb;
+            size_t smem = 0;
+            for (auto *t : kv.second) {
+                ts.push_back(t->t);
+                nbw.push_back(blocks_gamma_warp(t->t.n_keys));
+                nbb.push_back(blocks_gamma(t->t.n_keys, t->t.ns, t->t.nsp));
+                smem = std::max(smem, smem_stage(t->t.ns, t->t.nsp));
+            }
+            const float mw = time_tasks(ts, nbw, [&](const Grouped<GTask> &g) { g_gamma_warp(g, s); }, s);
+            const float mb = time_tasks(ts, nbb, [&](const Grouped<GTask> &g) { g_gamma(g, smem, s); }, s);
+            ch.gamma_warp[kv.first] = mb < kGain * mw ? 0 : 1;     // the warp form unless clearly slower
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { *err = std::string("autotune: ") + cudaGetErrorString(e); return HB_ERR_CUDA; }
+    p->choice = ch;
+    p->tuned = true;
+    fill_tasks(*p);
+    ensure_split_events(*p);
+    pack_all(*p);
+    return upload(*p, err, s);
+}
+
+bool plan_tuned(const Plan *p) { return p->tuned; }
+
+std::string plan_report(const Plan *p) {
+    std::string r;
+    char buf[160];
+    snprintf(buf, sizeof buf, "tuned=%d;", p->tuned ? 1 : 0);
+    r += buf;
+    std::map<std::pair<int, int>, int> tile;
+    for (auto &g : p->split)
+        for (auto &t : g.st.tasks) tile[{t.cn, t.cnp}] = g.lg;
+    for (auto &kv : tile) {
+        snprintf(buf, sizeof buf, " split %dx%d:%dx%d;", kv.first.first, kv.first.second, 128 >> kv.second,
+                 1 << kv.second);
+        r += buf;
+    }
+    for (auto &v : p->c4v)
+        for (auto &t : v.st.tasks) {
+            snprintf(buf, sizeof buf, " class4 ns%d cn%d:%dx%d;", t.ns, t.cn, v.ns_tile, v.jt);
+            if (r.find(buf) == std::string::npos) r += buf;
+        }
+    snprintf(buf, sizeof buf, " gamma warp/block tasks %d/%d", (int)p->gamw.tasks.size(), (int)p->gam.tasks.size());
+    r += buf;
+    return r;
 }
 
 int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, std::string *err) {
@@ -454,6 +680,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     L += g_classify(p->cls_tt.g, W, 0, s);
     L += g_pair_values(p->pv.g, W, s);
     L += g_sandwich(p->sw.g, s);
+    L += g_sandwich_small(p->sws.g, s);
     L += g_tn_partial(p->tn.g, p->smem_tn, s);
     L += g_tn_reduce(p->tnr.g, s);
     L += g_item_fill(p->itf.g, s);
@@ -462,6 +689,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     L += g_scan(p->scan.g, s);
     L += g_sort_scatter(p->sort.g, s);
     L += g_gamma(p->gam.g, p->smem_gamma, s);
+    L += g_gamma_warp(p->gamw.g, s);
     L += g_assemble(p->asmb.g, s);
     rec(p->ev[1]);
     // expansion (Eq. 7): classes 1, 3, 5, 6, 7
@@ -471,7 +699,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
             L += g_slice(p->slc.g, p->coef_rows, p->Kpad, p->S, p->delta_col, p->coef, s);
             for (size_t i = 0; i < p->split.size(); ++i) {
                 rec(p->ev_split[2 * i]);
-                LX += g_split(p->split[i].panel_ctx, &p->tm_coef, p->split[i].st.g, p->Kpad / 64, p->d_cols, p->err, s);
+                LX += g_split(p->split[i].panel_ctx, p->split[i].lg, &p->tm_coef, p->split[i].st.g, p->Kpad / 64, p->d_cols, p->err, s);
                 rec(p->ev_split[2 * i + 1]);
             }
             L += g_diag_rows(p->drows.g, s);

@@ -50,7 +50,7 @@ struct MixedState {
     __nv_bfloat16 *panel_slices = nullptr;   // [S][Kpad/64][n_co*n_co][64]
     bool panel_ready = false;
     bool borrowed_panel = false;
-    CUtensorMap tm_panel;
+    CUtensorMap tm_panel[3];                  // boxes of 8 x 16, 16 x 8, 32 x 4 continuum pairs (j' x j)
 };
 
 }  // namespace hb
@@ -274,8 +274,9 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     __syncthreads();
     const int lb = lb_s;
     const int tile_n = lb % a.ntn, tile_m = lb / a.ntn;     // N fastest: CTAs sharing a panel tile run together
+    const int lg = a.bjp_log2;                              // tile of (128 >> lg) j x (1 << lg) j'
     const int jt = tile_m / a.jpt_tiles, jpt = tile_m % a.jpt_tiles;
-    const int jj0 = jt * 8, jjp0 = jpt * 16;                // within the group ranges
+    const int jj0 = jt * (BM >> lg), jjp0 = jpt << lg;      // within the group ranges
     const int n0 = tile_n * BN;
     const int kb_per_chunk = KCHUNK / BKB;
     const int nchunks = (kblocks + kb_per_chunk - 1) / kb_per_chunk;
@@ -390,7 +391,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
             mbar_arrive(acc_empty);
         }
         if (ok) {
-            const int jj = jj0 + row / 16, jjp = jjp0 + row % 16;
+            const int jj = jj0 + (row >> lg), jjp = jjp0 + (row & ((1 << lg) - 1));
             if (jj < a.cn && jjp < a.cnp && (a.cf + jj) != (a.cfp + jjp)) {
 #pragma unroll
                 for (int c = 0; c < EPI_COLS; ++c) {
@@ -561,7 +562,7 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
         M.slices = B.slices;
         M.panel_rows = B.panel_rows;
         M.panel_slices = B.panel_slices;
-        M.tm_panel = B.tm_panel;
+        for (int i = 0; i < 3; ++i) M.tm_panel[i] = B.tm_panel[i];
         M.borrowed_panel = true;
         M.panel_ready = true;
         return HB_OK;
@@ -582,11 +583,15 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
     cuuint64_t dims[4] = {(cuuint64_t)BKB, (cuuint64_t)ctx->n_co, (cuuint64_t)ctx->n_co,
                           (cuuint64_t)M.slices * KB};
     cuuint64_t strides[3] = {(cuuint64_t)BKB * 2, (cuuint64_t)ctx->n_co * BKB * 2, (cuuint64_t)rows * BKB * 2};
-    cuuint32_t box[4] = {BKB, 16, 8, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = encode_fn()(&M.tm_panel, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, M.panel_slices, dims, strides, box,
-                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = CUDA_SUCCESS;
+    for (int i = 0; i < 3 && r == CUDA_SUCCESS; ++i) {
+        const int lg = 3 + i;
+        cuuint32_t box[4] = {BKB, (cuuint32_t)(1 << lg), (cuuint32_t)(BM >> lg), 1};
+        r = encode_fn()(&M.tm_panel[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, M.panel_slices, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (r != CUDA_SUCCESS) return mixed_fail(ctx, HB_ERR_CUDA, "panel tensor map: error " + std::to_string((int)r));
     e = set_smem_attr(M.slices);
     if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
@@ -622,12 +627,25 @@ int split_coef_alloc(int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm,
     return HB_OK;
 }
 
-int64_t blocks_split(int cn, int cnp, int N) {
+int64_t blocks_split(int cn, int cnp, int N, int lg) {
     if (cn <= 0 || cnp <= 0 || N <= 0) return 0;
-    return (int64_t)((N + BN - 1) / BN) * ((cn + 7) / 8) * ((cnp + 15) / 16);
+    const int bj = BM >> lg, bjp = 1 << lg;
+    return (int64_t)((N + BN - 1) / BN) * ((cn + bj - 1) / bj) * ((cnp + bjp - 1) / bjp);
 }
 int split_ntn(int N) { return (N + BN - 1) / BN; }
-int split_jpt(int cnp) { return (cnp + 15) / 16; }
+int split_jpt(int cnp, int lg) { return (cnp + (1 << lg) - 1) >> lg; }
+
+// Tile arrangement with the least padding of the cn x cnp rectangle (ties: 8 x 16).
+int split_tile_heuristic(int cn, int cnp) {
+    int best = 4;
+    int64_t best_area = -1;
+    for (int lg : {4, 3, 5}) {
+        const int bj = BM >> lg, bjp = 1 << lg;
+        const int64_t area = (int64_t)((cn + bj - 1) / bj) * bj * ((cnp + bjp - 1) / bjp) * bjp;
+        if (best_area < 0 || area < best_area) { best = lg; best_area = area; }
+    }
+    return best;
+}
 
 int g_slice(const Grouped<SliceTask> &g, int64_t R, int Kpad, int S, int skip_col, void *out, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
@@ -636,18 +654,19 @@ int g_slice(const Grouped<SliceTask> &g, int64_t R, int Kpad, int S, int skip_co
     return 1;
 }
 
-int g_split(const hb_ctx *panel_ctx, const CUtensorMap *tm_coef, const Grouped<SplitTask> &g, int kblocks,
+int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const Grouped<SplitTask> &g, int kblocks,
             const ExpCol *cols, int *err, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
     const MixedState &M = *panel_ctx->mixed;
+    const CUtensorMap &tm_panel = M.tm_panel[lg - 3];
     const size_t smem = M.slices * SLOT + 2048;
     const unsigned grid = (unsigned)g.blocks;
     switch (M.slices) {
-        case 2: split_expand_kernel<2><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
-        case 3: split_expand_kernel<3><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
-        case 4: split_expand_kernel<4><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
-        case 5: split_expand_kernel<5><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
-        default: split_expand_kernel<6><<<grid, NTHREADS, smem, s>>>(M.tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
+        case 2: split_expand_kernel<2><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
+        case 3: split_expand_kernel<3><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
+        case 4: split_expand_kernel<4><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
+        case 5: split_expand_kernel<5><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
+        default: split_expand_kernel<6><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
     }
     return 1;
 }

@@ -56,6 +56,28 @@ __global__ void sandwich_kernel(const SWTask *__restrict__ tasks, const int64_t 
     }
 }
 
+// The same for nsp <= 32: the lanes form G = 32 / P groups of P columns (P the
+// power of two >= nsp); group g takes records g, g+G, ... and the groups are
+// combined by a butterfly over the lanes that hold the same column.
+__global__ void sandwich_small_kernel(const SWTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                      int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const SWTask T = tasks[ti];
+    const int lane = threadIdx.x & 31;
+    const int row = (int)(blockIdx.x - blk[ti]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= T.n_rows) return;
+    const int nsp = T.nsp;
+    int P = 1;
+    while (P < nsp) P <<= 1;
+    const int G = 32 / P, g = lane / P, c = lane % P;
+    const int64_t b = T.row_ptr[row], e = T.row_ptr[row + 1];
+    double acc = 0.0;
+    if (c < nsp)
+        for (int64_t k = b + g; k < e; k += G) acc = fma(T.val[k], __ldg(T.Cp + (int64_t)T.pairs[k].col * nsp + c), acc);
+    for (int off = 16; off >= P; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (g == 0 && c < nsp) T.Wout[(int64_t)row * nsp + c] = acc;
+}
+
 // partial[c][n][n'] = sum_{m in chunk c} C[m][n] * Wm[m][n']; rows staged in
 // batches, each thread keeps 4 outputs; the task's blocks are (chunk, y) with
 // y covering the outputs in steps of 1024.
@@ -339,6 +361,31 @@ __global__ void gamma_kernel(const GTask *__restrict__ tasks, const int64_t *__r
     }
 }
 
+// The same for small outputs (ns * nsp <= 64): one warp per key, the lanes
+// over the outputs, the key's items read in order straight from memory.
+__global__ void gamma_warp_kernel(const GTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const GTask T = tasks[ti];
+    const int lane = threadIdx.x & 31;
+    const int key = (int)(blockIdx.x - blk[ti]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (key >= T.n_keys) return;
+    const int ns = T.ns, nsp = T.nsp, nout = ns * nsp;
+    const int64_t b = T.off[(int64_t)key * T.nc];
+    const int64_t e = T.off[(int64_t)(key + 1) * T.nc];
+    double acc0 = 0.0, acc1 = 0.0;
+    const int t0 = lane, t1 = lane + 32;
+    const int a0 = t0 / nsp, c0 = t0 % nsp, a1 = t1 / nsp, c1 = t1 % nsp;
+    for (int64_t i = b; i < e; ++i) {
+        const GammaItem it = T.items[T.order[i]];
+        if (t0 < nout)
+            acc0 = fma(it.phase * __ldg(T.C + (int64_t)it.m * ns + a0), __ldg(T.Cp + (int64_t)it.mp * nsp + c0), acc0);
+        if (t1 < nout)
+            acc1 = fma(it.phase * __ldg(T.C + (int64_t)it.m * ns + a1), __ldg(T.Cp + (int64_t)it.mp * nsp + c1), acc1);
+    }
+    if (t0 < nout) T.gamma[(int64_t)key * nout + t0] = acc0;
+    if (t1 < nout) T.gamma[(int64_t)key * nout + t1] = acc1;
+}
+
 // ------------------------------------------------------ coefficient rows
 // A[t][k] for the state pairs t = (n, n'):
 //   k <  Pt            : Gamma^(r>=s) = sum_spin gamma(r,s) + gamma(s,r) (r != s)
@@ -390,6 +437,7 @@ int64_t blocks_zero(int64_t n) { return (n + 1023) / 1024; }
 int sort_chunks(int64_t n_items) { return (int)((n_items + kSortChunk - 1) / kSortChunk); }
 int64_t blocks_sort(int64_t n_items) { return sort_chunks(n_items); }
 int64_t blocks_gamma(int n_keys, int ns, int nsp) { return (int64_t)n_keys * tn_ny(ns, nsp); }
+int64_t blocks_gamma_warp(int n_keys) { return (n_keys + 7) / 8; }
 size_t smem_stage(int ns, int nsp) { return sizeof(double) * stage_batch(ns, nsp) * (ns + nsp); }
 
 void gamma_item_counts(const hb_pair *pairs, const int64_t *row_ptr, int n_rows, int n_elec,
@@ -406,6 +454,7 @@ void gamma_item_counts(const hb_pair *pairs, const int64_t *row_ptr, int n_rows,
     } while (0)
 
 int g_sandwich(const Grouped<SWTask> &g, cudaStream_t s) { HB_GROUPED(sandwich_kernel, g, 256, 0, s); }
+int g_sandwich_small(const Grouped<SWTask> &g, cudaStream_t s) { HB_GROUPED(sandwich_small_kernel, g, 256, 0, s); }
 int g_tn_partial(const Grouped<TNTask> &g, size_t smem, cudaStream_t s) {
     HB_GROUPED(tn_partial_kernel, g, 256, smem, s);
 }
@@ -415,6 +464,7 @@ int g_zero(const Grouped<ZTask> &g, cudaStream_t s) { HB_GROUPED(zero_kernel, g,
 int g_sort_hist(const Grouped<SortTask> &g, cudaStream_t s) { HB_GROUPED(sort_hist_kernel, g, 256, 0, s); }
 int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s) { HB_GROUPED(sort_scatter_kernel, g, 32, 0, s); }
 int g_gamma(const Grouped<GTask> &g, size_t smem, cudaStream_t s) { HB_GROUPED(gamma_kernel, g, 256, smem, s); }
+int g_gamma_warp(const Grouped<GTask> &g, cudaStream_t s) { HB_GROUPED(gamma_warp_kernel, g, 256, 0, s); }
 int g_assemble(const Grouped<ATask> &g, cudaStream_t s) { HB_GROUPED(assemble_kernel, g, 256, 0, s); }
 
 int g_scan(const Grouped<ScanTask> &g, cudaStream_t s) {

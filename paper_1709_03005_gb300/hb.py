@@ -35,7 +35,9 @@ class hb_problem(C.Structure):
 
 
 class hb_options(C.Structure):
-    _fields_ = [("split_slices", C.c_int32), ("validate", C.c_int32), ("reserved", C.c_int32 * 14)]
+    _fields_ = [("split_slices", C.c_int32), ("validate", C.c_int32), ("autotune", C.c_int32),
+                ("split_tile", C.c_int32), ("class4_states", C.c_int32), ("class4_threads", C.c_int32),
+                ("reserved", C.c_int32 * 10)]
 
 
 class hb_layout(C.Structure):
@@ -73,7 +75,8 @@ assert PAIR_DTYPE.itemsize == 24
 EXPORTS = ["hb_init", "hb_init_shared", "hb_batch_create", "hb_batch_launch", "hb_batch_nodes",
            "hb_batch_destroy", "hb_query", "hb_group_offset", "hb_build_blocks", "hb_diag", "hb_classify",
            "hb_classify_noalloc", "hb_mlp_set", "hb_mlp_param_count", "hb_mlp_workspace_bytes", "hb_mlp_loss_grad",
-           "hb_mlp_adam", "hb_mlp_predict", "hb_diag_features", "hb_last_error", "hb_destroy"]
+           "hb_mlp_adam", "hb_mlp_predict", "hb_diag_features", "hb_batch_report", "hb_tuning_report",
+           "hb_last_error", "hb_destroy"]
 
 _lib = None
 
@@ -140,7 +143,8 @@ class Hamiltonian:
     cont_first, cont_count), l2_dets, e_core.
     """
 
-    def __init__(self, problem, split_slices=0, validate=True, stream=None, base=None):
+    def __init__(self, problem, split_slices=0, validate=True, stream=None, base=None, autotune=False,
+                 split_tile=0, class4_states=0, class4_threads=0):
         import torch
         self.lib = load()
         self.base = base        # keeps a borrowed-integral base context alive
@@ -164,7 +168,8 @@ class Hamiltonian:
                                    ptr(arr(p.eri_tttc, np.float64)), ptr(arr(p.eri_ttcc, np.float64)),
                                    ptr(arr(p.eri_tctc, np.float64)), len(p.groups), C.addressof(gs),
                                    p.l2_dets.shape[0], ptr(l2) if l2 is not None else None, float(p.e_core))
-        opts = hb_options(split_slices, 1 if validate else 0)
+        opts = hb_options(split_slices, 1 if validate else 0, 1 if autotune else 0, split_tile, class4_states,
+                          class4_threads)
         self.ctx = C.c_void_p()
         torch.cuda.init()
         if base is None:
@@ -237,6 +242,14 @@ class Hamiltonian:
     def set_mlp_params(self, packed):
         """Load a packed parameter vector (see unpack_mlp) for HB_PRECOND_MLP."""
         self.set_mlp(*unpack_mlp(packed))
+
+    def tuning_report(self):
+        """Launch shapes of this context's build plan (after a build), as text."""
+        self.lib.hb_tuning_report.argtypes = [C.c_void_p, C.c_char_p, C.c_int32]
+        self.lib.hb_tuning_report.restype = C.c_int32
+        buf = C.create_string_buffer(4096)
+        self.lib.hb_tuning_report(self.ctx, buf, len(buf))
+        return buf.value.decode()
 
     def close(self):
         if getattr(self, "ctx", None) and self.ctx.value:
@@ -433,6 +446,14 @@ class Batch:
     @property
     def nodes(self):
         return self.lib.hb_batch_nodes(self.handle)
+
+    def report(self):
+        """The launch shapes the batch's autotuner chose, as text."""
+        self.lib.hb_batch_report.argtypes = [C.c_void_p, C.c_char_p, C.c_int32]
+        self.lib.hb_batch_report.restype = C.c_int32
+        buf = C.create_string_buffer(4096)
+        self.lib.hb_batch_report(self.handle, buf, len(buf))
+        return buf.value.decode()
 
     def launch(self, stream=None, stats=True):
         st = hb_stats()
