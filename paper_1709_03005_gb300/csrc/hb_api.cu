@@ -379,14 +379,21 @@ int ensure_df(hb_ctx *ctx, cudaStream_t s) {
         if (rc != HB_OK) return fail(ctx, rc, ctx->base->err);
         ctx->tttc_df = ctx->base->tttc_df;
         ctx->h_df = ctx->base->h_df;
+        ctx->tttt_df = ctx->base->tttt_df;
+        ctx->jk_df = ctx->base->jk_df;
     } else {
         DALLOC(ctx->h_df, no * no);
         split_df(ctx->h, (int64_t)(no * no), ctx->h_df, s);
+        DALLOC(ctx->tttt_df, (size_t)ctx->Pt * ctx->Pt);
+        split_df(ctx->tttt, ctx->Pt * ctx->Pt, ctx->tttt_df, s);
+        DALLOC(ctx->jk_df, 2 * (size_t)ctx->n_to * ctx->n_to);
+        split_df(ctx->jk, 2 * (int64_t)ctx->n_to * ctx->n_to, ctx->jk_df, s);
         if (ctx->tttc && ntc > 0) {
             DALLOC(ctx->tttc_df, (size_t)ctx->Pt * ntc);
             split_df(ctx->tttc, (int64_t)((size_t)ctx->Pt * ntc), ctx->tttc_df, s);
         }
     }
+    for (auto &P : ctx->gps) DALLOC(P.A_df, (int64_t)P.n_nn * ctx->Kpad);
     int64_t nci = 0;
     for (auto &g : ctx->groups) nci += (int64_t)g.ndet * g.ns;
     DALLOC(ctx->ci_df, std::max<int64_t>(nci, 1));

@@ -28,6 +28,7 @@ struct GroupPair {
     double *gamma = nullptr, *W = nullptr, *partial = nullptr, *partial_s = nullptr, *S = nullptr, *E = nullptr;
     int32_t *nn = nullptr;
     double *A = nullptr;        // [n_nn][Kpad] contracted coefficients
+    float2 *A_df = nullptr;     // the same as float pairs (mixed build, made on first use)
 };
 
 // Scratch of one target group against the L2 functions (class 4).
@@ -61,7 +62,7 @@ struct hb_ctx {
     uint64_t *dets = nullptr, *l2 = nullptr;
     double *ci = nullptr;
     // double-float (hi, lo) copies for the mixed class-4 kernel, made on first use
-    float2 *tttc_df = nullptr, *h_df = nullptr, *ci_df = nullptr;
+    float2 *tttc_df = nullptr, *h_df = nullptr, *ci_df = nullptr, *tttt_df = nullptr, *jk_df = nullptr;
     int64_t *l2_rowptr = nullptr;
     int64_t l2_nnz = 0, tt_pairs = 0, tl2_pairs = 0;
     hb::MixedState *mixed = nullptr;
@@ -73,6 +74,7 @@ struct hb_ctx {
     hb::Ints ints() const {
         hb::Ints I;
         I.h = h; I.tttt = tttt; I.tttc = tttc; I.jk = jk;
+        I.h_df = h_df; I.tttt_df = tttt_df; I.jk_df = jk_df;
         I.n_to = n_to; I.n_co = n_co; I.n_orb = n_orb; I.Pt = Pt;
         return I;
     }

@@ -59,6 +59,55 @@ __device__ __forceinline__ double df_to_double(float hi, float lo) {
     return __longlong_as_double((long long)bits);
 }
 
+// Sum accumulators with one interface: add / subtract table entry i, where a
+// table exists as FP64 and as (hi, lo) float pairs.  AccD sums the FP64 table
+// on the FP64 pipe; AccF sums the float pairs in double-float.
+struct AccD {
+    double v = 0.0;
+    __device__ __forceinline__ void add(const double *t, const float2 *, int64_t i) { v += __ldg(t + i); }
+    __device__ __forceinline__ void sub(const double *t, const float2 *, int64_t i) { v -= __ldg(t + i); }
+    __device__ __forceinline__ void neg() { v = -v; }
+    __device__ __forceinline__ void add_const(double c) { v += c; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+
+struct AccF {
+    float h = 0.0f, l = 0.0f;
+    __device__ __forceinline__ void add(const double *, const float2 *t, int64_t i) {
+        const float2 x = __ldg(t + i);
+        df_add2(h, l, x.x, x.y);
+    }
+    __device__ __forceinline__ void sub(const double *, const float2 *t, int64_t i) {
+        const float2 x = __ldg(t + i);
+        df_add2(h, l, -x.x, -x.y);
+    }
+    __device__ __forceinline__ void neg() { h = -h; l = -l; }
+    __device__ __forceinline__ void add_const(double c) {   // host-side constants only (e_core)
+        const float ch = (float)c;
+        df_add2(h, l, ch, (float)(c - (double)ch));
+    }
+    __device__ __forceinline__ double value() const { return df_to_double(h, l); }
+};
+
+// (hi, lo) += a * b for double-float a, b (products exact by FMA, TwoSum on the
+// high words; the low words collect the rest)
+__device__ __forceinline__ void df_fma(float &hi, float &lo, float ah, float al, float bh, float bl) {
+    const float ph = ah * bh;
+    const float pe = fmaf(ah, bh, -ph);
+    const float pl = fmaf(ah, bl, fmaf(al, bh, pe));
+    float s, e;
+    df_two_sum(hi, ph, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pl));
+}
+
+// renormalise (hi, lo) so that |lo| <= ulp(hi) / 2
+__device__ __forceinline__ void df_norm(float &hi, float &lo) {
+    const float s = __fadd_rn(hi, lo);
+    lo = __fsub_rn(lo, __fsub_rn(s, hi));
+    hi = s;
+}
+
 // FP64 array -> (hi, lo) float pairs, hi = x rounded to float, lo = the rest
 // rounded to float (|x - hi - lo| <= 2^-48 |x| for x in the float range).
 void split_df(const double *x, int64_t n, float2 *out, cudaStream_t s);

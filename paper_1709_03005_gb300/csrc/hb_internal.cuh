@@ -40,6 +40,9 @@ struct Ints {
     const double *tttt;   // [Pt][Pt]
     const double *tttc;   // [Pt][n_to*n_co]
     const double *jk;     // [2][n_to][n_to]: (pp|qq), (pq|qp)
+    // (hi, lo) float-pair copies of h, tttt and jk for the double-float kernels
+    // of the mixed build (null until made)
+    const float2 *h_df, *tttt_df, *jk_df;
     int n_to, n_co, n_orb;
     int64_t Pt;
 };

@@ -13,6 +13,8 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s);
 // Identity of the panel a context reads (equal for contexts sharing integrals).
 const void *mixed_panel_key(const hb_ctx *ctx);
 int mixed_slices(const hb_ctx *ctx);
+// Diagonal panel rows (j, j) as float pairs [n_co][Kpad].
+const float2 *mixed_panel_diag(const hb_ctx *ctx);
 // Coefficient slices [S][Kpad/64][rows][64] bf16 and their tensor map.
 int split_coef_alloc(int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err);
 int64_t blocks_split(int cn, int cnp, int N, int lg);

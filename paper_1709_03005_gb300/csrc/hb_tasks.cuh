@@ -46,18 +46,23 @@ struct PVTask {         // <D_m|H^N|D'_m'> for the records of a group pair
     double *val;
 };
 
+// In the double-float launches of the stages below, val, Wout, Wm and partial
+// hold (hi, lo) float pairs in the bytes of their doubles, and the *_df CI
+// copies are read instead of C / Cp.
 struct SWTask {         // W = V C' row by row
     const hb_pair *pairs;
     const int64_t *row_ptr;
     const double *val;
     int n_rows;
     const double *Cp;
+    const float2 *Cp_df;
     int nsp;
     double *Wout;
 };
 
 struct TNTask {         // out = C^T W by chunked partials (n_rows = 0 gives zeros)
     const double *C, *Wm;
+    const float2 *C_df, *Wm_df;
     int n_rows, ns, nsp, ny;
     double *partial, *out;
 };
@@ -97,8 +102,10 @@ struct GTask {          // gamma[key][n][n'] over the sorted items
     const int64_t *off;
     int nc, n_keys;
     const double *C;
+    const float2 *C_df;
     int ns;
     const double *Cp;
+    const float2 *Cp_df;
     int nsp, ny;
     double *gamma;
 };
@@ -109,6 +116,7 @@ struct ATask {          // contracted coefficient rows A[(n,n')][k]
     int n_nn, ns, nsp, n_to, cont_spin, Kpad;
     double e_core;
     double *A;
+    float2 *A_df;             // optional float-pair copy of A (mixed build)
 };
 
 // One column of a merged expansion block: a state pair (n, n') of one group
@@ -142,8 +150,9 @@ struct SplitTask {      // one merged block on the tensor cores
     int64_t col0;             // first column in the ExpCol table
 };
 
-struct DRTask {         // FP64 rows with j == j' of one group pair
-    const double *P, *A;
+struct DRTask {         // rows with j == j' of one group pair, in double-float
+    const float2 *Pd;         // panel rows (j, j) as float pairs [n_co][Kpad]
+    const float2 *A;          // coefficient rows as float pairs [n_nn][Kpad]
     const int32_t *nn;
     int n_nn, Kpad, n_co, j_lo, j_hi, cf, cn, cfp, cnp, same, ny;
     int64_t row_off, col_off, ld;
@@ -177,19 +186,19 @@ struct L2Task {         // classes 2 and 8: L2-L2 CSR of one Hamiltonian
 // ------------------------------------------------------------ launchers
 // Each returns the number of kernel launches it made (0 for an empty stage).
 int g_classify(const Grouped<ClsTask> &g, int W, int mode, cudaStream_t s);
-int g_pair_values(const Grouped<PVTask> &g, int W, cudaStream_t s);
-int g_l2_csr(const Grouped<L2Task> &g, int W, cudaStream_t s);
-int g_sandwich(const Grouped<SWTask> &g, cudaStream_t s);
-int g_sandwich_small(const Grouped<SWTask> &g, cudaStream_t s);    // nsp <= 32 (used for nsp <= 16)
-int g_tn_partial(const Grouped<TNTask> &g, size_t smem, cudaStream_t s);
-int g_tn_reduce(const Grouped<TNTask> &g, cudaStream_t s);
+int g_pair_values(const Grouped<PVTask> &g, int W, int dfloat, cudaStream_t s);
+int g_l2_csr(const Grouped<L2Task> &g, int W, int dfloat, cudaStream_t s);
+int g_sandwich(const Grouped<SWTask> &g, int dfloat, cudaStream_t s);
+int g_sandwich_small(const Grouped<SWTask> &g, int dfloat, cudaStream_t s);    // nsp <= 32 (used for nsp <= 16)
+int g_tn_partial(const Grouped<TNTask> &g, size_t smem, int dfloat, cudaStream_t s);
+int g_tn_reduce(const Grouped<TNTask> &g, int dfloat, cudaStream_t s);
 int g_item_fill(const Grouped<IFTask> &g, cudaStream_t s);
 int g_zero(const Grouped<ZTask> &g, cudaStream_t s);
 int g_sort_hist(const Grouped<SortTask> &g, cudaStream_t s);
 int g_scan(const Grouped<ScanTask> &g, cudaStream_t s);
 int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s);
-int g_gamma(const Grouped<GTask> &g, size_t smem, cudaStream_t s);
-int g_gamma_warp(const Grouped<GTask> &g, cudaStream_t s);         // ns * nsp <= 64
+int g_gamma(const Grouped<GTask> &g, size_t smem, int dfloat, cudaStream_t s);
+int g_gamma_warp(const Grouped<GTask> &g, int dfloat, cudaStream_t s);         // ns * nsp <= 64
 int g_assemble(const Grouped<ATask> &g, cudaStream_t s);
 int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s);
 // dfloat = 0: FP64 (128 threads, 32 states a pass); 1: double-float with

@@ -195,16 +195,19 @@ void fill_tasks(Plan &p) {
             const GroupInfo &A = ctx->groups[P.g], &B = ctx->groups[P.gp];
             const uint64_t *da = ctx->dets + A.det_off, *db = ctx->dets + B.det_off;
             const double *Ca = ctx->ci + A.ci_off, *Cb = ctx->ci + B.ci_off;
+            const float2 *Ca_df = ctx->ci_df ? ctx->ci_df + A.ci_off : nullptr;
+            const float2 *Cb_df = ctx->ci_df ? ctx->ci_df + B.ci_off : nullptr;
             p.cls_tt.add(ClsTask{da, db, A.ndet, B.ndet, ctx->cont_spin, 2, 0, P.rowptr, P.pairs},
                          blocks_rows8(A.ndet));
             p.pv.add(PVTask{I, da, db, P.pairs, P.n_pairs, P.val}, blocks_pair_values(P.n_pairs));
-            (B.ns <= 16 ? p.sws : p.sw).add(SWTask{P.pairs, P.rowptr, P.val, A.ndet, Cb, B.ns, P.W},
+            (B.ns <= 16 ? p.sws : p.sw).add(SWTask{P.pairs, P.rowptr, P.val, A.ndet, Cb, Cb_df, B.ns, P.W},
                                             blocks_rows8(A.ndet));
             const int ny = tn_ny(A.ns, B.ns);
             // E = C^T (H^N C'); S = C^T C within a group (identical determinants
             // only, hb_init rejects repeats) and zero between groups
-            const TNTask te{Ca, P.W, A.ndet, A.ns, B.ns, ny, P.partial, P.E};
-            const TNTask ts{Ca, Ca, P.same ? A.ndet : 0, A.ns, B.ns, ny, P.partial_s, P.S};
+            const TNTask te{Ca, P.W, Ca_df, reinterpret_cast<const float2 *>(P.W), A.ndet, A.ns, B.ns, ny, P.partial,
+                            P.E};
+            const TNTask ts{Ca, Ca, Ca_df, Ca_df, P.same ? A.ndet : 0, A.ns, B.ns, ny, P.partial_s, P.S};
             p.tn.add(te, blocks_tn_partial(te.n_rows, A.ns, B.ns));
             p.tn.add(ts, blocks_tn_partial(ts.n_rows, A.ns, B.ns));
             p.tnr.add(te, blocks_tn_reduce(A.ns, B.ns));
@@ -217,7 +220,7 @@ void fill_tasks(Plan &p) {
             p.zero.add(ZTask{P.sort_off, n_off + 1}, blocks_zero(n_off + 1));
             p.sort.add(SortTask{P.items, P.n_items, nc, n_keys, P.sort_off, P.sort_cur, P.order}, blocks_sort(P.n_items));
             p.scan.add(ScanTask{P.sort_off, n_off, P.sort_cur}, 1);
-            const GTask gt{P.items, P.order, P.sort_off, nc, n_keys, Ca, A.ns, Cb, B.ns, ny, P.gamma};
+            const GTask gt{P.items, P.order, P.sort_off, nc, n_keys, Ca, Ca_df, A.ns, Cb, Cb_df, B.ns, ny, P.gamma};
             const int nout = A.ns * B.ns;
             bool warp = nout <= 64;
             if (warp) {
@@ -232,7 +235,7 @@ void fill_tasks(Plan &p) {
                 p.smem_gamma = std::max(p.smem_gamma, smem_stage(A.ns, B.ns));
             }
             p.asmb.add(ATask{P.gamma, P.S, P.E, P.nn, P.n_nn, A.ns, B.ns, ctx->n_to, ctx->cont_spin, ctx->Kpad,
-                             ctx->e_core, P.A},
+                             ctx->e_core, P.A, p.precision == HB_MIXED ? P.A_df : nullptr},
                        P.n_nn);
             p.flops += 2.0 * (double)A.cn * B.cn * P.n_nn * ctx->K;
             ++p.n_expand_tasks;
@@ -248,7 +251,7 @@ void fill_tasks(Plan &p) {
             blocks[it->second].members.push_back(Member{ctx, &P, &out});
             if (p.precision == HB_MIXED) {
                 const int j_lo = std::max(A.cf, B.cf), j_hi = std::min(A.cf + A.cn, B.cf + B.cn);
-                p.drows.add(DRTask{ctx->panel, P.A, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, j_lo, j_hi, A.cf, A.cn,
+                p.drows.add(DRTask{mixed_panel_diag(ctx), P.A_df, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, j_lo, j_hi, A.cf, A.cn,
                                    B.cf, B.cn, P.same, diag_rows_ny(P.n_nn), A.row_off, B.row_off, ctx->Dc, out.Hcc},
                             blocks_diag_rows(j_lo, j_hi, P.n_nn));
             }
@@ -455,11 +458,10 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
         p->delta_col = (int)(ctxs[0]->Pt + (int64_t)ctxs[0]->n_to * ctxs[0]->n_to + 1);
     }
     if (precision == HB_MIXED)
-        for (int i = 0; i < n && rc == HB_OK; ++i)
-            if (ctxs[i]->n_groups > 0 && ctxs[i]->n_l2 > 0) {
-                rc = ensure_df(ctxs[i], s);
-                if (rc != HB_OK) *err = ctxs[i]->err;
-            }
+        for (int i = 0; i < n && rc == HB_OK; ++i) {
+            rc = ensure_df(ctxs[i], s);
+            if (rc != HB_OK) *err = ctxs[i]->err;
+        }
     if (rc != HB_OK) { plan_destroy(p); return rc; }
     fill_tasks(*p);
     if (precision == HB_MIXED && p->coef_rows > 0) {
@@ -625,8 +627,9 @@ int plan_autotune(Plan *p, cudaStream_t s, std::string *err) {
                 nbb.push_back(blocks_gamma(t->t.n_keys, t->t.ns, t->t.nsp));
                 smem = std::max(smem, smem_stage(t->t.ns, t->t.nsp));
             }
-            const float mw = time_tasks(ts, nbw, [&](const Grouped<GTask> &g) { g_gamma_warp(g, s); }, s);
-            const float mb = time_tasks(ts, nbb, [&](const Grouped<GTask> &g) { g_gamma(g, smem, s); }, s);
+            const int DF = p->precision == HB_MIXED ? 1 : 0;
+            const float mw = time_tasks(ts, nbw, [&](const Grouped<GTask> &g) { g_gamma_warp(g, DF, s); }, s);
+            const float mb = time_tasks(ts, nbb, [&](const Grouped<GTask> &g) { g_gamma(g, smem, DF, s); }, s);
             ch.gamma_warp[kv.first] = mb < kGain * mw ? 0 : 1;     // the warp form unless clearly slower
         }
     }
@@ -668,6 +671,9 @@ std::string plan_report(const Plan *p) {
 int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, std::string *err) {
     int L = 0, LX = 0;
     const int W = p->W;
+    // the mixed build runs the target side and class 4 in double-float on the
+    // FP32 pipes, the plain build in FP64
+    const int DF = p->precision == HB_MIXED ? 1 : 0;
     p->timed = timing;
     // inside a capture an event record becomes a graph node only when external
     auto rec = [&](cudaEvent_t e) {
@@ -678,18 +684,18 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     rec(p->ev[0]);
     // target side (Eq. 8): classes, H^N, S, E, gamma, coefficient rows
     L += g_classify(p->cls_tt.g, W, 0, s);
-    L += g_pair_values(p->pv.g, W, s);
-    L += g_sandwich(p->sw.g, s);
-    L += g_sandwich_small(p->sws.g, s);
-    L += g_tn_partial(p->tn.g, p->smem_tn, s);
-    L += g_tn_reduce(p->tnr.g, s);
+    L += g_pair_values(p->pv.g, W, DF, s);
+    L += g_sandwich(p->sw.g, DF, s);
+    L += g_sandwich_small(p->sws.g, DF, s);
+    L += g_tn_partial(p->tn.g, p->smem_tn, DF, s);
+    L += g_tn_reduce(p->tnr.g, DF, s);
     L += g_item_fill(p->itf.g, s);
     L += g_zero(p->zero.g, s);
     L += g_sort_hist(p->sort.g, s);
     L += g_scan(p->scan.g, s);
     L += g_sort_scatter(p->sort.g, s);
-    L += g_gamma(p->gam.g, p->smem_gamma, s);
-    L += g_gamma_warp(p->gamw.g, s);
+    L += g_gamma(p->gam.g, p->smem_gamma, DF, s);
+    L += g_gamma_warp(p->gamw.g, DF, s);
     L += g_assemble(p->asmb.g, s);
     rec(p->ev[1]);
     // expansion (Eq. 7): classes 1, 3, 5, 6, 7
@@ -714,7 +720,9 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     for (auto &v : p->c4v) L += g_class4(v.st.g, W, p->precision == HB_MIXED ? 1 : 0, v.ns_tile, v.jt, s);
     rec(p->ev[3]);
     // classes 2 and 8
-    L += g_l2_csr(p->l2.g, W, s);
+    // the L2 rows stay FP64: their sums are short and the kernel is bound by the
+    // pair scan, where the longer double-float sums cost more than FP64 adds
+    L += g_l2_csr(p->l2.g, W, 0, s);
     rec(p->ev[4]);
     cudaError_t e = cudaGetLastError();
     p->launches = L;

@@ -8,6 +8,7 @@
 // (the standard rules for an orthonormal spin-orbital basis; the paper
 // evaluates them symbolically, Eq. 6).  (pp|qq) and (pq|qp) come from a small
 // n_to x n_to table that stays in L1/L2; other (tt|tt) integrals are gathered.
+#include "hb_df.cuh"
 #include "hb_tasks.cuh"
 
 namespace hb {
@@ -18,11 +19,17 @@ __device__ __forceinline__ double eri4(const Ints &I, int p, int q, int r, int s
     return __ldg(I.tttt + pair_idx(p, q) * I.Pt + pair_idx(r, s));
 }
 
-template <int W>
-__device__ double diag_value(const Ints &I, const uint64_t (&d)[2 * W]) {
-    const double *J = I.jk, *K = I.jk + I.n_to * I.n_to;
+__device__ __forceinline__ int64_t eri_idx(const Ints &I, int p, int q, int r, int s) {
+    return pair_idx(p, q) * I.Pt + pair_idx(r, s);
+}
+
+// Sums below run through an accumulator: AccD (FP64) or AccF (double-float
+// over the float-pair tables), the same terms in the same order.
+template <int W, class Acc>
+__device__ Acc diag_value(const Ints &I, const uint64_t (&d)[2 * W]) {
     const int n = I.n_to, no = I.n_orb;
-    double e = 0.0;
+    const int64_t nn = (int64_t)n * n;
+    Acc e;
     // one-electron and same-spin / opposite-spin pair sums
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -32,7 +39,7 @@ __device__ double diag_value(const Ints &I, const uint64_t (&d)[2 * W]) {
             while (x) {
                 const int p = 64 * w + __ffsll((long long)x) - 1;
                 x &= x - 1;
-                e += __ldg(I.h + (int64_t)p * no + p);
+                e.add(I.h, I.h_df, (int64_t)p * no + p);
                 // pairs (p, q) with q after p in canonical order
 #pragma unroll
                 for (int s2 = 0; s2 < 2; ++s2) {
@@ -47,8 +54,8 @@ __device__ double diag_value(const Ints &I, const uint64_t (&d)[2 * W]) {
                         while (y) {
                             const int q = 64 * w2 + __ffsll((long long)y) - 1;
                             y &= y - 1;
-                            e += __ldg(J + p * n + q);
-                            if (s2 == s) e -= __ldg(K + p * n + q);
+                            e.add(I.jk, I.jk_df, (int64_t)p * n + q);
+                            if (s2 == s) e.sub(I.jk, I.jk_df, nn + (int64_t)p * n + q);
                         }
                     }
                 }
@@ -58,12 +65,13 @@ __device__ double diag_value(const Ints &I, const uint64_t (&d)[2 * W]) {
     return e;
 }
 
-template <int W>
-__device__ double single_value(const Ints &I, const uint64_t (&bra)[2 * W], const uint64_t (&ket)[2 * W],
-                               int hpos, int ppos) {
+template <int W, class Acc>
+__device__ Acc single_value(const Ints &I, const uint64_t (&bra)[2 * W], const uint64_t (&ket)[2 * W], int hpos,
+                            int ppos) {
     const int sb = 64 * W;
     const int hs = hpos / sb, h = hpos % sb, p = ppos % sb;
-    double v = __ldg(I.h + (int64_t)p * I.n_orb + h);
+    Acc v;
+    v.add(I.h, I.h_df, (int64_t)p * I.n_orb + h);
     const int64_t ph = pair_idx(p, h) * I.Pt;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -73,19 +81,20 @@ __device__ double single_value(const Ints &I, const uint64_t (&bra)[2 * W], cons
             while (x) {
                 const int k = 64 * w + __ffsll((long long)x) - 1;
                 x &= x - 1;
-                v += __ldg(I.tttt + ph + pair_idx(k, k));
-                if (s == hs) v -= eri4(I, p, k, k, h);
+                v.add(I.tttt, I.tttt_df, ph + pair_idx(k, k));
+                if (s == hs) v.sub(I.tttt, I.tttt_df, eri_idx(I, p, k, k, h));
             }
         }
     }
     return v;
 }
 
-__device__ __forceinline__ double double_value(const Ints &I, int W, int h1, int h2, int p1, int p2) {
+template <class Acc>
+__device__ __forceinline__ Acc double_value(const Ints &I, int W, int h1, int h2, int p1, int p2) {
     const int sb = 64 * W;
-    double v = 0.0;
-    if (p1 / sb == h1 / sb && p2 / sb == h2 / sb) v += eri4(I, p1 % sb, h1 % sb, p2 % sb, h2 % sb);
-    if (p1 / sb == h2 / sb && p2 / sb == h1 / sb) v -= eri4(I, p1 % sb, h2 % sb, p2 % sb, h1 % sb);
+    Acc v;
+    if (p1 / sb == h1 / sb && p2 / sb == h2 / sb) v.add(I.tttt, I.tttt_df, eri_idx(I, p1 % sb, h1 % sb, p2 % sb, h2 % sb));
+    if (p1 / sb == h2 / sb && p2 / sb == h1 / sb) v.sub(I.tttt, I.tttt_df, eri_idx(I, p1 % sb, h2 % sb, p2 % sb, h1 % sb));
     return v;
 }
 
@@ -110,26 +119,33 @@ __device__ __forceinline__ int diff_bits(const uint64_t (&x)[2 * W], const uint6
 }
 
 // Full element <bra|H|ket> (same electron count), classification inline.
-template <int W>
-__device__ double element(const Ints &I, const uint64_t (&a)[2 * W], const uint64_t (&b)[2 * W], int deg) {
-    if (deg == 0) return diag_value<W>(I, a);
+template <int W, class Acc>
+__device__ Acc element(const Ints &I, const uint64_t (&a)[2 * W], const uint64_t (&b)[2 * W], int deg) {
+    if (deg == 0) return diag_value<W, Acc>(I, a);
     int h[2], p[2];
     diff_bits<W>(b, a, h);
     diff_bits<W>(a, b, p);
     if (deg == 1) {
         const int e = prefix_count(b, 2 * W, h[0]) + prefix_count(b, 2 * W, p[0]) - (h[0] < p[0]);
-        const double v = single_value<W>(I, a, b, h[0], p[0]);
-        return (e & 1) ? -v : v;
+        Acc v = single_value<W, Acc>(I, a, b, h[0], p[0]);
+        if (e & 1) v.neg();
+        return v;
     }
     const int e = prefix_count(b, 2 * W, h[0]) + prefix_count(b, 2 * W, h[1]) - 1 + prefix_count(b, 2 * W, p[1]) -
                   (h[0] < p[1]) - (h[1] < p[1]) + prefix_count(b, 2 * W, p[0]) - (h[0] < p[0]) - (h[1] < p[0]);
-    const double v = double_value(I, W, h[0], h[1], p[0], p[1]);
-    return (e & 1) ? -v : v;
+    Acc v = double_value<Acc>(I, W, h[0], h[1], p[0], p[1]);
+    if (e & 1) v.neg();
+    return v;
+}
+
+__device__ __forceinline__ void store_value(const AccD &v, double *out, int64_t k) { out[k] = v.v; }
+__device__ __forceinline__ void store_value(const AccF &v, double *out, int64_t k) {
+    reinterpret_cast<float2 *>(out)[k] = make_float2(v.h, v.l);
 }
 
 constexpr int kWarps = 8;
 
-template <int W>
+template <int W, class Acc>
 __global__ void __launch_bounds__(32 * kWarps)
 l2_csr_kernel(const L2Task *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     const int ti = task_of(blk, n_tasks, blockIdx.x);
@@ -164,18 +180,19 @@ l2_csr_kernel(const L2Task *__restrict__ tasks, const int64_t *__restrict__ blk,
         if (ok) {
             const int64_t at = pos + __popc(m & ((1u << lane) - 1u));
             if (at < end) {
-                double v = element<W>(I, a, b, deg);
-                if (deg == 0) v += T.e_core;
+                Acc v = element<W, Acc>(I, a, b, deg);
+                if (deg == 0) v.add_const(T.e_core);
                 T.col[at] = c;
-                T.val[at] = v;
+                T.val[at] = v.value();
             }
         }
         pos += __popc(m);
     }
 }
 
-// <A[row]|H|B[col]> for classified pairs (mode 0 records).
-template <int W>
+// <A[row]|H|B[col]> for classified pairs (mode 0 records).  FP64: val as
+// doubles; double-float: val as (hi, lo) float pairs in the same 8 bytes.
+template <int W, class Acc>
 __global__ void pair_values_kernel(const PVTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const PVTask &T = tasks[ti];
@@ -186,11 +203,12 @@ __global__ void pair_values_kernel(const PVTask *__restrict__ tasks, const int64
     uint64_t a[2 * W], b[2 * W];
     load_det<W>(T.a + (int64_t)r.row * 2 * W, a);
     load_det<W>(T.b + (int64_t)r.col * 2 * W, b);
-    double v;
-    if (r.degree == 0) v = diag_value<W>(I, a);
-    else if (r.degree == 1) v = r.phase * single_value<W>(I, a, b, r.hole[0], r.part[0]);
-    else v = r.phase * double_value(I, W, r.hole[0], r.hole[1], r.part[0], r.part[1]);
-    T.val[k] = v;
+    Acc v;
+    if (r.degree == 0) v = diag_value<W, Acc>(I, a);
+    else if (r.degree == 1) v = single_value<W, Acc>(I, a, b, r.hole[0], r.part[0]);
+    else v = double_value<Acc>(I, W, r.hole[0], r.hole[1], r.part[0], r.part[1]);
+    if (r.degree > 0 && r.phase < 0) v.neg();
+    store_value(v, T.val, k);
 }
 
 __global__ void jk_kernel(Ints I, double *jk) {
@@ -211,26 +229,33 @@ void build_jk(const Ints &I, double *jk, cudaStream_t s) {
 
 int64_t blocks_pair_values(int64_t n_pairs) { return (n_pairs + 255) / 256; }
 
-int g_l2_csr(const Grouped<L2Task> &g, int W, cudaStream_t s) {
+int g_l2_csr(const Grouped<L2Task> &g, int W, int dfloat, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
     const dim3 grid((unsigned)g.blocks), block(32 * kWarps);
+#define HB_L2(WW) (dfloat ? l2_csr_kernel<WW, AccF><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n) \
+                          : l2_csr_kernel<WW, AccD><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n))
     switch (W) {
-        case 1: l2_csr_kernel<1><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n); break;
-        case 2: l2_csr_kernel<2><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n); break;
-        case 3: l2_csr_kernel<3><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n); break;
-        default: l2_csr_kernel<4><<<grid, block, 0, s>>>(g.tasks, g.blk, g.n); break;
+        case 1: HB_L2(1); break;
+        case 2: HB_L2(2); break;
+        case 3: HB_L2(3); break;
+        default: HB_L2(4); break;
     }
+#undef HB_L2
     return 1;
 }
 
-int g_pair_values(const Grouped<PVTask> &g, int W, cudaStream_t s) {
+int g_pair_values(const Grouped<PVTask> &g, int W, int dfloat, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
+    const unsigned grid = (unsigned)g.blocks;
+#define HB_PV(WW) (dfloat ? pair_values_kernel<WW, AccF><<<grid, 256, 0, s>>>(g.tasks, g.blk, g.n) \
+                          : pair_values_kernel<WW, AccD><<<grid, 256, 0, s>>>(g.tasks, g.blk, g.n))
     switch (W) {
-        case 1: pair_values_kernel<1><<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n); break;
-        case 2: pair_values_kernel<2><<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n); break;
-        case 3: pair_values_kernel<3><<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n); break;
-        default: pair_values_kernel<4><<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n); break;
+        case 1: HB_PV(1); break;
+        case 2: HB_PV(2); break;
+        case 3: HB_PV(3); break;
+        default: HB_PV(4); break;
     }
+#undef HB_PV
     return 1;
 }
 

@@ -51,6 +51,7 @@ struct MixedState {
     bool panel_ready = false;
     bool borrowed_panel = false;
     CUtensorMap tm_panel[3];                  // boxes of 8 x 16, 16 x 8, 32 x 4 continuum pairs (j' x j)
+    float2 *pdiag = nullptr;                  // diagonal panel rows (j, j) as float pairs [n_co][Kpad]
 };
 
 }  // namespace hb
@@ -485,10 +486,11 @@ __global__ void slice_rows_grouped(const SliceTask *__restrict__ tasks, const in
     slice_row(T.X + row * Kpad, T.row0 + row, R, Kpad, S, skip_col, out, threadIdx.x & 31);
 }
 
-// FP64 rows with j == j' (both ranges): H[(n,j),(n',j)] over all K, incl. delta.
-// Per task one block per (j, 8 state pairs); the lanes of a warp split K.
-__global__ void diag_rows_fp64_kernel(const DRTask *__restrict__ tasks, const int64_t *__restrict__ blk,
-                                      int n_tasks) {
+// Rows with j == j' (both ranges): H[(n,j),(n',j)] over all K, incl. delta,
+// in double-float (they carry h_jj and the delta_jj' E term and so have a
+// wide dynamic range that the bf16 slices of one row do not cover).  Per task
+// one block per (j, 8 state pairs); the lanes of a warp split K.
+__global__ void diag_rows_kernel(const DRTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const DRTask &T = tasks[ti];
     const int lb = (int)(blockIdx.x - blk[ti]);
@@ -497,19 +499,36 @@ __global__ void diag_rows_fp64_kernel(const DRTask *__restrict__ tasks, const in
     const int t = (lb % T.ny) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= T.j_hi || t >= T.n_nn) return;
     const int Kpad = T.Kpad;
-    const double *prow = T.P + ((int64_t)j * T.n_co + j) * Kpad;
-    const double *arow = T.A + (int64_t)t * Kpad;
-    double acc = 0.0;
-    for (int k = lane; k < Kpad; k += 32) acc = fma(prow[k], arow[k], acc);
+    const float2 *prow = T.Pd + (int64_t)j * Kpad;
+    const float2 *arow = T.A + (int64_t)t * Kpad;
+    float h = 0.0f, l = 0.0f;
+    for (int k = lane; k < Kpad; k += 32) {
+        const float2 x = __ldg(prow + k), y = __ldg(arow + k);
+        df_fma(h, l, x.x, x.y, y.x, y.y);
+    }
 #pragma unroll
-    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    for (int off = 16; off; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, off), ol = __shfl_xor_sync(0xffffffffu, l, off);
+        df_add2(h, l, oh, ol);
+    }
     if (lane) return;
     const int na = T.nn[2 * t], nb = T.nn[2 * t + 1];
     const int64_t r = T.row_off + (int64_t)na * T.cn + (j - T.cf);
     const int64_t c = T.col_off + (int64_t)nb * T.cnp + (j - T.cfp);
     if (T.same && r < c) return;
-    T.H[r * T.ld + c] = acc;
-    if (r != c) T.H[c * T.ld + r] = acc;
+    const double v = df_to_double(h, l);
+    T.H[r * T.ld + c] = v;
+    if (r != c) T.H[c * T.ld + r] = v;
+}
+
+// Diagonal panel rows P[(j, j)][k] as float pairs.
+__global__ void panel_diag_df_kernel(const double *__restrict__ P, int n_co, int Kpad, float2 *__restrict__ out) {
+    const int j = blockIdx.x;
+    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
+        const double v = P[((int64_t)j * n_co + j) * Kpad + k];
+        const float h = (float)v;
+        out[(int64_t)j * Kpad + k] = make_float2(h, (float)(v - (double)h));
+    }
 }
 
 // ------------------------------------------------------ tensor maps (host)
@@ -563,6 +582,7 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
         M.panel_rows = B.panel_rows;
         M.panel_slices = B.panel_slices;
         for (int i = 0; i < 3; ++i) M.tm_panel[i] = B.tm_panel[i];
+        M.pdiag = B.pdiag;
         M.borrowed_panel = true;
         M.panel_ready = true;
         return HB_OK;
@@ -575,6 +595,10 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
     cudaError_t e = cudaMalloc(&M.panel_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * rows * ctx->Kpad);
     if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("panel slices: ") + cudaGetErrorString(e));
     ctx->dev_bytes += sizeof(__nv_bfloat16) * (size_t)M.slices * rows * ctx->Kpad;
+    e = cudaMalloc(&M.pdiag, sizeof(float2) * (size_t)ctx->n_co * ctx->Kpad);
+    if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("panel rows: ") + cudaGetErrorString(e));
+    ctx->dev_bytes += sizeof(float2) * (size_t)ctx->n_co * ctx->Kpad;
+    panel_diag_df_kernel<<<ctx->n_co, 256, 0, s>>>(ctx->panel, ctx->n_co, ctx->Kpad, M.pdiag);
     const int delta_col = (int)(ctx->Pt + (int64_t)ctx->n_to * ctx->n_to + 1);
     slice_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(ctx->panel, rows, ctx->Kpad, M.slices, delta_col,
                                                                  M.panel_slices);
@@ -600,6 +624,7 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
 }
 
 const void *mixed_panel_key(const hb_ctx *ctx) { return ctx->mixed ? ctx->mixed->panel_slices : nullptr; }
+const float2 *mixed_panel_diag(const hb_ctx *ctx) { return ctx->mixed ? ctx->mixed->pdiag : nullptr; }
 int mixed_slices(const hb_ctx *ctx) { return ctx->mixed ? ctx->mixed->slices : ctx->split_slices; }
 
 // Coefficient slices of `rows` rows in all: [S][Kpad/64][rows][64] bf16 and
@@ -679,13 +704,16 @@ int diag_rows_ny(int n_nn) { return (n_nn + 7) / 8; }
 
 int g_diag_rows(const Grouped<DRTask> &g, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
-    diag_rows_fp64_kernel<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n);
+    diag_rows_kernel<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n);
     return 1;
 }
 
 void release_mixed(hb_ctx *ctx) {
     if (!ctx->mixed) return;
-    if (!ctx->mixed->borrowed_panel) cudaFree(ctx->mixed->panel_slices);
+    if (!ctx->mixed->borrowed_panel) {
+        cudaFree(ctx->mixed->panel_slices);
+        cudaFree(ctx->mixed->pdiag);
+    }
     delete ctx->mixed;
     ctx->mixed = nullptr;
 }

@@ -11,6 +11,7 @@
 // stable counting sort so that every sum runs in a fixed order (no floating
 // point atomics anywhere).  Every stage is a grouped launch over the group
 // pairs of one or many Hamiltonians (one task per group pair).
+#include "hb_df.cuh"
 #include "hb_tasks.cuh"
 
 namespace hb {
@@ -423,7 +424,232 @@ __global__ void assemble_kernel(const ATask *__restrict__ tasks, const int64_t *
             v = T.E[sidx] + T.e_core * T.S[sidx];
         }
         T.A[(int64_t)t * Kpad + k] = v;
+        if (T.A_df) {
+            const float h = (float)v;
+            T.A_df[(int64_t)t * Kpad + k] = make_float2(h, (float)(v - (double)h));
+        }
     }
+}
+
+// ------------------------------------------------ double-float variants
+// The same sums on the FP32 pipes for the mixed build: every value is a
+// (hi, lo) float pair, products exact by FMA, TwoSum on the high words
+// (hb_df.cuh); the order of the terms is the FP64 kernels' order.
+__device__ __forceinline__ void shfl_df_add(float &h, float &l, int off) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, off), ol = __shfl_xor_sync(0xffffffffu, l, off);
+    df_add2(h, l, oh, ol);
+}
+
+__global__ void sandwich_df_kernel(const SWTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const SWTask T = tasks[ti];
+    const int lane = threadIdx.x & 31;
+    const int row = (int)(blockIdx.x - blk[ti]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= T.n_rows) return;
+    const int nsp = T.nsp;
+    const float2 *val = reinterpret_cast<const float2 *>(T.val);
+    float2 *Wout = reinterpret_cast<float2 *>(T.Wout);
+    const int64_t b = T.row_ptr[row], e = T.row_ptr[row + 1];
+    for (int n0 = 0; n0 < nsp; n0 += 16) {
+        float ah[16], al[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) { ah[c] = 0.0f; al[c] = 0.0f; }
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int col = T.pairs[k].col;
+            const float2 v = val[k];
+            const float2 *crow = T.Cp_df + (int64_t)col * nsp + n0;
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (n0 + c < nsp) {
+                    const float2 x = __ldg(crow + c);
+                    df_fma(ah[c], al[c], v.x, v.y, x.x, x.y);
+                }
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+#pragma unroll
+            for (int off = 16; off; off >>= 1) shfl_df_add(ah[c], al[c], off);
+        }
+        if (lane < 16 && n0 + lane < nsp) {
+            float mh = 0.0f, ml = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c == lane) { mh = ah[c]; ml = al[c]; }
+            Wout[(int64_t)row * nsp + n0 + lane] = make_float2(mh, ml);
+        }
+    }
+}
+
+__global__ void sandwich_small_df_kernel(const SWTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                         int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const SWTask T = tasks[ti];
+    const int lane = threadIdx.x & 31;
+    const int row = (int)(blockIdx.x - blk[ti]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= T.n_rows) return;
+    const int nsp = T.nsp;
+    const float2 *val = reinterpret_cast<const float2 *>(T.val);
+    float2 *Wout = reinterpret_cast<float2 *>(T.Wout);
+    int P = 1;
+    while (P < nsp) P <<= 1;
+    const int G = 32 / P, g = lane / P, c = lane % P;
+    const int64_t b = T.row_ptr[row], e = T.row_ptr[row + 1];
+    float ah = 0.0f, al = 0.0f;
+    if (c < nsp)
+        for (int64_t k = b + g; k < e; k += G) {
+            const float2 v = val[k];
+            const float2 x = __ldg(T.Cp_df + (int64_t)T.pairs[k].col * nsp + c);
+            df_fma(ah, al, v.x, v.y, x.x, x.y);
+        }
+    for (int off = 16; off >= P; off >>= 1) shfl_df_add(ah, al, off);
+    if (g == 0 && c < nsp) Wout[(int64_t)row * nsp + c] = make_float2(ah, al);
+}
+
+__global__ void tn_partial_df_kernel(const TNTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                     int n_tasks) {
+    extern __shared__ float2 shf[];
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const TNTask T = tasks[ti];
+    const int lb = (int)(blockIdx.x - blk[ti]);
+    const int c = lb / T.ny, by = lb % T.ny;
+    const int ns = T.ns, nsp = T.nsp;
+    const int kRowBatch = stage_batch(ns, nsp);
+    float2 *cs = shf;                     // [kRowBatch][ns]
+    float2 *ws = shf + kRowBatch * ns;    // [kRowBatch][nsp]
+    const int m0 = c * kRowsPerChunk;
+    const int rows = min(kRowsPerChunk, T.n_rows - m0);
+    const int nout = ns * nsp;
+    float ah[4] = {0.0f, 0.0f, 0.0f, 0.0f}, al[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int r0 = 0; r0 < rows; r0 += kRowBatch) {
+        const int nr = min(kRowBatch, rows - r0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nr * ns; i += blockDim.x) cs[i] = T.C_df[(int64_t)(m0 + r0) * ns + i];
+        for (int i = threadIdx.x; i < nr * nsp; i += blockDim.x) ws[i] = T.Wm_df[(int64_t)(m0 + r0) * nsp + i];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
+            if (t < nout) {
+                const int a = t / nsp, b = t % nsp;
+                for (int m = 0; m < nr; ++m) {
+                    const float2 x = cs[m * ns + a], y = ws[m * nsp + b];
+                    df_fma(ah[u], al[u], x.x, x.y, y.x, y.y);
+                }
+            }
+        }
+    }
+    float2 *partial = reinterpret_cast<float2 *>(T.partial);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
+        if (t < nout) partial[(int64_t)c * nout + t] = make_float2(ah[u], al[u]);
+    }
+}
+
+__global__ void reduce_partials_df_kernel(const TNTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                          int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const TNTask T = tasks[ti];
+    const int t = (int)(blockIdx.x - blk[ti]) * blockDim.x + threadIdx.x;
+    const int n_out = T.ns * T.nsp;
+    if (t >= n_out) return;
+    const int n_chunks = (T.n_rows + kRowsPerChunk - 1) / kRowsPerChunk;
+    const float2 *partial = reinterpret_cast<const float2 *>(T.partial);
+    float h = 0.0f, l = 0.0f;
+    for (int c = 0; c < n_chunks; ++c) {
+        const float2 x = partial[(int64_t)c * n_out + t];
+        df_add2(h, l, x.x, x.y);
+    }
+    T.out[t] = df_to_double(h, l);
+}
+
+__global__ void gamma_df_kernel(const GTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    extern __shared__ float2 smf[];
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const GTask T = tasks[ti];
+    const int lb = (int)(blockIdx.x - blk[ti]);
+    const int key = lb / T.ny, by = lb % T.ny;
+    const int ns = T.ns, nsp = T.nsp;
+    const int kItemBatch = stage_batch(ns, nsp);
+    float2 *ca = smf;                         // [kItemBatch][ns]
+    float2 *cb = smf + kItemBatch * ns;       // [kItemBatch][nsp]
+    const int64_t b = T.off[(int64_t)key * T.nc];
+    const int64_t e = T.off[(int64_t)(key + 1) * T.nc];
+    const int nout = ns * nsp;
+    float ah[4] = {0.0f, 0.0f, 0.0f, 0.0f}, al[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int64_t i0 = b; i0 < e; i0 += kItemBatch) {
+        const int cnt = (int)(e - i0 < kItemBatch ? e - i0 : kItemBatch);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt * ns; t += blockDim.x) {
+            const int i = t / ns, a = t % ns;
+            const GammaItem it = T.items[T.order[i0 + i]];
+            float2 x = T.C_df[(int64_t)it.m * ns + a];
+            if (it.phase < 0) { x.x = -x.x; x.y = -x.y; }
+            ca[i * ns + a] = x;
+        }
+        for (int t = threadIdx.x; t < cnt * nsp; t += blockDim.x) {
+            const int i = t / nsp, a = t % nsp;
+            const GammaItem it = T.items[T.order[i0 + i]];
+            cb[i * nsp + a] = T.Cp_df[(int64_t)it.mp * nsp + a];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
+            if (t < nout) {
+                const int a = t / nsp, c = t % nsp;
+                for (int i = 0; i < cnt; ++i) {
+                    const float2 x = ca[i * ns + a], y = cb[i * nsp + c];
+                    df_fma(ah[u], al[u], x.x, x.y, y.x, y.y);
+                }
+            }
+        }
+        // keep the low words small over long keys
+#pragma unroll
+        for (int u = 0; u < 4; ++u) df_norm(ah[u], al[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
+        if (t < nout) T.gamma[(int64_t)key * nout + t] = df_to_double(ah[u], al[u]);
+    }
+}
+
+__global__ void gamma_warp_df_kernel(const GTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                     int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const GTask T = tasks[ti];
+    const int lane = threadIdx.x & 31;
+    const int key = (int)(blockIdx.x - blk[ti]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (key >= T.n_keys) return;
+    const int ns = T.ns, nsp = T.nsp, nout = ns * nsp;
+    const int64_t b = T.off[(int64_t)key * T.nc];
+    const int64_t e = T.off[(int64_t)(key + 1) * T.nc];
+    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+    const int t0 = lane, t1 = lane + 32;
+    const int a0 = t0 / nsp, c0 = t0 % nsp, a1 = t1 / nsp, c1 = t1 % nsp;
+    // renormalise at the block kernel's batch ends, so both forms give the same bits
+    const int kb = stage_batch(ns, nsp);
+    int since = 0;
+    for (int64_t i = b; i < e; ++i) {
+        const GammaItem it = T.items[T.order[i]];
+        const float sg = it.phase < 0 ? -1.0f : 1.0f;
+        if (t0 < nout) {
+            const float2 x = __ldg(T.C_df + (int64_t)it.m * ns + a0), y = __ldg(T.Cp_df + (int64_t)it.mp * nsp + c0);
+            df_fma(h0, l0, sg * x.x, sg * x.y, y.x, y.y);
+        }
+        if (t1 < nout) {
+            const float2 x = __ldg(T.C_df + (int64_t)it.m * ns + a1), y = __ldg(T.Cp_df + (int64_t)it.mp * nsp + c1);
+            df_fma(h1, l1, sg * x.x, sg * x.y, y.x, y.y);
+        }
+        if (++since == kb || i + 1 == e) {
+            since = 0;
+            df_norm(h0, l0);
+            df_norm(h1, l1);
+        }
+    }
+    if (t0 < nout) T.gamma[(int64_t)key * nout + t0] = df_to_double(h0, l0);
+    if (t1 < nout) T.gamma[(int64_t)key * nout + t1] = df_to_double(h1, l1);
 }
 
 }  // namespace
@@ -453,18 +679,34 @@ void gamma_item_counts(const hb_pair *pairs, const int64_t *row_ptr, int n_rows,
         return 1;                                                                                   \
     } while (0)
 
-int g_sandwich(const Grouped<SWTask> &g, cudaStream_t s) { HB_GROUPED(sandwich_kernel, g, 256, 0, s); }
-int g_sandwich_small(const Grouped<SWTask> &g, cudaStream_t s) { HB_GROUPED(sandwich_small_kernel, g, 256, 0, s); }
-int g_tn_partial(const Grouped<TNTask> &g, size_t smem, cudaStream_t s) {
+int g_sandwich(const Grouped<SWTask> &g, int dfloat, cudaStream_t s) {
+    if (dfloat) HB_GROUPED(sandwich_df_kernel, g, 256, 0, s);
+    HB_GROUPED(sandwich_kernel, g, 256, 0, s);
+}
+int g_sandwich_small(const Grouped<SWTask> &g, int dfloat, cudaStream_t s) {
+    if (dfloat) HB_GROUPED(sandwich_small_df_kernel, g, 256, 0, s);
+    HB_GROUPED(sandwich_small_kernel, g, 256, 0, s);
+}
+int g_tn_partial(const Grouped<TNTask> &g, size_t smem, int dfloat, cudaStream_t s) {
+    if (dfloat) HB_GROUPED(tn_partial_df_kernel, g, 256, smem, s);
     HB_GROUPED(tn_partial_kernel, g, 256, smem, s);
 }
-int g_tn_reduce(const Grouped<TNTask> &g, cudaStream_t s) { HB_GROUPED(reduce_partials_kernel, g, 256, 0, s); }
+int g_tn_reduce(const Grouped<TNTask> &g, int dfloat, cudaStream_t s) {
+    if (dfloat) HB_GROUPED(reduce_partials_df_kernel, g, 256, 0, s);
+    HB_GROUPED(reduce_partials_kernel, g, 256, 0, s);
+}
 int g_item_fill(const Grouped<IFTask> &g, cudaStream_t s) { HB_GROUPED(item_fill_kernel, g, 256, 0, s); }
 int g_zero(const Grouped<ZTask> &g, cudaStream_t s) { HB_GROUPED(zero_kernel, g, 256, 0, s); }
 int g_sort_hist(const Grouped<SortTask> &g, cudaStream_t s) { HB_GROUPED(sort_hist_kernel, g, 256, 0, s); }
 int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s) { HB_GROUPED(sort_scatter_kernel, g, 32, 0, s); }
-int g_gamma(const Grouped<GTask> &g, size_t smem, cudaStream_t s) { HB_GROUPED(gamma_kernel, g, 256, smem, s); }
-int g_gamma_warp(const Grouped<GTask> &g, cudaStream_t s) { HB_GROUPED(gamma_warp_kernel, g, 256, 0, s); }
+int g_gamma(const Grouped<GTask> &g, size_t smem, int dfloat, cudaStream_t s) {
+    if (dfloat) HB_GROUPED(gamma_df_kernel, g, 256, smem, s);
+    HB_GROUPED(gamma_kernel, g, 256, smem, s);
+}
+int g_gamma_warp(const Grouped<GTask> &g, int dfloat, cudaStream_t s) {
+    if (dfloat) HB_GROUPED(gamma_warp_df_kernel, g, 256, 0, s);
+    HB_GROUPED(gamma_warp_kernel, g, 256, 0, s);
+}
 int g_assemble(const Grouped<ATask> &g, cudaStream_t s) { HB_GROUPED(assemble_kernel, g, 256, 0, s); }
 
 int g_scan(const Grouped<ScanTask> &g, cudaStream_t s) {
