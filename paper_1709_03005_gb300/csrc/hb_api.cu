@@ -304,6 +304,8 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         CK(cudaMemsetAsync(P.rowptr, 0, sizeof(int64_t), s));
         k1_count(ctx->dets + A.det_off, A.ndet, ctx->dets + B.det_off, B.ndet, W, 0, 2, 0, P.rowptr, s);
         exclusive_scan_inplace(P.rowptr, A.ndet, s);
+        DALLOC(P.seg_off, (int64_t)A.ndet * seg_count(B.ndet));
+        k1_seg_offsets(ctx->dets + A.det_off, A.ndet, ctx->dets + B.det_off, B.ndet, W, 0, 2, 0, P.seg_off, s);
     }
     for (int g = 0; g < p->n_groups; ++g) {
         GroupL2 L;
@@ -311,12 +313,17 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         CK(cudaMemsetAsync(L.rowptr, 0, sizeof(int64_t), s));
         k1_count(ctx->l2, p->n_l2, ctx->dets + ctx->groups[g].det_off, ctx->groups[g].ndet, W, 1, 2, 0, L.rowptr, s);
         exclusive_scan_inplace(L.rowptr, p->n_l2, s);
+        DALLOC(L.seg_off, (int64_t)std::max(p->n_l2, 1) * seg_count(ctx->groups[g].ndet));
+        k1_seg_offsets(ctx->l2, p->n_l2, ctx->dets + ctx->groups[g].det_off, ctx->groups[g].ndet, W, 1, 2, 0,
+                       L.seg_off, s);
         ctx->gl2.push_back(L);
     }
     DALLOC(ctx->l2_rowptr, p->n_l2 + 1);
     CK(cudaMemsetAsync(ctx->l2_rowptr, 0, sizeof(int64_t), s));
     k1_count(ctx->l2, p->n_l2, ctx->l2, p->n_l2, W, 0, 2, 0, ctx->l2_rowptr, s);
     exclusive_scan_inplace(ctx->l2_rowptr, p->n_l2, s);
+    DALLOC(ctx->l2_seg_off, (int64_t)std::max(p->n_l2, 1) * seg_count(p->n_l2));
+    k1_seg_offsets(ctx->l2, p->n_l2, ctx->l2, p->n_l2, W, 0, 2, 0, ctx->l2_seg_off, s);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     ctx->tt_pairs = 0;

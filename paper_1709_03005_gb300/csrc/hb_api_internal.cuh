@@ -19,6 +19,7 @@ struct GroupPair {
     int64_t n_pairs = 0, n_items = 0;
     int n_chunks = 0, n_nn = 0;
     int64_t *rowptr = nullptr;
+    int32_t *seg_off = nullptr;   // [ndet][segments] offsets of the column segments within each row
     hb_pair *pairs = nullptr;
     double *val = nullptr;
     int64_t *item_ptr = nullptr;
@@ -34,6 +35,7 @@ struct GroupPair {
 // Scratch of one target group against the L2 functions (class 4).
 struct GroupL2 {
     int64_t *rowptr = nullptr;
+    int32_t *seg_off = nullptr;
     hb_pair *pairs = nullptr;
     int64_t n_pairs = 0;
 };
@@ -64,6 +66,7 @@ struct hb_ctx {
     // double-float (hi, lo) copies for the mixed class-4 kernel, made on first use
     float2 *tttc_df = nullptr, *h_df = nullptr, *ci_df = nullptr, *tttt_df = nullptr, *jk_df = nullptr;
     int64_t *l2_rowptr = nullptr;
+    int32_t *l2_seg_off = nullptr;
     int64_t l2_nnz = 0, tt_pairs = 0, tl2_pairs = 0;
     hb::MixedState *mixed = nullptr;
     hb_ctx *base = nullptr;  // context whose staged integrals this one borrows (or null)

@@ -54,7 +54,13 @@ struct GammaItem {
     int32_t phase;
 };
 
-// K1 classification (k_classify.cu)
+// K1 classification (k_classify.cu).  The hot scans split the columns into
+// segments of kSegCols, each with its own output offset within the row.
+constexpr int kSegCols = 512;
+int seg_count(int n_b);
+// seg_off[row][seg]: matches of the row in the segments before seg.
+void k1_seg_offsets(const uint64_t *a, int n_a, const uint64_t *b, int n_b, int W, int mode, int max_degree,
+                    int lower, int32_t *seg_off, cudaStream_t s);
 void k1_count(const uint64_t *a, int n_a, const uint64_t *b, int n_b, int W, int mode, int max_degree,
               int lower, int64_t *counts_plus1, cudaStream_t s);
 void k1_fill_pairs(const uint64_t *a, int n_a, const uint64_t *b, int n_b, int W, int mode, int cont_spin,

@@ -35,6 +35,8 @@ struct ClsTask {        // K1: classify rows of a against b into records
     const uint64_t *a, *b;
     int n_a, n_b, cont_spin, max_degree, lower;
     const int64_t *row_ptr;
+    const int32_t *seg_off;   // [n_a][nseg] offsets of the column segments within each row
+    int nseg;
     hb_pair *out;
 };
 
@@ -175,8 +177,9 @@ struct C4Task {         // class 4 of one target group against the L2 functions
 struct L2Task {         // classes 2 and 8: L2-L2 CSR of one Hamiltonian
     Ints I;
     const uint64_t *dets;
-    int n;
+    int n, nseg;
     const int64_t *row_ptr;
+    const int32_t *seg_off;   // [n][nseg] offsets of the column segments within each row
     int64_t *row_ptr_out;
     int32_t *col;
     double *val;
@@ -208,6 +211,7 @@ void class4_shape(int ns, int cn, int *ns_tile, int *jt);
 
 // block counts of one task of each stage (host side)
 int64_t blocks_rows8(int64_t rows);                 // one warp per row, 8 warps a block
+int64_t blocks_seg_rows8(int64_t rows, int n_b);    // the same per column segment
 int64_t blocks_pair_values(int64_t n_pairs);
 int64_t blocks_tn_partial(int n_rows, int ns, int nsp);
 int64_t blocks_tn_reduce(int ns, int nsp);

@@ -14,6 +14,7 @@ namespace hb {
 namespace {
 
 constexpr int kWarpsPerBlock = 8;
+constexpr int kSeg = kSegCols;   // columns per segment of the hot scans
 
 template <int W>
 __device__ __forceinline__ void load_det(const uint64_t *p, uint64_t (&x)[2 * W]) {
@@ -132,6 +133,45 @@ k1_count_kernel(const uint64_t *__restrict__ A, int n_a, const uint64_t *__restr
     if (lane == 0) counts_plus1[row + 1] = cnt;
 }
 
+// Matches of each row within each segment of kSeg columns (one warp per
+// (row, segment)), turned into offsets from the row start by seg_scan_kernel.
+template <int W, int MODE>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+k1_seg_count_kernel(const uint64_t *__restrict__ A, int n_a, const uint64_t *__restrict__ B, int n_b,
+                    int max_degree, int lower, int nseg, int32_t *__restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (wid >= (int64_t)n_a * nseg) return;
+    const int row = (int)(wid / nseg), sg = (int)(wid % nseg);
+    uint64_t a[2 * W];
+    load_det<W>(A + (int64_t)row * 2 * W, a);
+    const int limit = lower ? min(n_b, row + 1) : n_b;
+    const int c_end = min(limit, (sg + 1) * kSeg);
+    int c_cnt = 0;
+    for (int c0 = sg * kSeg; c0 < c_end; c0 += 32) {
+        const int c = c0 + lane;
+        bool ok = false;
+        if (c < c_end) {
+            uint64_t b[2 * W];
+            load_det<W>(B + (int64_t)c * 2 * W, b);
+            ok = degree_of<W, MODE>(a, b) <= max_degree;
+        }
+        c_cnt += __popc(__ballot_sync(0xffffffffu, ok));
+    }
+    if (lane == 0) cnt[wid] = c_cnt;
+}
+
+__global__ void seg_scan_kernel(int32_t *__restrict__ cnt, int n_a, int nseg) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n_a) return;
+    int32_t acc = 0;
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int32_t c = cnt[(int64_t)row * nseg + sg];
+        cnt[(int64_t)row * nseg + sg] = acc;
+        acc += c;
+    }
+}
+
 template <int W, int MODE>
 __device__ __forceinline__ void fill_row(const uint64_t *__restrict__ A, const uint64_t *__restrict__ B, int n_b,
                                          int cont_spin, int max_degree, int lower,
@@ -175,16 +215,105 @@ k1_fill_kernel(const uint64_t *__restrict__ A, int n_a, const uint64_t *__restri
     fill_row<W, MODE>(A, B, n_b, cont_spin, max_degree, lower, row_ptr, out, row, threadIdx.x & 31);
 }
 
-// The same over many (a, b) tasks in one launch.
+// The same over many (a, b) tasks in one launch, with the column
+// determinants staged through shared memory: the 8 warps of a block (8 rows)
+// read each tile of columns from memory once, word-major so the lanes'
+// shared-memory reads are conflict free.
+template <int W>
+struct ColTile {
+    static constexpr int kCols = kSeg;       // a segment of column determinants
+};
+
+template <int W>
+__device__ __forceinline__ void stage_cols(uint64_t *tile, const uint64_t *__restrict__ B, int t0, int tn) {
+    constexpr int TC = ColTile<W>::kCols;
+    for (int i = threadIdx.x; i < tn * 2 * W; i += blockDim.x) {
+        const int c = i / (2 * W), w = i % (2 * W);
+        tile[w * TC + c] = __ldg(B + (int64_t)t0 * 2 * W + i);
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void tile_det(const uint64_t *tile, int c, uint64_t (&b)[2 * W]) {
+#pragma unroll
+    for (int w = 0; w < 2 * W; ++w) b[w] = tile[w * ColTile<W>::kCols + c];
+}
+
+// Matches are queued per warp (in column order) and turned into records 32
+// at a time, one per lane, so the record work never runs with a lone lane.
 template <int W, int MODE>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 k1_fill_grouped(const ClsTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    constexpr int TC = ColTile<W>::kCols;
+    __shared__ uint64_t tile[TC * 2 * W];
+    __shared__ int queue[kWarpsPerBlock][64];
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const ClsTask &T = tasks[ti];
-    const int row = (int)(blockIdx.x - blk[ti]) * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (row >= T.n_a) return;
-    fill_row<W, MODE>(T.a, T.b, T.n_b, T.cont_spin, T.max_degree, T.lower, T.row_ptr, T.out, row,
-                      threadIdx.x & 31);
+    const int lb = (int)(blockIdx.x - blk[ti]);
+    // block = (8 rows, one segment of columns)
+    const int rb = lb / T.nseg, sg = lb % T.nseg;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int row = rb * kWarpsPerBlock + warp;
+    const bool active = row < T.n_a;
+    int *q = queue[warp];
+    uint64_t a[2 * W];
+    int limit = 0;
+    int64_t pos = 0, end = 0;
+    if (active) {
+        load_det<W>(T.a + (int64_t)row * 2 * W, a);
+        limit = T.lower ? min(T.n_b, row + 1) : T.n_b;
+        pos = T.row_ptr[row] + T.seg_off[(int64_t)row * T.nseg + sg];
+        end = T.row_ptr[row + 1];
+    }
+    const int last_row = min(T.n_a, (rb + 1) * kWarpsPerBlock) - 1;
+    const int blim = T.lower ? min(T.n_b, last_row + 1) : T.n_b;
+    const int t0 = sg * TC;
+    if (t0 >= blim) return;
+    const int tn = min(TC, blim - t0);
+    stage_cols<W>(tile, T.b, t0, tn);
+    __syncthreads();
+    // records for the first `cnt` queued columns
+    auto drain = [&](int cnt) {
+        if (lane < cnt) {
+            const int cl = q[lane];
+            uint64_t b[2 * W];
+            tile_det<W>(tile, cl, b);
+            const int deg = degree_of<W, MODE>(a, b);
+            const int64_t at = pos + lane;
+            if (at < end) {
+                hb_pair r;
+                make_record<W, MODE>(a, b, deg, T.cont_spin, row, t0 + cl, r);
+                T.out[at] = r;
+            }
+        }
+        pos += cnt;
+    };
+    const int cend = active ? min(tn, limit - t0) : 0;
+    int qn = 0;
+    for (int c0 = 0; c0 < cend; c0 += 32) {
+        const int cl = c0 + lane;
+        bool ok = false;
+        if (cl < cend) {
+            uint64_t b[2 * W];
+            tile_det<W>(tile, cl, b);
+            ok = degree_of<W, MODE>(a, b) <= T.max_degree;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) q[qn + __popc(m & ((1u << lane) - 1u))] = cl;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            drain(32);
+            __syncwarp();
+            const int rest = qn - 32;
+            const int mv = lane < rest ? q[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) q[lane] = mv;
+            qn = rest;
+            __syncwarp();
+        }
+    }
+    if (qn > 0) drain(qn);
 }
 
 // Inclusive scan of x[1..n] in place (x[0] = 0 is set), single block.
@@ -268,6 +397,26 @@ void k1_fill_pairs(const uint64_t *a, int n_a, const uint64_t *b, int n_b, int W
     if (mode == 0) fill_dispatch<0>(a, n_a, b, n_b, W, cont_spin, max_degree, lower, row_ptr, out, s);
     else fill_dispatch<1>(a, n_a, b, n_b, W, cont_spin, max_degree, lower, row_ptr, out, s);
 }
+
+int seg_count(int n_b) { return n_b > 0 ? (n_b + kSeg - 1) / kSeg : 1; }
+
+void k1_seg_offsets(const uint64_t *a, int n_a, const uint64_t *b, int n_b, int W, int mode, int max_degree,
+                    int lower, int32_t *seg_off, cudaStream_t s) {
+    if (n_a <= 0) return;
+    const int nseg = seg_count(n_b);
+    const unsigned grid = (unsigned)(((int64_t)n_a * nseg + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    const dim3 block(32 * kWarpsPerBlock);
+#define HB_SEG(WW, MM) k1_seg_count_kernel<WW, MM><<<grid, block, 0, s>>>(a, n_a, b, n_b, max_degree, lower, nseg, seg_off)
+    if (mode == 0) {
+        switch (W) { case 1: HB_SEG(1, 0); break; case 2: HB_SEG(2, 0); break; case 3: HB_SEG(3, 0); break; default: HB_SEG(4, 0); break; }
+    } else {
+        switch (W) { case 1: HB_SEG(1, 1); break; case 2: HB_SEG(2, 1); break; case 3: HB_SEG(3, 1); break; default: HB_SEG(4, 1); break; }
+    }
+#undef HB_SEG
+    seg_scan_kernel<<<(n_a + 255) / 256, 256, 0, s>>>(seg_off, n_a, nseg);
+}
+
+int64_t blocks_seg_rows8(int64_t rows, int n_b) { return ((rows + 7) / 8) * seg_count(n_b); }
 
 void exclusive_scan_inplace(int64_t *x, int n, cudaStream_t s) {
     scan_kernel<<<1, 1024, 0, s>>>(x, n);

@@ -197,8 +197,9 @@ void fill_tasks(Plan &p) {
             const double *Ca = ctx->ci + A.ci_off, *Cb = ctx->ci + B.ci_off;
             const float2 *Ca_df = ctx->ci_df ? ctx->ci_df + A.ci_off : nullptr;
             const float2 *Cb_df = ctx->ci_df ? ctx->ci_df + B.ci_off : nullptr;
-            p.cls_tt.add(ClsTask{da, db, A.ndet, B.ndet, ctx->cont_spin, 2, 0, P.rowptr, P.pairs},
-                         blocks_rows8(A.ndet));
+            p.cls_tt.add(ClsTask{da, db, A.ndet, B.ndet, ctx->cont_spin, 2, 0, P.rowptr, P.seg_off, seg_count(B.ndet),
+                                 P.pairs},
+                         blocks_seg_rows8(A.ndet, B.ndet));
             p.pv.add(PVTask{I, da, db, P.pairs, P.n_pairs, P.val}, blocks_pair_values(P.n_pairs));
             (B.ns <= 16 ? p.sws : p.sw).add(SWTask{P.pairs, P.rowptr, P.val, A.ndet, Cb, Cb_df, B.ns, P.W},
                                             blocks_rows8(A.ndet));
@@ -260,8 +261,9 @@ void fill_tasks(Plan &p) {
             const GroupInfo &G = ctx->groups[g];
             GroupL2 &L = ctx->gl2[g];
             const uint64_t *dg = ctx->dets + G.det_off;
-            p.cls_tl2.add(ClsTask{ctx->l2, dg, ctx->n_l2, G.ndet, ctx->cont_spin, 2, 0, L.rowptr, L.pairs},
-                          blocks_rows8(ctx->n_l2));
+            p.cls_tl2.add(ClsTask{ctx->l2, dg, ctx->n_l2, G.ndet, ctx->cont_spin, 2, 0, L.rowptr, L.seg_off,
+                                  seg_count(G.ndet), L.pairs},
+                          blocks_seg_rows8(ctx->n_l2, G.ndet));
             int ns_tile = 32, jt = 128;
             if (p.precision == HB_MIXED) {
                 class4_shape(G.ns, G.cn, &ns_tile, &jt);
@@ -284,8 +286,9 @@ void fill_tasks(Plan &p) {
             if (p.precision == HB_MIXED) p.tune_c4.push_back(TuneC4{c4t});
         }
         if (ctx->n_l2 > 0)
-            p.l2.add(L2Task{I, ctx->l2, ctx->n_l2, ctx->l2_rowptr, out.l2_row_ptr, out.l2_col, out.l2_val, ctx->e_core},
-                     blocks_rows8(ctx->n_l2));
+            p.l2.add(L2Task{I, ctx->l2, ctx->n_l2, seg_count(ctx->n_l2), ctx->l2_rowptr, ctx->l2_seg_off, out.l2_row_ptr,
+                            out.l2_col, out.l2_val, ctx->e_core},
+                     blocks_seg_rows8(ctx->n_l2, ctx->n_l2));
     }
     // merged expansion blocks: columns member by member, state pairs in order
     for (auto &B : blocks) {

@@ -145,49 +145,95 @@ __device__ __forceinline__ void store_value(const AccF &v, double *out, int64_t 
 
 constexpr int kWarps = 8;
 
+// Block = 8 rows (one warp each) x one segment of kSegCols columns, staged
+// through shared memory word-major (conflict-free lane reads); the segment's
+// output offset within each row comes from the staging-time segment counts.
+// Matches are queued per warp in column order and evaluated 32 at a time,
+// one per lane.
 template <int W, class Acc>
 __global__ void __launch_bounds__(32 * kWarps)
 l2_csr_kernel(const L2Task *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    constexpr int TC = kSegCols;
+    __shared__ uint64_t tile[TC * 2 * W];
+    __shared__ int queue[kWarps][64];
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const L2Task &T = tasks[ti];
     const Ints I = T.I;
     const uint64_t *__restrict__ D = T.dets;
     const int n = T.n;
-    const int lane = threadIdx.x & 31;
-    const int row = (int)(blockIdx.x - blk[ti]) * kWarps + (threadIdx.x >> 5);
-    if (row >= n) return;
+    const int lb = (int)(blockIdx.x - blk[ti]);
+    const int rb = lb / T.nseg, sg = lb % T.nseg;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int row = rb * kWarps + warp;
+    const bool active = row < n;
+    int *q = queue[warp];
     uint64_t a[2 * W];
-    load_det<W>(D + (int64_t)row * 2 * W, a);
-    int64_t pos = T.row_ptr[row];
-    const int64_t end = T.row_ptr[row + 1];
-    if (lane == 0) {
-        T.row_ptr_out[row] = pos;
-        if (row == n - 1) T.row_ptr_out[n] = end;
+    int64_t pos = 0, end = 0;
+    if (active) {
+        load_det<W>(D + (int64_t)row * 2 * W, a);
+        pos = T.row_ptr[row] + T.seg_off[(int64_t)row * T.nseg + sg];
+        end = T.row_ptr[row + 1];
+        if (lane == 0 && sg == 0) {
+            T.row_ptr_out[row] = T.row_ptr[row];
+            if (row == n - 1) T.row_ptr_out[n] = end;
+        }
     }
-    for (int c0 = 0; c0 < n; c0 += 32) {
-        const int c = c0 + lane;
-        int deg = 99;
-        uint64_t b[2 * W];
-        if (c < n) {
-            load_det<W>(D + (int64_t)c * 2 * W, b);
+    const int t0 = sg * TC;
+    if (t0 >= n) return;
+    const int tn = min(TC, n - t0);
+    for (int i = threadIdx.x; i < tn * 2 * W; i += blockDim.x) {
+        const int c = i / (2 * W), w = i % (2 * W);
+        tile[w * TC + c] = __ldg(D + (int64_t)t0 * 2 * W + i);
+    }
+    __syncthreads();
+    if (!active) return;
+    auto drain = [&](int cnt) {
+        if (lane < cnt) {
+            const int cl = q[lane];
+            uint64_t b[2 * W];
             int x = 0;
 #pragma unroll
-            for (int i = 0; i < 2 * W; ++i) x += __popcll(a[i] ^ b[i]);
-            deg = x >> 1;
-        }
-        const bool ok = deg <= 2;
-        const unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            const int64_t at = pos + __popc(m & ((1u << lane) - 1u));
+            for (int i = 0; i < 2 * W; ++i) {
+                b[i] = tile[i * TC + cl];
+                x += __popcll(a[i] ^ b[i]);
+            }
+            const int deg = x >> 1;
+            const int64_t at = pos + lane;
             if (at < end) {
                 Acc v = element<W, Acc>(I, a, b, deg);
                 if (deg == 0) v.add_const(T.e_core);
-                T.col[at] = c;
+                T.col[at] = t0 + cl;
                 T.val[at] = v.value();
             }
         }
-        pos += __popc(m);
+        pos += cnt;
+    };
+    int qn = 0;
+    for (int c0 = 0; c0 < tn; c0 += 32) {
+        const int cl = c0 + lane;
+        bool ok = false;
+        if (cl < tn) {
+            int x = 0;
+#pragma unroll
+            for (int i = 0; i < 2 * W; ++i) x += __popcll(a[i] ^ tile[i * TC + cl]);
+            ok = (x >> 1) <= 2;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) q[qn + __popc(m & ((1u << lane) - 1u))] = cl;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            drain(32);
+            __syncwarp();
+            const int rest = qn - 32;
+            const int mv = lane < rest ? q[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) q[lane] = mv;
+            qn = rest;
+            __syncwarp();
+        }
     }
+    if (qn > 0) drain(qn);
 }
 
 // <A[row]|H|B[col]> for classified pairs (mode 0 records).  FP64: val as
