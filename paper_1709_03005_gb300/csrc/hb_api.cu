@@ -361,6 +361,7 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         DALLOC(P.W, (int64_t)A.ndet * B.ns);
         DALLOC(P.partial, (int64_t)tn_chunks(A.ndet) * nout);
         DALLOC(P.partial_s, P.same ? (int64_t)tn_chunks(A.ndet) * nout : 1);
+        DALLOC(P.gdiag, P.same ? (int64_t)tn_chunks(A.ndet) * 2 * p->n_to * nout : 1);
         DALLOC(P.S, nout);
         DALLOC(P.E, nout);
         std::vector<int32_t> nn;

@@ -27,6 +27,7 @@ struct GroupPair {
     int32_t *order = nullptr;
     int64_t *sort_off = nullptr, *sort_cur = nullptr;
     double *gamma = nullptr, *W = nullptr, *partial = nullptr, *partial_s = nullptr, *S = nullptr, *E = nullptr;
+    double *gdiag = nullptr;    // same group: partial sums of the diagonal gamma [chunks][2 n_to][ns * ns]
     int32_t *nn = nullptr;
     double *A = nullptr;        // [n_nn][Kpad] contracted coefficients
     float2 *A_df = nullptr;     // the same as float pairs (mixed build, made on first use)

@@ -112,6 +112,15 @@ struct GTask {          // gamma[key][n][n'] over the sorted items
     double *gamma;
 };
 
+struct GDTask {         // diagonal gamma(p, p) of a group with itself (deg-0 records)
+    const uint64_t *dets;     // the group's determinants
+    int W, n_to, ndet, ns, ny;
+    const double *C;
+    const float2 *C_df;
+    double *partial;          // [chunks][2 n_to][ns * ns] (float pairs in the double-float launch)
+    double *gamma;
+};
+
 struct ATask {          // contracted coefficient rows A[(n,n')][k]
     const double *gamma, *S, *E;
     const int32_t *nn;
@@ -203,6 +212,11 @@ int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s);
 int g_gamma(const Grouped<GTask> &g, size_t smem, int dfloat, cudaStream_t s);
 int g_gamma_warp(const Grouped<GTask> &g, int dfloat, cudaStream_t s);         // ns * nsp <= 64
 int g_assemble(const Grouped<ATask> &g, cudaStream_t s);
+// partial sums then their reduction into gamma[(s, p, p)] (after the item bins)
+int g_gdiag(const Grouped<GDTask> &partial, const Grouped<GDTask> &reduce, size_t smem, int dfloat, cudaStream_t s);
+int64_t blocks_gdiag_partial(int ndet, int n_to, int ns);
+int64_t blocks_gdiag_reduce(int n_to, int ns);
+size_t smem_gdiag(int ns);
 int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s);
 // dfloat = 0: FP64 (128 threads, 32 states a pass); 1: double-float with
 // ns_tile states a pass (8, 16 or 32) and jt threads a block (32, 64 or 128)

@@ -81,6 +81,8 @@ struct Plan {
     Stage<SortTask> sort;
     Stage<ScanTask> scan;
     Stage<GTask> gam, gamw;            // gamma bins: block / warp (ns * nsp <= 64) per key
+    Stage<GDTask> gdp, gdr;            // diagonal gamma of same-group pairs: partial sums, reduction
+    size_t smem_gd = 0;
     Stage<ATask> asmb;
     Stage<XTask> x64;
     Stage<SliceTask> slc;
@@ -149,14 +151,14 @@ void stage_bind(Stage<T> &st, uint8_t *dev) {
 
 // Task tables of every stage from the contexts and the output blocks.
 void fill_tasks(Plan &p) {
-    p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.sw.clear(); p.sws.clear(); p.gamw.clear(); p.tn.clear(); p.tnr.clear();
+    p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.sw.clear(); p.sws.clear(); p.gamw.clear(); p.gdp.clear(); p.gdr.clear(); p.tn.clear(); p.tnr.clear();
     p.itf.clear(); p.zero.clear(); p.sort.clear(); p.scan.clear(); p.gam.clear(); p.asmb.clear();
     p.x64.clear(); p.slc.clear(); p.drows.clear(); p.l2.clear();
     for (auto &v : p.c4v) v.st.clear();
     for (auto &sg : p.split) sg.st.clear();
     p.cols.clear();
     p.tune_split.clear(); p.tune_c4.clear(); p.tune_gamma.clear();
-    p.smem_tn = p.smem_gamma = 0;
+    p.smem_tn = p.smem_gamma = p.smem_gd = 0;
     p.flops = 0.0;
     p.n_expand_tasks = 0;
     int64_t coef_row = 0;
@@ -234,6 +236,12 @@ void fill_tasks(Plan &p) {
             } else {
                 p.gam.add(gt, blocks_gamma(n_keys, A.ns, B.ns));
                 p.smem_gamma = std::max(p.smem_gamma, smem_stage(A.ns, B.ns));
+            }
+            if (P.same) {
+                const GDTask gd{da, W, ctx->n_to, A.ndet, A.ns, tn_ny(A.ns, A.ns), Ca, Ca_df, P.gdiag, P.gamma};
+                p.gdp.add(gd, blocks_gdiag_partial(A.ndet, ctx->n_to, A.ns));
+                p.gdr.add(gd, blocks_gdiag_reduce(ctx->n_to, A.ns));
+                p.smem_gd = std::max(p.smem_gd, smem_gdiag(A.ns));
             }
             p.asmb.add(ATask{P.gamma, P.S, P.E, P.nn, P.n_nn, A.ns, B.ns, ctx->n_to, ctx->cont_spin, ctx->Kpad,
                              ctx->e_core, P.A, p.precision == HB_MIXED ? P.A_df : nullptr},
@@ -363,7 +371,8 @@ void ensure_split_events(Plan &p) {
 void pack_all(Plan &p) {
     p.host.clear();
     stage_pack(p.cls_tt, p.host); stage_pack(p.cls_tl2, p.host); stage_pack(p.pv, p.host);
-    stage_pack(p.sw, p.host); stage_pack(p.sws, p.host); stage_pack(p.gamw, p.host); stage_pack(p.tn, p.host); stage_pack(p.tnr, p.host); stage_pack(p.itf, p.host);
+    stage_pack(p.sw, p.host); stage_pack(p.sws, p.host); stage_pack(p.gamw, p.host);
+    stage_pack(p.gdp, p.host); stage_pack(p.gdr, p.host); stage_pack(p.tn, p.host); stage_pack(p.tnr, p.host); stage_pack(p.itf, p.host);
     stage_pack(p.zero, p.host); stage_pack(p.sort, p.host); stage_pack(p.scan, p.host); stage_pack(p.gam, p.host);
     stage_pack(p.asmb, p.host); stage_pack(p.x64, p.host); stage_pack(p.slc, p.host);
     for (auto &sg : p.split) stage_pack(sg.st, p.host);
@@ -376,7 +385,8 @@ void pack_all(Plan &p) {
 
 void bind_all(Plan &p) {
     stage_bind(p.cls_tt, p.dev); stage_bind(p.cls_tl2, p.dev); stage_bind(p.pv, p.dev);
-    stage_bind(p.sw, p.dev); stage_bind(p.sws, p.dev); stage_bind(p.gamw, p.dev); stage_bind(p.tn, p.dev); stage_bind(p.tnr, p.dev); stage_bind(p.itf, p.dev);
+    stage_bind(p.sw, p.dev); stage_bind(p.sws, p.dev); stage_bind(p.gamw, p.dev);
+    stage_bind(p.gdp, p.dev); stage_bind(p.gdr, p.dev); stage_bind(p.tn, p.dev); stage_bind(p.tnr, p.dev); stage_bind(p.itf, p.dev);
     stage_bind(p.zero, p.dev); stage_bind(p.sort, p.dev); stage_bind(p.scan, p.dev); stage_bind(p.gam, p.dev);
     stage_bind(p.asmb, p.dev); stage_bind(p.x64, p.dev); stage_bind(p.slc, p.dev);
     for (auto &sg : p.split) stage_bind(sg.st, p.dev);
@@ -699,6 +709,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     L += g_sort_scatter(p->sort.g, s);
     L += g_gamma(p->gam.g, p->smem_gamma, DF, s);
     L += g_gamma_warp(p->gamw.g, DF, s);
+    L += g_gdiag(p->gdp.g, p->gdr.g, p->smem_gd, DF, s);
     L += g_assemble(p->asmb.g, s);
     rec(p->ev[1]);
     // expansion (Eq. 7): classes 1, 3, 5, 6, 7

@@ -150,15 +150,17 @@ __global__ void item_count_kernel(const hb_pair *__restrict__ pairs, const int64
     int64_t cnt = 0;
     for (int64_t k = b + lane; k < e; k += 32) {
         const int d = pairs[k].degree;
-        cnt += d == 0 ? n_elec : (d == 1 ? 1 : 0);
+        cnt += d == 1 ? 1 : 0;
     }
 #pragma unroll
     for (int off = 16; off; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
     if (lane == 0) counts_plus1[row + 1] = cnt;
 }
 
-// Items in record order; a deg-0 record emits its occupied spin orbitals in
-// canonical order.  key = spin * n_to^2 + r * n_to + q.
+// Items in record order, one per single-excitation record.  key = spin *
+// n_to^2 + r * n_to + q.  (A deg-0 record is a determinant with itself, m = m'
+// of one group; its diagonal contributions gamma(p, p) are the masked C^T C of
+// gdiag_partial_kernel below.)
 __global__ void item_fill_kernel(const IFTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const IFTask T = tasks[ti];
@@ -167,7 +169,7 @@ __global__ void item_fill_kernel(const IFTask *__restrict__ tasks, const int64_t
     if (row >= T.n_rows) return;
     const int64_t b = T.row_ptr[row], e = T.row_ptr[row + 1];
     int64_t pos = T.item_ptr[row];
-    const int W = T.W, n_to = T.n_to, n_elec = T.n_elec;
+    const int W = T.W, n_to = T.n_to;
     const int sb = 64 * W;
     for (int64_t k0 = b; k0 < e; k0 += 32) {
         const int64_t k = k0 + lane;
@@ -175,40 +177,112 @@ __global__ void item_fill_kernel(const IFTask *__restrict__ tasks, const int64_t
         hb_pair r;
         if (k < e) {
             r = T.pairs[k];
-            cnt = r.degree == 0 ? n_elec : (r.degree == 1 ? 1 : 0);
+            cnt = r.degree == 1 ? 1 : 0;
         }
-        int incl = cnt;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += u;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        int64_t at = pos + (incl - cnt);
+        const unsigned m = __ballot_sync(0xffffffffu, cnt != 0);
         if (cnt) {
-            if (r.degree == 1) {
-                const int s = r.part[0] / sb, p = r.part[0] % sb, q = r.hole[0] % sb;
-                GammaItem it;
-                it.key = s * n_to * n_to + p * n_to + q;
-                it.m = r.row; it.mp = r.col; it.phase = r.phase;
-                T.items[at] = it;
-            } else {
-                const uint64_t *d = T.bra + (int64_t)r.row * 2 * W;
-                for (int w = 0; w < 2 * W; ++w) {
-                    uint64_t x = d[w];
-                    while (x) {
-                        const int bit = 64 * w + __ffsll((long long)x) - 1;
-                        x &= x - 1;
-                        const int s = bit / sb, p = bit % sb;
-                        GammaItem it;
-                        it.key = s * n_to * n_to + p * n_to + p;
-                        it.m = r.row; it.mp = r.col; it.phase = 1;
-                        T.items[at++] = it;
+            const int s = r.part[0] / sb, p = r.part[0] % sb, q = r.hole[0] % sb;
+            GammaItem it;
+            it.key = s * n_to * n_to + p * n_to + q;
+            it.m = r.row; it.mp = r.col; it.phase = r.phase;
+            T.items[pos + __popc(m & ((1u << lane) - 1u))] = it;
+        }
+        pos += __popc(m);
+    }
+}
+
+// --------------------------------------------- diagonal gamma (deg-0 records)
+// gamma^s(p, p)[n][n'] over identical determinants (m = m', one group) is
+//   sum_{m: p_s occupied in D_m} C[m][n] C[m][n']
+// a C^T C with a row mask per spin orbital: chunked partial sums (rows in
+// chunks of kRowsPerChunk, fixed order), then a reduction over the chunks.
+// Blocks: (chunk, spin orbital sp, y) with y covering the outputs.
+template <bool DF>
+__global__ void gdiag_partial_kernel(const GDTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                     int n_tasks) {
+    extern __shared__ double gsh[];
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const GDTask T = tasks[ti];
+    const int nsp2 = 2 * T.n_to;
+    const int lb = (int)(blockIdx.x - blk[ti]);
+    const int by = lb % T.ny, sp = (lb / T.ny) % nsp2, c = lb / (T.ny * nsp2);
+    const int ns = T.ns, nout = ns * ns;
+    const int spin = sp / T.n_to, p = sp % T.n_to;
+    const int word = spin * T.W + p / 64;
+    const uint64_t bit = 1ull << (p % 64);
+    const int m0 = c * kRowsPerChunk;
+    const int rows = min(kRowsPerChunk, T.ndet - m0);
+    const int kBatch = stage_batch(ns + 1, 0);
+    int *occ = reinterpret_cast<int *>(gsh + (size_t)kBatch * ns);   // [kBatch]
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    float ah[4] = {0.0f, 0.0f, 0.0f, 0.0f}, al[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int r0 = 0; r0 < rows; r0 += kBatch) {
+        const int nr = min(kBatch, rows - r0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nr; i += blockDim.x)
+            occ[i] = (T.dets[(int64_t)(m0 + r0 + i) * 2 * T.W + word] & bit) ? 1 : 0;
+        if (DF) {
+            float2 *cs = reinterpret_cast<float2 *>(gsh);
+            for (int i = threadIdx.x; i < nr * ns; i += blockDim.x) cs[i] = T.C_df[(int64_t)(m0 + r0) * ns + i];
+        } else {
+            for (int i = threadIdx.x; i < nr * ns; i += blockDim.x) gsh[i] = T.C[(int64_t)(m0 + r0) * ns + i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
+            if (t < nout) {
+                const int a = t / ns, b = t % ns;
+                for (int m = 0; m < nr; ++m) {
+                    if (!occ[m]) continue;
+                    if (DF) {
+                        const float2 *cs = reinterpret_cast<const float2 *>(gsh);
+                        const float2 x = cs[m * ns + a], y = cs[m * ns + b];
+                        df_fma(ah[u], al[u], x.x, x.y, y.x, y.y);
+                    } else {
+                        acc[u] = fma(gsh[m * ns + a], gsh[m * ns + b], acc[u]);
                     }
                 }
             }
         }
-        pos += total;
+    }
+    const int64_t base = ((int64_t)c * nsp2 + sp) * nout;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
+        if (t < nout) {
+            if (DF) reinterpret_cast<float2 *>(T.partial)[base + t] = make_float2(ah[u], al[u]);
+            else T.partial[base + t] = acc[u];
+        }
+    }
+}
+
+// gamma[(s, p, p)][t] = sum over the chunks, in order.  Blocks: (sp, t / 256).
+template <bool DF>
+__global__ void gdiag_reduce_kernel(const GDTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                    int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const GDTask T = tasks[ti];
+    const int nsp2 = 2 * T.n_to, nout = T.ns * T.ns;
+    const int tb = (nout + 255) / 256;
+    const int lb = (int)(blockIdx.x - blk[ti]);
+    const int sp = lb / tb, t = (lb % tb) * 256 + threadIdx.x;
+    if (t >= nout) return;
+    const int nc = (T.ndet + kRowsPerChunk - 1) / kRowsPerChunk;
+    const int spin = sp / T.n_to, p = sp % T.n_to;
+    const int64_t key = (int64_t)spin * T.n_to * T.n_to + (int64_t)p * T.n_to + p;
+    if (DF) {
+        const float2 *part = reinterpret_cast<const float2 *>(T.partial);
+        float h = 0.0f, l = 0.0f;
+        for (int c = 0; c < nc; ++c) {
+            const float2 x = part[((int64_t)c * nsp2 + sp) * nout + t];
+            df_add2(h, l, x.x, x.y);
+        }
+        T.gamma[key * nout + t] = df_to_double(h, l);
+    } else {
+        double acc = 0.0;
+        for (int c = 0; c < nc; ++c) acc += T.partial[((int64_t)c * nsp2 + sp) * nout + t];
+        T.gamma[key * nout + t] = acc;
     }
 }
 
@@ -708,6 +782,27 @@ int g_gamma_warp(const Grouped<GTask> &g, int dfloat, cudaStream_t s) {
     HB_GROUPED(gamma_warp_kernel, g, 256, 0, s);
 }
 int g_assemble(const Grouped<ATask> &g, cudaStream_t s) { HB_GROUPED(assemble_kernel, g, 256, 0, s); }
+
+int g_gdiag(const Grouped<GDTask> &partial, const Grouped<GDTask> &reduce, size_t smem, int dfloat, cudaStream_t s) {
+    int L = 0;
+    if (partial.blocks > 0) {
+        if (dfloat) gdiag_partial_kernel<true><<<(unsigned)partial.blocks, 256, smem, s>>>(partial.tasks, partial.blk, partial.n);
+        else gdiag_partial_kernel<false><<<(unsigned)partial.blocks, 256, smem, s>>>(partial.tasks, partial.blk, partial.n);
+        ++L;
+    }
+    if (reduce.blocks > 0) {
+        if (dfloat) gdiag_reduce_kernel<true><<<(unsigned)reduce.blocks, 256, 0, s>>>(reduce.tasks, reduce.blk, reduce.n);
+        else gdiag_reduce_kernel<false><<<(unsigned)reduce.blocks, 256, 0, s>>>(reduce.tasks, reduce.blk, reduce.n);
+        ++L;
+    }
+    return L;
+}
+
+int64_t blocks_gdiag_partial(int ndet, int n_to, int ns) {
+    return (int64_t)tn_chunks(ndet) * 2 * n_to * tn_ny(ns, ns);
+}
+int64_t blocks_gdiag_reduce(int n_to, int ns) { return (int64_t)2 * n_to * ((ns * ns + 255) / 256); }
+size_t smem_gdiag(int ns) { return (sizeof(double) * ns + sizeof(int)) * stage_batch(ns + 1, 0); }
 
 int g_scan(const Grouped<ScanTask> &g, cudaStream_t s) {
     if (g.n <= 0) return 0;
