@@ -10,6 +10,7 @@
 #include "hb_davidson.cuh"
 #include "hb_plan.cuh"
 #include "hb_df.cuh"
+#include "hb_tasks.cuh"
 
 using namespace hb;
 
@@ -97,8 +98,9 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
     if (!std::isfinite(p->e_core)) return fail(ctx, HB_ERR_INVALID_ARG, "e_core is not finite");
     if (o && o->split_tile != 0 && (o->split_tile < 3 || o->split_tile > 5))
         return fail(ctx, HB_ERR_INVALID_ARG, "split_tile must be 0, 3, 4 or 5");
-    if (o && o->class4_states != 0 && o->class4_states != 8 && o->class4_states != 16 && o->class4_states != 32)
-        return fail(ctx, HB_ERR_INVALID_ARG, "class4_states must be 0, 8, 16 or 32");
+    if (o && o->class4_states != 0 && o->class4_states != 8 && o->class4_states != 16 && o->class4_states != 24 &&
+        o->class4_states != 32)
+        return fail(ctx, HB_ERR_INVALID_ARG, "class4_states must be 0, 8, 16, 24 or 32");
     if (o && o->class4_threads != 0 && o->class4_threads != 32 && o->class4_threads != 64 && o->class4_threads != 128)
         return fail(ctx, HB_ERR_INVALID_ARG, "class4_threads must be 0, 32, 64 or 128");
     const int W = p->n_words, nw = 2 * W;
@@ -351,11 +353,12 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         exclusive_scan_inplace(P.item_ptr, A.ndet, s);
         CK(cudaMemcpyAsync(&P.n_items, P.item_ptr + A.ndet, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        P.n_chunks = sort_chunks(P.n_items);
+        P.n_chunks = sort_chunks(P.n_items, n_keys);
         DALLOC(P.items, P.n_items);
         DALLOC(P.order, P.n_items);
         DALLOC(P.sort_off, (int64_t)n_keys * P.n_chunks + 1);
         DALLOC(P.sort_cur, (int64_t)n_keys * P.n_chunks + 1);
+        DALLOC(P.sort_part, blocks_scan((int64_t)n_keys * P.n_chunks) + 1);
         const int64_t nout = (int64_t)A.ns * B.ns;
         DALLOC(P.gamma, n_keys * nout);
         DALLOC(P.W, (int64_t)A.ndet * B.ns);

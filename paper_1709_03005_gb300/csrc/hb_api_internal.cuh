@@ -25,7 +25,7 @@ struct GroupPair {
     int64_t *item_ptr = nullptr;
     GammaItem *items = nullptr;
     int32_t *order = nullptr;
-    int64_t *sort_off = nullptr, *sort_cur = nullptr;
+    int64_t *sort_off = nullptr, *sort_cur = nullptr, *sort_part = nullptr;
     double *gamma = nullptr, *W = nullptr, *partial = nullptr, *partial_s = nullptr, *S = nullptr, *E = nullptr;
     double *gdiag = nullptr;    // same group: partial sums of the diagonal gamma [chunks][2 n_to][ns * ns]
     int32_t *nn = nullptr;

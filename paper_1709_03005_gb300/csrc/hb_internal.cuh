@@ -85,7 +85,7 @@ void gamma_item_counts(const hb_pair *pairs, const int64_t *row_ptr, int n_rows,
                        int64_t *counts_plus1, cudaStream_t s);
 void gamma_item_fill(const hb_pair *pairs, const int64_t *row_ptr, int n_rows, const uint64_t *bra_dets, int W,
                      int n_to, int n_elec, const int64_t *item_ptr, GammaItem *items, cudaStream_t s);
-int sort_chunks(int64_t n_items);
+int sort_chunks(int64_t n_items, int n_keys);
 void gamma_sort(const GammaItem *items, int64_t n_items, int n_keys, int64_t *offsets_plus1, int64_t *cursors,
                 int32_t *order, cudaStream_t s);
 void gamma_bins(const GammaItem *items, const int32_t *order, const int64_t *offsets, int n_keys,

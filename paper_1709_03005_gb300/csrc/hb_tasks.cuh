@@ -96,6 +96,7 @@ struct ScanTask {       // x[0] = 0, x[1..n] inclusive scan; copy[0..n-1] = resu
     int64_t *x;
     int64_t n;
     int64_t *copy;
+    int64_t *part;            // [ceil(n / 4096)] segment sums (scratch)
 };
 
 struct GTask {          // gamma[key][n][n'] over the sorted items
@@ -208,6 +209,7 @@ int g_item_fill(const Grouped<IFTask> &g, cudaStream_t s);
 int g_zero(const Grouped<ZTask> &g, cudaStream_t s);
 int g_sort_hist(const Grouped<SortTask> &g, cudaStream_t s);
 int g_scan(const Grouped<ScanTask> &g, cudaStream_t s);
+int64_t blocks_scan(int64_t n);
 int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s);
 int g_gamma(const Grouped<GTask> &g, size_t smem, int dfloat, cudaStream_t s);
 int g_gamma_warp(const Grouped<GTask> &g, int dfloat, cudaStream_t s);         // ns * nsp <= 64
@@ -219,7 +221,7 @@ int64_t blocks_gdiag_reduce(int n_to, int ns);
 size_t smem_gdiag(int ns);
 int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s);
 // dfloat = 0: FP64 (128 threads, 32 states a pass); 1: double-float with
-// ns_tile states a pass (8, 16 or 32) and jt threads a block (32, 64 or 128)
+// ns_tile states a pass (8, 16, 24 or 32) and jt threads a block (32, 64 or 128)
 int g_class4(const Grouped<C4Task> &g, int W, int dfloat, int ns_tile, int jt, cudaStream_t s);
 void class4_shape(int ns, int cn, int *ns_tile, int *jt);
 
@@ -230,7 +232,7 @@ int64_t blocks_pair_values(int64_t n_pairs);
 int64_t blocks_tn_partial(int n_rows, int ns, int nsp);
 int64_t blocks_tn_reduce(int ns, int nsp);
 int64_t blocks_zero(int64_t n);
-int64_t blocks_sort(int64_t n_items);
+int64_t blocks_sort(int64_t n_items, int n_keys);
 int64_t blocks_gamma(int n_keys, int ns, int nsp);
 int64_t blocks_gamma_warp(int n_keys);
 int64_t blocks_expand_fp64(int cn, int cnp, int N);

@@ -260,7 +260,7 @@ int64_t blocks_class4(int n_l2, int cn, int jt) { return cn > 0 ? (int64_t)n_l2 
 void class4_shape(int ns, int cn, int *ns_tile, int *jt) {
     const int passes = (ns + 31) / 32;
     const int need = (ns + passes - 1) / passes;
-    *ns_tile = need <= 8 ? 8 : (need <= 16 ? 16 : 32);
+    *ns_tile = need <= 8 ? 8 : (need <= 16 ? 16 : (need <= 24 ? 24 : 32));
     int best = 128;
     int64_t best_idle = (int64_t)((cn + 127) / 128) * 128 - cn;
     for (int t : {64, 32}) {
@@ -291,6 +291,7 @@ int g_class4(const Grouped<C4Task> &g, int W, int dfloat, int ns_tile, int jt, c
     switch (ns_tile) {                                                                                    \
         case 8: class4_df_kernel<WW, 8><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;                 \
         case 16: class4_df_kernel<WW, 16><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
+        case 24: class4_df_kernel<WW, 24><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
         default: class4_df_kernel<WW, 32><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
     }
     switch (W) {

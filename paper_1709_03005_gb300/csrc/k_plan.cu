@@ -74,7 +74,7 @@ struct Plan {
     int W = 1, Kpad = 0, n_to = 0, S = 0, delta_col = 0;
     Stage<ClsTask> cls_tt, cls_tl2;
     Stage<PVTask> pv;
-    Stage<SWTask> sw, sws;             // sandwich: wide / narrow (nsp <= 16) states
+    Stage<SWTask> sw, sws;             // sandwich: lanes over records / over states
     Stage<TNTask> tn, tnr;
     Stage<IFTask> itf;
     Stage<ZTask> zero;
@@ -203,8 +203,10 @@ void fill_tasks(Plan &p) {
                                  P.pairs},
                          blocks_seg_rows8(A.ndet, B.ndet));
             p.pv.add(PVTask{I, da, db, P.pairs, P.n_pairs, P.val}, blocks_pair_values(P.n_pairs));
+            // lanes over the states for at most 16 of them (two or more record
+            // groups per warp), lanes over the records otherwise
             (B.ns <= 16 ? p.sws : p.sw).add(SWTask{P.pairs, P.rowptr, P.val, A.ndet, Cb, Cb_df, B.ns, P.W},
-                                            blocks_rows8(A.ndet));
+                                                blocks_rows8(A.ndet));
             const int ny = tn_ny(A.ns, B.ns);
             // E = C^T (H^N C'); S = C^T C within a group (identical determinants
             // only, hb_init rejects repeats) and zero between groups
@@ -221,8 +223,8 @@ void fill_tasks(Plan &p) {
             const int nc = P.n_chunks;
             const int64_t n_off = (int64_t)n_keys * nc;
             p.zero.add(ZTask{P.sort_off, n_off + 1}, blocks_zero(n_off + 1));
-            p.sort.add(SortTask{P.items, P.n_items, nc, n_keys, P.sort_off, P.sort_cur, P.order}, blocks_sort(P.n_items));
-            p.scan.add(ScanTask{P.sort_off, n_off, P.sort_cur}, 1);
+            p.sort.add(SortTask{P.items, P.n_items, nc, n_keys, P.sort_off, P.sort_cur, P.order}, blocks_sort(P.n_items, n_keys));
+            p.scan.add(ScanTask{P.sort_off, n_off, P.sort_cur, P.sort_part}, blocks_scan(n_off));
             const GTask gt{P.items, P.order, P.sort_off, nc, n_keys, Ca, Ca_df, A.ns, Cb, Cb_df, B.ns, ny, P.gamma};
             const int nout = A.ns * B.ns;
             bool warp = nout <= 64;
@@ -393,7 +395,6 @@ void bind_all(Plan &p) {
     stage_bind(p.drows, p.dev); stage_bind(p.l2, p.dev);
     for (auto &v : p.c4v) stage_bind(v.st, p.dev);
     p.d_cols = (const ExpCol *)(p.dev + p.off_cols);
-    p.scan.g.blocks = p.scan.g.n;     // one block per task
 }
 
 // Copy the packed tables through the pinned staging buffer (which is reused
@@ -604,7 +605,7 @@ int plan_autotune(Plan *p, cudaStream_t s, std::string *err) {
             float best = 0.0f, def_ms = 0.0f;
             std::pair<int, int> arg(-1, -1);
             std::vector<std::pair<int, int>> cand{{dnt, djt}};
-            for (int nt : {8, 16, 32})
+            for (int nt : {8, 16, 24, 32})
                 for (int jt : {32, 64, 128})
                     if (nt != dnt || jt != djt) cand.push_back({nt, jt});
             for (auto &c : cand) {

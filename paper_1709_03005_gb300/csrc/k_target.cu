@@ -287,7 +287,14 @@ __global__ void gdiag_reduce_kernel(const GDTask *__restrict__ tasks, const int6
 }
 
 // ------------------------------------------------- stable counting sort by key
-constexpr int kSortChunk = 4096;
+// Items per chunk of the counting sort: small enough that a short item list
+// still spreads over many warps, large enough that the (key, chunk) offset
+// table stays below about 2^20 entries.
+__host__ __device__ inline int sort_chunk_size(int64_t n_items, int n_keys) {
+    int c = 256;
+    while (c < 16384 && (n_items + c - 1) / c * (int64_t)n_keys > (1 << 20)) c <<= 1;
+    return c;
+}
 
 __global__ void zero_kernel(const ZTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     const int ti = task_of(blk, n_tasks, blockIdx.x);
@@ -305,60 +312,108 @@ __global__ void sort_hist_kernel(const SortTask *__restrict__ tasks, const int64
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const SortTask T = tasks[ti];
     const int chunk = (int)(blockIdx.x - blk[ti]);
-    const int64_t base = (int64_t)chunk * kSortChunk;
+    const int CS = sort_chunk_size(T.n_items, T.n_keys);
+    const int64_t base = (int64_t)chunk * CS;
     unsigned long long *hist = (unsigned long long *)T.off;
-    for (int i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
+    for (int i = threadIdx.x; i < CS; i += blockDim.x) {
         const int64_t k = base + i;
         if (k < T.n_items) atomicAdd(hist + 1 + (int64_t)T.items[k].key * T.nc + chunk, 1ull);
     }
 }
 
-// One block per task: x[0] = 0, x[1..n] := inclusive scan of x[1..n], and
-// copy[0..n-1] := x[0..n-1] (the exclusive offsets).
-__global__ void __launch_bounds__(1024) scan_grouped_kernel(const ScanTask *__restrict__ tasks, int n_tasks) {
-    __shared__ int64_t warp_sums[32];
-    __shared__ int64_t carry;
-    const ScanTask T = tasks[blockIdx.x];
-    const int64_t n = T.n;
+// Three-phase scan per task over segments of kScanSeg entries:
+//   x[0] = 0, x[1..n] := inclusive scan of x[1..n], copy[0..n-1] := x[0..n-1].
+// Phase 1: each segment's sum into part[seg]; phase 2 (one block per task):
+// exclusive scan of part in place; phase 3: each segment scanned with its
+// offset.  Integer sums, so the result is exact in any order.
+constexpr int kScanSeg = 4096;
+
+// block-wide inclusive scan of 4 values per thread (1024 threads); returns the
+// block total, v[] become inclusive prefixes within the block
+__device__ __forceinline__ int64_t block_scan4(int64_t (&v)[4], int64_t *warp_sums) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) { carry = 0; T.x[0] = 0; if (T.copy && n > 0) T.copy[0] = 0; }
-    __syncthreads();
-    int64_t *y = T.x + 1;
-    for (int64_t base = 0; base < n; base += 1024 * 4) {
-        int64_t v[4];
-        const int64_t i0 = base + tid * 4;
+    v[1] += v[0]; v[2] += v[1]; v[3] += v[2];
+    int64_t t = v[3];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = (i0 + k < n) ? y[i0 + k] : 0;
-        v[1] += v[0]; v[2] += v[1]; v[3] += v[2];
-        int64_t t = v[3];
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t u = __shfl_up_sync(0xffffffffu, t, off);
+        if (lane >= off) t += u;
+    }
+    if (lane == 31) warp_sums[warp] = t;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t s = warp_sums[lane];
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            int64_t u = __shfl_up_sync(0xffffffffu, t, off);
-            if (lane >= off) t += u;
+            const int64_t u = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane >= off) s += u;
         }
-        if (lane == 31) warp_sums[warp] = t;
-        __syncthreads();
-        if (warp == 0) {
-            int64_t s = warp_sums[lane];
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int64_t prefix = (warp > 0 ? warp_sums[warp - 1] : 0) + (t - v[3]);
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                int64_t u = __shfl_up_sync(0xffffffffu, s, off);
-                if (lane >= off) s += u;
-            }
-            warp_sums[lane] = s;
-        }
-        __syncthreads();
-        const int64_t prefix = carry + (warp > 0 ? warp_sums[warp - 1] : 0) + (t - v[3]);
+    for (int k = 0; k < 4; ++k) v[k] += prefix;
+    const int64_t total = warp_sums[31];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(1024) scan_sums_kernel(const ScanTask *__restrict__ tasks,
+                                                         const int64_t *__restrict__ blk, int n_tasks) {
+    __shared__ int64_t warp_sums[32];
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const ScanTask T = tasks[ti];
+    const int64_t seg = blockIdx.x - blk[ti];
+    const int64_t i0 = seg * kScanSeg + threadIdx.x * 4;
+    int64_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (i0 + k < T.n) ? T.x[1 + i0 + k] : 0;
+    const int64_t total = block_scan4(v, warp_sums);
+    if (threadIdx.x == 0) T.part[seg] = total;
+}
+
+__global__ void __launch_bounds__(1024) scan_part_kernel(const ScanTask *__restrict__ tasks, int n_tasks) {
+    __shared__ int64_t warp_sums[32];
+    const ScanTask T = tasks[blockIdx.x];
+    const int64_t nseg = (T.n + kScanSeg - 1) / kScanSeg;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nseg; base += 4096) {
+        const int64_t i0 = base + threadIdx.x * 4;
+        int64_t v[4], orig[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) orig[k] = v[k] = (i0 + k < nseg) ? T.part[i0 + k] : 0;
+        const int64_t total = block_scan4(v, warp_sums);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (i0 + k < n) {
-                y[i0 + k] = v[k] + prefix;
-                if (T.copy && i0 + k + 1 < n) T.copy[i0 + k + 1] = v[k] + prefix;
-            }
-        __syncthreads();
-        if (tid == 0) carry += warp_sums[31];
+            if (i0 + k < nseg) T.part[i0 + k] = carry + v[k] - orig[k];     // exclusive
+        carry += total;
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(1024) scan_apply_kernel(const ScanTask *__restrict__ tasks,
+                                                          const int64_t *__restrict__ blk, int n_tasks) {
+    __shared__ int64_t warp_sums[32];
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const ScanTask T = tasks[ti];
+    const int64_t seg = blockIdx.x - blk[ti];
+    const int64_t i0 = seg * kScanSeg + threadIdx.x * 4;
+    int64_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (i0 + k < T.n) ? T.x[1 + i0 + k] : 0;
+    block_scan4(v, warp_sums);
+    const int64_t off = T.part[seg];
+    if (seg == 0 && threadIdx.x == 0) {
+        T.x[0] = 0;
+        if (T.copy && T.n > 0) T.copy[0] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (i0 + k < T.n) {
+            T.x[1 + i0 + k] = v[k] + off;
+            if (T.copy && i0 + k + 1 < T.n) T.copy[i0 + k + 1] = v[k] + off;
+        }
 }
 
 // One warp per chunk walks its items in order, so equal keys keep their order.
@@ -369,8 +424,9 @@ __global__ void sort_scatter_kernel(const SortTask *__restrict__ tasks, const in
     const SortTask T = tasks[ti];
     const int chunk = (int)(blockIdx.x - blk[ti]);
     const int lane = threadIdx.x;
-    const int64_t base = (int64_t)chunk * kSortChunk;
-    for (int i0 = 0; i0 < kSortChunk; i0 += 32) {
+    const int CS = sort_chunk_size(T.n_items, T.n_keys);
+    const int64_t base = (int64_t)chunk * CS;
+    for (int i0 = 0; i0 < CS; i0 += 32) {
         const int64_t k = base + i0 + lane;
         const bool valid = k < T.n_items;
         const int key = valid ? T.items[k].key : -1 - lane;
@@ -568,15 +624,31 @@ __global__ void sandwich_small_df_kernel(const SWTask *__restrict__ tasks, const
     while (P < nsp) P <<= 1;
     const int G = 32 / P, g = lane / P, c = lane % P;
     const int64_t b = T.row_ptr[row], e = T.row_ptr[row + 1];
-    float ah = 0.0f, al = 0.0f;
-    if (c < nsp)
-        for (int64_t k = b + g; k < e; k += G) {
+    // four independent partial sums (records i = 0, 1, 2, 3 mod 4 of this
+    // lane's stride), combined in a fixed order
+    float h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, l[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (c < nsp) {
+        int64_t k = b + g;
+        for (; k + 3 * G < e; k += 4 * G) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t kk = k + u * G;
+                const float2 v = val[kk];
+                const float2 x = __ldg(T.Cp_df + (int64_t)T.pairs[kk].col * nsp + c);
+                df_fma(h[u], l[u], v.x, v.y, x.x, x.y);
+            }
+        }
+        for (int u = 0; k < e; k += G, ++u) {
             const float2 v = val[k];
             const float2 x = __ldg(T.Cp_df + (int64_t)T.pairs[k].col * nsp + c);
-            df_fma(ah, al, v.x, v.y, x.x, x.y);
+            df_fma(h[u], l[u], v.x, v.y, x.x, x.y);
         }
-    for (int off = 16; off >= P; off >>= 1) shfl_df_add(ah, al, off);
-    if (g == 0 && c < nsp) Wout[(int64_t)row * nsp + c] = make_float2(ah, al);
+    }
+    df_add2(h[0], l[0], h[1], l[1]);
+    df_add2(h[2], l[2], h[3], l[3]);
+    df_add2(h[0], l[0], h[2], l[2]);
+    for (int off = 16; off >= P; off >>= 1) shfl_df_add(h[0], l[0], off);
+    if (g == 0 && c < nsp) Wout[(int64_t)row * nsp + c] = make_float2(h[0], l[0]);
 }
 
 __global__ void tn_partial_df_kernel(const TNTask *__restrict__ tasks, const int64_t *__restrict__ blk,
@@ -734,8 +806,11 @@ int tn_ny(int ns, int nsp) { return (ns * nsp + 1023) / 1024; }
 int64_t blocks_tn_partial(int n_rows, int ns, int nsp) { return (int64_t)tn_chunks(n_rows) * tn_ny(ns, nsp); }
 int64_t blocks_tn_reduce(int ns, int nsp) { return (ns * nsp + 255) / 256; }
 int64_t blocks_zero(int64_t n) { return (n + 1023) / 1024; }
-int sort_chunks(int64_t n_items) { return (int)((n_items + kSortChunk - 1) / kSortChunk); }
-int64_t blocks_sort(int64_t n_items) { return sort_chunks(n_items); }
+int sort_chunks(int64_t n_items, int n_keys) {
+    const int c = sort_chunk_size(n_items, n_keys);
+    return (int)((n_items + c - 1) / c);
+}
+int64_t blocks_sort(int64_t n_items, int n_keys) { return sort_chunks(n_items, n_keys); }
 int64_t blocks_gamma(int n_keys, int ns, int nsp) { return (int64_t)n_keys * tn_ny(ns, nsp); }
 int64_t blocks_gamma_warp(int n_keys) { return (n_keys + 7) / 8; }
 size_t smem_stage(int ns, int nsp) { return sizeof(double) * stage_batch(ns, nsp) * (ns + nsp); }
@@ -804,10 +879,16 @@ int64_t blocks_gdiag_partial(int ndet, int n_to, int ns) {
 int64_t blocks_gdiag_reduce(int n_to, int ns) { return (int64_t)2 * n_to * ((ns * ns + 255) / 256); }
 size_t smem_gdiag(int ns) { return (sizeof(double) * ns + sizeof(int)) * stage_batch(ns + 1, 0); }
 
+int64_t blocks_scan(int64_t n) { return (n + kScanSeg - 1) / kScanSeg; }
+
 int g_scan(const Grouped<ScanTask> &g, cudaStream_t s) {
     if (g.n <= 0) return 0;
-    scan_grouped_kernel<<<g.n, 1024, 0, s>>>(g.tasks, g.n);
-    return 1;
+    // empty tasks write nothing: their x[0] is zeroed before the histogram
+    if (g.blocks <= 0) return 0;
+    scan_sums_kernel<<<(unsigned)g.blocks, 1024, 0, s>>>(g.tasks, g.blk, g.n);
+    scan_part_kernel<<<g.n, 1024, 0, s>>>(g.tasks, g.n);
+    scan_apply_kernel<<<(unsigned)g.blocks, 1024, 0, s>>>(g.tasks, g.blk, g.n);
+    return 3;
 }
 
 }  // namespace hb
