@@ -124,11 +124,13 @@ struct GDTask {         // diagonal gamma(p, p) of a group with itself (deg-0 re
 
 struct ATask {          // contracted coefficient rows A[(n,n')][k]
     const double *gamma, *S, *E;
+    const int64_t *off;       // gamma item offsets [key][chunk]: empty keys read as zero
+    int nc, same;
     const int32_t *nn;
     int n_nn, ns, nsp, n_to, cont_spin, Kpad;
     double e_core;
     double *A;
-    float2 *A_df;             // optional float-pair copy of A (mixed build)
+    float2 *A_df;             // float-pair copy of A (mixed build)
 };
 
 // One column of a merged expansion block: a state pair (n, n') of one group
@@ -213,7 +215,7 @@ int64_t blocks_scan(int64_t n);
 int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s);
 int g_gamma(const Grouped<GTask> &g, size_t smem, int dfloat, cudaStream_t s);
 int g_gamma_warp(const Grouped<GTask> &g, int dfloat, cudaStream_t s);         // ns * nsp <= 64
-int g_assemble(const Grouped<ATask> &g, cudaStream_t s);
+int g_assemble(const Grouped<ATask> &g, int dfloat, cudaStream_t s);
 // partial sums then their reduction into gamma[(s, p, p)] (after the item bins)
 int g_gdiag(const Grouped<GDTask> &partial, const Grouped<GDTask> &reduce, size_t smem, int dfloat, cudaStream_t s);
 int64_t blocks_gdiag_partial(int ndet, int n_to, int ns);

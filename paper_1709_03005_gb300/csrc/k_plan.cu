@@ -245,7 +245,8 @@ void fill_tasks(Plan &p) {
                 p.gdr.add(gd, blocks_gdiag_reduce(ctx->n_to, A.ns));
                 p.smem_gd = std::max(p.smem_gd, smem_gdiag(A.ns));
             }
-            p.asmb.add(ATask{P.gamma, P.S, P.E, P.nn, P.n_nn, A.ns, B.ns, ctx->n_to, ctx->cont_spin, ctx->Kpad,
+            p.asmb.add(ATask{P.gamma, P.S, P.E, P.sort_off, nc, P.same, P.nn, P.n_nn, A.ns, B.ns, ctx->n_to,
+                             ctx->cont_spin, ctx->Kpad,
                              ctx->e_core, P.A, p.precision == HB_MIXED ? P.A_df : nullptr},
                        P.n_nn);
             p.flops += 2.0 * (double)A.cn * B.cn * P.n_nn * ctx->K;
@@ -711,7 +712,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     L += g_gamma(p->gam.g, p->smem_gamma, DF, s);
     L += g_gamma_warp(p->gamw.g, DF, s);
     L += g_gdiag(p->gdp.g, p->gdr.g, p->smem_gd, DF, s);
-    L += g_assemble(p->asmb.g, s);
+    L += g_assemble(p->asmb.g, DF, s);
     rec(p->ev[1]);
     // expansion (Eq. 7): classes 1, 3, 5, 6, 7
     if (p->precision == HB_MIXED) {

@@ -278,7 +278,7 @@ __global__ void gdiag_reduce_kernel(const GDTask *__restrict__ tasks, const int6
             const float2 x = part[((int64_t)c * nsp2 + sp) * nout + t];
             df_add2(h, l, x.x, x.y);
         }
-        T.gamma[key * nout + t] = df_to_double(h, l);
+        reinterpret_cast<float2 *>(T.gamma)[key * nout + t] = make_float2(h, l);
     } else {
         double acc = 0.0;
         for (int c = 0; c < nc; ++c) acc += T.partial[((int64_t)c * nsp2 + sp) * nout + t];
@@ -289,10 +289,11 @@ __global__ void gdiag_reduce_kernel(const GDTask *__restrict__ tasks, const int6
 // ------------------------------------------------- stable counting sort by key
 // Items per chunk of the counting sort: small enough that a short item list
 // still spreads over many warps, large enough that the (key, chunk) offset
-// table stays below about 2^20 entries.
+// table is no larger than the item list (or 2^16 entries).
 __host__ __device__ inline int sort_chunk_size(int64_t n_items, int n_keys) {
     int c = 256;
-    while (c < 16384 && (n_items + c - 1) / c * (int64_t)n_keys > (1 << 20)) c <<= 1;
+    while (c < 16384 && (n_items + c - 1) / c * (int64_t)n_keys > (n_items > (1 << 16) ? n_items : (1 << 16)))
+        c <<= 1;
     return c;
 }
 
@@ -457,6 +458,7 @@ __global__ void gamma_kernel(const GTask *__restrict__ tasks, const int64_t *__r
     // with no items (nc == 0) both ends are off[0] = 0 and gamma is zero
     const int64_t b = T.off[(int64_t)key * T.nc];
     const int64_t e = T.off[(int64_t)(key + 1) * T.nc];
+    if (b == e) return;      // empty key: never written, the coefficient rows read it as zero
     const int nout = ns * nsp;
     // each thread keeps up to 4 outputs in registers
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -503,6 +505,7 @@ __global__ void gamma_warp_kernel(const GTask *__restrict__ tasks, const int64_t
     const int ns = T.ns, nsp = T.nsp, nout = ns * nsp;
     const int64_t b = T.off[(int64_t)key * T.nc];
     const int64_t e = T.off[(int64_t)(key + 1) * T.nc];
+    if (b == e) return;
     double acc0 = 0.0, acc1 = 0.0;
     const int t0 = lane, t1 = lane + 32;
     const int a0 = t0 / nsp, c0 = t0 % nsp, a1 = t1 / nsp, c1 = t1 % nsp;
@@ -524,6 +527,12 @@ __global__ void gamma_warp_kernel(const GTask *__restrict__ tasks, const int64_t
 //   k == Pt+n_to^2     : S            (multiplies h_jj')
 //   k == Pt+n_to^2+1   : E + e_core S (multiplies delta_jj')
 //   k >= K             : 0
+// A key with no items was never written and reads as zero, except the
+// diagonal keys of a group with itself (written by the masked C^T C).
+// FP64 build: gamma and A in FP64.  Mixed build: gamma as (hi, lo) float
+// pairs, the sums in double-float, A written as float pairs (A_df, read by the
+// j == j' rows) and as FP64 (read by the slicing).
+template <bool DF>
 __global__ void assemble_kernel(const ATask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const ATask T = tasks[ti];
@@ -533,30 +542,48 @@ __global__ void assemble_kernel(const ATask *__restrict__ tasks, const int64_t *
     const int ns = T.ns, nsp = T.nsp, n_to = T.n_to, Kpad = T.Kpad;
     const int nout = ns * nsp, sidx = n * nsp + np;
     const int Pt = n_to * (n_to + 1) / 2, nt2 = n_to * n_to;
+    auto present = [&](int key, bool diag) -> bool {
+        return (diag && T.same) || T.off[(int64_t)key * T.nc] != T.off[(int64_t)(key + 1) * T.nc];
+    };
     for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
         double v = 0.0;
+        float vh = 0.0f, vl = 0.0f;
+        auto add_key = [&](int key, bool diag, bool neg) {
+            if (!present(key, diag)) return;
+            if (DF) {
+                const float2 g = reinterpret_cast<const float2 *>(T.gamma)[(int64_t)key * nout + sidx];
+                df_add2(vh, vl, neg ? -g.x : g.x, neg ? -g.y : g.y);
+            } else {
+                const double g = T.gamma[(int64_t)key * nout + sidx];
+                v += neg ? -g : g;
+            }
+        };
         if (k < Pt) {
             // unpack k = r(r+1)/2 + s
-            int r = (int)((sqrt(8.0 * k + 1.0) - 1.0) * 0.5);
+            int r = (int)((sqrtf(8.0f * (float)k + 1.0f) - 1.0f) * 0.5f);
             while ((r + 1) * (r + 2) / 2 <= k) ++r;
             while (r * (r + 1) / 2 > k) --r;
             const int s = k - r * (r + 1) / 2;
             for (int sp = 0; sp < 2; ++sp) {
-                v += T.gamma[((int64_t)sp * nt2 + r * n_to + s) * nout + sidx];
-                if (r != s) v += T.gamma[((int64_t)sp * nt2 + s * n_to + r) * nout + sidx];
+                add_key(sp * nt2 + r * n_to + s, r == s, false);
+                if (r != s) add_key(sp * nt2 + s * n_to + r, false, false);
             }
         } else if (k < Pt + nt2) {
             const int pq = k - Pt;
-            v = -T.gamma[((int64_t)T.cont_spin * nt2 + pq) * nout + sidx];
+            add_key(T.cont_spin * nt2 + pq, pq / n_to == pq % n_to, true);
         } else if (k == Pt + nt2) {
-            v = T.S[sidx];
+            if (DF) { const float h = (float)T.S[sidx]; vh = h; vl = (float)(T.S[sidx] - (double)h); }
+            else v = T.S[sidx];
         } else if (k == Pt + nt2 + 1) {
-            v = T.E[sidx] + T.e_core * T.S[sidx];
+            const double x = T.E[sidx] + T.e_core * T.S[sidx];
+            if (DF) { const float h = (float)x; vh = h; vl = (float)(x - (double)h); }
+            else v = x;
         }
-        T.A[(int64_t)t * Kpad + k] = v;
-        if (T.A_df) {
-            const float h = (float)v;
-            T.A_df[(int64_t)t * Kpad + k] = make_float2(h, (float)(v - (double)h));
+        if (DF) {
+            T.A_df[(int64_t)t * Kpad + k] = make_float2(vh, vl);
+            T.A[(int64_t)t * Kpad + k] = df_to_double(vh, vl);
+        } else {
+            T.A[(int64_t)t * Kpad + k] = v;
         }
     }
 }
@@ -721,6 +748,7 @@ __global__ void gamma_df_kernel(const GTask *__restrict__ tasks, const int64_t *
     float2 *cb = smf + kItemBatch * ns;       // [kItemBatch][nsp]
     const int64_t b = T.off[(int64_t)key * T.nc];
     const int64_t e = T.off[(int64_t)(key + 1) * T.nc];
+    if (b == e) return;
     const int nout = ns * nsp;
     float ah[4] = {0.0f, 0.0f, 0.0f, 0.0f}, al[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int64_t i0 = b; i0 < e; i0 += kItemBatch) {
@@ -757,7 +785,7 @@ __global__ void gamma_df_kernel(const GTask *__restrict__ tasks, const int64_t *
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int t = by * 4 * blockDim.x + u * blockDim.x + threadIdx.x;
-        if (t < nout) T.gamma[(int64_t)key * nout + t] = df_to_double(ah[u], al[u]);
+        if (t < nout) reinterpret_cast<float2 *>(T.gamma)[(int64_t)key * nout + t] = make_float2(ah[u], al[u]);
     }
 }
 
@@ -771,6 +799,7 @@ __global__ void gamma_warp_df_kernel(const GTask *__restrict__ tasks, const int6
     const int ns = T.ns, nsp = T.nsp, nout = ns * nsp;
     const int64_t b = T.off[(int64_t)key * T.nc];
     const int64_t e = T.off[(int64_t)(key + 1) * T.nc];
+    if (b == e) return;
     float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
     const int t0 = lane, t1 = lane + 32;
     const int a0 = t0 / nsp, c0 = t0 % nsp, a1 = t1 / nsp, c1 = t1 % nsp;
@@ -794,8 +823,9 @@ __global__ void gamma_warp_df_kernel(const GTask *__restrict__ tasks, const int6
             df_norm(h1, l1);
         }
     }
-    if (t0 < nout) T.gamma[(int64_t)key * nout + t0] = df_to_double(h0, l0);
-    if (t1 < nout) T.gamma[(int64_t)key * nout + t1] = df_to_double(h1, l1);
+    float2 *g = reinterpret_cast<float2 *>(T.gamma);
+    if (t0 < nout) g[(int64_t)key * nout + t0] = make_float2(h0, l0);
+    if (t1 < nout) g[(int64_t)key * nout + t1] = make_float2(h1, l1);
 }
 
 }  // namespace
@@ -856,7 +886,10 @@ int g_gamma_warp(const Grouped<GTask> &g, int dfloat, cudaStream_t s) {
     if (dfloat) HB_GROUPED(gamma_warp_df_kernel, g, 256, 0, s);
     HB_GROUPED(gamma_warp_kernel, g, 256, 0, s);
 }
-int g_assemble(const Grouped<ATask> &g, cudaStream_t s) { HB_GROUPED(assemble_kernel, g, 256, 0, s); }
+int g_assemble(const Grouped<ATask> &g, int dfloat, cudaStream_t s) {
+    if (dfloat) HB_GROUPED(assemble_kernel<true>, g, 256, 0, s);
+    HB_GROUPED(assemble_kernel<false>, g, 256, 0, s);
+}
 
 int g_gdiag(const Grouped<GDTask> &partial, const Grouped<GDTask> &reduce, size_t smem, int dfloat, cudaStream_t s) {
     int L = 0;
