@@ -98,9 +98,8 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
     if (!std::isfinite(p->e_core)) return fail(ctx, HB_ERR_INVALID_ARG, "e_core is not finite");
     if (o && o->split_tile != 0 && (o->split_tile < 3 || o->split_tile > 5))
         return fail(ctx, HB_ERR_INVALID_ARG, "split_tile must be 0, 3, 4 or 5");
-    if (o && o->class4_states != 0 && o->class4_states != 8 && o->class4_states != 16 && o->class4_states != 24 &&
-        o->class4_states != 32)
-        return fail(ctx, HB_ERR_INVALID_ARG, "class4_states must be 0, 8, 16, 24 or 32");
+    if (o && o->class4_states != 0 && (o->class4_states < 8 || o->class4_states > 64 || o->class4_states % 8))
+        return fail(ctx, HB_ERR_INVALID_ARG, "class4_states must be 0 or a multiple of 8 up to 64");
     if (o && o->class4_threads != 0 && o->class4_threads != 32 && o->class4_threads != 64 && o->class4_threads != 128)
         return fail(ctx, HB_ERR_INVALID_ARG, "class4_threads must be 0, 32, 64 or 128");
     const int W = p->n_words, nw = 2 * W;

@@ -223,9 +223,10 @@ int64_t blocks_gdiag_reduce(int n_to, int ns);
 size_t smem_gdiag(int ns);
 int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s);
 // dfloat = 0: FP64 (128 threads, 32 states a pass); 1: double-float with
-// ns_tile states a pass (8, 16, 24 or 32) and jt threads a block (32, 64 or 128)
+// ns_tile states a pass (a multiple of 8 up to 64) and jt threads a block (32, 64 or 128)
 int g_class4(const Grouped<C4Task> &g, int W, int dfloat, int ns_tile, int jt, cudaStream_t s);
 void class4_shape(int ns, int cn, int *ns_tile, int *jt);
+
 
 // block counts of one task of each stage (host side)
 int64_t blocks_rows8(int64_t rows);                 // one warp per row, 8 warps a block

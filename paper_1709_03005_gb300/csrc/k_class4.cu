@@ -258,9 +258,12 @@ int64_t blocks_class4(int n_l2, int cn, int jt) { return cn > 0 ? (int64_t)n_l2 
 // the fewest passes over the states, then the smallest tile; the continuum
 // tile that leaves the fewest idle threads (ties to the larger block).
 void class4_shape(int ns, int cn, int *ns_tile, int *jt) {
+    // passes of at most 32 states (larger tiles cost more in registers and
+    // occupancy than the prototype values recomputed per pass), the state
+    // tile rounded up to a multiple of 8
     const int passes = (ns + 31) / 32;
     const int need = (ns + passes - 1) / passes;
-    *ns_tile = need <= 8 ? 8 : (need <= 16 ? 16 : (need <= 24 ? 24 : 32));
+    *ns_tile = need <= 8 ? 8 : (need + 7) / 8 * 8;
     int best = 128;
     int64_t best_idle = (int64_t)((cn + 127) / 128) * 128 - cn;
     for (int t : {64, 32}) {
@@ -292,7 +295,11 @@ int g_class4(const Grouped<C4Task> &g, int W, int dfloat, int ns_tile, int jt, c
         case 8: class4_df_kernel<WW, 8><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;                 \
         case 16: class4_df_kernel<WW, 16><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
         case 24: class4_df_kernel<WW, 24><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
-        default: class4_df_kernel<WW, 32><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
+        case 32: class4_df_kernel<WW, 32><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
+        case 40: class4_df_kernel<WW, 40><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
+        case 48: class4_df_kernel<WW, 48><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
+        case 56: class4_df_kernel<WW, 56><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
+        default: class4_df_kernel<WW, 64><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
     }
     switch (W) {
         case 1: HB_C4DF(1); break;

@@ -108,3 +108,24 @@ def test_mixed_deterministic():
     torch.cuda.synchronize()
     assert torch.equal(x, b2["Hcc"])
     H.close()
+
+
+@pytest.mark.parametrize("n_state", [7, 20, 50])
+def test_class4_wide_continuum(n_state):
+    """Class 4 (Eq. 5) of the mixed build (double-float) for 80 continuum
+    orbitals and 7, 20 or 50 states (one pass over the states): the FP64
+    tolerance against the oracle, per row scale."""
+    from paper_1709_03005_gb300 import hb
+    import torch
+    P = synth.make_config("mid", n_co=80, n_state=n_state, n_l2=300, seed=21 + n_state)
+    o = coracle.Oracle(P)
+    H = hb.Hamiltonian(P)
+    b, _ = H.build(hb.HB_MIXED)
+    torch.cuda.synchronize()
+    Hlc = b["Hlc"].cpu().numpy()
+    H.close()
+    rows = o.class4_rows(0, P.n_l2)
+    scale = np.maximum(np.abs(rows), np.abs(rows).max(axis=1, keepdims=True))
+    worst = float((np.abs(Hlc - rows) / np.maximum(scale, 1e-300)).max())
+    assert np.all(np.abs(Hlc - rows) <= 1e-12 * scale), worst
+    print(f"class 4, {n_state} states: worst |d| / row scale {worst:.2e}")
