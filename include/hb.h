@@ -71,6 +71,10 @@ enum {
 
 enum { HB_FP64 = 0, HB_MIXED = 1 };
 enum { HB_PRECOND_DIAG = 0, HB_PRECOND_MLP = 1 };
+/* OR'ed into hb_diag's precond: the block products H V on the tensor cores
+   in split-bf16 form (7 bits a slice, 6 slices a value, exact FP32 chunks);
+   the Rayleigh-Ritz projection and the orthogonalisation stay FP64. */
+enum { HB_DIAG_TENSOR = 0x100 };
 enum { HB_SPIN_ALPHA = 0, HB_SPIN_BETA = 1 };
 
 typedef struct hb_ctx hb_ctx;
@@ -185,7 +189,8 @@ int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *out, hb_sta
    to ||H x - lambda x||_2 <= tol for each pair.  evals: host [k]; evecs:
    device [dim][k] row-major or NULL; v0: device [dim][k] start vectors or
    NULL (unit vectors at the smallest diagonal entries).  precond:
-   HB_PRECOND_DIAG, or HB_PRECOND_MLP after hb_mlp_set.  Returns
+   HB_PRECOND_DIAG, or HB_PRECOND_MLP after hb_mlp_set, optionally OR
+   HB_DIAG_TENSOR (block products on the tensor cores).  Returns
    HB_ERR_NOT_CONVERGED after max_iter iterations (evals then hold the current
    Ritz values). */
 int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, int32_t max_iter,

@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "hb_api_internal.cuh"
+#include "hb_split.cuh"
 
 namespace hb {
 
@@ -17,6 +18,13 @@ struct DiagWork {
     int32_t *idx = nullptr;
     double *HlcT = nullptr;       // class-4 block transposed (Dc x n_l2)
     const double *HlcT_src = nullptr;
+    // block products on the tensor cores: slices of [Hcc | Hlc^T] (rows of the
+    // continuum block), of Hlc (rows of the L2 block) and of the vectors
+    bool tc = false;
+    int S = 6;
+    DenseOperand A1, A2, Xs;
+    float2 *part = nullptr;
+    int *err = nullptr;
 };
 
 void small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V);

@@ -29,3 +29,23 @@ int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const h
 int64_t blocks_diag_rows(int j_lo, int j_hi, int n_nn);
 int diag_rows_ny(int n_nn);
 int g_diag_rows(const hb::Grouped<hb::DRTask> &g, cudaStream_t s);
+
+// Dense split-precision GEMM (Davidson block products).  An operand holds bf16
+// slices of R rows over Kpad columns, [S][Kpad/64][R][64], and its tensor map.
+struct DenseOperand {
+    void *buf = nullptr;
+    int64_t R = 0;
+    int Kpad = 0, planes = 0;
+    CUtensorMap tm;
+};
+int dense_operand_alloc(int S, int64_t R, int Kpad, DenseOperand *op, std::string *err);
+void dense_operand_free(DenseOperand *op);
+// rows of [X1 | X2] (X2 may be null) into the operand's slices
+void dense_operand_fill(const DenseOperand &op, int S, const double *X1, int64_t ld1, int K1, const double *X2,
+                        int64_t ld2, int K2, int64_t rows, cudaStream_t s);
+// splits of the K blocks over the grid for an M x N product (and K blocks per split)
+int dense_splits(int64_t M, int64_t N, int kb_total, int *kb_per_split);
+// Y[n][m] (row stride ldy) = sum_k A[m][k] B[n][k] over kb_total K blocks of 64;
+// part: scratch of dense_splits(...) * M * N float pairs.  Returns launches.
+int dense_split_gemm(int S, const DenseOperand &A, int64_t M, const DenseOperand &B, int64_t N, int kb_total,
+                     float2 *part, double *Y, int64_t ldy, int *err, cudaStream_t s);

@@ -372,6 +372,24 @@ struct Ops {
     // Y[0:q] = H X[0:q], vectors stored as rows of length ld
     void matvec(const double *X, double *Y, int q, int64_t ld) {
         if (q <= 0) return;
+        if (w->tc) {
+            // split-bf16 tensor-core products: Y_c = [Hcc | Hlc^T] X, Y_l = Hlc X_c
+            // (+ the L2 block in FP64 below)
+            dense_operand_fill(w->Xs, w->S, X, ld, (int)n, nullptr, 0, 0, q, s);
+            ++launches;
+            if (Dc > 0) launches += dense_split_gemm(w->S, w->A1, Dc, w->Xs, q, w->A1.planes, w->part, Y, ld, w->err, s);
+            if (nl > 0) {
+                if (Dc > 0) {
+                    launches += dense_split_gemm(w->S, w->A2, nl, w->Xs, q, w->A2.planes, w->part, Y + Dc, ld, w->err, s);
+                } else {
+                    for (int j = 0; j < q; ++j) cudaMemsetAsync(Y + (int64_t)j * ld, 0, sizeof(double) * nl, s);
+                }
+                spmm_csr_kernel<<<(unsigned)((nl + 7) / 8), 256, 0, s>>>(H->l2_row_ptr, H->l2_col, H->l2_val, (int)nl,
+                                                                         X + Dc, ld, q, Y + Dc, ld);
+                ++launches;
+            }
+            return;
+        }
         if (Dc > 0) {
             dim3 g((unsigned)((Dc + GM - 1) / GM), (q + GN - 1) / GN);
             gemm_nt_kernel<<<g, 256, 0, s>>>(H->Hcc, Dc, X, ld, (int)Dc, q, (int)Dc, Y, ld, 0);
@@ -424,6 +442,51 @@ static int diag_fail(hb_ctx *ctx, int code, const std::string &m) {
     return code;
 }
 
+static void release_tensor_products(DiagWork *w) {
+    dense_operand_free(&w->A1);
+    dense_operand_free(&w->A2);
+    dense_operand_free(&w->Xs);
+    if (w->part) cudaFree(w->part);
+    if (w->err) cudaFree(w->err);
+    w->part = nullptr;
+    w->err = nullptr;
+    w->tc = false;
+}
+
+// Slices of [Hcc | Hlc^T] and of Hlc (fixed during the solve), the vector
+// slice buffer for up to mmax vectors and the split-K scratch.
+static int setup_tensor_products(hb_ctx *ctx, const hb_blocks *H, DiagWork *w, int mmax, cudaStream_t s) {
+    release_tensor_products(w);
+    const int64_t n = ctx->dim, Dc = ctx->Dc, nl = ctx->n_l2;
+    const int S = ctx->split_slices >= 2 && ctx->split_slices <= 6 ? ctx->split_slices : 6;
+    w->S = S;
+    std::string err;
+    const int K1 = (int)((n + 63) / 64 * 64), K2 = (int)((Dc + 63) / 64 * 64);
+    int rc = dense_operand_alloc(S, mmax, K1, &w->Xs, &err);
+    if (rc == HB_OK && Dc > 0) rc = dense_operand_alloc(S, Dc, K1, &w->A1, &err);
+    if (rc == HB_OK && Dc > 0 && nl > 0) rc = dense_operand_alloc(S, nl, K2, &w->A2, &err);
+    size_t part = 1;
+    int per = 0;
+    if (Dc > 0) part = std::max(part, (size_t)dense_splits(Dc, 1, K1 / 64, &per) * mmax * Dc);
+    if (Dc > 0 && nl > 0) part = std::max(part, (size_t)dense_splits(nl, 1, K2 / 64, &per) * mmax * nl);
+    cudaError_t e = cudaSuccess;
+    if (rc == HB_OK) e = cudaMalloc(&w->part, sizeof(float2) * part);
+    if (rc == HB_OK && e == cudaSuccess) e = cudaMalloc(&w->err, sizeof(int));
+    if (rc == HB_OK && e == cudaSuccess) e = cudaMemsetAsync(w->err, 0, sizeof(int), s);
+    if (rc == HB_OK && e != cudaSuccess) {
+        rc = HB_ERR_OOM;
+        err = std::string("Davidson tensor-core scratch: ") + cudaGetErrorString(e);
+    }
+    if (rc != HB_OK) {
+        release_tensor_products(w);
+        return diag_fail(ctx, rc, err);
+    }
+    if (Dc > 0) dense_operand_fill(w->A1, S, H->Hcc, Dc, (int)Dc, nl > 0 ? w->HlcT : nullptr, nl, (int)nl, Dc, s);
+    if (Dc > 0 && nl > 0) dense_operand_fill(w->A2, S, H->Hlc, Dc, (int)Dc, nullptr, 0, 0, nl, s);
+    w->tc = true;
+    return HB_OK;
+}
+
 int hb::ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t s) {
     DiagWork *w = (DiagWork *)ctx->diag;
     const int64_t n = ctx->dim;
@@ -471,6 +534,10 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
     if ((ctx->Dc > 0 && !H->Hcc) || (ctx->Dc > 0 && ctx->n_l2 > 0 && !H->Hlc) ||
         (ctx->n_l2 > 0 && (!H->l2_row_ptr || !H->l2_col || !H->l2_val)))
         return diag_fail(ctx, HB_ERR_INVALID_ARG, "matrix blocks are NULL");
+    const bool tensor = (precond & HB_DIAG_TENSOR) != 0;
+    precond &= ~HB_DIAG_TENSOR;
+    if (precond != HB_PRECOND_DIAG && precond != HB_PRECOND_MLP)
+        return diag_fail(ctx, HB_ERR_INVALID_ARG, "precond must be HB_PRECOND_DIAG or HB_PRECOND_MLP (| HB_DIAG_TENSOR)");
     if (precond == HB_PRECOND_MLP && !ctx->mlp)
         return diag_fail(ctx, HB_ERR_INVALID_ARG, "HB_PRECOND_MLP without weights (hb_mlp_set)");
     cudaStream_t s = (cudaStream_t)stream;
@@ -489,6 +556,12 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         dim3 g((unsigned)((ctx->Dc + 31) / 32), (unsigned)((ctx->n_l2 + 31) / 32));
         transpose_kernel<<<g, dim3(32, 8), 0, s>>>(H->Hlc, ctx->n_l2, ctx->Dc, w->HlcT);
         ++ops.launches;
+    }
+    if (tensor) {
+        // slices of the fixed operands, once per call
+        rc = setup_tensor_products(ctx, H, w, mmax, s);
+        if (rc != HB_OK) return rc;
+        ops.launches += 2;
     }
     diag_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(H->Hcc, ctx->Dc, H->l2_row_ptr, H->l2_col, H->l2_val,
                                                              ctx->n_l2, w->d);
@@ -655,6 +728,12 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
     cudaEventDestroy(e1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return diag_fail(ctx, HB_ERR_CUDA, std::string("Davidson: ") + cudaGetErrorString(e));
+    if (w->tc) {
+        int word = 0;
+        cudaMemcpy(&word, w->err, sizeof(int), cudaMemcpyDeviceToHost);
+        release_tensor_products(w);
+        if (word) return diag_fail(ctx, HB_ERR_TIMEOUT, "Davidson tensor-core product gave up waiting");
+    }
     if (st) {
         memset(st, 0, sizeof(*st));
         st->ms_total = ms;
@@ -671,6 +750,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
 void hb::release_diag(hb_ctx *ctx) {
     DiagWork *w = (DiagWork *)ctx->diag;
     if (!w) return;
+    release_tensor_products(w);
     for (void *p : {(void *)w->V, (void *)w->AV, (void *)w->X, (void *)w->AX, (void *)w->W2, (void *)w->d, (void *)w->partial,
                     (void *)w->small, (void *)w->theta, (void *)w->idx, (void *)w->HlcT})
         if (p) cudaFree(p);

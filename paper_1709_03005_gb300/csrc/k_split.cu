@@ -16,9 +16,9 @@
 // stays below 2^24 units, so the FP32 accumulation is exact.  Separate TMEM
 // accumulators hold s = 0, 1, 2 and one holds s >= 3 (its rounding is below
 // 2^-45 of the result).  The epilogue drains the accumulators after each
-// chunk; the MMAs of the next chunk wait for that drain.  After each chunk the epilogue warps fold the four
-// accumulators into a double-float running sum (TwoSum), and at the end write
-// it as FP64.  Pairs with i + l >= S are dropped (below 2^-7S relative).
+// chunk; the MMAs of the next chunk wait for that drain.  After each chunk the
+// epilogue warps fold the four accumulators into a double-float running sum
+// (TwoSum for s <= 2), and at the end write it as FP64.  Pairs with i + l >= S are dropped (below 2^-7S relative).
 //
 // Kernel structure (one CTA per 128 x 128 output tile, 10 warps):
 //   warp 0  TMA producer: per 64-wide K block and slice, one panel tile
@@ -36,6 +36,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "hb_api_internal.cuh"
@@ -157,6 +158,35 @@ __device__ __forceinline__ bool mma_block(uint64_t *full_bar, uint64_t *empty_ba
     return true;
 }
 
+// Fold one chunk's accumulators (EPI_COLS columns of this thread's TMEM lane,
+// accumulator s at column offset s * stride) into the double-float sums:
+// s = 0, 1, 2 by TwoSum (2^-14 of the result for s = 2 still needs it to keep
+// the low word below an ulp of the high one), s >= 3 (2^-21) into the low word.
+template <int S>
+__device__ __forceinline__ void drain_chunk(uint32_t tbase, int stride, float (&hi)[EPI_COLS], float (&lo)[EPI_COLS]) {
+    constexpr int n_acc = S < 4 ? S : 4;       // accumulators written by the MMAs
+#pragma unroll
+    for (int c0 = 0; c0 < EPI_COLS; c0 += 16) {
+        float v[16], w[16];
+        tmem_ld16(tbase + c0, v);
+        if (n_acc > 1) tmem_ld16(tbase + stride + c0, w);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            df_add(hi[c0 + i], lo[c0 + i], v[i]);
+            if (n_acc > 1) df_add(hi[c0 + i], lo[c0 + i], w[i]);
+        }
+        if (n_acc > 2) {
+            tmem_ld16(tbase + 2 * stride + c0, v);
+            if (n_acc > 3) tmem_ld16(tbase + 3 * stride + c0, w);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                df_add(hi[c0 + i], lo[c0 + i], v[i]);
+                if (n_acc > 3) lo[c0 + i] = __fadd_rn(lo[c0 + i], w[i]);
+            }
+        }
+    }
+}
+
 template <int S>
 __global__ void __launch_bounds__(NTHREADS, 1)
 split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_constant__ CUtensorMap tm_coef,
@@ -272,31 +302,11 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
 #pragma unroll
         for (int c = 0; c < EPI_COLS; ++c) { hi[c] = 0.0f; lo[c] = 0.0f; }
         bool ok = true;
-        const int n_acc = S < 4 ? S : 4;         // accumulators written by the MMAs
         for (int c = 0; c < nchunks && ok; ++c) {
             ok = mbar_wait(acc_full, c & 1, err, 6);
             if (!ok) break;
             tc_fence_after();
-            // s = 0 and s = 1 need the exact TwoSum; s = 2 and s >= 3 are 2^-14
-            // and 2^-21 of the result, so their FP32 sum joins the low word
-#pragma unroll
-            for (int c0 = 0; c0 < EPI_COLS; c0 += 16) {
-                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + col0 + c0;
-                float v[16], w[16];
-                tmem_ld16(tbase, v);
-                if (n_acc > 1) tmem_ld16(tbase + BN, w);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    df_add(hi[c0 + i], lo[c0 + i], v[i]);
-                    if (n_acc > 1) df_add(hi[c0 + i], lo[c0 + i], w[i]);
-                }
-                if (n_acc > 2) {
-                    tmem_ld16(tbase + 2 * BN, v);
-                    if (n_acc > 3) tmem_ld16(tbase + 3 * BN, w);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) lo[c0 + i] = __fadd_rn(lo[c0 + i], n_acc > 3 ? __fadd_rn(v[i], w[i]) : v[i]);
-                }
-            }
+            drain_chunk<S>(tmem + ((uint32_t)(q * 32) << 16) + col0, BN, hi, lo);
             tc_fence_before();
             mbar_arrive(acc_empty);
         }
@@ -324,6 +334,201 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ------------------------------------------- dense split GEMM (Davidson)
+// part[z][n][m] = sum over the K blocks of split z of A[m][k] X[n][k], for the
+// Davidson block products H V: A (rows m of the Hamiltonian) and X (rows n =
+// the block's vectors) as bf16 slices with their row exponents folded in,
+// the same exact slice-pair accumulation as the expansion kernel; the K
+// dimension is split over blockIdx.z (one exact chunk each) and the
+// double-float partials are summed in a fixed order by dense_reduce_kernel.
+struct DenseArgs {
+    int M, N;                  // rows of A and of X
+    int kb_total, kb_per_split;
+    int a_planes, b_planes;    // K blocks per slice plane of A and of X
+    float2 *part;              // [nsplit][N][M]
+    int *err;
+};
+
+template <int S>
+__global__ void __launch_bounds__(NTHREADS, 1)
+dense_split_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b, DenseArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *slots = base;
+    uint64_t *full_bar = (uint64_t *)(base + S * SLOT);
+    uint64_t *empty_bar = full_bar + MAXS;
+    uint64_t *acc_full = empty_bar + MAXS;
+    uint64_t *acc_empty = acc_full + 1;
+    uint64_t *final_bar = acc_empty + 1;
+    uint32_t *tmem_slot = (uint32_t *)(final_bar + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, z = blockIdx.z;
+    const int kb0 = z * a.kb_per_split;
+    const int kb1 = min(a.kb_total, kb0 + a.kb_per_split);
+    const int nkb = kb1 - kb0;
+    const int kb_per_chunk = KCHUNK / BKB;
+    const int nchunks = (nkb + kb_per_chunk - 1) / kb_per_chunk;
+    int *err = a.err;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < MAXS; ++i) { mbar_init(&full_bar[i], 1); mbar_init(&empty_bar[i], 1); }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, EPI_THREADS);
+        mbar_init(final_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (warp == 0) {
+        // TMA producer (kk: K block within this split, for slot parity and phases)
+        if (lane == 0) {
+            int kk = 0;
+            bool ok = true;
+            for (; kk < nkb && ok; ++kk) {
+                const int kb = kb0 + kk;
+                for (int t = 0; t < S && ok; ++t) {
+                    const int sl = (kk & 1) ? slot_of<S>(1, t) : t;
+                    if (kk > 0) ok = mbar_wait(&empty_bar[sl], (kk - 1) & 1, err, 1);
+                    if (!ok) break;
+                    uint8_t *sA = slots + sl * SLOT;
+                    mbar_expect_tx(&full_bar[sl], (uint32_t)SLOT);
+                    tma_load_3d(sA, &tm_a, &full_bar[sl], 0, m0, t * a.a_planes + kb);
+                    tma_load_3d(sA + A_TILE, &tm_b, &full_bar[sl], 0, n0, t * a.b_planes + kb);
+                }
+            }
+            if (kk > 0)
+                for (int sl = 0; sl < S; ++sl) mbar_wait(&full_bar[sl], (kk - 1) & 1, err, 2);
+        }
+    } else if (warp == 1) {
+        // MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc_bf16(BM, BN);
+            const uint64_t desc0 = smem_desc_sw128(smem_u32(slots));
+            bool ok = true;
+            int kk = 0;
+            for (int c = 0; c < nchunks && ok; ++c) {
+                if (c > 0) ok = mbar_wait(acc_empty, (c - 1) & 1, err, 3);
+                if (!ok) break;
+                tc_fence_after();
+                const int kk_end = min(nkb, (c + 1) * kb_per_chunk);
+                uint32_t fresh = 0xFu;
+                for (; kk < kk_end && ok; ++kk) {
+                    if (kk & 1) ok = mma_block<S, 1>(full_bar, empty_bar, 1u, tmem, desc0, idesc, fresh, err);
+                    else ok = mma_block<S, 0>(full_bar, empty_bar, 0u, tmem, desc0, idesc, fresh, err);
+                }
+                if (ok) mma_commit(acc_full);
+            }
+            mma_commit(final_bar);
+            mbar_wait(final_bar, 0, err, 5);
+        }
+    } else {
+        // epilogue: rows m of A = TMEM lanes, columns = vectors n
+        const int ew = warp - 2;
+        const int q = warp & 3;
+        const int col0 = (ew >> 2) * EPI_COLS;
+        const int row = q * 32 + lane;
+        float hi[EPI_COLS], lo[EPI_COLS];
+#pragma unroll
+        for (int c = 0; c < EPI_COLS; ++c) { hi[c] = 0.0f; lo[c] = 0.0f; }
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+            ok = mbar_wait(acc_full, c & 1, err, 6);
+            if (!ok) break;
+            tc_fence_after();
+            drain_chunk<S>(tmem + ((uint32_t)(q * 32) << 16) + col0, BN, hi, lo);
+            tc_fence_before();
+            mbar_arrive(acc_empty);
+        }
+        const int m = m0 + row;
+        if (ok && m < a.M) {
+            float2 *out = a.part + (int64_t)z * a.N * a.M + m;
+#pragma unroll
+            for (int c = 0; c < EPI_COLS; ++c) {
+                const int n = n0 + col0 + c;
+                if (n < a.N) out[(int64_t)n * a.M] = make_float2(hi[c], lo[c]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// Y[n][m] (row stride ldy) = sum over the splits, in order, of part[z][n][m].
+__global__ void dense_reduce_kernel(const float2 *__restrict__ part, int nsplit, int M, int N, double *__restrict__ Y,
+                                    int64_t ldy) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)M * N) return;
+    const int n = (int)(t / M), m = (int)(t % M);
+    float h = 0.0f, l = 0.0f;
+    for (int z = 0; z < nsplit; ++z) {
+        const float2 x = part[((int64_t)z * N + n) * M + m];
+        df_add2(h, l, x.x, x.y);
+    }
+    Y[(int64_t)n * ldy + m] = df_to_double(h, l);
+}
+
+// Rows of [X1 | X2] (K1 then K2 entries, row strides ld1, ld2; X2 may be
+// absent) into bf16 slices [S][Kpad/64][R][64], one warp per row, the same
+// digits as slice_row.
+__global__ void slice_rows2_kernel(const double *__restrict__ X1, int64_t ld1, int K1, const double *__restrict__ X2,
+                                   int64_t ld2, int K2, int64_t rows, int Kpad, int S, int64_t R,
+                                   __nv_bfloat16 *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    const double *x1 = X1 + row * ld1;
+    const double *x2 = X2 ? X2 + row * ld2 : nullptr;
+    auto at = [&](int k) -> double { return k < K1 ? x1[k] : ((x2 && k < K1 + K2) ? x2[k - K1] : 0.0); };
+    const int KB = Kpad / BKB;
+    int emax = -2000;
+    for (int k = lane; k < Kpad; k += 32) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(at(k));
+        const int be = (int)((b >> 52) & 0x7FF);
+        if (be == 0) continue;
+        const int e = be - 1022;
+        emax = e > emax ? e : emax;
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const int o = __shfl_xor_sync(0xffffffffu, emax, off);
+        emax = o > emax ? o : emax;
+    }
+    for (int k = lane; k < Kpad; k += 32) {
+        long long F = 0;
+        if (emax > -2000) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(at(k));
+            const int be = (int)((b >> 52) & 0x7FF);
+            if (be != 0) {
+                const long long mnt = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+                const int sh = (be - 1075) + 7 * S - emax;
+                long long f;
+                if (sh >= 0) f = mnt << sh;
+                else if (sh > -63) f = (mnt + (1ll << (-sh - 1))) >> (-sh);
+                else f = 0;
+                F = (b >> 63) ? -f : f;
+            }
+        }
+        const int kb = k / BKB, kk = k % BKB;
+        for (int i = 0; i < S; ++i) {
+            const int sh = 7 * (S - 1 - i);
+            long long d = sh > 0 ? ((F + (1ll << (sh - 1))) >> sh) : F;
+            F -= d << sh;
+            out[(((int64_t)i * KB + kb) * R + row) * BKB + kk] = __float2bfloat16_rn(ldexpf((float)d, emax - 7 - 7 * i));
+        }
     }
 }
 
@@ -615,6 +820,89 @@ int g_diag_rows(const Grouped<DRTask> &g, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
     diag_rows_kernel<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n);
     return 1;
+}
+
+// ------------------------------------------------ dense split GEMM (host)
+int dense_operand_alloc(int S, int64_t R, int Kpad, DenseOperand *op, std::string *err) {
+    op->buf = nullptr;
+    op->R = R < 1 ? 1 : R;
+    op->Kpad = Kpad;
+    op->planes = Kpad / BKB;
+    if (!encode_fn()) { *err = "cuTensorMapEncodeTiled is not available"; return HB_ERR_CUDA; }
+    const size_t bytes = sizeof(__nv_bfloat16) * (size_t)S * op->planes * op->R * BKB;
+    cudaError_t e = cudaMalloc(&op->buf, bytes);
+    if (e != cudaSuccess) { *err = std::string("Davidson operand slices: ") + cudaGetErrorString(e); return HB_ERR_OOM; }
+    cuuint64_t dims[3] = {(cuuint64_t)BKB, (cuuint64_t)op->R, (cuuint64_t)S * op->planes};
+    cuuint64_t strides[2] = {(cuuint64_t)BKB * 2, (cuuint64_t)op->R * BKB * 2};
+    cuuint32_t box[3] = {BKB, BM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&op->tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, op->buf, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        cudaFree(op->buf);
+        op->buf = nullptr;
+        *err = "Davidson operand tensor map: error " + std::to_string((int)r);
+        return HB_ERR_CUDA;
+    }
+    return HB_OK;
+}
+
+void dense_operand_free(DenseOperand *op) {
+    if (op->buf) cudaFree(op->buf);
+    op->buf = nullptr;
+}
+
+void dense_operand_fill(const DenseOperand &op, int S, const double *X1, int64_t ld1, int K1, const double *X2,
+                        int64_t ld2, int K2, int64_t rows, cudaStream_t s) {
+    if (rows <= 0) return;
+    slice_rows2_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(X1, ld1, K1, X2, ld2, K2, rows, op.Kpad, S, op.R,
+                                                                  (__nv_bfloat16 *)op.buf);
+}
+
+int dense_splits(int64_t M, int64_t N, int kb_total, int *kb_per_split) {
+    const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const int kpc = KCHUNK / BKB;
+    const int max_split = (kb_total + kpc - 1) / kpc;
+    int ns = (int)std::max<int64_t>(1, std::min<int64_t>(max_split, (3 * 152 + tiles - 1) / tiles));
+    int per = (kb_total + ns - 1) / ns;
+    per = (per + kpc - 1) / kpc * kpc;
+    *kb_per_split = per;
+    return (kb_total + per - 1) / per;
+}
+
+int dense_split_gemm(int S, const DenseOperand &A, int64_t M, const DenseOperand &B, int64_t N, int kb_total,
+                     float2 *part, double *Y, int64_t ldy, int *err, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || kb_total <= 0) return 0;
+    static bool attr[MAXS + 1] = {false};
+    const int bytes = S * SLOT + 2048;
+    DenseArgs a;
+    a.M = (int)M; a.N = (int)N;
+    a.kb_total = kb_total;
+    const int nsplit = dense_splits(M, N, kb_total, &a.kb_per_split);
+    a.a_planes = A.planes; a.b_planes = B.planes;
+    a.part = part;
+    a.err = err;
+    const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)nsplit);
+#define HB_DENSE(SS)                                                                                    \
+    do {                                                                                                \
+        if (!attr[SS]) {                                                                                \
+            cudaFuncSetAttribute(dense_split_kernel<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); \
+            attr[SS] = true;                                                                            \
+        }                                                                                               \
+        dense_split_kernel<SS><<<grid, NTHREADS, bytes, s>>>(A.tm, B.tm, a);                            \
+    } while (0)
+    switch (S) {
+        case 2: HB_DENSE(2); break;
+        case 3: HB_DENSE(3); break;
+        case 4: HB_DENSE(4); break;
+        case 5: HB_DENSE(5); break;
+        default: HB_DENSE(6); break;
+    }
+#undef HB_DENSE
+    const int64_t tot = M * N;
+    dense_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nsplit, (int)M, (int)N, Y, ldy);
+    return 2;
 }
 
 void release_mixed(hb_ctx *ctx) {

@@ -15,6 +15,7 @@ HB_OK, HB_ERR_INVALID_ARG, HB_ERR_CUDA, HB_ERR_OOM, HB_ERR_TIMEOUT, HB_ERR_NOT_C
     HB_ERR_UNSUPPORTED = range(7)
 HB_FP64, HB_MIXED = 0, 1
 HB_PRECOND_DIAG, HB_PRECOND_MLP = 0, 1
+HB_DIAG_TENSOR = 0x100
 HB_NOALLOC_MAX_ROWS = 262144
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

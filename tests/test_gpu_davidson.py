@@ -18,24 +18,28 @@ def _lib():
     build_ext.build()
 
 
-def _solve(P, k, precision=0, tol=1e-8):
+def _solve(P, k, precision=0, tol=1e-8, tensor=False):
     import torch
     from paper_1709_03005_gb300 import hb
     H = hb.Hamiltonian(P)
     b, _ = H.build(precision)
     evecs = torch.zeros((P.dim, k), dtype=torch.float64, device="cuda")
-    w, st, ok = H.diag(b, k, tol, 500, evecs=evecs)
+    flags = hb.HB_DIAG_TENSOR if tensor else 0
+    w, st, ok = H.diag(b, k, tol, 500, precond=hb.HB_PRECOND_DIAG | flags, evecs=evecs)
     torch.cuda.synchronize()
     X = evecs.cpu().numpy()
     H.close()
     return w, X, st
 
 
-@pytest.mark.parametrize("key,k,precision", [("c1", 5, 0), ("mid", 12, 0), ("mid", 12, 1)])
-def test_davidson_small(key, k, precision):
+@pytest.mark.parametrize("key,k,precision,tensor", [("c1", 5, 0, False), ("mid", 12, 0, False), ("mid", 12, 1, False),
+                                                    ("c1", 5, 1, True), ("mid", 12, 1, True)])
+def test_davidson_small(key, k, precision, tensor):
+    """tensor: block products H V on the tensor cores (split bf16); the
+    residuals are checked with the oracle's FP64 matrix."""
     P = synth.make_config(key)
     R = coracle.Oracle(P).dense()
-    w, X, st = _solve(P, k, precision)
+    w, X, st = _solve(P, k, precision, tensor=tensor)
     ref, _ = eig.lowest(R, k)
     np.testing.assert_allclose(w, ref, atol=1e-8, rtol=0)
     res = np.linalg.norm(R @ X - X * w, axis=0)
@@ -44,16 +48,18 @@ def test_davidson_small(key, k, precision):
     assert st.iterations > 0
 
 
-def test_davidson_medium_twenty_roots():
+@pytest.mark.parametrize("tensor", [False, True])
+def test_davidson_medium_twenty_roots(tensor):
     """The 8000-dimensional workload, lowest 20 roots to a residual of 1e-8."""
     P = synth.make_config("c2")
     R = coracle.Oracle(P).dense()
-    w, X, st = _solve(P, 20, precision=1)
+    w, X, st = _solve(P, 20, precision=1, tensor=tensor)
     ref = np.linalg.eigvalsh(R)[:20]
     np.testing.assert_allclose(w, ref, atol=1e-8, rtol=0)
     res = np.linalg.norm(R @ X - X * w, axis=0)
     assert res.max() <= 1.5e-8, res.max()
-    print(f"c2: {st.iterations} iterations, {st.ms_total:.1f} ms, max residual {st.max_residual:.2e}")
+    print(f"c2 (tensor products {tensor}): {st.iterations} iterations, {st.ms_total:.1f} ms, "
+          f"matvec {st.ms_matvec:.1f} ms, max residual {st.max_residual:.2e}")
 
 
 def test_davidson_not_converged_status():
