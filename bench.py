@@ -256,16 +256,25 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_value = world * e2e_steps * positions(dim) / (time.perf_counter() - t0)
 
-    # Davidson after the timed build steps
+    # Davidson after the timed build steps: block products on the tensor cores
+    # (split bf16) on the mixed path, and with FP64 products beside it
     davidson = None
     if args.davidson_k > 0:
-        try:
+        def solve(flags):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ev, dst, ok = H.diag(blocks, args.davidson_k, 1e-8, 400, allow_not_converged=True)
+            ev, dst, ok = H.diag(blocks, args.davidson_k, 1e-8, 400, precond=hb.HB_PRECOND_DIAG | flags,
+                                 allow_not_converged=True)
             torch.cuda.synchronize()
-            davidson = {"k": args.davidson_k, "tol": 1e-8, "seconds": time.perf_counter() - t0,
-                        "iterations": dst.iterations, "converged": ok, "max_residual": dst.max_residual}
+            return {"seconds": time.perf_counter() - t0, "iterations": dst.iterations, "converged": ok,
+                    "max_residual": dst.max_residual, "matvec_ms": dst.ms_matvec}
+        try:
+            tensor = precision == hb.HB_MIXED
+            davidson = {"k": args.davidson_k, "tol": 1e-8,
+                        "products": "tensor cores, split bf16" if tensor else "FP64"}
+            davidson.update(solve(hb.HB_DIAG_TENSOR if tensor else 0))
+            if tensor:
+                davidson["fp64_products"] = solve(0)
         except hb.HBError as e:
             davidson = {"unavailable": str(e)}
 
