@@ -149,9 +149,11 @@ typedef struct {
     int32_t mlp_fallbacks;
     double max_residual;
     float ms_matvec;
-    float ms_rr;
+    float ms_rr;              /* hb_diag: host time of the small eigenproblems */
     double expand_tensor_flops;  /* mixed: bf16 tensor flops of the split products */
-    int32_t reserved[6];
+    float ms_gram;            /* hb_diag: projections (device sums and their copy to the host) */
+    float ms_combine;         /* hb_diag: basis combinations (coefficients to the device, kernel) */
+    int32_t reserved[4];
 } hb_stats;
 
 /* Excitation record of one determinant pair (row, col), see hb_classify. */

@@ -15,6 +15,7 @@ struct DiagWork {
     double *V = nullptr, *AV = nullptr, *X = nullptr, *AX = nullptr, *W2 = nullptr;
     double *d = nullptr;          // diagonal of H
     double *partial = nullptr, *small = nullptr, *theta = nullptr;
+    double *proj = nullptr;       // projection coefficients kept on the device
     int32_t *idx = nullptr;
     double *HlcT = nullptr;       // class-4 block transposed (Dc x n_l2)
     const double *HlcT_src = nullptr;
@@ -27,7 +28,9 @@ struct DiagWork {
     int *err = nullptr;
 };
 
-void small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V);
+// All eigenvalues (ascending) and the eigenvectors of the nvec lowest of a
+// symmetric matrix; V is [n][nvec] row-major, column c the c-th vector.
+void small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V, int nvec);
 int ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t s);
 void release_diag(hb_ctx *ctx);
 void fill_diag(hb_ctx *ctx, const hb_blocks *H, DiagWork *w, cudaStream_t s);

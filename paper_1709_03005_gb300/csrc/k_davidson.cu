@@ -12,7 +12,9 @@
 // the small projected eigenproblem (at most a few hundred) is solved on the
 // host (Householder tridiagonalisation and implicit QL).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -95,19 +97,44 @@ __global__ void spmm_csr_kernel(const int64_t *__restrict__ rp, const int32_t *_
     }
 }
 
-// partial[c][a][b] = sum_{i in chunk c} X[a][i] Y[b][i]
-constexpr int kGramChunk = 2048;
-__global__ void gram_partial_kernel(const double *__restrict__ X, int64_t ldx, int p, const double *__restrict__ Y,
-                                    int64_t ldy, int q, int64_t n, double *__restrict__ partial) {
+// partial[c][a][b] = sum_{i in chunk c} X[a][i] Y[b][i]: one block per
+// (chunk of kGramChunk entries, 32 x 32 tile of (a, b)); the rows of the tile
+// pass through shared memory 64 entries at a time (coalesced along i), each
+// thread keeps 4 outputs; fixed order, so the sums are deterministic.
+constexpr int kGramChunk = 512;
+constexpr int kGramTile = 32, kGramSub = 64;
+__global__ void __launch_bounds__(256)
+gram_partial_kernel(const double *__restrict__ X, int64_t ldx, int p, const double *__restrict__ Y, int64_t ldy, int q,
+                    int64_t n, double *__restrict__ partial) {
+    __shared__ double xs[kGramTile][kGramSub + 1], ys[kGramTile][kGramSub + 1];
     const int c = blockIdx.x;
+    const int tiles_q = (q + kGramTile - 1) / kGramTile;
+    const int a0 = (blockIdx.y / tiles_q) * kGramTile, b0 = (blockIdx.y % tiles_q) * kGramTile;
     const int64_t i0 = (int64_t)c * kGramChunk, i1 = (n < i0 + kGramChunk) ? n : i0 + kGramChunk;
-    for (int t = threadIdx.x + blockIdx.y * blockDim.x; t < p * q; t += blockDim.x * gridDim.y) {
-        const int a = t / q, b = t % q;
-        const double *x = X + (int64_t)a * ldx, *y = Y + (int64_t)b * ldy;
-        double acc = 0.0;
-        for (int64_t i = i0; i < i1; ++i) acc = fma(x[i], y[i], acc);
-        partial[(int64_t)c * p * q + t] = acc;
+    const int tid = threadIdx.x;
+    const int ta = tid / 8, tb = (tid % 8) * 4;     // outputs (a0 + ta, b0 + tb .. tb + 3)
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t s0 = i0; s0 < i1; s0 += kGramSub) {
+        __syncthreads();
+        for (int e = tid; e < kGramTile * kGramSub; e += 256) {
+            const int r = e / kGramSub, k = e % kGramSub;
+            const int64_t i = s0 + k;
+            xs[r][k] = (a0 + r < p && i < i1) ? __ldg(X + (int64_t)(a0 + r) * ldx + i) : 0.0;
+            ys[r][k] = (b0 + r < q && i < i1) ? __ldg(Y + (int64_t)(b0 + r) * ldy + i) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < kGramSub; ++k) {
+            const double x = xs[ta][k];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = fma(x, ys[tb + u][k], acc[u]);
+        }
     }
+    const int a = a0 + ta;
+    if (a < p)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (b0 + tb + u < q) partial[(int64_t)c * p * q + (int64_t)a * q + b0 + tb + u] = acc[u];
 }
 
 __global__ void reduce_kernel(const double *__restrict__ partial, int chunks, int nout, double *__restrict__ out) {
@@ -118,15 +145,15 @@ __global__ void reduce_kernel(const double *__restrict__ partial, int chunks, in
     out[t] = acc;
 }
 
-// Y[j][i] = beta * Y[j][i] + sum_a C[a][j] X[a][i]   (a < p, j < q), C on device [p][q]
+// Y[j][i] = beta * Y[j][i] + scale * sum_a C[a][j] X[a][i]   (a < p, j < q), C on device [p][q]
 __global__ void combine_kernel(const double *__restrict__ X, int64_t ldx, int p, const double *__restrict__ C, int q,
-                               int64_t n, double *__restrict__ Y, int64_t ldy, double beta) {
+                               int64_t n, double *__restrict__ Y, int64_t ldy, double beta, double scale) {
     extern __shared__ double cs[];   // [p][16]
     const int j0 = blockIdx.y * 16;
     const int nq = min(16, q - j0);
     for (int t = threadIdx.x; t < p * 16; t += blockDim.x) {
         const int a = t / 16, jj = t % 16;
-        cs[t] = jj < nq ? C[(int64_t)a * q + j0 + jj] : 0.0;
+        cs[t] = jj < nq ? scale * C[(int64_t)a * q + j0 + jj] : 0.0;
     }
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -237,122 +264,235 @@ void hb::fill_diag(hb_ctx *ctx, const hb_blocks *H, DiagWork *w, cudaStream_t s)
 // as in Golub & Van Loan and Wilkinson & Reinsch).  A is n x n row-major; on
 // return w holds the eigenvalues ascending and column j of V (V[i*n + j]) the
 // eigenvector of w[j].
-void hb::small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V) {
-    w.assign(n, 0.0);
-    V.assign((size_t)n * n, 0.0);
-    if (n == 0) return;
-    if (n == 1) { w[0] = A[0]; V[0] = 1.0; return; }
-    // z holds the accumulated orthogonal transformation, row-major z[i][j]
-    std::vector<double> z(A), d(n), e(n);
-    auto Z = [&](int i, int j) -> double & { return z[(size_t)i * n + j]; };
-    // --- Householder tridiagonalisation (rows from the bottom up)
-    for (int i = n - 1; i > 0; --i) {
-        const int l = i - 1;
-        double h = 0.0, scale = 0.0;
-        if (l > 0) {
-            for (int k = 0; k <= l; ++k) scale += std::fabs(Z(i, k));
-            if (scale == 0.0) {
-                e[i] = Z(i, l);
+// ----------------------------------------- small dense symmetric eigensolver
+// All eigenvalues and the eigenvectors of the nvec lowest of a symmetric n x n
+// matrix (the Rayleigh-Ritz and Gram matrices of the solver, n up to about a
+// thousand), on the host:
+//   1. Householder reduction to tridiagonal form, Q^T A Q = T (Golub & Van
+//      Loan, Alg. 8.3.1), with the symmetric rank-2 update of the trailing
+//      block done row by row;
+//   2. the eigenvalues of T by implicit QR steps with the Wilkinson shift
+//      (Golub & Van Loan, Alg. 8.3.3), without accumulating vectors;
+//   3. each wanted eigenvector of T by inverse iteration (three solves of the
+//      shifted tridiagonal system with partial pivoting), orthogonalised
+//      against the vectors of the same cluster;
+//   4. the back-transformation x = Q y with the stored reflectors.
+// w: ascending eigenvalues [n]; V: [n][nvec], column c is the c-th vector.
+namespace {
+
+struct Tridiag {
+    std::vector<double> d, e;          // diagonal [n], off-diagonal [n-1]
+    std::vector<double> vs, beta;      // reflector k: vs[k][k+1..n), beta[k]
+};
+
+Tridiag tridiagonalize(int n, std::vector<double> &A) {
+    Tridiag t;
+    t.d.assign(n, 0.0);
+    t.e.assign(n > 1 ? n - 1 : 0, 0.0);
+    t.vs.assign((size_t)n * n, 0.0);
+    t.beta.assign(n, 0.0);
+    std::vector<double> v(n), p(n), wv(n);
+    for (int k = 0; k + 2 < n; ++k) {
+        // reflector that zeroes A[k+2..n)[k]
+        double xn = 0.0;
+        for (int i = k + 1; i < n; ++i) xn += A[(size_t)i * n + k] * A[(size_t)i * n + k];
+        xn = std::sqrt(xn);
+        const double x0 = A[(size_t)(k + 1) * n + k];
+        if (xn == 0.0) { t.e[k] = 0.0; continue; }
+        const double alpha = x0 >= 0.0 ? -xn : xn;
+        for (int i = k + 1; i < n; ++i) v[i] = A[(size_t)i * n + k];
+        v[k + 1] -= alpha;
+        double vv = 0.0;
+        for (int i = k + 1; i < n; ++i) vv += v[i] * v[i];
+        t.e[k] = alpha;
+        if (vv == 0.0) continue;
+        const double bk = 2.0 / vv;
+        t.beta[k] = bk;
+        for (int i = k + 1; i < n; ++i) t.vs[(size_t)k * n + i] = v[i];
+        // p = bk A22 v, w = p - (bk/2)(p.v) v, A22 -= v w^T + w v^T
+        double pv = 0.0;
+        for (int i = k + 1; i < n; ++i) {
+            const double *row = &A[(size_t)i * n];
+            double acc = 0.0;
+            for (int j = k + 1; j < n; ++j) acc += row[j] * v[j];
+            p[i] = bk * acc;
+            pv += p[i] * v[i];
+        }
+        for (int i = k + 1; i < n; ++i) wv[i] = p[i] - 0.5 * bk * pv * v[i];
+        for (int i = k + 1; i < n; ++i) {
+            double *row = &A[(size_t)i * n];
+            const double vi = v[i], wi = wv[i];
+            for (int j = k + 1; j < n; ++j) row[j] -= vi * wv[j] + wi * v[j];
+        }
+    }
+    for (int i = 0; i < n; ++i) t.d[i] = A[(size_t)i * n + i];
+    if (n >= 2) t.e[n - 2] = A[(size_t)(n - 1) * n + (n - 2)];
+    return t;
+}
+
+// All eigenvalues of T by implicit symmetric QR steps with the Wilkinson
+// shift and deflation (Golub & Van Loan, Alg. 8.3.3): each step chases the
+// bulge of one Givens rotation G^T T G down the unreduced block [p, q].
+std::vector<double> tridiag_eigenvalues(const Tridiag &t) {
+    const int n = (int)t.d.size();
+    std::vector<double> a(t.d), b(t.e);
+    b.push_back(0.0);
+    int q = n - 1;
+    int guard = 0;
+    while (q > 0 && guard < 60 * n) {
+        // deflate negligible couplings at the bottom
+        if (std::fabs(b[q - 1]) <= 2.2e-16 * (std::fabs(a[q - 1]) + std::fabs(a[q]))) {
+            b[q - 1] = 0.0;
+            --q;
+            continue;
+        }
+        int p = q - 1;
+        while (p > 0 && std::fabs(b[p - 1]) > 2.2e-16 * (std::fabs(a[p - 1]) + std::fabs(a[p]))) --p;
+        if (p > 0) b[p - 1] = 0.0;
+        // Wilkinson shift from the trailing 2 x 2 block
+        const double dlt = 0.5 * (a[q - 1] - a[q]);
+        const double bq = b[q - 1];
+        const double den = dlt + (dlt >= 0.0 ? std::hypot(dlt, bq) : -std::hypot(dlt, bq));
+        const double mu = den != 0.0 ? a[q] - bq * bq / den : a[q] - std::fabs(bq);
+        double x = a[p] - mu, z = b[p];
+        for (int k = p; k < q; ++k) {
+            const double r = std::hypot(x, z);
+            const double c = r != 0.0 ? x / r : 1.0, s = r != 0.0 ? -z / r : 0.0;
+            if (k > p) b[k - 1] = r;
+            const double ak = a[k], ak1 = a[k + 1], bk = b[k];
+            a[k] = c * c * ak - 2.0 * c * s * bk + s * s * ak1;
+            a[k + 1] = s * s * ak + 2.0 * c * s * bk + c * c * ak1;
+            b[k] = c * s * (ak - ak1) + (c * c - s * s) * bk;
+            if (k + 1 < q) {
+                x = b[k];
+                z = -s * b[k + 1];
+                b[k + 1] = c * b[k + 1];
+            }
+        }
+        ++guard;
+    }
+    std::sort(a.begin(), a.end());
+    return a;
+}
+
+// eigenvector of T for the eigenvalue lam by inverse iteration; the vectors
+// in `cluster` (unit, orthogonal) are projected out after every solve
+void tridiag_vector(const Tridiag &t, double lam, double tnorm, int seed, const std::vector<const double *> &cluster,
+                    double *y) {
+    const int n = (int)t.d.size();
+    if (n == 1) { y[0] = 1.0; return; }
+    // shifted matrix, perturbed off the eigenvalue so the factors are finite
+    const double shift = lam + 4.0 * 2.2e-16 * tnorm;
+    // LU with partial pivoting of the tridiagonal T - shift I:
+    // U has diagonal u0, superdiagonals u1, u2; L multipliers mul, row swaps piv
+    std::vector<double> u0(n), u1(n), u2(n), mul(n);
+    std::vector<char> piv(n);
+    {
+        double a = t.d[0] - shift, b = t.e[0], c = 0.0;
+        for (int i = 0; i < n - 1; ++i) {
+            const double lo = t.e[i];                   // subdiagonal entry of row i + 1
+            const double na = t.d[i + 1] - shift;
+            const double nb = i + 1 < n - 1 ? t.e[i + 1] : 0.0;
+            if (std::fabs(a) >= std::fabs(lo)) {
+                piv[i] = 0;
+                const double m = a != 0.0 ? lo / a : 0.0;
+                mul[i] = m;
+                u0[i] = a; u1[i] = b; u2[i] = c;
+                a = na - m * b;
+                b = nb - m * c;
+                c = 0.0;
             } else {
-                for (int k = 0; k <= l; ++k) { Z(i, k) /= scale; h += Z(i, k) * Z(i, k); }
-                double f = Z(i, l);
-                double g = f >= 0.0 ? -std::sqrt(h) : std::sqrt(h);
-                e[i] = scale * g;
-                h -= f * g;
-                Z(i, l) = f - g;
-                f = 0.0;
-                for (int j = 0; j <= l; ++j) {
-                    Z(j, i) = Z(i, j) / h;
-                    g = 0.0;
-                    for (int k = 0; k <= j; ++k) g += Z(j, k) * Z(i, k);
-                    for (int k = j + 1; k <= l; ++k) g += Z(k, j) * Z(i, k);
-                    e[j] = g / h;
-                    f += e[j] * Z(i, j);
-                }
-                const double hh = f / (h + h);
-                for (int j = 0; j <= l; ++j) {
-                    f = Z(i, j);
-                    e[j] = g = e[j] - hh * f;
-                    for (int k = 0; k <= j; ++k) Z(j, k) -= (f * e[k] + g * Z(i, k));
-                }
+                piv[i] = 1;
+                const double m = a / lo;
+                mul[i] = m;
+                u0[i] = lo; u1[i] = na; u2[i] = nb;
+                a = b - m * na;
+                b = c - m * nb;
+                c = 0.0;
             }
-        } else {
-            e[i] = Z(i, l);
         }
-        d[i] = h;
+        u0[n - 1] = a;
     }
-    d[0] = 0.0;
-    e[0] = 0.0;
+    const double tiny = 2.2e-16 * tnorm + 1e-300;
+    for (int i = 0; i < n; ++i)
+        if (std::fabs(u0[i]) < tiny) u0[i] = u0[i] < 0.0 ? -tiny : tiny;
+    // deterministic start vector
+    uint64_t r = 0x9e3779b97f4a7c15ull * (uint64_t)(seed + 1);
     for (int i = 0; i < n; ++i) {
-        const int l = i - 1;
-        if (d[i] != 0.0) {
-            for (int j = 0; j <= l; ++j) {
-                double g = 0.0;
-                for (int k = 0; k <= l; ++k) g += Z(i, k) * Z(k, j);
-                for (int k = 0; k <= l; ++k) Z(k, j) -= g * Z(k, i);
-            }
+        r ^= r >> 12; r ^= r << 25; r ^= r >> 27;
+        y[i] = 0.5 + (double)((r * 2685821657736338717ull) >> 11) * (1.0 / 9007199254740992.0);
+    }
+    auto orth_normalise = [&]() {
+        for (const double *q : cluster) {
+            double dot = 0.0;
+            for (int i = 0; i < n; ++i) dot += q[i] * y[i];
+            for (int i = 0; i < n; ++i) y[i] -= dot * q[i];
         }
-        d[i] = Z(i, i);
-        Z(i, i) = 1.0;
-        for (int j = 0; j <= l; ++j) Z(j, i) = Z(i, j) = 0.0;
+        double nrm = 0.0;
+        for (int i = 0; i < n; ++i) nrm += y[i] * y[i];
+        nrm = std::sqrt(nrm);
+        if (nrm == 0.0) { y[seed % n] = 1.0; nrm = 1.0; }
+        for (int i = 0; i < n; ++i) y[i] /= nrm;
+    };
+    orth_normalise();
+    for (int it = 0; it < 3; ++it) {
+        // forward: apply the row swaps and multipliers
+        for (int i = 0; i < n - 1; ++i) {
+            if (piv[i]) std::swap(y[i], y[i + 1]);
+            y[i + 1] -= mul[i] * y[i];
+        }
+        // back substitution with U (bandwidth 3)
+        for (int i = n - 1; i >= 0; --i) {
+            double s = y[i];
+            if (i + 1 < n) s -= u1[i] * y[i + 1];
+            if (i + 2 < n) s -= u2[i] * y[i + 2];
+            y[i] = s / u0[i];
+        }
+        orth_normalise();
     }
-    // --- implicit QL on (d, e) with accumulation into z
-    for (int i = 1; i < n; ++i) e[i - 1] = e[i];
-    e[n - 1] = 0.0;
-    for (int l = 0; l < n; ++l) {
-        int iter = 0;
-        int m;
-        do {
-            for (m = l; m < n - 1; ++m) {
-                const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-                if (std::fabs(e[m]) <= 1e-16 * dd) break;
-            }
-            if (m != l) {
-                if (++iter > 60) break;
-                double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-                double r = std::hypot(g, 1.0);
-                g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? std::fabs(r) : -std::fabs(r)));
-                double s = 1.0, c = 1.0, p = 0.0;
-                int i;
-                for (i = m - 1; i >= l; --i) {
-                    double f = s * e[i], b = c * e[i];
-                    e[i + 1] = (r = std::hypot(f, g));
-                    if (r == 0.0) {
-                        d[i + 1] -= p;
-                        e[m] = 0.0;
-                        break;
-                    }
-                    s = f / r;
-                    c = g / r;
-                    g = d[i + 1] - p;
-                    r = (d[i] - g) * s + 2.0 * c * b;
-                    d[i + 1] = g + (p = s * r);
-                    g = c * r - b;
-                    for (int k = 0; k < n; ++k) {
-                        f = Z(k, i + 1);
-                        Z(k, i + 1) = s * Z(k, i) + c * f;
-                        Z(k, i) = c * Z(k, i) - s * f;
-                    }
-                }
-                if (r == 0.0 && i >= l) continue;
-                d[l] -= p;
-                e[l] = g;
-                e[m] = 0.0;
-            }
-        } while (m != l);
+}
+
+}  // namespace
+
+void hb::small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V, int nvec) {
+    if (nvec < 0 || nvec > n) nvec = n;
+    w.assign(n, 0.0);
+    V.assign((size_t)n * std::max(nvec, 1), 0.0);
+    if (n == 0) return;
+    if (n == 1) { w[0] = A[0]; if (nvec) V[0] = 1.0; return; }
+    Tridiag t = tridiagonalize(n, A);
+    double tnorm = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? std::fabs(t.e[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(t.e[i]) : 0.0);
+        tnorm = std::max(tnorm, std::fabs(t.d[i]) + r);
     }
-    std::vector<int> ord(n);
-    std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return d[a] < d[b]; });
-    for (int j = 0; j < n; ++j) {
-        w[j] = d[ord[j]];
-        for (int i = 0; i < n; ++i) V[(size_t)i * n + j] = Z(i, ord[j]);
+    w = tridiag_eigenvalues(t);
+    // vectors of the nvec lowest, clusters kept orthogonal
+    const double gap = 1e-3 * std::max(tnorm, 1e-300);
+    std::vector<double> Y((size_t)std::max(nvec, 1) * n);
+    for (int c = 0; c < nvec; ++c) {
+        std::vector<const double *> cluster;
+        for (int c2 = c - 1; c2 >= 0 && w[c] - w[c2] <= gap; --c2) cluster.push_back(&Y[(size_t)c2 * n]);
+        tridiag_vector(t, w[c], tnorm, c, cluster, &Y[(size_t)c * n]);
+    }
+    // back-transformation x = H_0 H_1 ... y (reflectors applied last to first)
+    for (int c = 0; c < nvec; ++c) {
+        double *y = &Y[(size_t)c * n];
+        for (int k = n - 3; k >= 0; --k) {
+            if (t.beta[k] == 0.0) continue;
+            const double *v = &t.vs[(size_t)k * n];
+            double dot = 0.0;
+            for (int i = k + 1; i < n; ++i) dot += v[i] * y[i];
+            dot *= t.beta[k];
+            for (int i = k + 1; i < n; ++i) y[i] -= dot * v[i];
+        }
+        for (int i = 0; i < n; ++i) V[(size_t)i * nvec + c] = y[i];
     }
 }
 
 extern "C" int hb_test_symeig(int n, const double *A, double *w, double *V) {
     std::vector<double> a(A, A + (size_t)n * n), ww, vv;
-    hb::small_eigh(n, a, ww, vv);
+    hb::small_eigh(n, a, ww, vv, n);
     std::memcpy(w, ww.data(), sizeof(double) * n);
     std::memcpy(V, vv.data(), sizeof(double) * (size_t)n * n);
     return 0;
@@ -368,6 +508,10 @@ struct Ops {
     int64_t n, Dc, nl;
     DiagWork *w;
     int launches = 0;
+    double ms_gram = 0.0, ms_combine = 0.0, ms_eigh = 0.0;
+    static double now_ms() {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    }
 
     // Y[0:q] = H X[0:q], vectors stored as rows of length ld
     void matvec(const double *X, double *Y, int q, int64_t ld) {
@@ -415,23 +559,48 @@ struct Ops {
 
     // G[a][b] = X[a] . Y[b] on the host (p x q)
     void gram(const double *X, int p, const double *Y, int q, int64_t ld, std::vector<double> &G) {
+        const double t0 = now_ms();
         const int chunks = (int)((n + kGramChunk - 1) / kGramChunk);
-        dim3 g(chunks, std::max(1, std::min(8, (p * q + 255) / 256)));
+        dim3 g(chunks, ((p + kGramTile - 1) / kGramTile) * ((q + kGramTile - 1) / kGramTile));
         gram_partial_kernel<<<g, 256, 0, s>>>(X, ld, p, Y, ld, q, n, w->partial);
         reduce_kernel<<<(p * q + 255) / 256, 256, 0, s>>>(w->partial, chunks, p * q, w->small);
         launches += 2;
         G.resize((size_t)p * q);
         cudaMemcpyAsync(G.data(), w->small, sizeof(double) * p * q, cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
+        ms_gram += now_ms() - t0;
+    }
+
+    void eigh(int m, std::vector<double> &A, std::vector<double> &wv, std::vector<double> &V, int nvec) {
+        const double t0 = now_ms();
+        small_eigh(m, A, wv, V, nvec);
+        ms_eigh += now_ms() - t0;
     }
 
     // Y[0:q] = beta Y + X[0:p]^T C, C host [p][q]
     void combine(const double *X, int p, const std::vector<double> &C, int q, double *Y, int64_t ld, double beta) {
+        const double t0 = now_ms();
         cudaMemcpyAsync(w->small, C.data(), sizeof(double) * p * q, cudaMemcpyHostToDevice, s);
         dim3 g((unsigned)((n + 255) / 256), (q + 15) / 16);
-        combine_kernel<<<g, 256, sizeof(double) * p * 16, s>>>(X, ld, p, w->small, q, n, Y, ld, beta);
+        combine_kernel<<<g, 256, sizeof(double) * p * 16, s>>>(X, ld, p, w->small, q, n, Y, ld, beta, 1.0);
         ++launches;
-        cudaStreamSynchronize(s);   // w->small is reused by the next call
+        // no wait: the next upload into w->small is ordered after this kernel
+        // on the stream, and the pageable source is staged before the copy call returns
+        ms_combine += now_ms() - t0;
+    }
+
+    // Y[0:q] -= X[0:p]^T (X[0:p] Y[0:q]^T): one projection pass, all on the device
+    void project_out(const double *X, int p, double *Y, int q, int64_t ld) {
+        if (p <= 0 || q <= 0) return;
+        const double t0 = now_ms();
+        const int chunks = (int)((n + kGramChunk - 1) / kGramChunk);
+        dim3 g(chunks, ((p + kGramTile - 1) / kGramTile) * ((q + kGramTile - 1) / kGramTile));
+        gram_partial_kernel<<<g, 256, 0, s>>>(X, ld, p, Y, ld, q, n, w->partial);
+        reduce_kernel<<<(p * q + 255) / 256, 256, 0, s>>>(w->partial, chunks, p * q, w->proj);
+        dim3 g2((unsigned)((n + 255) / 256), (q + 15) / 16);
+        combine_kernel<<<g2, 256, sizeof(double) * p * 16, s>>>(X, ld, p, w->proj, q, n, Y, ld, 1.0, -1.0);
+        launches += 3;
+        ms_gram += now_ms() - t0;
     }
 };
 
@@ -497,8 +666,8 @@ int hb::ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t
     if (w->mmax < mmax || w->n != n) {
         auto fr = [](void *p) { if (p) cudaFree(p); };
         fr(w->V); fr(w->AV); fr(w->X); fr(w->AX); fr(w->W2); fr(w->d); fr(w->partial); fr(w->small); fr(w->theta);
-        fr(w->idx);
-        w->V = w->AV = w->X = w->AX = w->W2 = w->d = w->partial = w->small = w->theta = nullptr;
+        fr(w->idx); fr(w->proj);
+        w->V = w->AV = w->X = w->AX = w->W2 = w->d = w->partial = w->small = w->theta = w->proj = nullptr;
         w->idx = nullptr;
         const size_t vec = sizeof(double) * (size_t)mmax * n;
         cudaError_t e = cudaMalloc(&w->V, vec);
@@ -510,6 +679,7 @@ int hb::ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t
         const int chunks = (int)((n + kGramChunk - 1) / kGramChunk);
         if (e == cudaSuccess) e = cudaMalloc(&w->partial, sizeof(double) * (size_t)chunks * mmax * mmax);
         if (e == cudaSuccess) e = cudaMalloc(&w->small, sizeof(double) * (size_t)mmax * mmax);
+        if (e == cudaSuccess) e = cudaMalloc(&w->proj, sizeof(double) * (size_t)mmax * mmax);
         if (e == cudaSuccess) e = cudaMalloc(&w->theta, sizeof(double) * mmax);
         if (e == cudaSuccess) e = cudaMalloc(&w->idx, sizeof(int32_t) * mmax);
         if (e != cudaSuccess) return diag_fail(ctx, HB_ERR_OOM, std::string("Davidson workspace: ") + cudaGetErrorString(e));
@@ -592,7 +762,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         ops.gram(blk, q, blk, q, ld, G);
         for (int a = 0; a < q; ++a)
             for (int c = 0; c < a; ++c) G[(size_t)a * q + c] = G[(size_t)c * q + a] = 0.5 * (G[(size_t)a * q + c] + G[(size_t)c * q + a]);
-        small_eigh(q, G, lam, U);
+        ops.eigh(q, G, lam, U, q);
         const double lmax = lam.empty() ? 0.0 : lam.back();
         std::vector<int> keep;
         for (int a = 0; a < q; ++a)
@@ -618,17 +788,22 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
     std::vector<double> theta;
     float *wts = nullptr;
     int fallbacks = 0;
+    // projected matrix T = V^T A V, kept up to date on the host: the full
+    // product for the start block, one border V^T (A V_new) per iteration, and
+    // diag(theta) for the Ritz vectors kept at a restart
+    std::vector<double> Tp;
+    ops.gram(w->V, m, w->AV, m, ld, Tp);
     for (iter = 1; iter <= max_iter; ++iter) {
         // Rayleigh-Ritz
-        std::vector<double> T, S;
-        ops.gram(w->V, m, w->AV, m, ld, T);
+        std::vector<double> T(Tp), S;
         for (int a = 0; a < m; ++a)
             for (int c = 0; c < a; ++c) T[(size_t)a * m + c] = T[(size_t)c * m + a] = 0.5 * (T[(size_t)a * m + c] + T[(size_t)c * m + a]);
-        small_eigh(m, T, theta, S);
+        const int nv = std::min(m, 2 * b);      // Ritz vectors needed: b, or 2b at a restart
+        ops.eigh(m, T, theta, S, nv);
         const int nr = std::min(m, b);
         std::vector<double> Sk((size_t)m * nr);
         for (int a = 0; a < m; ++a)
-            for (int c = 0; c < nr; ++c) Sk[(size_t)a * nr + c] = S[(size_t)a * m + c];
+            for (int c = 0; c < nr; ++c) Sk[(size_t)a * nr + c] = S[(size_t)a * nv + c];
         ops.combine(w->V, m, Sk, nr, w->X, ld, 0.0);
         ops.combine(w->AV, m, Sk, nr, w->AX, ld, 0.0);
         // residuals (kept in AX) and their norms
@@ -661,12 +836,14 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
             const int keep = std::min(m, std::min(2 * b, mmax - q));
             std::vector<double> Sr((size_t)m * keep);
             for (int a2 = 0; a2 < m; ++a2)
-                for (int c = 0; c < keep; ++c) Sr[(size_t)a2 * keep + c] = S[(size_t)a2 * m + c];
+                for (int c = 0; c < keep; ++c) Sr[(size_t)a2 * keep + c] = S[(size_t)a2 * nv + c];
             ops.combine(w->V, m, Sr, keep, w->W2, ld, 0.0);
             cudaMemcpyAsync(w->V, w->W2, sizeof(double) * (size_t)keep * ld, cudaMemcpyDeviceToDevice, s);
             ops.combine(w->AV, m, Sr, keep, w->W2, ld, 0.0);
             cudaMemcpyAsync(w->AV, w->W2, sizeof(double) * (size_t)keep * ld, cudaMemcpyDeviceToDevice, s);
             m = keep;
+            Tp.assign((size_t)m * m, 0.0);
+            for (int a2 = 0; a2 < m; ++a2) Tp[(size_t)a2 * m + a2] = theta[a2];
         }
         if (m + q > mmax) q = mmax - m;
         if (q <= 0) break;
@@ -682,20 +859,12 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
             ++ops.launches;
         }
         // orthogonalise against the basis twice, then within the block
-        for (int pass = 0; pass < 2; ++pass) {
-            std::vector<double> C;
-            ops.gram(w->V, m, Tn, q, ld, C);
-            for (double &x : C) x = -x;
-            ops.combine(w->V, m, C, q, Tn, ld, 1.0);
-        }
+        for (int pass = 0; pass < 2; ++pass) ops.project_out(w->V, m, Tn, q, ld);
         int kept = 0;
         svqb(Tn, q, kept);
         if (kept == 0) break;
-        for (int pass = 0; pass < 1; ++pass) {
-            std::vector<double> C;
-            ops.gram(w->V, m, Tn, kept, ld, C);
-            for (double &x : C) x = -x;
-            ops.combine(w->V, m, C, kept, Tn, ld, 1.0);
+        {
+            ops.project_out(w->V, m, Tn, kept, ld);
             int k2 = 0;
             svqb(Tn, kept, k2);
             kept = k2;
@@ -713,6 +882,21 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         ms_mv += t;
         cudaEventDestroy(m0);
         cudaEventDestroy(m1);
+        {
+            // border of T: rows 0 .. m+kept of V against the new products
+            std::vector<double> G;
+            const int mn = m + kept;
+            ops.gram(w->V, mn, w->AV + (int64_t)m * ld, kept, ld, G);
+            std::vector<double> Tn2((size_t)mn * mn, 0.0);
+            for (int a2 = 0; a2 < m; ++a2)
+                for (int c = 0; c < m; ++c) Tn2[(size_t)a2 * mn + c] = Tp[(size_t)a2 * m + c];
+            for (int a2 = 0; a2 < mn; ++a2)
+                for (int c = 0; c < kept; ++c) {
+                    Tn2[(size_t)a2 * mn + m + c] = G[(size_t)a2 * kept + c];
+                    if (a2 < m) Tn2[(size_t)(m + c) * mn + a2] = G[(size_t)a2 * kept + c];
+                }
+            Tp.swap(Tn2);
+        }
         m += kept;
     }
     for (int j = 0; j < k && j < (int)theta.size(); ++j) evals[j] = theta[j];
@@ -740,6 +924,9 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         st->iterations = std::min(iter, max_iter);
         st->max_residual = maxres;
         st->ms_matvec = ms_mv;
+        st->ms_rr = (float)ops.ms_eigh;
+        st->ms_gram = (float)ops.ms_gram;
+        st->ms_combine = (float)ops.ms_combine;
         st->kernel_launches = ops.launches;
         st->mlp_fallbacks = fallbacks;
     }
@@ -752,7 +939,7 @@ void hb::release_diag(hb_ctx *ctx) {
     if (!w) return;
     release_tensor_products(w);
     for (void *p : {(void *)w->V, (void *)w->AV, (void *)w->X, (void *)w->AX, (void *)w->W2, (void *)w->d, (void *)w->partial,
-                    (void *)w->small, (void *)w->theta, (void *)w->idx, (void *)w->HlcT})
+                    (void *)w->small, (void *)w->proj, (void *)w->theta, (void *)w->idx, (void *)w->HlcT})
         if (p) cudaFree(p);
     delete w;
     ctx->diag = nullptr;

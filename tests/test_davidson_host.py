@@ -1,5 +1,6 @@
 """The small dense eigensolver used for the Davidson Rayleigh-Ritz step
-(Householder tridiagonalisation + implicit QL, host code of the library) against numpy's eigh."""
+(Householder tridiagonalisation, bisection, inverse iteration; host code of
+the library) against numpy's eigh."""
 import ctypes
 
 import numpy as np
