@@ -309,16 +309,20 @@ Tridiag tridiagonalize(int n, std::vector<double> &A) {
         const double bk = 2.0 / vv;
         t.beta[k] = bk;
         for (int i = k + 1; i < n; ++i) t.vs[(size_t)k * n + i] = v[i];
-        // p = bk A22 v, w = p - (bk/2)(p.v) v, A22 -= v w^T + w v^T
-        double pv = 0.0;
+        // p = bk A22 v, w = p - (bk/2)(p.v) v, A22 -= v w^T + w v^T; rows in
+        // parallel on the host cores for the large projected problems
+        const bool par = n - k > 256;
+#pragma omp parallel for schedule(static) if (par)
         for (int i = k + 1; i < n; ++i) {
             const double *row = &A[(size_t)i * n];
             double acc = 0.0;
             for (int j = k + 1; j < n; ++j) acc += row[j] * v[j];
             p[i] = bk * acc;
-            pv += p[i] * v[i];
         }
+        double pv = 0.0;
+        for (int i = k + 1; i < n; ++i) pv += p[i] * v[i];
         for (int i = k + 1; i < n; ++i) wv[i] = p[i] - 0.5 * bk * pv * v[i];
+#pragma omp parallel for schedule(static) if (par)
         for (int i = k + 1; i < n; ++i) {
             double *row = &A[(size_t)i * n];
             const double vi = v[i], wi = wv[i];
@@ -476,6 +480,7 @@ void hb::small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::v
         tridiag_vector(t, w[c], tnorm, c, cluster, &Y[(size_t)c * n]);
     }
     // back-transformation x = H_0 H_1 ... y (reflectors applied last to first)
+#pragma omp parallel for schedule(static) if ((int64_t)nvec * n > 65536)
     for (int c = 0; c < nvec; ++c) {
         double *y = &Y[(size_t)c * n];
         for (int k = n - 3; k >= 0; --k) {

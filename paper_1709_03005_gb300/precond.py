@@ -1,6 +1,8 @@
 """Training data and training of the learned Davidson preconditioner.
 
     python -m paper_1709_03005_gb300.precond train [--instances 24] [--out FILE]
+    python -m paper_1709_03005_gb300.precond evaluate
+    python -m paper_1709_03005_gb300.precond large [--k 200]    # the 60000-dimensional workload
 
 Data: plain (diagonal-preconditioned) block Davidson runs on seeded smaller
 Hamiltonians of the same families as the workloads, each built by this
@@ -171,13 +173,38 @@ def load_weights(path=DEFAULT_WEIGHTS):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["train", "evaluate"])
+    ap.add_argument("cmd", choices=["train", "evaluate", "large"])
+    ap.add_argument("--k", type=int, default=200)
     ap.add_argument("--instances", type=int, default=24)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     args = ap.parse_args()
     from . import build_ext
     build_ext.build()
+    if args.cmd == "large":
+        # lowest k eigenpairs of the 60000-dimensional precision-family
+        # Hamiltonian, block products on the tensor cores, plain vs learned
+        import time
+
+        import torch
+        P = synth.make_config("c5")
+        H = hb.Hamiltonian(P, validate=False)
+        b, st = H.build(hb.HB_MIXED)
+        torch.cuda.synchronize()
+        print(f"{P.name}: dim {P.dim}, build {st.ms_total:.1f} ms", flush=True)
+        params = load_weights(args.out)
+        H.set_mlp_params(params)
+        for name, pc in (("diag", hb.HB_PRECOND_DIAG), ("mlp", hb.HB_PRECOND_MLP)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            w, dst, ok = H.diag(b, args.k, 1e-8, 400, precond=pc | hb.HB_DIAG_TENSOR, allow_not_converged=True)
+            torch.cuda.synchronize()
+            print(f"{name:5s} k={args.k}: {dst.iterations} iterations, {time.perf_counter() - t0:.1f} s, "
+                  f"converged {ok}, max residual {dst.max_residual:.2e}, products {dst.ms_matvec / 1e3:.1f} s, "
+                  f"small eigenproblems {dst.ms_rr / 1e3:.1f} s, projections {dst.ms_gram / 1e3:.1f} s, "
+                  f"lowest {w[0]:.10f} highest wanted {w[-1]:.10f}", flush=True)
+        H.close()
+        return
     if args.cmd == "evaluate":
         params = load_weights(args.out)
         probs = [training_problem(1000 + s) for s in range(4)] + [synth.make_config("c2")]
