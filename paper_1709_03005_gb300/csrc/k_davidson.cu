@@ -145,27 +145,34 @@ __global__ void reduce_kernel(const double *__restrict__ partial, int chunks, in
     out[t] = acc;
 }
 
-// Y[j][i] = beta * Y[j][i] + scale * sum_a C[a][j] X[a][i]   (a < p, j < q), C on device [p][q]
+// Y[j][i] = beta * Y[j][i] + scale * sum_a C[a][j] X[a][i]   (a < p, j < q), C on device [p][q];
+// the coefficients pass through shared memory kCombineRows rows at a time.
+constexpr int kCombineRows = 256;
 __global__ void combine_kernel(const double *__restrict__ X, int64_t ldx, int p, const double *__restrict__ C, int q,
                                int64_t n, double *__restrict__ Y, int64_t ldy, double beta, double scale) {
-    extern __shared__ double cs[];   // [p][16]
+    __shared__ double cs[kCombineRows * 16];
     const int j0 = blockIdx.y * 16;
     const int nq = min(16, q - j0);
-    for (int t = threadIdx.x; t < p * 16; t += blockDim.x) {
-        const int a = t / 16, jj = t % 16;
-        cs[t] = jj < nq ? scale * C[(int64_t)a * q + j0 + jj] : 0.0;
-    }
-    __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     double acc[16];
 #pragma unroll
     for (int jj = 0; jj < 16; ++jj) acc[jj] = 0.0;
-    for (int a = 0; a < p; ++a) {
-        const double x = __ldg(X + (int64_t)a * ldx + i);
+    for (int a0 = 0; a0 < p; a0 += kCombineRows) {
+        const int na = min(kCombineRows, p - a0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < na * 16; t += blockDim.x) {
+            const int a = t / 16, jj = t % 16;
+            cs[t] = jj < nq ? scale * C[(int64_t)(a0 + a) * q + j0 + jj] : 0.0;
+        }
+        __syncthreads();
+        if (i < n)
+            for (int a = 0; a < na; ++a) {
+                const double x = __ldg(X + (int64_t)(a0 + a) * ldx + i);
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) acc[jj] = fma(cs[a * 16 + jj], x, acc[jj]);
+                for (int jj = 0; jj < 16; ++jj) acc[jj] = fma(cs[a * 16 + jj], x, acc[jj]);
+            }
     }
+    if (i >= n) return;
 #pragma unroll
     for (int jj = 0; jj < 16; ++jj)
         if (jj < nq) {
@@ -587,7 +594,7 @@ struct Ops {
         const double t0 = now_ms();
         cudaMemcpyAsync(w->small, C.data(), sizeof(double) * p * q, cudaMemcpyHostToDevice, s);
         dim3 g((unsigned)((n + 255) / 256), (q + 15) / 16);
-        combine_kernel<<<g, 256, sizeof(double) * p * 16, s>>>(X, ld, p, w->small, q, n, Y, ld, beta, 1.0);
+        combine_kernel<<<g, 256, 0, s>>>(X, ld, p, w->small, q, n, Y, ld, beta, 1.0);
         ++launches;
         // no wait: the next upload into w->small is ordered after this kernel
         // on the stream, and the pageable source is staged before the copy call returns
@@ -603,7 +610,7 @@ struct Ops {
         gram_partial_kernel<<<g, 256, 0, s>>>(X, ld, p, Y, ld, q, n, w->partial);
         reduce_kernel<<<(p * q + 255) / 256, 256, 0, s>>>(w->partial, chunks, p * q, w->proj);
         dim3 g2((unsigned)((n + 255) / 256), (q + 15) / 16);
-        combine_kernel<<<g2, 256, sizeof(double) * p * 16, s>>>(X, ld, p, w->proj, q, n, Y, ld, 1.0, -1.0);
+        combine_kernel<<<g2, 256, 0, s>>>(X, ld, p, w->proj, q, n, Y, ld, 1.0, -1.0);
         launches += 3;
         ms_gram += now_ms() - t0;
     }
