@@ -192,7 +192,10 @@ int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *out, hb_sta
    device [dim][k] row-major or NULL; v0: device [dim][k] start vectors or
    NULL (unit vectors at the smallest diagonal entries).  precond:
    HB_PRECOND_DIAG, or HB_PRECOND_MLP after hb_mlp_set, optionally OR
-   HB_DIAG_TENSOR (block products on the tensor cores).  Returns
+   HB_DIAG_TENSOR (block products on the tensor cores).  With HB_PRECOND_MLP
+   the solve falls back to the diagonal preconditioner for good when the
+   largest wanted residual has not halved over 10 iterations (counted in
+   st->mlp_fallbacks).  Returns
    HB_ERR_NOT_CONVERGED after max_iter iterations (evals then hold the current
    Ritz values). */
 int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, int32_t max_iter,
@@ -300,6 +303,15 @@ int hb_mlp_loss_grad(const float *params, const float *feats, const float *a, co
 int hb_mlp_adam(int64_t n_param, float *params, const float *grads, float *m, float *v, int32_t step,
                 float lr, void *stream);
 
+/* Adam training of the packed parameters (device, in place) on a device data
+   set feats [n][8], a [n], b [n] (loss of hb_mlp_loss_grad): `steps` updates,
+   each over the next window of `batch` samples (wrapping around), learning
+   rate lr; the last window's loss into *last_loss (host, may be NULL).  The
+   scratch is allocated and freed by the call.  Errors: HB_ERR_INVALID_ARG,
+   HB_ERR_OOM, HB_ERR_CUDA.  Not in the paper: the learned preconditioner. */
+int hb_mlp_train(float *params, const float *feats, const float *a, const float *b, int64_t n, int64_t batch,
+                 int32_t steps, float lr, float *last_loss, void *stream);
+
 /* Factors w(f_i) for n feature rows (device). */
 int hb_mlp_predict(const float *params, const float *feats, int64_t n, float *out, void *stream);
 
@@ -307,6 +319,12 @@ int hb_mlp_predict(const float *params, const float *feats, int64_t n, float *ou
    feats (device) [q][dim][8], as hb_diag computes them. */
 int hb_diag_features(hb_ctx *ctx, const hb_blocks *H, const double *theta, int32_t q, float *feats,
                      void *stream);
+
+/* A text description of a context (sizes of every class of Section 2.2,
+   the target groups, device memory, the build plan's launch shapes) written
+   to the file at `path`.  Errors: HB_ERR_INVALID_ARG (NULL argument or the
+   file cannot be written). */
+int hb_dump(const hb_ctx *ctx, const char *path);
 
 const char *hb_last_error(const hb_ctx *ctx);
 void hb_destroy(hb_ctx *ctx);

@@ -1,5 +1,6 @@
 // C ABI of the Hamiltonian build: validation, staging, orchestration.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -516,6 +517,28 @@ extern "C" int32_t hb_tuning_report(const hb_ctx *ctx, char *buf, int32_t len) {
     memcpy(buf, r.data(), n);
     buf[n] = 0;
     return (int32_t)r.size();
+}
+
+extern "C" int hb_dump(const hb_ctx *ctx, const char *path) {
+    if (!ctx || !path) return fail(nullptr, HB_ERR_INVALID_ARG, "NULL argument");
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(nullptr, HB_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    fprintf(f, "orbitals: %d target + %d continuum, n_words %d, electrons %d + 1 (continuum spin %s)\n", ctx->n_to,
+            ctx->n_co, ctx->W, ctx->n_elec, ctx->cont_spin == HB_SPIN_ALPHA ? "alpha" : "beta");
+    fprintf(f, "dimension %lld = contracted %lld + L2 %d\n", (long long)ctx->dim, (long long)ctx->Dc, ctx->n_l2);
+    fprintf(f, "labels K %d (padded %d), e_core %.17g, split slices %d\n", ctx->K, ctx->Kpad, ctx->e_core,
+            ctx->split_slices);
+    for (int g = 0; g < ctx->n_groups; ++g) {
+        const GroupInfo &G = ctx->groups[g];
+        fprintf(f, "group %d: %d determinants, %d states, continuum [%d, %d), rows from %lld\n", g, G.ndet, G.ns, G.cf,
+                G.cf + G.cn, (long long)G.row_off);
+    }
+    fprintf(f, "pairs within a double excitation: target x target %lld, target x L2 %lld, L2 x L2 %lld\n",
+            (long long)ctx->tt_pairs, (long long)ctx->tl2_pairs, (long long)ctx->l2_nnz);
+    fprintf(f, "device bytes %zu, borrows integrals: %s\n", ctx->dev_bytes, ctx->base ? "yes" : "no");
+    fprintf(f, "build plan: %s\n", ctx->plan ? plan_report((const hb::Plan *)ctx->plan).c_str() : "no build yet");
+    const bool ok = fclose(f) == 0;
+    return ok ? HB_OK : fail(nullptr, HB_ERR_INVALID_ARG, std::string("cannot write ") + path);
 }
 
 extern "C" const char *hb_last_error(const hb_ctx *ctx) {

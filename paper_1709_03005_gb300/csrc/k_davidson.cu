@@ -800,6 +800,8 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
     std::vector<double> theta;
     float *wts = nullptr;
     int fallbacks = 0;
+    constexpr int kStall = 10;
+    std::vector<double> res_hist;
     // projected matrix T = V^T A V, kept up to date on the host: the full
     // product for the start block, one border V^T (A V_new) per iteration, and
     // diag(theta) for the Ritz vectors kept at a restart
@@ -860,6 +862,15 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         if (m + q > mmax) q = mmax - m;
         if (q <= 0) break;
         cudaMemcpyAsync(w->idx, which.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, s);
+        // the learned factor is dropped for the rest of the solve when the
+        // largest wanted residual has not halved over the last kStall iterations
+        res_hist.push_back(maxres);
+        if (precond == HB_PRECOND_MLP && (int)res_hist.size() > kStall &&
+            maxres > 0.5 * res_hist[res_hist.size() - 1 - kStall]) {
+            precond = HB_PRECOND_DIAG;
+            wts = nullptr;
+            ++fallbacks;
+        }
         if (precond == HB_PRECOND_MLP) {
             int frc = mlp_weights_for(ctx, w, theta.data(), nr, &wts, s);
             if (frc != HB_OK) { wts = nullptr; ++fallbacks; }

@@ -379,6 +379,44 @@ extern "C" int hb_mlp_adam(int64_t n_param, float *params, const float *grads, f
     return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ERR_CUDA;
 }
 
+// Adam training over a device data set: the samples are taken in consecutive
+// windows of `batch` (wrapping around), one loss-and-gradient pass and one
+// update per step, the loss of the last step in *last_loss (host).  Scratch
+// (gradients, moments, workspace) is allocated and freed by the call.
+extern "C" int hb_mlp_train(float *params, const float *feats, const float *a, const float *b, int64_t n,
+                            int64_t batch, int32_t steps, float lr, float *last_loss, void *stream) {
+    if (!params || !feats || !a || !b || n <= 0 || batch <= 0 || steps < 1 || !(lr > 0.0f))
+        return HB_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t bs = batch < n ? batch : n;
+    float *g = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
+    void *work = nullptr;
+    cudaError_t e = cudaMalloc(&g, sizeof(float) * MLP_NPARAM);
+    if (e == cudaSuccess) e = cudaMalloc(&m, sizeof(float) * MLP_NPARAM);
+    if (e == cudaSuccess) e = cudaMalloc(&v, sizeof(float) * MLP_NPARAM);
+    if (e == cudaSuccess) e = cudaMalloc(&loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&work, (size_t)hb_mlp_workspace_bytes(bs));
+    if (e == cudaSuccess) e = cudaMemsetAsync(m, 0, sizeof(float) * MLP_NPARAM, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(float) * MLP_NPARAM, s);
+    int rc = e == cudaSuccess ? HB_OK : HB_ERR_OOM;
+    int64_t off = 0;
+    for (int32_t step = 1; step <= steps && rc == HB_OK; ++step) {
+        const int64_t cnt = off + bs <= n ? bs : n - off;
+        rc = hb_mlp_loss_grad(params, feats + off * MLP_IN, a + off, b + off, cnt, g, loss, work, stream);
+        if (rc == HB_OK) rc = hb_mlp_adam(MLP_NPARAM, params, g, m, v, step, lr, stream);
+        off += cnt;
+        if (off >= n) off = 0;
+    }
+    if (rc == HB_OK && last_loss) {
+        e = cudaMemcpyAsync(last_loss, loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = HB_ERR_CUDA;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(g); cudaFree(m); cudaFree(v); cudaFree(loss); cudaFree(work);
+    return rc;
+}
+
 extern "C" int hb_mlp_predict(const float *params, const float *feats, int64_t n, float *out, void *stream) {
     if (!params || !feats || !out || n <= 0) return HB_ERR_INVALID_ARG;
     mlp_predict_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(params, feats, n, out);

@@ -76,7 +76,8 @@ assert PAIR_DTYPE.itemsize == 24
 EXPORTS = ["hb_init", "hb_init_shared", "hb_batch_create", "hb_batch_launch", "hb_batch_nodes",
            "hb_batch_destroy", "hb_query", "hb_group_offset", "hb_build_blocks", "hb_diag", "hb_classify",
            "hb_classify_noalloc", "hb_mlp_set", "hb_mlp_param_count", "hb_mlp_workspace_bytes", "hb_mlp_loss_grad",
-           "hb_mlp_adam", "hb_mlp_predict", "hb_diag_features", "hb_batch_report", "hb_tuning_report",
+           "hb_mlp_adam", "hb_mlp_train", "hb_mlp_predict", "hb_diag_features", "hb_batch_report", "hb_tuning_report",
+           "hb_dump",
            "hb_last_error", "hb_destroy"]
 
 _lib = None
@@ -244,6 +245,12 @@ class Hamiltonian:
         """Load a packed parameter vector (see unpack_mlp) for HB_PRECOND_MLP."""
         self.set_mlp(*unpack_mlp(packed))
 
+    def dump(self, path):
+        """hb_dump: a text description of the context into the file at path."""
+        self.lib.hb_dump.argtypes = [C.c_void_p, C.c_char_p]
+        self.lib.hb_dump.restype = C.c_int
+        _check(self.lib.hb_dump(self.ctx, str(path).encode()), self.ctx)
+
     def tuning_report(self):
         """Launch shapes of this context's build plan (after a build), as text."""
         self.lib.hb_tuning_report.argtypes = [C.c_void_p, C.c_char_p, C.c_int32]
@@ -352,6 +359,8 @@ def _mlp_fns():
     lib.hb_mlp_adam.restype = C.c_int
     lib.hb_mlp_predict.argtypes = [vp, vp, i64, vp, vp]
     lib.hb_mlp_predict.restype = C.c_int
+    lib.hb_mlp_train.argtypes = [vp, vp, vp, vp, i64, i64, i32, C.c_float, C.POINTER(C.c_float), vp]
+    lib.hb_mlp_train.restype = C.c_int
     lib.hb_diag_features.argtypes = [vp, C.POINTER(hb_blocks), vp, i32, vp, vp]
     lib.hb_diag_features.restype = C.c_int
     return lib
@@ -378,6 +387,15 @@ def mlp_loss_grad(params, feats, a, b, work=None, stream=None):
 def mlp_adam(params, grads, m, v, step, lr, stream=None):
     _check(_mlp_fns().hb_mlp_adam(params.numel(), _ptr(params), _ptr(grads), _ptr(m), _ptr(v), step, lr,
                                   _stream_handle(stream)))
+
+
+def mlp_train(params, feats, a, b, batch, steps, lr, stream=None):
+    """hb_mlp_train: Adam over consecutive windows of the data set, params updated in place;
+    returns the loss of the last window."""
+    loss = C.c_float(0.0)
+    _check(_mlp_fns().hb_mlp_train(_ptr(params), _ptr(feats), _ptr(a), _ptr(b), feats.shape[0], batch, steps, lr,
+                                   C.byref(loss), _stream_handle(stream)))
+    return loss.value
 
 
 def mlp_predict(params, feats, stream=None):

@@ -73,3 +73,37 @@ def test_unit_network_reproduces_plain_davidson():
     assert s0.iterations == s1.iterations
     np.testing.assert_allclose(w0, w1, atol=1e-9)
     H.close()
+
+
+def test_train_loop_matches_the_separate_calls():
+    """hb_mlp_train is loss-and-gradient plus Adam over consecutive windows
+    (wrapping around): the same kernels called one by one give the same bits,
+    and the returned loss is the oracle's loss of the last window."""
+    import torch
+    from paper_1709_03005_gb300 import hb
+    p, f, a, b = _random(3, n=2500, scale=0.1)
+    t = lambda x: torch.from_numpy(x.copy()).cuda()
+    tf, ta, tb = t(f), t(a), t(b)
+    pt = t(p)
+    last = hb.mlp_train(pt, tf, ta, tb, 1000, 4, 1e-3)
+    pr = t(p)
+    m = torch.zeros_like(pr)
+    v = torch.zeros_like(pr)
+    windows = [(0, 1000), (1000, 2000), (2000, 2500), (0, 1000)]
+    for step, (lo, hi) in enumerate(windows, 1):
+        if step == 4:
+            p3 = pr.cpu().numpy().astype(np.float64)
+        loss, g = hb.mlp_loss_grad(pr, tf[lo:hi].contiguous(), ta[lo:hi].contiguous(), tb[lo:hi].contiguous())
+        hb.mlp_adam(pr, g, m, v, step, 1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(pt, pr)
+    assert last == float(loss)
+    # the loss of the last window at the parameters it was taken at
+    ref, _ = mlp.loss_grad(p3, f[:1000].astype(np.float64), a[:1000].astype(np.float64),
+                           b[:1000].astype(np.float64))
+    assert abs(last - ref) <= 1e-5 * abs(ref)
+    assert not np.array_equal(p3, p.astype(np.float64))
+    with pytest.raises(hb.HBError):
+        hb.mlp_train(pt, tf, ta, tb, 0, 4, 1e-3)
+    with pytest.raises(hb.HBError):
+        hb.mlp_train(pt, tf, ta, tb, 100, 0, 1e-3)

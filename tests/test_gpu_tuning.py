@@ -86,3 +86,20 @@ def test_batch_reports_its_choices():
     rep = B.report()
     assert rep.startswith("tuned=1") and "split" in rep and "class4" in rep, rep
     B.close()
+
+
+def test_dump_describes_the_context(tmp_path):
+    from paper_1709_03005_gb300 import hb
+    P = _problems()[0]
+    H = hb.Hamiltonian(P)
+    path = tmp_path / "ctx.txt"
+    H.dump(path)
+    text = path.read_text()
+    assert f"dimension {P.dim}" in text and "no build yet" in text
+    assert text.count("\ngroup ") == 3
+    H.build(hb.HB_MIXED)
+    H.dump(path)
+    assert "build plan: tuned=0" in path.read_text()
+    with pytest.raises(hb.HBError):
+        H.dump(tmp_path / "missing" / "ctx.txt")
+    H.close()
