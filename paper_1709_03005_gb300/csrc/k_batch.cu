@@ -81,7 +81,7 @@ extern "C" int hb_batch_create(hb_batch **out, hb_ctx *const *ctxs, int32_t n, i
     }
     cudaStreamDestroy(cs);
     if (rc == HB_OK) {
-        e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        e = cudaGraphInstantiate(&b->exec, b->graph, cudaGraphInstantiateFlagUseNodePriority);
         if (e != cudaSuccess) rc = bfail(HB_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
         else cudaGraphGetNodes(b->graph, nullptr, &b->nodes);
     }

@@ -111,8 +111,14 @@ struct Plan {
     CUtensorMap tm_coef;
     int64_t coef_rows = 0;
     int *err = nullptr;
-    // timers: target, expansion, class 4, L2 boundaries; split kernels
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // classes 4, 2 and 8 run on a second stream beside the target side and
+    // the expansion (they read only staged data and write their own blocks);
+    // the target side and the expansion, the longer chain, at higher priority
+    cudaStream_t main = nullptr, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, join_main = nullptr;
+    // timers: start, target, expansion (main stream); class 4, L2, side start
+    // (side stream); end after the join; split kernels
+    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> ev_split;
     int launches = 0, expand_launches = 0;
     bool timed = false;
@@ -449,8 +455,15 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
         }
     int rc = HB_OK;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&p->ev[i]);
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreate(&p->ev[i]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->uploaded, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join_main, cudaEventDisableTiming);
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->main, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, least);
     if (e == cudaSuccess) e = cudaMalloc(&p->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, sizeof(int), s);
     if (e != cudaSuccess) {
@@ -685,18 +698,27 @@ std::string plan_report(const Plan *p) {
 
 int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, std::string *err) {
     int L = 0, LX = 0;
+    const cudaStream_t s0 = s;
     const int W = p->W;
     // the mixed build runs the target side and class 4 in double-float on the
     // FP32 pipes, the plain build in FP64
     const int DF = p->precision == HB_MIXED ? 1 : 0;
     p->timed = timing;
     // inside a capture an event record becomes a graph node only when external
-    auto rec = [&](cudaEvent_t e) {
+    auto rec_on = [&](cudaEvent_t e, cudaStream_t st) {
         if (!timing) return;
-        if (capture) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
-        else cudaEventRecord(e, s);
+        if (capture) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+        else cudaEventRecord(e, st);
     };
-    rec(p->ev[0]);
+    rec_on(p->ev[0], s);
+    // fork: both chains wait for the caller's stream (inside a capture the
+    // internal streams join the capture here)
+    cudaStream_t s2 = p->side;
+    cudaEventRecord(p->fork, s);
+    cudaStreamWaitEvent(p->main, p->fork, 0);
+    cudaStreamWaitEvent(s2, p->fork, 0);
+    s = p->main;
+    auto rec = [&](cudaEvent_t e) { rec_on(e, s); };
     // target side (Eq. 8): classes, H^N, S, E, gamma, coefficient rows
     L += g_classify(p->cls_tt.g, W, 0, s);
     L += g_pair_values(p->pv.g, W, DF, s);
@@ -731,15 +753,23 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     }
     L += LX;
     rec(p->ev[2]);
+    cudaEventRecord(p->join_main, s);
     // class 4 (Eq. 5)
-    L += g_classify(p->cls_tl2.g, W, 1, s);
-    for (auto &v : p->c4v) L += g_class4(v.st.g, W, p->precision == HB_MIXED ? 1 : 0, v.ns_tile, v.jt, s);
-    rec(p->ev[3]);
+    rec_on(p->ev[5], s2);
+    L += g_classify(p->cls_tl2.g, W, 1, s2);
+    for (auto &v : p->c4v) L += g_class4(v.st.g, W, p->precision == HB_MIXED ? 1 : 0, v.ns_tile, v.jt, s2);
+    rec_on(p->ev[3], s2);
     // classes 2 and 8
     // the L2 rows stay FP64: their sums are short and the kernel is bound by the
     // pair scan, where the longer double-float sums cost more than FP64 adds
-    L += g_l2_csr(p->l2.g, W, 0, s);
-    rec(p->ev[4]);
+    L += g_l2_csr(p->l2.g, W, 0, s2);
+    rec_on(p->ev[4], s2);
+    cudaEventRecord(p->join, s2);
+    // join into the caller's stream
+    s = s0;
+    cudaStreamWaitEvent(s, p->join_main, 0);
+    cudaStreamWaitEvent(s, p->join, 0);
+    rec(p->ev[6]);
     cudaError_t e = cudaGetLastError();
     p->launches = L;
     p->expand_launches = LX;
@@ -757,11 +787,11 @@ void plan_stats(Plan *p, hb_stats *st) {
     st->expand_launches = p->expand_launches;
     st->expand_flops = p->flops;
     if (!p->timed) return;
-    cudaEventSynchronize(p->ev[4]);
-    cudaEventElapsedTime(&st->ms_total, p->ev[0], p->ev[4]);
+    cudaEventSynchronize(p->ev[6]);
+    cudaEventElapsedTime(&st->ms_total, p->ev[0], p->ev[6]);
     cudaEventElapsedTime(&st->ms_target, p->ev[0], p->ev[1]);
     cudaEventElapsedTime(&st->ms_expand, p->ev[1], p->ev[2]);
-    cudaEventElapsedTime(&st->ms_class4, p->ev[2], p->ev[3]);
+    cudaEventElapsedTime(&st->ms_class4, p->ev[5], p->ev[3]);
     cudaEventElapsedTime(&st->ms_l2, p->ev[3], p->ev[4]);
     if (p->precision == HB_MIXED) {
         float total = 0.0f;
@@ -790,6 +820,14 @@ void plan_destroy(Plan *p) {
     for (cudaEvent_t e : p->ev_split)
         if (e) cudaEventDestroy(e);
     if (p->uploaded) cudaEventDestroy(p->uploaded);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->join) cudaEventDestroy(p->join);
+    if (p->join_main) cudaEventDestroy(p->join_main);
+    for (cudaStream_t st : {p->main, p->side})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
     if (p->dev) cudaFree(p->dev);
     if (p->pinned) cudaFreeHost(p->pinned);
     if (p->coef) cudaFree(p->coef);
