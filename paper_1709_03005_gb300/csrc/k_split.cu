@@ -167,31 +167,62 @@ __device__ __forceinline__ void drain_chunk(uint32_t tbase, int stride, float (&
     constexpr int n_acc = S < 4 ? S : 4;       // accumulators written by the MMAs
 #pragma unroll
     for (int c0 = 0; c0 < EPI_COLS; c0 += 16) {
-        float v[16], w[16];
-        tmem_ld16(tbase + c0, v);
-        if (n_acc > 1) tmem_ld16(tbase + stride + c0, w);
+        // two accumulators' 16 columns in flight together, one wait each pair
+        uint32_t v[16], w[16];
+        tmem_ld16_async(tbase + c0, v);
+        if (n_acc > 1) tmem_ld16_async(tbase + stride + c0, w);
+        tmem_wait_ld();
+        tmem_regs_ready(v);
+        if (n_acc > 1) tmem_regs_ready(w);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            df_add(hi[c0 + i], lo[c0 + i], v[i]);
-            if (n_acc > 1) df_add(hi[c0 + i], lo[c0 + i], w[i]);
+            df_add(hi[c0 + i], lo[c0 + i], __uint_as_float(v[i]));
+            if (n_acc > 1) df_add(hi[c0 + i], lo[c0 + i], __uint_as_float(w[i]));
         }
         if (n_acc > 2) {
-            tmem_ld16(tbase + 2 * stride + c0, v);
-            if (n_acc > 3) tmem_ld16(tbase + 3 * stride + c0, w);
+            tmem_ld16_async(tbase + 2 * stride + c0, v);
+            if (n_acc > 3) tmem_ld16_async(tbase + 3 * stride + c0, w);
+            tmem_wait_ld();
+            tmem_regs_ready(v);
+            if (n_acc > 3) tmem_regs_ready(w);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                df_add(hi[c0 + i], lo[c0 + i], v[i]);
-                if (n_acc > 3) lo[c0 + i] = __fadd_rn(lo[c0 + i], w[i]);
+                df_add(hi[c0 + i], lo[c0 + i], __uint_as_float(v[i]));
+                if (n_acc > 3) lo[c0 + i] = __fadd_rn(lo[c0 + i], __uint_as_float(w[i]));
             }
         }
     }
 }
 
+// Position of tile `tile` of a grouped launch: its task, the first rows of
+// its continuum-pair block and its first column.
+struct TilePos {
+    int ti, jj0, jjp0, n0;
+};
+
+__device__ __forceinline__ TilePos tile_pos(const SplitTask *__restrict__ tasks, const int64_t *__restrict__ blk,
+                                            int n_tasks, int tile) {
+    TilePos p;
+    p.ti = task_of(blk, n_tasks, tile);
+    const int lb = (int)(tile - __ldg(blk + p.ti));
+    const SplitTask &a = tasks[p.ti];
+    const int ntn = a.ntn, jpt_tiles = a.jpt_tiles, lg = a.bjp_log2;
+    const int tile_n = lb % ntn, tile_m = lb / ntn;   // N fastest: CTAs sharing a panel tile run together
+    p.jj0 = (tile_m / jpt_tiles) * (BM >> lg);        // tile of (128 >> lg) j x (1 << lg) j'
+    p.jjp0 = (tile_m % jpt_tiles) << lg;
+    p.n0 = tile_n * BN;
+    return p;
+}
+
+// Persistent: each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// The slot ring, the accumulator hand-over and their barrier phases run on
+// across tiles, so the loads and MMAs of the next tile start while the
+// epilogue warps still write the last one out from registers.
 template <int S>
 __global__ void __launch_bounds__(NTHREADS, 1)
 split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_constant__ CUtensorMap tm_coef,
-                    const SplitTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks, int kblocks,
-                    const ExpCol *__restrict__ cols, int *err) {
+                    const SplitTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks, int n_tiles,
+                    int kblocks, const ExpCol *__restrict__ cols, int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *slots = base;                                  // [S][SLOT]
@@ -201,36 +232,18 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     uint64_t *acc_empty = acc_full + 1;                     // [1]
     uint64_t *final_bar = acc_empty + 1;                    // [1]
     uint32_t *tmem_slot = (uint32_t *)(final_bar + 1);
+    // the epilogue's tile: arguments and column destinations, double-buffered
+    __shared__ SplitTask ta[2];
+    __shared__ TilePos tp[2];
+    __shared__ ExpCol colmeta[2][BN];
+    __shared__ int epi_fail;                 // an epilogue wait gave up (read only after a barrier)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // the task's arguments in shared memory: read where needed, not held in registers
-    __shared__ SplitTask a;
-    __shared__ int lb_s;
-    if (threadIdx.x == 0) {
-        const int ti = task_of(blk, n_tasks, blockIdx.x);
-        a = tasks[ti];
-        lb_s = (int)(blockIdx.x - blk[ti]);
-    }
-    __syncthreads();
-    const int lb = lb_s;
-    const int tile_n = lb % a.ntn, tile_m = lb / a.ntn;     // N fastest: CTAs sharing a panel tile run together
-    const int lg = a.bjp_log2;                              // tile of (128 >> lg) j x (1 << lg) j'
-    const int jt = tile_m / a.jpt_tiles, jpt = tile_m % a.jpt_tiles;
-    const int jj0 = jt * (BM >> lg), jjp0 = jpt << lg;      // within the group ranges
-    const int n0 = tile_n * BN;
     const int kb_per_chunk = KCHUNK / BKB;
     const int nchunks = (kblocks + kb_per_chunk - 1) / kb_per_chunk;
-    // destinations of this tile's 128 columns (ExpCol with H == null: no column)
-    __shared__ ExpCol colmeta[BN];
-    if (threadIdx.x < BN) {
-        const int t = n0 + threadIdx.x;
-        ExpCol c;
-        if (t < a.N) c = cols[a.col0 + t];
-        else c.H = nullptr;
-        colmeta[threadIdx.x] = c;
-    }
 
     if (threadIdx.x == 0) {
+        epi_fail = 0;
         for (int i = 0; i < MAXS; ++i) { mbar_init(&full_bar[i], 1); mbar_init(&empty_bar[i], 1); }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, EPI_THREADS);
@@ -251,24 +264,29 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
         if (lane == 0) {
-            int kb = 0;
+            int G = 0;                            // K blocks issued by this CTA over all its tiles
             bool ok = true;
-            for (; kb < kblocks && ok; ++kb) {
-                for (int t = 0; t < S && ok; ++t) {
-                    const int sl = (kb & 1) ? slot_of<S>(1, t) : t;
-                    // each slot is filled once per K block: wait for its release in block kb-1
-                    if (kb > 0) ok = mbar_wait(&empty_bar[sl], (kb - 1) & 1, err, 1);
-                    if (!ok) break;
-                    uint8_t *sA = slots + sl * SLOT;
-                    mbar_expect_tx(&full_bar[sl], (uint32_t)SLOT);
-                    const int plane = t * kblocks + kb;
-                    tma_load_4d(sA, &tm_panel, &full_bar[sl], 0, a.cfp + jjp0, a.cf + jj0, plane);
-                    tma_load_3d(sA + A_TILE, &tm_coef, &full_bar[sl], 0, (int)(a.coef_row0 + n0), plane);
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                const TilePos p = tile_pos(tasks, blk, n_tasks, tile);
+                const int cx = tasks[p.ti].cfp + p.jjp0, cy = tasks[p.ti].cf + p.jj0;
+                const int crow = (int)(tasks[p.ti].coef_row0 + p.n0);
+                for (int kb = 0; kb < kblocks && ok; ++kb, ++G) {
+                    for (int t = 0; t < S && ok; ++t) {
+                        const int sl = (G & 1) ? slot_of<S>(1, t) : t;
+                        // each slot is filled once per K block: wait for its release in block G-1
+                        if (G > 0) ok = mbar_wait(&empty_bar[sl], (G - 1) & 1, err, 1);
+                        if (!ok) break;
+                        uint8_t *sA = slots + sl * SLOT;
+                        mbar_expect_tx(&full_bar[sl], (uint32_t)SLOT);
+                        const int plane = t * kblocks + kb;
+                        tma_load_4d(sA, &tm_panel, &full_bar[sl], 0, cx, cy, plane);
+                        tma_load_3d(sA + A_TILE, &tm_coef, &full_bar[sl], 0, crow, plane);
+                    }
                 }
             }
             // wait until this producer's copies of the last block have landed
-            if (kb > 0)
-                for (int sl = 0; sl < S; ++sl) mbar_wait(&full_bar[sl], (kb - 1) & 1, err, 2);
+            if (G > 0)
+                for (int sl = 0; sl < S; ++sl) mbar_wait(&full_bar[sl], (G - 1) & 1, err, 2);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
@@ -276,46 +294,77 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
             const uint32_t idesc = instr_desc_bf16(BM, BN);
             const uint64_t desc0 = smem_desc_sw128(smem_u32(slots));   // + (offset >> 4) per operand tile
             bool ok = true;
-            int kb = 0;
-            for (int c = 0; c < nchunks && ok; ++c) {
-                if (c > 0) ok = mbar_wait(acc_empty, (c - 1) & 1, err, 3);
-                if (!ok) break;
-                tc_fence_after();
-                const int kb_end = min(kblocks, (c + 1) * kb_per_chunk);
-                uint32_t fresh = 0xFu;           // accumulators not yet written in this chunk
-                for (; kb < kb_end && ok; ++kb) {
-                    if (kb & 1) ok = mma_block<S, 1>(full_bar, empty_bar, 1u, tmem, desc0, idesc, fresh, err);
-                    else ok = mma_block<S, 0>(full_bar, empty_bar, 0u, tmem, desc0, idesc, fresh, err);
+            int G = 0, C = 0;                     // K blocks and chunks over all tiles
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                for (int c = 0; c < nchunks && ok; ++c, ++C) {
+                    if (C > 0) ok = mbar_wait(acc_empty, (C - 1) & 1, err, 3);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const int kb_end = min(kblocks, (c + 1) * kb_per_chunk);
+                    uint32_t fresh = 0xFu;        // accumulators not yet written in this chunk
+                    for (int kb = c * kb_per_chunk; kb < kb_end && ok; ++kb, ++G) {
+                        if (G & 1) ok = mma_block<S, 1>(full_bar, empty_bar, 1u, tmem, desc0, idesc, fresh, err);
+                        else ok = mma_block<S, 0>(full_bar, empty_bar, 0u, tmem, desc0, idesc, fresh, err);
+                    }
+                    if (ok) mma_commit(acc_full);         // accumulators of chunk C complete
                 }
-                if (ok) mma_commit(acc_full);             // accumulators of chunk c complete
             }
             mma_commit(final_bar);
             mbar_wait(final_bar, 0, err, 5);
         }
     } else {
         // ------------------------------------------------------ epilogue
+        const int e = threadIdx.x - 64;          // 0 .. EPI_THREADS-1
         const int ew = warp - 2;
         const int q = warp & 3;                  // TMEM lane quadrant this warp may access
         const int col0 = (ew >> 2) * EPI_COLS;
         const int row = q * 32 + lane;           // tile row = TMEM lane
-        float hi[EPI_COLS], lo[EPI_COLS];
+        int C = 0, it = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+            const int buf = it & 1;
+            // the buffer was last read by the stores of tile it-2, which every
+            // epilogue warp finished before the barriers of tile it-1
+            if (e == 0) {
+                tp[buf] = tile_pos(tasks, blk, n_tasks, tile);
+                ta[buf] = tasks[tp[buf].ti];
+            }
+            // every epilogue thread reaches both barriers of a tile, so the
+            // failure flag read after the first is the same for all of them
+            named_bar_sync(1, EPI_THREADS);
+            if (epi_fail) break;
+            const SplitTask &a = ta[buf];
+            if (e < BN) {
+                const int t = tp[buf].n0 + e;
+                ExpCol cm;
+                if (t < a.N) cm = cols[a.col0 + t];
+                else cm.H = nullptr;
+                colmeta[buf][e] = cm;
+            }
+            named_bar_sync(1, EPI_THREADS);
+            float hi[EPI_COLS], lo[EPI_COLS];
 #pragma unroll
-        for (int c = 0; c < EPI_COLS; ++c) { hi[c] = 0.0f; lo[c] = 0.0f; }
-        bool ok = true;
-        for (int c = 0; c < nchunks && ok; ++c) {
-            ok = mbar_wait(acc_full, c & 1, err, 6);
-            if (!ok) break;
-            tc_fence_after();
-            drain_chunk<S>(tmem + ((uint32_t)(q * 32) << 16) + col0, BN, hi, lo);
-            tc_fence_before();
-            mbar_arrive(acc_empty);
-        }
-        if (ok) {
-            const int jj = jj0 + (row >> lg), jjp = jjp0 + (row & ((1 << lg) - 1));
+            for (int c = 0; c < EPI_COLS; ++c) { hi[c] = 0.0f; lo[c] = 0.0f; }
+            bool ok = true;
+            for (int c = 0; c < nchunks; ++c, ++C) {
+                if (ok) ok = mbar_wait(acc_full, C & 1, err, 6);
+                if (!ok) continue;
+                tc_fence_after();
+                drain_chunk<S>(tmem + ((uint32_t)(q * 32) << 16) + col0, BN, hi, lo);
+                tc_fence_before();
+                mbar_arrive(acc_empty);
+            }
+            if (!ok) {
+                epi_fail = 1;
+                continue;                        // leaves at the next tile's first barrier
+            }
+            // the accumulators are free again: the MMAs of the next tile run
+            // while this one is written out
+            const int lg = a.bjp_log2;
+            const int jj = tp[buf].jj0 + (row >> lg), jjp = tp[buf].jjp0 + (row & ((1 << lg) - 1));
             if (jj < a.cn && jjp < a.cnp && (a.cf + jj) != (a.cfp + jjp)) {
 #pragma unroll
                 for (int c = 0; c < EPI_COLS; ++c) {
-                    const ExpCol &m = colmeta[col0 + c];
+                    const ExpCol &m = colmeta[buf][col0 + c];
                     if (m.H) {
                         const int64_t r = m.rbase + jj;
                         const int64_t cc = m.cbase + jjp;
@@ -666,8 +715,25 @@ EncodeTiled encode_fn() {
 
 }  // namespace
 
+// dynamic shared memory of the expansion kernel: the operand slots, the
+// barriers and the 1 KB alignment
+static int split_smem_bytes(int S) { return S * SLOT + 2048; }
+
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 1;
+    }
+    return n;
+}
+
 static cudaError_t set_smem_attr(int S) {
-    const int bytes = S * SLOT + 2048;
+    const int bytes = split_smem_bytes(S);
     switch (S) {
         case 2: return cudaFuncSetAttribute(split_expand_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         case 3: return cudaFuncSetAttribute(split_expand_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -798,15 +864,20 @@ int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const G
     if (g.blocks <= 0) return 0;
     const MixedState &M = *panel_ctx->mixed;
     const CUtensorMap &tm_panel = M.tm_panel[lg - 3];
-    const size_t smem = M.slices * SLOT + 2048;
-    const unsigned grid = (unsigned)g.blocks;
+    const size_t smem = split_smem_bytes(M.slices);
+    // persistent: one CTA per SM at most (each holds all of its SM's tensor memory)
+    const int n_tiles = (int)g.blocks;
+    const unsigned grid = (unsigned)std::min(n_tiles, sm_count());
+#define HB_SPLIT(SS) \
+    split_expand_kernel<SS><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, n_tiles, kblocks, cols, err)
     switch (M.slices) {
-        case 2: split_expand_kernel<2><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
-        case 3: split_expand_kernel<3><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
-        case 4: split_expand_kernel<4><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
-        case 5: split_expand_kernel<5><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
-        default: split_expand_kernel<6><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, kblocks, cols, err); break;
+        case 2: HB_SPLIT(2); break;
+        case 3: HB_SPLIT(3); break;
+        case 4: HB_SPLIT(4); break;
+        case 5: HB_SPLIT(5); break;
+        default: HB_SPLIT(6); break;
     }
+#undef HB_SPLIT
     return 1;
 }
 
