@@ -203,7 +203,9 @@ struct L2Task {         // classes 2 and 8: L2-L2 CSR of one Hamiltonian
 int g_classify(const Grouped<ClsTask> &g, int W, int mode, cudaStream_t s);
 int g_pair_values(const Grouped<PVTask> &g, int W, int dfloat, cudaStream_t s);
 int g_l2_csr(const Grouped<L2Task> &g, int W, int dfloat, cudaStream_t s);
-int g_sandwich(const Grouped<SWTask> &g, int dfloat, cudaStream_t s);
+// width: states per pass of the double-float kernel (16, 24 or 32; the
+// largest state count of the launch, rounded up, passes of 32 beyond)
+int g_sandwich(const Grouped<SWTask> &g, int dfloat, int width, cudaStream_t s);
 int g_sandwich_small(const Grouped<SWTask> &g, int dfloat, cudaStream_t s);    // nsp <= 32 (used for nsp <= 16)
 int g_tn_partial(const Grouped<TNTask> &g, size_t smem, int dfloat, cudaStream_t s);
 int g_tn_reduce(const Grouped<TNTask> &g, int dfloat, cudaStream_t s);

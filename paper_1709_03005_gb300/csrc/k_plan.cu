@@ -75,6 +75,7 @@ struct Plan {
     Stage<ClsTask> cls_tt, cls_tl2;
     Stage<PVTask> pv;
     Stage<SWTask> sw, sws;             // sandwich: lanes over records / over states
+    int sw_width = 16;                 // states per pass of the record-lane sandwich
     Stage<TNTask> tn, tnr;
     Stage<IFTask> itf;
     Stage<ZTask> zero;
@@ -157,7 +158,7 @@ void stage_bind(Stage<T> &st, uint8_t *dev) {
 
 // Task tables of every stage from the contexts and the output blocks.
 void fill_tasks(Plan &p) {
-    p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.sw.clear(); p.sws.clear(); p.gamw.clear(); p.gdp.clear(); p.gdr.clear(); p.tn.clear(); p.tnr.clear();
+    p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.sw.clear(); p.sws.clear(); p.sw_width = 16; p.gamw.clear(); p.gdp.clear(); p.gdr.clear(); p.tn.clear(); p.tnr.clear();
     p.itf.clear(); p.zero.clear(); p.sort.clear(); p.scan.clear(); p.gam.clear(); p.asmb.clear();
     p.x64.clear(); p.slc.clear(); p.drows.clear(); p.l2.clear();
     for (auto &v : p.c4v) v.st.clear();
@@ -211,8 +212,12 @@ void fill_tasks(Plan &p) {
             p.pv.add(PVTask{I, da, db, P.pairs, P.n_pairs, P.val}, blocks_pair_values(P.n_pairs));
             // lanes over the states for at most 16 of them (two or more record
             // groups per warp), lanes over the records otherwise
-            (B.ns <= 16 ? p.sws : p.sw).add(SWTask{P.pairs, P.rowptr, P.val, A.ndet, Cb, Cb_df, B.ns, P.W},
-                                                blocks_rows8(A.ndet));
+            {
+                const SWTask sw{P.pairs, P.rowptr, P.val, A.ndet, Cb, Cb_df, B.ns, P.W};
+                if (B.ns <= 16) p.sws.add(sw, blocks_rows8(A.ndet));
+                else p.sw.add(sw, A.ndet);                    // a block per row
+            }
+            if (B.ns > 16) p.sw_width = std::max(p.sw_width, B.ns <= 24 ? 24 : 32);
             const int ny = tn_ny(A.ns, B.ns);
             // E = C^T (H^N C'); S = C^T C within a group (identical determinants
             // only, hb_init rejects repeats) and zero between groups
@@ -225,7 +230,7 @@ void fill_tasks(Plan &p) {
             p.tnr.add(ts, blocks_tn_reduce(A.ns, B.ns));
             p.smem_tn = std::max(p.smem_tn, smem_stage(A.ns, B.ns));
             p.itf.add(IFTask{P.pairs, P.rowptr, A.ndet, da, W, ctx->n_to, ctx->n_elec, P.item_ptr, P.items},
-                      blocks_rows8(A.ndet));
+                      A.ndet);                                // a block per row
             const int nc = P.n_chunks;
             const int64_t n_off = (int64_t)n_keys * nc;
             p.zero.add(ZTask{P.sort_off, n_off + 1}, blocks_zero(n_off + 1));
@@ -330,7 +335,7 @@ void fill_tasks(Plan &p) {
                     ++t;
                 }
             if (p.precision == HB_MIXED)
-                p.slc.add(SliceTask{P.A, P.n_nn, coef_row + (mstart - col0)}, blocks_rows8(P.n_nn));
+                p.slc.add(SliceTask{P.A, P.n_nn, coef_row + (mstart - col0)}, P.n_nn);   // a block per row
         }
         const int N = (int)((int64_t)p.cols.size() - col0);
         const BlockKey &k = B.key;
@@ -722,7 +727,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     // target side (Eq. 8): classes, H^N, S, E, gamma, coefficient rows
     L += g_classify(p->cls_tt.g, W, 0, s);
     L += g_pair_values(p->pv.g, W, DF, s);
-    L += g_sandwich(p->sw.g, DF, s);
+    L += g_sandwich(p->sw.g, DF, p->sw_width, s);
     L += g_sandwich_small(p->sws.g, DF, s);
     L += g_tn_partial(p->tn.g, p->smem_tn, DF, s);
     L += g_tn_reduce(p->tnr.g, DF, s);

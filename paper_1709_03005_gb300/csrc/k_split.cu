@@ -530,25 +530,20 @@ __global__ void dense_reduce_kernel(const float2 *__restrict__ part, int nsplit,
     Y[(int64_t)n * ldy + m] = df_to_double(h, l);
 }
 
-// Rows of [X1 | X2] (K1 then K2 entries, row strides ld1, ld2; X2 may be
-// absent) into bf16 slices [S][Kpad/64][R][64], one warp per row, the same
-// digits as slice_row.
-__global__ void slice_rows2_kernel(const double *__restrict__ X1, int64_t ld1, int K1, const double *__restrict__ X2,
-                                   int64_t ld2, int K2, int64_t rows, int Kpad, int S, int64_t R,
-                                   __nv_bfloat16 *__restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= rows) return;
-    const double *x1 = X1 + row * ld1;
-    const double *x2 = X2 ? X2 + row * ld2 : nullptr;
-    auto at = [&](int k) -> double { return k < K1 ? x1[k] : ((x2 && k < K1 + K2) ? x2[k - K1] : 0.0); };
-    const int KB = Kpad / BKB;
+// One row into its S bf16 slices by a whole block (the digits of slice_row):
+// every thread reads its share of the row, the row exponent is reduced through
+// shared memory, then each thread writes the digits of its elements.  at(k)
+// gives element k (0 beyond the row's data).
+template <class At>
+__device__ __forceinline__ void slice_row_block(At at, int64_t dest, int64_t R, int Kpad, int S,
+                                                __nv_bfloat16 *__restrict__ out) {
+    __shared__ int red[32];
     int emax = -2000;
-    for (int k = lane; k < Kpad; k += 32) {
+    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(at(k));
         const int be = (int)((b >> 52) & 0x7FF);
-        if (be == 0) continue;
-        const int e = be - 1022;
+        if (be == 0) continue;                 // zero (FP64 subnormals ignored)
+        const int e = be - 1022;               // |x| in [2^(e-1), 2^e)
         emax = e > emax ? e : emax;
     }
 #pragma unroll
@@ -556,17 +551,23 @@ __global__ void slice_rows2_kernel(const double *__restrict__ X1, int64_t ld1, i
         const int o = __shfl_xor_sync(0xffffffffu, emax, off);
         emax = o > emax ? o : emax;
     }
-    for (int k = lane; k < Kpad; k += 32) {
+    const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) red[warp] = emax;
+    __syncthreads();
+    emax = -2000;
+    for (int w = 0; w < nw; ++w) emax = red[w] > emax ? red[w] : emax;
+    const int KB = Kpad / BKB;
+    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
         long long F = 0;
         if (emax > -2000) {
             const unsigned long long b = (unsigned long long)__double_as_longlong(at(k));
             const int be = (int)((b >> 52) & 0x7FF);
             if (be != 0) {
-                const long long mnt = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-                const int sh = (be - 1075) + 7 * S - emax;
+                const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));   // x = m 2^(be-1075)
+                const int sh = (be - 1075) + 7 * S - emax;      // F = m 2^sh, rounded to nearest
                 long long f;
-                if (sh >= 0) f = mnt << sh;
-                else if (sh > -63) f = (mnt + (1ll << (-sh - 1))) >> (-sh);
+                if (sh >= 0) f = m << sh;
+                else if (sh > -63) f = (m + (1ll << (-sh - 1))) >> (-sh);
                 else f = 0;
                 F = (b >> 63) ? -f : f;
             }
@@ -574,11 +575,24 @@ __global__ void slice_rows2_kernel(const double *__restrict__ X1, int64_t ld1, i
         const int kb = k / BKB, kk = k % BKB;
         for (int i = 0; i < S; ++i) {
             const int sh = 7 * (S - 1 - i);
-            long long d = sh > 0 ? ((F + (1ll << (sh - 1))) >> sh) : F;
+            long long d = sh > 0 ? ((F + (1ll << (sh - 1))) >> sh) : F;   // nearest digit
             F -= d << sh;
-            out[(((int64_t)i * KB + kb) * R + row) * BKB + kk] = __float2bfloat16_rn(ldexpf((float)d, emax - 7 - 7 * i));
+            out[(((int64_t)i * KB + kb) * R + dest) * BKB + kk] =
+                __float2bfloat16_rn(ldexpf((float)d, emax - 7 - 7 * i));   // exact: |d| <= 128
         }
     }
+}
+
+// Rows of [X1 | X2] (K1 then K2 entries, row strides ld1, ld2; X2 may be
+// absent) into bf16 slices [S][Kpad/64][R][64], one block per row.
+__global__ void __launch_bounds__(1024)
+slice_rows2_kernel(const double *__restrict__ X1, int64_t ld1, int K1, const double *__restrict__ X2, int64_t ld2,
+                   int K2, int Kpad, int S, int64_t R, __nv_bfloat16 *__restrict__ out) {
+    const int64_t row = blockIdx.x;
+    const double *x1 = X1 + row * ld1;
+    const double *x2 = X2 ? X2 + row * ld2 : nullptr;
+    slice_row_block([&](int k) -> double { return k < K1 ? __ldg(x1 + k) : ((x2 && k < K1 + K2) ? __ldg(x2 + k - K1) : 0.0); },
+                    row, R, Kpad, S, out);
 }
 
 // ------------------------------------------------------------- slicing
@@ -640,46 +654,83 @@ __global__ void slice_rows_kernel(const double *__restrict__ X, int64_t rows, in
     slice_row(X + row * Kpad, row, rows, Kpad, S, skip_col, out, threadIdx.x & 31);
 }
 
-__global__ void slice_rows_grouped(const SliceTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks,
-                                   int64_t R, int Kpad, int S, int skip_col, __nv_bfloat16 *__restrict__ out) {
+__global__ void __launch_bounds__(256)
+slice_rows_grouped(const SliceTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks, int64_t R,
+                   int Kpad, int S, int skip_col, __nv_bfloat16 *__restrict__ out) {
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const SliceTask &T = tasks[ti];
-    const int64_t row = (blockIdx.x - blk[ti]) * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= T.rows) return;
-    slice_row(T.X + row * Kpad, T.row0 + row, R, Kpad, S, skip_col, out, threadIdx.x & 31);
+    const int64_t row = blockIdx.x - blk[ti];
+    const double *x = T.X + row * Kpad;
+    slice_row_block([&](int k) -> double { return k == skip_col ? 0.0 : __ldg(x + k); }, T.row0 + row, R, Kpad, S, out);
 }
 
 // Rows with j == j' (both ranges): H[(n,j),(n',j)] over all K, incl. delta,
 // in double-float (they carry h_jj and the delta_jj' E term and so have a
 // wide dynamic range that the bf16 slices of one row do not cover).  Per task
 // one block per (j, 8 state pairs); the lanes of a warp split K.
-__global__ void diag_rows_kernel(const DRTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+// A block computes a tile of kDRj rows j x kDRt coefficient rows t; the
+// panel and coefficient rows pass through shared memory in K-chunks (the next
+// chunk is read into registers while the current one is used) and every
+// thread keeps four double-float partial sums (k mod 4), combined in a fixed
+// order at the end.
+constexpr int kDRj = 16, kDRt = 16, kDRk = 128;
+constexpr int kDRthreads = kDRj * kDRt;
+constexpr int kDRper = kDRj * kDRk / kDRthreads;     // elements of each tile a thread moves per chunk
+
+__global__ void __launch_bounds__(kDRthreads)
+diag_rows_kernel(const DRTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    static_assert(kDRj == kDRt, "both tiles are moved by the same index pattern");
+    __shared__ float2 sp[kDRj][kDRk + 1], sa[kDRt][kDRk + 1];
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const DRTask &T = tasks[ti];
     const int lb = (int)(blockIdx.x - blk[ti]);
-    const int j = T.j_lo + lb / T.ny;
-    const int lane = threadIdx.x & 31;
-    const int t = (lb % T.ny) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= T.j_hi || t >= T.n_nn) return;
-    const int Kpad = T.Kpad;
-    const float2 *prow = T.Pd + (int64_t)j * Kpad;
-    const float2 *arow = T.A + (int64_t)t * Kpad;
-    float h = 0.0f, l = 0.0f;
-    for (int k = lane; k < Kpad; k += 32) {
-        const float2 x = __ldg(prow + k), y = __ldg(arow + k);
-        df_fma(h, l, x.x, x.y, y.x, y.y);
-    }
+    const int j0 = T.j_lo + (lb / T.ny) * kDRj, t0 = (lb % T.ny) * kDRt;
+    const int tl = threadIdx.x % kDRt, jl = threadIdx.x / kDRt;
+    const int j = j0 + jl, t = t0 + tl;
+    const int Kpad = T.Kpad, j_hi = T.j_hi, n_nn = T.n_nn;
+    const float2 *__restrict__ Pd = T.Pd;
+    const float2 *__restrict__ A = T.A;
+    float2 rp[kDRper], ra[kDRper];
+    auto fetch = [&](int k0) {
 #pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, h, off), ol = __shfl_xor_sync(0xffffffffu, l, off);
-        df_add2(h, l, oh, ol);
+        for (int u = 0; u < kDRper; ++u) {
+            const int i = threadIdx.x + u * kDRthreads;
+            const int r = i / kDRk, k = k0 + i % kDRk;
+            const bool kin = k < Kpad;
+            rp[u] = (kin && j0 + r < j_hi) ? __ldg(Pd + (int64_t)(j0 + r) * Kpad + k) : make_float2(0.0f, 0.0f);
+            ra[u] = (kin && t0 + r < n_nn) ? __ldg(A + (int64_t)(t0 + r) * Kpad + k) : make_float2(0.0f, 0.0f);
+        }
+    };
+    float h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, l[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    fetch(0);
+    for (int k0 = 0; k0 < Kpad; k0 += kDRk) {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kDRper; ++u) {
+            const int i = threadIdx.x + u * kDRthreads;
+            sp[i / kDRk][i % kDRk] = rp[u];
+            sa[i / kDRk][i % kDRk] = ra[u];
+        }
+        __syncthreads();
+        if (k0 + kDRk < Kpad) fetch(k0 + kDRk);
+#pragma unroll 2
+        for (int k = 0; k < kDRk; k += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 x = sp[jl][k + u], y = sa[tl][k + u];
+                df_fma(h[u], l[u], x.x, x.y, y.x, y.y);
+            }
+        }
     }
-    if (lane) return;
+    if (j >= j_hi || t >= n_nn) return;
+    df_add2(h[0], l[0], h[1], l[1]);
+    df_add2(h[2], l[2], h[3], l[3]);
+    df_add2(h[0], l[0], h[2], l[2]);
     const int na = T.nn[2 * t], nb = T.nn[2 * t + 1];
     const int64_t r = T.row_off + (int64_t)na * T.cn + (j - T.cf);
     const int64_t c = T.col_off + (int64_t)nb * T.cnp + (j - T.cfp);
     if (T.same && r < c) return;
-    const double v = df_to_double(h, l);
+    const double v = df_to_double(h[0], l[0]);
     T.H[r * T.ld + c] = v;
     if (r != c) T.H[c * T.ld + r] = v;
 }
@@ -883,13 +934,13 @@ int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const G
 
 int64_t blocks_diag_rows(int j_lo, int j_hi, int n_nn) {
     if (j_hi <= j_lo || n_nn <= 0) return 0;
-    return (int64_t)(j_hi - j_lo) * ((n_nn + 7) / 8);
+    return (int64_t)((j_hi - j_lo + kDRj - 1) / kDRj) * ((n_nn + kDRt - 1) / kDRt);
 }
-int diag_rows_ny(int n_nn) { return (n_nn + 7) / 8; }
+int diag_rows_ny(int n_nn) { return (n_nn + kDRt - 1) / kDRt; }
 
 int g_diag_rows(const Grouped<DRTask> &g, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
-    diag_rows_kernel<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n);
+    diag_rows_kernel<<<(unsigned)g.blocks, kDRthreads, 0, s>>>(g.tasks, g.blk, g.n);
     return 1;
 }
 
@@ -927,8 +978,8 @@ void dense_operand_free(DenseOperand *op) {
 void dense_operand_fill(const DenseOperand &op, int S, const double *X1, int64_t ld1, int K1, const double *X2,
                         int64_t ld2, int K2, int64_t rows, cudaStream_t s) {
     if (rows <= 0) return;
-    slice_rows2_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(X1, ld1, K1, X2, ld2, K2, rows, op.Kpad, S, op.R,
-                                                                  (__nv_bfloat16 *)op.buf);
+    slice_rows2_kernel<<<(unsigned)rows, 1024, 0, s>>>(X1, ld1, K1, X2, ld2, K2, op.Kpad, S, op.R,
+                                                       (__nv_bfloat16 *)op.buf);
 }
 
 int dense_splits(int64_t M, int64_t N, int kb_total, int *kb_per_split) {

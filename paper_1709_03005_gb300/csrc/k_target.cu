@@ -22,19 +22,28 @@ namespace {
 // Wout[m][n'] = sum over records k of row m of v_k * Cp[col_k][n'].  One warp
 // per row: lane l takes records l, l+32, ... (fixed order), 16 columns at a
 // time, then a butterfly reduction over the lanes (fixed order as well).
-__global__ void sandwich_kernel(const SWTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+// One block per row: warp w of kSWWarps sums the w-th contiguous part of the
+// row's records (rows of very different lengths, e.g. a reference determinant
+// coupled to every other one, then cost no more than a quarter of the longest),
+// each warp reduces by a fixed xor tree and warp 0 adds the warps in order.
+constexpr int kSWWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSWWarps)
+sandwich_kernel(const SWTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    __shared__ double red[kSWWarps][16];
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const SWTask T = tasks[ti];
-    const int lane = threadIdx.x & 31;
-    const int row = (int)(blockIdx.x - blk[ti]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= T.n_rows) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int row = (int)(blockIdx.x - blk[ti]);
     const int nsp = T.nsp;
     const int64_t b = T.row_ptr[row], e = T.row_ptr[row + 1];
+    const int64_t per = (e - b + kSWWarps - 1) / kSWWarps;
+    const int64_t kb = b + w * per, ke = min(e, kb + per);
     for (int n0 = 0; n0 < nsp; n0 += 16) {
         double acc[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) acc[c] = 0.0;
-        for (int64_t k = b + lane; k < e; k += 32) {
+        for (int64_t k = kb + lane; k < ke; k += 32) {
             const int col = T.pairs[k].col;
             const double v = T.val[k];
             const double *crow = T.Cp + (int64_t)col * nsp + n0;
@@ -47,13 +56,20 @@ __global__ void sandwich_kernel(const SWTask *__restrict__ tasks, const int64_t 
 #pragma unroll
             for (int off = 16; off; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
         }
-        if (lane < 16 && n0 + lane < nsp) {
+        if (lane < 16) {
             double mine = 0.0;
 #pragma unroll
             for (int c = 0; c < 16; ++c)
                 if (c == lane) mine = acc[c];
-            T.Wout[(int64_t)row * nsp + n0 + lane] = mine;
+            red[w][lane] = mine;
         }
+        __syncthreads();
+        if (w == 0 && lane < 16 && n0 + lane < nsp) {
+            double sum = red[0][lane];
+            for (int q = 1; q < kSWWarps; ++q) sum += red[q][lane];
+            T.Wout[(int64_t)row * nsp + n0 + lane] = sum;
+        }
+        __syncthreads();
     }
 }
 
@@ -161,26 +177,42 @@ __global__ void item_count_kernel(const hb_pair *__restrict__ pairs, const int64
 // n_to^2 + r * n_to + q.  (A deg-0 record is a determinant with itself, m = m'
 // of one group; its diagonal contributions gamma(p, p) are the masked C^T C of
 // gdiag_partial_kernel below.)
-__global__ void item_fill_kernel(const IFTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+// One block per row: warp w of kIFWarps takes the w-th contiguous part of the
+// row's records, counts its items, and writes them after those of the warps
+// before it, so the items keep the order of the records.
+constexpr int kIFWarps = 4;
+
+__global__ void __launch_bounds__(32 * kIFWarps)
+item_fill_kernel(const IFTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    __shared__ int wcnt[kIFWarps];
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const IFTask T = tasks[ti];
-    const int lane = threadIdx.x & 31;
-    const int row = (int)(blockIdx.x - blk[ti]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= T.n_rows) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int row = (int)(blockIdx.x - blk[ti]);
     const int64_t b = T.row_ptr[row], e = T.row_ptr[row + 1];
+    const int64_t per = (e - b + kIFWarps - 1) / kIFWarps;
+    const int64_t kb = b + w * per, ke = min(e, kb + per);
+    int cnt = 0;
+    for (int64_t k = kb + lane; k - lane < ke; k += 32) {
+        const bool one = k < ke && T.pairs[k].degree == 1;
+        cnt += __popc(__ballot_sync(0xffffffffu, one));
+    }
+    if (lane == 0) wcnt[w] = cnt;
+    __syncthreads();
     int64_t pos = T.item_ptr[row];
+    for (int q = 0; q < w; ++q) pos += wcnt[q];
     const int W = T.W, n_to = T.n_to;
     const int sb = 64 * W;
-    for (int64_t k0 = b; k0 < e; k0 += 32) {
+    for (int64_t k0 = kb; k0 < ke; k0 += 32) {
         const int64_t k = k0 + lane;
-        int cnt = 0;
+        int one = 0;
         hb_pair r;
-        if (k < e) {
+        if (k < ke) {
             r = T.pairs[k];
-            cnt = r.degree == 1 ? 1 : 0;
+            one = r.degree == 1 ? 1 : 0;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, cnt != 0);
-        if (cnt) {
+        const unsigned m = __ballot_sync(0xffffffffu, one != 0);
+        if (one) {
             const int s = r.part[0] / sb, p = r.part[0] % sb, q = r.hole[0] % sb;
             GammaItem it;
             it.key = s * n_to * n_to + p * n_to + q;
@@ -196,11 +228,20 @@ __global__ void item_fill_kernel(const IFTask *__restrict__ tasks, const int64_t
 //   sum_{m: p_s occupied in D_m} C[m][n] C[m][n']
 // a C^T C with a row mask per spin orbital: chunked partial sums (rows in
 // chunks of kRowsPerChunk, fixed order), then a reduction over the chunks.
-// Blocks: (chunk, spin orbital sp, y) with y covering the outputs.
+// Blocks: (chunk, spin orbital sp, y) with y covering the outputs.  A block
+// first lists the chunk's rows with p_s occupied (in increasing order, by a
+// ballot prefix), then stages only those CI rows.
+__host__ __device__ inline int gdiag_batch(int ns) {
+    const int b = 5632 / (ns > 0 ? ns : 1);          // 44 KB of staged rows (+ the static row list)
+    return b > kRowsPerChunk ? kRowsPerChunk : (b < 1 ? 1 : b);
+}
+
 template <bool DF>
-__global__ void gdiag_partial_kernel(const GDTask *__restrict__ tasks, const int64_t *__restrict__ blk,
-                                     int n_tasks) {
+__global__ void __launch_bounds__(kRowsPerChunk)
+gdiag_partial_kernel(const GDTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     extern __shared__ double gsh[];
+    __shared__ int occ_rows[kRowsPerChunk];
+    __shared__ int warp_cnt[kRowsPerChunk / 32];
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const GDTask T = tasks[ti];
     const int nsp2 = 2 * T.n_to;
@@ -212,20 +253,28 @@ __global__ void gdiag_partial_kernel(const GDTask *__restrict__ tasks, const int
     const uint64_t bit = 1ull << (p % 64);
     const int m0 = c * kRowsPerChunk;
     const int rows = min(kRowsPerChunk, T.ndet - m0);
-    const int kBatch = stage_batch(ns + 1, 0);
-    int *occ = reinterpret_cast<int *>(gsh + (size_t)kBatch * ns);   // [kBatch]
+    // the chunk's rows with p_s occupied (blockDim.x == kRowsPerChunk)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool o = (int)threadIdx.x < rows && (T.dets[(int64_t)(m0 + threadIdx.x) * 2 * T.W + word] & bit);
+    const unsigned bal = __ballot_sync(0xffffffffu, o);
+    if (lane == 0) warp_cnt[w] = __popc(bal);
+    __syncthreads();
+    int pos = __popc(bal & ((1u << lane) - 1u)), n_occ = 0;
+    for (int q = 0; q < kRowsPerChunk / 32; ++q) {
+        if (q < w) pos += warp_cnt[q];
+        n_occ += warp_cnt[q];
+    }
+    if (o) occ_rows[pos] = threadIdx.x;
+    const int kB = gdiag_batch(ns);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     float ah[4] = {0.0f, 0.0f, 0.0f, 0.0f}, al[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int r0 = 0; r0 < rows; r0 += kBatch) {
-        const int nr = min(kBatch, rows - r0);
+    for (int r0 = 0; r0 < n_occ; r0 += kB) {
+        const int nr = min(kB, n_occ - r0);
         __syncthreads();
-        for (int i = threadIdx.x; i < nr; i += blockDim.x)
-            occ[i] = (T.dets[(int64_t)(m0 + r0 + i) * 2 * T.W + word] & bit) ? 1 : 0;
-        if (DF) {
-            float2 *cs = reinterpret_cast<float2 *>(gsh);
-            for (int i = threadIdx.x; i < nr * ns; i += blockDim.x) cs[i] = T.C_df[(int64_t)(m0 + r0) * ns + i];
-        } else {
-            for (int i = threadIdx.x; i < nr * ns; i += blockDim.x) gsh[i] = T.C[(int64_t)(m0 + r0) * ns + i];
+        for (int i = threadIdx.x; i < nr * ns; i += blockDim.x) {
+            const int64_t m = m0 + occ_rows[r0 + i / ns];
+            if (DF) reinterpret_cast<float2 *>(gsh)[i] = T.C_df[m * ns + i % ns];
+            else gsh[i] = T.C[m * ns + i % ns];
         }
         __syncthreads();
 #pragma unroll
@@ -234,7 +283,6 @@ __global__ void gdiag_partial_kernel(const GDTask *__restrict__ tasks, const int
             if (t < nout) {
                 const int a = t / ns, b = t % ns;
                 for (int m = 0; m < nr; ++m) {
-                    if (!occ[m]) continue;
                     if (DF) {
                         const float2 *cs = reinterpret_cast<const float2 *>(gsh);
                         const float2 x = cs[m * ns + a], y = cs[m * ns + b];
@@ -597,43 +645,72 @@ __device__ __forceinline__ void shfl_df_add(float &h, float &l, int off) {
     df_add2(h, l, oh, ol);
 }
 
-__global__ void sandwich_df_kernel(const SWTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+// Passes of W states, one block per row as in sandwich_kernel: a lane of warp
+// w sums every 32nd record of the warp's part of the row for all W states of
+// the pass, the warp reduces by a fixed xor tree and warp 0 adds the warps in
+// order.  The coefficient pairs are read 16 bytes at a time where aligned.
+template <int W>
+__global__ void __launch_bounds__(32 * kSWWarps)
+sandwich_df_kernel(const SWTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    __shared__ float2 red[kSWWarps][W];
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const SWTask T = tasks[ti];
-    const int lane = threadIdx.x & 31;
-    const int row = (int)(blockIdx.x - blk[ti]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= T.n_rows) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int row = (int)(blockIdx.x - blk[ti]);
     const int nsp = T.nsp;
     const float2 *val = reinterpret_cast<const float2 *>(T.val);
     float2 *Wout = reinterpret_cast<float2 *>(T.Wout);
     const int64_t b = T.row_ptr[row], e = T.row_ptr[row + 1];
-    for (int n0 = 0; n0 < nsp; n0 += 16) {
-        float ah[16], al[16];
+    const int64_t per = (e - b + kSWWarps - 1) / kSWWarps;
+    const int64_t kb = b + w * per, ke = min(e, kb + per);
+    const bool vec = (nsp & 1) == 0 && (reinterpret_cast<uintptr_t>(T.Cp_df) & 15) == 0;
+    for (int n0 = 0; n0 < nsp; n0 += W) {
+        float ah[W], al[W];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) { ah[c] = 0.0f; al[c] = 0.0f; }
-        for (int64_t k = b + lane; k < e; k += 32) {
+        for (int c = 0; c < W; ++c) { ah[c] = 0.0f; al[c] = 0.0f; }
+        for (int64_t k = kb + lane; k < ke; k += 32) {
             const int col = T.pairs[k].col;
             const float2 v = val[k];
             const float2 *crow = T.Cp_df + (int64_t)col * nsp + n0;
+            if (vec) {
+                // n0 + c even and nsp even: the pair (c, c + 1) is in range together
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                if (n0 + c < nsp) {
-                    const float2 x = __ldg(crow + c);
-                    df_fma(ah[c], al[c], v.x, v.y, x.x, x.y);
-                }
+                for (int c = 0; c < W; c += 2)
+                    if (n0 + c < nsp) {
+                        const float4 x = __ldg(reinterpret_cast<const float4 *>(crow + c));
+                        df_fma(ah[c], al[c], v.x, v.y, x.x, x.y);
+                        df_fma(ah[c + 1], al[c + 1], v.x, v.y, x.z, x.w);
+                    }
+            } else {
+#pragma unroll
+                for (int c = 0; c < W; ++c)
+                    if (n0 + c < nsp) {
+                        const float2 x = __ldg(crow + c);
+                        df_fma(ah[c], al[c], v.x, v.y, x.x, x.y);
+                    }
+            }
         }
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
+        for (int c = 0; c < W; ++c) {
+            if (n0 + c < nsp) {
 #pragma unroll
-            for (int off = 16; off; off >>= 1) shfl_df_add(ah[c], al[c], off);
+                for (int off = 16; off; off >>= 1) shfl_df_add(ah[c], al[c], off);
+            }
         }
-        if (lane < 16 && n0 + lane < nsp) {
+        if (lane < W) {
             float mh = 0.0f, ml = 0.0f;
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
+            for (int c = 0; c < W; ++c)
                 if (c == lane) { mh = ah[c]; ml = al[c]; }
-            Wout[(int64_t)row * nsp + n0 + lane] = make_float2(mh, ml);
+            red[w][lane] = make_float2(mh, ml);
         }
+        __syncthreads();
+        if (w == 0 && lane < W && n0 + lane < nsp) {
+            float sh = red[0][lane].x, sl = red[0][lane].y;
+            for (int q = 1; q < kSWWarps; ++q) df_add2(sh, sl, red[q][lane].x, red[q][lane].y);
+            Wout[(int64_t)row * nsp + n0 + lane] = make_float2(sh, sl);
+        }
+        __syncthreads();
     }
 }
 
@@ -858,9 +935,13 @@ void gamma_item_counts(const hb_pair *pairs, const int64_t *row_ptr, int n_rows,
         return 1;                                                                                   \
     } while (0)
 
-int g_sandwich(const Grouped<SWTask> &g, int dfloat, cudaStream_t s) {
-    if (dfloat) HB_GROUPED(sandwich_df_kernel, g, 256, 0, s);
-    HB_GROUPED(sandwich_kernel, g, 256, 0, s);
+int g_sandwich(const Grouped<SWTask> &g, int dfloat, int width, cudaStream_t s) {
+    if (dfloat) {
+        if (width <= 16) HB_GROUPED(sandwich_df_kernel<16>, g, 32 * kSWWarps, 0, s);
+        if (width <= 24) HB_GROUPED(sandwich_df_kernel<24>, g, 32 * kSWWarps, 0, s);
+        HB_GROUPED(sandwich_df_kernel<32>, g, 32 * kSWWarps, 0, s);
+    }
+    HB_GROUPED(sandwich_kernel, g, 32 * kSWWarps, 0, s);
 }
 int g_sandwich_small(const Grouped<SWTask> &g, int dfloat, cudaStream_t s) {
     if (dfloat) HB_GROUPED(sandwich_small_df_kernel, g, 256, 0, s);
@@ -874,7 +955,7 @@ int g_tn_reduce(const Grouped<TNTask> &g, int dfloat, cudaStream_t s) {
     if (dfloat) HB_GROUPED(reduce_partials_df_kernel, g, 256, 0, s);
     HB_GROUPED(reduce_partials_kernel, g, 256, 0, s);
 }
-int g_item_fill(const Grouped<IFTask> &g, cudaStream_t s) { HB_GROUPED(item_fill_kernel, g, 256, 0, s); }
+int g_item_fill(const Grouped<IFTask> &g, cudaStream_t s) { HB_GROUPED(item_fill_kernel, g, 32 * kIFWarps, 0, s); }
 int g_zero(const Grouped<ZTask> &g, cudaStream_t s) { HB_GROUPED(zero_kernel, g, 256, 0, s); }
 int g_sort_hist(const Grouped<SortTask> &g, cudaStream_t s) { HB_GROUPED(sort_hist_kernel, g, 256, 0, s); }
 int g_sort_scatter(const Grouped<SortTask> &g, cudaStream_t s) { HB_GROUPED(sort_scatter_kernel, g, 32, 0, s); }
@@ -894,8 +975,8 @@ int g_assemble(const Grouped<ATask> &g, int dfloat, cudaStream_t s) {
 int g_gdiag(const Grouped<GDTask> &partial, const Grouped<GDTask> &reduce, size_t smem, int dfloat, cudaStream_t s) {
     int L = 0;
     if (partial.blocks > 0) {
-        if (dfloat) gdiag_partial_kernel<true><<<(unsigned)partial.blocks, 256, smem, s>>>(partial.tasks, partial.blk, partial.n);
-        else gdiag_partial_kernel<false><<<(unsigned)partial.blocks, 256, smem, s>>>(partial.tasks, partial.blk, partial.n);
+        if (dfloat) gdiag_partial_kernel<true><<<(unsigned)partial.blocks, kRowsPerChunk, smem, s>>>(partial.tasks, partial.blk, partial.n);
+        else gdiag_partial_kernel<false><<<(unsigned)partial.blocks, kRowsPerChunk, smem, s>>>(partial.tasks, partial.blk, partial.n);
         ++L;
     }
     if (reduce.blocks > 0) {
@@ -910,7 +991,7 @@ int64_t blocks_gdiag_partial(int ndet, int n_to, int ns) {
     return (int64_t)tn_chunks(ndet) * 2 * n_to * tn_ny(ns, ns);
 }
 int64_t blocks_gdiag_reduce(int n_to, int ns) { return (int64_t)2 * n_to * ((ns * ns + 255) / 256); }
-size_t smem_gdiag(int ns) { return (sizeof(double) * ns + sizeof(int)) * stage_batch(ns + 1, 0); }
+size_t smem_gdiag(int ns) { return sizeof(double) * ns * gdiag_batch(ns); }
 
 int64_t blocks_scan(int64_t n) { return (n + kScanSeg - 1) / kScanSeg; }
 
