@@ -114,7 +114,10 @@ typedef struct {
     int32_t split_tile;       /* 0 = chosen; 3, 4, 5: tensor-core tiles of (128 >> v) j x (1 << v) j' */
     int32_t class4_states;    /* 0 = chosen; 8, 16, ..., 64: target states per pass of the mixed class-4 kernel */
     int32_t class4_threads;   /* 0 = chosen; 32, 64, 128: continuum orbitals per class-4 block */
-    int32_t reserved[10];
+    int32_t class4_path;      /* mixed build, class 4: 0 = tensor cores for groups of 32..64 states and
+                                 the double-float kernel for the rest; 1 = the double-float kernel
+                                 only; 2 = tensor cores for every group of 1..64 states */
+    int32_t reserved[9];
 } hb_options;
 
 typedef struct {

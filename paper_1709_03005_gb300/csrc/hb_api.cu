@@ -9,6 +9,7 @@
 
 #include "hb_api_internal.cuh"
 #include "hb_davidson.cuh"
+#include "hb_c4tc.cuh"
 #include "hb_plan.cuh"
 #include "hb_df.cuh"
 #include "hb_tasks.cuh"
@@ -103,6 +104,8 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
         return fail(ctx, HB_ERR_INVALID_ARG, "class4_states must be 0 or a multiple of 8 up to 64");
     if (o && o->class4_threads != 0 && o->class4_threads != 32 && o->class4_threads != 64 && o->class4_threads != 128)
         return fail(ctx, HB_ERR_INVALID_ARG, "class4_threads must be 0, 32, 64 or 128");
+    if (o && (o->class4_path < 0 || o->class4_path > 2))
+        return fail(ctx, HB_ERR_INVALID_ARG, "class4_path must be 0, 1 or 2");
     const int W = p->n_words, nw = 2 * W;
     // electron counts: every target determinant has the same alpha/beta split,
     // the continuum electron sets the L2 split
@@ -225,6 +228,7 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         ctx->force_tile = o->split_tile;
         ctx->force_c4_states = o->class4_states;
         ctx->force_c4_threads = o->class4_threads;
+        ctx->c4_path = o->class4_path;
     }
     ctx->Pt = (int64_t)p->n_to * (p->n_to + 1) / 2;
     ctx->K = (int)(ctx->Pt + (int64_t)p->n_to * p->n_to + 2);
@@ -554,6 +558,7 @@ extern "C" void hb_destroy(hb_ctx *ctx) {
         ctx->plan = nullptr;
     }
     release_mixed(ctx);
+    hb::release_c4tc(ctx);
     hb::release_diag(ctx);
     hb::release_mlp(ctx);
     delete ctx;

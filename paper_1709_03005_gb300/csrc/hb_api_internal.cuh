@@ -53,6 +53,7 @@ struct hb_ctx {
     int split_slices = 5;
     int autotune = 0;
     int force_tile = 0, force_c4_states = 0, force_c4_threads = 0;   // 0: chosen by the plan
+    int c4_path = 0;         // mixed class 4: 0 tensor cores for 32..64 states, 1 double-float only, 2 tensor cores for 1..64
     int64_t Pt = 0;
     int K = 0, Kpad = 0;
     int64_t Dc = 0, dim = 0;
@@ -74,6 +75,7 @@ struct hb_ctx {
     void *plan = nullptr;    // cached grouped-launch plan of this context's own builds (k_plan.cu)
     void *diag = nullptr;   // Davidson workspace (k_davidson.cu)
     void *mlp = nullptr;    // learned preconditioner weights (k_mlp.cu)
+    void *c4tc = nullptr;   // class-4 tensor-core operands (k_class4_tc.cu)
 
     hb::Ints ints() const {
         hb::Ints I;

@@ -186,6 +186,35 @@ struct C4Task {         // class 4 of one target group against the L2 functions
     double *Hlc;
 };
 
+struct C4FTask {        // class-4 term lists of one target group (tensor-core path)
+    const hb_pair *pairs;
+    const int64_t *row_ptr;
+    int n_l2;
+    const uint64_t *dets;     // the group's determinants
+    int W, n_to, cont_spin, ndet;
+    int64_t x_h0, x_zero;     // first one-electron row and the zero row of the integral table
+    const int64_t *term_ptr;  // [n_l2 + 1], padded rows
+    int2 *terms;              // (integral row, signed CI row)
+};
+
+struct C4TTask {        // class 4 of one target group on the tensor cores
+    const void *xs;                   // integral slices [S][x_rows][jpad] (bf16)
+    int64_t x_rows;
+    int jpad;
+    const int64_t *term_ptr;
+    const int2 *terms;
+    int n_l2, n_jt, j0, cf, cn, ns;   // n_jt tiles of 128 orbitals from j0 (a multiple of 8)
+    const void *cs;                   // CI slices [S][c_rows][64] (bf16)
+    int64_t c_rows;
+    int64_t col_off, ld;
+    double *Hlc;
+};
+
+struct C4Item {         // one work item of the tensor-core class-4 kernel
+    int64_t t0;               // its first term
+    int ti, l, jt, nkb;       // task, L2 row, orbital tile, K blocks of 32 terms
+};
+
 struct L2Task {         // classes 2 and 8: L2-L2 CSR of one Hamiltonian
     Ints I;
     const uint64_t *dets;

@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "hb_c4tc.cuh"
 #include "hb_plan.cuh"
 #include "hb_split.cuh"
 #include "hb_tasks.cuh"
@@ -94,10 +95,15 @@ struct Plan {
         Stage<C4Task> st;
     };
     std::vector<C4Var> c4v;            // class-4 launch shapes (one grouped launch each)
+    Stage<C4FTask> c4f;                // class 4 on the tensor cores: term lists, then the GEMMs
+    Stage<C4TTask> c4t;
     Stage<L2Task> l2;
     std::vector<ExpCol> cols;          // columns of the merged expansion blocks
     size_t off_cols = 0;
     const ExpCol *d_cols = nullptr;
+    std::vector<C4Item> c4items;       // work items of the tensor-core class-4 launch
+    size_t off_c4items = 0;
+    const C4Item *d_c4items = nullptr;
     size_t smem_tn = 0, smem_gamma = 0;
     double flops = 0.0;
     int n_expand_tasks = 0;
@@ -117,9 +123,10 @@ struct Plan {
     // the target side and the expansion, the longer chain, at higher priority
     cudaStream_t main = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, join_main = nullptr;
-    // timers: start, target, expansion (main stream); class 4, L2, side start
-    // (side stream); end after the join; split kernels
-    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t c4_done = nullptr;     // the tensor-core class-4 kernel has finished (side stream)
+    // timers: start, target, expansion (main stream); class-4 end, L2 end, side
+    // start (side stream); end after the join; L2 start (side stream); split kernels
+    cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> ev_split;
     int launches = 0, expand_launches = 0;
     bool timed = false;
@@ -162,8 +169,10 @@ void fill_tasks(Plan &p) {
     p.itf.clear(); p.zero.clear(); p.sort.clear(); p.scan.clear(); p.gam.clear(); p.asmb.clear();
     p.x64.clear(); p.slc.clear(); p.drows.clear(); p.l2.clear();
     for (auto &v : p.c4v) v.st.clear();
+    p.c4f.clear(); p.c4t.clear();
     for (auto &sg : p.split) sg.st.clear();
     p.cols.clear();
+    p.c4items.clear();
     p.tune_split.clear(); p.tune_c4.clear(); p.tune_gamma.clear();
     p.smem_tn = p.smem_gamma = p.smem_gd = 0;
     p.flops = 0.0;
@@ -286,6 +295,16 @@ void fill_tasks(Plan &p) {
             p.cls_tl2.add(ClsTask{ctx->l2, dg, ctx->n_l2, G.ndet, ctx->cont_spin, 2, 0, L.rowptr, L.seg_off,
                                   seg_count(G.ndet), L.pairs},
                           blocks_seg_rows8(ctx->n_l2, G.ndet));
+            if (p.precision == HB_MIXED && c4tc_group_on(ctx, g)) {
+                C4FTask ft;
+                C4TTask tt;
+                int64_t fb = 0, items = 0;
+                c4tc_tasks(ctx, g, out.Hlc, &ft, &fb, &tt, &items);
+                c4tc_items(ctx, g, (int)p.c4t.tasks.size(), &p.c4items);
+                p.c4f.add(ft, fb);
+                p.c4t.add(tt, items);
+                continue;
+            }
             int ns_tile = 32, jt = 128;
             if (p.precision == HB_MIXED) {
                 class4_shape(G.ns, G.cn, &ns_tile, &jt);
@@ -392,9 +411,14 @@ void pack_all(Plan &p) {
     for (auto &sg : p.split) stage_pack(sg.st, p.host);
     stage_pack(p.drows, p.host); stage_pack(p.l2, p.host);
     for (auto &v : p.c4v) stage_pack(v.st, p.host);
+    stage_pack(p.c4f, p.host); stage_pack(p.c4t, p.host);
     p.off_cols = align256(p.host.size());
     p.host.resize(p.off_cols + sizeof(ExpCol) * p.cols.size());
     if (!p.cols.empty()) memcpy(p.host.data() + p.off_cols, p.cols.data(), sizeof(ExpCol) * p.cols.size());
+    p.off_c4items = align256(p.host.size());
+    p.host.resize(p.off_c4items + sizeof(C4Item) * p.c4items.size());
+    if (!p.c4items.empty())
+        memcpy(p.host.data() + p.off_c4items, p.c4items.data(), sizeof(C4Item) * p.c4items.size());
 }
 
 void bind_all(Plan &p) {
@@ -406,7 +430,9 @@ void bind_all(Plan &p) {
     for (auto &sg : p.split) stage_bind(sg.st, p.dev);
     stage_bind(p.drows, p.dev); stage_bind(p.l2, p.dev);
     for (auto &v : p.c4v) stage_bind(v.st, p.dev);
+    stage_bind(p.c4f, p.dev); stage_bind(p.c4t, p.dev);
     p.d_cols = (const ExpCol *)(p.dev + p.off_cols);
+    p.d_c4items = (const C4Item *)(p.dev + p.off_c4items);
 }
 
 // Copy the packed tables through the pinned staging buffer (which is reused
@@ -460,17 +486,18 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
         }
     int rc = HB_OK;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreate(&p->ev[i]);
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&p->ev[i]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->uploaded, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join_main, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->c4_done, cudaEventDisableTiming);
     int least = 0, greatest = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->main, cudaStreamNonBlocking, greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, least);
-    if (e == cudaSuccess) e = cudaMalloc(&p->err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMalloc(&p->err, 2 * sizeof(int));   // split kernel, class-4 kernel
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) {
         *err = std::string("plan: ") + cudaGetErrorString(e);
         plan_destroy(p);
@@ -490,6 +517,14 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
         if (rc != HB_OK) { plan_destroy(p); return rc; }
         p->delta_col = (int)(ctxs[0]->Pt + (int64_t)ctxs[0]->n_to * ctxs[0]->n_to + 1);
     }
+    if (precision == HB_MIXED && p->S == 0) p->S = mixed_slices(ctxs[0]);
+    // class 4 on the tensor cores: integral and CI slices, term-list sizes
+    if (precision == HB_MIXED)
+        for (int i = 0; i < n && rc == HB_OK; ++i) {
+            if (ctxs[i]->n_l2 < 1 || ctxs[i]->c4_path == 1) continue;
+            rc = c4tc_prepare(ctxs[i], p->S, s);
+            if (rc != HB_OK) *err = ctxs[i]->err;
+        }
     if (precision == HB_MIXED)
         for (int i = 0; i < n && rc == HB_OK; ++i) {
             rc = ensure_df(ctxs[i], s);
@@ -696,6 +731,11 @@ std::string plan_report(const Plan *p) {
             snprintf(buf, sizeof buf, " class4 ns%d cn%d:%dx%d;", t.ns, t.cn, v.ns_tile, v.jt);
             if (r.find(buf) == std::string::npos) r += buf;
         }
+    if (!p->c4t.tasks.empty()) {
+        snprintf(buf, sizeof buf, " class4 tensor cores: %d groups, %d work items;", (int)p->c4t.tasks.size(),
+                 (int)p->c4items.size());
+        r += buf;
+    }
     snprintf(buf, sizeof buf, " gamma warp/block tasks %d/%d", (int)p->gamw.tasks.size(), (int)p->gam.tasks.size());
     r += buf;
     return r;
@@ -722,6 +762,33 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     cudaEventRecord(p->fork, s);
     cudaStreamWaitEvent(p->main, p->fork, 0);
     cudaStreamWaitEvent(s2, p->fork, 0);
+    // class 4 (Eq. 5) and classes 2 and 8
+    // the L2 rows stay FP64: their sums are short and the kernel is bound by the
+    // pair scan, where the longer double-float sums cost more than FP64 adds
+    rec_on(p->ev[5], s2);
+    L += g_classify(p->cls_tl2.g, W, 1, s2);
+    if (p->c4t.g.blocks > 0) {
+        // the tensor-core class-4 kernel and the expansion kernel each hold
+        // whole SMs until their work is done, and the L2 kernel's blocks do
+        // not fit beside either: the L2 rows run beside the target side, then
+        // class 4, and the expansion starts once both are done
+        rec_on(p->ev[7], s2);
+        L += g_l2_csr(p->l2.g, W, 0, s2);
+        rec_on(p->ev[4], s2);
+        cudaMemsetAsync(p->err + 1, 0, sizeof(int), s2);
+        L += g_c4fill(p->c4f.g, s2);
+        L += g_c4tc(p->c4t.g, p->d_c4items, (int)p->c4items.size(), p->S, p->err + 1, s2);
+        for (auto &v : p->c4v) L += g_class4(v.st.g, W, 1, v.ns_tile, v.jt, s2);
+        rec_on(p->ev[3], s2);
+        cudaEventRecord(p->c4_done, s2);
+    } else {
+        for (auto &v : p->c4v) L += g_class4(v.st.g, W, p->precision == HB_MIXED ? 1 : 0, v.ns_tile, v.jt, s2);
+        rec_on(p->ev[3], s2);
+        rec_on(p->ev[7], s2);
+        L += g_l2_csr(p->l2.g, W, 0, s2);
+        rec_on(p->ev[4], s2);
+    }
+    cudaEventRecord(p->join, s2);
     s = p->main;
     auto rec = [&](cudaEvent_t e) { rec_on(e, s); };
     // target side (Eq. 8): classes, H^N, S, E, gamma, coefficient rows
@@ -743,6 +810,10 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     rec(p->ev[1]);
     // expansion (Eq. 7): classes 1, 3, 5, 6, 7
     if (p->precision == HB_MIXED) {
+        // the tensor-core class-4 kernel and the expansion kernel each hold
+        // whole SMs until their work is done: let class 4 run beside the
+        // target side and finish before the expansion starts
+        if (p->c4t.g.blocks > 0) cudaStreamWaitEvent(s, p->c4_done, 0);
         if (p->coef_rows > 0) {
             cudaMemsetAsync(p->err, 0, sizeof(int), s);
             L += g_slice(p->slc.g, p->coef_rows, p->Kpad, p->S, p->delta_col, p->coef, s);
@@ -759,17 +830,6 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     L += LX;
     rec(p->ev[2]);
     cudaEventRecord(p->join_main, s);
-    // class 4 (Eq. 5)
-    rec_on(p->ev[5], s2);
-    L += g_classify(p->cls_tl2.g, W, 1, s2);
-    for (auto &v : p->c4v) L += g_class4(v.st.g, W, p->precision == HB_MIXED ? 1 : 0, v.ns_tile, v.jt, s2);
-    rec_on(p->ev[3], s2);
-    // classes 2 and 8
-    // the L2 rows stay FP64: their sums are short and the kernel is bound by the
-    // pair scan, where the longer double-float sums cost more than FP64 adds
-    L += g_l2_csr(p->l2.g, W, 0, s2);
-    rec_on(p->ev[4], s2);
-    cudaEventRecord(p->join, s2);
     // join into the caller's stream
     s = s0;
     cudaStreamWaitEvent(s, p->join_main, 0);
@@ -796,8 +856,16 @@ void plan_stats(Plan *p, hb_stats *st) {
     cudaEventElapsedTime(&st->ms_total, p->ev[0], p->ev[6]);
     cudaEventElapsedTime(&st->ms_target, p->ev[0], p->ev[1]);
     cudaEventElapsedTime(&st->ms_expand, p->ev[1], p->ev[2]);
-    cudaEventElapsedTime(&st->ms_class4, p->ev[5], p->ev[3]);
-    cudaEventElapsedTime(&st->ms_l2, p->ev[3], p->ev[4]);
+    cudaEventElapsedTime(&st->ms_l2, p->ev[7], p->ev[4]);
+    if (p->c4t.g.blocks > 0) {
+        // class-4 classification, then (after the L2 rows) the tensor-core part
+        float a = 0.0f, b = 0.0f;
+        cudaEventElapsedTime(&a, p->ev[5], p->ev[7]);
+        cudaEventElapsedTime(&b, p->ev[4], p->ev[3]);
+        st->ms_class4 = a + b;
+    } else {
+        cudaEventElapsedTime(&st->ms_class4, p->ev[5], p->ev[3]);
+    }
     if (p->precision == HB_MIXED) {
         float total = 0.0f;
         for (size_t i = 0; i + 1 < p->ev_split.size(); i += 2) {
@@ -814,7 +882,10 @@ void plan_stats(Plan *p, hb_stats *st) {
 int plan_error_word(Plan *p, int *word) {
     *word = 0;
     if (!p->err) return HB_OK;
-    return cudaMemcpy(word, p->err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+    int w[2] = {0, 0};
+    if (cudaMemcpy(w, p->err, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return HB_ERR_CUDA;
+    *word = w[0] ? w[0] : w[1];
+    return HB_OK;
 }
 
 void plan_destroy(Plan *p) {
@@ -828,6 +899,7 @@ void plan_destroy(Plan *p) {
     if (p->fork) cudaEventDestroy(p->fork);
     if (p->join) cudaEventDestroy(p->join);
     if (p->join_main) cudaEventDestroy(p->join_main);
+    if (p->c4_done) cudaEventDestroy(p->c4_done);
     for (cudaStream_t st : {p->main, p->side})
         if (st) {
             cudaStreamSynchronize(st);

@@ -38,7 +38,8 @@ class hb_problem(C.Structure):
 class hb_options(C.Structure):
     _fields_ = [("split_slices", C.c_int32), ("validate", C.c_int32), ("autotune", C.c_int32),
                 ("split_tile", C.c_int32), ("class4_states", C.c_int32), ("class4_threads", C.c_int32),
-                ("reserved", C.c_int32 * 10)]
+                ("class4_path", C.c_int32),
+                ("reserved", C.c_int32 * 9)]
 
 
 class hb_layout(C.Structure):
@@ -146,7 +147,7 @@ class Hamiltonian:
     """
 
     def __init__(self, problem, split_slices=0, validate=True, stream=None, base=None, autotune=False,
-                 split_tile=0, class4_states=0, class4_threads=0):
+                 split_tile=0, class4_states=0, class4_threads=0, class4_path=0):
         import torch
         self.lib = load()
         self.base = base        # keeps a borrowed-integral base context alive
@@ -171,7 +172,7 @@ class Hamiltonian:
                                    ptr(arr(p.eri_tctc, np.float64)), len(p.groups), C.addressof(gs),
                                    p.l2_dets.shape[0], ptr(l2) if l2 is not None else None, float(p.e_core))
         opts = hb_options(split_slices, 1 if validate else 0, 1 if autotune else 0, split_tile, class4_states,
-                          class4_threads)
+                          class4_threads, class4_path)
         self.ctx = C.c_void_p()
         torch.cuda.init()
         if base is None:

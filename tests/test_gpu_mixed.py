@@ -5,7 +5,8 @@ condition scale of the Eq. 7 sum computed by the oracle.  For elements without
 cancellation this is the relative bound 1e-10; for elements that cancel far
 below the size of their terms no finite-precision evaluation (an FP64 sum in
 another order included) is closer than a small multiple of the unit roundoff of
-that scale.  Every other class is built in FP64 on both paths.
+that scale.  Class 4 (double-float or split-bf16 tensor cores) and classes 2, 8
+(FP64) are held to 1e-12 of their block scale.
 """
 import numpy as np
 import pytest
@@ -36,7 +37,7 @@ def _check_mixed(P, slices=0, what=""):
     assert not bad.any(), f"{what}: {bad.sum()} elements beyond 1e-10 of their condition scale; " \
                           f"worst ratio {(d / np.maximum(cond, 1e-300)).max():.3e}"
     np.testing.assert_array_equal(G, G.T)
-    # classes 4, 2, 8 are FP64 in both paths
+    # class 4 (double-float or tensor cores), classes 2 and 8 (FP64)
     for blk in (np.s_[Dc:, :Dc], np.s_[Dc:, Dc:]):
         g, r = G[blk], R[blk]
         if r.size:
@@ -129,3 +130,39 @@ def test_class4_wide_continuum(n_state):
     worst = float((np.abs(Hlc - rows) / np.maximum(scale, 1e-300)).max())
     assert np.all(np.abs(Hlc - rows) <= 1e-12 * scale), worst
     print(f"class 4, {n_state} states: worst |d| / row scale {worst:.2e}")
+
+
+@pytest.mark.parametrize("name,kw", CASES[:3] + [("mid", None)], ids=[c[0] for c in CASES[:3]] + ["mid"])
+def test_class4_tensor_cores(name, kw):
+    """Class 4 on the tensor cores for every group (class4_path=2; by default
+    only groups of 32..64 states take it): the Eq. 5 block against the oracle
+    at 1e-12 of the block scale, against the double-float kernel
+    (class4_path=1) likewise, and every other block identical to that build."""
+    import torch
+    from paper_1709_03005_gb300 import hb
+    if kw is None:
+        P = synth.make_config("mid")
+    else:
+        kw = dict(kw)
+        P = synth.make_tiny(kw.pop("seed"), **kw)
+    o = coracle.Oracle(P)
+    R = o.dense()
+    Dc = o.Dc
+    Ht = hb.Hamiltonian(P, class4_path=2)
+    Hd = hb.Hamiltonian(P, class4_path=1)
+    bt, _ = Ht.build(hb.HB_MIXED)
+    bd, _ = Hd.build(hb.HB_MIXED)
+    torch.cuda.synchronize()
+    assert "class4 tensor cores" in Ht.tuning_report() or P.n_l2 == 0
+    for key in ("Hcc", "row_ptr", "col", "val"):
+        assert torch.equal(bt[key], bd[key]), key
+    G = hb.dense_from_blocks(bt).cpu().numpy()
+    D = hb.dense_from_blocks(bd).cpu().numpy()
+    blk = np.s_[Dc:, :Dc]
+    r = R[blk]
+    if r.size:
+        scale = np.abs(r).max()
+        assert np.all(np.abs(G[blk] - r) <= 1e-12 * np.maximum(np.abs(r), scale))
+        assert np.all(np.abs(G[blk] - D[blk]) <= 1e-12 * np.maximum(np.abs(r), scale))
+    Ht.close()
+    Hd.close()
