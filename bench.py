@@ -97,9 +97,10 @@ def measured_peaks():
         return {}
 
 
-def profiled_traffic(kernel, source):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel source has not changed since the counters were taken (else None)."""
+def profiled_traffic(kernel, source, config):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on this workload and the kernel source has not changed since the
+    counters were taken (else None)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -108,7 +109,7 @@ def profiled_traffic(kernel, source):
             sha = hashlib.sha1(f.read()).hexdigest()
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_sha1") != sha:
+    if not rec or rec.get("source_sha1") != sha or rec.get("config") != config:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -289,7 +290,7 @@ def run_ours(args, rank, world, local_rank):
                 "achieved": tflops / (kern_ms / 1e3) / 1e12 if kern_ms else None,
                 "flops_per_launch": tflops, "kernel_ms": kern_ms,
                 "fp64_equivalent_tflops": flops_exp / (kern_ms / 1e3) / 1e12 if kern_ms else None,
-                "traffic": profiled_traffic("split_expand_kernel", "paper_1709_03005_gb300/csrc/k_split.cu")}
+                "traffic": profiled_traffic("split_expand_kernel", "paper_1709_03005_gb300/csrc/k_split.cu", args.config)}
     else:
         kern_ms = avg_exp_ms
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_alu_peak_tflops(),
@@ -297,7 +298,7 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": "expand_fp64_kernel: Eq. 7 contraction in FP64",
                 "achieved": flops_exp / (kern_ms / 1e3) / 1e12 if kern_ms else None,
                 "flops_per_launch": flops_exp, "kernel_ms": kern_ms,
-                "traffic": profiled_traffic("expand_fp64_kernel", "paper_1709_03005_gb300/csrc/k_expand.cu")}
+                "traffic": profiled_traffic("expand_fp64_kernel", "paper_1709_03005_gb300/csrc/k_expand.cu", args.config)}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] and roof["peak"] else None
 
     # the batched workload: 16 symmetry / spin-coupling Hamiltonians, one graph
