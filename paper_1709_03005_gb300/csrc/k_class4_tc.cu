@@ -620,6 +620,12 @@ int c4tc_min_states(const hb_ctx *ctx) { return ctx->c4_path == 2 ? 1 : 32; }
 int c4tc_prepare(hb_ctx *ctx, int S, cudaStream_t s) {
     if (ctx->c4tc) return HB_OK;
     if (S < 2 || S > 6) return c4_fail(ctx, HB_ERR_INVALID_ARG, "slices must be 2..6");
+    bool any = false;      // nothing to make unless some group takes the tensor-core path
+    for (int g = 0; g < ctx->n_groups; ++g) {
+        const GroupInfo &Gi = ctx->groups[g];
+        any = any || (Gi.ns >= c4tc_min_states(ctx) && Gi.ns <= TNP && Gi.cn > 0 && Gi.ndet > 0 && ctx->n_l2 > 0);
+    }
+    if (!any) return HB_OK;
     C4TC *c = new C4TC();
     ctx->c4tc = c;
     c->S = S;
