@@ -97,6 +97,20 @@ def measured_peaks():
         return {}
 
 
+def pinned_problem(P):
+    """A copy of the problem whose arrays live in page-locked host memory."""
+    import dataclasses
+    import torch
+
+    def pin(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    groups = [dataclasses.replace(g, dets=pin(g.dets), ci=pin(g.ci)) for g in P.groups]
+    return dataclasses.replace(P, h=pin(P.h), eri_tttt=pin(P.eri_tttt), eri_tttc=pin(P.eri_tttc),
+                               eri_ttcc=pin(P.eri_ttcc), eri_tctc=pin(P.eri_tctc), l2_dets=pin(P.l2_dets),
+                               groups=groups)
+
+
 def profiled_traffic(kernel, source, config):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on this workload and the kernel source has not changed since the
@@ -240,18 +254,22 @@ def run_ours(args, rank, world, local_rank):
     total_ms, value = replica_throughput(float(np.sum(times)), args.steps, dim, world, "cuda")
 
     # end to end through the public API with host buffers: staging (H2D of the
-    # problem), build, and the D2H read of every block, each step
+    # problem from pinned host memory), build, and the D2H read of every block
+    # into pinned host memory, each step
     e2e_steps = max(1, min(args.steps, 3))
+    Pp = pinned_problem(P)
     h2d = sum(np.asarray(a).nbytes for a in (P.h, P.eri_tttt, P.eri_tttc, P.eri_ttcc, P.eri_tctc, P.l2_dets)) + \
         sum(g.dets.nbytes + g.ci.nbytes for g in P.groups)
-    d2h = 0
+    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in blocks.items()}
+    d2h = sum(v.numel() * v.element_size() for v in host.values())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        H2 = hb.Hamiltonian(P, validate=False)
+        H2 = hb.Hamiltonian(Pp, validate=False)
         b2, _ = H2.build(precision)
-        host = {k: v.cpu() for k, v in b2.items()}
-        d2h = sum(v.numel() * v.element_size() for v in host.values())
+        for k, v in b2.items():
+            host[k].copy_(v, non_blocking=True)
+        torch.cuda.synchronize()
         H2.close()
         del b2
     torch.cuda.synchronize()
