@@ -97,6 +97,22 @@ def measured_peaks():
         return {}
 
 
+def overrides(args):
+    """Integer workload sizes given with --set KEY=INT."""
+    out = {}
+    for kv in args.set:
+        k, v = kv.split("=", 1)
+        out[k.strip()] = int(v)
+    return out
+
+
+def workload_text(args):
+    text = CONFIG_TEXT.get(args.config, args.config)
+    if args.set:
+        text += " with " + ", ".join(args.set)
+    return text
+
+
 def pinned_problem(P):
     """A copy of the problem whose arrays live in page-locked host memory."""
     import dataclasses
@@ -198,7 +214,7 @@ def run_reference(args, rank, world):
     from paper_1709_03005_gb300 import synth
     if rank != 0:
         return
-    P = synth.make_config(args.config)
+    P = synth.make_config(args.config, **overrides(args))
     for _ in range(args.warmup):
         cpu_baseline(P)
     vals = []
@@ -213,7 +229,7 @@ def run_reference(args, rank, world):
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1),
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic", "impl": "reference",
-                      "config": {"workload": CONFIG_TEXT.get(args.config, args.config)},
+                      "config": {"workload": workload_text(args)},
                       "cpu_baseline": cb, "e2e": {"value": v, "unit": "H elements/s", "h2d_bytes_per_step": 0,
                                                   "d2h_bytes_per_step": 0}}), flush=True)
 
@@ -224,7 +240,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     build_ext.build()
     precision = hb.HB_MIXED if args.precision == "mixed" else hb.HB_FP64
-    P = synth.make_config(args.config)
+    P = synth.make_config(args.config, **overrides(args))
     dim = P.dim
     H = hb.Hamiltonian(P)
     blocks = H.allocate()
@@ -308,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
                 "achieved": tflops / (kern_ms / 1e3) / 1e12 if kern_ms else None,
                 "flops_per_launch": tflops, "kernel_ms": kern_ms,
                 "fp64_equivalent_tflops": flops_exp / (kern_ms / 1e3) / 1e12 if kern_ms else None,
-                "traffic": profiled_traffic("split_expand_kernel", "paper_1709_03005_gb300/csrc/k_split.cu", args.config)}
+                "traffic": profiled_traffic("split_expand_kernel", "paper_1709_03005_gb300/csrc/k_split.cu", None if args.set else args.config)}
     else:
         kern_ms = avg_exp_ms
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_alu_peak_tflops(),
@@ -316,7 +332,7 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": "expand_fp64_kernel: Eq. 7 contraction in FP64",
                 "achieved": flops_exp / (kern_ms / 1e3) / 1e12 if kern_ms else None,
                 "flops_per_launch": flops_exp, "kernel_ms": kern_ms,
-                "traffic": profiled_traffic("expand_fp64_kernel", "paper_1709_03005_gb300/csrc/k_expand.cu", args.config)}
+                "traffic": profiled_traffic("expand_fp64_kernel", "paper_1709_03005_gb300/csrc/k_expand.cu", None if args.set else args.config)}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] and roof["peak"] else None
 
     # the batched workload: 16 symmetry / spin-coupling Hamiltonians, one graph
@@ -366,7 +382,7 @@ def run_ours(args, rank, world, local_rank):
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "bf16x6-split/f32->f64" if precision == hb.HB_MIXED else "f64", "data": "synthetic",
-               "config": {"workload": CONFIG_TEXT.get(args.config, args.config), "dim": dim,
+               "config": {"workload": workload_text(args), "dim": dim,
                           "positions": positions(dim), "l2_flush": "256 MB write between timed steps",
                           "parallelism": f"replicas x{world}", "precision": args.precision},
                "roofline": roof, "cpu_baseline": cb,
@@ -386,6 +402,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2")
+    ap.add_argument("--set", action="append", default=[], metavar="KEY=INT",
+                    help="override an integer size of the workload (e.g. n_l2=4000), for small profiling cases")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--davidson-k", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -73,7 +73,8 @@ def test_autotune_is_bit_identical():
 def test_invalid_shape_options_rejected():
     from paper_1709_03005_gb300 import hb
     P = _problems()[0]
-    for kw in (dict(split_tile=6), dict(class4_states=12), dict(class4_threads=96)):
+    for kw in (dict(split_tile=6), dict(class4_states=12), dict(class4_threads=96), dict(class4_path=3),
+               dict(class4_path=-1)):
         with pytest.raises(hb.HBError):
             hb.Hamiltonian(P, **kw)
 
