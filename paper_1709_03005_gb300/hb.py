@@ -439,7 +439,8 @@ class Batch:
     """Stage several problems that share orbitals and integrals (the first one
     owns the staged integrals) and build them all with one graph launch."""
 
-    def __init__(self, problems, precision=HB_MIXED, stream=None):
+    def __init__(self, problems, precision=HB_MIXED, stream=None, **options):
+        """options: hb_options fields for every context (split_tile, class4_path, ...)."""
         lib = load()
         lib.hb_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                         C.c_void_p]
@@ -451,9 +452,9 @@ class Batch:
         lib.hb_batch_destroy.argtypes = [C.c_void_p]
         lib.hb_batch_destroy.restype = None
         self.lib = lib
-        self.hams = [Hamiltonian(problems[0], stream=stream)]
+        self.hams = [Hamiltonian(problems[0], stream=stream, **options)]
         for p in problems[1:]:
-            self.hams.append(Hamiltonian(p, validate=False, stream=stream, base=self.hams[0]))
+            self.hams.append(Hamiltonian(p, validate=False, stream=stream, base=self.hams[0], **options))
         self.blocks = [h.allocate() for h in self.hams]
         n = len(self.hams)
         ctxs = (C.c_void_p * n)(*[h.ctx.value for h in self.hams])

@@ -58,3 +58,32 @@ def test_batch_members_match_oracle(family):
         ranges = [(g.cont_first, g.cont_count) for g in P.groups]
         assert len(set(ranges)) < len(ranges)
     B.close()
+
+
+def test_batch_class4_tensor_cores(family):
+    """Class 4 of every group on the tensor cores (class4_path=2) in one
+    grouped launch over several Hamiltonians, whose contexts borrow the first
+    one's integral slices: identical to building each context on its own, and
+    the smallest member within 1e-12 of the oracle's class-4 block."""
+    import torch
+    from paper_1709_03005_gb300 import hb
+    order = np.argsort([P.dim for P in family])
+    members = [family[i] for i in order[:4]]
+    B = hb.Batch(members, hb.HB_MIXED, class4_path=2)
+    B.launch()
+    torch.cuda.synchronize()
+    assert "class4 tensor cores" in B.report(), B.report()
+    for h, b in zip(B.hams, B.blocks):
+        ref, _ = h.build(hb.HB_MIXED)
+        torch.cuda.synchronize()
+        for key in ("Hcc", "Hlc", "row_ptr", "col", "val"):
+            assert torch.equal(ref[key], b[key]), key
+    P = members[0]
+    o = coracle.Oracle(P)
+    R = o.dense()
+    G = hb.dense_from_blocks(B.blocks[0]).cpu().numpy()
+    blk = np.s_[o.Dc:, :o.Dc]
+    r = R[blk]
+    if r.size:
+        assert np.all(np.abs(G[blk] - r) <= 1e-12 * np.maximum(np.abs(r), np.abs(r).max()))
+    B.close()
