@@ -140,10 +140,14 @@ typedef struct {
 
 typedef struct {
     float ms_total;           /* build: enqueue to completion on the stream */
+    /* The stages run on two streams (target side then expansion; class 4 and
+       the L2 rows beside them), so these spans overlap and their sum exceeds
+       ms_total.  With class 4 on the tensor cores the expansion waits for it,
+       and ms_expand includes that wait. */
     float ms_target;          /* classification + target-side contraction */
     float ms_expand;          /* continuum-continuum expansion */
-    float ms_class4;
-    float ms_l2;
+    float ms_class4;          /* class-4 classification and kernels */
+    float ms_l2;              /* classes 2 and 8 */
     float ms_expand_gemm;     /* dominant kernel alone (expansion contraction) */
     int32_t expand_launches;
     int32_t kernel_launches;  /* kernels launched by the call */
@@ -184,9 +188,14 @@ int hb_query(const hb_ctx *ctx, hb_layout *out);
 int64_t hb_group_offset(const hb_ctx *ctx, int32_t g);
 
 /* Build every class (1-8) into the caller's device buffers.  precision:
-   HB_FP64 (double arithmetic throughout) or HB_MIXED (the continuum-continuum
-   contraction on bf16 tensor cores with split operands, FP32 accumulation and
-   double-float recovery; everything else double).  `st` may be NULL. */
+   HB_FP64 (double arithmetic throughout) or HB_MIXED: the continuum-continuum
+   contraction (Eq. 7), and class 4 (Eq. 5) of groups of 32..64 states (see
+   hb_options.class4_path), on bf16 tensor cores with split operands, exact
+   FP32 accumulation and double-float recovery; the target-side contraction
+   and the other class-4 groups in double-float on the FP32 pipes; classes 2
+   and 8 in FP64.  The results are written as FP64.  `st` may be NULL.
+   Errors: HB_ERR_INVALID_ARG, HB_ERR_OOM, HB_ERR_CUDA, HB_ERR_TIMEOUT (a
+   bounded wait of a tensor-core kernel gave up). */
 int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *out, hb_stats *st,
                     void *stream);
 
