@@ -481,7 +481,7 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
         CK(cudaStreamSynchronize(s));
         if (plan_error_word(plan, &word) != HB_OK) return fail(ctx, HB_ERR_CUDA, "reading the mixed error word");
         if (word != 0)
-            return fail(ctx, HB_ERR_TIMEOUT, "split expansion kernel gave up waiting (code " + std::to_string(word) + ")");
+            return fail(ctx, HB_ERR_TIMEOUT, "a tensor-core kernel (split expansion, codes 1-6, or class 4, codes 21-26) gave up waiting (code " + std::to_string(word) + ")");
     }
     if (st) plan_stats(plan, st);
     return HB_OK;

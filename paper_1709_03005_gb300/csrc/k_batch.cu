@@ -120,7 +120,7 @@ extern "C" int hb_batch_launch(hb_batch *b, hb_stats *st, void *stream) {
         if (e != cudaSuccess) return bfail(HB_ERR_CUDA, cudaGetErrorString(e));
         int word = 0;
         if (plan_error_word(b->plan, &word) != HB_OK) return bfail(HB_ERR_CUDA, "reading the mixed error word");
-        if (word) return bfail(HB_ERR_TIMEOUT, "split expansion kernel gave up waiting");
+        if (word) return bfail(HB_ERR_TIMEOUT, "a tensor-core kernel gave up waiting (code " + std::to_string(word) + ")");
     }
     return HB_OK;
 }
