@@ -123,6 +123,10 @@ struct Plan {
     // the target side and the expansion, the longer chain, at higher priority
     cudaStream_t main = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, join_main = nullptr;
+    // the target side's independent chains: the gamma items (aux1), the
+    // diagonal gamma and then the j == j' rows (aux2), beside the E, S chain
+    cudaStream_t aux1 = nullptr, aux2 = nullptr;
+    cudaEvent_t k1_done = nullptr, items_done = nullptr, gd_done = nullptr, asm_done = nullptr, dr_done = nullptr;
     cudaEvent_t c4_done = nullptr;     // the tensor-core class-4 kernel has finished (side stream)
     // timers: start, target, expansion (main stream); class-4 end, L2 end, side
     // start (side stream); end after the join; L2 start (side stream); split kernels
@@ -496,6 +500,10 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->main, cudaStreamNonBlocking, greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, least);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->aux1, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->aux2, cudaStreamNonBlocking, greatest);
+    for (cudaEvent_t *ev : {&p->k1_done, &p->items_done, &p->gd_done, &p->asm_done, &p->dr_done})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&p->err, 2 * sizeof(int));   // split kernel, class-4 kernel
     if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) {
@@ -791,25 +799,42 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     cudaEventRecord(p->join, s2);
     s = p->main;
     auto rec = [&](cudaEvent_t e) { rec_on(e, s); };
-    // target side (Eq. 8): classes, H^N, S, E, gamma, coefficient rows
+    cudaStream_t sa = p->aux1, sb = p->aux2;
+    // target side (Eq. 8) in three chains that meet at the coefficient rows:
+    // the diagonal gamma needs only the determinants and CI vectors
+    cudaStreamWaitEvent(sb, p->fork, 0);
+    L += g_gdiag(p->gdp.g, p->gdr.g, p->smem_gd, DF, sb);
+    cudaEventRecord(p->gd_done, sb);
     L += g_classify(p->cls_tt.g, W, 0, s);
+    cudaEventRecord(p->k1_done, s);
+    // the gamma items of the single-excitation records, sorted by key, and gamma
+    cudaStreamWaitEvent(sa, p->k1_done, 0);
+    L += g_item_fill(p->itf.g, sa);
+    L += g_zero(p->zero.g, sa);
+    L += g_sort_hist(p->sort.g, sa);
+    L += g_scan(p->scan.g, sa);
+    L += g_sort_scatter(p->sort.g, sa);
+    L += g_gamma(p->gam.g, p->smem_gamma, DF, sa);
+    L += g_gamma_warp(p->gamw.g, DF, sa);
+    cudaEventRecord(p->items_done, sa);
+    // H^N values, the sandwich and E, S
     L += g_pair_values(p->pv.g, W, DF, s);
     L += g_sandwich(p->sw.g, DF, p->sw_width, s);
     L += g_sandwich_small(p->sws.g, DF, s);
     L += g_tn_partial(p->tn.g, p->smem_tn, DF, s);
     L += g_tn_reduce(p->tnr.g, DF, s);
-    L += g_item_fill(p->itf.g, s);
-    L += g_zero(p->zero.g, s);
-    L += g_sort_hist(p->sort.g, s);
-    L += g_scan(p->scan.g, s);
-    L += g_sort_scatter(p->sort.g, s);
-    L += g_gamma(p->gam.g, p->smem_gamma, DF, s);
-    L += g_gamma_warp(p->gamw.g, DF, s);
-    L += g_gdiag(p->gdp.g, p->gdr.g, p->smem_gd, DF, s);
+    cudaStreamWaitEvent(s, p->items_done, 0);
+    cudaStreamWaitEvent(s, p->gd_done, 0);
     L += g_assemble(p->asmb.g, DF, s);
     rec(p->ev[1]);
     // expansion (Eq. 7): classes 1, 3, 5, 6, 7
     if (p->precision == HB_MIXED) {
+        // the rows with j == j' (double-float) beside the tensor-core kernel,
+        // whose last round of tiles leaves SMs free
+        cudaEventRecord(p->asm_done, s);
+        cudaStreamWaitEvent(sb, p->asm_done, 0);
+        if (p->coef_rows > 0) L += g_diag_rows(p->drows.g, sb);
+        cudaEventRecord(p->dr_done, sb);
         // the tensor-core class-4 kernel and the expansion kernel each hold
         // whole SMs until their work is done: let class 4 run beside the
         // target side and finish before the expansion starts
@@ -822,8 +847,8 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
                 LX += g_split(p->split[i].panel_ctx, p->split[i].lg, &p->tm_coef, p->split[i].st.g, p->Kpad / 64, p->d_cols, p->err, s);
                 rec(p->ev_split[2 * i + 1]);
             }
-            L += g_diag_rows(p->drows.g, s);
         }
+        cudaStreamWaitEvent(s, p->dr_done, 0);
     } else {
         LX += g_expand_fp64(p->x64.g, p->d_cols, s);
     }
@@ -900,7 +925,9 @@ void plan_destroy(Plan *p) {
     if (p->join) cudaEventDestroy(p->join);
     if (p->join_main) cudaEventDestroy(p->join_main);
     if (p->c4_done) cudaEventDestroy(p->c4_done);
-    for (cudaStream_t st : {p->main, p->side})
+    for (cudaEvent_t ev : {p->k1_done, p->items_done, p->gd_done, p->asm_done, p->dr_done})
+        if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t st : {p->main, p->side, p->aux1, p->aux2})
         if (st) {
             cudaStreamSynchronize(st);
             cudaStreamDestroy(st);
