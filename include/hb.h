@@ -112,7 +112,8 @@ typedef struct {
     int32_t autotune;         /* 1 = time the launch-shape candidates on the first build
                                  (results are bit-identical for every candidate) */
     int32_t split_tile;       /* 0 = chosen; 3, 4, 5: tensor-core tiles of (128 >> v) j x (1 << v) j' */
-    int32_t class4_states;    /* 0 = chosen; 8, 16, ..., 64: target states per pass of the mixed class-4 kernel */
+    int32_t class4_states;    /* 0 = chosen; 4, 8, ..., 32, 40, 48, 56, 64: target states per pass of the
+                                 double-float class-4 kernel */
     int32_t class4_threads;   /* 0 = chosen; 32, 64, 128: continuum orbitals per class-4 block */
     int32_t class4_path;      /* mixed build, class 4: 0 = tensor cores for groups of 32..64 states and
                                  the double-float kernel for the rest; 1 = the double-float kernel

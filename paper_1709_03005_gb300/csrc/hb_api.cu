@@ -100,8 +100,9 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
     if (!std::isfinite(p->e_core)) return fail(ctx, HB_ERR_INVALID_ARG, "e_core is not finite");
     if (o && o->split_tile != 0 && (o->split_tile < 3 || o->split_tile > 5))
         return fail(ctx, HB_ERR_INVALID_ARG, "split_tile must be 0, 3, 4 or 5");
-    if (o && o->class4_states != 0 && (o->class4_states < 8 || o->class4_states > 64 || o->class4_states % 8))
-        return fail(ctx, HB_ERR_INVALID_ARG, "class4_states must be 0 or a multiple of 8 up to 64");
+    if (o && o->class4_states != 0 &&
+        (o->class4_states < 4 || o->class4_states > 64 || o->class4_states % (o->class4_states > 32 ? 8 : 4)))
+        return fail(ctx, HB_ERR_INVALID_ARG, "class4_states must be 0, a multiple of 4 up to 32 or of 8 up to 64");
     if (o && o->class4_threads != 0 && o->class4_threads != 32 && o->class4_threads != 64 && o->class4_threads != 128)
         return fail(ctx, HB_ERR_INVALID_ARG, "class4_threads must be 0, 32, 64 or 128");
     if (o && (o->class4_path < 0 || o->class4_path > 2))

@@ -260,10 +260,10 @@ int64_t blocks_class4(int n_l2, int cn, int jt) { return cn > 0 ? (int64_t)n_l2 
 void class4_shape(int ns, int cn, int *ns_tile, int *jt) {
     // passes of at most 32 states (larger tiles cost more in registers and
     // occupancy than the prototype values recomputed per pass), the state
-    // tile rounded up to a multiple of 8
+    // tile rounded up to a multiple of 4 (8 beyond 32)
     const int passes = (ns + 31) / 32;
     const int need = (ns + passes - 1) / passes;
-    *ns_tile = need <= 8 ? 8 : (need + 7) / 8 * 8;
+    *ns_tile = need <= 4 ? 4 : (need + 3) / 4 * 4;
     int best = 128;
     int64_t best_idle = (int64_t)((cn + 127) / 128) * 128 - cn;
     for (int t : {64, 32}) {
@@ -292,9 +292,13 @@ int g_class4(const Grouped<C4Task> &g, int W, int dfloat, int ns_tile, int jt, c
     }
 #define HB_C4DF(WW)                                                                                       \
     switch (ns_tile) {                                                                                    \
+        case 4: class4_df_kernel<WW, 4><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;                 \
         case 8: class4_df_kernel<WW, 8><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;                 \
+        case 12: class4_df_kernel<WW, 12><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
         case 16: class4_df_kernel<WW, 16><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
+        case 20: class4_df_kernel<WW, 20><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
         case 24: class4_df_kernel<WW, 24><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
+        case 28: class4_df_kernel<WW, 28><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
         case 32: class4_df_kernel<WW, 32><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
         case 40: class4_df_kernel<WW, 40><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \
         case 48: class4_df_kernel<WW, 48><<<grid, jt, 0, s>>>(g.tasks, g.blk, g.n); break;               \

@@ -667,7 +667,7 @@ int plan_autotune(Plan *p, cudaStream_t s, std::string *err) {
             float best = 0.0f, def_ms = 0.0f;
             std::pair<int, int> arg(-1, -1);
             std::vector<std::pair<int, int>> cand{{dnt, djt}};
-            for (int nt : {8, 16, 24, 32, 40, 48, 56, 64})
+            for (int nt : {4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64})
                 for (int jt : {32, 64, 128})
                     if (nt != dnt || jt != djt) cand.push_back({nt, jt});
             for (auto &c : cand) {

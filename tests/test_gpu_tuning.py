@@ -30,7 +30,9 @@ def _problems():
 
 SHAPES = [dict(split_tile=3, class4_states=8, class4_threads=32),
           dict(split_tile=4, class4_states=16, class4_threads=64),
-          dict(split_tile=5, class4_states=32, class4_threads=128)]
+          dict(split_tile=5, class4_states=32, class4_threads=128),
+          dict(split_tile=4, class4_states=4, class4_threads=32),
+          dict(split_tile=3, class4_states=20, class4_threads=64)]
 
 
 @pytest.mark.parametrize("idx", [0, 1])
@@ -73,7 +75,8 @@ def test_autotune_is_bit_identical():
 def test_invalid_shape_options_rejected():
     from paper_1709_03005_gb300 import hb
     P = _problems()[0]
-    for kw in (dict(split_tile=6), dict(class4_states=12), dict(class4_threads=96), dict(class4_path=3),
+    for kw in (dict(split_tile=6), dict(class4_states=14), dict(class4_states=36), dict(class4_threads=96),
+               dict(class4_path=3),
                dict(class4_path=-1)):
         with pytest.raises(hb.HBError):
             hb.Hamiltonian(P, **kw)
