@@ -179,7 +179,7 @@ __device__ __forceinline__ void prototype_df(const C4Task &T, const hb_pair &r, 
 // Block = blockDim.x continuum orbitals (32, 64 or 128) of one L2 row; NS
 // target states per pass.
 template <int W, int NS>
-__global__ void __launch_bounds__(kJ)
+__global__ void __launch_bounds__(kJ, NS <= 24 ? 6 : 1)
 class4_df_kernel(const C4Task *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
     __shared__ float2 cs[kBatch][NS];
     __shared__ hb_pair rs[kBatch];
