@@ -46,6 +46,8 @@ struct PVTask {         // <D_m|H^N|D'_m'> for the records of a group pair
     const hb_pair *pairs;
     int64_t n_pairs;
     double *val;
+    const int64_t *row_ptr;   // records of row m: [row_ptr[m], row_ptr[m + 1]), ascending columns
+    int n_rows, same;         // same group: the diagonal records (m, m) go to g_diag_values
 };
 
 // In the double-float launches of the stages below, val, Wout, Wm and partial
@@ -231,6 +233,9 @@ struct L2Task {         // classes 2 and 8: L2-L2 CSR of one Hamiltonian
 // Each returns the number of kernel launches it made (0 for an empty stage).
 int g_classify(const Grouped<ClsTask> &g, int W, int mode, cudaStream_t s);
 int g_pair_values(const Grouped<PVTask> &g, int W, int dfloat, cudaStream_t s);
+// the diagonal records (m, m) of same-group tasks, one thread per row
+int g_diag_values(const Grouped<PVTask> &g, int W, int dfloat, cudaStream_t s);
+int64_t blocks_diag_values(int n_rows);
 int g_l2_csr(const Grouped<L2Task> &g, int W, int dfloat, cudaStream_t s);
 // width: states per pass of the double-float kernel (16, 24 or 32; the
 // largest state count of the launch, rounded up, passes of 32 beyond)

@@ -75,6 +75,7 @@ struct Plan {
     int W = 1, Kpad = 0, n_to = 0, S = 0, delta_col = 0;
     Stage<ClsTask> cls_tt, cls_tl2;
     Stage<PVTask> pv;
+    Stage<PVTask> pvd;                 // the diagonal records of same-group pairs
     Stage<SWTask> sw, sws;             // sandwich: lanes over records / over states
     int sw_width = 16;                 // states per pass of the record-lane sandwich
     Stage<TNTask> tn, tnr;
@@ -169,7 +170,7 @@ void stage_bind(Stage<T> &st, uint8_t *dev) {
 
 // Task tables of every stage from the contexts and the output blocks.
 void fill_tasks(Plan &p) {
-    p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.sw.clear(); p.sws.clear(); p.sw_width = 16; p.gamw.clear(); p.gdp.clear(); p.gdr.clear(); p.tn.clear(); p.tnr.clear();
+    p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.pvd.clear(); p.sw.clear(); p.sws.clear(); p.sw_width = 16; p.gamw.clear(); p.gdp.clear(); p.gdr.clear(); p.tn.clear(); p.tnr.clear();
     p.itf.clear(); p.zero.clear(); p.sort.clear(); p.scan.clear(); p.gam.clear(); p.asmb.clear();
     p.x64.clear(); p.slc.clear(); p.drows.clear(); p.l2.clear();
     for (auto &v : p.c4v) v.st.clear();
@@ -222,7 +223,9 @@ void fill_tasks(Plan &p) {
             p.cls_tt.add(ClsTask{da, db, A.ndet, B.ndet, ctx->cont_spin, 2, 0, P.rowptr, P.seg_off, seg_count(B.ndet),
                                  P.pairs},
                          blocks_seg_rows8(A.ndet, B.ndet));
-            p.pv.add(PVTask{I, da, db, P.pairs, P.n_pairs, P.val}, blocks_pair_values(P.n_pairs));
+            const PVTask pvt{I, da, db, P.pairs, P.n_pairs, P.val, P.rowptr, A.ndet, P.same};
+            p.pv.add(pvt, blocks_pair_values(P.n_pairs));
+            if (P.same) p.pvd.add(pvt, blocks_diag_values(A.ndet));
             // lanes over the states for at most 16 of them (two or more record
             // groups per warp), lanes over the records otherwise
             {
@@ -407,7 +410,7 @@ void ensure_split_events(Plan &p) {
 
 void pack_all(Plan &p) {
     p.host.clear();
-    stage_pack(p.cls_tt, p.host); stage_pack(p.cls_tl2, p.host); stage_pack(p.pv, p.host);
+    stage_pack(p.cls_tt, p.host); stage_pack(p.cls_tl2, p.host); stage_pack(p.pv, p.host); stage_pack(p.pvd, p.host);
     stage_pack(p.sw, p.host); stage_pack(p.sws, p.host); stage_pack(p.gamw, p.host);
     stage_pack(p.gdp, p.host); stage_pack(p.gdr, p.host); stage_pack(p.tn, p.host); stage_pack(p.tnr, p.host); stage_pack(p.itf, p.host);
     stage_pack(p.zero, p.host); stage_pack(p.sort, p.host); stage_pack(p.scan, p.host); stage_pack(p.gam, p.host);
@@ -426,7 +429,7 @@ void pack_all(Plan &p) {
 }
 
 void bind_all(Plan &p) {
-    stage_bind(p.cls_tt, p.dev); stage_bind(p.cls_tl2, p.dev); stage_bind(p.pv, p.dev);
+    stage_bind(p.cls_tt, p.dev); stage_bind(p.cls_tl2, p.dev); stage_bind(p.pv, p.dev); stage_bind(p.pvd, p.dev);
     stage_bind(p.sw, p.dev); stage_bind(p.sws, p.dev); stage_bind(p.gamw, p.dev);
     stage_bind(p.gdp, p.dev); stage_bind(p.gdr, p.dev); stage_bind(p.tn, p.dev); stage_bind(p.tnr, p.dev); stage_bind(p.itf, p.dev);
     stage_bind(p.zero, p.dev); stage_bind(p.sort, p.dev); stage_bind(p.scan, p.dev); stage_bind(p.gam, p.dev);
@@ -819,6 +822,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     cudaEventRecord(p->items_done, sa);
     // H^N values, the sandwich and E, S
     L += g_pair_values(p->pv.g, W, DF, s);
+    L += g_diag_values(p->pvd.g, W, DF, s);
     L += g_sandwich(p->sw.g, DF, p->sw_width, s);
     L += g_sandwich_small(p->sws.g, DF, s);
     L += g_tn_partial(p->tn.g, p->smem_tn, DF, s);

@@ -246,6 +246,9 @@ __global__ void pair_values_kernel(const PVTask *__restrict__ tasks, const int64
     if (k >= T.n_pairs) return;
     const Ints I = T.I;
     const hb_pair r = T.pairs[k];
+    // within one group the diagonal records (O(N^2) sums, one per row) are
+    // left to diag_values_kernel, so that no warp here waits on one
+    if (r.degree == 0 && T.same) return;
     uint64_t a[2 * W], b[2 * W];
     load_det<W>(T.a + (int64_t)r.row * 2 * W, a);
     load_det<W>(T.b + (int64_t)r.col * 2 * W, b);
@@ -255,6 +258,31 @@ __global__ void pair_values_kernel(const PVTask *__restrict__ tasks, const int64
     else v = double_value<Acc>(I, W, r.hole[0], r.hole[1], r.part[0], r.part[1]);
     if (r.degree > 0 && r.phase < 0) v.neg();
     store_value(v, T.val, k);
+}
+
+// <D_m|H^N|D_m> of a same-group task: the record (m, m) of row m, found by
+// binary search over the row's ascending columns (a scan if that fails).
+template <int W, class Acc>
+__global__ void diag_values_kernel(const PVTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const PVTask &T = tasks[ti];
+    const int m = (int)((blockIdx.x - blk[ti]) * (int64_t)blockDim.x + threadIdx.x);
+    if (m >= T.n_rows) return;
+    int64_t lo = T.row_ptr[m], hi = T.row_ptr[m + 1] - 1, at = -1;
+    while (lo <= hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int c = T.pairs[mid].col;
+        if (c == m) { at = mid; break; }
+        if (c < m) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    if (at < 0)
+        for (int64_t k = T.row_ptr[m]; k < T.row_ptr[m + 1]; ++k)
+            if (T.pairs[k].col == m) { at = k; break; }
+    if (at < 0 || T.pairs[at].degree != 0) return;
+    uint64_t a[2 * W];
+    load_det<W>(T.a + (int64_t)m * 2 * W, a);
+    store_value(diag_value<W, Acc>(T.I, a), T.val, at);
 }
 
 __global__ void jk_kernel(Ints I, double *jk) {
@@ -274,6 +302,22 @@ void build_jk(const Ints &I, double *jk, cudaStream_t s) {
 }
 
 int64_t blocks_pair_values(int64_t n_pairs) { return (n_pairs + 255) / 256; }
+int64_t blocks_diag_values(int n_rows) { return (n_rows + 255) / 256; }
+
+int g_diag_values(const Grouped<PVTask> &g, int W, int dfloat, cudaStream_t s) {
+    if (g.blocks <= 0) return 0;
+    const unsigned grid = (unsigned)g.blocks;
+#define HB_DV(WW) (dfloat ? diag_values_kernel<WW, AccF><<<grid, 256, 0, s>>>(g.tasks, g.blk, g.n) \
+                          : diag_values_kernel<WW, AccD><<<grid, 256, 0, s>>>(g.tasks, g.blk, g.n))
+    switch (W) {
+        case 1: HB_DV(1); break;
+        case 2: HB_DV(2); break;
+        case 3: HB_DV(3); break;
+        default: HB_DV(4); break;
+    }
+#undef HB_DV
+    return 1;
+}
 
 int g_l2_csr(const Grouped<L2Task> &g, int W, int dfloat, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
