@@ -124,10 +124,10 @@ struct Plan {
     // the target side and the expansion, the longer chain, at higher priority
     cudaStream_t main = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, join_main = nullptr;
-    // the target side's independent chains: the gamma items (aux1), the
-    // diagonal gamma and then the j == j' rows (aux2), beside the E, S chain
+    // the target side's independent chains: the diagonal H^N values and the
+    // gamma items (aux1), the diagonal gamma (aux2), beside the E, S chain
     cudaStream_t aux1 = nullptr, aux2 = nullptr;
-    cudaEvent_t k1_done = nullptr, items_done = nullptr, gd_done = nullptr, asm_done = nullptr, dr_done = nullptr;
+    cudaEvent_t k1_done = nullptr, items_done = nullptr, gd_done = nullptr, dv_done = nullptr;
     cudaEvent_t c4_done = nullptr;     // the tensor-core class-4 kernel has finished (side stream)
     // timers: start, target, expansion (main stream); class-4 end, L2 end, side
     // start (side stream); end after the join; L2 start (side stream); split kernels
@@ -505,7 +505,7 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, least);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->aux1, cudaStreamNonBlocking, greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->aux2, cudaStreamNonBlocking, greatest);
-    for (cudaEvent_t *ev : {&p->k1_done, &p->items_done, &p->gd_done, &p->asm_done, &p->dr_done})
+    for (cudaEvent_t *ev : {&p->k1_done, &p->items_done, &p->gd_done, &p->dv_done})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&p->err, 2 * sizeof(int));   // split kernel, class-4 kernel
     if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, 2 * sizeof(int), s);
@@ -780,8 +780,8 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     L += g_classify(p->cls_tl2.g, W, 1, s2);
     if (p->c4t.g.blocks > 0) {
         // the tensor-core class-4 kernel and the expansion kernel each hold
-        // whole SMs until their work is done, and the L2 kernel's blocks do
-        // not fit beside either: the L2 rows run beside the target side, then
+        // whole SMs until their work is done, and the L2 rows' blocks do not
+        // fit beside either: the L2 rows run beside the target side, then
         // class 4, and the expansion starts once both are done
         rec_on(p->ev[7], s2);
         L += g_l2_csr(p->l2.g, W, 0, s2);
@@ -812,6 +812,9 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     cudaEventRecord(p->k1_done, s);
     // the gamma items of the single-excitation records, sorted by key, and gamma
     cudaStreamWaitEvent(sa, p->k1_done, 0);
+    // the diagonal H^N values (a sequential sum per row) beside the others
+    L += g_diag_values(p->pvd.g, W, DF, sa);
+    cudaEventRecord(p->dv_done, sa);
     L += g_item_fill(p->itf.g, sa);
     L += g_zero(p->zero.g, sa);
     L += g_sort_hist(p->sort.g, sa);
@@ -822,7 +825,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     cudaEventRecord(p->items_done, sa);
     // H^N values, the sandwich and E, S
     L += g_pair_values(p->pv.g, W, DF, s);
-    L += g_diag_values(p->pvd.g, W, DF, s);
+    cudaStreamWaitEvent(s, p->dv_done, 0);
     L += g_sandwich(p->sw.g, DF, p->sw_width, s);
     L += g_sandwich_small(p->sws.g, DF, s);
     L += g_tn_partial(p->tn.g, p->smem_tn, DF, s);
@@ -833,15 +836,9 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     rec(p->ev[1]);
     // expansion (Eq. 7): classes 1, 3, 5, 6, 7
     if (p->precision == HB_MIXED) {
-        // the rows with j == j' (double-float) beside the tensor-core kernel,
-        // whose last round of tiles leaves SMs free
-        cudaEventRecord(p->asm_done, s);
-        cudaStreamWaitEvent(sb, p->asm_done, 0);
-        if (p->coef_rows > 0) L += g_diag_rows(p->drows.g, sb);
-        cudaEventRecord(p->dr_done, sb);
-        // the tensor-core class-4 kernel and the expansion kernel each hold
-        // whole SMs until their work is done: let class 4 run beside the
-        // target side and finish before the expansion starts
+        // with class 4 on the tensor cores, the expansion waits for it (see
+        // the side stream above); the double-float class-4 kernel runs beside
+        // the expansion, which was faster than running it first
         if (p->c4t.g.blocks > 0) cudaStreamWaitEvent(s, p->c4_done, 0);
         if (p->coef_rows > 0) {
             cudaMemsetAsync(p->err, 0, sizeof(int), s);
@@ -851,8 +848,10 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
                 LX += g_split(p->split[i].panel_ctx, p->split[i].lg, &p->tm_coef, p->split[i].st.g, p->Kpad / 64, p->d_cols, p->err, s);
                 rec(p->ev_split[2 * i + 1]);
             }
+            // the rows with j == j' (double-float); beside the split kernel they
+            // slowed it by more than they saved
+            L += g_diag_rows(p->drows.g, s);
         }
-        cudaStreamWaitEvent(s, p->dr_done, 0);
     } else {
         LX += g_expand_fp64(p->x64.g, p->d_cols, s);
     }
@@ -929,7 +928,7 @@ void plan_destroy(Plan *p) {
     if (p->join) cudaEventDestroy(p->join);
     if (p->join_main) cudaEventDestroy(p->join_main);
     if (p->c4_done) cudaEventDestroy(p->c4_done);
-    for (cudaEvent_t ev : {p->k1_done, p->items_done, p->gd_done, p->asm_done, p->dr_done})
+    for (cudaEvent_t ev : {p->k1_done, p->items_done, p->gd_done, p->dv_done})
         if (ev) cudaEventDestroy(ev);
     for (cudaStream_t st : {p->main, p->side, p->aux1, p->aux2})
         if (st) {
