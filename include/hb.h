@@ -161,7 +161,8 @@ typedef struct {
     double expand_tensor_flops;  /* mixed: bf16 tensor flops of the split products */
     float ms_gram;            /* hb_diag: projections (device sums and their copy to the host) */
     float ms_combine;         /* hb_diag: basis combinations (coefficients to the device, kernel) */
-    int32_t reserved[4];
+    float ms_class4_kernel;   /* the class-4 kernels after their classification (part of ms_class4) */
+    int32_t reserved[3];
 } hb_stats;
 
 /* Excitation record of one determinant pair (row, col), see hb_classify. */

@@ -76,6 +76,54 @@ static int dalloc(hb_ctx *ctx, T **p, size_t n) {
         if (_r != HB_OK) return _r;                      \
     } while (0)
 
+// The L2 x L2 block (classes 2 and 8) is symmetric: list each entry below the
+// diagonal with the position of its mirror, so that a build evaluates only the
+// upper triangle.  If some mirror were absent the lists stay unused.
+static int l2_mirror_prepare(hb_ctx *ctx, int n, int W, cudaStream_t s) {
+    int32_t *col_all = nullptr;
+    int *missing = nullptr;
+    auto done = [&](int rc) {
+        cudaFree(col_all);
+        cudaFree(missing);
+        return rc;
+    };
+    cudaError_t e = cudaMalloc((void **)&col_all, sizeof(int32_t) * (size_t)ctx->l2_nnz);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&missing, sizeof(int));
+    if (e != cudaSuccess) return done(cuda_fail(ctx, e, "cudaMalloc"));
+    int64_t *low = nullptr;
+    int rc = dalloc(ctx, &low, (size_t)n + 1);
+    if (rc != HB_OK) return done(rc);
+    e = cudaMemsetAsync(missing, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(low, 0, sizeof(int64_t), s);
+    l2_struct(ctx->l2, n, W, ctx->l2_rowptr, col_all, s);
+    l2_lower_counts(col_all, ctx->l2_rowptr, n, low, s);
+    exclusive_scan_inplace(low, n, s);
+    int64_t nl = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, low + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return done(cuda_fail(ctx, e, "L2 mirror positions"));
+    int64_t *dst = nullptr, *src = nullptr;
+    int32_t *mcol = nullptr;
+    if ((rc = dalloc(ctx, &dst, (size_t)nl)) != HB_OK) return done(rc);
+    if ((rc = dalloc(ctx, &src, (size_t)nl)) != HB_OK) return done(rc);
+    if ((rc = dalloc(ctx, &mcol, (size_t)nl)) != HB_OK) return done(rc);
+    l2_mirror_fill(col_all, ctx->l2_rowptr, n, low, dst, src, mcol, missing, s);
+    int miss = 1;
+    e = cudaMemcpyAsync(&miss, missing, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return done(cuda_fail(ctx, e, "L2 mirror positions"));
+    if (!miss) {
+        ctx->l2_low_ptr = low;
+        ctx->l2_mdst = dst;
+        ctx->l2_msrc = src;
+        ctx->l2_mcol = mcol;
+        ctx->l2_nlow = nl;
+    }
+    return done(HB_OK);
+}
+
 static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o) {
     if (!p) return fail(ctx, HB_ERR_INVALID_ARG, "problem is NULL");
     if (p->n_words < 1 || p->n_words > HB_MAXW)
@@ -344,6 +392,10 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         ctx->tl2_pairs += L.n_pairs;
     }
     CK(cudaMemcpy(&ctx->l2_nnz, ctx->l2_rowptr + p->n_l2, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (p->n_l2 > 1 && ctx->l2_nnz > 0) {
+        const int rc = l2_mirror_prepare(ctx, p->n_l2, W, s);
+        if (rc != HB_OK) return rc;
+    }
     // --- per group pair scratch; the gamma item count needs the records
     const int n_keys = 2 * p->n_to * p->n_to;
     for (auto &P : ctx->gps) {

@@ -70,6 +70,10 @@ struct hb_ctx {
     int64_t *l2_rowptr = nullptr;
     int32_t *l2_seg_off = nullptr;
     int64_t l2_nnz = 0, tt_pairs = 0, tl2_pairs = 0;
+    // the L2 x L2 entries below the diagonal and their mirrors (null: none found)
+    int64_t *l2_low_ptr = nullptr, *l2_mdst = nullptr, *l2_msrc = nullptr;
+    int32_t *l2_mcol = nullptr;
+    int64_t l2_nlow = 0;
     hb::MixedState *mixed = nullptr;
     hb_ctx *base = nullptr;  // context whose staged integrals this one borrows (or null)
     void *plan = nullptr;    // cached grouped-launch plan of this context's own builds (k_plan.cu)

@@ -67,6 +67,16 @@ void k1_fill_pairs(const uint64_t *a, int n_a, const uint64_t *b, int n_b, int W
                    int max_degree, int lower, const int64_t *row_ptr, hb_pair *out, cudaStream_t s);
 // x[0] = 0, x[1..n] := inclusive scan of x[1..n] (CSR offsets); one block.
 void exclusive_scan_inplace(int64_t *x, int n, cudaStream_t s);
+// Mirror positions of the L2 x L2 block (classes 2 and 8), found once per context:
+// l2_struct writes the column of every entry (rows of row_ptr, ascending
+// columns); l2_lower_counts writes at low_ptr[r + 1] how many entries of row r
+// lie below the diagonal; l2_mirror_fill lists, for each such entry (in row
+// order, at low_ptr[r] + k), its position, the position of its mirror (c, r)
+// and its column c, and sets *missing if some mirror is absent.
+void l2_struct(const uint64_t *dets, int n, int W, const int64_t *row_ptr, int32_t *col, cudaStream_t s);
+void l2_lower_counts(const int32_t *col, const int64_t *row_ptr, int n, int64_t *low_ptr, cudaStream_t s);
+void l2_mirror_fill(const int32_t *col, const int64_t *row_ptr, int n, const int64_t *low_ptr, int64_t *dst,
+                    int64_t *src, int32_t *mcol, int *missing, cudaStream_t s);
 
 // K5 Slater-Condon (k_slater.cu)
 void build_jk(const Ints &I, double *jk, cudaStream_t s);

@@ -227,6 +227,17 @@ struct L2Task {         // classes 2 and 8: L2-L2 CSR of one Hamiltonian
     int32_t *col;
     double *val;
     double e_core;
+    // non-null: entries below the diagonal of row r are [row_ptr[r], row_ptr[r] +
+    // low_ptr[r + 1] - low_ptr[r]) and come from g_l2_mirror; only col >= row here
+    const int64_t *low_ptr;
+};
+
+struct L2MTask {        // classes 2 and 8: the entries below the diagonal from their mirrors
+    const int64_t *dst, *src;  // position of each lower entry and of its mirror (col, row)
+    const int32_t *mcol;       // its column
+    int64_t n;
+    int32_t *col;
+    double *val;
 };
 
 // ------------------------------------------------------------ launchers
@@ -237,6 +248,8 @@ int g_pair_values(const Grouped<PVTask> &g, int W, int dfloat, cudaStream_t s);
 int g_diag_values(const Grouped<PVTask> &g, int W, int dfloat, cudaStream_t s);
 int64_t blocks_diag_values(int n_rows);
 int g_l2_csr(const Grouped<L2Task> &g, int W, int dfloat, cudaStream_t s);
+int g_l2_mirror(const Grouped<L2MTask> &g, cudaStream_t s);
+constexpr int kL2MirrorThreads = 256;
 // width: states per pass of the double-float kernel (16, 24 or 32; the
 // largest state count of the launch, rounded up, passes of 32 beyond)
 int g_sandwich(const Grouped<SWTask> &g, int dfloat, int width, cudaStream_t s);

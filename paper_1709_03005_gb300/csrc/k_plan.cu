@@ -99,6 +99,7 @@ struct Plan {
     Stage<C4FTask> c4f;                // class 4 on the tensor cores: term lists, then the GEMMs
     Stage<C4TTask> c4t;
     Stage<L2Task> l2;
+    Stage<L2MTask> l2m;          // the L2 x L2 entries below the diagonal, after l2
     std::vector<ExpCol> cols;          // columns of the merged expansion blocks
     size_t off_cols = 0;
     const ExpCol *d_cols = nullptr;
@@ -130,8 +131,9 @@ struct Plan {
     cudaEvent_t k1_done = nullptr, items_done = nullptr, gd_done = nullptr, dv_done = nullptr;
     cudaEvent_t c4_done = nullptr;     // the tensor-core class-4 kernel has finished (side stream)
     // timers: start, target, expansion (main stream); class-4 end, L2 end, side
-    // start (side stream); end after the join; L2 start (side stream); split kernels
-    cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // start (side stream); end after the join; L2 start, class-4 classification
+    // end (side stream); split kernels
+    cudaEvent_t ev[9] = {};
     std::vector<cudaEvent_t> ev_split;
     int launches = 0, expand_launches = 0;
     bool timed = false;
@@ -172,7 +174,7 @@ void stage_bind(Stage<T> &st, uint8_t *dev) {
 void fill_tasks(Plan &p) {
     p.cls_tt.clear(); p.cls_tl2.clear(); p.pv.clear(); p.pvd.clear(); p.sw.clear(); p.sws.clear(); p.sw_width = 16; p.gamw.clear(); p.gdp.clear(); p.gdr.clear(); p.tn.clear(); p.tnr.clear();
     p.itf.clear(); p.zero.clear(); p.sort.clear(); p.scan.clear(); p.gam.clear(); p.asmb.clear();
-    p.x64.clear(); p.slc.clear(); p.drows.clear(); p.l2.clear();
+    p.x64.clear(); p.slc.clear(); p.drows.clear(); p.l2.clear(); p.l2m.clear();
     for (auto &v : p.c4v) v.st.clear();
     p.c4f.clear(); p.c4t.clear();
     for (auto &sg : p.split) sg.st.clear();
@@ -333,10 +335,14 @@ void fill_tasks(Plan &p) {
             var->st.add(c4t, blocks_class4(ctx->n_l2, G.cn, jt));
             if (p.precision == HB_MIXED) p.tune_c4.push_back(TuneC4{c4t});
         }
-        if (ctx->n_l2 > 0)
+        if (ctx->n_l2 > 0) {
             p.l2.add(L2Task{I, ctx->l2, ctx->n_l2, seg_count(ctx->n_l2), ctx->l2_rowptr, ctx->l2_seg_off, out.l2_row_ptr,
-                            out.l2_col, out.l2_val, ctx->e_core},
+                            out.l2_col, out.l2_val, ctx->e_core, ctx->l2_low_ptr},
                      blocks_seg_rows8(ctx->n_l2, ctx->n_l2));
+            if (ctx->l2_low_ptr && ctx->l2_nlow > 0)
+                p.l2m.add(L2MTask{ctx->l2_mdst, ctx->l2_msrc, ctx->l2_mcol, ctx->l2_nlow, out.l2_col, out.l2_val},
+                          (ctx->l2_nlow + kL2MirrorThreads - 1) / kL2MirrorThreads);
+        }
     }
     // merged expansion blocks: columns member by member, state pairs in order
     for (auto &B : blocks) {
@@ -416,7 +422,7 @@ void pack_all(Plan &p) {
     stage_pack(p.zero, p.host); stage_pack(p.sort, p.host); stage_pack(p.scan, p.host); stage_pack(p.gam, p.host);
     stage_pack(p.asmb, p.host); stage_pack(p.x64, p.host); stage_pack(p.slc, p.host);
     for (auto &sg : p.split) stage_pack(sg.st, p.host);
-    stage_pack(p.drows, p.host); stage_pack(p.l2, p.host);
+    stage_pack(p.drows, p.host); stage_pack(p.l2, p.host); stage_pack(p.l2m, p.host);
     for (auto &v : p.c4v) stage_pack(v.st, p.host);
     stage_pack(p.c4f, p.host); stage_pack(p.c4t, p.host);
     p.off_cols = align256(p.host.size());
@@ -435,7 +441,7 @@ void bind_all(Plan &p) {
     stage_bind(p.zero, p.dev); stage_bind(p.sort, p.dev); stage_bind(p.scan, p.dev); stage_bind(p.gam, p.dev);
     stage_bind(p.asmb, p.dev); stage_bind(p.x64, p.dev); stage_bind(p.slc, p.dev);
     for (auto &sg : p.split) stage_bind(sg.st, p.dev);
-    stage_bind(p.drows, p.dev); stage_bind(p.l2, p.dev);
+    stage_bind(p.drows, p.dev); stage_bind(p.l2, p.dev); stage_bind(p.l2m, p.dev);
     for (auto &v : p.c4v) stage_bind(v.st, p.dev);
     stage_bind(p.c4f, p.dev); stage_bind(p.c4t, p.dev);
     p.d_cols = (const ExpCol *)(p.dev + p.off_cols);
@@ -493,7 +499,7 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
         }
     int rc = HB_OK;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&p->ev[i]);
+    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreate(&p->ev[i]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->uploaded, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
@@ -778,6 +784,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     // pair scan, where the longer double-float sums cost more than FP64 adds
     rec_on(p->ev[5], s2);
     L += g_classify(p->cls_tl2.g, W, 1, s2);
+    rec_on(p->ev[8], s2);
     if (p->c4t.g.blocks > 0) {
         // the tensor-core class-4 kernel and the expansion kernel each hold
         // whole SMs until their work is done, and the L2 rows' blocks do not
@@ -785,6 +792,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
         // class 4, and the expansion starts once both are done
         rec_on(p->ev[7], s2);
         L += g_l2_csr(p->l2.g, W, 0, s2);
+        L += g_l2_mirror(p->l2m.g, s2);
         rec_on(p->ev[4], s2);
         cudaMemsetAsync(p->err + 1, 0, sizeof(int), s2);
         L += g_c4fill(p->c4f.g, s2);
@@ -797,6 +805,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
         rec_on(p->ev[3], s2);
         rec_on(p->ev[7], s2);
         L += g_l2_csr(p->l2.g, W, 0, s2);
+        L += g_l2_mirror(p->l2m.g, s2);
         rec_on(p->ev[4], s2);
     }
     cudaEventRecord(p->join, s2);
@@ -891,8 +900,10 @@ void plan_stats(Plan *p, hb_stats *st) {
         cudaEventElapsedTime(&a, p->ev[5], p->ev[7]);
         cudaEventElapsedTime(&b, p->ev[4], p->ev[3]);
         st->ms_class4 = a + b;
+        st->ms_class4_kernel = b;
     } else {
         cudaEventElapsedTime(&st->ms_class4, p->ev[5], p->ev[3]);
+        cudaEventElapsedTime(&st->ms_class4_kernel, p->ev[8], p->ev[3]);
     }
     if (p->precision == HB_MIXED) {
         float total = 0.0f;

@@ -181,12 +181,23 @@ l2_csr_kernel(const L2Task *__restrict__ tasks, const int64_t *__restrict__ blk,
     const int t0 = sg * TC;
     if (t0 >= n) return;
     const int tn = min(TC, n - t0);
+    // upper triangle only: a segment below the diagonal of every row of the block has nothing to do
+    if (T.low_ptr && t0 + tn <= rb * kWarps) return;
     for (int i = threadIdx.x; i < tn * 2 * W; i += blockDim.x) {
         const int c = i / (2 * W), w = i % (2 * W);
         tile[w * TC + c] = __ldg(D + (int64_t)t0 * 2 * W + i);
     }
     __syncthreads();
     if (!active) return;
+    int cmin = 0;             // first column of the segment evaluated in this row
+    if (T.low_ptr) {
+        if (t0 + tn <= row) return;
+        if (t0 <= row) {
+            // the diagonal's segment: the entries of this row from the diagonal on
+            cmin = row - t0;
+            pos = T.row_ptr[row] + (T.low_ptr[row + 1] - T.low_ptr[row]);
+        }
+    }
     auto drain = [&](int cnt) {
         if (lane < cnt) {
             const int cl = q[lane];
@@ -212,7 +223,7 @@ l2_csr_kernel(const L2Task *__restrict__ tasks, const int64_t *__restrict__ blk,
     for (int c0 = 0; c0 < tn; c0 += 32) {
         const int cl = c0 + lane;
         bool ok = false;
-        if (cl < tn) {
+        if (cl < tn && cl >= cmin) {
             int x = 0;
 #pragma unroll
             for (int i = 0; i < 2 * W; ++i) x += __popcll(a[i] ^ tile[i * TC + cl]);
@@ -234,6 +245,86 @@ l2_csr_kernel(const L2Task *__restrict__ tasks, const int64_t *__restrict__ blk,
         }
     }
     if (qn > 0) drain(qn);
+}
+
+// The L2 x L2 block is symmetric (the excitation test and the Slater-Condon
+// value do not depend on the order of the pair), so a build evaluates the
+// entries with col >= row and copies each entry below the diagonal from its
+// mirror.  The positions depend only on the determinants; the kernels after
+// this one find them once per context.
+__global__ void l2_mirror_kernel(const L2MTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks) {
+    const int ti = task_of(blk, n_tasks, blockIdx.x);
+    const L2MTask &T = tasks[ti];
+    const int64_t i = (int64_t)(blockIdx.x - blk[ti]) * kL2MirrorThreads + threadIdx.x;
+    if (i >= T.n) return;
+    const int64_t d = T.dst[i];
+    T.col[d] = T.mcol[i];
+    T.val[d] = T.val[T.src[i]];
+}
+
+// One warp per row: the columns of its entries in ascending order.
+template <int W>
+__global__ void l2_struct_kernel(const uint64_t *__restrict__ D, int n, const int64_t *__restrict__ row_ptr,
+                                 int32_t *__restrict__ col) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= n) return;
+    uint64_t a[2 * W];
+    load_det<W>(D + row * 2 * W, a);
+    int64_t pos = row_ptr[row];
+    const int64_t end = row_ptr[row + 1];
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int c = c0 + lane;
+        bool ok = false;
+        if (c < n) {
+            int x = 0;
+#pragma unroll
+            for (int i = 0; i < 2 * W; ++i) x += __popcll(a[i] ^ __ldg(D + (int64_t)c * 2 * W + i));
+            ok = (x >> 1) <= 2;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        const int64_t at = pos + __popc(m & ((1u << lane) - 1u));
+        if (ok && at < end) col[at] = c;
+        pos += __popc(m);
+    }
+}
+
+// First position in [b, e) whose column is >= c (columns ascending).
+__device__ __forceinline__ int64_t lower_bound_col(const int32_t *__restrict__ col, int64_t b, int64_t e, int c) {
+    while (b < e) {
+        const int64_t m = b + ((e - b) >> 1);
+        if (col[m] < c) b = m + 1;
+        else e = m;
+    }
+    return b;
+}
+
+__global__ void l2_lower_counts_kernel(const int32_t *__restrict__ col, const int64_t *__restrict__ row_ptr, int n,
+                                       int64_t *__restrict__ low_ptr) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    low_ptr[r + 1] = lower_bound_col(col, row_ptr[r], row_ptr[r + 1], r) - row_ptr[r];
+}
+
+__global__ void l2_mirror_fill_kernel(const int32_t *__restrict__ col, const int64_t *__restrict__ row_ptr, int n,
+                                      const int64_t *__restrict__ low_ptr, int64_t *__restrict__ dst,
+                                      int64_t *__restrict__ src, int32_t *__restrict__ mcol, int *missing) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t q0 = low_ptr[r], nl = low_ptr[r + 1] - q0;
+    for (int64_t k = 0; k < nl; ++k) {
+        const int64_t at = row_ptr[r] + k;
+        const int c = col[at];
+        const int64_t e = row_ptr[c + 1];
+        int64_t m = lower_bound_col(col, row_ptr[c], e, r);
+        if (m >= e || col[m] != r) {
+            atomicExch(missing, 1);
+            m = at;
+        }
+        dst[q0 + k] = at;
+        src[q0 + k] = m;
+        mcol[q0 + k] = c;
+    }
 }
 
 // <A[row]|H|B[col]> for classified pairs (mode 0 records).  FP64: val as
@@ -332,6 +423,34 @@ int g_l2_csr(const Grouped<L2Task> &g, int W, int dfloat, cudaStream_t s) {
     }
 #undef HB_L2
     return 1;
+}
+
+int g_l2_mirror(const Grouped<L2MTask> &g, cudaStream_t s) {
+    if (g.blocks <= 0) return 0;
+    l2_mirror_kernel<<<(unsigned)g.blocks, kL2MirrorThreads, 0, s>>>(g.tasks, g.blk, g.n);
+    return 1;
+}
+
+void l2_struct(const uint64_t *dets, int n, int W, const int64_t *row_ptr, int32_t *col, cudaStream_t s) {
+    if (n <= 0) return;
+    const unsigned grid = (unsigned)(((int64_t)n * 32 + 255) / 256);
+    switch (W) {
+        case 1: l2_struct_kernel<1><<<grid, 256, 0, s>>>(dets, n, row_ptr, col); break;
+        case 2: l2_struct_kernel<2><<<grid, 256, 0, s>>>(dets, n, row_ptr, col); break;
+        case 3: l2_struct_kernel<3><<<grid, 256, 0, s>>>(dets, n, row_ptr, col); break;
+        default: l2_struct_kernel<4><<<grid, 256, 0, s>>>(dets, n, row_ptr, col); break;
+    }
+}
+
+void l2_lower_counts(const int32_t *col, const int64_t *row_ptr, int n, int64_t *low_ptr, cudaStream_t s) {
+    if (n <= 0) return;
+    l2_lower_counts_kernel<<<(n + 255) / 256, 256, 0, s>>>(col, row_ptr, n, low_ptr);
+}
+
+void l2_mirror_fill(const int32_t *col, const int64_t *row_ptr, int n, const int64_t *low_ptr, int64_t *dst,
+                    int64_t *src, int32_t *mcol, int *missing, cudaStream_t s) {
+    if (n <= 0) return;
+    l2_mirror_fill_kernel<<<(n + 255) / 256, 256, 0, s>>>(col, row_ptr, n, low_ptr, dst, src, mcol, missing);
 }
 
 int g_pair_values(const Grouped<PVTask> &g, int W, int dfloat, cudaStream_t s) {

@@ -59,7 +59,8 @@ class hb_stats(C.Structure):
                 ("expand_launches", C.c_int32), ("kernel_launches", C.c_int32), ("expand_flops", C.c_double),
                 ("iterations", C.c_int32), ("mlp_fallbacks", C.c_int32), ("max_residual", C.c_double),
                 ("ms_matvec", C.c_float), ("ms_rr", C.c_float), ("expand_tensor_flops", C.c_double),
-                ("ms_gram", C.c_float), ("ms_combine", C.c_float), ("reserved", C.c_int32 * 4)]
+                ("ms_gram", C.c_float), ("ms_combine", C.c_float), ("ms_class4_kernel", C.c_float),
+                ("reserved", C.c_int32 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
