@@ -166,6 +166,36 @@ def test_build_fp64_medium_sampled():
     H.close()
 
 
+@pytest.mark.parametrize("key,precision", [("mid", 0), ("mid", 1), ("c1", 1)])
+def test_l2_block_every_entry_written(key, precision):
+    """Classes 2 and 8 evaluate the upper triangle of the symmetric L2 x L2
+    block and copy each lower entry from its mirror.  With the output filled
+    with NaN and -1 beforehand, every entry is written, the block is exactly
+    symmetric, and it matches the oracle's CSR."""
+    import scipy.sparse as sp
+    from paper_1709_03005_gb300 import hb
+    P = synth.make_config(key)
+    o = coracle.Oracle(P)
+    rp, cols, vals = o.l2_csr()
+    H = hb.Hamiltonian(P)
+    b = H.allocate()
+    b["val"].fill_(float("nan"))
+    b["col"].fill_(-1)
+    H.build(precision, blocks=b)
+    n = P.n_l2
+    g_rp = b["row_ptr"].cpu().numpy()
+    g_col = b["col"][: rp[-1]].cpu().numpy()
+    g_val = b["val"][: rp[-1]].cpu().numpy()
+    np.testing.assert_array_equal(g_rp, rp)
+    np.testing.assert_array_equal(g_col, cols)
+    assert np.isfinite(g_val).all()
+    A = sp.csr_matrix((g_val, g_col, g_rp), shape=(n, n))
+    assert abs(A - A.T).max() == 0.0
+    scale = np.abs(vals).max()
+    assert np.all(np.abs(g_val - vals) <= 1e-12 * np.maximum(np.abs(vals), scale))
+    H.close()
+
+
 def test_build_is_deterministic():
     import torch
     from paper_1709_03005_gb300 import hb
