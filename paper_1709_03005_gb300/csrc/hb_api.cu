@@ -76,44 +76,35 @@ static int dalloc(hb_ctx *ctx, T **p, size_t n) {
         if (_r != HB_OK) return _r;                      \
     } while (0)
 
-// The L2 x L2 block (classes 2 and 8) is symmetric: list each entry below the
-// diagonal with the position of its mirror, so that a build evaluates only the
-// upper triangle.  If some mirror were absent the lists stay unused.
+// The L2 x L2 block (classes 2 and 8) is symmetric with a full diagonal, so
+// (nnz - n) / 2 entries lie below the diagonal: list each with the position
+// of its mirror, so that a build evaluates only the upper triangle.  If some
+// mirror were absent the lists stay unused.  One allocation, one host
+// synchronisation.
 static int l2_mirror_prepare(hb_ctx *ctx, int n, int W, cudaStream_t s) {
-    int32_t *col_all = nullptr;
-    int *missing = nullptr;
-    auto done = [&](int rc) {
-        cudaFree(col_all);
-        cudaFree(missing);
-        return rc;
-    };
-    cudaError_t e = cudaMalloc((void **)&col_all, sizeof(int32_t) * (size_t)ctx->l2_nnz);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&missing, sizeof(int));
-    if (e != cudaSuccess) return done(cuda_fail(ctx, e, "cudaMalloc"));
-    int64_t *low = nullptr;
-    int rc = dalloc(ctx, &low, (size_t)n + 1);
-    if (rc != HB_OK) return done(rc);
-    e = cudaMemsetAsync(missing, 0, sizeof(int), s);
+    const int64_t below = ctx->l2_nnz - n;
+    if (below <= 0 || below % 2) return HB_OK;
+    const int64_t nl = below / 2;
+    // one allocation (each cudaMalloc costs tens of microseconds): the int64
+    // lists, then every entry's column (for this search only), the lower
+    // entries' columns and the flag
+    uint8_t *buf = nullptr;
+    const size_t n8 = (size_t)n + 1 + 2 * (size_t)nl, n4 = (size_t)ctx->l2_nnz + (size_t)nl + 1;
+    int rc = dalloc(ctx, &buf, 8 * n8 + 4 * n4);
+    if (rc != HB_OK) return rc;
+    int64_t *low = (int64_t *)buf, *dst = low + n + 1, *src = dst + nl;
+    int32_t *col_all = (int32_t *)(src + nl), *mcol = col_all + ctx->l2_nnz, *missing = mcol + nl;
+    cudaError_t e = cudaMemsetAsync(missing, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(low, 0, sizeof(int64_t), s);
     l2_struct(ctx->l2, n, W, ctx->l2_rowptr, col_all, s);
     l2_lower_counts(col_all, ctx->l2_rowptr, n, low, s);
     exclusive_scan_inplace(low, n, s);
-    int64_t nl = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, low + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    l2_mirror_fill(col_all, ctx->l2_rowptr, n, low, nl, dst, src, mcol, missing, s);
+    int32_t miss = 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&miss, missing, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return done(cuda_fail(ctx, e, "L2 mirror positions"));
-    int64_t *dst = nullptr, *src = nullptr;
-    int32_t *mcol = nullptr;
-    if ((rc = dalloc(ctx, &dst, (size_t)nl)) != HB_OK) return done(rc);
-    if ((rc = dalloc(ctx, &src, (size_t)nl)) != HB_OK) return done(rc);
-    if ((rc = dalloc(ctx, &mcol, (size_t)nl)) != HB_OK) return done(rc);
-    l2_mirror_fill(col_all, ctx->l2_rowptr, n, low, dst, src, mcol, missing, s);
-    int miss = 1;
-    e = cudaMemcpyAsync(&miss, missing, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return done(cuda_fail(ctx, e, "L2 mirror positions"));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "L2 mirror positions");
     if (!miss) {
         ctx->l2_low_ptr = low;
         ctx->l2_mdst = dst;
@@ -121,7 +112,7 @@ static int l2_mirror_prepare(hb_ctx *ctx, int n, int W, cudaStream_t s) {
         ctx->l2_mcol = mcol;
         ctx->l2_nlow = nl;
     }
-    return done(HB_OK);
+    return HB_OK;
 }
 
 static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o) {

@@ -71,12 +71,13 @@ void exclusive_scan_inplace(int64_t *x, int n, cudaStream_t s);
 // l2_struct writes the column of every entry (rows of row_ptr, ascending
 // columns); l2_lower_counts writes at low_ptr[r + 1] how many entries of row r
 // lie below the diagonal; l2_mirror_fill lists, for each such entry (in row
-// order, at low_ptr[r] + k), its position, the position of its mirror (c, r)
-// and its column c, and sets *missing if some mirror is absent.
+// order, at low_ptr[r] + k, nl in all), its position, the position of its
+// mirror (c, r) and its column c, and sets *missing if some mirror is absent
+// or the prefix does not end at nl.
 void l2_struct(const uint64_t *dets, int n, int W, const int64_t *row_ptr, int32_t *col, cudaStream_t s);
 void l2_lower_counts(const int32_t *col, const int64_t *row_ptr, int n, int64_t *low_ptr, cudaStream_t s);
-void l2_mirror_fill(const int32_t *col, const int64_t *row_ptr, int n, const int64_t *low_ptr, int64_t *dst,
-                    int64_t *src, int32_t *mcol, int *missing, cudaStream_t s);
+void l2_mirror_fill(const int32_t *col, const int64_t *row_ptr, int n, const int64_t *low_ptr, int64_t nl,
+                    int64_t *dst, int64_t *src, int32_t *mcol, int *missing, cudaStream_t s);
 
 // K5 Slater-Condon (k_slater.cu)
 void build_jk(const Ints &I, double *jk, cudaStream_t s);

@@ -306,25 +306,37 @@ __global__ void l2_lower_counts_kernel(const int32_t *__restrict__ col, const in
     low_ptr[r + 1] = lower_bound_col(col, row_ptr[r], row_ptr[r + 1], r) - row_ptr[r];
 }
 
+// One thread per entry below the diagonal (nl of them, in row order): its row
+// by binary search over the prefix, then its mirror by binary search in the
+// row of its column.
 __global__ void l2_mirror_fill_kernel(const int32_t *__restrict__ col, const int64_t *__restrict__ row_ptr, int n,
-                                      const int64_t *__restrict__ low_ptr, int64_t *__restrict__ dst,
+                                      const int64_t *__restrict__ low_ptr, int64_t nl, int64_t *__restrict__ dst,
                                       int64_t *__restrict__ src, int32_t *__restrict__ mcol, int *missing) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const int64_t q0 = low_ptr[r], nl = low_ptr[r + 1] - q0;
-    for (int64_t k = 0; k < nl; ++k) {
-        const int64_t at = row_ptr[r] + k;
-        const int c = col[at];
-        const int64_t e = row_ptr[c + 1];
-        int64_t m = lower_bound_col(col, row_ptr[c], e, r);
-        if (m >= e || col[m] != r) {
-            atomicExch(missing, 1);
-            m = at;
-        }
-        dst[q0 + k] = at;
-        src[q0 + k] = m;
-        mcol[q0 + k] = c;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q == 0 && low_ptr[n] != nl) atomicExch(missing, 1);
+    if (q >= nl) return;
+    if (q >= low_ptr[n]) {
+        atomicExch(missing, 1);
+        return;
     }
+    int lo = 0, hi = n;      // the last row r with low_ptr[r] <= q
+    while (hi - lo > 1) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if (low_ptr[mid] <= q) lo = mid;
+        else hi = mid;
+    }
+    const int r = lo;
+    const int64_t at = row_ptr[r] + (q - low_ptr[r]);
+    const int c = col[at];
+    const int64_t e = row_ptr[c + 1];
+    int64_t m = lower_bound_col(col, row_ptr[c], e, r);
+    if (m >= e || col[m] != r) {
+        atomicExch(missing, 1);
+        m = at;
+    }
+    dst[q] = at;
+    src[q] = m;
+    mcol[q] = c;
 }
 
 // <A[row]|H|B[col]> for classified pairs (mode 0 records).  FP64: val as
@@ -447,10 +459,11 @@ void l2_lower_counts(const int32_t *col, const int64_t *row_ptr, int n, int64_t 
     l2_lower_counts_kernel<<<(n + 255) / 256, 256, 0, s>>>(col, row_ptr, n, low_ptr);
 }
 
-void l2_mirror_fill(const int32_t *col, const int64_t *row_ptr, int n, const int64_t *low_ptr, int64_t *dst,
-                    int64_t *src, int32_t *mcol, int *missing, cudaStream_t s) {
+void l2_mirror_fill(const int32_t *col, const int64_t *row_ptr, int n, const int64_t *low_ptr, int64_t nl,
+                    int64_t *dst, int64_t *src, int32_t *mcol, int *missing, cudaStream_t s) {
     if (n <= 0) return;
-    l2_mirror_fill_kernel<<<(n + 255) / 256, 256, 0, s>>>(col, row_ptr, n, low_ptr, dst, src, mcol, missing);
+    const int64_t blocks = nl > 0 ? (nl + 255) / 256 : 1;
+    l2_mirror_fill_kernel<<<(unsigned)blocks, 256, 0, s>>>(col, row_ptr, n, low_ptr, nl, dst, src, mcol, missing);
 }
 
 int g_pair_values(const Grouped<PVTask> &g, int W, int dfloat, cudaStream_t s) {
