@@ -267,3 +267,24 @@ def test_tl2_classification_record():
                 tgt_h = [(so // n) * 64 * W + so % n for so in holes]
                 assert list(out[1:1 + len(holes)]) == tgt_h
         assert cnt > 0
+
+
+@pytest.mark.parametrize("key", ["c1", "mid"])
+def test_l2_block_is_symmetric(key):
+    """Classes 2 and 8 (Section 2.2): the oracle evaluates every L2 x L2 entry
+    from its own pair, and the block comes out symmetric, pattern exactly and
+    values to rounding, with every diagonal entry present.  The GPU build
+    evaluates the upper triangle and copies each lower entry from its mirror on
+    the strength of this (nnz - n entries off the diagonal, half below it)."""
+    import scipy.sparse as sp
+    P = synth.make_config(key)
+    rp, cols, vals = coracle.Oracle(P).l2_csr()
+    n = P.n_l2
+    for r in range(n):
+        row = cols[rp[r]:rp[r + 1]]
+        assert np.all(np.diff(row) > 0) and r in row
+    assert (rp[-1] - n) % 2 == 0
+    A = sp.csr_matrix((vals, cols, rp), shape=(n, n))
+    S = sp.csr_matrix((np.ones_like(vals), cols, rp), shape=(n, n))
+    assert (S != S.T).nnz == 0
+    assert abs(A - A.T).max() <= 1e-14 * np.abs(vals).max()
