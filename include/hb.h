@@ -39,7 +39,8 @@
  *                      this is the lower-triangle block of the matrix
  *   CSR  row_ptr[n_l2+1] (int64), col[nnz] (int32), val[nnz] (double):
  *                      classes 2 and 8, the full symmetric L2 x L2 block with
- *                      one entry per pair within a double excitation
+ *                      one entry per pair within a double excitation (each
+ *                      entry below the diagonal is a copy of its mirror)
  *   Dc = contracted dimension, dim = Dc + n_l2.
  *
  * Errors: every call returns an int status (HB_OK = 0); no exception crosses
@@ -176,8 +177,10 @@ typedef struct {
 } hb_pair;
 
 /* Validate and copy a problem (Eq. 1-2), stage it on the current device and
-   build the continuum-continuum integral panels.  Allocates the device memory
-   the context needs (reported by hb_query).  Errors: HB_ERR_INVALID_ARG for
+   build the continuum-continuum integral panels.  Also finds the sparsity
+   pattern of every class and, for the L2 x L2 block, the position of each
+   entry's mirror.  Allocates the device memory the context needs (reported
+   by hb_query).  Errors: HB_ERR_INVALID_ARG for
    inconsistent input (electron counts, spins, duplicate determinants, ranges,
    non-finite integrals, orbital counts beyond 16-bit labels), HB_ERR_OOM,
    HB_ERR_CUDA, HB_ERR_UNSUPPORTED (n_words > 4). */
