@@ -39,3 +39,37 @@ def test_binding_fails_loudly_without_library(tmp_path):
             hb.load(str(tmp_path / "missing.so"))
     finally:
         hb._lib = saved
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every structure the binding mirrors has the header's size and field
+    offsets (a C program built with the host compiler prints them)."""
+    import shutil
+    import subprocess
+    import pytest
+    from paper_1709_03005_gb300 import hb
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = [hb.hb_group, hb.hb_problem, hb.hb_options, hb.hb_layout, hb.hb_blocks, hb.hb_stats,
+               hb.hb_mlp_weights]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hb.h"', "int main(void) {"]
+    for S in structs:
+        name = S.__name__
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in S._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, key, value = line.split()
+        got[(name, key)] = int(value)
+    for S in structs:
+        name = S.__name__
+        assert got[(name, "size")] == ctypes.sizeof(S), name
+        for field, _ in S._fields_:
+            assert got[(name, field)] == getattr(S, field).offset, (name, field)
