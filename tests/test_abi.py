@@ -42,8 +42,9 @@ def test_binding_fails_loudly_without_library(tmp_path):
 
 
 def test_struct_layouts_match_the_binding(tmp_path):
-    """Every structure the binding mirrors has the header's size and field
-    offsets (a C program built with the host compiler prints them)."""
+    """Every structure the binding mirrors (ctypes structures and the numpy
+    record of hb_pair) has the header's size and field offsets (a C program
+    built with the host compiler prints them)."""
     import shutil
     import subprocess
     import pytest
@@ -59,6 +60,10 @@ def test_struct_layouts_match_the_binding(tmp_path):
         lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
         for field, _ in S._fields_:
             lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    pair = hb.PAIR_DTYPE
+    lines.append('    printf("hb_pair size %zu\\n", sizeof(hb_pair));')
+    for field in pair.names:
+        lines.append(f'    printf("hb_pair {field} %zu\\n", offsetof(hb_pair, {field}));')
     lines += ["    return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines) + "\n")
@@ -73,3 +78,7 @@ def test_struct_layouts_match_the_binding(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(S), name
         for field, _ in S._fields_:
             assert got[(name, field)] == getattr(S, field).offset, (name, field)
+    # the classification records, read as a numpy structured array
+    assert got[("hb_pair", "size")] == pair.itemsize
+    for field in pair.names:
+        assert got[("hb_pair", field)] == pair.fields[field][1], field
