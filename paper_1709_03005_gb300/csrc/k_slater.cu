@@ -328,11 +328,16 @@ __global__ void l2_mirror_fill_kernel(const int32_t *__restrict__ col, const int
     const int r = lo;
     const int64_t at = row_ptr[r] + (q - low_ptr[r]);
     const int c = col[at];
-    const int64_t e = row_ptr[c + 1];
-    int64_t m = lower_bound_col(col, row_ptr[c], e, r);
-    if (m >= e || col[m] != r) {
-        atomicExch(missing, 1);
-        m = at;
+    int64_t m = at;
+    if (c < 0 || c >= r) {
+        atomicExch(missing, 1);          // not below the diagonal: the lists stay unused
+    } else {
+        const int64_t e = row_ptr[c + 1];
+        m = lower_bound_col(col, row_ptr[c], e, r);
+        if (m >= e || col[m] != r) {
+            atomicExch(missing, 1);
+            m = at;
+        }
     }
     dst[q] = at;
     src[q] = m;
