@@ -122,7 +122,8 @@ struct Plan {
     int *err = nullptr;
     // classes 4, 2 and 8 run on a second stream beside the target side and
     // the expansion (they read only staged data and write their own blocks);
-    // the target side and the expansion, the longer chain, at higher priority
+    // the target side and the expansion at higher priority, the second stream
+    // taking the SMs they leave
     cudaStream_t main = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, join_main = nullptr;
     // the target side's independent chains: the diagonal H^N values and the
