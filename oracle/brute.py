@@ -70,3 +70,84 @@ def contracted_hamiltonian(problem, return_parts=False):
     if return_parts:
         return Ht, H, T, dets
     return Ht
+
+
+def _is_target_only(label, n_to):
+    """Labels with no continuum index (and the constant e_core)."""
+    return label[0] == "core" or all(i < n_to for i in label[1:])
+
+
+def symbolic_blocks(problem):
+    """Values and condition scales of every element of the contracted matrix,
+    from the operator definition resolved by integral (fock.apply_hamiltonian_terms).
+
+    For a continuum-continuum element (Eq. 7 after Eq. 8) the symbolic
+    coefficient of label b is D^b = sum_{m m'} c_mn c_m'n' C^b(m j, m' j');
+    the value is sum_b D^b X(b) and the condition scale is
+        |sum_{b without continuum index} D^b X(b)| + sum_{other b} |D^b X(b)|
+    (the labels without a continuum index, and e_core, form one term because a
+    prototype holds them as one number that does not depend on j).  For a
+    class-4 element (Eq. 5) the scale is sum_m sum_b |c_mn C^b(m j, l) X(b)|,
+    for an L2-L2 element sum_b |C^b X(b)|: the sums of the magnitudes of the
+    terms any evaluation order adds.  Returns (value, scale), both dim x dim.
+    Tiny problems only."""
+    P = problem
+    n_orb, W, sc, nt = P.n_orb, P.n_words, P.cont_spin, P.n_to
+    eri = P.full_eri()
+
+    def X(label):
+        return fock.label_value(label, P.h, eri, P.e_core)
+
+    rows = []          # (kind, payload) per basis function in the contracted order
+    for gi, g in enumerate(P.groups):
+        for n in range(g.ci.shape[1]):
+            for jj in range(g.cont_count):
+                rows.append(("c", gi, n, g.cont_first + jj))
+    for l in range(P.n_l2):
+        rows.append(("l", l))
+    dim = len(rows)
+
+    def det_cj(g, m, j):
+        return fock.words_to_tuple(g.dets[m], W, n_orb, extra=[(sc, nt + j)])
+
+    terms = {}
+
+    def terms_of(ket):
+        if ket not in terms:
+            terms[ket] = fock.apply_hamiltonian_terms(ket, n_orb, P.e_core)
+        return terms[ket]
+
+    V = np.zeros((dim, dim))
+    S = np.zeros((dim, dim))
+    for a, ra in enumerate(rows):
+        for b, rb in enumerate(rows):
+            if ra[0] == "c" and rb[0] == "c":
+                g, gp = P.groups[ra[1]], P.groups[rb[1]]
+                n, j, n_, jp = ra[2], ra[3], rb[2], rb[3]
+                D = {}
+                for mp in range(gp.dets.shape[0]):
+                    tk = terms_of(det_cj(gp, mp, jp))
+                    for m in range(g.dets.shape[0]):
+                        for lab, c in tk.get(det_cj(g, m, j), {}).items():
+                            D[lab] = D.get(lab, 0.0) + g.ci[m, n] * gp.ci[mp, n_] * c
+                tgt = sum(d * X(lab) for lab, d in D.items() if _is_target_only(lab, nt))
+                oth = [d * X(lab) for lab, d in D.items() if not _is_target_only(lab, nt)]
+                V[a, b] = tgt + sum(oth)
+                S[a, b] = abs(tgt) + sum(abs(x) for x in oth)
+            elif ra[0] == "l" and rb[0] == "l":
+                tk = terms_of(fock.words_to_tuple(P.l2_dets[rb[1]], W, n_orb))
+                t = tk.get(fock.words_to_tuple(P.l2_dets[ra[1]], W, n_orb), {})
+                V[a, b] = sum(c * X(lab) for lab, c in t.items())
+                S[a, b] = sum(abs(c * X(lab)) for lab, c in t.items())
+            else:
+                (cr, lr) = (ra, rb) if ra[0] == "c" else (rb, ra)
+                g, n, j = P.groups[cr[1]], cr[2], cr[3]
+                tk = terms_of(fock.words_to_tuple(P.l2_dets[lr[1]], W, n_orb))
+                v = s = 0.0
+                for m in range(g.dets.shape[0]):
+                    for lab, c in tk.get(det_cj(g, m, j), {}).items():
+                        x = g.ci[m, n] * c * X(lab)
+                        v += x
+                        s += abs(x)
+                V[a, b], S[a, b] = v, s
+    return V, S

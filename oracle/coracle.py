@@ -73,6 +73,10 @@ def load():
         lib.orc_cc_expand_abs.argtypes = [vp, vp, i64, i64, i64]
         lib.orc_cc_expand_rows.argtypes = [vp, vp, C.c_int, C.c_int]
         lib.orc_class4_rows.argtypes = [vp, C.c_int, C.c_int, vp]
+        lib.orc_class4_rows_abs.argtypes = [vp, C.c_int, C.c_int, vp]
+        lib.orc_l2_rows_abs.argtypes = [vp, C.c_int, C.c_int, vp]
+        lib.orc_l2_element_abs.restype = dbl
+        lib.orc_l2_element_abs.argtypes = [vp, C.c_int, C.c_int]
         _lib = lib
     return _lib
 
@@ -168,6 +172,32 @@ class Oracle:
         out = np.zeros((max(l1 - l0, 1), max(self.Dc, 1)))
         self.lib.orc_class4_rows(self.sp, int(l0), int(l1), _ptr(out))
         return out[: l1 - l0, : self.Dc]
+
+    def class4_rows_abs(self, l0, l1) -> np.ndarray:
+        """Condition scales of the class-4 rows [l0, l1): sum of the magnitudes
+        of the Eq. 5 terms of every element."""
+        out = np.zeros((max(l1 - l0, 1), max(self.Dc, 1)))
+        self.lib.orc_class4_rows_abs(self.sp, int(l0), int(l1), _ptr(out))
+        return out[: l1 - l0, : self.Dc]
+
+    def l2_rows_abs(self, a0, a1) -> np.ndarray:
+        """Condition scales of the L2 x L2 rows [a0, a1)."""
+        out = np.zeros((max(a1 - a0, 1), max(self.problem.n_l2, 1)))
+        self.lib.orc_l2_rows_abs(self.sp, int(a0), int(a1), _ptr(out))
+        return out[: a1 - a0, : self.problem.n_l2]
+
+    def condition(self) -> np.ndarray:
+        """dim x dim condition scales of every element (continuum block from
+        cc_condition, class 4 and L2 rows from their own sums), symmetric."""
+        S = np.zeros((self.dim, self.dim))
+        Dc = self.Dc
+        S[:Dc, :Dc] = self.cc_condition()
+        if self.problem.n_l2:
+            c4 = self.class4_rows_abs(0, self.problem.n_l2)
+            S[Dc:, :Dc] = c4
+            S[:Dc, Dc:] = c4.T
+            S[Dc:, Dc:] = self.l2_rows_abs(0, self.problem.n_l2)
+        return S
 
     def cc_condition(self) -> np.ndarray:
         """Dc x Dc matrix of sum_b |D^b X(I^b)| for every continuum element."""

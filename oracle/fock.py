@@ -115,3 +115,61 @@ def words_to_tuple(words, W: int, n_orb: int, extra=()) -> tuple:
     if len(set(occ)) != len(occ):
         raise ValueError("doubly occupied spin orbital")
     return tuple(occ)
+
+
+def canonical_label(p: int, q: int, r: int | None = None, s: int | None = None) -> tuple:
+    """Canonical name of an integral under its permutational symmetry.
+
+    One-electron h_pq (real, symmetric): ('h', max, min).  Two-electron (pq|rs)
+    (real orbitals, 8-fold symmetric): ('g', P, Q) with P = (max(p,q), min(p,q)),
+    Q likewise for (r, s), and P >= Q.  Two index tuples name the same integral
+    exactly when their canonical labels are equal."""
+    if r is None:
+        return ("h", max(p, q), min(p, q))
+    a, b = (max(p, q), min(p, q)), (max(r, s), min(r, s))
+    return ("g",) + (a + b if a >= b else b + a)
+
+
+def apply_hamiltonian_terms(det: tuple, n_orb: int, e_core: float = 0.0) -> dict:
+    """H|det> resolved by integral: {det': {label: coefficient}}.
+
+    The same operator walk as apply_hamiltonian, but every contribution is
+    filed under the canonical label of the integral it multiplies (the
+    constant e_core under ('core',)), so <det'|H|det> = sum over labels of
+    coefficient * integral.  This is the symbolic form of a matrix element
+    (the paper's Eq. 6, C^a X(I^a)) reached by the definition of the
+    operators, with no Slater-Condon case analysis."""
+    out = defaultdict(lambda: defaultdict(float))
+    if e_core:
+        out[det][("core",)] += 1.0
+    for Q in det:
+        s, q = divmod(Q, n_orb)
+        sq, d1 = annihilate(det, Q)
+        for p in range(n_orb):
+            sp, d2 = create(d1, s * n_orb + p)
+            if sp:
+                out[d2][canonical_label(p, q)] += sq * sp
+    for Q in det:
+        s, q = divmod(Q, n_orb)
+        sq, d1 = annihilate(det, Q)
+        for S in d1:
+            t, ss = divmod(S, n_orb)
+            s_s, d2 = annihilate(d1, S)
+            for r in range(n_orb):
+                sr, d3 = create(d2, t * n_orb + r)
+                if not sr:
+                    continue
+                for p in range(n_orb):
+                    sp, d4 = create(d3, s * n_orb + p)
+                    if sp:
+                        out[d4][canonical_label(p, q, r, ss)] += 0.5 * sq * s_s * sr * sp
+    return out
+
+
+def label_value(label: tuple, h: np.ndarray, eri: np.ndarray, e_core: float = 0.0) -> float:
+    """The integral a canonical label names."""
+    if label[0] == "core":
+        return e_core
+    if label[0] == "h":
+        return h[label[1], label[2]]
+    return eri[label[1], label[2], label[3], label[4]]

@@ -785,3 +785,68 @@ void orc_cc_expand_rows(const orc_cc *c, double *out, int jj0, int jj1) {
     free(ks);
     free(kd);
 }
+
+/* Condition scale of the class-4 row l (Eq. 5 with absolute values): for
+   every contracted column (g, n, j), sum over the target determinants m and
+   the labels of their prototype against chi_l of |c_mn C X(I)|, the sum of
+   the magnitudes of the terms that any evaluation order adds. */
+void orc_class4_row_abs(const orc_problem *P, int l, double *out) {
+    const int W = P->W, We = ext_words(P), ph = P->n_to, sc = P->cont_spin;
+    const uint64_t *chi = P->l2 + (int64_t)l * 2 * W;
+    uint64_t I[2 * ORC_MAXW], J[2 * ORC_MAXW];
+    orc_sym buf[4096];
+    int64_t off = 0;
+    extend(P, chi, -1, 0, J);
+    for (int g = 0; g < P->n_groups; ++g) {
+        const int ns = P->g_nstate[g], cf = P->g_cfirst[g], cn = P->g_ccount[g];
+        const uint64_t *Dg = P->g_dets[g];
+        const double *Cg = P->g_ci[g];
+        for (int64_t t = 0; t < (int64_t)ns * cn; ++t) out[off + t] = 0.0;
+        for (int m = 0; m < P->g_ndet[g]; ++m) {
+            const uint64_t *Dm = Dg + (int64_t)m * 2 * W;
+            int d = 0;
+            for (int w = 0; w < 2 * W; ++w) d += popc64(Dm[w] & ~chi[w]);
+            if (d > 1) continue;
+            extend(P, Dm, ph, sc, I);
+            int n = orc_symbols(We, I, J, buf, 4096);
+            for (int jj = 0; jj < cn; ++jj) {
+                const int jg = P->n_to + cf + jj;
+                double s = 0.0;
+                for (int k = 0; k < n; ++k) s += fabs(buf[k].coef * orc_X(P, buf[k].label, ph, jg, -1, 0));
+                for (int a = 0; a < ns; ++a) out[off + (int64_t)a * cn + jj] += fabs(Cg[(int64_t)m * ns + a]) * s;
+            }
+        }
+        off += (int64_t)ns * cn;
+    }
+}
+
+/* Condition scale of an L2-L2 element: sum of |C X(I)| over its symbols
+   (plus |e_core| on the diagonal). */
+double orc_l2_element_abs(const orc_problem *P, int a, int b) {
+    const int W = P->W;
+    orc_sym buf[4096];
+    int n = orc_symbols(W, P->l2 + (int64_t)a * 2 * W, P->l2 + (int64_t)b * 2 * W, buf, 4096);
+    double v = 0.0;
+    for (int k = 0; k < n && k < 4096; ++k) v += fabs(buf[k].coef * orc_X(P, buf[k].label, -1, 0, -1, 0));
+    if (a == b) v += fabs(P->e_core);
+    return v;
+}
+
+/* Condition scales of the dense rows [a0, a1) of the L2 x L2 block. */
+void orc_l2_rows_abs(const orc_problem *P, int a0, int a1, double *out) {
+    const int nl = P->n_l2, W = P->W;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int a = a0; a < a1; ++a)
+        for (int b = 0; b < nl; ++b) {
+            int nd = 0;
+            for (int w = 0; w < 2 * W; ++w) nd += popc64(P->l2[(int64_t)a * 2 * W + w] ^ P->l2[(int64_t)b * 2 * W + w]);
+            out[(int64_t)(a - a0) * nl + b] = nd <= 4 ? orc_l2_element_abs(P, a, b) : 0.0;
+        }
+}
+
+/* Class-4 condition rows [l0, l1) into out[(l - l0) * Dc + c]. */
+void orc_class4_rows_abs(const orc_problem *P, int l0, int l1, double *out) {
+    const int64_t Dc = orc_contracted_dim(P);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int l = l0; l < l1; ++l) orc_class4_row_abs(P, l, out + (int64_t)(l - l0) * Dc);
+}

@@ -87,7 +87,7 @@ class Problem:
 
     def full_eri(self) -> np.ndarray:
         """Full (pq|rs) tensor over all orbitals from the Cholesky factor (small only)."""
-        assert self.chol is not None and self.n_orb <= 40
+        assert self.chol is not None and self.n_orb <= 80
         n = self.n_orb
         P = np.zeros((n, n, self.chol.shape[1]))
         for p in range(n):
@@ -208,7 +208,7 @@ def orthonormal_ci(rng, n_det, n_state):
 
 def make_problem(name, seed, n_to, n_co, n_elec, n_det, n_state, n_l2, rank,
                  cont_diag=(-3.0, -0.5), n_words=None, cont_spin=ALPHA,
-                 n_groups=1, cont_ranges=None, keep_chol=None):
+                 n_groups=1, cont_ranges=None, keep_chol=None, e_core=0.0):
     """Single-spin-coupling problem: all groups share Ms and the continuum spin.
 
     cont_spin=ALPHA: targets have Ms=0 (N/2 alpha, N/2 beta), continuum alpha.
@@ -249,7 +249,7 @@ def make_problem(name, seed, n_to, n_co, n_elec, n_det, n_state, n_l2, rank,
     return Problem(name=name, n_to=n_to, n_co=n_co, n_elec=n_elec, n_words=W,
                    cont_spin=cont_spin, h=h, eri_tttt=eri[0], eri_tttc=eri[1],
                    eri_ttcc=eri[2], eri_tctc=eri[3], groups=groups,
-                   l2_dets=np.ascontiguousarray(l2), chol=L if keep else None,
+                   l2_dets=np.ascontiguousarray(l2), e_core=float(e_core), chol=L if keep else None,
                    meta=dict(seed=seed, rank=rank))
 
 
@@ -280,11 +280,11 @@ def make_config(key: str, **overrides) -> Problem:
 
 
 def make_tiny(seed, n_to=5, n_co=3, n_elec=4, n_det=6, n_state=2, n_l2=5, rank=6,
-              n_groups=1, cont_spin=ALPHA, cont_ranges=None, n_words=None):
+              n_groups=1, cont_spin=ALPHA, cont_ranges=None, n_words=None, e_core=0.0):
     """Tiny random problems for brute-force pinning (all integrals kept)."""
     return make_problem(f"tiny{seed}", seed, n_to, n_co, n_elec, n_det, n_state, n_l2,
                         rank, n_words=n_words, cont_spin=cont_spin, n_groups=n_groups,
-                        cont_ranges=cont_ranges, keep_chol=True)
+                        cont_ranges=cont_ranges, keep_chol=True, e_core=e_core)
 
 
 def random_det_pairs(rng, n_orb, n_alpha, n_beta, W, count, max_exc=3, orbitals=None):

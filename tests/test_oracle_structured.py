@@ -86,6 +86,7 @@ CASES = [
     dict(n_to=6, n_co=4, n_elec=6, n_det=10, n_state=4, n_l2=9),
     dict(n_l2=0),
     dict(n_groups=2, n_co=4, n_det=5, n_state=[2, 2], cont_ranges=[(0, 2), (2, 2)], n_l2=3),
+    dict(n_groups=2, n_state=[2, 2], cont_ranges=[(0, 3), (0, 2)], e_core=-4.75),
 ]
 
 
