@@ -1,16 +1,19 @@
 """Benchmark of the Hamiltonian build (and Davidson) on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config c2] [--precision mixed|fp64]
+                    [--config c3] [--precision mixed|fp64] [--fp64-steps 3]
+                    [--davidson-k 20] [--davidson-config c2]
 
-One step is one build of every class of the close-coupling Hamiltonian
-(hb_build_blocks) for the medium workload (30 target + 150 continuum orbitals,
-N = 10 + 1 electrons, 2000 target determinants, 20 target states, 5000 L2
-functions, dimension 8000), with the integrals already resident on the device.
-The metric is H elements per second: dim(dim+1)/2 lower-triangle positions per
-build (the positions the paper's whole-matrix timings cover).  Davidson (lowest
-20 eigenpairs to a residual of 1e-8) is timed after the build steps and
-reported under "davidson".
+One step is one mixed-precision build of every class of the close-coupling
+Hamiltonian (hb_build_blocks) for the precision workload (40 target + 400
+continuum orbitals, N = 14 + 1 electrons, 20000 target determinants, 50 target
+states, 30000 L2 functions, dimension 50000), with the integrals already
+resident on the device.  The metric is H elements per second: dim(dim+1)/2
+lower-triangle positions per build (the positions the paper's whole-matrix
+timings cover).  The plain FP64 GPU build of the same instance is timed after
+the steps ("fp64", "speedup_vs_fp64").  Davidson (lowest 20 eigenpairs of the
+medium workload, dimension 8000, to a residual of 1e-8) is timed after that,
+on the GPU and with the CPU baseline (numpy block Davidson), under "davidson".
 
 Prints one JSON line (rank 0).  Under torchrun every rank builds its own
 replica (independent problem, no data-path collective) and the time is the
@@ -151,49 +154,76 @@ def fp64_alu_peak_tflops():
 
 def cpu_baseline(problem, budget_s=20.0):
     """Time the oracle (as it stands) on this host's cores on the same workload,
-    or on a bounded sample of it: every group-pair contraction, then the
-    expansion of as many continuum rows, class-4 rows and L2 rows as fit the
-    budget; the value is the positions covered per second."""
+    or on a bounded sample of it.  Every group-pair contraction (Eq. 8) runs in
+    full; then each of the three expansion stages (continuum rows of Eq. 7,
+    class-4 rows of Eq. 5, L2 rows) runs on leading rows until its share of the
+    budget is spent.  A stage that did not finish is extrapolated to all of its
+    rows at the rate measured, so the value is the whole workload's positions
+    over the whole workload's estimated oracle time (contraction included)."""
     from oracle import coracle
     o = coracle.Oracle(problem)
-    t0 = time.perf_counter()
-    covered = 0.0
     gs = problem.groups
-    full = True
+    share = budget_s / 3.0
+    t_contract = t_cc = 0.0
+    cc_done = cc_all = 0.0
+    npairs = len(gs) * (len(gs) + 1) // 2
     for g in range(len(gs)):
         for gp in range(g + 1):
-            cc = o.contract(g, gp)
+            t0 = time.perf_counter()
+            cc = o.contract(g, gp, cond=False)
+            t_contract += time.perf_counter() - t0
             cn = gs[g].cont_count
             per_row = gs[g].ci.shape[1] * gs[gp].ci.shape[1] * gs[gp].cont_count
-            step = max(1, cn // 8)
+            cc_all += cn * per_row
+            step = max(1, cn // 16)
             for jj0 in range(0, cn, step):
-                jj1 = min(cn, jj0 + step)
-                cc.expand_rows(jj0, jj1)
-                covered += (jj1 - jj0) * per_row / (2.0 if g == gp else 1.0)
-                if time.perf_counter() - t0 > budget_s:
-                    full = False
+                if t_cc > share * (g * (g + 1) // 2 + gp + 1) / npairs:
                     break
+                jj1 = min(cn, jj0 + step)
+                t0 = time.perf_counter()
+                cc.expand_rows(jj0, jj1)
+                t_cc += time.perf_counter() - t0
+                cc_done += (jj1 - jj0) * per_row
             del cc
-            if not full:
-                break
-        if not full:
-            break
+    stages = [("contraction", t_contract, 1.0)]
+    stages.append(("expansion", t_cc, cc_done / max(cc_all, 1.0)))
     nl = problem.n_l2
-    if nl:
-        rows = nl if full else max(1, nl // 100)
-        o.class4_rows(0, rows)
-        covered += rows * o.Dc
-        if full:
-            o.l2_csr()
-            covered += positions(nl)
-        else:
-            o.l2_rows(0, rows)
-            covered += rows * nl / 2.0
-    dt = time.perf_counter() - t0
+    for name, fn in (("class 4", o.class4_rows), ("L2", o.l2_rows)):
+        if not nl:
+            break
+        t, done, step = 0.0, 0, 64
+        while done < nl and t < share:
+            n = min(step, nl - done)
+            t0 = time.perf_counter()
+            fn(done, done + n)
+            t += time.perf_counter() - t0
+            done += n
+            step *= 2
+        stages.append((name, t, done / nl))
+    est = stages[0][1] + sum(t / f for _, t, f in stages[1:] if f > 0)
+    measured = sum(t for _, t, _ in stages)
+    full = all(f >= 1.0 for _, _, f in stages)
+    detail = ", ".join(f"{n} {100 * f:.1f} % in {t:.2f} s" for n, t, f in stages[1:])
     what = "whole workload: every block once" if full else \
-        "bounded sample: every contraction, the leading continuum rows, 1 % of the class-4 and L2 rows"
-    return {"value": covered / dt, "unit": "H elements/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{what} of {problem.name} ({covered:.3e} positions, {dt:.2f} s)"}
+        f"bounded sample of {problem.name}: every contraction ({t_contract:.2f} s), then {detail}; unfinished " \
+        f"stages extrapolated at their measured rate to {est:.1f} s for the whole workload"
+    return {"value": positions(problem.dim) / est, "unit": "H elements/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{what} ({measured:.1f} s measured)"}
+
+
+def cpu_davidson(problem, k, tol=1e-8):
+    """CPU baseline of the Davidson step: the oracle's plain numpy block
+    Davidson (FP64, OpenBLAS on all host cores) on the oracle's dense matrix
+    of the same instance; the dense build itself is not timed."""
+    from oracle import coracle, eig
+    H = coracle.Oracle(problem).dense()
+    d = np.ascontiguousarray(np.diag(H))
+    t0 = time.perf_counter()
+    w, X, it = eig.davidson(lambda V: H @ V, d, k, tol=tol, max_iter=400)
+    dt = time.perf_counter() - t0
+    res = float(np.linalg.norm(H @ X - X * w, axis=0).max())
+    return {"seconds": dt, "iterations": it, "max_residual": res, "cores": os.cpu_count(),
+            "kind": "oracle (numpy block Davidson, FP64)", "evals": w}
 
 
 def replica_throughput(local_ms, steps, dim, world, device):
@@ -215,12 +245,15 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     P = synth.make_config(args.config, **overrides(args))
+    # each step is a bounded sample sized so that warm-up and steps together
+    # take a few minutes
+    budget = min(20.0, max(1.5, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_baseline(P)
+        cpu_baseline(P, budget)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(P))
+        vals.append(cpu_baseline(P, budget))
     dt = time.perf_counter() - t0
     v = float(np.mean([x["value"] for x in vals]))
     cb = dict(vals[-1])
@@ -242,46 +275,68 @@ def run_ours(args, rank, world, local_rank):
     precision = hb.HB_MIXED if args.precision == "mixed" else hb.HB_FP64
     P = synth.make_config(args.config, **overrides(args))
     dim = P.dim
-    H = hb.Hamiltonian(P)
+    H = hb.Hamiltonian(P, validate=False)
     blocks = H.allocate()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def timed_builds(prec, steps, clock=None):
+        times, st_list = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = H.build(prec, blocks)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            st_list.append(st)
+        return times, st_list
+
     for _ in range(args.warmup):
         H.build(precision, blocks)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    times, exp_ms, gemm_ms, launches, flops_exp = [], [], [], 0, 0.0
     with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            _, st = H.build(precision, blocks)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            exp_ms.append(st.ms_expand)
-            gemm_ms.append(st.ms_expand_gemm)
-            launches += st.kernel_launches
-            flops_exp = st.expand_flops
+        times, sts = timed_builds(precision, args.steps)
         torch.cuda.synchronize()
     total_ms, value = replica_throughput(float(np.sum(times)), args.steps, dim, world, "cuda")
+    st = sts[-1]
+    launches = sum(x.kernel_launches for x in sts)
+    gemm_ms = float(np.mean([x.ms_expand_gemm for x in sts]))
+    exp_ms = float(np.mean([x.ms_expand for x in sts]))
+
+    # the plain FP64 GPU build of the same instance, after the timed steps
+    fp64 = None
+    if precision == hb.HB_MIXED and args.fp64_steps > 0:
+        H.build(hb.HB_FP64, blocks)
+        torch.cuda.synchronize()
+        t64, s64 = timed_builds(hb.HB_FP64, args.fp64_steps)
+        ms64 = float(np.mean(t64))
+        fp64 = {"ms_per_step": ms64, "value": positions(dim) / (ms64 / 1e3), "unit": "H elements/s",
+                "steps": args.fp64_steps, "expand_kernel_ms": float(np.mean([x.ms_expand_gemm for x in s64])),
+                "stages_ms": {"target": s64[-1].ms_target, "expand": s64[-1].ms_expand,
+                              "class4": s64[-1].ms_class4, "l2": s64[-1].ms_l2}}
 
     # end to end through the public API with host buffers: staging (H2D of the
-    # problem from pinned host memory), build, and the D2H read of every block
-    # into pinned host memory, each step
+    # problem from pinned host memory, hb_init), build, and the D2H read of
+    # every block into pinned host memory, each step
     e2e_steps = max(1, min(args.steps, 3))
     Pp = pinned_problem(P)
     h2d = sum(np.asarray(a).nbytes for a in (P.h, P.eri_tttt, P.eri_tttc, P.eri_ttcc, P.eri_tctc, P.l2_dets)) + \
         sum(g.dets.nbytes + g.ci.nbytes for g in P.groups)
     host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in blocks.items()}
     d2h = sum(v.numel() * v.element_size() for v in host.values())
+    init_ms = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
+        t1 = time.perf_counter()
         H2 = hb.Hamiltonian(Pp, validate=False)
+        torch.cuda.synchronize()
+        init_ms.append(1e3 * (time.perf_counter() - t1))
         b2, _ = H2.build(precision)
         for k, v in b2.items():
             host[k].copy_(v, non_blocking=True)
@@ -290,50 +345,75 @@ def run_ours(args, rank, world, local_rank):
         del b2
     torch.cuda.synchronize()
     e2e_value = world * e2e_steps * positions(dim) / (time.perf_counter() - t0)
-
-    # Davidson after the timed build steps: block products on the tensor cores
-    # (split bf16) on the mixed path, and with FP64 products beside it
-    davidson = None
-    if args.davidson_k > 0:
-        def solve(flags):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ev, dst, ok = H.diag(blocks, args.davidson_k, 1e-8, 400, precond=hb.HB_PRECOND_DIAG | flags,
-                                 allow_not_converged=True)
-            torch.cuda.synchronize()
-            return {"seconds": time.perf_counter() - t0, "iterations": dst.iterations, "converged": ok,
-                    "max_residual": dst.max_residual, "matvec_ms": dst.ms_matvec}
-        try:
-            tensor = precision == hb.HB_MIXED
-            davidson = {"k": args.davidson_k, "tol": 1e-8,
-                        "products": "tensor cores, split bf16" if tensor else "FP64"}
-            davidson.update(solve(hb.HB_DIAG_TENSOR if tensor else 0))
-            if tensor:
-                davidson["fp64_products"] = solve(0)
-        except hb.HBError as e:
-            davidson = {"unavailable": str(e)}
+    del host
 
     peaks = measured_peaks()
-    avg_exp_ms = float(np.mean(exp_ms)) if exp_ms else None
     if precision == hb.HB_MIXED:
-        kern_ms = float(np.mean(gemm_ms)) if gemm_ms else None
+        kern_ms = gemm_ms
         tflops = st.expand_tensor_flops
-        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peaks.get("bf16_tflops"),
+        pk = peaks.get("bf16_tflops")
+        fp64eq = st.expand_flops / (kern_ms / 1e3) / 1e12 if kern_ms else None
+        pipe = tflops / (kern_ms / 1e3) / 1e12 if kern_ms else None
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": pk,
                 "peak_source": "measured bf16 burst (of measured)",
-                "kernel": "split_expand_kernel: Eq. 7 contraction as 21 bf16 slice-pair products",
-                "achieved": tflops / (kern_ms / 1e3) / 1e12 if kern_ms else None,
-                "flops_per_launch": tflops, "kernel_ms": kern_ms,
-                "fp64_equivalent_tflops": flops_exp / (kern_ms / 1e3) / 1e12 if kern_ms else None,
-                "traffic": profiled_traffic("split_expand_kernel", "paper_1709_03005_gb300/csrc/k_split.cu", None if args.set else args.config)}
+                "kernel": "split_expand_kernel: Eq. 7 contraction on bf16 tensor cores, 6 slices per operand",
+                "achieved": fp64eq, "flops_per_launch": st.expand_flops,
+                "flops_definition": "algorithmic FP64-equivalent flops 2 K (elements) of Eq. 7 per launch",
+                "kernel_ms": kern_ms,
+                "pipe_achieved": pipe, "pipe_frac": pipe / pk if pipe and pk else None,
+                "pipe_flops_per_launch": tflops,
+                "pipe_definition": "bf16 tensor flops issued: the 21 slice-pair products of every FP64-equivalent "
+                                   "product",
+                "traffic": profiled_traffic("split_expand_kernel", "paper_1709_03005_gb300/csrc/k_split.cu",
+                                            None if args.set else args.config)}
     else:
-        kern_ms = avg_exp_ms
+        kern_ms = exp_ms
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_alu_peak_tflops(),
                 "peak_source": "derived FP64 peak: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
                 "kernel": "expand_fp64_kernel: Eq. 7 contraction in FP64",
-                "achieved": flops_exp / (kern_ms / 1e3) / 1e12 if kern_ms else None,
-                "flops_per_launch": flops_exp, "kernel_ms": kern_ms,
-                "traffic": profiled_traffic("expand_fp64_kernel", "paper_1709_03005_gb300/csrc/k_expand.cu", None if args.set else args.config)}
+                "achieved": st.expand_flops / (kern_ms / 1e3) / 1e12 if kern_ms else None,
+                "flops_per_launch": st.expand_flops, "kernel_ms": kern_ms,
+                "traffic": profiled_traffic("expand_fp64_kernel", "paper_1709_03005_gb300/csrc/k_expand.cu",
+                                            None if args.set else args.config)}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] and roof["peak"] else None
+    H.close()
+    del blocks
+    torch.cuda.empty_cache()
+
+    # Davidson on the medium workload (lowest 20 eigenpairs): block products
+    # on the tensor cores (split bf16) and in FP64 on the GPU, the CPU
+    # baseline beside them
+    davidson = None
+    if args.davidson_k > 0:
+        Pd = synth.make_config(args.davidson_config)
+        Hd = hb.Hamiltonian(Pd, validate=False)
+        bd, _ = Hd.build(hb.HB_MIXED)
+        torch.cuda.synchronize()
+
+        def solve(flags):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev, dst, ok = Hd.diag(bd, args.davidson_k, 1e-8, 400, precond=hb.HB_PRECOND_DIAG | flags,
+                                  allow_not_converged=True)
+            torch.cuda.synchronize()
+            return {"seconds": time.perf_counter() - t0, "iterations": dst.iterations, "converged": ok,
+                    "max_residual": dst.max_residual, "matvec_ms": dst.ms_matvec, "rr_ms": dst.ms_rr,
+                    "gram_ms": dst.ms_gram, "combine_ms": dst.ms_combine}, ev
+        try:
+            davidson = {"workload": CONFIG_TEXT.get(args.davidson_config, args.davidson_config),
+                        "k": args.davidson_k, "tol": 1e-8}
+            davidson["tensor_products"], ev_t = solve(hb.HB_DIAG_TENSOR)
+            davidson["fp64_products"], ev_f = solve(0)
+            if rank == 0 and args.cpu_baseline:
+                cd = cpu_davidson(Pd, args.davidson_k)
+                davidson["cpu_baseline"] = {k: v for k, v in cd.items() if k != "evals"}
+                davidson["max_eval_diff_vs_cpu"] = float(np.abs(ev_t - cd["evals"]).max())
+                davidson["speedup_vs_cpu"] = cd["seconds"] / davidson["tensor_products"]["seconds"]
+        except hb.HBError as e:
+            davidson = {"unavailable": str(e)}
+        Hd.close()
+        del bd
+        torch.cuda.empty_cache()
 
     # the batched workload: 16 symmetry / spin-coupling Hamiltonians, one graph
     # launch; the plain FP64 batch is timed beside it for the speedup
@@ -385,14 +465,15 @@ def run_ours(args, rank, world, local_rank):
                "config": {"workload": workload_text(args), "dim": dim,
                           "positions": positions(dim), "l2_flush": "256 MB write between timed steps",
                           "parallelism": f"replicas x{world}", "precision": args.precision},
+               "fp64": fp64, "speedup_vs_fp64": fp64["ms_per_step"] / (total_ms / args.steps) if fp64 else None,
+               "init_ms": float(np.mean(init_ms)),
                "roofline": roof, "cpu_baseline": cb,
                "e2e": {"value": e2e_value, "unit": "H elements/s", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},
                "gpu_launches": launches, "clocks": clk.summary(), "davidson": davidson, "batched": batched,
                "stages_ms": {"target": st.ms_target, "expand": st.ms_expand, "class4": st.ms_class4,
-                             "l2": st.ms_l2}}
+                             "class4_kernel": st.ms_class4_kernel, "l2": st.ms_l2, "expand_kernel": gemm_ms}}
         print(json.dumps(out), flush=True)
-    H.close()
 
 
 def main():
@@ -401,11 +482,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="c3")
     ap.add_argument("--set", action="append", default=[], metavar="KEY=INT",
                     help="override an integer size of the workload (e.g. n_l2=4000), for small profiling cases")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--davidson-k", type=int, default=20)
+    ap.add_argument("--davidson-config", default="c2")
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     args = ap.parse_args()

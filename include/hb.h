@@ -278,9 +278,11 @@ int hb_classify(const uint64_t *a, int32_t n_a, const uint64_t *b, int32_t n_b,
    n_a > HB_NOALLOC_MAX_ROWS returns HB_ERR_INVALID_ARG.  The function calls no
    allocating routine.  Its first call on a device looks up the array's device
    address (cudaGetSymbolAddress) with that device current; make that first
-   call before any stream capture.  All calls share the array, so calls whose
-   work overlaps on the GPU race: serialise them.  Errors are reported through
-   hb_last_error(NULL). */
+   call before any stream capture.  The address is kept for the life of the
+   process: a cudaDeviceReset of that device invalidates it, and the entry
+   point must not be called on that device after such a reset.  All calls
+   share the array, so calls whose work overlaps on the GPU race: serialise
+   them.  Errors are reported through hb_last_error(NULL). */
 #define HB_NOALLOC_MAX_ROWS 262144
 int hb_classify_noalloc(const uint64_t *a, int32_t n_a, const uint64_t *b, int32_t n_b,
                         int32_t n_words, int32_t mode, int32_t cont_spin, int32_t max_degree,

@@ -86,11 +86,13 @@ def symbolic_blocks(problem):
     the value is sum_b D^b X(b) and the condition scale is
         |sum_{b without continuum index} D^b X(b)| + sum_{other b} |D^b X(b)|
     (the labels without a continuum index, and e_core, form one term because a
-    prototype holds them as one number that does not depend on j).  For a
-    class-4 element (Eq. 5) the scale is sum_m sum_b |c_mn C^b(m j, l) X(b)|,
-    for an L2-L2 element sum_b |C^b X(b)|: the sums of the magnitudes of the
-    terms any evaluation order adds.  Returns (value, scale), both dim x dim.
-    Tiny problems only."""
+    prototype holds them as one number that does not depend on j), and its full
+    scale, every term of the contraction included, is
+        sum_b |X(b)| sum_{m m'} |c_mn c_m'n' C^b(m j, m' j')|.
+    For a class-4 element (Eq. 5) both scales are
+    sum_m sum_b |c_mn C^b(m j, l) X(b)|, for an L2-L2 element sum_b |C^b X(b)|:
+    the sums of the magnitudes of the terms any evaluation order adds.
+    Returns (value, scale, full scale), each dim x dim.  Tiny problems only."""
     P = problem
     n_orb, W, sc, nt = P.n_orb, P.n_words, P.cont_spin, P.n_to
     eri = P.full_eri()
@@ -119,17 +121,21 @@ def symbolic_blocks(problem):
 
     V = np.zeros((dim, dim))
     S = np.zeros((dim, dim))
+    F = np.zeros((dim, dim))
     for a, ra in enumerate(rows):
         for b, rb in enumerate(rows):
             if ra[0] == "c" and rb[0] == "c":
                 g, gp = P.groups[ra[1]], P.groups[rb[1]]
                 n, j, n_, jp = ra[2], ra[3], rb[2], rb[3]
                 D = {}
+                f = 0.0
                 for mp in range(gp.dets.shape[0]):
                     tk = terms_of(det_cj(gp, mp, jp))
                     for m in range(g.dets.shape[0]):
                         for lab, c in tk.get(det_cj(g, m, j), {}).items():
                             D[lab] = D.get(lab, 0.0) + g.ci[m, n] * gp.ci[mp, n_] * c
+                            f += abs(g.ci[m, n] * gp.ci[mp, n_] * c * X(lab))
+                F[a, b] = f
                 tgt = sum(d * X(lab) for lab, d in D.items() if _is_target_only(lab, nt))
                 oth = [d * X(lab) for lab, d in D.items() if not _is_target_only(lab, nt)]
                 V[a, b] = tgt + sum(oth)
@@ -138,7 +144,7 @@ def symbolic_blocks(problem):
                 tk = terms_of(fock.words_to_tuple(P.l2_dets[rb[1]], W, n_orb))
                 t = tk.get(fock.words_to_tuple(P.l2_dets[ra[1]], W, n_orb), {})
                 V[a, b] = sum(c * X(lab) for lab, c in t.items())
-                S[a, b] = sum(abs(c * X(lab)) for lab, c in t.items())
+                S[a, b] = F[a, b] = sum(abs(c * X(lab)) for lab, c in t.items())
             else:
                 (cr, lr) = (ra, rb) if ra[0] == "c" else (rb, ra)
                 g, n, j = P.groups[cr[1]], cr[2], cr[3]
@@ -149,5 +155,5 @@ def symbolic_blocks(problem):
                         x = g.ci[m, n] * c * X(lab)
                         v += x
                         s += abs(x)
-                V[a, b], S[a, b] = v, s
-    return V, S
+                V[a, b], S[a, b], F[a, b] = v, s, s
+    return V, S, F

@@ -54,6 +54,8 @@ def load():
         lib.orc_excitation_tl2.argtypes = [vp, vp, vp, vp]
         lib.orc_cc_contract.restype = vp
         lib.orc_cc_contract.argtypes = [vp, C.c_int, C.c_int]
+        lib.orc_cc_contract_ex.restype = vp
+        lib.orc_cc_contract_ex.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         lib.orc_cc_free.argtypes = [vp]
         lib.orc_cc_nlabels.restype = i64
         lib.orc_cc_nlabels.argtypes = [vp, C.c_int]
@@ -71,6 +73,9 @@ def load():
         lib.orc_cc_element_abs.restype = dbl
         lib.orc_cc_element_abs.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         lib.orc_cc_expand_abs.argtypes = [vp, vp, i64, i64, i64]
+        lib.orc_cc_element_cond.restype = dbl
+        lib.orc_cc_element_cond.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+        lib.orc_cc_expand_cond.argtypes = [vp, vp, i64, i64, i64]
         lib.orc_cc_expand_rows.argtypes = [vp, vp, C.c_int, C.c_int]
         lib.orc_class4_rows.argtypes = [vp, C.c_int, C.c_int, vp]
         lib.orc_class4_rows_abs.argtypes = [vp, C.c_int, C.c_int, vp]
@@ -152,8 +157,10 @@ class Oracle:
         self.lib.orc_build_dense(self.sp, _ptr(H))
         return H
 
-    def contract(self, g, gp):
-        return _CC(self, g, gp)
+    def contract(self, g, gp, cond=True):
+        """Eq. 8 for the group pair (g, gp); cond=False skips the magnitude
+        sums that element_cond needs."""
+        return _CC(self, g, gp, cond)
 
     def class4_row(self, l) -> np.ndarray:
         out = np.zeros(max(self.Dc, 1))
@@ -186,12 +193,13 @@ class Oracle:
         self.lib.orc_l2_rows_abs(self.sp, int(a0), int(a1), _ptr(out))
         return out[: a1 - a0, : self.problem.n_l2]
 
-    def condition(self) -> np.ndarray:
-        """dim x dim condition scales of every element (continuum block from
-        cc_condition, class 4 and L2 rows from their own sums), symmetric."""
+    def condition(self, full=True) -> np.ndarray:
+        """dim x dim condition scales of every element, symmetric: the sums of
+        the magnitudes of the terms of each element (continuum block from
+        cc_condition(full), class 4 and L2 rows from their own sums)."""
         S = np.zeros((self.dim, self.dim))
         Dc = self.Dc
-        S[:Dc, :Dc] = self.cc_condition()
+        S[:Dc, :Dc] = self.cc_condition(full)
         if self.problem.n_l2:
             c4 = self.class4_rows_abs(0, self.problem.n_l2)
             S[Dc:, :Dc] = c4
@@ -199,13 +207,16 @@ class Oracle:
             S[Dc:, Dc:] = self.l2_rows_abs(0, self.problem.n_l2)
         return S
 
-    def cc_condition(self) -> np.ndarray:
-        """Dc x Dc matrix of sum_b |D^b X(I^b)| for every continuum element."""
+    def cc_condition(self, full=False) -> np.ndarray:
+        """Dc x Dc matrix of sum_b |D^b X(I^b)| for every continuum element
+        (full=True: sum_b |X(I^b)| sum_{m m'} |c c C^b|, the contraction's
+        terms included)."""
         H = np.zeros((self.Dc, self.Dc))
+        fn = self.lib.orc_cc_expand_cond if full else self.lib.orc_cc_expand_abs
         for g in range(len(self.problem.groups)):
             for gp in range(g + 1):
                 cc = self.lib.orc_cc_contract(self.sp, g, gp)
-                self.lib.orc_cc_expand_abs(cc, _ptr(H), self.Dc, int(self.offsets[g]), int(self.offsets[gp]))
+                fn(cc, _ptr(H), self.Dc, int(self.offsets[g]), int(self.offsets[gp]))
                 self.lib.orc_cc_free(cc)
         return H
 
@@ -231,16 +242,21 @@ class Oracle:
 
 
 class _CC:
-    def __init__(self, orc: Oracle, g, gp):
+    def __init__(self, orc: Oracle, g, gp, cond=True):
         self.orc, self.g, self.gp = orc, g, gp
-        self.h = orc.lib.orc_cc_contract(orc.sp, g, gp)
+        self.h = orc.lib.orc_cc_contract_ex(orc.sp, g, gp, 1 if cond else 0)
 
     def element(self, n, j, np_, jp) -> float:
         """Continuum indices j, jp are 0-based within the continuum."""
         return self.orc.lib.orc_cc_element(self.h, n, j, np_, jp)
 
     def element_abs(self, n, j, np_, jp) -> float:
+        """sum_b |D^b X(I^b)| (contracted coefficients)."""
         return self.orc.lib.orc_cc_element_abs(self.h, n, j, np_, jp)
+
+    def element_cond(self, n, j, np_, jp) -> float:
+        """sum_b |X(I^b)| sum_{m m'} |c_mn c_m'n' C^b| (every term of Eq. 8 and Eq. 7)."""
+        return self.orc.lib.orc_cc_element_cond(self.h, n, j, np_, jp)
 
     def expand_rows(self, jj0, jj1):
         """Elements [(jj, jj', n, n')] for rows jj0 <= jj < jj1 of this block."""

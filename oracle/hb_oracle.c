@@ -376,6 +376,11 @@ typedef struct {
     orc_map same;   /* same continuum orbital prototype, labels with placeholder */
     orc_map diff;   /* different continuum orbitals prototype */
     double *K0;     /* j-independent part of the same-orbital prototype [n][n'] */
+    /* the same sums over |c_mn c_m'n' C| (|c c C X| for K0): the magnitudes of
+       the terms the contraction (Eq. 8) adds, for the full condition scale */
+    orc_map same_abs, diff_abs;
+    double *K0abs;
+    int with_abs;   /* 0: the magnitudes were not accumulated */
 } orc_cc;
 
 /* Merge map b into map a (blocks added label by label). */
@@ -389,14 +394,18 @@ static void map_merge(orc_map *a, const orc_map *b) {
     }
 }
 
-orc_cc *orc_cc_contract(const orc_problem *P, int g, int gp) {
+orc_cc *orc_cc_contract_ex(const orc_problem *P, int g, int gp, int with_abs) {
     orc_cc *c = (orc_cc *)calloc(1, sizeof(orc_cc));
+    c->with_abs = with_abs;
     c->P = P; c->g = g; c->gp = gp;
     c->ns = P->g_nstate[g]; c->nsp = P->g_nstate[gp];
     const int ns = c->ns, nsp = c->nsp, bsz = ns * nsp;
     map_init(&c->same, bsz);
     map_init(&c->diff, bsz);
+    map_init(&c->same_abs, bsz);
+    map_init(&c->diff_abs, bsz);
     c->K0 = (double *)calloc((size_t)bsz, sizeof(double));
+    c->K0abs = (double *)calloc((size_t)bsz, sizeof(double));
     const int W = P->W, We = ext_words(P), ph = P->n_to, phk = P->n_to + 1, sc = P->cont_spin;
     const uint64_t *Dg = P->g_dets[g], *Dgp = P->g_dets[gp];
     const double *Cg = P->g_ci[g], *Cgp = P->g_ci[gp];
@@ -404,10 +413,13 @@ orc_cc *orc_cc_contract(const orc_problem *P, int g, int gp) {
        own maps (Eq. 8 sums), merged in thread order at the end */
 #pragma omp parallel
     {
-        orc_map same, diff;
+        orc_map same, diff, same_a, diff_a;
         map_init(&same, bsz);
         map_init(&diff, bsz);
+        map_init(&same_a, bsz);
+        map_init(&diff_a, bsz);
         double *K0 = (double *)calloc((size_t)bsz, sizeof(double));
+        double *K0a = (double *)calloc((size_t)bsz, sizeof(double));
         orc_sym *buf = (orc_sym *)malloc(sizeof(orc_sym) * 8192);
         double *cc = (double *)malloc(sizeof(double) * bsz);
         uint64_t I[2 * ORC_MAXW], J[2 * ORC_MAXW];
@@ -433,13 +445,20 @@ orc_cc *orc_cc_contract(const orc_problem *P, int g, int gp) {
                     if (!has) {
                         double x = buf[k].coef * orc_X(P, L, -1, 0, -1, 0);
                         for (int t = 0; t < bsz; ++t) K0[t] += cc[t] * x;
+                        if (with_abs) for (int t = 0; t < bsz; ++t) K0a[t] += fabs(cc[t] * x);
                     } else {
                         double *blk = map_get(&same, L);
                         for (int t = 0; t < bsz; ++t) blk[t] += cc[t] * buf[k].coef;
+                        if (with_abs) {
+                            blk = map_get(&same_a, L);
+                            for (int t = 0; t < bsz; ++t) blk[t] += fabs(cc[t] * buf[k].coef);
+                        }
                     }
                 }
-                if (nd == 0 && P->e_core != 0.0)
+                if (nd == 0 && P->e_core != 0.0) {
                     for (int t = 0; t < bsz; ++t) K0[t] += cc[t] * P->e_core;
+                    if (with_abs) for (int t = 0; t < bsz; ++t) K0a[t] += fabs(cc[t] * P->e_core);
+                }
                 /* prototype 2: different continuum orbitals (j in bra, j' in ket) */
                 if (nd <= 2) {
                     extend(P, Dm, ph, sc, I);
@@ -448,6 +467,10 @@ orc_cc *orc_cc_contract(const orc_problem *P, int g, int gp) {
                     for (int k = 0; k < n; ++k) {
                         double *blk = map_get(&diff, buf[k].label);
                         for (int t = 0; t < bsz; ++t) blk[t] += cc[t] * buf[k].coef;
+                        if (with_abs) {
+                            blk = map_get(&diff_a, buf[k].label);
+                            for (int t = 0; t < bsz; ++t) blk[t] += fabs(cc[t] * buf[k].coef);
+                        }
                     }
                 }
             }
@@ -458,19 +481,30 @@ orc_cc *orc_cc_contract(const orc_problem *P, int g, int gp) {
             {
                 map_merge(&c->same, &same);
                 map_merge(&c->diff, &diff);
+                map_merge(&c->same_abs, &same_a);
+                map_merge(&c->diff_abs, &diff_a);
                 for (int t = 0; t < bsz; ++t) c->K0[t] += K0[t];
+                for (int t = 0; t < bsz; ++t) c->K0abs[t] += K0a[t];
             }
         }
         map_free(&same);
         map_free(&diff);
+        map_free(&same_a);
+        map_free(&diff_a);
         free(K0);
+        free(K0a);
         free(buf);
         free(cc);
     }
     return c;
 }
 
-void orc_cc_free(orc_cc *c) { map_free(&c->same); map_free(&c->diff); free(c->K0); free(c); }
+orc_cc *orc_cc_contract(const orc_problem *P, int g, int gp) { return orc_cc_contract_ex(P, g, gp, 1); }
+
+void orc_cc_free(orc_cc *c) {
+    map_free(&c->same); map_free(&c->diff); map_free(&c->same_abs); map_free(&c->diff_abs);
+    free(c->K0); free(c->K0abs); free(c);
+}
 
 int64_t orc_cc_nlabels(const orc_cc *c, int which) { return which ? c->diff.n : c->same.n; }
 
@@ -849,4 +883,44 @@ void orc_class4_rows_abs(const orc_problem *P, int l0, int l1, double *out) {
     const int64_t Dc = orc_contracted_dim(P);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int l = l0; l < l1; ++l) orc_class4_row_abs(P, l, out + (int64_t)(l - l0) * Dc);
+}
+
+/* Full condition scale of a contracted continuum element: the sum of the
+   magnitudes of every term of Eq. 8 followed by Eq. 7,
+       sum_b |X(I^b)| sum_{m m'} |c_mn c_m'n' C^b_{m m'}|,
+   the labels without a continuum index included term by term.  Rounding in
+   any evaluation order of the contraction and the expansion (an FP64 one
+   included) is bounded by a multiple of the unit roundoff of this scale. */
+double orc_cc_element_cond(const orc_cc *c, int n, int j, int np, int jp) {
+    const orc_problem *P = c->P;
+    if (!c->with_abs) return NAN;
+    const int ph = P->n_to, phk = P->n_to + 1, t = n * c->nsp + np;
+    const int jg = P->n_to + j, jpg = P->n_to + jp;
+    const orc_map *m = (j == jp) ? &c->same_abs : &c->diff_abs;
+    double v = (j == jp) ? c->K0abs[t] : 0.0;
+    for (int64_t i = 0; i < m->cap; ++i) {
+        int s = m->slot[i];
+        if (s < 0) continue;
+        double x = (j == jp) ? orc_X(P, m->keys[i], ph, jg, -1, 0) : orc_X(P, m->keys[i], ph, jg, phk, jpg);
+        v += m->blocks[(int64_t)s * m->bsz + t] * fabs(x);
+    }
+    return v;
+}
+
+/* The same for a whole group-pair block, written like orc_cc_expand. */
+void orc_cc_expand_cond(const orc_cc *c, double *H, int64_t ld, int64_t row0, int64_t col0) {
+    const orc_problem *P = c->P;
+    const int cfg = P->g_cfirst[c->g], cng = P->g_ccount[c->g];
+    const int cfp = P->g_cfirst[c->gp], cnp = P->g_ccount[c->gp];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int jj = 0; jj < cng; ++jj)
+        for (int jjp = 0; jjp < cnp; ++jjp)
+            for (int n = 0; n < c->ns; ++n)
+                for (int np = 0; np < c->nsp; ++np) {
+                    int64_t r = row0 + (int64_t)n * cng + jj, cl = col0 + (int64_t)np * cnp + jjp;
+                    if (c->g == c->gp && r < cl) continue;
+                    double v = orc_cc_element_cond(c, n, cfg + jj, np, cfp + jjp);
+                    H[r * ld + cl] = v;
+                    H[cl * ld + r] = v;
+                }
 }

@@ -34,7 +34,10 @@ int noalloc_fail(int code, const std::string &msg) {
 
 // Device address of the static array on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  The cached
+// address lives as long as the device's primary context: after a
+// cudaDeviceReset it is stale, which is why the header rules out calls on a
+// device after a reset.
 int rows_address(int64_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -7,6 +7,8 @@ import pytest
 from oracle import coracle
 from paper_1709_03005_gb300 import synth
 
+from gpu_util import FP64_FALLBACK, MIXED_C4_FALLBACK, MIXED_C4_TC_ABS, MIXED_CC_FALLBACK, check_elements
+
 pytestmark = pytest.mark.gpu
 
 
@@ -42,18 +44,12 @@ def test_batch_members_match_oracle(family):
     B = hb.Batch(members, hb.HB_MIXED)
     B.launch()
     torch.cuda.synchronize()
+    from gpu_util import assert_blocks_close
     for P, b in zip(members, B.blocks):
         o = coracle.Oracle(P)
         R = o.dense()
-        cond = o.cc_condition()
         G = hb.dense_from_blocks(b).cpu().numpy()
-        Dc = o.Dc
-        d = np.abs(G[:Dc, :Dc] - R[:Dc, :Dc])
-        assert np.all(d <= 1e-10 * cond), (P.name, (d / np.maximum(cond, 1e-300)).max())
-        for blk in (np.s_[Dc:, :Dc], np.s_[Dc:, Dc:]):
-            g, r = G[blk], R[blk]
-            if r.size:
-                assert np.all(np.abs(g - r) <= 1e-12 * np.maximum(np.abs(r), np.abs(r).max())), P.name
+        assert_blocks_close(G, R, o, 1e-10, P.name, mixed=True)
         # classes 5 and 6: two groups of the same irrep share a continuum range
         ranges = [(g.cont_first, g.cont_count) for g in P.groups]
         assert len(set(ranges)) < len(ranges)
@@ -83,7 +79,53 @@ def test_batch_class4_tensor_cores(family):
     R = o.dense()
     G = hb.dense_from_blocks(B.blocks[0]).cpu().numpy()
     blk = np.s_[o.Dc:, :o.Dc]
-    r = R[blk]
-    if r.size:
-        assert np.all(np.abs(G[blk] - r) <= 1e-12 * np.maximum(np.abs(r), np.abs(r).max()))
+    if R[blk].size:
+        check_elements(G[blk], R[blk], o.condition()[blk], 1e-10, MIXED_C4_FALLBACK, "class 4 tensor cores",
+                       abs_frac=MIXED_C4_TC_ABS)
+    B.close()
+
+
+def test_batch_every_member_sampled(family):
+    """Every one of the 16 Hamiltonians of the batched build against the
+    oracle: sampled continuum elements over random group pairs, whole class-4
+    rows and whole L2 rows."""
+    import torch
+    from paper_1709_03005_gb300 import hb
+    B = hb.Batch(family, hb.HB_MIXED)
+    B.launch()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(44)
+    for P, H, b in zip(family, B.hams, B.blocks):
+        o = coracle.Oracle(P)
+        Hcc = b["Hcc"].cpu().numpy()
+        ng = len(P.groups)
+        ref, cond, got = [], [], []
+        for _ in range(10):
+            g, gp = sorted(rng.integers(0, ng, 2).tolist(), reverse=True)
+            cc = o.contract(g, gp)
+            G, Gp = P.groups[g], P.groups[gp]
+            for _ in range(20):
+                n, n_ = int(rng.integers(G.ci.shape[1])), int(rng.integers(Gp.ci.shape[1]))
+                jj, jjp = int(rng.integers(G.cont_count)), int(rng.integers(Gp.cont_count))
+                t = (n, G.cont_first + jj, n_, Gp.cont_first + jjp)
+                ref.append(cc.element(*t))
+                cond.append(cc.element_cond(*t))
+                got.append(Hcc[H.group_offsets[g] + n * G.cont_count + jj, H.group_offsets[gp] + n_ * Gp.cont_count + jjp])
+            del cc
+        check_elements(np.array(got), np.array(ref), np.array(cond), 1e-10, MIXED_CC_FALLBACK, f"{P.name} cc",
+                       blockmax=np.abs(Hcc).max())
+        if P.n_l2:
+            rows = np.sort(rng.choice(P.n_l2, min(4, P.n_l2), replace=False))
+            Hlc = b["Hlc"].cpu().numpy()
+            for l in rows:
+                check_elements(Hlc[l], o.class4_row(int(l)), o.class4_rows_abs(int(l), int(l) + 1)[0], 1e-10,
+                               MIXED_C4_FALLBACK, f"{P.name} class 4 row {l}", blockmax=np.abs(Hlc).max(),
+                               abs_frac=MIXED_C4_TC_ABS)
+            rp = b["row_ptr"].cpu().numpy()
+            for a in rows:
+                row = o.l2_rows(int(a), int(a) + 1)[0]
+                dense = np.zeros(P.n_l2)
+                dense[b["col"][rp[a]:rp[a + 1]].cpu().numpy()] = b["val"][rp[a]:rp[a + 1]].cpu().numpy()
+                check_elements(dense, row, o.l2_rows_abs(int(a), int(a) + 1)[0], 1e-12, FP64_FALLBACK,
+                               f"{P.name} L2 row {a}")
     B.close()

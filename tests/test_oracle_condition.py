@@ -2,9 +2,12 @@
 
 The GPU parity tests of the continuum block at full size compare sampled
 elements with `orc_cc_element` (Eq. 7 for one element after the Eq. 8
-contraction), and the mixed-precision tests measure errors against the
-condition scale sum_b |D^b X(I^b)| of each element (`orc_cc_element_abs`,
-`cc_condition`), plus the class-4 and L2 scales.  These are separate code
+contraction), and every GPU parity test measures the errors of elements that
+cancel against condition scales: sum_b |D^b X(I^b)| over the contracted
+coefficients (`orc_cc_element_abs`, `cc_condition()`), the full scale
+sum_b |X(I^b)| sum_{mm'} |c c C^b| over every term of Eq. 8 and Eq. 7
+(`orc_cc_element_cond`, `cc_condition(full=True)`), and the class-4 and L2
+scales.  These are separate code
 paths from the dense build, so they are pinned here on their own:
 
 * against the brute-force operator build resolved by integral
@@ -65,31 +68,37 @@ def test_symbolic_brute_is_the_operator_matrix(name, kw):
     """The label-resolved operator build sums to the plain operator build."""
     kw = dict(kw)
     P = synth.make_tiny(kw.pop("seed"), **kw)
-    V, S = brute.symbolic_blocks(P)
+    V, S, F = brute.symbolic_blocks(P)
     Hb = brute.contracted_hamiltonian(P)
     np.testing.assert_allclose(V, Hb, rtol=0, atol=1e-13 * max(1.0, np.abs(Hb).max()))
     assert np.all(S >= np.abs(V) * (1 - 1e-13))
+    assert np.all(F >= S * (1 - 1e-13))
 
 
 @pytest.mark.parametrize("name,kw", TINY, ids=[t[0] for t in TINY])
 def test_element_and_condition_against_brute(name, kw):
     """orc_cc_element at every continuum element equals the brute-force
     contracted matrix; the oracle's condition scales of all three classes
-    (continuum, class 4, L2) equal the brute-force sums of term magnitudes."""
+    (continuum, class 4, L2), with contracted coefficients and in full, equal
+    the brute-force sums of term magnitudes."""
     kw = dict(kw)
     P = synth.make_tiny(kw.pop("seed"), **kw)
     o = coracle.Oracle(P)
-    V, S = brute.symbolic_blocks(P)
+    V, S, F = brute.symbolic_blocks(P)
     Dc = o.Dc
     E = _cc_elements(o, P, lambda cc, *a: cc.element(*a))
     Ea = _cc_elements(o, P, lambda cc, *a: cc.element_abs(*a))
+    Ec = _cc_elements(o, P, lambda cc, *a: cc.element_cond(*a))
     scale = max(1.0, np.abs(V).max())
     np.testing.assert_allclose(E, V[:Dc, :Dc], rtol=0, atol=1e-13 * scale)
     np.testing.assert_allclose(Ea, S[:Dc, :Dc], rtol=1e-13, atol=1e-15 * scale)
+    np.testing.assert_allclose(Ec, F[:Dc, :Dc], rtol=1e-13, atol=1e-15 * scale)
+    np.testing.assert_allclose(o.condition(full=False), S, rtol=1e-13, atol=1e-15 * scale)
     Sc = o.condition()
-    np.testing.assert_allclose(Sc, S, rtol=1e-13, atol=1e-15 * scale)
-    # the dense condition of the continuum block is the element function's
-    np.testing.assert_array_equal(Sc[:Dc, :Dc], Ea)
+    np.testing.assert_allclose(Sc, F, rtol=1e-13, atol=1e-15 * scale)
+    # the dense scales of the continuum block are the element functions'
+    np.testing.assert_array_equal(Sc[:Dc, :Dc], Ec)
+    np.testing.assert_array_equal(o.cc_condition(), Ea)
 
 
 @pytest.mark.parametrize("key,kw", [("c1", {}), ("mid", {}),
@@ -150,9 +159,10 @@ def test_single_label_elements_have_condition_equal_to_value():
                     assert S[r, c] == abs(R[r, c]), (m, mp, j, jp)
                     checked += R[r, c] != 0.0
     assert checked > 0
-    # class 4: pairs (m, l) whose (N+1)-electron excitation is a double
-    # have no one-electron term and, with no two-electron integrals, vanish
-    V, Sb = brute.symbolic_blocks(P)
+    # with identity CI vectors the contraction adds single terms, so the full
+    # scale is the contracted one; class 4 against the brute-force scales
+    np.testing.assert_array_equal(o.condition(full=False)[:Dc, :Dc], S[:Dc, :Dc])
+    V, Sb, F = brute.symbolic_blocks(P)
     np.testing.assert_allclose(S[Dc:, :Dc], Sb[Dc:, :Dc], rtol=1e-14, atol=0)
 
 
