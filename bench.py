@@ -13,7 +13,11 @@ lower-triangle positions per build (the positions the paper's whole-matrix
 timings cover).  The plain FP64 GPU build of the same instance is timed after
 the steps ("fp64", "speedup_vs_fp64").  Davidson (lowest 20 eigenpairs of the
 medium workload, dimension 8000, to a residual of 1e-8) is timed after that,
-on the GPU and with the CPU baseline (numpy block Davidson), under "davidson".
+on the GPU and with the CPU baseline (numpy block Davidson), under "davidson";
+the lowest 200 eigenpairs of the 60000-dimensional workload under
+"davidson_c5"; the build and Davidson of the L2-heavy shape of the paper's
+H3PO4 run (dimension 122815, 122103 L2 functions) under "l2_heavy"; the
+16-Hamiltonian batched build under "batched".
 
 Prints one JSON line (rank 0).  Under torchrun every rank builds its own
 replica (independent problem, no data-path collective) and the time is the
@@ -415,6 +419,62 @@ def run_ours(args, rank, world, local_rank):
         del bd
         torch.cuda.empty_cache()
 
+    # the L2-heavy shape of the paper's H3PO4 run (contracted 712, 122103 L2
+    # functions): the build and the lowest 20 eigenpairs
+    l2_heavy = None
+    if args.l2_heavy:
+        try:
+            Pl = synth.make_config("h3po4")
+            Hl = hb.Hamiltonian(Pl, validate=False)
+            bl, _ = Hl.build(hb.HB_MIXED)
+            torch.cuda.synchronize()
+            tl = []
+            for _ in range(3):
+                flush.zero_()
+                _, stl = Hl.build(hb.HB_MIXED, bl)
+                tl.append(stl.ms_total)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev, dst, ok = Hl.diag(bl, 20, 1e-8, 400, precond=hb.HB_PRECOND_DIAG | hb.HB_DIAG_TENSOR,
+                                  allow_not_converged=True)
+            torch.cuda.synchronize()
+            l2_heavy = {"workload": "l2_heavy_h3po4: 50 target + 89 continuum orbitals, N=14+1, 2000 target dets, "
+                                    "8 states, 122103 L2, dim 122815", "l2_nnz": int(Hl.layout.l2_nnz),
+                        "build_ms": float(np.median(tl)), "value": positions(Hl.dim) / (np.median(tl) / 1e3),
+                        "unit": "H elements/s",
+                        "davidson": {"k": 20, "tol": 1e-8, "seconds": time.perf_counter() - t0,
+                                     "iterations": dst.iterations, "fp64_iterations": dst.fp64_iterations,
+                                     "converged": ok, "max_residual": dst.max_residual, "matvec_ms": dst.ms_matvec}}
+            Hl.close()
+            del bl
+            torch.cuda.empty_cache()
+        except hb.HBError as e:
+            l2_heavy = {"unavailable": str(e)}
+
+    # the learned-preconditioner workload: lowest 200 eigenpairs, dimension 60000
+    davidson_c5 = None
+    if args.c5_k > 0:
+        try:
+            P5 = synth.make_config("c5")
+            H5 = hb.Hamiltonian(P5, validate=False)
+            b5, st5 = H5.build(hb.HB_MIXED)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev, dst, ok = H5.diag(b5, args.c5_k, 1e-8, 400, precond=hb.HB_PRECOND_DIAG | hb.HB_DIAG_TENSOR,
+                                  allow_not_converged=True)
+            torch.cuda.synchronize()
+            davidson_c5 = {"workload": "c5_learned: 40 target + 400 continuum orbitals, N=14+1, 20000 target dets, "
+                                       "50 states, 40000 L2, dim 60000", "k": args.c5_k, "tol": 1e-8,
+                           "precond": "diagonal", "seconds": time.perf_counter() - t0, "iterations": dst.iterations,
+                           "fp64_iterations": dst.fp64_iterations, "converged": ok,
+                           "max_residual": dst.max_residual, "matvec_ms": dst.ms_matvec, "rr_ms": dst.ms_rr,
+                           "gram_ms": dst.ms_gram, "combine_ms": dst.ms_combine}
+            H5.close()
+            del b5
+            torch.cuda.empty_cache()
+        except hb.HBError as e:
+            davidson_c5 = {"unavailable": str(e)}
+
     # the batched workload: 16 symmetry / spin-coupling Hamiltonians, one graph
     # launch; the plain FP64 batch is timed beside it for the speedup
     batched = None
@@ -470,7 +530,8 @@ def run_ours(args, rank, world, local_rank):
                "roofline": roof, "cpu_baseline": cb,
                "e2e": {"value": e2e_value, "unit": "H elements/s", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},
-               "gpu_launches": launches, "clocks": clk.summary(), "davidson": davidson, "batched": batched,
+               "gpu_launches": launches, "clocks": clk.summary(), "davidson": davidson, "davidson_c5": davidson_c5,
+               "l2_heavy": l2_heavy, "batched": batched,
                "stages_ms": {"target": st.ms_target, "expand": st.ms_expand, "class4": st.ms_class4,
                              "class4_kernel": st.ms_class4_kernel, "l2": st.ms_l2, "expand_kernel": gemm_ms}}
         print(json.dumps(out), flush=True)
@@ -489,6 +550,8 @@ def main():
     ap.add_argument("--davidson-k", type=int, default=20)
     ap.add_argument("--davidson-config", default="c2")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--c5-k", type=int, default=200, help="eigenpairs of the dimension-60000 workload (0: skip)")
+    ap.add_argument("--no-l2-heavy", dest="l2_heavy", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     args = ap.parse_args()

@@ -81,7 +81,14 @@ enum { HB_SPIN_ALPHA = 0, HB_SPIN_BETA = 1 };
 typedef struct hb_ctx hb_ctx;
 
 /* One target symmetry (Eq. 2): phi_n = sum_m c[m][n] D_m, coupled to the
-   contiguous continuum range [cont_first, cont_first + cont_count). */
+   contiguous continuum range [cont_first, cont_first + cont_count).
+   energy (host [n_state], or NULL): target-state energies for the
+   target-energy substitution of Section 3.1.  When given (for every group or
+   for none), the CI vectors are taken to be eigenvectors of the N-electron
+   target Hamiltonian H^N (+ e_core on its diagonal), and the target-only part
+   of the continuum-continuum block, <phi_gn|H^N + e_core|phi_g'n'>, is
+   delta_gg' delta_nn' energy[n] instead of the Eq. 8 sum over the target-only
+   integrals.  hb_target_diag returns such energies and CI vectors. */
 typedef struct {
     int32_t n_det;
     int32_t n_state;
@@ -89,6 +96,7 @@ typedef struct {
     const double *ci;       /* host, [n_det][n_state], row-major */
     int32_t cont_first;
     int32_t cont_count;
+    const double *energy;   /* host, [n_state], or NULL */
 } hb_group;
 
 /* The problem of Eq. 1: orbitals, integrals, target groups, L2 functions.
@@ -163,7 +171,8 @@ typedef struct {
     float ms_gram;            /* hb_diag: projections (device sums and their copy to the host) */
     float ms_combine;         /* hb_diag: basis combinations (coefficients to the device, kernel) */
     float ms_class4_kernel;   /* the class-4 kernels after their classification (part of ms_class4) */
-    int32_t reserved[3];
+    int32_t fp64_iterations;  /* hb_diag: iterations with FP64 products after the convergence check */
+    int32_t reserved[2];
 } hb_stats;
 
 /* Excitation record of one determinant pair (row, col), see hb_classify. */
@@ -218,6 +227,24 @@ int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *out, hb_sta
 int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, int32_t max_iter,
             int32_t precond, const double *v0, double *evals, double *evecs, hb_stats *st,
             void *stream);
+
+/* Target states of group g of a problem (Section 3.1 with the classes 2/8
+   machinery of Section 2.2): the lowest k eigenpairs of the N-electron target
+   Hamiltonian H^N + e_core over the group's determinants.  H^N is built on the
+   device by the L2-L2 Slater-Condon kernels applied to the N-electron
+   determinants (CSR, FP64) and solved by hb_diag's block Davidson with the
+   diagonal preconditioner to ||H^N c - E c||_2 <= tol for each pair.  Only
+   the problem's orbital counts, h, eri_tttt, e_core and the group's
+   determinants are read.  energies: host [k], ascending; ci: host [n_det][k],
+   row-major, orthonormal columns (each column's sign fixed so that its
+   largest-magnitude entry is positive): ready to be passed as the group's ci
+   and energy for the target-energy substitution.  st (or NULL) receives the
+   solve's statistics.  The call allocates and frees its own device memory.
+   Errors: HB_ERR_INVALID_ARG (g out of range, k < 1 or k > n_det, NULL
+   outputs), HB_ERR_NOT_CONVERGED after max_iter iterations (outputs then hold
+   the current Ritz pairs), HB_ERR_OOM, HB_ERR_CUDA. */
+int hb_target_diag(const hb_problem *p, int32_t g, int32_t k, double tol, int32_t max_iter, double *energies,
+                   double *ci, hb_stats *st, void *stream);
 
 /* Stage a problem whose orbitals and integrals are those of `base` (for
    instance another spatial-symmetry or spin-coupling block of the same

@@ -38,7 +38,8 @@ class _Problem(C.Structure):
                 ("g_ndet", C.c_void_p), ("g_nstate", C.c_void_p),
                 ("g_cfirst", C.c_void_p), ("g_ccount", C.c_void_p),
                 ("g_dets", C.c_void_p), ("g_ci", C.c_void_p),
-                ("n_l2", C.c_int32), ("l2", C.c_void_p), ("e_core", C.c_double)]
+                ("n_l2", C.c_int32), ("l2", C.c_void_p), ("e_core", C.c_double),
+                ("g_energy", C.c_void_p)]
 
 
 def load():
@@ -119,13 +120,21 @@ class Oracle:
         t2 = arr(P.eri_ttcc, np.float64)
         tc = arr(P.eri_tctc, np.float64)
         l2 = arr(P.l2_dets, np.uint64) if P.n_l2 else arr(np.zeros((1, 2 * P.n_words)), np.uint64)
+        ens = [getattr(g, "energy", None) for g in gs]
+        if any(e is not None for e in ens):
+            if any(e is None for e in ens):
+                raise ValueError("target energies must be given for every group or for none")
+            ens = [arr(e, np.float64) for e in ens]
+            g_energy = _ptr(arr([_ptr(e) for e in ens], np.uint64))
+        else:
+            g_energy = None
         self._keep = keep
         self.s = _Problem(P.n_to, P.n_co, P.n_elec, P.n_words, P.cont_spin,
                           _ptr(h), _ptr(t4), _ptr(t3), _ptr(t2), _ptr(tc),
                           len(gs), _ptr(self.g_ndet), _ptr(self.g_nstate),
                           _ptr(self.g_cfirst), _ptr(self.g_ccount),
                           _ptr(self.g_dets), _ptr(self.g_ci),
-                          P.n_l2, _ptr(l2), float(P.e_core))
+                          P.n_l2, _ptr(l2), float(P.e_core), g_energy)
         self.sp = C.addressof(self.s)
         self.offsets = np.concatenate([[0], np.cumsum(self.g_nstate.astype(np.int64) *
                                                       self.g_ccount.astype(np.int64))])

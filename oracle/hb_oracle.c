@@ -54,6 +54,9 @@ typedef struct {
     int32_t n_l2;
     const uint64_t *l2;
     double e_core;
+    /* target-energy substitution (Section 3.1): per group, the state
+       energies, or NULL when the target-only part is the Eq. 8 sum */
+    const double *const *g_energy;
 } orc_problem;
 
 static int popc64(uint64_t x) { return __builtin_popcountll(x); }
@@ -443,6 +446,7 @@ orc_cc *orc_cc_contract_ex(const orc_problem *P, int g, int gp, int with_abs) {
                     int has = 0;
                     for (int s2 = 0; s2 < 4; ++s2) has |= (int)(((L >> (16 * s2)) & 0xFFFFu) == (uint64_t)ph);
                     if (!has) {
+                        if (P->g_energy) continue;   /* replaced by the target energies below */
                         double x = buf[k].coef * orc_X(P, L, -1, 0, -1, 0);
                         for (int t = 0; t < bsz; ++t) K0[t] += cc[t] * x;
                         if (with_abs) for (int t = 0; t < bsz; ++t) K0a[t] += fabs(cc[t] * x);
@@ -455,7 +459,7 @@ orc_cc *orc_cc_contract_ex(const orc_problem *P, int g, int gp, int with_abs) {
                         }
                     }
                 }
-                if (nd == 0 && P->e_core != 0.0) {
+                if (nd == 0 && P->e_core != 0.0 && !P->g_energy) {
                     for (int t = 0; t < bsz; ++t) K0[t] += cc[t] * P->e_core;
                     if (with_abs) for (int t = 0; t < bsz; ++t) K0a[t] += fabs(cc[t] * P->e_core);
                 }
@@ -495,6 +499,15 @@ orc_cc *orc_cc_contract_ex(const orc_problem *P, int g, int gp, int with_abs) {
         free(K0a);
         free(buf);
         free(cc);
+    }
+    if (P->g_energy) {
+        /* the target states are eigenstates of H^N + e_core: their target-only
+           part is delta_gg' delta_nn' E_n (Section 3.1) */
+        for (int a = 0; a < ns; ++a)
+            for (int b = 0; b < nsp; ++b) {
+                c->K0[a * nsp + b] = (g == gp && a == b) ? P->g_energy[g][a] : 0.0;
+                c->K0abs[a * nsp + b] = fabs(c->K0[a * nsp + b]);
+            }
     }
     return c;
 }
@@ -690,6 +703,7 @@ void orc_l2_csr(const orc_problem *P, int64_t *row_ptr, int32_t *cols, double *v
     const int W = P->W, nl = P->n_l2;
     if (!vals) {
         row_ptr[0] = 0;
+#pragma omp parallel for schedule(dynamic, 64)
         for (int a = 0; a < nl; ++a) {
             int64_t c = 0;
             for (int b = 0; b < nl; ++b) {
@@ -697,8 +711,9 @@ void orc_l2_csr(const orc_problem *P, int64_t *row_ptr, int32_t *cols, double *v
                 for (int w = 0; w < 2 * W; ++w) nd += popc64(P->l2[(int64_t)a * 2 * W + w] ^ P->l2[(int64_t)b * 2 * W + w]);
                 c += (nd <= 4);
             }
-            row_ptr[a + 1] = row_ptr[a] + c;
+            row_ptr[a + 1] = c;
         }
+        for (int a = 0; a < nl; ++a) row_ptr[a + 1] += row_ptr[a];
         return;
     }
 #pragma omp parallel for schedule(dynamic, 8)

@@ -115,7 +115,10 @@ static int l2_mirror_prepare(hb_ctx *ctx, int n, int W, cudaStream_t s) {
     return HB_OK;
 }
 
-static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o) {
+// l2_extra: electrons of an L2 determinant beyond the target's N (1 for the
+// (N+1)-electron problem; 0 when the L2 list holds N-electron target
+// determinants, as in hb_target_diag).
+static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, int l2_extra = 1) {
     if (!p) return fail(ctx, HB_ERR_INVALID_ARG, "problem is NULL");
     if (p->n_words < 1 || p->n_words > HB_MAXW)
         return fail(ctx, HB_ERR_UNSUPPORTED, "n_words must be 1..4 (up to 256 target orbitals)");
@@ -130,6 +133,10 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
         return fail(ctx, HB_ERR_INVALID_ARG, "groups need a continuum");
     if (p->n_elec < 1 || p->n_elec > 2 * p->n_to)
         return fail(ctx, HB_ERR_INVALID_ARG, "n_elec out of range");
+    int n_energy = 0;
+    for (int g = 0; g < p->n_groups && p->groups; ++g) n_energy += p->groups[g].energy != nullptr;
+    if (n_energy != 0 && n_energy != p->n_groups)
+        return fail(ctx, HB_ERR_INVALID_ARG, "target energies must be given for every group or for none");
     if (!p->h || !p->eri_tttt) return fail(ctx, HB_ERR_INVALID_ARG, "h or eri_tttt is NULL");
     if (p->n_groups > 0 && (!p->eri_tttc || !p->eri_ttcc || !p->eri_tctc))
         return fail(ctx, HB_ERR_INVALID_ARG, "continuum integral arrays are NULL");
@@ -171,6 +178,8 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
             return fail(ctx, HB_ERR_INVALID_ARG, "group " + std::to_string(g) + ": continuum range");
         if (!all_finite(G.ci, (size_t)G.n_det * G.n_state))
             return fail(ctx, HB_ERR_INVALID_ARG, "group " + std::to_string(g) + ": non-finite CI");
+        if (G.energy && !all_finite(G.energy, (size_t)G.n_state))
+            return fail(ctx, HB_ERR_INVALID_ARG, "group " + std::to_string(g) + ": non-finite target energy");
         for (int m = 0; m < G.n_det; ++m) {
             const uint64_t *d = G.dets + (size_t)m * nw;
             if (!check_bits(d)) return fail(ctx, HB_ERR_INVALID_ARG, "determinant uses a non-target orbital");
@@ -189,7 +198,8 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
         const uint64_t *d = p->l2_dets + (size_t)l * nw;
         if (!check_bits(d)) return fail(ctx, HB_ERR_INVALID_ARG, "L2 determinant uses a non-target orbital");
         const int a = popcount_words(d, W), b = popcount_words(d + W, W);
-        if (a + b != p->n_elec + 1) return fail(ctx, HB_ERR_INVALID_ARG, "L2 determinant with wrong electron count");
+        if (a + b != p->n_elec + l2_extra)
+            return fail(ctx, HB_ERR_INVALID_ARG, "L2 determinant with wrong electron count");
         if (na >= 0) {
             const int ea = na + (p->cont_spin == HB_SPIN_ALPHA), eb = nb + (p->cont_spin == HB_SPIN_BETA);
             if (a != ea || b != eb) return fail(ctx, HB_ERR_INVALID_ARG, "L2 determinant with a different Ms");
@@ -275,16 +285,17 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
     ctx->Kpad = (ctx->K + 63) / 64 * 64;
     const int W = ctx->W, nw = 2 * W;
     // groups and offsets
-    int64_t det_off = 0, ci_off = 0, row_off = 0;
+    int64_t det_off = 0, ci_off = 0, row_off = 0, e_off = 0;
     for (int g = 0; g < p->n_groups; ++g) {
         const hb_group &G = p->groups[g];
         GroupInfo gi;
         gi.ndet = G.n_det; gi.ns = G.n_state; gi.cf = G.cont_first; gi.cn = G.cont_count;
-        gi.det_off = det_off; gi.ci_off = ci_off; gi.row_off = row_off;
+        gi.det_off = det_off; gi.ci_off = ci_off; gi.row_off = row_off; gi.e_off = e_off;
         ctx->groups.push_back(gi);
         det_off += (int64_t)G.n_det * nw;
         ci_off += (int64_t)G.n_det * G.n_state;
         row_off += (int64_t)G.n_state * G.cont_count;
+        e_off += G.n_state;
     }
     ctx->Dc = row_off;
     ctx->dim = row_off + p->n_l2;
@@ -313,6 +324,12 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         const GroupInfo &gi = ctx->groups[g];
         CK(cudaMemcpyAsync(ctx->dets + gi.det_off, G.dets, sizeof(uint64_t) * G.n_det * nw, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(ctx->ci + gi.ci_off, G.ci, sizeof(double) * G.n_det * G.n_state, cudaMemcpyHostToDevice, s));
+    }
+    if (p->n_groups > 0 && p->groups[0].energy) {
+        DALLOC(ctx->energy, e_off);
+        for (int g = 0; g < p->n_groups; ++g)
+            CK(cudaMemcpyAsync(ctx->energy + ctx->groups[g].e_off, p->groups[g].energy,
+                               sizeof(double) * p->groups[g].n_state, cudaMemcpyHostToDevice, s));
     }
     DALLOC(ctx->l2, std::max(p->n_l2, 1) * nw);
     if (p->n_l2 > 0)
@@ -529,6 +546,69 @@ extern "C" int hb_build_blocks(hb_ctx *ctx, int32_t precision, const hb_blocks *
     }
     if (st) plan_stats(plan, st);
     return HB_OK;
+}
+
+extern "C" int hb_target_diag(const hb_problem *p, int32_t g, int32_t k, double tol, int32_t max_iter,
+                              double *energies, double *ci, hb_stats *st, void *stream) {
+    if (!p || !energies || !ci) return fail(nullptr, HB_ERR_INVALID_ARG, "NULL argument");
+    if (g < 0 || g >= p->n_groups || !p->groups) return fail(nullptr, HB_ERR_INVALID_ARG, "group out of range");
+    const hb_group &G = p->groups[g];
+    if (k < 1 || k > G.n_det || !G.dets) return fail(nullptr, HB_ERR_INVALID_ARG, "k must be 1..n_det");
+    // The target Hamiltonian over the group's determinants is the L2-L2 block
+    // (classes 2 and 8) of a problem whose L2 list is those N-electron
+    // determinants and which has no target group.
+    hb_problem q{};
+    q.n_to = p->n_to; q.n_co = p->n_co; q.n_elec = p->n_elec; q.n_words = p->n_words; q.cont_spin = p->cont_spin;
+    q.h = p->h; q.eri_tttt = p->eri_tttt;
+    q.n_groups = 0; q.groups = nullptr;
+    q.n_l2 = G.n_det; q.l2_dets = G.dets; q.e_core = p->e_core;
+    hb_options o{};
+    o.validate = 1;
+    hb_ctx *ctx = new hb_ctx();
+    int rc = validate_problem(ctx, &q, &o, 0);
+    if (rc == HB_OK) rc = stage_problem(ctx, &q, &o, (cudaStream_t)stream);
+    if (rc != HB_OK) { g_last_error = ctx->err; hb_destroy(ctx); return rc; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = G.n_det, nnz = std::max<int64_t>(ctx->l2_nnz, 1);
+    hb_blocks H{};
+    double *evecs = nullptr;
+    cudaError_t e = cudaMalloc((void **)&H.l2_row_ptr, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&H.l2_col, sizeof(int32_t) * nnz);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&H.l2_val, sizeof(double) * nnz);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&evecs, sizeof(double) * n * k);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaMalloc");
+    if (rc == HB_OK) rc = hb_build_blocks(ctx, HB_FP64, &H, nullptr, stream);
+    int rc_diag = HB_OK;
+    std::vector<double> V;
+    if (rc == HB_OK) {
+        rc_diag = hb_diag(ctx, &H, k, tol, max_iter, HB_PRECOND_DIAG, nullptr, energies, evecs, st, stream);
+        if (rc_diag == HB_OK || rc_diag == HB_ERR_NOT_CONVERGED) {
+            V.resize((size_t)n * k);
+            e = cudaMemcpyAsync(V.data(), evecs, sizeof(double) * n * k, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = cuda_fail(ctx, e, "eigenvector readback");
+        } else {
+            rc = rc_diag;
+        }
+    }
+    if (rc == HB_OK) {
+        // a fixed sign per column: its largest-magnitude entry positive
+        for (int c = 0; c < k; ++c) {
+            int64_t best = 0;
+            for (int64_t i = 1; i < n; ++i)
+                if (std::fabs(V[i * k + c]) > std::fabs(V[best * k + c])) best = i;
+            const double sg = V[best * k + c] < 0 ? -1.0 : 1.0;
+            for (int64_t i = 0; i < n; ++i) ci[i * k + c] = sg * V[i * k + c];
+        }
+        rc = rc_diag;
+    }
+    if (rc != HB_OK) g_last_error = ctx->err;
+    cudaFree(H.l2_row_ptr);
+    cudaFree(H.l2_col);
+    cudaFree(H.l2_val);
+    cudaFree(evecs);
+    hb_destroy(ctx);
+    return rc;
 }
 
 extern "C" int hb_classify(const uint64_t *a, int32_t n_a, const uint64_t *b, int32_t n_b, int32_t n_words,

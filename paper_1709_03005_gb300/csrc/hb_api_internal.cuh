@@ -11,6 +11,7 @@ namespace hb {
 struct GroupInfo {
     int ndet = 0, ns = 0, cf = 0, cn = 0;
     int64_t det_off = 0, ci_off = 0, row_off = 0;
+    int64_t e_off = 0;          // first of the group's target energies in hb_ctx::energy
 };
 
 // Scratch of one target-group pair (g >= g'), classes 1, 3, 5, 6, 7.
@@ -65,6 +66,9 @@ struct hb_ctx {
     double *h = nullptr, *tttt = nullptr, *tttc = nullptr, *jk = nullptr, *panel = nullptr;
     uint64_t *dets = nullptr, *l2 = nullptr;
     double *ci = nullptr;
+    // target-energy substitution (Section 3.1): every group's state energies,
+    // or null when the target-only part is the Eq. 8 sum
+    double *energy = nullptr;
     // double-float (hi, lo) copies for the mixed class-4 kernel, made on first use
     float2 *tttc_df = nullptr, *h_df = nullptr, *ci_df = nullptr, *tttt_df = nullptr, *jk_df = nullptr;
     int64_t *l2_rowptr = nullptr;

@@ -18,6 +18,8 @@ struct DiagWork {
     double *proj = nullptr;       // projection coefficients kept on the device
     int32_t *idx = nullptr;
     double *HlcT = nullptr;       // class-4 block transposed (Dc x n_l2)
+    double *XT = nullptr;         // the L2 part of a block of vectors, [n_l2][q] (vectors interleaved)
+    int64_t XT_rows = 0;
     const double *HlcT_src = nullptr;
     // block products on the tensor cores: slices of [Hcc | Hlc^T] (rows of the
     // continuum block), of Hlc (rows of the L2 block) and of the vectors

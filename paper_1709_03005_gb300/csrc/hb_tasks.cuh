@@ -133,6 +133,7 @@ struct ATask {          // contracted coefficient rows A[(n,n')][k]
     double e_core;
     double *A;
     float2 *A_df;             // float-pair copy of A (mixed build)
+    const double *En;         // target-energy substitution: the group's state energies, or null
 };
 
 // One column of a merged expansion block: a state pair (n, n') of one group

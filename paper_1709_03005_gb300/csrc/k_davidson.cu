@@ -79,21 +79,59 @@ gemm_nt_kernel(const double *__restrict__ A, int64_t lda, const double *__restri
     }
 }
 
-// Y[j][l] += sum_p val[p] X[j][col[p]] over CSR rows l; one warp per row, lanes
-// over vectors (in groups of 32), entries in order.
+// XT[l][j] = X[j][l] for l < rows, j < q: the vectors interleaved, so that
+// one CSR column's q values are contiguous.  32 x 32 tiles through shared
+// memory, both sides coalesced.
+__global__ void interleave_kernel(const double *__restrict__ X, int64_t ldx, int64_t rows, int q,
+                                  double *__restrict__ XT) {
+    __shared__ double t[32][33];
+    const int64_t l0 = (int64_t)blockIdx.x * 32;
+    const int j0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = j0 + r;
+        const int64_t l = l0 + threadIdx.x;
+        t[r][threadIdx.x] = (j < q && l < rows) ? __ldg(X + (int64_t)j * ldx + l) : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t l = l0 + r;
+        const int j = j0 + threadIdx.x;
+        if (l < rows && j < q) XT[l * q + j] = t[threadIdx.x][r];
+    }
+}
+
+// Y[j][l] += sum_p val[p] XT[col[p]][j] over CSR rows l (classes 2 and 8 of
+// the matrix): one warp per row, lanes over vectors (in groups of 32),
+// entries in order.  Each entry reads its column's vectors as one contiguous
+// run of XT, so the warp's loads coalesce; the L2 block of an L2-heavy matrix
+// (hundreds of millions of entries) streams once per product.
 __global__ void spmm_csr_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                const double *__restrict__ val, int rows, const double *__restrict__ X, int64_t ldx,
-                                int q, double *__restrict__ Y, int64_t ldy) {
+                                const double *__restrict__ val, int rows, const double *__restrict__ XT, int q,
+                                double *__restrict__ Y, int64_t ldy) {
     const int lane = threadIdx.x & 31;
     const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (l >= rows) return;
     const int64_t b = rp[l], e = rp[l + 1];
     for (int j0 = 0; j0 < q; j0 += 32) {
         const int j = j0 + lane;
-        if (j >= q) break;
         double acc = 0.0;
-        for (int64_t p = b; p < e; ++p) acc = fma(__ldg(val + p), __ldg(X + (int64_t)j * ldx + __ldg(col + p)), acc);
-        Y[(int64_t)j * ldy + l] += acc;
+        // 32 entries at a time: the warp loads their (column, value) pairs in
+        // one coalesced read, then every lane walks them in order, taking each
+        // pair from the lane that holds it; the gathers of one batch do not
+        // depend on each other, so they are in flight together.
+        for (int64_t p0 = b; p0 < e; p0 += 32) {
+            const int64_t p = p0 + lane;
+            const int c_mine = p < e ? __ldg(col + p) : 0;
+            const double v_mine = p < e ? __ldg(val + p) : 0.0;
+            const int cnt = (int)min((int64_t)32, e - p0);
+#pragma unroll 8
+            for (int t = 0; t < cnt; ++t) {
+                const int c = __shfl_sync(0xffffffffu, c_mine, t);
+                const double v = __shfl_sync(0xffffffffu, v_mine, t);
+                if (j < q) acc = fma(v, __ldg(XT + (int64_t)c * q + j), acc);
+            }
+        }
+        if (j < q) Y[(int64_t)j * ldy + l] += acc;
     }
 }
 
@@ -519,6 +557,7 @@ struct Ops {
     cudaStream_t s;
     int64_t n, Dc, nl;
     DiagWork *w;
+    bool force_fp64 = false;   // products in FP64 even when the tensor-core slices exist
     int launches = 0;
     double ms_gram = 0.0, ms_combine = 0.0, ms_eigh = 0.0;
     static double now_ms() {
@@ -528,7 +567,7 @@ struct Ops {
     // Y[0:q] = H X[0:q], vectors stored as rows of length ld
     void matvec(const double *X, double *Y, int q, int64_t ld) {
         if (q <= 0) return;
-        if (w->tc) {
+        if (w->tc && !force_fp64) {
             // split-bf16 tensor-core products: Y_c = [Hcc | Hlc^T] X, Y_l = Hlc X_c
             // (+ the L2 block in FP64 below)
             dense_operand_fill(w->Xs, w->S, X, ld, (int)n, nullptr, 0, 0, q, s);
@@ -540,9 +579,7 @@ struct Ops {
                 } else {
                     for (int j = 0; j < q; ++j) cudaMemsetAsync(Y + (int64_t)j * ld, 0, sizeof(double) * nl, s);
                 }
-                spmm_csr_kernel<<<(unsigned)((nl + 7) / 8), 256, 0, s>>>(H->l2_row_ptr, H->l2_col, H->l2_val, (int)nl,
-                                                                         X + Dc, ld, q, Y + Dc, ld);
-                ++launches;
+                l2_product(X, Y, q, ld);
             }
             return;
         }
@@ -563,9 +600,20 @@ struct Ops {
             } else {
                 for (int j = 0; j < q; ++j) cudaMemsetAsync(Y + (int64_t)j * ld, 0, sizeof(double) * nl, s);
             }
+            l2_product(X, Y, q, ld);
+        }
+    }
+
+    // Y_l += (L2 block) X_l for the q vectors: interleave the L2 part of the
+    // vectors, then the CSR product
+    void l2_product(const double *X, double *Y, int q, int64_t ld) {
+        for (int j0 = 0; j0 < q; j0 += w->mmax) {
+            const int qq = std::min(q - j0, w->mmax);
+            dim3 gi((unsigned)((nl + 31) / 32), (unsigned)((qq + 31) / 32));
+            interleave_kernel<<<gi, dim3(32, 8), 0, s>>>(X + (int64_t)j0 * ld + Dc, ld, nl, qq, w->XT);
             spmm_csr_kernel<<<(unsigned)((nl + 7) / 8), 256, 0, s>>>(H->l2_row_ptr, H->l2_col, H->l2_val, (int)nl,
-                                                                     X + Dc, ld, q, Y + Dc, ld);
-            ++launches;
+                                                                     w->XT, qq, Y + (int64_t)j0 * ld + Dc, ld);
+            launches += 2;
         }
     }
 
@@ -698,6 +746,14 @@ int hb::ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t
         w->mmax = mmax;
         w->n = n;
     }
+    if (ctx->n_l2 > 0 && w->XT_rows < (int64_t)ctx->n_l2 * w->mmax) {
+        if (w->XT) cudaFree(w->XT);
+        w->XT = nullptr;
+        w->XT_rows = 0;
+        cudaError_t e = cudaMalloc(&w->XT, sizeof(double) * (size_t)ctx->n_l2 * w->mmax);
+        if (e != cudaSuccess) return diag_fail(ctx, HB_ERR_OOM, "Davidson interleaved-vector buffer");
+        w->XT_rows = (int64_t)ctx->n_l2 * w->mmax;
+    }
     if (ctx->Dc > 0 && ctx->n_l2 > 0 && (!w->HlcT || w->HlcT_src != H->Hlc)) {
         if (!w->HlcT) {
             cudaError_t e = cudaMalloc(&w->HlcT, sizeof(double) * (size_t)ctx->Dc * ctx->n_l2);
@@ -801,6 +857,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
     float *wts = nullptr;
     int fallbacks = 0;
     constexpr int kStall = 10;
+    int refreshes = 0, fp64_iters = 0;
     std::vector<double> res_hist;
     // projected matrix T = V^T A V, kept up to date on the host: the full
     // product for the start block, one border V^T (A V_new) per iteration, and
@@ -808,6 +865,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
     std::vector<double> Tp;
     ops.gram(w->V, m, w->AV, m, ld, Tp);
     for (iter = 1; iter <= max_iter; ++iter) {
+        if (ops.force_fp64) ++fp64_iters;
         // Rayleigh-Ritz
         std::vector<double> T(Tp), S;
         for (int a = 0; a < m; ++a)
@@ -839,7 +897,41 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         bool done = true;
         for (int j = 0; j < k; ++j)
             if (std::sqrt(std::max(0.0, RR[(size_t)j * nr + j])) > tol) done = false;
-        if (done) { converged = true; break; }
+        if (done) {
+            // The residuals above come from products carried through the
+            // restarts (A X = (A V) S): the Rayleigh-Ritz step fits the errors
+            // of those products, so they measure the residual of a perturbed
+            // operator.  Confirm them with fresh FP64 products H X of the Ritz
+            // vectors (the split-bf16 products err by about 2^-42 of each row
+            // and vector scale, which for long delocalised vectors reaches
+            // 1e-8 in norm).  The basis restarts from those vectors and
+            // products; a solve that is not yet converged finishes with FP64
+            // products (iterative refinement of the tensor-core solve).
+            ops.force_fp64 = true;
+            cudaMemcpyAsync(w->V, w->X, sizeof(double) * (size_t)nr * ld, cudaMemcpyDeviceToDevice, s);
+            ops.matvec(w->V, w->AV, nr, ld);
+            m = nr;
+            ops.gram(w->V, m, w->AV, m, ld, Tp);
+            cudaMemcpyAsync(w->AX, w->AV, sizeof(double) * (size_t)nr * ld, cudaMemcpyDeviceToDevice, s);
+            {
+                dim3 g((unsigned)((n + 255) / 256), nr);
+                residual_kernel<<<g, 256, 0, s>>>(w->AX, w->X, ld, w->theta, nr, n, w->AX);
+                ++ops.launches;
+            }
+            ops.gram(w->AX, nr, w->AX, nr, ld, RR);
+            which.clear();
+            maxres = 0.0;
+            for (int j = 0; j < nr; ++j) {
+                const double r = std::sqrt(std::max(0.0, RR[(size_t)j * nr + j]));
+                if (j < k) maxres = std::max(maxres, r);
+                if (r > tol) which.push_back(j);
+            }
+            done = true;
+            for (int j = 0; j < k; ++j)
+                if (std::sqrt(std::max(0.0, RR[(size_t)j * nr + j])) > tol) done = false;
+            ++refreshes;
+            if (done) { converged = true; break; }
+        }
         if (iter == max_iter) break;
         // corrections for the unconverged Ritz pairs (lowest first, at most b)
         if ((int)which.size() > b) which.resize(b);
@@ -950,6 +1042,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         st->ms_rr = (float)ops.ms_eigh;
         st->ms_gram = (float)ops.ms_gram;
         st->ms_combine = (float)ops.ms_combine;
+        st->fp64_iterations = fp64_iters;
         st->kernel_launches = ops.launches;
         st->mlp_fallbacks = fallbacks;
     }
@@ -962,7 +1055,8 @@ void hb::release_diag(hb_ctx *ctx) {
     if (!w) return;
     release_tensor_products(w);
     for (void *p : {(void *)w->V, (void *)w->AV, (void *)w->X, (void *)w->AX, (void *)w->W2, (void *)w->d, (void *)w->partial,
-                    (void *)w->small, (void *)w->proj, (void *)w->theta, (void *)w->idx, (void *)w->HlcT})
+                    (void *)w->small, (void *)w->proj, (void *)w->theta, (void *)w->idx, (void *)w->HlcT,
+                    (void *)w->XT})
         if (p) cudaFree(p);
     delete w;
     ctx->diag = nullptr;

@@ -277,7 +277,8 @@ void fill_tasks(Plan &p) {
             }
             p.asmb.add(ATask{P.gamma, P.S, P.E, P.sort_off, nc, P.same, P.nn, P.n_nn, A.ns, B.ns, ctx->n_to,
                              ctx->cont_spin, ctx->Kpad,
-                             ctx->e_core, P.A, p.precision == HB_MIXED ? P.A_df : nullptr},
+                             ctx->e_core, P.A, p.precision == HB_MIXED ? P.A_df : nullptr,
+                             ctx->energy ? ctx->energy + A.e_off : nullptr},
                        P.n_nn);
             p.flops += 2.0 * (double)A.cn * B.cn * P.n_nn * ctx->K;
             ++p.n_expand_tasks;

@@ -573,7 +573,8 @@ __global__ void gamma_warp_kernel(const GTask *__restrict__ tasks, const int64_t
 //   k <  Pt            : Gamma^(r>=s) = sum_spin gamma(r,s) + gamma(s,r) (r != s)
 //   Pt <= k < Pt+n_to^2: -gamma^{cont spin}(p, q)
 //   k == Pt+n_to^2     : S            (multiplies h_jj')
-//   k == Pt+n_to^2+1   : E + e_core S (multiplies delta_jj')
+//   k == Pt+n_to^2+1   : E + e_core S (multiplies delta_jj'); with the target-
+//                        energy substitution (Section 3.1) delta_gg' delta_nn' E_n
 //   k >= K             : 0
 // A key with no items was never written and reads as zero, except the
 // diagonal keys of a group with itself (written by the masked C^T C).
@@ -623,7 +624,7 @@ __global__ void assemble_kernel(const ATask *__restrict__ tasks, const int64_t *
             if (DF) { const float h = (float)T.S[sidx]; vh = h; vl = (float)(T.S[sidx] - (double)h); }
             else v = T.S[sidx];
         } else if (k == Pt + nt2 + 1) {
-            const double x = T.E[sidx] + T.e_core * T.S[sidx];
+            const double x = T.En ? ((T.same && n == np) ? T.En[n] : 0.0) : T.E[sidx] + T.e_core * T.S[sidx];
             if (DF) { const float h = (float)x; vh = h; vl = (float)(x - (double)h); }
             else v = x;
         }

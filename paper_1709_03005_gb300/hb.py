@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhb.so")
 
 class hb_group(C.Structure):
     _fields_ = [("n_det", C.c_int32), ("n_state", C.c_int32), ("dets", C.c_void_p), ("ci", C.c_void_p),
-                ("cont_first", C.c_int32), ("cont_count", C.c_int32)]
+                ("cont_first", C.c_int32), ("cont_count", C.c_int32), ("energy", C.c_void_p)]
 
 
 class hb_problem(C.Structure):
@@ -60,7 +60,7 @@ class hb_stats(C.Structure):
                 ("iterations", C.c_int32), ("mlp_fallbacks", C.c_int32), ("max_residual", C.c_double),
                 ("ms_matvec", C.c_float), ("ms_rr", C.c_float), ("expand_tensor_flops", C.c_double),
                 ("ms_gram", C.c_float), ("ms_combine", C.c_float), ("ms_class4_kernel", C.c_float),
-                ("reserved", C.c_int32 * 3)]
+                ("fp64_iterations", C.c_int32), ("reserved", C.c_int32 * 2)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -79,7 +79,7 @@ EXPORTS = ["hb_init", "hb_init_shared", "hb_batch_create", "hb_batch_launch", "h
            "hb_batch_destroy", "hb_query", "hb_group_offset", "hb_build_blocks", "hb_diag", "hb_classify",
            "hb_classify_noalloc", "hb_mlp_set", "hb_mlp_param_count", "hb_mlp_workspace_bytes", "hb_mlp_loss_grad",
            "hb_mlp_adam", "hb_mlp_train", "hb_mlp_predict", "hb_diag_features", "hb_batch_report", "hb_tuning_report",
-           "hb_dump",
+           "hb_dump", "hb_target_diag",
            "hb_last_error", "hb_destroy"]
 
 _lib = None
@@ -139,6 +139,54 @@ def _ptr(t):
 # the build
 # --------------------------------------------------------------------------
 
+def _marshal_problem(p, keep):
+    """hb_problem (and its hb_group array) for a problem object; the numpy
+    copies it points into are appended to `keep`."""
+    def arr(x, dt):
+        a = np.ascontiguousarray(x, dtype=dt)
+        keep.append(a)
+        return a
+
+    gs = (hb_group * max(1, len(p.groups)))()
+    for i, g in enumerate(p.groups):
+        d = arr(g.dets, np.uint64)
+        c = arr(g.ci, np.float64)
+        en = getattr(g, "energy", None)
+        e = arr(en, np.float64).ctypes.data if en is not None else None
+        gs[i] = hb_group(d.shape[0], c.shape[1], d.ctypes.data, c.ctypes.data, g.cont_first, g.cont_count, e)
+    ptr = lambda a: a.ctypes.data
+    l2 = arr(p.l2_dets, np.uint64) if p.l2_dets.shape[0] else None
+    prob = hb_problem(p.n_to, p.n_co, p.n_elec, p.n_words, p.cont_spin,
+                      ptr(arr(p.h, np.float64)), ptr(arr(p.eri_tttt, np.float64)),
+                      ptr(arr(p.eri_tttc, np.float64)), ptr(arr(p.eri_ttcc, np.float64)),
+                      ptr(arr(p.eri_tctc, np.float64)), len(p.groups), C.addressof(gs),
+                      p.l2_dets.shape[0], ptr(l2) if l2 is not None else None, float(p.e_core))
+    keep.append(gs)
+    return prob, gs
+
+
+def target_diag(problem, g, k, tol=1e-10, max_iter=400, stream=None):
+    """hb_target_diag: the lowest k eigenpairs of the N-electron target
+    Hamiltonian over group g's determinants.  Returns (energies [k],
+    ci [n_det, k], stats), ready for the group's `energy` and `ci`
+    (target-energy substitution)."""
+    import torch
+    lib = load()
+    lib.hb_target_diag.argtypes = [C.POINTER(hb_problem), C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                   C.c_void_p, C.c_void_p, C.POINTER(hb_stats), C.c_void_p]
+    lib.hb_target_diag.restype = C.c_int
+    torch.cuda.init()
+    keep = []
+    prob, _ = _marshal_problem(problem, keep)
+    nd = problem.groups[g].dets.shape[0] if 0 <= g < len(problem.groups) else 1   # the library checks g
+    en = np.zeros(k)
+    ci = np.zeros((nd, k))
+    st = hb_stats()
+    _check(lib.hb_target_diag(C.byref(prob), g, k, tol, max_iter, en.ctypes.data, ci.ctypes.data, C.byref(st),
+                              _stream_handle(stream)))
+    return en, ci, st
+
+
 class Hamiltonian:
     """A staged problem (hb_init) whose blocks can be built and diagonalised.
 
@@ -154,24 +202,7 @@ class Hamiltonian:
         self.base = base        # keeps a borrowed-integral base context alive
         p = problem
         keep = []
-
-        def arr(x, dt):
-            a = np.ascontiguousarray(x, dtype=dt)
-            keep.append(a)
-            return a
-
-        gs = (hb_group * max(1, len(p.groups)))()
-        for i, g in enumerate(p.groups):
-            d = arr(g.dets, np.uint64)
-            c = arr(g.ci, np.float64)
-            gs[i] = hb_group(d.shape[0], c.shape[1], d.ctypes.data, c.ctypes.data, g.cont_first, g.cont_count)
-        ptr = lambda a: a.ctypes.data
-        l2 = arr(p.l2_dets, np.uint64) if p.l2_dets.shape[0] else None
-        self._problem = hb_problem(p.n_to, p.n_co, p.n_elec, p.n_words, p.cont_spin,
-                                   ptr(arr(p.h, np.float64)), ptr(arr(p.eri_tttt, np.float64)),
-                                   ptr(arr(p.eri_tttc, np.float64)), ptr(arr(p.eri_ttcc, np.float64)),
-                                   ptr(arr(p.eri_tctc, np.float64)), len(p.groups), C.addressof(gs),
-                                   p.l2_dets.shape[0], ptr(l2) if l2 is not None else None, float(p.e_core))
+        self._problem, gs = _marshal_problem(p, keep)
         opts = hb_options(split_slices, 1 if validate else 0, 1 if autotune else 0, split_tile, class4_states,
                           class4_threads, class4_path)
         self.ctx = C.c_void_p()

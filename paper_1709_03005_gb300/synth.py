@@ -48,6 +48,7 @@ class Group:
     ci: np.ndarray          # (n_det, n_state) float64, row-major c[m, n]
     cont_first: int         # first continuum orbital (0-based within continuum)
     cont_count: int         # number of continuum orbitals coupled to this group
+    energy: np.ndarray | None = None   # target-state energies (target-energy substitution) or None
 
 
 @dataclass
@@ -266,6 +267,11 @@ CONFIGS = {
                n_state=50, n_l2=30000, rank=60, cont_diag=(0.0, 50.0)),
     "c5": dict(name="c5_learned", seed=5, n_to=40, n_co=400, n_elec=14, n_det=20000,
                n_state=50, n_l2=40000, rank=60, cont_diag=(0.0, 50.0)),
+    # the L2-heavy shape of the paper's H3PO4 run (Section 4.1): contracted
+    # dimension 712 (8 states x 89 continuum orbitals), 122103 L2 functions,
+    # dimension 122815; the L2 x L2 block holds about 3.8e8 entries
+    "h3po4": dict(name="l2_heavy_h3po4", seed=7, n_to=50, n_co=89, n_elec=14, n_det=2000, n_state=8,
+                  n_l2=122103, rank=60),
     # a mid-size case that spans several GPU tiles with ragged tails and that the
     # oracle builds in full within seconds
     "mid": dict(name="mid_ragged", seed=11, n_to=12, n_co=37, n_elec=6, n_det=300,

@@ -110,3 +110,41 @@ def l2_csr_cond(o, rp, cols, chunk=512):
         for a in range(a0, a1):
             out[rp[a]:rp[a + 1]] = S[a - a0, cols[rp[a]:rp[a + 1]]]
     return out
+
+
+def sampled_checks(P, o, cc, b, rng, precision, n_cc=400, n_rows=12, what=""):
+    """Sampled continuum elements, whole class-4 rows and whole L2 rows of the
+    built blocks b against the oracle.  Returns the fraction of sampled
+    continuum elements within 1e-10 of their own magnitude."""
+    mixed = precision == 1
+    rel = 1e-10 if mixed else 1e-12
+    ns, nco = P.groups[0].ci.shape[1], P.n_co
+    idx = [(int(n), int(j), int(n_), int(j if rng.random() < 0.1 else jp))
+           for n, n_, j, jp in zip(*[rng.integers(0, m, n_cc) for m in (ns, ns, nco, nco)])]
+    ref = np.array([cc.element(*t) for t in idx])
+    cond = np.array([cc.element_cond(*t) for t in idx])
+    Hcc = b["Hcc"]
+    got = np.array([float(Hcc[n * nco + j, n_ * nco + jp]) for n, j, n_, jp in idx])
+    bm = float(Hcc.abs().max())
+    _, _, n_canc, worst = check_elements(got, ref, cond, rel, MIXED_CC_FALLBACK if mixed else FP64_FALLBACK,
+                                         f"{what} cc sampled", blockmax=bm)
+    strict10 = float(np.mean(np.abs(got - ref) <= 1e-10 * np.abs(ref)))
+    print(f"{what}: {100 * strict10:.2f} % of sampled continuum elements within 1e-10 of their magnitude, "
+          f"{n_canc} by the cancellation clause, worst |d|/cond {worst:.2e}")
+    rows = np.sort(rng.choice(P.n_l2, n_rows, replace=False))
+    ref4 = np.stack([o.class4_row(int(l)) for l in rows])
+    cond4 = np.stack([o.class4_rows_abs(int(l), int(l) + 1)[0] for l in rows])
+    g4 = b["Hlc"][rows].cpu().numpy()
+    check_elements(g4, ref4, cond4, rel, MIXED_C4_FALLBACK if mixed else FP64_FALLBACK, f"{what} class 4 rows",
+                   blockmax=float(b["Hlc"].abs().max()), abs_frac=MIXED_C4_TC_ABS if mixed else None)
+    rp = b["row_ptr"].cpu().numpy()
+    for a in rng.choice(P.n_l2, n_rows, replace=False):
+        row = o.l2_rows(int(a), int(a) + 1)[0]
+        rcond = o.l2_rows_abs(int(a), int(a) + 1)[0]
+        cols = b["col"][rp[a]:rp[a + 1]].cpu().numpy()
+        vals = b["val"][rp[a]:rp[a + 1]].cpu().numpy()
+        dense = np.zeros(P.n_l2)
+        dense[cols] = vals
+        check_elements(dense, row, rcond, 1e-12, FP64_FALLBACK, f"{what} L2 row {a}")
+        assert set(cols.tolist()) >= set(np.nonzero(row)[0].tolist())
+    return strict10

@@ -289,3 +289,40 @@ def test_l2_block_is_symmetric(key):
     S = sp.csr_matrix((np.ones_like(vals), cols, rp), shape=(n, n))
     assert (S != S.T).nnz == 0
     assert abs(A - A.T).max() <= 1e-14 * np.abs(vals).max()
+
+
+def _target_hamiltonian(P, g):
+    """H^N + e_core over group g's determinants, by the oracle's Slater-Condon
+    evaluation of the L2-L2 elements (which takes any electron count)."""
+    import copy
+    Q = copy.copy(P)
+    Q.l2_dets = P.groups[g].dets
+    Q.groups = []
+    return coracle.Oracle(Q).l2_rows(0, Q.n_l2)
+
+
+@pytest.mark.parametrize("e_core", [0.0, -2.5])
+def test_target_energy_substitution_identity(e_core):
+    """Section 3.1: with CI vectors that are eigenvectors of H^N + e_core
+    (numpy eigh) the target-only part of every continuum element is
+    delta_nn' E_n, so the build with the target energies substituted equals the
+    plain build, whatever the integrals touching the continuum."""
+    P = synth.make_tiny(45, n_to=6, n_co=3, n_elec=4, n_det=14, n_state=3, n_l2=6, e_core=e_core)
+    HN = _target_hamiltonian(P, 0)
+    np.testing.assert_allclose(HN, HN.T, atol=1e-14)
+    E, V = np.linalg.eigh(HN)
+    P.groups[0].ci = np.ascontiguousarray(V[:, :3])
+    R = coracle.Oracle(P).dense()
+    P.groups[0].energy = E[:3].copy()
+    Rs = coracle.Oracle(P).dense()
+    np.testing.assert_allclose(Rs, R, rtol=0, atol=1e-12 * np.abs(R).max())
+    # with other energies only the delta_jj' delta_nn' diagonal of the continuum block moves
+    P.groups[0].energy = E[:3] + np.array([1.0, 2.0, 3.0])
+    Rt = coracle.Oracle(P).dense()
+    D = Rt - Rs
+    nco = P.n_co
+    expect = np.zeros_like(D)
+    for n in range(3):
+        for j in range(nco):
+            expect[n * nco + j, n * nco + j] = n + 1.0
+    np.testing.assert_allclose(D, expect, rtol=0, atol=1e-12 * np.abs(R).max())
