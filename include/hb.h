@@ -89,14 +89,29 @@ typedef struct hb_ctx hb_ctx;
    of the continuum-continuum block, <phi_gn|H^N + e_core|phi_g'n'>, is
    delta_gg' delta_nn' energy[n] instead of the Eq. 8 sum over the target-only
    integrals.  hb_target_diag returns such energies and CI vectors. */
+/* Spin-adapted groups (Eq. 2 with configuration state functions as the
+   eta_im): with n_csf > 0, CSF i is sum_k csf_coef[k] D[csf_det[k]] over
+   csf_ptr[i] <= k < csf_ptr[i+1] (determinants of this group's list) and ci
+   is [n_csf][n_state] over the CSFs.  hb_init expands the CI vectors over the
+   determinants on the device (one more contraction level ahead of Eq. 8).
+   Groups may share determinants only when they have the same determinant set
+   and the same continuum range and are adjacent in the list (for instance a
+   singlet and a triplet target over the same configurations, coupled to the
+   same continuum: classes 5 and 6 between target spins); the library builds
+   them as one group whose states are the groups' states in order, which is
+   the same row layout. */
 typedef struct {
     int32_t n_det;
     int32_t n_state;
     const uint64_t *dets;   /* host, [n_det][2*n_words] */
-    const double *ci;       /* host, [n_det][n_state], row-major */
+    const double *ci;       /* host, [n_det][n_state] (or [n_csf][n_state]), row-major */
     int32_t cont_first;
     int32_t cont_count;
     const double *energy;   /* host, [n_state], or NULL */
+    int32_t n_csf;          /* 0: ci is over the determinants */
+    const int32_t *csf_ptr; /* host, [n_csf + 1] (n_csf > 0) */
+    const int32_t *csf_det; /* host, [csf_ptr[n_csf]], indices into dets */
+    const double *csf_coef; /* host, [csf_ptr[n_csf]] */
 } hb_group;
 
 /* The problem of Eq. 1: orbitals, integrals, target groups, L2 functions.

@@ -30,6 +30,20 @@ import numpy as np
 from . import fock
 
 
+def det_ci(group) -> np.ndarray:
+    """CI vectors of a target group over its determinants: ci itself, or, for a
+    group given over configuration state functions, C_det[d, n] =
+    sum_i csf_coef(i, d) ci[i, n] (one more contraction level)."""
+    if getattr(group, "csf_ptr", None) is None:
+        return np.asarray(group.ci, np.float64)
+    ptr, det, coef = group.csf_ptr, group.csf_det, group.csf_coef
+    B = np.zeros((len(ptr) - 1, group.dets.shape[0]))
+    for i in range(len(ptr) - 1):
+        for k in range(ptr[i], ptr[i + 1]):
+            B[i, det[k]] += coef[k]
+    return B.T @ np.asarray(group.ci, np.float64)
+
+
 def uncontracted(problem):
     """(list of determinant tuples, T matrix) for a synth.Problem."""
     P = problem
@@ -44,12 +58,13 @@ def uncontracted(problem):
 
     cols = []
     for g in P.groups:
-        for n in range(g.ci.shape[1]):
+        ci = det_ci(g)
+        for n in range(ci.shape[1]):
             for j in range(g.cont_first, g.cont_first + g.cont_count):
                 col = {}
                 for m in range(g.dets.shape[0]):
                     d = fock.words_to_tuple(g.dets[m], W, n_orb, extra=[(sc, P.n_to + j)])
-                    col[add(d)] = col.get(add(d), 0.0) + g.ci[m, n]
+                    col[add(d)] = col.get(add(d), 0.0) + ci[m, n]
                 cols.append(col)
     for l in range(P.n_l2):
         d = fock.words_to_tuple(P.l2_dets[l], W, n_orb)
@@ -126,6 +141,7 @@ def symbolic_blocks(problem):
         for b, rb in enumerate(rows):
             if ra[0] == "c" and rb[0] == "c":
                 g, gp = P.groups[ra[1]], P.groups[rb[1]]
+                cg, cgp = det_ci(g), det_ci(gp)
                 n, j, n_, jp = ra[2], ra[3], rb[2], rb[3]
                 D = {}
                 f = 0.0
@@ -133,8 +149,8 @@ def symbolic_blocks(problem):
                     tk = terms_of(det_cj(gp, mp, jp))
                     for m in range(g.dets.shape[0]):
                         for lab, c in tk.get(det_cj(g, m, j), {}).items():
-                            D[lab] = D.get(lab, 0.0) + g.ci[m, n] * gp.ci[mp, n_] * c
-                            f += abs(g.ci[m, n] * gp.ci[mp, n_] * c * X(lab))
+                            D[lab] = D.get(lab, 0.0) + cg[m, n] * cgp[mp, n_] * c
+                            f += abs(cg[m, n] * cgp[mp, n_] * c * X(lab))
                 F[a, b] = f
                 tgt = sum(d * X(lab) for lab, d in D.items() if _is_target_only(lab, nt))
                 oth = [d * X(lab) for lab, d in D.items() if not _is_target_only(lab, nt)]
@@ -148,11 +164,12 @@ def symbolic_blocks(problem):
             else:
                 (cr, lr) = (ra, rb) if ra[0] == "c" else (rb, ra)
                 g, n, j = P.groups[cr[1]], cr[2], cr[3]
+                cg = det_ci(g)
                 tk = terms_of(fock.words_to_tuple(P.l2_dets[lr[1]], W, n_orb))
                 v = s = 0.0
                 for m in range(g.dets.shape[0]):
                     for lab, c in tk.get(det_cj(g, m, j), {}).items():
-                        x = g.ci[m, n] * c * X(lab)
+                        x = cg[m, n] * c * X(lab)
                         v += x
                         s += abs(x)
                 V[a, b], S[a, b], F[a, b] = v, s, s

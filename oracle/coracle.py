@@ -91,6 +91,12 @@ def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
 
 
+def _det_ci(group) -> np.ndarray:
+    """The group's CI vectors over its determinants (CSF groups expanded)."""
+    from .brute import det_ci
+    return det_ci(group)
+
+
 class Oracle:
     """Holds a synth.Problem in the C oracle's layout (keeps arrays alive)."""
 
@@ -111,7 +117,7 @@ class Oracle:
         self.g_cfirst = arr([g.cont_first for g in gs], np.int32)
         self.g_ccount = arr([g.cont_count for g in gs], np.int32)
         dets = [arr(g.dets, np.uint64) for g in gs]
-        cis = [arr(g.ci, np.float64) for g in gs]
+        cis = [arr(_det_ci(g), np.float64) for g in gs]
         self.g_dets = arr([_ptr(d) for d in dets], np.uint64)
         self.g_ci = arr([_ptr(c) for c in cis], np.uint64)
         h = arr(P.h, np.float64)

@@ -173,3 +173,27 @@ def label_value(label: tuple, h: np.ndarray, eri: np.ndarray, e_core: float = 0.
     if label[0] == "h":
         return h[label[1], label[2]]
     return eri[label[1], label[2], label[3], label[4]]
+
+
+def apply_s2(det: tuple, n_orb: int) -> dict:
+    """S^2 |det> as {det': coefficient}, by S^2 = S- S+ + Sz (Sz + 1) with
+    S+ = sum_p a+_{p alpha} a_{p beta} (spin orbital s * n_orb + p)."""
+    out = defaultdict(float)
+    na = sum(1 for so in det if so < n_orb)
+    sz = 0.5 * (na - (len(det) - na))
+    out[det] += sz * (sz + 1.0)
+    for p in range(n_orb):
+        s1, d1 = annihilate(det, n_orb + p)
+        if not s1:
+            continue
+        s2, d2 = create(d1, p)
+        if not s2:
+            continue
+        for q in range(n_orb):
+            s3, d3 = annihilate(d2, q)
+            if not s3:
+                continue
+            s4, d4 = create(d3, n_orb + q)
+            if s4:
+                out[d4] += s1 * s2 * s3 * s4
+    return out

@@ -190,7 +190,9 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
             if (a != na || b != nb)
                 return fail(ctx, HB_ERR_INVALID_ARG, "target determinants differ in Ms (one spin coupling per problem)");
             if (!seen.insert(std::vector<uint64_t>(d, d + nw)).second)
-                return fail(ctx, HB_ERR_INVALID_ARG, "duplicate target determinant (groups must be disjoint)");
+                return fail(ctx, HB_ERR_INVALID_ARG, "duplicate target determinant (groups that share determinants "
+                                                     "must have the same determinant set and continuum range and be "
+                                                     "adjacent)");
         }
     }
     seen.clear();
@@ -239,13 +241,39 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
     return HB_OK;
 }
 
+// Validate and stage a problem; groups given over CSFs or sharing their
+// determinants go through the merged-group plan (k_csf.cu) first.
+static int init_context(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStream_t s) {
+    GroupPlan plan;
+    std::string err;
+    int rc = prepare_groups(p, &plan, &err);
+    if (rc != HB_OK) return fail(ctx, rc, err);
+    if (!plan.needed) {
+        rc = validate_problem(ctx, p, o);
+        if (rc == HB_OK) rc = stage_problem(ctx, p, o, s);
+        return rc;
+    }
+    hb_problem q = *p;
+    q.n_groups = (int32_t)plan.groups.size();
+    q.groups = plan.groups.data();
+    rc = validate_problem(ctx, &q, o);
+    if (rc == HB_OK) rc = stage_problem(ctx, &q, o, s);
+    if (rc != HB_OK) return rc;
+    rc = expand_group_ci(ctx, plan, s, &err);
+    if (rc != HB_OK) return fail(ctx, rc, err);
+    ctx->user_row_off.resize(plan.user_of.size());
+    for (size_t g = 0; g < plan.user_of.size(); ++g) {
+        const GroupInfo &gi = ctx->groups[plan.user_of[g].first];
+        ctx->user_row_off[g] = gi.row_off + (int64_t)plan.user_of[g].second * gi.cn;
+    }
+    return HB_OK;
+}
+
 extern "C" int hb_init(hb_ctx **out, const hb_problem *p, const hb_options *o, void *stream) {
     if (!out) return fail(nullptr, HB_ERR_INVALID_ARG, "ctx pointer is NULL");
     *out = nullptr;
     hb_ctx *ctx = new hb_ctx();
-    int rc = validate_problem(ctx, p, o);
-    if (rc != HB_OK) { g_last_error = ctx->err; delete ctx; return rc; }
-    rc = stage_problem(ctx, p, o, (cudaStream_t)stream);
+    int rc = init_context(ctx, p, o, (cudaStream_t)stream);
     if (rc != HB_OK) { g_last_error = ctx->err; hb_destroy(ctx); return rc; }
     *out = ctx;
     return HB_OK;
@@ -259,9 +287,7 @@ extern "C" int hb_init_shared(hb_ctx **out, const hb_problem *p, const hb_option
         return fail(nullptr, HB_ERR_INVALID_ARG, "problem orbitals differ from the base context");
     hb_ctx *ctx = new hb_ctx();
     ctx->base = base;
-    int rc = validate_problem(ctx, p, o);
-    if (rc != HB_OK) { g_last_error = ctx->err; delete ctx; return rc; }
-    rc = stage_problem(ctx, p, o, (cudaStream_t)stream);
+    int rc = init_context(ctx, p, o, (cudaStream_t)stream);
     if (rc != HB_OK) { g_last_error = ctx->err; hb_destroy(ctx); return rc; }
     *out = ctx;
     return HB_OK;
@@ -494,7 +520,13 @@ extern "C" int hb_query(const hb_ctx *ctx, hb_layout *out) {
 }
 
 extern "C" int64_t hb_group_offset(const hb_ctx *ctx, int32_t g) {
-    if (!ctx || g < 0 || g > ctx->n_groups) return -1;
+    if (!ctx || g < 0) return -1;
+    if (!ctx->user_row_off.empty()) {
+        const int32_t n = (int32_t)ctx->user_row_off.size();
+        if (g > n) return -1;
+        return g == n ? ctx->Dc : ctx->user_row_off[g];
+    }
+    if (g > ctx->n_groups) return -1;
     return g == ctx->n_groups ? ctx->Dc : ctx->groups[g].row_off;
 }
 

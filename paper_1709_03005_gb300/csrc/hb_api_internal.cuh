@@ -6,6 +6,8 @@
 
 #include "hb_internal.cuh"
 
+struct hb_ctx;
+
 namespace hb {
 
 struct GroupInfo {
@@ -44,6 +46,28 @@ struct GroupL2 {
 
 struct MixedState;   // split-precision operands (k_split.cu)
 
+// Target groups as the build sees them when some groups are given over CSFs
+// or share their determinants (k_csf.cu): merged groups with zeroed host CI
+// (validated and staged like any group) and, per input group, the
+// determinant -> (CSF, coefficient) lists that fill its columns of the merged
+// group's CI on the device.
+struct GroupPlan {
+    bool needed = false;
+    std::vector<hb_group> groups;                 // the merged groups
+    std::vector<std::vector<double>> zero_ci, energy;
+    struct Member {
+        int internal = 0, col_off = 0, ns = 0, n_csf = 0;
+        const double *ci = nullptr;               // host [n_csf][ns]
+        std::vector<int64_t> dptr;                // [n_det + 1] over the merged determinant order
+        std::vector<int32_t> dcsf;
+        std::vector<double> dcoef;
+    };
+    std::vector<Member> members;
+    std::vector<std::pair<int, int>> user_of;     // input group -> (merged group, first state)
+};
+int prepare_groups(const hb_problem *p, GroupPlan *out, std::string *err);
+int expand_group_ci(hb_ctx *ctx, const GroupPlan &plan, cudaStream_t s, std::string *err);
+
 }  // namespace hb
 
 struct hb_ctx {
@@ -69,6 +93,8 @@ struct hb_ctx {
     // target-energy substitution (Section 3.1): every group's state energies,
     // or null when the target-only part is the Eq. 8 sum
     double *energy = nullptr;
+    // first row of each input group when groups were merged (empty otherwise)
+    std::vector<int64_t> user_row_off;
     // double-float (hi, lo) copies for the mixed class-4 kernel, made on first use
     float2 *tttc_df = nullptr, *h_df = nullptr, *ci_df = nullptr, *tttt_df = nullptr, *jk_df = nullptr;
     int64_t *l2_rowptr = nullptr;

@@ -24,7 +24,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhb.so")
 
 class hb_group(C.Structure):
     _fields_ = [("n_det", C.c_int32), ("n_state", C.c_int32), ("dets", C.c_void_p), ("ci", C.c_void_p),
-                ("cont_first", C.c_int32), ("cont_count", C.c_int32), ("energy", C.c_void_p)]
+                ("cont_first", C.c_int32), ("cont_count", C.c_int32), ("energy", C.c_void_p),
+                ("n_csf", C.c_int32), ("csf_ptr", C.c_void_p), ("csf_det", C.c_void_p), ("csf_coef", C.c_void_p)]
 
 
 class hb_problem(C.Structure):
@@ -153,7 +154,13 @@ def _marshal_problem(p, keep):
         c = arr(g.ci, np.float64)
         en = getattr(g, "energy", None)
         e = arr(en, np.float64).ctypes.data if en is not None else None
-        gs[i] = hb_group(d.shape[0], c.shape[1], d.ctypes.data, c.ctypes.data, g.cont_first, g.cont_count, e)
+        cp = getattr(g, "csf_ptr", None)
+        if cp is not None:
+            cp, cd, cc = arr(cp, np.int32), arr(g.csf_det, np.int32), arr(g.csf_coef, np.float64)
+            csf = (cp.shape[0] - 1, cp.ctypes.data, cd.ctypes.data, cc.ctypes.data)
+        else:
+            csf = (0, None, None, None)
+        gs[i] = hb_group(d.shape[0], c.shape[1], d.ctypes.data, c.ctypes.data, g.cont_first, g.cont_count, e, *csf)
     ptr = lambda a: a.ctypes.data
     l2 = arr(p.l2_dets, np.uint64) if p.l2_dets.shape[0] else None
     prob = hb_problem(p.n_to, p.n_co, p.n_elec, p.n_words, p.cont_spin,

@@ -49,6 +49,12 @@ class Group:
     cont_first: int         # first continuum orbital (0-based within continuum)
     cont_count: int         # number of continuum orbitals coupled to this group
     energy: np.ndarray | None = None   # target-state energies (target-energy substitution) or None
+    # configuration state functions: CSF i = sum_k csf_coef[k] dets[csf_det[k]] for
+    # csf_ptr[i] <= k < csf_ptr[i+1]; when given, ci is over the CSFs ([n_csf, n_state])
+    csf_ptr: np.ndarray | None = None
+    csf_det: np.ndarray | None = None
+    csf_coef: np.ndarray | None = None
+    spin: float | None = None           # total spin of the group's CSFs (information only)
 
 
 @dataclass
@@ -408,3 +414,120 @@ def make_batched_family(seed=4, n_hams=16, n_to=40, cont_per_irrep=(20, 60), n_e
                                 meta=dict(seed=seed, gamma=gam, spin=spin, target_dim=target,
                                           orb_irrep=orb_irrep)))
     return problems
+
+
+# --------------------------------------------------------------------------
+# spin-adapted target groups: configuration state functions (CSFs)
+# --------------------------------------------------------------------------
+
+def _fermion_apply(occ: tuple, ops):
+    """Apply operators ((+1 create | -1 annihilate), spin orbital) right to
+    left to the sorted spin-orbital tuple occ; returns (sign, tuple) or
+    (0, None).  Input generation only (spin eigenfunctions)."""
+    sign, cur = 1, list(occ)
+    for kind, so in reversed(ops):
+        i = 0
+        while i < len(cur) and cur[i] < so:
+            i += 1
+        present = i < len(cur) and cur[i] == so
+        if kind < 0:
+            if not present:
+                return 0, None
+            del cur[i]
+        else:
+            if present:
+                return 0, None
+            cur.insert(i, so)
+        sign *= -1 if i % 2 else 1
+    return sign, tuple(cur)
+
+
+def spin_eigenfunctions(alpha_occ_list, beta_occ_list, n_orb):
+    """S^2 within the determinants of one spatial configuration (fixed Ms):
+    returns (S values, eigenvectors as columns) with S from S(S+1).
+    Determinants are alpha string then beta string in the canonical order of
+    the input format (spin orbital s*n_orb + p, alpha first)."""
+    dets = [tuple(sorted(list(a) + [n_orb + p for p in b])) for a, b in zip(alpha_occ_list, beta_occ_list)]
+    index = {d: i for i, d in enumerate(dets)}
+    n = len(dets)
+    S2 = np.zeros((n, n))
+    for j, d in enumerate(dets):
+        na = sum(1 for so in d if so < n_orb)
+        nb = len(d) - na
+        sz = 0.5 * (na - nb)
+        S2[j, j] += sz * sz + sz
+        # S- S+ = sum_{p,q} a+_{q beta} a_{q alpha} a+_{p alpha} a_{p beta}
+        for p in range(n_orb):
+            for q in range(n_orb):
+                sg, d2 = _fermion_apply(d, [(+1, n_orb + q), (-1, q), (+1, p), (-1, n_orb + p)])
+                if sg and d2 in index:
+                    S2[index[d2], j] += sg
+    w, V = np.linalg.eigh(0.5 * (S2 + S2.T))
+    S = 0.5 * (np.sqrt(np.maximum(4.0 * w + 1.0, 0.0)) - 1.0)
+    return np.round(S * 2.0) / 2.0, V
+
+
+def make_csf_problem(seed=12, n_to=8, n_co=6, n_elec=4, n_config=10, n_state=(2, 2), spins=(0.0, 1.0),
+                     n_l2=12, rank=8, keep_chol=True):
+    """Target groups given over configuration state functions: for each total
+    spin S in `spins`, a group whose states are random orthonormal
+    combinations of the CSFs of spin S built on the same sampled spatial
+    configurations (singles and doubles of the closed-shell reference, all
+    Ms = 0 determinants of each).  The groups share their determinant list
+    and their continuum range: singlet and triplet targets coupled to the
+    same continuum (classes 5 and 6 between target spins).  Each group carries
+    csf_ptr, csf_det, csf_coef (CSF i = sum_k csf_coef[k] D[csf_det[k]] over
+    csf_ptr[i] <= k < csf_ptr[i+1]) and ci over its CSFs."""
+    rng = np.random.default_rng(seed)
+    W = max(1, (n_to + 63) // 64)
+    half = n_elec // 2
+    h = make_h(rng, n_to, n_co)
+    L = make_chol(rng, n_to + n_co, rank)
+    eri = eri_classes(L, n_to, n_co)
+    pool = sd_pool(half, n_elec - half, n_to)
+    configs = {}
+    for a, b in pool:
+        docc = tuple(sorted(set(a) & set(b)))
+        socc = tuple(sorted(set(a) ^ set(b)))
+        configs.setdefault((docc, socc), None)
+    keys = list(configs)
+    pick = [0] + list(1 + rng.choice(len(keys) - 1, min(n_config, len(keys)) - 1, replace=False))
+    dets, csfs = [], {S: [] for S in spins}
+    for ci_ in pick:
+        docc, socc = keys[ci_]
+        k = len(socc)
+        n_open_a = (k + (half - (n_elec - half))) // 2
+        alist, blist = [], []
+        for up in itertools.combinations(socc, n_open_a):
+            a = tuple(sorted(docc + up))
+            b = tuple(sorted(docc + tuple(o for o in socc if o not in up)))
+            alist.append(a)
+            blist.append(b)
+        base = len(dets)
+        for a, b in zip(alist, blist):
+            dets.append(occ_to_words(a, b, W))
+        Svals, V = spin_eigenfunctions(alist, blist, n_to)
+        for c in range(V.shape[1]):
+            if Svals[c] in csfs:
+                idx = [base + i for i in range(len(alist)) if abs(V[i, c]) > 1e-12]
+                csfs[Svals[c]].append((idx, [V[i - base, c] for i in idx]))
+    dets = np.stack(dets)
+    groups = []
+    for g, S in enumerate(spins):
+        lst = csfs[S]
+        ns = n_state[g] if isinstance(n_state, (list, tuple)) else n_state
+        if len(lst) < ns:
+            raise ValueError(f"only {len(lst)} CSFs of spin {S}")
+        ptr = np.zeros(len(lst) + 1, np.int32)
+        for i, (idx, _) in enumerate(lst):
+            ptr[i + 1] = ptr[i] + len(idx)
+        cdet = np.concatenate([np.asarray(i, np.int32) for i, _ in lst])
+        coef = np.concatenate([np.asarray(c, np.float64) for _, c in lst])
+        groups.append(Group(dets.copy(), orthonormal_ci(rng, len(lst), ns), 0, n_co, csf_ptr=ptr, csf_det=cdet,
+                            csf_coef=coef, spin=S))
+    l2pool = sd_pool(half + 1, n_elec - half, n_to)
+    l2, _ = sample_dets(rng, l2pool, n_l2, W) if n_l2 > 0 else (np.zeros((0, 2 * W), np.uint64), None)
+    return Problem(name=f"csf{seed}", n_to=n_to, n_co=n_co, n_elec=n_elec, n_words=W, cont_spin=ALPHA, h=h,
+                   eri_tttt=eri[0], eri_tttc=eri[1], eri_ttcc=eri[2], eri_tctc=eri[3], groups=groups,
+                   l2_dets=np.ascontiguousarray(l2), chol=L if keep_chol else None,
+                   meta=dict(seed=seed, rank=rank, spins=list(spins)))
