@@ -153,6 +153,7 @@ typedef struct {
     int64_t device_bytes;     /* device memory held by the context */
     int32_t n_groups;
     int32_t n_words;
+    int64_t workspace_bytes;  /* the last hb_workspace_size result (0 before the first call) */
 } hb_layout;
 
 typedef struct {
@@ -187,7 +188,8 @@ typedef struct {
     float ms_combine;         /* hb_diag: basis combinations (coefficients to the device, kernel) */
     float ms_class4_kernel;   /* the class-4 kernels after their classification (part of ms_class4) */
     int32_t fp64_iterations;  /* hb_diag: iterations with FP64 products after the convergence check */
-    int32_t reserved[2];
+    float mlp_loss;           /* hb_mlp_train: loss of the last window */
+    int32_t reserved[1];
 } hb_stats;
 
 /* Excitation record of one determinant pair (row, col), see hb_classify. */
@@ -212,6 +214,34 @@ int hb_init(hb_ctx **ctx, const hb_problem *p, const hb_options *o, void *stream
 
 /* Sizes of the result and of the context (Section 2.2 classes). */
 int hb_query(const hb_ctx *ctx, hb_layout *out);
+
+/* Caller-owned workspace (no counterpart in the paper).  hb_init allocates
+   the staged problem (integrals, determinants, CI vectors, the expansion
+   panel and the per-group-pair buffers whose sizes come from its
+   classification pass; hb_layout.device_bytes).  Everything a build or a
+   solve sets up after that (the build plan, the double-float copies, the
+   tensor-core slices and class-4 tables, the Davidson vectors and scratch,
+   the learned factors) is allocated on first use with cudaMalloc, or, once a
+   workspace is set, carved out of it: builds and solves then allocate no
+   device memory.
+
+   hb_workspace_size measures the bytes: the build set-up for `precision`
+   (HB_FP64, HB_MIXED, or -1 for none) is made once under a byte count and
+   released, and the solver's bytes for diag_k eigenpairs (0: none) with the
+   given precond flags (HB_DIAG_TENSOR, HB_PRECOND_MLP) are added; the result
+   includes 16 MiB and 1.6 % for the autotuner's timing buffers and alignment.
+   It is also reported as hb_layout.workspace_bytes.  It must be called before
+   hb_set_workspace; it synchronises `stream`.
+
+   hb_set_workspace gives the context a device buffer of `bytes` bytes that the
+   caller owns and keeps alive until hb_destroy (or until the context is no
+   longer used).  Whatever a previous build or solve had set up is released
+   first.  A build or solve whose set-up does not fit returns HB_ERR_OOM.  A
+   workspace can be set once per context.  Errors: HB_ERR_INVALID_ARG (NULL,
+   a workspace already set), HB_ERR_CUDA. */
+int hb_workspace_size(hb_ctx *ctx, int32_t precision, int32_t diag_k, int32_t precond, int64_t *bytes,
+                      void *stream);
+int hb_set_workspace(hb_ctx *ctx, void *dev_ptr, size_t bytes);
 
 /* First row of target group g in the contracted basis. */
 int64_t hb_group_offset(const hb_ctx *ctx, int32_t g);
@@ -364,14 +394,32 @@ int hb_mlp_loss_grad(const float *params, const float *feats, const float *a, co
 int hb_mlp_adam(int64_t n_param, float *params, const float *grads, float *m, float *v, int32_t step,
                 float lr, void *stream);
 
-/* Adam training of the packed parameters (device, in place) on a device data
-   set feats [n][8], a [n], b [n] (loss of hb_mlp_loss_grad): `steps` updates,
-   each over the next window of `batch` samples (wrapping around), learning
-   rate lr; the last window's loss into *last_loss (host, may be NULL).  The
-   scratch is allocated and freed by the call.  Errors: HB_ERR_INVALID_ARG,
-   HB_ERR_OOM, HB_ERR_CUDA.  Not in the paper: the learned preconditioner. */
-int hb_mlp_train(float *params, const float *feats, const float *a, const float *b, int64_t n, int64_t batch,
-                 int32_t steps, float lr, float *last_loss, void *stream);
+/* A training set of the learned preconditioner (device arrays): features
+   feats [n][8], targets a [n], b [n] (loss of hb_mlp_loss_grad), and the
+   schedule: `steps` Adam updates (learning rate lr), each over the next window
+   of `batch` samples, wrapping around. */
+typedef struct {
+    int64_t n;
+    const float *feats;
+    const float *a, *b;
+    int64_t batch;
+    int32_t steps;
+    float lr;
+} hb_mlp_dataset;
+
+/* Adam training of the packed parameters `params` (device, in place) on the
+   data set d; the trained network then becomes the context's preconditioner
+   network (as hb_mlp_set).  Scratch comes from the context's memory (its
+   workspace when one is set).  st (or NULL): iterations = steps, mlp_loss =
+   the last window's loss.  Errors: HB_ERR_INVALID_ARG, HB_ERR_OOM, HB_ERR_CUDA.
+   Not in the paper: the learned preconditioner. */
+int hb_mlp_train(hb_ctx *ctx, const hb_mlp_dataset *d, float *params, hb_stats *st, void *stream);
+
+/* The same loop without a context: params (device, in place), the data set as
+   arrays, the last window's loss into *last_loss (host, may be NULL); the
+   scratch is allocated and freed by the call. */
+int hb_mlp_train_params(float *params, const float *feats, const float *a, const float *b, int64_t n,
+                        int64_t batch, int32_t steps, float lr, float *last_loss, void *stream);
 
 /* Factors w(f_i) for n feature rows (device). */
 int hb_mlp_predict(const float *params, const float *feats, int64_t n, float *out, void *stream);

@@ -59,12 +59,70 @@ bool all_finite(const double *x, size_t n) {
         if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call);         \
     } while (0)
 
+namespace hb {
+
+cudaError_t dmalloc(hb_ctx *ctx, void **p, size_t bytes) {
+    *p = nullptr;
+    DevPool &P = ctx->pool;
+    bytes = (bytes + 255) / 256 * 256;
+    if (bytes == 0) bytes = 256;
+    if (P.base) {
+        auto it = P.free_blocks.begin();
+        while (it != P.free_blocks.end() && it->second < bytes) ++it;
+        if (it == P.free_blocks.end()) return cudaErrorMemoryAllocation;
+        const size_t off = it->first, len = it->second;
+        P.free_blocks.erase(it);
+        if (len > bytes) P.free_blocks[off + bytes] = len - bytes;
+        *p = P.base + off;
+    } else {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    P.live[*p] = bytes;
+    P.live_bytes += bytes;
+    P.peak_bytes = std::max(P.peak_bytes, P.live_bytes);
+    return cudaSuccess;
+}
+
+void dfree(hb_ctx *ctx, void *p) {
+    if (!p) return;
+    DevPool &P = ctx->pool;
+    auto it = P.live.find(p);
+    const size_t bytes = it == P.live.end() ? 0 : it->second;
+    if (it != P.live.end()) {
+        P.live.erase(it);
+        P.live_bytes -= bytes;
+    }
+    uint8_t *q = (uint8_t *)p;
+    if (P.base && q >= P.base && q < P.base + P.size) {
+        size_t off = (size_t)(q - P.base), len = bytes;
+        auto next = P.free_blocks.lower_bound(off);
+        if (next != P.free_blocks.end() && next->first == off + len) {
+            len += next->second;
+            next = P.free_blocks.erase(next);
+        }
+        if (next != P.free_blocks.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                off = prev->first;
+                len += prev->second;
+                P.free_blocks.erase(prev);
+            }
+        }
+        P.free_blocks[off] = len;
+    } else {
+        cudaFree(p);
+    }
+}
+
+}  // namespace hb
+
 template <class T>
 static int dalloc(hb_ctx *ctx, T **p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * n);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    cudaError_t e = hb::dmalloc_n(ctx, p, n);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device allocation");
     ctx->allocs.push_back(*p);
     ctx->dev_bytes += sizeof(T) * n;
     return HB_OK;
@@ -251,6 +309,7 @@ static int init_context(hb_ctx *ctx, const hb_problem *p, const hb_options *o, c
     if (!plan.needed) {
         rc = validate_problem(ctx, p, o);
         if (rc == HB_OK) rc = stage_problem(ctx, p, o, s);
+        ctx->pool.init_allocs = ctx->allocs.size();
         return rc;
     }
     hb_problem q = *p;
@@ -266,6 +325,7 @@ static int init_context(hb_ctx *ctx, const hb_problem *p, const hb_options *o, c
         const GroupInfo &gi = ctx->groups[plan.user_of[g].first];
         ctx->user_row_off[g] = gi.row_off + (int64_t)plan.user_of[g].second * gi.cn;
     }
+    ctx->pool.init_allocs = ctx->allocs.size();
     return HB_OK;
 }
 
@@ -514,6 +574,7 @@ extern "C" int hb_query(const hb_ctx *ctx, hb_layout *out) {
     out->tl2_pairs = ctx->tl2_pairs;
     out->n_labels = ctx->K;
     out->device_bytes = (int64_t)ctx->dev_bytes;
+    out->workspace_bytes = ctx->pool.measured;
     out->n_groups = ctx->n_groups;
     out->n_words = ctx->W;
     return HB_OK;
@@ -643,6 +704,57 @@ extern "C" int hb_target_diag(const hb_problem *p, int32_t g, int32_t k, double 
     return rc;
 }
 
+extern "C" int hb_workspace_size(hb_ctx *ctx, int32_t precision, int32_t diag_k, int32_t precond, int64_t *bytes,
+                                 void *stream) {
+    if (!ctx || !bytes) return fail(ctx, HB_ERR_INVALID_ARG, "NULL argument");
+    if (precision != HB_FP64 && precision != HB_MIXED && precision != -1)
+        return fail(ctx, HB_ERR_INVALID_ARG, "precision must be HB_FP64, HB_MIXED or -1 (no build)");
+    if (diag_k < 0) return fail(ctx, HB_ERR_INVALID_ARG, "diag_k < 0");
+    if (ctx->pool.base) return fail(ctx, HB_ERR_INVALID_ARG, "a workspace is already set");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    // measure from nothing: the build's own set-up (plan, double-float copies,
+    // tensor-core slices and tables) runs under the byte count, then goes again
+    release_lazy(ctx);
+    const size_t live0 = ctx->pool.live_bytes;
+    ctx->pool.peak_bytes = live0;
+    if (precision != -1) {
+        hb_blocks none{};
+        hb_ctx *one[1] = {ctx};
+        hb::Plan *plan = nullptr;
+        std::string err;
+        int rc = plan_create(one, 1, &none, precision, &plan, &err, s);
+        if (rc != HB_OK) { release_lazy(ctx); return fail(ctx, rc, err); }
+        cudaStreamSynchronize(s);
+        plan_destroy(plan);
+    }
+    // the build's set-up stays while a solve runs, so the two add up
+    int64_t need = (int64_t)(ctx->pool.peak_bytes - live0);
+    release_lazy(ctx);
+    if (diag_k > 0) need += diag_workspace_bytes(ctx, diag_k, precond);
+    // the autotuner's timing buffers and the allocator's alignment
+    need += (16 << 20) + need / 64;
+    ctx->pool.measured = need;
+    *bytes = need;
+    return HB_OK;
+}
+
+extern "C" int hb_set_workspace(hb_ctx *ctx, void *dev_ptr, size_t bytes) {
+    if (!ctx || !dev_ptr || bytes < 256) return fail(ctx, HB_ERR_INVALID_ARG, "NULL or empty workspace");
+    if (ctx->pool.base) return fail(ctx, HB_ERR_INVALID_ARG, "a workspace is already set");
+    CK(cudaSetDevice(ctx->device));
+    // what a previous build or solve set up with cudaMalloc goes; it is made
+    // again inside the workspace on next use
+    release_lazy(ctx);
+    const uintptr_t a = (uintptr_t)dev_ptr, a256 = (a + 255) / 256 * 256;
+    if (a256 - a >= bytes) return fail(ctx, HB_ERR_INVALID_ARG, "workspace too small");
+    ctx->pool.base = (uint8_t *)a256;
+    ctx->pool.size = (bytes - (a256 - a)) / 256 * 256;
+    ctx->pool.free_blocks.clear();
+    ctx->pool.free_blocks[0] = ctx->pool.size;
+    return HB_OK;
+}
+
 extern "C" int hb_classify(const uint64_t *a, int32_t n_a, const uint64_t *b, int32_t n_b, int32_t n_words,
                            int32_t mode, int32_t cont_spin, int32_t max_degree, int32_t lower, int64_t *row_ptr,
                            hb_pair *pairs, int64_t cap, int64_t *total, void *stream) {
@@ -705,9 +817,27 @@ extern "C" const char *hb_last_error(const hb_ctx *ctx) {
     return ctx ? ctx->err.c_str() : g_last_error.c_str();
 }
 
+void hb::release_lazy(hb_ctx *ctx) {
+    if (ctx->plan) {
+        cudaDeviceSynchronize();
+        plan_destroy((hb::Plan *)ctx->plan);
+        ctx->plan = nullptr;
+    }
+    release_mixed(ctx);
+    hb::release_c4tc(ctx);
+    hb::release_diag(ctx);
+    // the double-float copies (ensure_df) are the allocations after hb_init's
+    const size_t n0 = ctx->pool.init_allocs;
+    if (ctx->allocs.size() > n0) {
+        for (size_t i = n0; i < ctx->allocs.size(); ++i) hb::dfree(ctx, ctx->allocs[i]);
+        ctx->allocs.resize(n0);
+        ctx->tttc_df = ctx->h_df = ctx->ci_df = ctx->tttt_df = ctx->jk_df = nullptr;
+        for (auto &P : ctx->gps) P.A_df = nullptr;
+    }
+}
+
 extern "C" void hb_destroy(hb_ctx *ctx) {
     if (!ctx) return;
-    for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->plan) {
         cudaDeviceSynchronize();
         plan_destroy((hb::Plan *)ctx->plan);
@@ -717,5 +847,6 @@ extern "C" void hb_destroy(hb_ctx *ctx) {
     hb::release_c4tc(ctx);
     hb::release_diag(ctx);
     hb::release_mlp(ctx);
+    for (void *p : ctx->allocs) hb::dfree(ctx, p);
     delete ctx;
 }

@@ -1,7 +1,9 @@
 // The context behind the C ABI (host side).
 #pragma once
 
+#include <map>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "hb_internal.cuh"
@@ -45,6 +47,34 @@ struct GroupL2 {
 };
 
 struct MixedState;   // split-precision operands (k_split.cu)
+
+// Device memory a context takes after hb_init (build plans, tensor-core
+// slices and tables, double-float copies, solver scratch): cudaMalloc, or,
+// once the caller has given a workspace (hb_set_workspace), first-fit blocks of
+// that buffer, 256-byte aligned, with freed blocks merged with their free
+// neighbours.  Every block is recorded with its size, so the bytes a build or
+// a solve needs can be measured (hb_workspace_size).
+struct DevPool {
+    uint8_t *base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_blocks;        // offset -> bytes
+    std::unordered_map<void *, size_t> live;     // block -> bytes (both modes)
+    size_t live_bytes = 0, peak_bytes = 0;
+    size_t init_allocs = 0;                      // hb_ctx::allocs made by hb_init
+    int64_t measured = 0;                        // the last hb_workspace_size result
+};
+cudaError_t dmalloc(hb_ctx *ctx, void **p, size_t bytes);
+void dfree(hb_ctx *ctx, void *p);
+template <class T>
+cudaError_t dmalloc_n(hb_ctx *ctx, T **p, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = dmalloc(ctx, &q, sizeof(T) * (n ? n : 1));
+    *p = (T *)q;
+    return e;
+}
+// Drop the build plan, tensor-core operands, double-float copies and solver
+// scratch of a context (they are made again on next use).
+void release_lazy(hb_ctx *ctx);
 
 // Target groups as the build sees them when some groups are given over CSFs
 // or share their determinants (k_csf.cu): merged groups with zeroed host CI
@@ -105,6 +135,7 @@ struct hb_ctx {
     int32_t *l2_mcol = nullptr;
     int64_t l2_nlow = 0;
     hb::MixedState *mixed = nullptr;
+    hb::DevPool pool;        // device memory beyond the staged problem
     hb_ctx *base = nullptr;  // context whose staged integrals this one borrows (or null)
     void *plan = nullptr;    // cached grouped-launch plan of this context's own builds (k_plan.cu)
     void *diag = nullptr;   // Davidson workspace (k_davidson.cu)

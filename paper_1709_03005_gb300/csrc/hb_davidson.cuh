@@ -34,6 +34,7 @@ struct DiagWork {
 // symmetric matrix; V is [n][nvec] row-major, column c the c-th vector.
 void small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::vector<double> &V, int nvec);
 int ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t s);
+int64_t diag_workspace_bytes(const hb_ctx *ctx, int k, int precond);
 void release_diag(hb_ctx *ctx);
 void fill_diag(hb_ctx *ctx, const hb_blocks *H, DiagWork *w, cudaStream_t s);
 

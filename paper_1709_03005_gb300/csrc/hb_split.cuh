@@ -16,7 +16,7 @@ int mixed_slices(const hb_ctx *ctx);
 // Diagonal panel rows (j, j) as float pairs [n_co][Kpad].
 const float2 *mixed_panel_diag(const hb_ctx *ctx);
 // Coefficient slices [S][Kpad/64][rows][64] bf16 and their tensor map.
-int split_coef_alloc(int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err);
+int split_coef_alloc(hb_ctx *mem, int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err);
 int64_t blocks_split(int cn, int cnp, int N, int lg);
 int split_ntn(int N);
 int split_jpt(int cnp, int lg);
@@ -38,8 +38,8 @@ struct DenseOperand {
     int Kpad = 0, planes = 0;
     CUtensorMap tm;
 };
-int dense_operand_alloc(int S, int64_t R, int Kpad, DenseOperand *op, std::string *err);
-void dense_operand_free(DenseOperand *op);
+int dense_operand_alloc(hb_ctx *mem, int S, int64_t R, int Kpad, DenseOperand *op, std::string *err);
+void dense_operand_free(hb_ctx *mem, DenseOperand *op);
 // rows of [X1 | X2] (X2 may be null) into the operand's slices
 void dense_operand_fill(const DenseOperand &op, int S, const double *X1, int64_t ld1, int K1, const double *X2,
                         int64_t ld2, int K2, int64_t rows, cudaStream_t s);

@@ -602,7 +602,7 @@ int c4_fail(hb_ctx *ctx, int rc, const std::string &msg) {
 
 template <class T>
 cudaError_t c4_alloc(hb_ctx *ctx, T **p, size_t n) {
-    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (n ? n : 1));
+    cudaError_t e = dmalloc_n(ctx, p, n);
     if (e == cudaSuccess) ctx->dev_bytes += sizeof(T) * (n ? n : 1);
     return e;
 }
@@ -644,10 +644,10 @@ int c4tc_prepare(hb_ctx *ctx, int S, cudaStream_t s) {
         c->borrowed = true;
     } else {
         int *ex = nullptr;
-        e = cudaMalloc(&ex, sizeof(int) * (ctx->n_co > 0 ? ctx->n_co : 1));
+        e = dmalloc_n(ctx, &ex, (size_t)(ctx->n_co > 0 ? ctx->n_co : 1));
         if (e == cudaSuccess) e = c4_alloc(ctx, &c->xs, (size_t)S * c->x_rows * c->jpad);
         if (e != cudaSuccess) {
-            cudaFree(ex);
+            dfree(ctx, ex);
             return c4_fail(ctx, HB_ERR_OOM, cudaGetErrorString(e));
         }
         if (ctx->n_co > 0) {
@@ -658,7 +658,7 @@ int c4tc_prepare(hb_ctx *ctx, int S, cudaStream_t s) {
         x_slice_kernel<<<(unsigned)((c->x_rows * c->jpad + 255) / 256), 256, 0, s>>>(ctx->tttc, ctx->h, n_tc_rows, ctx->n_to, ctx->n_co, ctx->n_orb, c->x_rows,
                                             c->jpad, S, ex, c->xs);
         e = cudaStreamSynchronize(s);
-        cudaFree(ex);
+        dfree(ctx, ex);
         if (e != cudaSuccess) return c4_fail(ctx, HB_ERR_CUDA, cudaGetErrorString(e));
     }
     e = set_attr<2>();
@@ -677,11 +677,11 @@ int c4tc_prepare(hb_ctx *ctx, int S, cudaStream_t s) {
         // CI slices
         cg.c_rows = 2 * (int64_t)Gi.ndet + 1;
         int *en = nullptr;
-        e = cudaMalloc(&en, sizeof(int) * TNP);
+        e = dmalloc_n(ctx, &en, (size_t)TNP);
         if (e == cudaSuccess) e = c4_alloc(ctx, &cg.cs, (size_t)S * cg.c_rows * TNP);
         if (e == cudaSuccess) e = c4_alloc(ctx, &cg.term_ptr, (size_t)ctx->n_l2 + 1);
         if (e != cudaSuccess) {
-            cudaFree(en);
+            dfree(ctx, en);
             return c4_fail(ctx, HB_ERR_OOM, cudaGetErrorString(e));
         }
         fill_int_kernel<<<1, TNP, 0, s>>>(en, TNP, -2000);
@@ -695,7 +695,7 @@ int c4tc_prepare(hb_ctx *ctx, int S, cudaStream_t s) {
         std::vector<int64_t> h(ctx->n_l2 + 1);
         e = cudaMemcpyAsync(h.data(), cg.term_ptr, sizeof(int64_t) * h.size(), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFree(en);
+        dfree(ctx, en);
         if (e != cudaSuccess) return c4_fail(ctx, HB_ERR_CUDA, cudaGetErrorString(e));
         for (size_t i = 1; i < h.size(); ++i) h[i] += h[i - 1];
         cg.n_terms = h.back();
@@ -765,11 +765,11 @@ int g_c4tc(const Grouped<C4TTask> &g, const C4Item *items, int n_items, int S, i
 void release_c4tc(hb_ctx *ctx) {
     C4TC *c = (C4TC *)ctx->c4tc;
     if (!c) return;
-    if (!c->borrowed) cudaFree(c->xs);
+    if (!c->borrowed) dfree(ctx, c->xs);
     for (auto &g : c->g) {
-        cudaFree(g.cs);
-        cudaFree(g.term_ptr);
-        cudaFree(g.terms);
+        dfree(ctx, g.cs);
+        dfree(ctx, g.term_ptr);
+        dfree(ctx, g.terms);
     }
     delete c;
     ctx->c4tc = nullptr;

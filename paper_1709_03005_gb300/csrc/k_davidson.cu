@@ -671,12 +671,12 @@ static int diag_fail(hb_ctx *ctx, int code, const std::string &m) {
     return code;
 }
 
-static void release_tensor_products(DiagWork *w) {
-    dense_operand_free(&w->A1);
-    dense_operand_free(&w->A2);
-    dense_operand_free(&w->Xs);
-    if (w->part) cudaFree(w->part);
-    if (w->err) cudaFree(w->err);
+static void release_tensor_products(hb_ctx *ctx, DiagWork *w) {
+    dense_operand_free(ctx, &w->A1);
+    dense_operand_free(ctx, &w->A2);
+    dense_operand_free(ctx, &w->Xs);
+    dfree(ctx, w->part);
+    dfree(ctx, w->err);
     w->part = nullptr;
     w->err = nullptr;
     w->tc = false;
@@ -685,35 +685,66 @@ static void release_tensor_products(DiagWork *w) {
 // Slices of [Hcc | Hlc^T] and of Hlc (fixed during the solve), the vector
 // slice buffer for up to mmax vectors and the split-K scratch.
 static int setup_tensor_products(hb_ctx *ctx, const hb_blocks *H, DiagWork *w, int mmax, cudaStream_t s) {
-    release_tensor_products(w);
+    release_tensor_products(ctx, w);
     const int64_t n = ctx->dim, Dc = ctx->Dc, nl = ctx->n_l2;
     const int S = ctx->split_slices >= 2 && ctx->split_slices <= 6 ? ctx->split_slices : 6;
     w->S = S;
     std::string err;
     const int K1 = (int)((n + 63) / 64 * 64), K2 = (int)((Dc + 63) / 64 * 64);
-    int rc = dense_operand_alloc(S, mmax, K1, &w->Xs, &err);
-    if (rc == HB_OK && Dc > 0) rc = dense_operand_alloc(S, Dc, K1, &w->A1, &err);
-    if (rc == HB_OK && Dc > 0 && nl > 0) rc = dense_operand_alloc(S, nl, K2, &w->A2, &err);
+    int rc = dense_operand_alloc(ctx, S, mmax, K1, &w->Xs, &err);
+    if (rc == HB_OK && Dc > 0) rc = dense_operand_alloc(ctx, S, Dc, K1, &w->A1, &err);
+    if (rc == HB_OK && Dc > 0 && nl > 0) rc = dense_operand_alloc(ctx, S, nl, K2, &w->A2, &err);
     size_t part = 1;
     int per = 0;
     if (Dc > 0) part = std::max(part, (size_t)dense_splits(Dc, 1, K1 / 64, &per) * mmax * Dc);
     if (Dc > 0 && nl > 0) part = std::max(part, (size_t)dense_splits(nl, 1, K2 / 64, &per) * mmax * nl);
     cudaError_t e = cudaSuccess;
-    if (rc == HB_OK) e = cudaMalloc(&w->part, sizeof(float2) * part);
-    if (rc == HB_OK && e == cudaSuccess) e = cudaMalloc(&w->err, sizeof(int));
+    if (rc == HB_OK) e = dmalloc_n(ctx, &w->part, part);
+    if (rc == HB_OK && e == cudaSuccess) e = dmalloc_n(ctx, &w->err, 1);
     if (rc == HB_OK && e == cudaSuccess) e = cudaMemsetAsync(w->err, 0, sizeof(int), s);
     if (rc == HB_OK && e != cudaSuccess) {
         rc = HB_ERR_OOM;
         err = std::string("Davidson tensor-core scratch: ") + cudaGetErrorString(e);
     }
     if (rc != HB_OK) {
-        release_tensor_products(w);
+        release_tensor_products(ctx, w);
         return diag_fail(ctx, rc, err);
     }
     if (Dc > 0) dense_operand_fill(w->A1, S, H->Hcc, Dc, (int)Dc, nl > 0 ? w->HlcT : nullptr, nl, (int)nl, Dc, s);
     if (Dc > 0 && nl > 0) dense_operand_fill(w->A2, S, H->Hlc, Dc, (int)Dc, nullptr, 0, 0, nl, s);
     w->tc = true;
     return HB_OK;
+}
+
+// Device bytes a solve for k eigenpairs takes from the context's memory (the
+// allocations of ensure_diag_work, of the interleaved vectors and the class-4
+// transpose, of the tensor-core slices, and of the learned factors), each
+// rounded as the context's allocator rounds it.
+int64_t hb::diag_workspace_bytes(const hb_ctx *ctx, int k, int precond) {
+    auto r = [](double b) { return (int64_t)((std::max<double>(b, 1.0) + 255.0) / 256.0) * 256; };
+    const int64_t n = ctx->dim, Dc = ctx->Dc, nl = ctx->n_l2;
+    if (n < 1 || k < 1) return 0;
+    const int b = (int)std::min<int64_t>(n, k + std::max(4, std::min(16, k / 2)));
+    const int mmax = (int)std::min<int64_t>(n, std::max(5 * b, k + 4 * b));
+    const int64_t chunks = (n + kGramChunk - 1) / kGramChunk;
+    int64_t t = 5 * r(8.0 * mmax * n) + r(8.0 * n) + r(8.0 * chunks * mmax * mmax) + 2 * r(8.0 * mmax * mmax) +
+                r(8.0 * mmax) + r(4.0 * mmax);
+    if (nl > 0) t += r(8.0 * nl * mmax);
+    if (Dc > 0 && nl > 0) t += r(8.0 * Dc * nl);
+    if (precond & HB_DIAG_TENSOR) {
+        const int S = ctx->split_slices >= 2 && ctx->split_slices <= 6 ? ctx->split_slices : 6;
+        const int64_t K1 = (n + 63) / 64 * 64, K2 = (Dc + 63) / 64 * 64;
+        t += r(2.0 * S * K1 * mmax);
+        if (Dc > 0) t += r(2.0 * S * K1 * Dc);
+        if (Dc > 0 && nl > 0) t += r(2.0 * S * K2 * nl);
+        size_t part = 1;
+        int per = 0;
+        if (Dc > 0) part = std::max(part, (size_t)dense_splits(Dc, 1, (int)(K1 / 64), &per) * mmax * Dc);
+        if (Dc > 0 && nl > 0) part = std::max(part, (size_t)dense_splits(nl, 1, (int)(K2 / 64), &per) * mmax * nl);
+        t += r(8.0 * part) + r(4.0);
+    }
+    if ((precond & 0xff) == HB_PRECOND_MLP) t += r(16.0 * n) + r(4.0 * b * n);
+    return t;
 }
 
 int hb::ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t s) {
@@ -724,39 +755,40 @@ int hb::ensure_diag_work(hb_ctx *ctx, const hb_blocks *H, int mmax, cudaStream_t
         ctx->diag = w;
     }
     if (w->mmax < mmax || w->n != n) {
-        auto fr = [](void *p) { if (p) cudaFree(p); };
+        auto fr = [&](void *p) { dfree(ctx, p); };
         fr(w->V); fr(w->AV); fr(w->X); fr(w->AX); fr(w->W2); fr(w->d); fr(w->partial); fr(w->small); fr(w->theta);
-        fr(w->idx); fr(w->proj);
-        w->V = w->AV = w->X = w->AX = w->W2 = w->d = w->partial = w->small = w->theta = w->proj = nullptr;
+        fr(w->idx); fr(w->proj); fr(w->XT);
+        w->V = w->AV = w->X = w->AX = w->W2 = w->d = w->partial = w->small = w->theta = w->proj = w->XT = nullptr;
         w->idx = nullptr;
-        const size_t vec = sizeof(double) * (size_t)mmax * n;
-        cudaError_t e = cudaMalloc(&w->V, vec);
-        if (e == cudaSuccess) e = cudaMalloc(&w->AV, vec);
-        if (e == cudaSuccess) e = cudaMalloc(&w->X, vec);
-        if (e == cudaSuccess) e = cudaMalloc(&w->AX, vec);
-        if (e == cudaSuccess) e = cudaMalloc(&w->W2, vec);
-        if (e == cudaSuccess) e = cudaMalloc(&w->d, sizeof(double) * n);
+        w->XT_rows = 0;
+        const size_t vec = (size_t)mmax * n;
+        cudaError_t e = dmalloc_n(ctx, &w->V, vec);
+        if (e == cudaSuccess) e = dmalloc_n(ctx, &w->AV, vec);
+        if (e == cudaSuccess) e = dmalloc_n(ctx, &w->X, vec);
+        if (e == cudaSuccess) e = dmalloc_n(ctx, &w->AX, vec);
+        if (e == cudaSuccess) e = dmalloc_n(ctx, &w->W2, vec);
+        if (e == cudaSuccess) e = dmalloc_n(ctx, &w->d, (size_t)n);
         const int chunks = (int)((n + kGramChunk - 1) / kGramChunk);
-        if (e == cudaSuccess) e = cudaMalloc(&w->partial, sizeof(double) * (size_t)chunks * mmax * mmax);
-        if (e == cudaSuccess) e = cudaMalloc(&w->small, sizeof(double) * (size_t)mmax * mmax);
-        if (e == cudaSuccess) e = cudaMalloc(&w->proj, sizeof(double) * (size_t)mmax * mmax);
-        if (e == cudaSuccess) e = cudaMalloc(&w->theta, sizeof(double) * mmax);
-        if (e == cudaSuccess) e = cudaMalloc(&w->idx, sizeof(int32_t) * mmax);
+        if (e == cudaSuccess) e = dmalloc_n(ctx, &w->partial, (size_t)chunks * mmax * mmax);
+        if (e == cudaSuccess) e = dmalloc_n(ctx, &w->small, (size_t)mmax * mmax);
+        if (e == cudaSuccess) e = dmalloc_n(ctx, &w->proj, (size_t)mmax * mmax);
+        if (e == cudaSuccess) e = dmalloc_n(ctx, &w->theta, (size_t)mmax);
+        if (e == cudaSuccess) e = dmalloc_n(ctx, &w->idx, (size_t)mmax);
         if (e != cudaSuccess) return diag_fail(ctx, HB_ERR_OOM, std::string("Davidson workspace: ") + cudaGetErrorString(e));
         w->mmax = mmax;
         w->n = n;
     }
     if (ctx->n_l2 > 0 && w->XT_rows < (int64_t)ctx->n_l2 * w->mmax) {
-        if (w->XT) cudaFree(w->XT);
+        dfree(ctx, w->XT);
         w->XT = nullptr;
         w->XT_rows = 0;
-        cudaError_t e = cudaMalloc(&w->XT, sizeof(double) * (size_t)ctx->n_l2 * w->mmax);
+        cudaError_t e = dmalloc_n(ctx, &w->XT, (size_t)ctx->n_l2 * w->mmax);
         if (e != cudaSuccess) return diag_fail(ctx, HB_ERR_OOM, "Davidson interleaved-vector buffer");
         w->XT_rows = (int64_t)ctx->n_l2 * w->mmax;
     }
     if (ctx->Dc > 0 && ctx->n_l2 > 0 && (!w->HlcT || w->HlcT_src != H->Hlc)) {
         if (!w->HlcT) {
-            cudaError_t e = cudaMalloc(&w->HlcT, sizeof(double) * (size_t)ctx->Dc * ctx->n_l2);
+            cudaError_t e = dmalloc_n(ctx, &w->HlcT, (size_t)ctx->Dc * ctx->n_l2);
             if (e != cudaSuccess) return diag_fail(ctx, HB_ERR_OOM, "Davidson transpose buffer");
         }
         w->HlcT_src = H->Hlc;
@@ -1030,7 +1062,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
     if (w->tc) {
         int word = 0;
         cudaMemcpy(&word, w->err, sizeof(int), cudaMemcpyDeviceToHost);
-        release_tensor_products(w);
+        release_tensor_products(ctx, w);
         if (word) return diag_fail(ctx, HB_ERR_TIMEOUT, "Davidson tensor-core product gave up waiting");
     }
     if (st) {
@@ -1053,11 +1085,11 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
 void hb::release_diag(hb_ctx *ctx) {
     DiagWork *w = (DiagWork *)ctx->diag;
     if (!w) return;
-    release_tensor_products(w);
+    release_tensor_products(ctx, w);
     for (void *p : {(void *)w->V, (void *)w->AV, (void *)w->X, (void *)w->AX, (void *)w->W2, (void *)w->d, (void *)w->partial,
                     (void *)w->small, (void *)w->proj, (void *)w->theta, (void *)w->idx, (void *)w->HlcT,
                     (void *)w->XT})
-        if (p) cudaFree(p);
+        dfree(ctx, p);
     delete w;
     ctx->diag = nullptr;
 }

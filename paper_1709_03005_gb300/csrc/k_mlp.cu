@@ -267,8 +267,9 @@ static int mlp_fail(hb_ctx *ctx, int code, const std::string &m) {
 static int ensure_rows(hb_ctx *ctx, MlpState &M, DiagWork *w, cudaStream_t s) {
     const int64_t n = ctx->dim;
     if (M.n != n || !M.row_info) {
-        if (M.row_info) cudaFree(M.row_info);
-        if (cudaMalloc(&M.row_info, sizeof(float) * 4 * n) != cudaSuccess) return HB_ERR_OOM;
+        dfree(ctx, M.row_info);
+        M.row_info = nullptr;
+        if (dmalloc_n(ctx, &M.row_info, (size_t)4 * n) != cudaSuccess) return HB_ERR_OOM;
         M.n = n;
         M.rows_ready = false;
     }
@@ -297,8 +298,9 @@ int hb::mlp_weights_for(hb_ctx *ctx, DiagWork *w, const double *theta, int nr, f
     if (!M || !M->wh) return mlp_fail(ctx, HB_ERR_UNSUPPORTED, "no preconditioner network");
     if (ensure_rows(ctx, *M, w, s) != HB_OK) return HB_ERR_OOM;
     if (M->mmax < nr || !M->w) {
-        if (M->w) cudaFree(M->w);
-        if (cudaMalloc(&M->w, sizeof(float) * (size_t)nr * ctx->dim) != cudaSuccess) return HB_ERR_OOM;
+        dfree(ctx, M->w);
+        M->w = nullptr;
+        if (dmalloc_n(ctx, &M->w, (size_t)nr * ctx->dim) != cudaSuccess) return HB_ERR_OOM;
         M->mmax = nr;
     }
     // theta is already on the device in w->theta (hb_diag copies it before the call)
@@ -314,7 +316,7 @@ void hb::release_mlp(hb_ctx *ctx) {
     MlpState *M = (MlpState *)ctx->mlp;
     if (!M) return;
     for (void *p : {(void *)M->wh, (void *)M->bias, (void *)M->row_info, (void *)M->w, (void *)M->feats})
-        if (p) cudaFree(p);
+        dfree(ctx, p);
     delete M;
     ctx->mlp = nullptr;
 }
@@ -342,8 +344,8 @@ extern "C" int hb_mlp_set(hb_ctx *ctx, const hb_mlp_weights *wt) {
     for (int i = 0; i < MLP_NPARAM; ++i) ph[i] = __float2half_rn(p[i]);
     MlpState *M = (MlpState *)ctx->mlp;
     if (!M) { M = new MlpState(); ctx->mlp = M; }
-    if (!M->wh && cudaMalloc(&M->wh, sizeof(__half) * MLP_NPARAM) != cudaSuccess) return HB_ERR_OOM;
-    if (!M->bias && cudaMalloc(&M->bias, sizeof(float) * MLP_NPARAM) != cudaSuccess) return HB_ERR_OOM;
+    if (!M->wh && dmalloc_n(ctx, &M->wh, (size_t)MLP_NPARAM) != cudaSuccess) return HB_ERR_OOM;
+    if (!M->bias && dmalloc_n(ctx, &M->bias, (size_t)MLP_NPARAM) != cudaSuccess) return HB_ERR_OOM;
     if (cudaMemcpy(M->wh, ph.data(), sizeof(__half) * MLP_NPARAM, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(M->bias, p.data(), sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice) != cudaSuccess)
         return mlp_fail(ctx, HB_ERR_CUDA, "uploading weights");
@@ -383,19 +385,24 @@ extern "C" int hb_mlp_adam(int64_t n_param, float *params, const float *grads, f
 // windows of `batch` (wrapping around), one loss-and-gradient pass and one
 // update per step, the loss of the last step in *last_loss (host).  Scratch
 // (gradients, moments, workspace) is allocated and freed by the call.
-extern "C" int hb_mlp_train(float *params, const float *feats, const float *a, const float *b, int64_t n,
-                            int64_t batch, int32_t steps, float lr, float *last_loss, void *stream) {
+// The Adam loop of both training entry points; the scratch comes from `mem`
+// (a context's memory) or from cudaMalloc when mem is null.
+static int mlp_train_loop(hb_ctx *mem, float *params, const float *feats, const float *a, const float *b, int64_t n,
+                          int64_t batch, int32_t steps, float lr, float *last_loss, void *stream) {
     if (!params || !feats || !a || !b || n <= 0 || batch <= 0 || steps < 1 || !(lr > 0.0f))
         return HB_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t bs = batch < n ? batch : n;
     float *g = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
     void *work = nullptr;
-    cudaError_t e = cudaMalloc(&g, sizeof(float) * MLP_NPARAM);
-    if (e == cudaSuccess) e = cudaMalloc(&m, sizeof(float) * MLP_NPARAM);
-    if (e == cudaSuccess) e = cudaMalloc(&v, sizeof(float) * MLP_NPARAM);
-    if (e == cudaSuccess) e = cudaMalloc(&loss, sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&work, (size_t)hb_mlp_workspace_bytes(bs));
+    auto alloc = [&](void **p, size_t bytes) {
+        return mem ? dmalloc(mem, p, bytes) : cudaMalloc(p, bytes);
+    };
+    cudaError_t e = alloc((void **)&g, sizeof(float) * MLP_NPARAM);
+    if (e == cudaSuccess) e = alloc((void **)&m, sizeof(float) * MLP_NPARAM);
+    if (e == cudaSuccess) e = alloc((void **)&v, sizeof(float) * MLP_NPARAM);
+    if (e == cudaSuccess) e = alloc((void **)&loss, sizeof(float));
+    if (e == cudaSuccess) e = alloc(&work, (size_t)hb_mlp_workspace_bytes(bs));
     if (e == cudaSuccess) e = cudaMemsetAsync(m, 0, sizeof(float) * MLP_NPARAM, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(float) * MLP_NPARAM, s);
     int rc = e == cudaSuccess ? HB_OK : HB_ERR_OOM;
@@ -413,8 +420,36 @@ extern "C" int hb_mlp_train(float *params, const float *feats, const float *a, c
         if (e != cudaSuccess) rc = HB_ERR_CUDA;
     }
     cudaStreamSynchronize(s);
-    cudaFree(g); cudaFree(m); cudaFree(v); cudaFree(loss); cudaFree(work);
+    for (void *p : {(void *)g, (void *)m, (void *)v, (void *)loss, work}) {
+        if (mem) dfree(mem, p);
+        else if (p) cudaFree(p);
+    }
     return rc;
+}
+
+extern "C" int hb_mlp_train_params(float *params, const float *feats, const float *a, const float *b, int64_t n,
+                                   int64_t batch, int32_t steps, float lr, float *last_loss, void *stream) {
+    return mlp_train_loop(nullptr, params, feats, a, b, n, batch, steps, lr, last_loss, stream);
+}
+
+extern "C" int hb_mlp_train(hb_ctx *ctx, const hb_mlp_dataset *d, float *params, hb_stats *st, void *stream) {
+    if (!ctx || !d || !params) return mlp_fail(ctx, HB_ERR_INVALID_ARG, "NULL argument");
+    float last = 0.0f;
+    int rc = mlp_train_loop(ctx, params, d->feats, d->a, d->b, d->n, d->batch, d->steps, d->lr, &last, stream);
+    if (rc != HB_OK) return mlp_fail(ctx, rc, "training failed (arguments, memory or launch)");
+    // the trained network becomes the context's preconditioner network
+    std::vector<float> p(MLP_NPARAM);
+    if (cudaMemcpy(p.data(), params, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return mlp_fail(ctx, HB_ERR_CUDA, "reading the trained parameters");
+    hb_mlp_weights w{MLP_IN, MLP_W, &p[OFF_W1], &p[OFF_B1], &p[OFF_W2], &p[OFF_B2], &p[OFF_W3], &p[OFF_B3]};
+    rc = hb_mlp_set(ctx, &w);
+    if (rc != HB_OK) return rc;
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->iterations = d->steps;
+        st->mlp_loss = last;
+    }
+    return HB_OK;
 }
 
 extern "C" int hb_mlp_predict(const float *params, const float *feats, int64_t n, float *out, void *stream) {
@@ -436,11 +471,11 @@ extern "C" int hb_diag_features(hb_ctx *ctx, const hb_blocks *H, const double *t
     rc = ensure_rows(ctx, *M, w, s);
     if (rc != HB_OK) return rc;
     double *th = nullptr;
-    if (cudaMalloc(&th, sizeof(double) * q) != cudaSuccess) return HB_ERR_OOM;
+    if (dmalloc_n(ctx, &th, (size_t)q) != cudaSuccess) return HB_ERR_OOM;
     cudaMemcpyAsync(th, theta, sizeof(double) * q, cudaMemcpyHostToDevice, s);
     dim3 g((unsigned)((ctx->dim + 255) / 256), q);
     diag_features_kernel<<<g, 256, 0, s>>>(w->d, M->row_info, ctx->dim, th, q, feats);
     cudaStreamSynchronize(s);
-    cudaFree(th);
+    dfree(ctx, th);
     return cudaGetLastError() == cudaSuccess ? HB_OK : HB_ERR_CUDA;
 }

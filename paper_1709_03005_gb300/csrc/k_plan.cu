@@ -457,12 +457,12 @@ int upload(Plan &p, std::string *err, cudaStream_t s) {
     if (p.upload_pending) e = cudaEventSynchronize(p.uploaded);
     p.upload_pending = false;
     if (e == cudaSuccess && p.host.size() > p.dev_size) {
-        if (p.dev) cudaFree(p.dev);
+        if (p.dev) dfree(p.ctxs[0], p.dev);
         if (p.pinned) cudaFreeHost(p.pinned);
         p.dev = nullptr;
         p.pinned = nullptr;
         p.dev_size = 0;
-        e = cudaMalloc((void **)&p.dev, p.host.size());
+        e = dmalloc_n(p.ctxs[0], &p.dev, p.host.size());
         if (e == cudaSuccess) e = cudaMallocHost((void **)&p.pinned, p.host.size());
         if (e == cudaSuccess) p.dev_size = p.host.size();
     }
@@ -515,7 +515,7 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->aux2, cudaStreamNonBlocking, greatest);
     for (cudaEvent_t *ev : {&p->k1_done, &p->items_done, &p->gd_done, &p->dv_done})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&p->err, 2 * sizeof(int));   // split kernel, class-4 kernel
+    if (e == cudaSuccess) e = dmalloc_n(ctxs[0], &p->err, 2);   // split kernel, class-4 kernel
     if (e == cudaSuccess) e = cudaMemsetAsync(p->err, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) {
         *err = std::string("plan: ") + cudaGetErrorString(e);
@@ -552,7 +552,7 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
     if (rc != HB_OK) { plan_destroy(p); return rc; }
     fill_tasks(*p);
     if (precision == HB_MIXED && p->coef_rows > 0) {
-        rc = split_coef_alloc(p->S, p->coef_rows, p->Kpad, &p->coef, &p->tm_coef, err);
+        rc = split_coef_alloc(ctxs[0], p->S, p->coef_rows, p->Kpad, &p->coef, &p->tm_coef, err);
         if (rc != HB_OK) { plan_destroy(p); return rc; }
         ensure_split_events(*p);
     }
@@ -588,14 +588,14 @@ namespace {
 // Mean time of `launch` over a private copy of the given tasks (one warm-up
 // launch, then `reps` timed launches on stream s).
 template <class T, class F>
-float time_tasks(const std::vector<T> &tasks, const std::vector<int64_t> &nblocks, F launch, cudaStream_t s,
-                 int reps = 2) {
+float time_tasks(hb_ctx *mem, const std::vector<T> &tasks, const std::vector<int64_t> &nblocks, F launch,
+                 cudaStream_t s, int reps = 2) {
     std::vector<int64_t> blk(1, 0);
     for (int64_t b : nblocks) blk.push_back(blk.back() + b);
     if (tasks.empty() || blk.back() == 0) return 0.0f;
     const size_t bt = sizeof(T) * tasks.size(), ob = align256(bt), total = ob + sizeof(int64_t) * blk.size();
     uint8_t *d = nullptr;
-    if (cudaMalloc(&d, total) != cudaSuccess) return 1e30f;
+    if (dmalloc_n(mem, &d, total) != cudaSuccess) return 1e30f;
     cudaMemcpyAsync(d, tasks.data(), bt, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d + ob, blk.data(), sizeof(int64_t) * blk.size(), cudaMemcpyHostToDevice, s);
     Grouped<T> g;
@@ -616,7 +616,7 @@ float time_tasks(const std::vector<T> &tasks, const std::vector<int64_t> &nblock
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaStreamSynchronize(s);
-    cudaFree(d);
+    dfree(mem, d);
     return ms / reps;
 }
 
@@ -657,7 +657,7 @@ int plan_autotune(Plan *p, cudaStream_t s, std::string *err) {
                     ts.push_back(u);
                     nb.push_back(blocks_split(cn, cnp, u.N, lg));
                 }
-                const float ms = time_tasks(ts, nb, [&](const Grouped<SplitTask> &g) {
+                const float ms = time_tasks(p->ctxs[0], ts, nb, [&](const Grouped<SplitTask> &g) {
                     g_split(pc, lg, &p->tm_coef, g, p->Kpad / 64, p->d_cols, p->err, s);
                 }, s);
                 if (best_lg < 0) { best = def_ms = ms; best_lg = lg; }
@@ -691,7 +691,7 @@ int plan_autotune(Plan *p, cudaStream_t s, std::string *err) {
                     ts.push_back(u);
                     nb.push_back(blocks_class4(u.n_l2, cn, jt));
                 }
-                const float ms = time_tasks(ts, nb, [&](const Grouped<C4Task> &g) {
+                const float ms = time_tasks(p->ctxs[0], ts, nb, [&](const Grouped<C4Task> &g) {
                     g_class4(g, W, 1, nt, jt, s);
                 }, s);
                 if (arg.first < 0) { best = def_ms = ms; arg = c; }
@@ -715,8 +715,8 @@ int plan_autotune(Plan *p, cudaStream_t s, std::string *err) {
                 smem = std::max(smem, smem_stage(t->t.ns, t->t.nsp));
             }
             const int DF = p->precision == HB_MIXED ? 1 : 0;
-            const float mw = time_tasks(ts, nbw, [&](const Grouped<GTask> &g) { g_gamma_warp(g, DF, s); }, s);
-            const float mb = time_tasks(ts, nbb, [&](const Grouped<GTask> &g) { g_gamma(g, smem, DF, s); }, s);
+            const float mw = time_tasks(p->ctxs[0], ts, nbw, [&](const Grouped<GTask> &g) { g_gamma_warp(g, DF, s); }, s);
+            const float mb = time_tasks(p->ctxs[0], ts, nbb, [&](const Grouped<GTask> &g) { g_gamma(g, smem, DF, s); }, s);
             ch.gamma_warp[kv.first] = mb < kGain * mw ? 0 : 1;     // the warp form unless clearly slower
         }
     }
@@ -948,9 +948,12 @@ void plan_destroy(Plan *p) {
             cudaStreamSynchronize(st);
             cudaStreamDestroy(st);
         }
-    if (p->dev) cudaFree(p->dev);
+    hb_ctx *mem = p->ctxs.empty() ? nullptr : p->ctxs[0];
+    if (mem) {
+        dfree(mem, p->dev);
+        dfree(mem, p->coef);
+        dfree(mem, p->err);
+    }
     if (p->pinned) cudaFreeHost(p->pinned);
-    if (p->coef) cudaFree(p->coef);
-    if (p->err) cudaFree(p->err);
     delete p;
 }

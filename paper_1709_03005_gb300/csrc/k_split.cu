@@ -823,10 +823,10 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
     if (!encode_fn()) return mixed_fail(ctx, HB_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     const int64_t rows = (int64_t)ctx->n_co * ctx->n_co;
     M.panel_rows = rows;
-    cudaError_t e = cudaMalloc(&M.panel_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * rows * ctx->Kpad);
+    cudaError_t e = dmalloc(ctx, (void **)&M.panel_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * rows * ctx->Kpad);
     if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("panel slices: ") + cudaGetErrorString(e));
     ctx->dev_bytes += sizeof(__nv_bfloat16) * (size_t)M.slices * rows * ctx->Kpad;
-    e = cudaMalloc(&M.pdiag, sizeof(float2) * (size_t)ctx->n_co * ctx->Kpad);
+    e = dmalloc_n(ctx, &M.pdiag, (size_t)ctx->n_co * ctx->Kpad);
     if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("panel rows: ") + cudaGetErrorString(e));
     ctx->dev_bytes += sizeof(float2) * (size_t)ctx->n_co * ctx->Kpad;
     panel_diag_df_kernel<<<ctx->n_co, 256, 0, s>>>(ctx->panel, ctx->n_co, ctx->Kpad, M.pdiag);
@@ -860,11 +860,11 @@ int mixed_slices(const hb_ctx *ctx) { return ctx->mixed ? ctx->mixed->slices : c
 
 // Coefficient slices of `rows` rows in all: [S][Kpad/64][rows][64] bf16 and
 // the 3D map whose box is one 128 x 64 tile of one slice plane.
-int split_coef_alloc(int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err) {
+int split_coef_alloc(hb_ctx *mem, int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err) {
     *buf = nullptr;
     if (!encode_fn()) { *err = "cuTensorMapEncodeTiled is not available"; return HB_ERR_CUDA; }
     if (rows < 1) rows = 1;
-    cudaError_t e = cudaMalloc(buf, sizeof(__nv_bfloat16) * (size_t)S * rows * Kpad);
+    cudaError_t e = dmalloc(mem, buf, sizeof(__nv_bfloat16) * (size_t)S * rows * Kpad);
     if (e != cudaSuccess) { *err = std::string("coefficient slices: ") + cudaGetErrorString(e); return HB_ERR_OOM; }
     const int KB = Kpad / BKB;
     cuuint64_t dims[3] = {(cuuint64_t)BKB, (cuuint64_t)rows, (cuuint64_t)S * KB};
@@ -875,7 +875,7 @@ int split_coef_alloc(int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
-        cudaFree(*buf);
+        dfree(mem, *buf);
         *buf = nullptr;
         *err = "coefficient tensor map: error " + std::to_string((int)r);
         return HB_ERR_CUDA;
@@ -945,14 +945,14 @@ int g_diag_rows(const Grouped<DRTask> &g, cudaStream_t s) {
 }
 
 // ------------------------------------------------ dense split GEMM (host)
-int dense_operand_alloc(int S, int64_t R, int Kpad, DenseOperand *op, std::string *err) {
+int dense_operand_alloc(hb_ctx *mem, int S, int64_t R, int Kpad, DenseOperand *op, std::string *err) {
     op->buf = nullptr;
     op->R = R < 1 ? 1 : R;
     op->Kpad = Kpad;
     op->planes = Kpad / BKB;
     if (!encode_fn()) { *err = "cuTensorMapEncodeTiled is not available"; return HB_ERR_CUDA; }
     const size_t bytes = sizeof(__nv_bfloat16) * (size_t)S * op->planes * op->R * BKB;
-    cudaError_t e = cudaMalloc(&op->buf, bytes);
+    cudaError_t e = dmalloc(mem, (void **)&op->buf, bytes);
     if (e != cudaSuccess) { *err = std::string("Davidson operand slices: ") + cudaGetErrorString(e); return HB_ERR_OOM; }
     cuuint64_t dims[3] = {(cuuint64_t)BKB, (cuuint64_t)op->R, (cuuint64_t)S * op->planes};
     cuuint64_t strides[2] = {(cuuint64_t)BKB * 2, (cuuint64_t)op->R * BKB * 2};
@@ -962,7 +962,7 @@ int dense_operand_alloc(int S, int64_t R, int Kpad, DenseOperand *op, std::strin
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
-        cudaFree(op->buf);
+        dfree(mem, op->buf);
         op->buf = nullptr;
         *err = "Davidson operand tensor map: error " + std::to_string((int)r);
         return HB_ERR_CUDA;
@@ -970,8 +970,8 @@ int dense_operand_alloc(int S, int64_t R, int Kpad, DenseOperand *op, std::strin
     return HB_OK;
 }
 
-void dense_operand_free(DenseOperand *op) {
-    if (op->buf) cudaFree(op->buf);
+void dense_operand_free(hb_ctx *mem, DenseOperand *op) {
+    if (op->buf) dfree(mem, op->buf);
     op->buf = nullptr;
 }
 
@@ -1030,8 +1030,8 @@ int dense_split_gemm(int S, const DenseOperand &A, int64_t M, const DenseOperand
 void release_mixed(hb_ctx *ctx) {
     if (!ctx->mixed) return;
     if (!ctx->mixed->borrowed_panel) {
-        cudaFree(ctx->mixed->panel_slices);
-        cudaFree(ctx->mixed->pdiag);
+        dfree(ctx, ctx->mixed->panel_slices);
+        dfree(ctx, ctx->mixed->pdiag);
     }
     delete ctx->mixed;
     ctx->mixed = nullptr;

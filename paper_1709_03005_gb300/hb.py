@@ -46,7 +46,8 @@ class hb_options(C.Structure):
 class hb_layout(C.Structure):
     _fields_ = [("dim", C.c_int64), ("contracted_dim", C.c_int64), ("n_l2", C.c_int64), ("l2_nnz", C.c_int64),
                 ("tt_pairs", C.c_int64), ("tl2_pairs", C.c_int64), ("n_labels", C.c_int64),
-                ("device_bytes", C.c_int64), ("n_groups", C.c_int32), ("n_words", C.c_int32)]
+                ("device_bytes", C.c_int64), ("n_groups", C.c_int32), ("n_words", C.c_int32),
+                ("workspace_bytes", C.c_int64)]
 
 
 class hb_blocks(C.Structure):
@@ -61,7 +62,7 @@ class hb_stats(C.Structure):
                 ("iterations", C.c_int32), ("mlp_fallbacks", C.c_int32), ("max_residual", C.c_double),
                 ("ms_matvec", C.c_float), ("ms_rr", C.c_float), ("expand_tensor_flops", C.c_double),
                 ("ms_gram", C.c_float), ("ms_combine", C.c_float), ("ms_class4_kernel", C.c_float),
-                ("fp64_iterations", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("fp64_iterations", C.c_int32), ("mlp_loss", C.c_float), ("reserved", C.c_int32 * 1)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -79,8 +80,8 @@ assert PAIR_DTYPE.itemsize == 24
 EXPORTS = ["hb_init", "hb_init_shared", "hb_batch_create", "hb_batch_launch", "hb_batch_nodes",
            "hb_batch_destroy", "hb_query", "hb_group_offset", "hb_build_blocks", "hb_diag", "hb_classify",
            "hb_classify_noalloc", "hb_mlp_set", "hb_mlp_param_count", "hb_mlp_workspace_bytes", "hb_mlp_loss_grad",
-           "hb_mlp_adam", "hb_mlp_train", "hb_mlp_predict", "hb_diag_features", "hb_batch_report", "hb_tuning_report",
-           "hb_dump", "hb_target_diag",
+           "hb_mlp_adam", "hb_mlp_train", "hb_mlp_train_params", "hb_mlp_predict", "hb_diag_features", "hb_batch_report", "hb_tuning_report",
+           "hb_dump", "hb_target_diag", "hb_workspace_size", "hb_set_workspace",
            "hb_last_error", "hb_destroy"]
 
 _lib = None
@@ -285,6 +286,26 @@ class Hamiltonian:
         """Load a packed parameter vector (see unpack_mlp) for HB_PRECOND_MLP."""
         self.set_mlp(*unpack_mlp(packed))
 
+    def workspace_size(self, precision=HB_MIXED, diag_k=0, precond=HB_PRECOND_DIAG, stream=None):
+        """hb_workspace_size: device bytes the context's builds (and a solve
+        for diag_k eigenpairs) take beyond hb_init."""
+        self.lib.hb_workspace_size.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int64),
+                                               C.c_void_p]
+        self.lib.hb_workspace_size.restype = C.c_int
+        out = C.c_int64()
+        _check(self.lib.hb_workspace_size(self.ctx, precision, diag_k, precond, C.byref(out),
+                                          _stream_handle(stream)), self.ctx)
+        _check(self.lib.hb_query(self.ctx, C.byref(self.layout)), self.ctx)
+        return out.value
+
+    def set_workspace(self, buf):
+        """hb_set_workspace with a caller-owned device tensor (kept alive here)."""
+        self.lib.hb_set_workspace.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+        self.lib.hb_set_workspace.restype = C.c_int
+        self._workspace = buf
+        _check(self.lib.hb_set_workspace(self.ctx, C.c_void_p(buf.data_ptr()),
+                                         buf.numel() * buf.element_size()), self.ctx)
+
     def dump(self, path):
         """hb_dump: a text description of the context into the file at path."""
         self.lib.hb_dump.argtypes = [C.c_void_p, C.c_char_p]
@@ -399,7 +420,9 @@ def _mlp_fns():
     lib.hb_mlp_adam.restype = C.c_int
     lib.hb_mlp_predict.argtypes = [vp, vp, i64, vp, vp]
     lib.hb_mlp_predict.restype = C.c_int
-    lib.hb_mlp_train.argtypes = [vp, vp, vp, vp, i64, i64, i32, C.c_float, C.POINTER(C.c_float), vp]
+    lib.hb_mlp_train_params.argtypes = [vp, vp, vp, vp, i64, i64, i32, C.c_float, C.POINTER(C.c_float), vp]
+    lib.hb_mlp_train_params.restype = C.c_int
+    lib.hb_mlp_train.argtypes = [vp, C.POINTER(hb_mlp_dataset), vp, C.POINTER(hb_stats), vp]
     lib.hb_mlp_train.restype = C.c_int
     lib.hb_diag_features.argtypes = [vp, C.POINTER(hb_blocks), vp, i32, vp, vp]
     lib.hb_diag_features.restype = C.c_int
@@ -429,11 +452,25 @@ def mlp_adam(params, grads, m, v, step, lr, stream=None):
                                   _stream_handle(stream)))
 
 
+class hb_mlp_dataset(C.Structure):
+    _fields_ = [("n", C.c_int64), ("feats", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p), ("batch", C.c_int64),
+                ("steps", C.c_int32), ("lr", C.c_float)]
+
+
+def mlp_train_ctx(H, params, feats, a, b, batch, steps, lr, stream=None):
+    """hb_mlp_train: Adam on the data set with the context's memory; the trained
+    network becomes H's preconditioner network.  Returns the stats (mlp_loss)."""
+    d = hb_mlp_dataset(feats.shape[0], feats.data_ptr(), a.data_ptr(), b.data_ptr(), batch, steps, lr)
+    st = hb_stats()
+    _check(_mlp_fns().hb_mlp_train(H.ctx, C.byref(d), _ptr(params), C.byref(st), _stream_handle(stream)), H.ctx)
+    return st
+
+
 def mlp_train(params, feats, a, b, batch, steps, lr, stream=None):
-    """hb_mlp_train: Adam over consecutive windows of the data set, params updated in place;
+    """hb_mlp_train_params: Adam over consecutive windows of the data set, params updated in place;
     returns the loss of the last window."""
     loss = C.c_float(0.0)
-    _check(_mlp_fns().hb_mlp_train(_ptr(params), _ptr(feats), _ptr(a), _ptr(b), feats.shape[0], batch, steps, lr,
+    _check(_mlp_fns().hb_mlp_train_params(_ptr(params), _ptr(feats), _ptr(a), _ptr(b), feats.shape[0], batch, steps, lr,
                                    C.byref(loss), _stream_handle(stream)))
     return loss.value
 

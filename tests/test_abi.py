@@ -53,7 +53,7 @@ def test_struct_layouts_match_the_binding(tmp_path):
     if cc is None:
         pytest.skip("no host C compiler")
     structs = [hb.hb_group, hb.hb_problem, hb.hb_options, hb.hb_layout, hb.hb_blocks, hb.hb_stats,
-               hb.hb_mlp_weights]
+               hb.hb_mlp_weights, hb.hb_mlp_dataset]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hb.h"', "int main(void) {"]
     for S in structs:
         name = S.__name__
