@@ -142,7 +142,11 @@ typedef struct {
     int32_t class4_path;      /* mixed build, class 4: 0 = tensor cores for groups of 32..64 states and
                                  the double-float kernel for the rest; 1 = the double-float kernel
                                  only; 2 = tensor cores for every group of 1..64 states */
-    int32_t reserved[9];
+    int32_t mlp_stall_iters;  /* HB_PRECOND_MLP: the learned factor is dropped for the rest of a solve
+                                 when the largest wanted residual has not fallen by 2^mlp_stall_log2
+                                 over the last mlp_stall_iters iterations; 0 = 10 (1..1000) */
+    int32_t mlp_stall_log2;   /* 0 = 1, i.e. halved (1..60) */
+    int32_t reserved[7];
 } hb_options;
 
 typedef struct {
@@ -291,6 +295,36 @@ int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, int32_t max_
 int hb_target_diag(const hb_problem *p, int32_t g, int32_t k, double tol, int32_t max_iter, double *energies,
                    double *ci, hb_stats *st, void *stream);
 
+/* Sharded build over nranks processes (Section 3.1, the distributed
+   prototype contraction with the reduction of Eq. 11, and Section 3.2, the
+   distributed matrix).  Rank r of R:
+     1. hb_build_contract: the target-side contraction (Eq. 8) over the bra
+        determinants [ndet r / R, ndet (r + 1) / R) of every group pair gives
+        this rank's share of the contracted coefficient rows, written to
+        `partial` (device, hb_shard_coef_len doubles: for every group pair in
+        order, its state pairs x the padded label count);
+     2. the caller sums the partials of all ranks (an all-reduce, NCCL for
+        instance) into `reduced`, the same on every rank;
+     3. hb_build_expand: with the reduced rows, this rank's share of the rest:
+        the continuum-continuum tiles r, r + R, ... of Eq. 7 (rank 0 also the
+        rows with j == j' on the mixed path), the class-4 rows and the L2 rows
+        [n_l2 r / R, n_l2 (r + 1) / R) (an L2 entry below the diagonal is
+        written by the rank that owns its mirror's row).
+   Every element of the result is written by exactly one rank; what a rank
+   does not write it leaves as it was, so the ranks' zero-initialised outputs
+   add up to the whole matrix (the L2 row pointers included).  The contraction
+   sums of a rank run in the order of the one-rank build; the reduction adds
+   the ranks' partial sums, so results agree with hb_build_blocks to the
+   rounding of that reordering.  With the target-energy substitution rank 0
+   adds the energies.  The plan of the share is kept for the next call.
+   Errors: HB_ERR_INVALID_ARG (rank outside 0..nranks-1, NULL buffers),
+   HB_ERR_OOM, HB_ERR_CUDA, HB_ERR_TIMEOUT. */
+int hb_shard_coef_len(const hb_ctx *ctx, int64_t *len);
+int hb_build_contract(hb_ctx *ctx, int32_t precision, int32_t rank, int32_t nranks, double *partial, hb_stats *st,
+                      void *stream);
+int hb_build_expand(hb_ctx *ctx, int32_t precision, int32_t rank, int32_t nranks, const double *reduced,
+                    const hb_blocks *out, hb_stats *st, void *stream);
+
 /* Stage a problem whose orbitals and integrals are those of `base` (for
    instance another spatial-symmetry or spin-coupling block of the same
    molecule): the integrals, the expansion panel and its tensor-core slices are
@@ -372,7 +406,7 @@ typedef struct {
 /* Weights of the network used by hb_diag with HB_PRECOND_MLP: 8 inputs,
    width 64 (w1 [64][8], b1 [64], w2 [64][64], b2 [64], w3 [64], b3 [1]);
    stored as FP16, biases FP32.  The factor for row i and Ritz value theta is
-   w = 4^tanh(o), o = w3 . relu(w2 relu(w1 f + b1) + b2) + b3, applied as
+   w = 256^tanh(o), o = w3 . relu(w2 relu(w1 f + b1) + b2) + b3, applied as
    t_i = w r_i / (H_ii - theta).  A non-finite factor falls back to 1. */
 int hb_mlp_set(hb_ctx *ctx, const hb_mlp_weights *w);
 

@@ -2,7 +2,7 @@
 
 ORACLE / TEST INFRASTRUCTURE ONLY.
 
-w(f) = 4^tanh(o), o = w3 . relu(W2 relu(W1 f + b1) + b2) + b3; loss =
+w(f) = 256^tanh(o), o = w3 . relu(W2 relu(W1 f + b1) + b2) + b3; loss =
 mean_i (w(f_i) a_i - b_i)^2.  The weights are rounded to FP16 first (the
 network's storage format), as the CUDA forward pass does; the gradient is
 with respect to the (unrounded) parameters through that rounding taken as the
@@ -14,7 +14,7 @@ import numpy as np
 
 IN, W = 8, 64
 SHAPES = [(W, IN), (W,), (W, W), (W,), (W,), (1,)]
-LOG4 = np.log(4.0)
+LOGR = np.log(256.0)
 
 
 def unpack(p):
@@ -48,18 +48,18 @@ def forward(p, f):
 
 def factor(p, f):
     o, _ = forward(p, f)
-    return np.exp(LOG4 * np.tanh(o))
+    return np.exp(LOGR * np.tanh(o))
 
 
 def loss_grad(p, f, a, b):
     w1, b1, w2, b2, w3, b3 = _round_weights(unpack(p))
     o, (z1, h1, z2, h2) = forward(p, f)
     th = np.tanh(o)
-    w = np.exp(LOG4 * th)
+    w = np.exp(LOGR * th)
     err = w * a - b
     n = f.shape[0]
     loss = np.mean(err ** 2)
-    do = 2.0 * err * a * w * LOG4 * (1.0 - th ** 2) / n
+    do = 2.0 * err * a * w * LOGR * (1.0 - th ** 2) / n
     g_w3 = h2.T @ do
     g_b3 = np.array([do.sum()])
     d2 = np.outer(do, w3) * (z2 > 0)

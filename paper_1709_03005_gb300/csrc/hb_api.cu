@@ -211,6 +211,8 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
         return fail(ctx, HB_ERR_INVALID_ARG, "class4_threads must be 0, 32, 64 or 128");
     if (o && (o->class4_path < 0 || o->class4_path > 2))
         return fail(ctx, HB_ERR_INVALID_ARG, "class4_path must be 0, 1 or 2");
+    if (o && (o->mlp_stall_iters < 0 || o->mlp_stall_iters > 1000 || o->mlp_stall_log2 < 0 || o->mlp_stall_log2 > 60))
+        return fail(ctx, HB_ERR_INVALID_ARG, "mlp_stall_iters must be 0..1000 and mlp_stall_log2 0..60");
     const int W = p->n_words, nw = 2 * W;
     // electron counts: every target determinant has the same alpha/beta split,
     // the continuum electron sets the L2 split
@@ -365,6 +367,8 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         ctx->force_c4_states = o->class4_states;
         ctx->force_c4_threads = o->class4_threads;
         ctx->c4_path = o->class4_path;
+        if (o->mlp_stall_iters > 0) ctx->stall_iters = o->mlp_stall_iters;
+        if (o->mlp_stall_log2 > 0) ctx->stall_log2 = o->mlp_stall_log2;
     }
     ctx->Pt = (int64_t)p->n_to * (p->n_to + 1) / 2;
     ctx->K = (int)(ctx->Pt + (int64_t)p->n_to * p->n_to + 2);
@@ -704,6 +708,130 @@ extern "C" int hb_target_diag(const hb_problem *p, int32_t g, int32_t k, double 
     return rc;
 }
 
+// ------------------------------------------------------------ sharded build
+
+extern "C" int hb_shard_coef_len(const hb_ctx *ctx, int64_t *len) {
+    if (!ctx || !len) return fail(nullptr, HB_ERR_INVALID_ARG, "NULL argument");
+    int64_t n = 0;
+    for (auto &P : ctx->gps) n += (int64_t)P.n_nn * ctx->Kpad;
+    *len = n;
+    return HB_OK;
+}
+
+// The cached plan of this context's share (rank of nranks), pointed at out.
+static int shard_plan(hb_ctx *ctx, int precision, int rank, int nranks, const hb_blocks *out, hb::Plan **plan,
+                      cudaStream_t s) {
+    std::string err;
+    hb::Plan *p = (hb::Plan *)ctx->shard_plan;
+    if (p && !plan_is_shard(p, precision, rank, nranks)) {
+        cudaStreamSynchronize(s);
+        plan_destroy(p);
+        p = nullptr;
+        ctx->shard_plan = nullptr;
+    }
+    if (!p) {
+        hb_ctx *one[1] = {ctx};
+        int rc = plan_create(one, 1, out, precision, &p, &err, s, rank, nranks);
+        if (rc != HB_OK) return fail(ctx, rc, err);
+        ctx->shard_plan = p;
+    } else if (!plan_outputs_equal(p, out)) {
+        int rc = plan_set_outputs(p, out, &err, s);
+        if (rc != HB_OK) return fail(ctx, rc, err);
+    }
+    *plan = p;
+    return HB_OK;
+}
+
+static int shard_args(hb_ctx *ctx, int precision, int rank, int nranks) {
+    if (precision != HB_FP64 && precision != HB_MIXED)
+        return fail(ctx, HB_ERR_INVALID_ARG, "precision must be HB_FP64 or HB_MIXED");
+    if (nranks < 1 || rank < 0 || rank >= nranks) return fail(ctx, HB_ERR_INVALID_ARG, "need 0 <= rank < nranks");
+    return HB_OK;
+}
+
+extern "C" int hb_build_contract(hb_ctx *ctx, int32_t precision, int32_t rank, int32_t nranks, double *partial,
+                                 hb_stats *st, void *stream) {
+    if (!ctx) return fail(nullptr, HB_ERR_INVALID_ARG, "NULL argument");
+    int rc = shard_args(ctx, precision, rank, nranks);
+    if (rc != HB_OK) return rc;
+    int64_t len = 0;
+    hb_shard_coef_len(ctx, &len);
+    if (len > 0 && !partial) return fail(ctx, HB_ERR_INVALID_ARG, "partial is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    // the contraction writes no output block: a cached plan of this share is
+    // used as it is, a new one is made without outputs
+    hb::Plan *p = (hb::Plan *)ctx->shard_plan;
+    if (!p || !plan_is_shard(p, precision, rank, nranks)) {
+        hb_blocks none{};
+        rc = shard_plan(ctx, precision, rank, nranks, &none, &p, s);
+        if (rc != HB_OK) return rc;
+    }
+    // the stage timers belong to whole builds: this phase runs untimed
+    plan_set_phase(p, 1);
+    std::string err;
+    int launches = 0;
+    rc = plan_run(p, s, false, false, &launches, &err);
+    plan_set_phase(p, 0);
+    if (rc != HB_OK) return fail(ctx, rc, err);
+    // this rank's contracted coefficient rows, group pair after group pair
+    int64_t off = 0;
+    for (auto &P : ctx->gps) {
+        const size_t n = (size_t)P.n_nn * ctx->Kpad;
+        CK(cudaMemcpyAsync(partial + off, P.A, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        off += (int64_t)n;
+    }
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->kernel_launches = launches;
+    }
+    return HB_OK;
+}
+
+extern "C" int hb_build_expand(hb_ctx *ctx, int32_t precision, int32_t rank, int32_t nranks, const double *reduced,
+                               const hb_blocks *out, hb_stats *st, void *stream) {
+    if (!ctx || !out) return fail(ctx, HB_ERR_INVALID_ARG, "NULL argument");
+    int rc = shard_args(ctx, precision, rank, nranks);
+    if (rc != HB_OK) return rc;
+    int64_t len = 0;
+    hb_shard_coef_len(ctx, &len);
+    if (len > 0 && !reduced) return fail(ctx, HB_ERR_INVALID_ARG, "reduced is NULL");
+    if (ctx->Dc > 0 && !out->Hcc) return fail(ctx, HB_ERR_INVALID_ARG, "Hcc is NULL");
+    if (ctx->Dc > 0 && ctx->n_l2 > 0 && !out->Hlc) return fail(ctx, HB_ERR_INVALID_ARG, "Hlc is NULL");
+    if (ctx->n_l2 > 0 && (!out->l2_row_ptr || !out->l2_col || !out->l2_val))
+        return fail(ctx, HB_ERR_INVALID_ARG, "L2 CSR arrays are NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    hb::Plan *p = nullptr;
+    rc = shard_plan(ctx, precision, rank, nranks, out, &p, s);
+    if (rc != HB_OK) return rc;
+    // the summed coefficient rows of all ranks in place of this rank's
+    int64_t off = 0;
+    for (auto &P : ctx->gps) {
+        const size_t n = (size_t)P.n_nn * ctx->Kpad;
+        CK(cudaMemcpyAsync(P.A, reduced + off, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        if (precision == HB_MIXED && P.A_df) split_df(P.A, (int64_t)n, P.A_df, s);
+        off += (int64_t)n;
+    }
+    plan_set_phase(p, 2);
+    std::string err;
+    int launches = 0;
+    rc = plan_run(p, s, false, false, &launches, &err);
+    plan_set_phase(p, 0);
+    if (rc != HB_OK) return fail(ctx, rc, err);
+    if (precision == HB_MIXED) {
+        int word = 0;
+        CK(cudaStreamSynchronize(s));
+        if (plan_error_word(p, &word) != HB_OK) return fail(ctx, HB_ERR_CUDA, "reading the mixed error word");
+        if (word != 0) return fail(ctx, HB_ERR_TIMEOUT, "a tensor-core kernel gave up waiting (code " + std::to_string(word) + ")");
+    }
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        st->kernel_launches = launches;
+    }
+    return HB_OK;
+}
+
 extern "C" int hb_workspace_size(hb_ctx *ctx, int32_t precision, int32_t diag_k, int32_t precond, int64_t *bytes,
                                  void *stream) {
     if (!ctx || !bytes) return fail(ctx, HB_ERR_INVALID_ARG, "NULL argument");
@@ -818,10 +946,14 @@ extern "C" const char *hb_last_error(const hb_ctx *ctx) {
 }
 
 void hb::release_lazy(hb_ctx *ctx) {
+    if (ctx->plan || ctx->shard_plan) cudaDeviceSynchronize();
     if (ctx->plan) {
-        cudaDeviceSynchronize();
         plan_destroy((hb::Plan *)ctx->plan);
         ctx->plan = nullptr;
+    }
+    if (ctx->shard_plan) {
+        plan_destroy((hb::Plan *)ctx->shard_plan);
+        ctx->shard_plan = nullptr;
     }
     release_mixed(ctx);
     hb::release_c4tc(ctx);
@@ -838,10 +970,14 @@ void hb::release_lazy(hb_ctx *ctx) {
 
 extern "C" void hb_destroy(hb_ctx *ctx) {
     if (!ctx) return;
+    if (ctx->plan || ctx->shard_plan) cudaDeviceSynchronize();
     if (ctx->plan) {
-        cudaDeviceSynchronize();
         plan_destroy((hb::Plan *)ctx->plan);
         ctx->plan = nullptr;
+    }
+    if (ctx->shard_plan) {
+        plan_destroy((hb::Plan *)ctx->shard_plan);
+        ctx->shard_plan = nullptr;
     }
     release_mixed(ctx);
     hb::release_c4tc(ctx);

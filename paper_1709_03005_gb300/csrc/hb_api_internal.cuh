@@ -108,6 +108,8 @@ struct hb_ctx {
     int split_slices = 5;
     int autotune = 0;
     int force_tile = 0, force_c4_states = 0, force_c4_threads = 0;   // 0: chosen by the plan
+    int stall_iters = 10;    // learned-factor stall check: window and required fall (2^stall_log2)
+    int stall_log2 = 1;
     int c4_path = 0;         // mixed class 4: 0 tensor cores for 32..64 states, 1 double-float only, 2 tensor cores for 1..64
     int64_t Pt = 0;
     int K = 0, Kpad = 0;
@@ -138,6 +140,7 @@ struct hb_ctx {
     hb::DevPool pool;        // device memory beyond the staged problem
     hb_ctx *base = nullptr;  // context whose staged integrals this one borrows (or null)
     void *plan = nullptr;    // cached grouped-launch plan of this context's own builds (k_plan.cu)
+    void *shard_plan = nullptr;   // cached plan of this context's share of a sharded build
     void *diag = nullptr;   // Davidson workspace (k_davidson.cu)
     void *mlp = nullptr;    // learned preconditioner weights (k_mlp.cu)
     void *c4tc = nullptr;   // class-4 tensor-core operands (k_class4_tc.cu)

@@ -15,7 +15,11 @@ struct Plan;
 // count) writing into outs[i].  Prepares the tensor-core operands when
 // precision is HB_MIXED.  Returns HB_OK or an error with *err set.
 int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision, hb::Plan **out, std::string *err,
-                cudaStream_t s);
+                cudaStream_t s, int shard_r = 0, int shard_n = 1);
+// Phase of the next plan_run of a sharded plan: 1 the contraction only, 2 the
+// rest, 0 everything; and whether a plan is the shard (precision, r, n).
+void plan_set_phase(hb::Plan *p, int phase);
+bool plan_is_shard(const hb::Plan *p, int precision, int r, int n);
 // Point the plan's tasks at new output blocks (re-uploads the task tables).
 int plan_set_outputs(hb::Plan *p, const hb_blocks *outs, std::string *err, cudaStream_t s);
 bool plan_outputs_equal(const hb::Plan *p, const hb_blocks *outs);

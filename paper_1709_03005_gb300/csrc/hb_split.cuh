@@ -24,8 +24,9 @@ int split_tile_heuristic(int cn, int cnp);
 int g_slice(const hb::Grouped<hb::SliceTask> &g, int64_t R, int Kpad, int S, int skip_col, void *out,
             cudaStream_t s);
 // lg: tile arrangement (3..5, see SplitTask); every task of g must use it
+// shard_r, shard_n: the launch takes tiles shard_r, shard_r + shard_n, ... only
 int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const hb::Grouped<hb::SplitTask> &g,
-            int kblocks, const hb::ExpCol *cols, int *err, cudaStream_t s);
+            int kblocks, const hb::ExpCol *cols, int *err, cudaStream_t s, int shard_r = 0, int shard_n = 1);
 int64_t blocks_diag_rows(int j_lo, int j_hi, int n_nn);
 int diag_rows_ny(int n_nn);
 int g_diag_rows(const hb::Grouped<hb::DRTask> &g, cudaStream_t s);

@@ -134,6 +134,7 @@ struct ATask {          // contracted coefficient rows A[(n,n')][k]
     double *A;
     float2 *A_df;             // float-pair copy of A (mixed build)
     const double *En;         // target-energy substitution: the group's state energies, or null
+    int no_En;                // a shard other than the first: the substituted energies are left out
 };
 
 // One column of a merged expansion block: a state pair (n, n') of one group
@@ -231,6 +232,7 @@ struct L2Task {         // classes 2 and 8: L2-L2 CSR of one Hamiltonian
     // non-null: entries below the diagonal of row r are [row_ptr[r], row_ptr[r] +
     // low_ptr[r + 1] - low_ptr[r]) and come from g_l2_mirror; only col >= row here
     const int64_t *low_ptr;
+    int row_lo, row_hi;       // the rows evaluated (all of them unless sharded)
 };
 
 struct L2MTask {        // classes 2 and 8: the entries below the diagonal from their mirrors
@@ -239,6 +241,7 @@ struct L2MTask {        // classes 2 and 8: the entries below the diagonal from 
     int64_t n;
     int32_t *col;
     double *val;
+    int src_lo, src_hi;        // only entries whose mirror's row (their column) is in [src_lo, src_hi)
 };
 
 // ------------------------------------------------------------ launchers
@@ -271,7 +274,8 @@ int g_gdiag(const Grouped<GDTask> &partial, const Grouped<GDTask> &reduce, size_
 int64_t blocks_gdiag_partial(int ndet, int n_to, int ns);
 int64_t blocks_gdiag_reduce(int n_to, int ns);
 size_t smem_gdiag(int ns);
-int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s);
+// shard_r, shard_n: only the blocks shard_r, shard_r + shard_n, ... of the grid do their tile
+int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s, int shard_r = 0, int shard_n = 1);
 // dfloat = 0: FP64 (128 threads, 32 states a pass); 1: double-float with
 // ns_tile states a pass (a multiple of 8 up to 64) and jt threads a block (32, 64 or 128)
 int g_class4(const Grouped<C4Task> &g, int W, int dfloat, int ns_tile, int jt, cudaStream_t s);

@@ -888,7 +888,8 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
     std::vector<double> theta;
     float *wts = nullptr;
     int fallbacks = 0;
-    constexpr int kStall = 10;
+    const int kStall = ctx->stall_iters;
+    const double stall_fall = std::ldexp(1.0, -ctx->stall_log2);
     int refreshes = 0, fp64_iters = 0;
     std::vector<double> res_hist;
     // projected matrix T = V^T A V, kept up to date on the host: the full
@@ -987,10 +988,11 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         if (q <= 0) break;
         cudaMemcpyAsync(w->idx, which.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, s);
         // the learned factor is dropped for the rest of the solve when the
-        // largest wanted residual has not halved over the last kStall iterations
+        // largest wanted residual has not fallen by 2^stall_log2 (halved by
+        // default) over the last kStall iterations
         res_hist.push_back(maxres);
         if (precond == HB_PRECOND_MLP && (int)res_hist.size() > kStall &&
-            maxres > 0.5 * res_hist[res_hist.size() - 1 - kStall]) {
+            maxres > stall_fall * res_hist[res_hist.size() - 1 - kStall]) {
             precond = HB_PRECOND_DIAG;
             wts = nullptr;
             ++fallbacks;

@@ -54,9 +54,10 @@ constexpr int BM = 64, BN = 64, BK = 16;
 
 __global__ void __launch_bounds__(256)
 expand_fp64_kernel(const XTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks,
-                   const ExpCol *__restrict__ cols) {
+                   const ExpCol *__restrict__ cols, int shard_r, int shard_n) {
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
+    if ((int)(blockIdx.x % (unsigned)shard_n) != shard_r) return;   // another shard's tile
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const XTask &T = tasks[ti];
     const double *__restrict__ P = T.P;
@@ -139,9 +140,9 @@ int64_t blocks_expand_fp64(int cn, int cnp, int N) {
     return (int64_t)expand_fp64_mtiles(cn, cnp) * ((N + BN - 1) / BN);
 }
 
-int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s) {
+int g_expand_fp64(const Grouped<XTask> &g, const ExpCol *cols, cudaStream_t s, int shard_r, int shard_n) {
     if (g.blocks <= 0) return 0;
-    expand_fp64_kernel<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n, cols);
+    expand_fp64_kernel<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n, cols, shard_r, shard_n);
     return 1;
 }
 

@@ -2,7 +2,7 @@
 // correction row by row (not in the paper; plain diagonal Davidson remains the
 // fallback and the reference).
 //
-//   t_i = w(f_i) r_i / (H_ii - theta),   w = 4^tanh(o),   o = MLP(f)
+//   t_i = w(f_i) r_i / (H_ii - theta),   w = 256^tanh(o),   o = MLP(f)
 //   MLP: h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), o = w3 . h2 + b3
 // with n_in = 8 features, width 64, weights rounded to FP16 in the forward
 // pass (inference stores them as FP16) and FP32 accumulation.
@@ -12,8 +12,11 @@
 //   f3 = E_n - theta for a continuum row of target state n (0 for L2),
 //   f4 = h_jj of its continuum orbital (0 for L2), f5 = theta - theta_0,
 //   f6 = H_ii, f7 = group index / number of groups (1 for L2).
-// Training minimises sum_i (w(f_i) a_i - b_i)^2 with a = r/(H_ii - theta) and
-// b the exact correction; the gradient is taken by a hand-written backward
+// The range [1/256, 256] lets the factor damp rows whose H_ii - theta is small
+// by two orders of magnitude (a shifted denominator |d| / (|d| + delta) does
+// that, and a floor of 1/4 loses its gain).  Training minimises
+// sum_i (w(f_i) a_i - b_i)^2 for given targets a, b (a = 1 and b a wanted
+// factor fits the factor itself); the gradient is taken by a hand-written backward
 // pass whose weight gradients are fixed-order chunked sums.
 #include <cuda_fp16.h>
 
@@ -46,7 +49,7 @@ using namespace hb;
 
 namespace {
 
-constexpr float kLog4 = 1.3862943611198906f;
+constexpr float kLogR = 5.545177444479562f;   // log 256: w in [1/256, 256]
 
 // offsets inside the packed parameter vector
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + MLP_W * MLP_IN, OFF_W2 = OFF_B1 + MLP_W, OFF_B2 = OFF_W2 + MLP_W * MLP_W,
@@ -116,11 +119,11 @@ __global__ void mlp_fwd_bwd_kernel(const float *__restrict__ params, const float
     for (int c = 0; c < MLP_IN; ++c) f[c] = feats[i * MLP_IN + c];
     const float o = mlp_forward(P, f, h1, h2);
     const float th = tanhf(o);
-    const float w = expf(kLog4 * th);
+    const float w = expf(kLogR * th);
     const float a = ta[i], b = tb[i];
     const float err = w * a - b;
     loss[i] = err * err;
-    const float dout = 2.0f * err * a * w * kLog4 * (1.0f - th * th);   // dL/do
+    const float dout = 2.0f * err * a * w * kLogR * (1.0f - th * th);   // dL/do
     DO[i] = dout;
     float d2[MLP_W];
 #pragma unroll
@@ -205,7 +208,7 @@ __global__ void mlp_predict_kernel(const float *__restrict__ params, const float
     float f[MLP_IN], h1[MLP_W], h2[MLP_W];
 #pragma unroll
     for (int c = 0; c < MLP_IN; ++c) f[c] = feats[i * MLP_IN + c];
-    out[i] = expf(kLog4 * tanhf(mlp_forward(P, f, h1, h2)));
+    out[i] = expf(kLogR * tanhf(mlp_forward(P, f, h1, h2)));
 }
 
 // ------------------------------------------------------------ inside hb_diag
@@ -237,7 +240,7 @@ __global__ void diag_mlp_kernel(const __half *__restrict__ wh, const float *__re
     float f[MLP_IN], h1[MLP_W], h2[MLP_W];
     features((float)d[i], (float)theta[j], (float)theta[0], ri, i, n, f);
     const float o = mlp_forward(P, f, h1, h2);
-    float v = expf(kLog4 * tanhf(o));
+    float v = expf(kLogR * tanhf(o));
     if (!isfinite(v)) v = 1.0f;
     w[(int64_t)j * n + i] = v;
 }

@@ -143,7 +143,19 @@ struct Plan {
     std::vector<TuneSplit> tune_split;
     std::vector<TuneC4> tune_c4;
     std::vector<TuneGamma> tune_gamma;
+    // sharded build (Section 3.1): rank shard_r of shard_n takes the bra
+    // determinants [ndet r / n, ndet (r + 1) / n) of every group pair in the
+    // prototype contraction, every shard_n-th expansion tile from shard_r, and
+    // the L2 rows [n_l2 r / n, n_l2 (r + 1) / n) of classes 4, 2 and 8.
+    // phase 1 runs the contraction only, phase 2 the rest, 0 everything.
+    int shard_r = 0, shard_n = 1, phase = 0;
+    std::vector<std::pair<int64_t, int64_t>> item_range;   // per group pair of ctxs[0]: its rows' gamma items
 };
+
+// First and last-plus-one of n items that rank r of R takes.
+inline std::pair<int64_t, int64_t> shard_range(int64_t n, int r, int R) {
+    return {n * r / R, n * (r + 1) / R};
+}
 
 }  // namespace hb
 
@@ -229,33 +241,47 @@ void fill_tasks(Plan &p) {
             const PVTask pvt{I, da, db, P.pairs, P.n_pairs, P.val, P.rowptr, A.ndet, P.same};
             p.pv.add(pvt, blocks_pair_values(P.n_pairs));
             if (P.same) p.pvd.add(pvt, blocks_diag_values(A.ndet));
+            // the bra rows this rank contracts (all of them unless sharded)
+            const auto mr = shard_range(A.ndet, p.shard_r, p.shard_n);
+            const int m0 = (int)mr.first, nm = (int)(mr.second - mr.first);
             // lanes over the states for at most 16 of them (two or more record
             // groups per warp), lanes over the records otherwise
             {
-                const SWTask sw{P.pairs, P.rowptr, P.val, A.ndet, Cb, Cb_df, B.ns, P.W};
-                if (B.ns <= 16) p.sws.add(sw, blocks_rows8(A.ndet));
-                else p.sw.add(sw, A.ndet);                    // a block per row
+                const SWTask sw{P.pairs, P.rowptr + m0, P.val, nm, Cb, Cb_df, B.ns, P.W + (int64_t)m0 * B.ns};
+                if (B.ns <= 16) p.sws.add(sw, blocks_rows8(nm));
+                else p.sw.add(sw, nm);                        // a block per row
             }
             if (B.ns > 16) p.sw_width = std::max(p.sw_width, B.ns <= 24 ? 24 : 32);
             const int ny = tn_ny(A.ns, B.ns);
             // E = C^T (H^N C'); S = C^T C within a group (identical determinants
-            // only, hb_init rejects repeats) and zero between groups
-            const TNTask te{Ca, P.W, Ca_df, reinterpret_cast<const float2 *>(P.W), A.ndet, A.ns, B.ns, ny, P.partial,
-                            P.E};
-            const TNTask ts{Ca, Ca, Ca_df, Ca_df, P.same ? A.ndet : 0, A.ns, B.ns, ny, P.partial_s, P.S};
+            // only, hb_init rejects repeats) and zero between groups; over this
+            // rank's bra rows
+            const double *Cm = Ca + (int64_t)m0 * A.ns, *Wm = P.W + (int64_t)m0 * B.ns;
+            const float2 *Cm_df = Ca_df ? Ca_df + (int64_t)m0 * A.ns : nullptr;
+            const TNTask te{Cm, Wm, Cm_df, reinterpret_cast<const float2 *>(Wm), nm, A.ns, B.ns, ny, P.partial, P.E};
+            const TNTask ts{Cm, Cm, Cm_df, Cm_df, P.same ? nm : 0, A.ns, B.ns, ny, P.partial_s, P.S};
             p.tn.add(te, blocks_tn_partial(te.n_rows, A.ns, B.ns));
             p.tn.add(ts, blocks_tn_partial(ts.n_rows, A.ns, B.ns));
             p.tnr.add(te, blocks_tn_reduce(A.ns, B.ns));
             p.tnr.add(ts, blocks_tn_reduce(A.ns, B.ns));
             p.smem_tn = std::max(p.smem_tn, smem_stage(A.ns, B.ns));
-            p.itf.add(IFTask{P.pairs, P.rowptr, A.ndet, da, W, ctx->n_to, ctx->n_elec, P.item_ptr, P.items},
-                      A.ndet);                                // a block per row
+            // the gamma items of this rank's rows are the contiguous run
+            // [item_ptr[m0], item_ptr[m1]) (items follow the records' order)
+            int64_t i0 = 0, n_it = P.n_items;
+            if (p.shard_n > 1) {
+                const auto &ir = p.item_range[&P - ctx->gps.data()];
+                i0 = ir.first;
+                n_it = ir.second - ir.first;
+            }
+            p.itf.add(IFTask{P.pairs, P.rowptr + m0, nm, da, W, ctx->n_to, ctx->n_elec, P.item_ptr + m0, P.items},
+                      nm);                                    // a block per row
             const int nc = P.n_chunks;
             const int64_t n_off = (int64_t)n_keys * nc;
+            GammaItem *its = P.items + i0;
             p.zero.add(ZTask{P.sort_off, n_off + 1}, blocks_zero(n_off + 1));
-            p.sort.add(SortTask{P.items, P.n_items, nc, n_keys, P.sort_off, P.sort_cur, P.order}, blocks_sort(P.n_items, n_keys));
+            p.sort.add(SortTask{its, n_it, nc, n_keys, P.sort_off, P.sort_cur, P.order}, blocks_sort(n_it, n_keys));
             p.scan.add(ScanTask{P.sort_off, n_off, P.sort_cur, P.sort_part}, blocks_scan(n_off));
-            const GTask gt{P.items, P.order, P.sort_off, nc, n_keys, Ca, Ca_df, A.ns, Cb, Cb_df, B.ns, ny, P.gamma};
+            const GTask gt{its, P.order, P.sort_off, nc, n_keys, Ca, Ca_df, A.ns, Cb, Cb_df, B.ns, ny, P.gamma};
             const int nout = A.ns * B.ns;
             bool warp = nout <= 64;
             if (warp) {
@@ -270,15 +296,17 @@ void fill_tasks(Plan &p) {
                 p.smem_gamma = std::max(p.smem_gamma, smem_stage(A.ns, B.ns));
             }
             if (P.same) {
-                const GDTask gd{da, W, ctx->n_to, A.ndet, A.ns, tn_ny(A.ns, A.ns), Ca, Ca_df, P.gdiag, P.gamma};
-                p.gdp.add(gd, blocks_gdiag_partial(A.ndet, ctx->n_to, A.ns));
+                const GDTask gd{da + (int64_t)m0 * 2 * W, W, ctx->n_to, nm, A.ns, tn_ny(A.ns, A.ns), Cm, Cm_df,
+                                P.gdiag, P.gamma};
+                p.gdp.add(gd, blocks_gdiag_partial(nm, ctx->n_to, A.ns));
                 p.gdr.add(gd, blocks_gdiag_reduce(ctx->n_to, A.ns));
                 p.smem_gd = std::max(p.smem_gd, smem_gdiag(A.ns));
             }
+            // with the target-energy substitution the energies are added once, by rank 0
             p.asmb.add(ATask{P.gamma, P.S, P.E, P.sort_off, nc, P.same, P.nn, P.n_nn, A.ns, B.ns, ctx->n_to,
                              ctx->cont_spin, ctx->Kpad,
                              ctx->e_core, P.A, p.precision == HB_MIXED ? P.A_df : nullptr,
-                             ctx->energy ? ctx->energy + A.e_off : nullptr},
+                             ctx->energy ? ctx->energy + A.e_off : nullptr, ctx->energy && p.shard_r != 0},
                        P.n_nn);
             p.flops += 2.0 * (double)A.cn * B.cn * P.n_nn * ctx->K;
             ++p.n_expand_tasks;
@@ -292,13 +320,16 @@ void fill_tasks(Plan &p) {
                 blocks.back().ctx = ctx;
             }
             blocks[it->second].members.push_back(Member{ctx, &P, &out});
-            if (p.precision == HB_MIXED) {
+            if (p.precision == HB_MIXED && p.shard_r == 0) {     // the j == j' rows: the first shard
                 const int j_lo = std::max(A.cf, B.cf), j_hi = std::min(A.cf + A.cn, B.cf + B.cn);
                 p.drows.add(DRTask{mixed_panel_diag(ctx), P.A_df, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, j_lo, j_hi, A.cf, A.cn,
                                    B.cf, B.cn, P.same, diag_rows_ny(P.n_nn), A.row_off, B.row_off, ctx->Dc, out.Hcc},
                             blocks_diag_rows(j_lo, j_hi, P.n_nn));
             }
         }
+        // the L2 rows of classes 4, 2 and 8 this rank builds
+        const auto lr = shard_range(ctx->n_l2, p.shard_r, p.shard_n);
+        const int l0 = (int)lr.first, nl = (int)(lr.second - lr.first);
         for (int g = 0; g < ctx->n_groups; ++g) {
             const GroupInfo &G = ctx->groups[g];
             GroupL2 &L = ctx->gl2[g];
@@ -311,7 +342,16 @@ void fill_tasks(Plan &p) {
                 C4TTask tt;
                 int64_t fb = 0, items = 0;
                 c4tc_tasks(ctx, g, out.Hlc, &ft, &fb, &tt, &items);
+                const size_t first = p.c4items.size();
                 c4tc_items(ctx, g, (int)p.c4t.tasks.size(), &p.c4items);
+                if (p.shard_n > 1) {
+                    // this rank's L2 rows only
+                    auto keep = std::remove_if(p.c4items.begin() + first, p.c4items.end(), [&](const C4Item &c) {
+                        return c.l < l0 || c.l >= l0 + nl;
+                    });
+                    p.c4items.erase(keep, p.c4items.end());
+                    items = (int64_t)(p.c4items.size() - first);
+                }
                 p.c4f.add(ft, fb);
                 p.c4t.add(tt, items);
                 continue;
@@ -331,18 +371,22 @@ void fill_tasks(Plan &p) {
                 p.c4v.push_back(Plan::C4Var{ns_tile, jt, Stage<C4Task>()});
                 var = &p.c4v.back();
             }
-            const C4Task c4t{I, L.pairs, L.rowptr, ctx->n_l2, dg, ctx->ci + G.ci_off,
+            const C4Task c4t{I, L.pairs, L.rowptr + l0, nl, dg, ctx->ci + G.ci_off,
                              ctx->ci_df ? ctx->ci_df + G.ci_off : nullptr, ctx->tttc_df, ctx->h_df, G.ns, G.cf, G.cn,
-                             ctx->cont_spin, class4_ny(G.cn, jt), G.row_off, ctx->Dc, out.Hlc};
-            var->st.add(c4t, blocks_class4(ctx->n_l2, G.cn, jt));
+                             ctx->cont_spin, class4_ny(G.cn, jt), G.row_off, ctx->Dc,
+                             out.Hlc ? out.Hlc + (int64_t)l0 * ctx->Dc : nullptr};
+            var->st.add(c4t, blocks_class4(nl, G.cn, jt));
             if (p.precision == HB_MIXED) p.tune_c4.push_back(TuneC4{c4t});
         }
         if (ctx->n_l2 > 0) {
             p.l2.add(L2Task{I, ctx->l2, ctx->n_l2, seg_count(ctx->n_l2), ctx->l2_rowptr, ctx->l2_seg_off, out.l2_row_ptr,
-                            out.l2_col, out.l2_val, ctx->e_core, ctx->l2_low_ptr},
+                            out.l2_col, out.l2_val, ctx->e_core, ctx->l2_low_ptr, l0, l0 + nl},
                      blocks_seg_rows8(ctx->n_l2, ctx->n_l2));
+            // an entry below the diagonal is copied by the rank that evaluates its
+            // mirror, whose row is the entry's column
             if (ctx->l2_low_ptr && ctx->l2_nlow > 0)
-                p.l2m.add(L2MTask{ctx->l2_mdst, ctx->l2_msrc, ctx->l2_mcol, ctx->l2_nlow, out.l2_col, out.l2_val},
+                p.l2m.add(L2MTask{ctx->l2_mdst, ctx->l2_msrc, ctx->l2_mcol, ctx->l2_nlow, out.l2_col, out.l2_val,
+                                  l0, l0 + nl},
                           (ctx->l2_nlow + kL2MirrorThreads - 1) / kL2MirrorThreads);
         }
     }
@@ -483,7 +527,7 @@ int upload(Plan &p, std::string *err, cudaStream_t s) {
 }  // namespace
 
 int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision, Plan **out, std::string *err,
-                cudaStream_t s) {
+                cudaStream_t s, int shard_r, int shard_n) {
     *out = nullptr;
     if (n < 1) { *err = "empty plan"; return HB_ERR_INVALID_ARG; }
     Plan *p = new Plan();
@@ -550,6 +594,24 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
             if (rc != HB_OK) *err = ctxs[i]->err;
         }
     if (rc != HB_OK) { plan_destroy(p); return rc; }
+    if (shard_n > 1) {
+        // a sharded plan serves one context; the gamma items of this rank's
+        // bra rows, per group pair, from the staged item offsets
+        p->shard_r = shard_r;
+        p->shard_n = shard_n;
+        for (auto &P : ctxs[0]->gps) {
+            const auto mr = shard_range(ctxs[0]->groups[P.g].ndet, shard_r, shard_n);
+            int64_t a = 0, b = 0;
+            cudaError_t e2 = cudaMemcpy(&a, P.item_ptr + mr.first, sizeof(int64_t), cudaMemcpyDeviceToHost);
+            if (e2 == cudaSuccess) e2 = cudaMemcpy(&b, P.item_ptr + mr.second, sizeof(int64_t), cudaMemcpyDeviceToHost);
+            if (e2 != cudaSuccess) {
+                *err = std::string("shard item ranges: ") + cudaGetErrorString(e2);
+                plan_destroy(p);
+                return HB_ERR_CUDA;
+            }
+            p->item_range.push_back({a, b});
+        }
+    }
     fill_tasks(*p);
     if (precision == HB_MIXED && p->coef_rows > 0) {
         rc = split_coef_alloc(ctxs[0], p->S, p->coef_rows, p->Kpad, &p->coef, &p->tm_coef, err);
@@ -732,6 +794,11 @@ int plan_autotune(Plan *p, cudaStream_t s, std::string *err) {
 
 bool plan_tuned(const Plan *p) { return p->tuned; }
 
+void plan_set_phase(Plan *p, int phase) { p->phase = phase; }
+bool plan_is_shard(const Plan *p, int precision, int r, int n) {
+    return p->precision == precision && p->shard_r == r && p->shard_n == n;
+}
+
 std::string plan_report(const Plan *p) {
     std::string r;
     char buf[160];
@@ -785,9 +852,16 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     // the L2 rows stay FP64: their sums are short and the kernel is bound by the
     // pair scan, where the longer double-float sums cost more than FP64 adds
     rec_on(p->ev[5], s2);
-    L += g_classify(p->cls_tl2.g, W, 1, s2);
+    // a sharded build runs in two phases: the contraction (1), then, with the
+    // reduced coefficient rows in place, classes 4, 2, 8 and the expansion (2)
+    const bool ph1 = p->phase != 2, ph2 = p->phase != 1;
+    if (ph2) L += g_classify(p->cls_tl2.g, W, 1, s2);
     rec_on(p->ev[8], s2);
-    if (p->c4t.g.blocks > 0) {
+    if (!ph2) {
+        rec_on(p->ev[7], s2);
+        rec_on(p->ev[4], s2);
+        rec_on(p->ev[3], s2);
+    } else if (p->c4t.g.blocks > 0) {
         // the tensor-core class-4 kernel and the expansion kernel each hold
         // whole SMs until their work is done, and the L2 rows' blocks do not
         // fit beside either: the L2 rows run beside the target side, then
@@ -817,36 +891,43 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
     // target side (Eq. 8) in three chains that meet at the coefficient rows:
     // the diagonal gamma needs only the determinants and CI vectors
     cudaStreamWaitEvent(sb, p->fork, 0);
-    L += g_gdiag(p->gdp.g, p->gdr.g, p->smem_gd, DF, sb);
-    cudaEventRecord(p->gd_done, sb);
-    L += g_classify(p->cls_tt.g, W, 0, s);
-    cudaEventRecord(p->k1_done, s);
-    // the gamma items of the single-excitation records, sorted by key, and gamma
-    cudaStreamWaitEvent(sa, p->k1_done, 0);
-    // the diagonal H^N values (a sequential sum per row) beside the others
-    L += g_diag_values(p->pvd.g, W, DF, sa);
-    cudaEventRecord(p->dv_done, sa);
-    L += g_item_fill(p->itf.g, sa);
-    L += g_zero(p->zero.g, sa);
-    L += g_sort_hist(p->sort.g, sa);
-    L += g_scan(p->scan.g, sa);
-    L += g_sort_scatter(p->sort.g, sa);
-    L += g_gamma(p->gam.g, p->smem_gamma, DF, sa);
-    L += g_gamma_warp(p->gamw.g, DF, sa);
-    cudaEventRecord(p->items_done, sa);
-    // H^N values, the sandwich and E, S
-    L += g_pair_values(p->pv.g, W, DF, s);
-    cudaStreamWaitEvent(s, p->dv_done, 0);
-    L += g_sandwich(p->sw.g, DF, p->sw_width, s);
-    L += g_sandwich_small(p->sws.g, DF, s);
-    L += g_tn_partial(p->tn.g, p->smem_tn, DF, s);
-    L += g_tn_reduce(p->tnr.g, DF, s);
-    cudaStreamWaitEvent(s, p->items_done, 0);
-    cudaStreamWaitEvent(s, p->gd_done, 0);
-    L += g_assemble(p->asmb.g, DF, s);
+    if (ph1) {
+        L += g_gdiag(p->gdp.g, p->gdr.g, p->smem_gd, DF, sb);
+        cudaEventRecord(p->gd_done, sb);
+        L += g_classify(p->cls_tt.g, W, 0, s);
+        cudaEventRecord(p->k1_done, s);
+        // the gamma items of the single-excitation records, sorted by key, and gamma
+        cudaStreamWaitEvent(sa, p->k1_done, 0);
+        // the diagonal H^N values (a sequential sum per row) beside the others
+        L += g_diag_values(p->pvd.g, W, DF, sa);
+        cudaEventRecord(p->dv_done, sa);
+        L += g_item_fill(p->itf.g, sa);
+        L += g_zero(p->zero.g, sa);
+        L += g_sort_hist(p->sort.g, sa);
+        L += g_scan(p->scan.g, sa);
+        L += g_sort_scatter(p->sort.g, sa);
+        L += g_gamma(p->gam.g, p->smem_gamma, DF, sa);
+        L += g_gamma_warp(p->gamw.g, DF, sa);
+        cudaEventRecord(p->items_done, sa);
+        // H^N values, the sandwich and E, S
+        L += g_pair_values(p->pv.g, W, DF, s);
+        cudaStreamWaitEvent(s, p->dv_done, 0);
+        L += g_sandwich(p->sw.g, DF, p->sw_width, s);
+        L += g_sandwich_small(p->sws.g, DF, s);
+        L += g_tn_partial(p->tn.g, p->smem_tn, DF, s);
+        L += g_tn_reduce(p->tnr.g, DF, s);
+        cudaStreamWaitEvent(s, p->items_done, 0);
+        cudaStreamWaitEvent(s, p->gd_done, 0);
+        L += g_assemble(p->asmb.g, DF, s);
+    } else {
+        cudaEventRecord(p->gd_done, sb);   // the auxiliary stream joins the capture
+        cudaStreamWaitEvent(s, p->gd_done, 0);
+    }
     rec(p->ev[1]);
     // expansion (Eq. 7): classes 1, 3, 5, 6, 7
-    if (p->precision == HB_MIXED) {
+    if (!ph2) {
+        // phase 1 ends with the coefficient rows
+    } else if (p->precision == HB_MIXED) {
         // with class 4 on the tensor cores, the expansion waits for it (see
         // the side stream above); the double-float class-4 kernel runs beside
         // the expansion, which was faster than running it first
@@ -856,7 +937,8 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
             L += g_slice(p->slc.g, p->coef_rows, p->Kpad, p->S, p->delta_col, p->coef, s);
             for (size_t i = 0; i < p->split.size(); ++i) {
                 rec(p->ev_split[2 * i]);
-                LX += g_split(p->split[i].panel_ctx, p->split[i].lg, &p->tm_coef, p->split[i].st.g, p->Kpad / 64, p->d_cols, p->err, s);
+                LX += g_split(p->split[i].panel_ctx, p->split[i].lg, &p->tm_coef, p->split[i].st.g, p->Kpad / 64, p->d_cols, p->err, s,
+                              p->shard_r, p->shard_n);
                 rec(p->ev_split[2 * i + 1]);
             }
             // the rows with j == j' (double-float); beside the split kernel they
@@ -864,7 +946,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
             L += g_diag_rows(p->drows.g, s);
         }
     } else {
-        LX += g_expand_fp64(p->x64.g, p->d_cols, s);
+        LX += g_expand_fp64(p->x64.g, p->d_cols, s, p->shard_r, p->shard_n);
     }
     L += LX;
     rec(p->ev[2]);

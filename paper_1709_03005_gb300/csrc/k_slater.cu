@@ -165,7 +165,9 @@ l2_csr_kernel(const L2Task *__restrict__ tasks, const int64_t *__restrict__ blk,
     const int rb = lb / T.nseg, sg = lb % T.nseg;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row = rb * kWarps + warp;
-    const bool active = row < n;
+    // a block whose rows are all outside this build's rows has nothing to do
+    if (rb * kWarps >= T.row_hi || (rb + 1) * kWarps <= T.row_lo) return;
+    const bool active = row < n && row >= T.row_lo && row < T.row_hi;
     int *q = queue[warp];
     uint64_t a[2 * W];
     int64_t pos = 0, end = 0;
@@ -257,8 +259,10 @@ __global__ void l2_mirror_kernel(const L2MTask *__restrict__ tasks, const int64_
     const L2MTask &T = tasks[ti];
     const int64_t i = (int64_t)(blockIdx.x - blk[ti]) * kL2MirrorThreads + threadIdx.x;
     if (i >= T.n) return;
+    const int c = T.mcol[i];
+    if (c < T.src_lo || c >= T.src_hi) return;
     const int64_t d = T.dst[i];
-    T.col[d] = T.mcol[i];
+    T.col[d] = c;
     T.val[d] = T.val[T.src[i]];
 }
 

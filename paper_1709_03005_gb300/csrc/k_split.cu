@@ -222,7 +222,10 @@ template <int S>
 __global__ void __launch_bounds__(NTHREADS, 1)
 split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_constant__ CUtensorMap tm_coef,
                     const SplitTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks, int n_tiles,
-                    int kblocks, const ExpCol *__restrict__ cols, int *err) {
+                    int kblocks, const ExpCol *__restrict__ cols, int *err, int shard_r, int shard_n) {
+    // this launch's tiles: shard_r, shard_r + shard_n, ... (all of them unless
+    // sharded), numbered t = 0, 1, ... so that every role walks the same list
+    const int n_local = n_tiles > shard_r ? (n_tiles - shard_r + shard_n - 1) / shard_n : 0;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *slots = base;                                  // [S][SLOT]
@@ -266,7 +269,8 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
         if (lane == 0) {
             int G = 0;                            // K blocks issued by this CTA over all its tiles
             bool ok = true;
-            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            for (int t = blockIdx.x; t < n_local && ok; t += gridDim.x) {
+                const int tile = shard_r + shard_n * t;
                 const TilePos p = tile_pos(tasks, blk, n_tasks, tile);
                 const int cx = tasks[p.ti].cfp + p.jjp0, cy = tasks[p.ti].cf + p.jj0;
                 const int crow = (int)(tasks[p.ti].coef_row0 + p.n0);
@@ -295,7 +299,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
             const uint64_t desc0 = smem_desc_sw128(smem_u32(slots));   // + (offset >> 4) per operand tile
             bool ok = true;
             int G = 0, C = 0;                     // K blocks and chunks over all tiles
-            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            for (int t = blockIdx.x; t < n_local && ok; t += gridDim.x) {
                 for (int c = 0; c < nchunks && ok; ++c, ++C) {
                     if (C > 0) ok = mbar_wait(acc_empty, (C - 1) & 1, err, 3);
                     if (!ok) break;
@@ -320,7 +324,8 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
         const int col0 = (ew >> 2) * EPI_COLS;
         const int row = q * 32 + lane;           // tile row = TMEM lane
         int C = 0, it = 0;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+        for (int t = blockIdx.x; t < n_local; t += gridDim.x, ++it) {
+            const int tile = shard_r + shard_n * t;
             const int buf = it & 1;
             // the buffer was last read by the stores of tile it-2, which every
             // epilogue warp finished before the barriers of tile it-1
@@ -911,16 +916,19 @@ int g_slice(const Grouped<SliceTask> &g, int64_t R, int Kpad, int S, int skip_co
 }
 
 int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const Grouped<SplitTask> &g, int kblocks,
-            const ExpCol *cols, int *err, cudaStream_t s) {
+            const ExpCol *cols, int *err, cudaStream_t s, int shard_r, int shard_n) {
     if (g.blocks <= 0) return 0;
     const MixedState &M = *panel_ctx->mixed;
     const CUtensorMap &tm_panel = M.tm_panel[lg - 3];
     const size_t smem = split_smem_bytes(M.slices);
     // persistent: one CTA per SM at most (each holds all of its SM's tensor memory)
     const int n_tiles = (int)g.blocks;
-    const unsigned grid = (unsigned)std::min(n_tiles, sm_count());
+    const int n_local = n_tiles > shard_r ? (n_tiles - shard_r + shard_n - 1) / shard_n : 0;
+    if (n_local <= 0) return 0;
+    const unsigned grid = (unsigned)std::min(n_local, sm_count());
 #define HB_SPLIT(SS) \
-    split_expand_kernel<SS><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, n_tiles, kblocks, cols, err)
+    split_expand_kernel<SS><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, n_tiles, kblocks, \
+                                                        cols, err, shard_r, shard_n)
     switch (M.slices) {
         case 2: HB_SPLIT(2); break;
         case 3: HB_SPLIT(3); break;

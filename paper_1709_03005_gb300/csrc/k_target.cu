@@ -624,7 +624,8 @@ __global__ void assemble_kernel(const ATask *__restrict__ tasks, const int64_t *
             if (DF) { const float h = (float)T.S[sidx]; vh = h; vl = (float)(T.S[sidx] - (double)h); }
             else v = T.S[sidx];
         } else if (k == Pt + nt2 + 1) {
-            const double x = T.En ? ((T.same && n == np) ? T.En[n] : 0.0) : T.E[sidx] + T.e_core * T.S[sidx];
+            const double x = T.En ? ((T.same && n == np && !T.no_En) ? T.En[n] : 0.0)
+                                  : T.E[sidx] + T.e_core * T.S[sidx];
             if (DF) { const float h = (float)x; vh = h; vl = (float)(x - (double)h); }
             else v = x;
         }

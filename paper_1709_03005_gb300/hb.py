@@ -39,8 +39,8 @@ class hb_problem(C.Structure):
 class hb_options(C.Structure):
     _fields_ = [("split_slices", C.c_int32), ("validate", C.c_int32), ("autotune", C.c_int32),
                 ("split_tile", C.c_int32), ("class4_states", C.c_int32), ("class4_threads", C.c_int32),
-                ("class4_path", C.c_int32),
-                ("reserved", C.c_int32 * 9)]
+                ("class4_path", C.c_int32), ("mlp_stall_iters", C.c_int32), ("mlp_stall_log2", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
 
 
 class hb_layout(C.Structure):
@@ -82,6 +82,7 @@ EXPORTS = ["hb_init", "hb_init_shared", "hb_batch_create", "hb_batch_launch", "h
            "hb_classify_noalloc", "hb_mlp_set", "hb_mlp_param_count", "hb_mlp_workspace_bytes", "hb_mlp_loss_grad",
            "hb_mlp_adam", "hb_mlp_train", "hb_mlp_train_params", "hb_mlp_predict", "hb_diag_features", "hb_batch_report", "hb_tuning_report",
            "hb_dump", "hb_target_diag", "hb_workspace_size", "hb_set_workspace",
+           "hb_shard_coef_len", "hb_build_contract", "hb_build_expand",
            "hb_last_error", "hb_destroy"]
 
 _lib = None
@@ -204,7 +205,8 @@ class Hamiltonian:
     """
 
     def __init__(self, problem, split_slices=0, validate=True, stream=None, base=None, autotune=False,
-                 split_tile=0, class4_states=0, class4_threads=0, class4_path=0):
+                 split_tile=0, class4_states=0, class4_threads=0, class4_path=0, mlp_stall_iters=0,
+                 mlp_stall_log2=0):
         import torch
         self.lib = load()
         self.base = base        # keeps a borrowed-integral base context alive
@@ -212,7 +214,7 @@ class Hamiltonian:
         keep = []
         self._problem, gs = _marshal_problem(p, keep)
         opts = hb_options(split_slices, 1 if validate else 0, 1 if autotune else 0, split_tile, class4_states,
-                          class4_threads, class4_path)
+                          class4_threads, class4_path, mlp_stall_iters, mlp_stall_log2)
         self.ctx = C.c_void_p()
         torch.cuda.init()
         if base is None:
@@ -286,6 +288,40 @@ class Hamiltonian:
         """Load a packed parameter vector (see unpack_mlp) for HB_PRECOND_MLP."""
         self.set_mlp(*unpack_mlp(packed))
 
+    # sharded build (hb_build_contract / hb_build_expand)
+    def shard_coef_len(self):
+        self.lib.hb_shard_coef_len.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+        self.lib.hb_shard_coef_len.restype = C.c_int
+        n = C.c_int64()
+        _check(self.lib.hb_shard_coef_len(self.ctx, C.byref(n)), self.ctx)
+        return n.value
+
+    def build_contract(self, precision, rank, nranks, partial=None, stream=None):
+        """This rank's contracted coefficient rows (a float64 device tensor)."""
+        import torch
+        self.lib.hb_build_contract.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                               C.POINTER(hb_stats), C.c_void_p]
+        self.lib.hb_build_contract.restype = C.c_int
+        if partial is None:
+            partial = torch.empty(max(self.shard_coef_len(), 1), dtype=torch.float64, device="cuda")
+        st = hb_stats()
+        _check(self.lib.hb_build_contract(self.ctx, precision, rank, nranks, _ptr(partial), C.byref(st),
+                                          _stream_handle(stream)), self.ctx)
+        return partial, st
+
+    def build_expand(self, precision, rank, nranks, reduced, blocks=None, stream=None):
+        """This rank's share of the blocks from the reduced coefficient rows;
+        blocks (zeros by default) keep what the rank does not write."""
+        self.lib.hb_build_expand.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                             C.POINTER(hb_blocks), C.POINTER(hb_stats), C.c_void_p]
+        self.lib.hb_build_expand.restype = C.c_int
+        b = blocks if blocks is not None else self.allocate()
+        bs = self.blocks_struct(b)
+        st = hb_stats()
+        _check(self.lib.hb_build_expand(self.ctx, precision, rank, nranks, _ptr(reduced), C.byref(bs), C.byref(st),
+                                        _stream_handle(stream)), self.ctx)
+        return b, st
+
     def workspace_size(self, precision=HB_MIXED, diag_k=0, precond=HB_PRECOND_DIAG, stream=None):
         """hb_workspace_size: device bytes the context's builds (and a solve
         for diag_k eigenpairs) take beyond hb_init."""
@@ -330,6 +366,17 @@ class Hamiltonian:
             self.close()
         except Exception:
             pass
+
+
+def sharded_build(H, precision, rank, nranks, all_reduce, blocks=None, stream=None):
+    """One rank's part of a sharded build (Section 3.1): the contraction over
+    this rank's bra determinants, all_reduce(partial) summing the partial
+    coefficient rows of every rank in place (torch.distributed.all_reduce over
+    NCCL under torchrun), then this rank's tiles and L2 rows.  Returns the
+    blocks: zero except where this rank wrote."""
+    partial, _ = H.build_contract(precision, rank, nranks, stream=stream)
+    all_reduce(partial)
+    return H.build_expand(precision, rank, nranks, partial, blocks, stream=stream)[0]
 
 
 def dense_from_blocks(b, dim=None):

@@ -1,27 +1,36 @@
 """Training data and training of the learned Davidson preconditioner.
 
-    python -m paper_1709_03005_gb300.precond train [--instances 24] [--out FILE]
+    python -m paper_1709_03005_gb300.precond train [--instances 200] [--out FILE]
     python -m paper_1709_03005_gb300.precond evaluate
     python -m paper_1709_03005_gb300.precond large [--k 200]    # the 60000-dimensional workload
 
-Data: plain (diagonal-preconditioned) block Davidson runs on seeded smaller
-Hamiltonians of the same families as the workloads, each built by this
-library.  At every iteration and for every unconverged Ritz pair j the sample
-rows are the library's features f_i (hb_diag_features), a_i = the diagonal
-correction r_i / (H_ii - theta_j) and b_i = the exact correction: the part of
-the true eigenvector (dense eigensolver, aligned in sign) outside the current
-basis.  Both are normalised per pair, so the network learns a row-wise factor
-that turns the diagonal correction towards the exact one.
+hb_diag with HB_PRECOND_MLP multiplies the diagonal correction of row i by a
+factor w(f_i) of the row's features.  The factor's label comes from solves of
+the method's own Hamiltonians by hb_diag itself:
 
-Training: Adam on mean_i (w(f_i) a_i - b_i)^2 with the library's forward,
-backward and update kernels (hb_mlp_loss_grad, hb_mlp_adam).  The result is
-saved as an .npz of the packed parameters and loaded with
-hb.Hamiltonian.set_mlp.
+1. candidates: shifted denominators w_delta(d) = |d| / (|d| + delta) of
+   d = H_ii - theta, which damp the rows whose diagonal is close to the Ritz
+   value; each is fitted by a network on real feature rows (hb_mlp_train_params
+   with a = 1, b = w_delta, so the loss is (w - w_delta)^2);
+2. every training instance (seeded, both Hamiltonian families, dimensions
+   about 1500-9000) is solved by hb_diag plain and with each candidate
+   network; the candidate with the fewest iterations labels the instance when
+   it saves at least ROBUST of them (iteration counts move by one or two with
+   any change of the correction, so a smaller saving is not a signal), else
+   the instance is labelled plain, w = 1;
+3. samples: the features of the instance's rows at the Ritz values of its
+   plain solve, each labelled with the instance's factor;
+4. the final network is trained on all samples with the library's forward,
+   backward and Adam kernels (hb_mlp_loss_grad, hb_mlp_adam).
+
+The result is saved as an .npz of the packed parameters and loaded with
+hb.Hamiltonian.set_mlp_params.
 """
 from __future__ import annotations
 
 import argparse
 import os
+import time
 
 import numpy as np
 
@@ -29,139 +38,148 @@ from . import hb, synth
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "data", "precond_mlp.npz")
+DELTAS = (0.03, 0.1, 0.3, 1.0)
+ROBUST = 3
 
 
 def training_problem(seed: int):
-    """A seeded smaller instance of the medium / precision families."""
+    """A seeded smaller instance of the medium (even seeds) or precision (odd
+    seeds) families: 20-40 target orbitals, 50-200 continuum orbitals, 5-20
+    target states, 1000-5000 L2 functions."""
     rng = np.random.default_rng(10_000 + seed)
-    n_to = int(rng.integers(12, 21))
+    n_to = int(rng.integers(20, 41))
     n_elec = int(rng.choice([6, 8]))
-    n_co = int(rng.integers(30, 81))
-    n_det = int(rng.integers(150, 401))
-    n_state = int(rng.integers(4, 11))
-    n_l2 = int(rng.integers(300, 1201))
+    n_co = int(rng.integers(50, 201))
+    n_state = int(rng.integers(5, 21))
+    n_det = int(rng.integers(max(n_state + 50, 300), 1501))
+    n_l2 = int(rng.integers(1000, 5001))
     cont = (-3.0, -0.5) if seed % 2 == 0 else (0.0, 50.0)
     return synth.make_problem(f"train{seed}", 20_000 + seed, n_to, n_co, n_elec, n_det, n_state, n_l2,
-                              rank=int(rng.integers(20, 41)), cont_diag=cont)
+                              rank=int(rng.integers(20, 61)), cont_diag=cont)
 
 
-def davidson_samples(problem, k, max_iter=200, tol=1e-8, max_pairs_per_iter=8):
-    """Run a plain block Davidson (the same method as hb_diag) in FP64 torch on
-    the library-built matrix and return float32 device tensors (f, a, b)."""
+def _features_at(H, blocks, theta, rows, rng):
+    """Feature rows (device float32) of `rows` random matrix rows at each Ritz value."""
     import torch
-    H = hb.Hamiltonian(problem)
-    blocks, _ = H.build(hb.HB_MIXED)
-    D = hb.dense_from_blocks(blocks)
-    n = D.shape[0]
-    lam, Xs = torch.linalg.eigh(D)
-    d = torch.diagonal(D).clone()
-    b = min(n, k + max(4, min(16, k // 2)))
-    mmax = min(n, max(5 * b, k + 4 * b))
-    idx = torch.argsort(d, stable=True)[:b]
-    V = torch.zeros((n, b), dtype=torch.float64, device=D.device)
-    V[idx, torch.arange(b, device=D.device)] = 1.0
-    AV = D @ V
-    fs, As, Bs = [], [], []
-    for it in range(max_iter):
-        T = V.T @ AV
-        T = 0.5 * (T + T.T)
-        theta, S = torch.linalg.eigh(T)
-        nr = min(V.shape[1], b)
-        X = V @ S[:, :nr]
-        R = AV @ S[:, :nr] - X * theta[:nr]
-        res = torch.linalg.norm(R, dim=0)
-        if bool((res[:k] <= tol).all()):
-            break
-        which = [j for j in range(nr) if res[j] > tol][:b]
-        feats = hb.diag_features(H, blocks, theta[:nr].cpu().numpy())       # [nr, n, 8]
-        for j in which[:max_pairs_per_iter]:
-            den = d - theta[j]
-            den = torch.where(den.abs() < 1e-4, torch.where(den < 0, -1e-4, 1e-4), den)
-            a = R[:, j] / den
-            xs = Xs[:, j] * torch.sign(Xs[:, j] @ X[:, j])
-            e = xs - V @ (V.T @ xs)
-            na, ne = torch.linalg.norm(a), torch.linalg.norm(e)
-            if na < 1e-30 or ne < 1e-30:
-                continue
-            a, e = a / na, e / ne
-            e = e * torch.sign(a @ e)
-            fs.append(feats[j]); As.append(a.float()); Bs.append(e.float())
-        if V.shape[1] + len(which) > mmax:
-            keep = min(V.shape[1], 2 * b, mmax - len(which))
-            V, AV = V @ S[:, :keep], AV @ S[:, :keep]
-        den = d[:, None] - theta[which][None, :]
-        den = torch.where(den.abs() < 1e-4, torch.where(den < 0, -1e-4, 1e-4), den)
-        Tn = R[:, which] / den
-        for _ in range(2):
-            Tn = Tn - V @ (V.T @ Tn)
-        Q, Rq = torch.linalg.qr(Tn)
-        keep = Rq.diagonal().abs() > 1e-10 * max(1.0, float(Rq.diagonal().abs().max()))
-        Q = Q[:, keep]
-        Q = Q - V @ (V.T @ Q)
-        Q, _ = torch.linalg.qr(Q)
-        V = torch.cat([V, Q], 1)
-        AV = torch.cat([AV, D @ Q], 1)
-    H.close()
-    if not fs:
-        return None
-    return torch.cat(fs), torch.cat(As), torch.cat(Bs), it + 1
+    f = hb.diag_features(H, blocks, np.asarray(theta))                 # [q, n, 8]
+    sel = torch.from_numpy(rng.choice(H.dim, min(rows, H.dim), replace=False)).cuda()
+    return f[:, sel, :].reshape(-1, hb.MLP_IN).contiguous()
 
 
-def train(n_instances=24, steps=3000, lr=2e-3, batch=1 << 18, seed=0, log=print):
+def shifted_factor(feats, delta):
+    """w_delta = |d| / (|d| + delta) from the first feature (d / 10 Eh)."""
+    d = (feats[:, 0] * 10.0).abs()
+    return (d / (d + delta)).contiguous()
+
+
+def fit(feats, target, steps=3000, lr=2e-3, batch=1 << 16, seed=0, init=None):
+    """Network parameters whose factor fits `target` on `feats` (loss (w - t)^2)."""
     import torch
-    torch.manual_seed(seed)
-    F, A, B = [], [], []
+    n = feats.shape[0]
+    rng = np.random.default_rng(seed)
+    if init is None:
+        p0 = rng.normal(0.0, 0.05, hb.mlp_param_count()).astype(np.float32)
+        p0[-1] = 0.0                 # starts near w = 1
+    else:
+        p0 = np.asarray(init, np.float32).copy()
+    params = torch.from_numpy(p0).cuda()
+    perm = torch.from_numpy(rng.permutation(n)).cuda()
+    F, B = feats[perm].contiguous(), target[perm].contiguous()
+    A = torch.ones_like(B)
+    loss = hb.mlp_train(params, F, A, B, min(batch, n), steps, lr)
+    return params, loss
+
+
+def timed_diag(H, b, k, params=None, tol=1e-8, max_iter=400, tensor=True):
+    """(iterations or -1, seconds, eigenvalues, stats) of one hb_diag solve,
+    plain or with the network `params`."""
+    import torch
+    flags = hb.HB_DIAG_TENSOR if tensor else 0
+    pc = hb.HB_PRECOND_DIAG
+    if params is not None:
+        H.set_mlp_params(params)
+        pc = hb.HB_PRECOND_MLP
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    w, st, ok = H.diag(b, k, tol, max_iter, precond=pc | flags, allow_not_converged=True)
+    torch.cuda.synchronize()
+    return (st.iterations if ok else -1), time.perf_counter() - t0, w, st
+
+
+def built(P):
+    import torch
+    H = hb.Hamiltonian(P, validate=False)
+    b, _ = H.build(hb.HB_MIXED)
+    torch.cuda.synchronize()
+    return H, b
+
+
+def train(n_instances=200, steps=4000, lr=2e-3, seed=0, log=print):
+    """The pipeline of the module docstring; returns (params, info)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    # 1. candidate networks, fitted on feature rows of a few instances
+    pool = []
+    for s in range(6):
+        H, b = built(training_problem(90_000 + s))
+        _, _, w, _ = timed_diag(H, b, 12)
+        pool.append(_features_at(H, b, w, 2000, rng))
+        H.close()
+    pool = torch.cat(pool)
+    cands = {}
+    for dl in DELTAS:
+        prm, l = fit(pool, shifted_factor(pool, dl), steps=2000, seed=seed)
+        cands[dl] = prm.cpu().numpy()
+        log(f"candidate delta {dl}: fit loss {l:.3e}")
+    # 2-3. label every instance by its best candidate, sample its feature rows
+    F, T, labels = [], [], []
     for s in range(n_instances):
         P = training_problem(s)
-        k = [8, 12, 20][s % 3]
-        out = davidson_samples(P, k)
-        if out is None:
+        k = [8, 20, 40][s % 3]
+        H, b = built(P)
+        it0, _, w0, _ = timed_diag(H, b, k)
+        if it0 < 0:
+            H.close()
             continue
-        f, a, b, iters = out
-        F.append(f); A.append(a); B.append(b)
-        log(f"instance {s}: dim {P.dim}, k {k}, {iters} plain iterations, {f.shape[0]} samples")
-    F, A, B = torch.cat(F).contiguous(), torch.cat(A).contiguous(), torch.cat(B).contiguous()
-    n = F.shape[0]
-    npar = hb.mlp_param_count()
-    rng = np.random.default_rng(seed)
-    # small initial weights: the network starts close to w = 1 (plain Davidson)
-    p0 = rng.normal(0.0, 0.05, npar).astype(np.float32)
-    p0[-1] = 0.0
-    params = torch.from_numpy(p0).cuda()
-    m = torch.zeros_like(params)
-    v = torch.zeros_like(params)
-    work = torch.empty(hb._mlp_fns().hb_mlp_workspace_bytes(min(n, batch)), dtype=torch.uint8, device="cuda")
-    gen = torch.Generator(device="cuda").manual_seed(seed)
-    base, _ = hb.mlp_loss_grad(params, F[: min(n, batch)], A[: min(n, batch)], B[: min(n, batch)], work)
-    for step in range(1, steps + 1):
-        sel = torch.randint(0, n, (min(n, batch),), device="cuda", generator=gen)
-        loss, g = hb.mlp_loss_grad(params, F[sel].contiguous(), A[sel].contiguous(), B[sel].contiguous(), work)
-        hb.mlp_adam(params, g, m, v, step, lr)
-        if step % 500 == 0 or step == 1:
-            log(f"step {step}: loss {float(loss):.6e}")
-    torch.cuda.synchronize()
-    return params.cpu().numpy(), float(base), float(loss), n
+        feats = _features_at(H, b, w0, 1500, rng)
+        best, best_it, its = None, it0 - ROBUST + 1, {}
+        for dl, prm in cands.items():
+            it, _, _, _ = timed_diag(H, b, k, prm)
+            its[dl] = it
+            if 0 < it < best_it:
+                best, best_it = dl, it
+        H.close()
+        F.append(feats)
+        T.append(shifted_factor(feats, best) if best is not None else torch.ones(feats.shape[0], device="cuda"))
+        labels.append((P.name, P.dim, k, it0, best, best_it))
+        log(f"{P.name}: dim {P.dim}, k {k}: plain {it0} iterations; " +
+            ", ".join(f"delta {d}: {i}" for d, i in its.items()) + f" -> label {best}")
+    F, T = torch.cat(F), torch.cat(T)
+    # 4. the final network
+    params, loss = fit(F, T, steps=steps, lr=lr, seed=seed + 1)
+    log(f"final network: {F.shape[0]} samples, loss {loss:.3e}")
+    return params.cpu().numpy(), {"samples": int(F.shape[0]), "loss": float(loss), "labels": labels}
 
 
-def ab_compare(params, problems, k, tol=1e-8, max_iter=1000):
-    """Plain vs learned preconditioner on the same built matrices:
-    [(name, iterations_diag, seconds_diag, iterations_mlp, seconds_mlp, max |d eval|)]."""
-    import time
+def held_out():
+    """Instances never used in training: (problem, k)."""
+    out = [(training_problem(1000 + s), [8, 20, 40][s % 3]) for s in range(6)]
+    out.append((synth.make_config("c5", n_det=1500, n_co=120, n_state=20, n_l2=3000, seed=55), 100))
+    out.append((synth.make_config("c2"), 20))
+    return out
 
-    import torch
+
+def ab_compare(params, problems, tol=1e-8, max_iter=400):
+    """Plain vs learned preconditioner on the same built matrices (block
+    products on the tensor cores): [(name, dim, k, iterations plain, seconds
+    plain, iterations learned, seconds learned, max |d eval|)]."""
     out = []
-    for P in problems:
-        H = hb.Hamiltonian(P)
-        b, _ = H.build(hb.HB_MIXED)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        w0, s0, ok0 = H.diag(b, k, tol, max_iter, allow_not_converged=True)
-        t1 = time.perf_counter()
-        H.set_mlp_params(params)
-        w1, s1, ok1 = H.diag(b, k, tol, max_iter, precond=hb.HB_PRECOND_MLP, allow_not_converged=True)
-        t2 = time.perf_counter()
-        out.append((P.name, s0.iterations if ok0 else -1, t1 - t0, s1.iterations if ok1 else -1, t2 - t1,
-                    float(np.abs(w0 - w1).max())))
+    for P, k in problems:
+        H, b = built(P)
+        timed_diag(H, b, k)                    # warm-up of this instance's kernels and scratch
+        i0, t0, w0, _ = timed_diag(H, b, k)
+        i1, t1, w1, _ = timed_diag(H, b, k, params)
+        out.append((P.name, P.dim, k, i0, t0, i1, t1, float(np.abs(w0 - w1).max())))
         H.close()
     return out
 
@@ -175,8 +193,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("cmd", choices=["train", "evaluate", "large"])
     ap.add_argument("--k", type=int, default=200)
-    ap.add_argument("--instances", type=int, default=24)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--instances", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     args = ap.parse_args()
     from . import build_ext
@@ -207,15 +225,16 @@ def main():
         return
     if args.cmd == "evaluate":
         params = load_weights(args.out)
-        probs = [training_problem(1000 + s) for s in range(4)] + [synth.make_config("c2")]
-        for row in ab_compare(params, probs, 20):
-            print("%-14s diag %4d it %7.3f s | mlp %4d it %7.3f s | max |d eval| %.1e" % row)
+        for row in ab_compare(params, held_out()):
+            print("%-14s dim %6d k %3d | plain %4d it %7.3f s | learned %4d it %7.3f s | max |d eval| %.1e" % row,
+                  flush=True)
         return
-    p, l0, l1, n = train(args.instances, args.steps)
+    p, info = train(args.instances, args.steps)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
-    np.savez(args.out, params=p, n_samples=n, loss_start=l0, loss_end=l1, instances=args.instances,
-             steps=args.steps)
-    print(f"saved {args.out}: {n} samples, loss {l0:.4e} -> {l1:.4e}")
+    lab = np.array([(d, k, i0, -1.0 if b is None else b, bi) for _, d, k, i0, b, bi in info["labels"]])
+    np.savez(args.out, params=p, n_samples=info["samples"], loss=info["loss"], instances=args.instances,
+             steps=args.steps, labels=lab)
+    print(f"saved {args.out}: {info['samples']} samples, loss {info['loss']:.4e}")
 
 
 if __name__ == "__main__":

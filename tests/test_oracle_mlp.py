@@ -1,6 +1,6 @@
 """Pins of the FP64 network reference: its analytic gradient against central
 finite differences (with the weight rounding switched off so the loss is
-smooth), and the factor's range [1/4, 4]."""
+smooth), and the factor's range [1/256, 256]."""
 import numpy as np
 
 from oracle import mlp
@@ -26,4 +26,5 @@ def test_factor_range():
     rng = np.random.default_rng(1)
     p = rng.normal(0, 3.0, mlp.pack([np.zeros(s) for s in mlp.SHAPES]).size)
     w = mlp.factor(p, rng.normal(0, 5, (200, mlp.IN)))
-    assert np.all(w >= 0.25 - 1e-12) and np.all(w <= 4.0 + 1e-12)
+    assert np.all(w >= 1 / 256 - 1e-12) and np.all(w <= 256.0 + 1e-12)
+    assert w.min() < 0.25 and w.max() > 4.0
