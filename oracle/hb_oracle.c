@@ -41,6 +41,7 @@
 #include <string.h>
 
 #define ORC_MAXW 8          /* words per spin in extended strings */
+#define ORC_CHUNKS 64       /* fixed bra-determinant chunks of the contraction */
 #define ORC_ONE_E 0xFFFFu   /* marker in slots r,s of a one-electron label */
 #define ORC_OVERLAP 0xFFFEu /* marker label for the overlap (core energy) term */
 
@@ -338,6 +339,12 @@ static void map_init(orc_map *m, int64_t bsz) {
     m->blocks = (double *)calloc((size_t)(m->bcap * bsz), sizeof(double));
 }
 static void map_free(orc_map *m) { free(m->keys); free(m->slot); free(m->blocks); }
+/* Empty the map, keeping its storage. */
+static void map_reset(orc_map *m) {
+    memset(m->blocks, 0, sizeof(double) * (size_t)(m->n * m->bsz));
+    for (int64_t i = 0; i < m->cap; ++i) m->slot[i] = -1;
+    m->n = 0;
+}
 static uint64_t hmix(uint64_t x) { x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ull; x ^= x >> 33; return x; }
 
 static double *map_get(orc_map *m, uint64_t key) {
@@ -412,8 +419,13 @@ orc_cc *orc_cc_contract_ex(const orc_problem *P, int g, int gp, int with_abs) {
     const int W = P->W, We = ext_words(P), ph = P->n_to, phk = P->n_to + 1, sc = P->cont_spin;
     const uint64_t *Dg = P->g_dets[g], *Dgp = P->g_dets[gp];
     const double *Cg = P->g_ci[g], *Cgp = P->g_ci[gp];
-    /* bra determinants are split over threads; every thread contracts into its
-       own maps (Eq. 8 sums), merged in thread order at the end */
+    /* bra determinants are split into ORC_CHUNKS fixed chunks whatever the
+       thread count; a thread contracts a chunk into its own maps (the Eq. 8
+       sums over the chunk's determinants in order) and merges them into the
+       result in chunk order, so the sums, and the label order of the merged
+       maps, do not depend on the number of threads */
+    const int ndet_g = P->g_ndet[g];
+    const int nchunk = ndet_g < ORC_CHUNKS ? ndet_g : ORC_CHUNKS;
 #pragma omp parallel
     {
         orc_map same, diff, same_a, diff_a;
@@ -426,61 +438,67 @@ orc_cc *orc_cc_contract_ex(const orc_problem *P, int g, int gp, int with_abs) {
         orc_sym *buf = (orc_sym *)malloc(sizeof(orc_sym) * 8192);
         double *cc = (double *)malloc(sizeof(double) * bsz);
         uint64_t I[2 * ORC_MAXW], J[2 * ORC_MAXW];
-#pragma omp for schedule(static)
-        for (int m = 0; m < P->g_ndet[g]; ++m) {
-            const uint64_t *Dm = Dg + (int64_t)m * 2 * W;
-            for (int mp = 0; mp < P->g_ndet[gp]; ++mp) {
-                const uint64_t *Dmp = Dgp + (int64_t)mp * 2 * W;
-                int nd = 0;
-                for (int w = 0; w < 2 * W; ++w) nd += popc64(Dm[w] ^ Dmp[w]);
-                if (nd > 4) continue;
-                for (int a = 0; a < ns; ++a)
-                    for (int b = 0; b < nsp; ++b)
-                        cc[a * nsp + b] = Cg[(int64_t)m * ns + a] * Cgp[(int64_t)mp * nsp + b];
-                /* prototype 1: the same continuum orbital in bra and ket */
-                extend(P, Dm, ph, sc, I);
-                extend(P, Dmp, ph, sc, J);
-                int n = orc_symbols(We, I, J, buf, 8192);
-                for (int k = 0; k < n; ++k) {
-                    uint64_t L = buf[k].label;
-                    int has = 0;
-                    for (int s2 = 0; s2 < 4; ++s2) has |= (int)(((L >> (16 * s2)) & 0xFFFFu) == (uint64_t)ph);
-                    if (!has) {
-                        if (P->g_energy) continue;   /* replaced by the target energies below */
-                        double x = buf[k].coef * orc_X(P, L, -1, 0, -1, 0);
-                        for (int t = 0; t < bsz; ++t) K0[t] += cc[t] * x;
-                        if (with_abs) for (int t = 0; t < bsz; ++t) K0a[t] += fabs(cc[t] * x);
-                    } else {
-                        double *blk = map_get(&same, L);
-                        for (int t = 0; t < bsz; ++t) blk[t] += cc[t] * buf[k].coef;
-                        if (with_abs) {
-                            blk = map_get(&same_a, L);
-                            for (int t = 0; t < bsz; ++t) blk[t] += fabs(cc[t] * buf[k].coef);
+#pragma omp for ordered schedule(dynamic, 1)
+        for (int ch = 0; ch < nchunk; ++ch) {
+            const int m0 = (int)((int64_t)ndet_g * ch / nchunk), m1 = (int)((int64_t)ndet_g * (ch + 1) / nchunk);
+            map_reset(&same);
+            map_reset(&diff);
+            map_reset(&same_a);
+            map_reset(&diff_a);
+            memset(K0, 0, sizeof(double) * (size_t)bsz);
+            memset(K0a, 0, sizeof(double) * (size_t)bsz);
+            for (int m = m0; m < m1; ++m) {
+                const uint64_t *Dm = Dg + (int64_t)m * 2 * W;
+                for (int mp = 0; mp < P->g_ndet[gp]; ++mp) {
+                    const uint64_t *Dmp = Dgp + (int64_t)mp * 2 * W;
+                    int nd = 0;
+                    for (int w = 0; w < 2 * W; ++w) nd += popc64(Dm[w] ^ Dmp[w]);
+                    if (nd > 4) continue;
+                    for (int a = 0; a < ns; ++a)
+                        for (int b = 0; b < nsp; ++b)
+                            cc[a * nsp + b] = Cg[(int64_t)m * ns + a] * Cgp[(int64_t)mp * nsp + b];
+                    /* prototype 1: the same continuum orbital in bra and ket */
+                    extend(P, Dm, ph, sc, I);
+                    extend(P, Dmp, ph, sc, J);
+                    int n = orc_symbols(We, I, J, buf, 8192);
+                    for (int k = 0; k < n; ++k) {
+                        uint64_t L = buf[k].label;
+                        int has = 0;
+                        for (int s2 = 0; s2 < 4; ++s2) has |= (int)(((L >> (16 * s2)) & 0xFFFFu) == (uint64_t)ph);
+                        if (!has) {
+                            if (P->g_energy) continue;   /* replaced by the target energies below */
+                            double x = buf[k].coef * orc_X(P, L, -1, 0, -1, 0);
+                            for (int t = 0; t < bsz; ++t) K0[t] += cc[t] * x;
+                            if (with_abs) for (int t = 0; t < bsz; ++t) K0a[t] += fabs(cc[t] * x);
+                        } else {
+                            double *blk = map_get(&same, L);
+                            for (int t = 0; t < bsz; ++t) blk[t] += cc[t] * buf[k].coef;
+                            if (with_abs) {
+                                blk = map_get(&same_a, L);
+                                for (int t = 0; t < bsz; ++t) blk[t] += fabs(cc[t] * buf[k].coef);
+                            }
                         }
                     }
-                }
-                if (nd == 0 && P->e_core != 0.0 && !P->g_energy) {
-                    for (int t = 0; t < bsz; ++t) K0[t] += cc[t] * P->e_core;
-                    if (with_abs) for (int t = 0; t < bsz; ++t) K0a[t] += fabs(cc[t] * P->e_core);
-                }
-                /* prototype 2: different continuum orbitals (j in bra, j' in ket) */
-                if (nd <= 2) {
-                    extend(P, Dm, ph, sc, I);
-                    extend(P, Dmp, phk, sc, J);
-                    n = orc_symbols(We, I, J, buf, 8192);
-                    for (int k = 0; k < n; ++k) {
-                        double *blk = map_get(&diff, buf[k].label);
-                        for (int t = 0; t < bsz; ++t) blk[t] += cc[t] * buf[k].coef;
-                        if (with_abs) {
-                            blk = map_get(&diff_a, buf[k].label);
-                            for (int t = 0; t < bsz; ++t) blk[t] += fabs(cc[t] * buf[k].coef);
+                    if (nd == 0 && P->e_core != 0.0 && !P->g_energy) {
+                        for (int t = 0; t < bsz; ++t) K0[t] += cc[t] * P->e_core;
+                        if (with_abs) for (int t = 0; t < bsz; ++t) K0a[t] += fabs(cc[t] * P->e_core);
+                    }
+                    /* prototype 2: different continuum orbitals (j in bra, j' in ket) */
+                    if (nd <= 2) {
+                        extend(P, Dm, ph, sc, I);
+                        extend(P, Dmp, phk, sc, J);
+                        n = orc_symbols(We, I, J, buf, 8192);
+                        for (int k = 0; k < n; ++k) {
+                            double *blk = map_get(&diff, buf[k].label);
+                            for (int t = 0; t < bsz; ++t) blk[t] += cc[t] * buf[k].coef;
+                            if (with_abs) {
+                                blk = map_get(&diff_a, buf[k].label);
+                                for (int t = 0; t < bsz; ++t) blk[t] += fabs(cc[t] * buf[k].coef);
+                            }
                         }
                     }
                 }
             }
-        }
-#pragma omp for ordered schedule(static, 1)
-        for (int th = 0; th < omp_get_num_threads(); ++th) {
 #pragma omp ordered
             {
                 map_merge(&c->same, &same);
