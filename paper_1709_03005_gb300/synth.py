@@ -167,40 +167,90 @@ def make_h(rng, n_to, n_co, cont_diag=(-3.0, -0.5), offdiag_sd=0.05, orb_irrep=N
     return h
 
 
-def make_chol(rng, n_orb, rank, orb_irrep=None):
-    """Packed-pair Cholesky-like factor L[pair(p,q), k] ~ N(0, 0.5/rank)."""
+def make_chol(rng, n_orb, rank, orb_irrep=None, return_irrep=False):
+    """Packed-pair Cholesky-like factor L[pair(p,q), k] ~ N(0, 0.5/rank).  With
+    orbital irreps every vector k carries an irrep and L[pair, k] vanishes
+    unless the pair's irrep (XOR of its orbitals') is the vector's; with
+    return_irrep the vectors' irreps are returned too."""
     npair = n_orb * (n_orb + 1) // 2
     L = rng.normal(0.0, np.sqrt(0.5 / rank), size=(npair, rank))
     if orb_irrep is not None:
         ir = np.asarray(orb_irrep)
         vec_irrep = rng.integers(0, 8, size=rank)
         vec_irrep[: max(1, rank // 8)] = 0   # keep totally symmetric vectors present
+        pp, qq = np.tril_indices(n_orb)
         pi = np.empty(npair, dtype=np.int64)
-        for p in range(n_orb):
-            for q in range(p + 1):
-                pi[pair_index(p, q)] = ir[p] ^ ir[q]
+        pi[_pair_index_array(pp, qq)] = ir[pp] ^ ir[qq]
         L[pi[:, None] != vec_irrep[None, :]] = 0.0
+        if return_irrep:
+            return L, vec_irrep
     return L
 
 
-def eri_classes(L, n_to, n_co):
-    """The four class arrays of (pq|rs) = sum_k L[pq,k] L[rs,k]."""
+def _pair_index_array(p, q):
+    """pair_index over arrays (p >= 0, q >= 0, either order)."""
+    hi, lo = np.maximum(p, q), np.minimum(p, q)
+    return hi * (hi + 1) // 2 + lo
+
+
+def eri_classes(L, n_to, n_co, orb_irrep=None, vec_irrep=None):
+    """The four class arrays of (pq|rs) = sum_k L[pq,k] L[rs,k].  With the
+    orbitals' and the vectors' irreps (make_chol(..., return_irrep=True)) only
+    the symmetry-allowed blocks are formed: rows and columns of pair irrep x
+    against the vectors of irrep x, into arrays that are zero elsewhere."""
     Pt = n_to * (n_to + 1) // 2
-    Ltt = L[:Pt]
-    tc = np.empty(n_to * n_co, dtype=np.int64)
-    for r in range(n_to):
-        for j in range(n_co):
-            tc[r * n_co + j] = pair_index(n_to + j, r)
-    cc = np.empty(n_co * n_co, dtype=np.int64)
-    for j in range(n_co):
-        for k in range(n_co):
-            cc[j * n_co + k] = pair_index(n_to + j, n_to + k)
-    Ltc = L[tc]
-    eri_tttt = Ltt @ Ltt.T
-    eri_tttc = Ltt @ Ltc.T
-    eri_ttcc = Ltt @ L[cc].T
-    eri_tctc = Ltc @ Ltc.T
-    return eri_tttt, eri_tttc, eri_ttcc, eri_tctc
+    r_, j_ = np.meshgrid(np.arange(n_to), np.arange(n_co), indexing="ij")
+    tc = _pair_index_array(n_to + j_.ravel(), r_.ravel())            # [r * n_co + j]
+    j1, j2 = np.meshgrid(np.arange(n_co), np.arange(n_co), indexing="ij")
+    cc = _pair_index_array(n_to + j1.ravel(), n_to + j2.ravel())     # [j * n_co + k]
+    tt = np.arange(Pt)
+    Ltt, Ltc = L[:Pt], L[tc]
+    if orb_irrep is None:
+        return Ltt @ Ltt.T, Ltt @ Ltc.T, Ltt @ L[cc].T, Ltc @ Ltc.T
+    # orbitals sorted by irrep within the target and within the continuum: every
+    # symmetry block of the class arrays is a contiguous sub-array
+    ir = np.asarray(orb_irrep, dtype=np.int64)
+    t_ir, c_ir = ir[:n_to], ir[n_to:]
+    assert np.all(np.diff(t_ir) >= 0) and np.all(np.diff(c_ir) >= 0), "orbitals must be sorted by irrep"
+    vec_irrep = np.asarray(vec_irrep)
+    t_rng = {x: (int(np.searchsorted(t_ir, x)), int(np.searchsorted(t_ir, x, side="right"))) for x in range(8)}
+    c_rng = {x: (int(np.searchsorted(c_ir, x)), int(np.searchsorted(c_ir, x, side="right"))) for x in range(8)}
+    tt_ir = t_ir[np.tril_indices(n_to)[0]] ^ t_ir[np.tril_indices(n_to)[1]]
+    tt_ir = tt_ir[np.argsort(_pair_index_array(*np.tril_indices(n_to)))]     # by packed pair index
+    tttt = Ltt @ Ltt.T
+    tttc = np.zeros((Pt, n_to, n_co))
+    ttcc = np.zeros((Pt, n_co, n_co))
+    tctc = np.zeros((n_to, n_co, n_to, n_co))
+    Ltc3 = Ltc.reshape(n_to, n_co, -1)
+    for x in range(8):
+        k = np.flatnonzero(vec_irrep == x)
+        rows = np.flatnonzero(tt_ir == x)
+        if len(k) == 0:
+            continue
+        Lr = Ltt[rows][:, k]
+        # (tt|tc): target orbital q of irrep u, continuum j of irrep u ^ x
+        for u in range(8):
+            (q0, q1), (a0, a1) = t_rng[u], c_rng[u ^ x]
+            if q1 > q0 and a1 > a0 and len(rows):
+                cols = Ltc3[q0:q1, a0:a1][:, :, k].reshape(-1, len(k))
+                tttc[rows, q0:q1, a0:a1] = (Lr @ cols.T).reshape(len(rows), q1 - q0, a1 - a0)
+        # (tt|cc): continuum j of irrep a, k of irrep a ^ x
+        for a in range(8):
+            (a0, a1), (b0, b1) = c_rng[a], c_rng[a ^ x]
+            if a1 > a0 and b1 > b0 and len(rows):
+                jj, kk = np.meshgrid(np.arange(a0, a1), np.arange(b0, b1), indexing="ij")
+                cols = L[_pair_index_array(n_to + jj.ravel(), n_to + kk.ravel())][:, k]
+                ttcc[rows, a0:a1, b0:b1] = (Lr @ cols.T).reshape(len(rows), a1 - a0, b1 - b0)
+        # (tc|tc): (q of irrep t, j of irrep t ^ x) against (p of irrep u, j' of irrep u ^ x)
+        blocks = [(t, *t_rng[t], *c_rng[t ^ x]) for t in range(8)]
+        blocks = [b for b in blocks if b[2] > b[1] and b[4] > b[3]]
+        for (t, q0, q1, a0, a1) in blocks:
+            Lq = Ltc3[q0:q1, a0:a1][:, :, k].reshape(-1, len(k))
+            for (u, p0, p1, b0, b1) in blocks:
+                Lp = Ltc3[p0:p1, b0:b1][:, :, k].reshape(-1, len(k))
+                tctc[q0:q1, a0:a1, p0:p1, b0:b1] = (Lq @ Lp.T).reshape(q1 - q0, a1 - a0, p1 - p0, b1 - b0)
+    return (tttt, tttc.reshape(Pt, n_to * n_co), ttcc.reshape(Pt, n_co * n_co),
+            tctc.reshape(n_to * n_co, n_to * n_co))
 
 
 def orthonormal_ci(rng, n_det, n_state):
@@ -337,8 +387,8 @@ def _irrep_of(occ_a, occ_b, orb_irrep):
     return x
 
 
-def make_batched_family(seed=4, n_hams=16, n_to=40, cont_per_irrep=(20, 60), n_elec=8, rank=32,
-                        dim_range=(500, 20000), max_det=600):
+def make_batched_family(seed=4, n_hams=16, n_to=40, cont_per_irrep=(50, 150), n_elec=8, rank=32,
+                        dim_range=(500, 20000), max_det=600, max_states=16):
     """16 Hamiltonians of one D2h-like molecule: total symmetry Gamma in 0..7
     times two spin couplings (Ms = 0 targets + alpha continuum electron, and
     Ms = +1 targets + beta continuum electron).  Orbitals carry irreps (XOR is
@@ -347,8 +397,11 @@ def make_batched_family(seed=4, n_hams=16, n_to=40, cont_per_irrep=(20, 60), n_e
     of irrep i and couples to the continuum orbitals of irrep i ^ Gamma (a
     contiguous range, orbitals ordered by irrep); two extra groups repeat an
     irrep with disjoint determinants (classes 5 and 6).  The target dimension of
-    each Hamiltonian is log-uniform in dim_range, about 40 % contracted and
-    60 % L2."""
+    each Hamiltonian is log-uniform in dim_range: up to 60 % L2 (as far as the
+    L2 pool of its symmetry allows), the rest contracted.  The groups enter in a
+    fixed order, the two same-irrep pairs first, one state each while they fit;
+    then states are added, up to max_states per group, until the contracted
+    part reaches its share."""
     rng = np.random.default_rng(seed)
     n_irrep = 8
     t_irrep = np.repeat(np.arange(n_irrep), n_to // n_irrep)
@@ -358,8 +411,8 @@ def make_batched_family(seed=4, n_hams=16, n_to=40, cont_per_irrep=(20, 60), n_e
     n_co = int(cont_counts.sum())
     orb_irrep = np.concatenate([t_irrep, c_irrep])
     h = make_h(rng, n_to, n_co, orb_irrep=orb_irrep)
-    L = make_chol(rng, n_to + n_co, rank, orb_irrep=orb_irrep)
-    eri = eri_classes(L, n_to, n_co)
+    L, vec_irrep = make_chol(rng, n_to + n_co, rank, orb_irrep=orb_irrep, return_irrep=True)
+    eri = eri_classes(L, n_to, n_co, orb_irrep, vec_irrep)
     W = max(1, (n_to + 63) // 64)
     half = n_elec // 2
     pools = {}
@@ -381,14 +434,23 @@ def make_batched_family(seed=4, n_hams=16, n_to=40, cont_per_irrep=(20, 60), n_e
         target = int(dims[hidx])
         n_l2 = min(int(0.6 * target), len(l2_by[gam]))
         contracted = target - n_l2
-        # groups: every target irrep, plus two repeats of irreps 0 and 1
-        irreps = list(range(n_irrep)) + [0, 1]
-        ns = rng.integers(1, 7, size=len(irreps))
-        cdim = sum(int(ns[g]) * int(cont_counts[irreps[g] ^ gam]) for g in range(len(irreps)))
-        # scale the state counts towards the contracted share
-        if cdim > 0:
-            f = max(0.2, contracted / cdim)
-            ns = np.maximum(1, np.minimum(6, np.round(ns * f))).astype(int)
+        # groups: the same-irrep pairs of irreps 0 and 1, then the other irreps
+        order = [0, 0, 1, 1] + list(range(2, n_irrep))
+        width = [int(cont_counts[ir ^ gam]) for ir in order]
+        take, cdim = 0, 0
+        while take < len(order) and (take < 2 or cdim + width[take] <= contracted):
+            cdim += width[take]
+            take += 1
+        irreps, width = order[:take], width[:take]
+        ns = np.ones(take, dtype=int)
+        grew = True
+        while grew:
+            grew = False
+            for g in rng.permutation(take):
+                if ns[g] < max_states and cdim + width[g] <= contracted + width[g] // 2:
+                    ns[g] += 1
+                    cdim += width[g]
+                    grew = True
         used = {i: 0 for i in range(n_irrep)}
         groups = []
         for g, ir in enumerate(irreps):
