@@ -23,7 +23,9 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+        # no contraction of a*b + c into fused multiply-adds: with the fixed
+        # summation order the results are then the same bits on every host
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c11",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _OUT)
     return _OUT
