@@ -146,7 +146,10 @@ typedef struct {
                                  when the largest wanted residual has not fallen by 2^mlp_stall_log2
                                  over the last mlp_stall_iters iterations; 0 = 10 (1..1000) */
     int32_t mlp_stall_log2;   /* 0 = 1, i.e. halved (1..60) */
-    int32_t reserved[7];
+    int32_t diag_basis;       /* hb_diag: the basis holds at most diag_basis blocks of b vectors
+                                 (b = k + min(16, max(4, k / 2))) before a thick restart to 2b;
+                                 0 = 5 (3..10) */
+    int32_t reserved[6];
 } hb_options;
 
 typedef struct {
@@ -193,7 +196,8 @@ typedef struct {
     float ms_class4_kernel;   /* the class-4 kernels after their classification (part of ms_class4) */
     int32_t fp64_iterations;  /* hb_diag: iterations with FP64 products after the convergence check */
     float mlp_loss;           /* hb_mlp_train: loss of the last window */
-    int32_t reserved[1];
+    int32_t proj_gflop;       /* hb_diag: FP64 GFLOP of the projections and basis combinations
+                                 (the Gram sums, norms, project-outs and combines: 2 flops per term) */
 } hb_stats;
 
 /* Excitation record of one determinant pair (row, col), see hb_classify. */

@@ -213,6 +213,8 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
         return fail(ctx, HB_ERR_INVALID_ARG, "class4_path must be 0, 1 or 2");
     if (o && (o->mlp_stall_iters < 0 || o->mlp_stall_iters > 1000 || o->mlp_stall_log2 < 0 || o->mlp_stall_log2 > 60))
         return fail(ctx, HB_ERR_INVALID_ARG, "mlp_stall_iters must be 0..1000 and mlp_stall_log2 0..60");
+    if (o && o->diag_basis != 0 && (o->diag_basis < 3 || o->diag_basis > 10))
+        return fail(ctx, HB_ERR_INVALID_ARG, "diag_basis must be 0 or 3..10");
     const int W = p->n_words, nw = 2 * W;
     // electron counts: every target determinant has the same alpha/beta split,
     // the continuum electron sets the L2 split
@@ -369,6 +371,7 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         ctx->c4_path = o->class4_path;
         if (o->mlp_stall_iters > 0) ctx->stall_iters = o->mlp_stall_iters;
         if (o->mlp_stall_log2 > 0) ctx->stall_log2 = o->mlp_stall_log2;
+        if (o->diag_basis > 0) ctx->diag_basis = o->diag_basis;
     }
     ctx->Pt = (int64_t)p->n_to * (p->n_to + 1) / 2;
     ctx->K = (int)(ctx->Pt + (int64_t)p->n_to * p->n_to + 2);

@@ -175,6 +175,28 @@ gram_partial_kernel(const double *__restrict__ X, int64_t ldx, int p, const doub
             if (b0 + tb + u < q) partial[(int64_t)c * p * q + (int64_t)a * q + b0 + tb + u] = acc[u];
 }
 
+// partial[c][a] = sum_{i in chunk c} X[a][i]^2: one block per (chunk, vector),
+// each thread a strided share of the chunk, then a fixed-order tree over the
+// block, so the sums are deterministic
+__global__ void __launch_bounds__(256)
+norms_partial_kernel(const double *__restrict__ X, int64_t ldx, int p, int64_t n, double *__restrict__ partial) {
+    __shared__ double red[256];
+    const int c = blockIdx.x, a = blockIdx.y;
+    const int64_t i0 = (int64_t)c * kGramChunk, i1 = (n < i0 + kGramChunk) ? n : i0 + kGramChunk;
+    double acc = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double x = __ldg(X + (int64_t)a * ldx + i);
+        acc = fma(x, x, acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)c * p + a] = red[0];
+}
+
 __global__ void reduce_kernel(const double *__restrict__ partial, int chunks, int nout, double *__restrict__ out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nout) return;
@@ -336,42 +358,94 @@ Tridiag tridiagonalize(int n, std::vector<double> &A) {
     t.e.assign(n > 1 ? n - 1 : 0, 0.0);
     t.vs.assign((size_t)n * n, 0.0);
     t.beta.assign(n, 0.0);
-    std::vector<double> v(n), p(n), wv(n);
-    for (int k = 0; k + 2 < n; ++k) {
-        // reflector that zeroes A[k+2..n)[k]
+    std::vector<double> p(n), pn(n), wv(n), col(n);
+    std::vector<char> ready(n, 0), skip(n, 0);
+    int have_p = 0;
+    // reflector k from x = column k below the diagonal (x[i] for i > k):
+    // v = x - alpha e_{k+1}, alpha = -sign(x_{k+1}) |x|, beta = 2 / v.v
+    auto reflector = [&](int k, const double *x) {
         double xn = 0.0;
-        for (int i = k + 1; i < n; ++i) xn += A[(size_t)i * n + k] * A[(size_t)i * n + k];
+        for (int i = k + 1; i < n; ++i) xn += x[i] * x[i];
         xn = std::sqrt(xn);
-        const double x0 = A[(size_t)(k + 1) * n + k];
-        if (xn == 0.0) { t.e[k] = 0.0; continue; }
-        const double alpha = x0 >= 0.0 ? -xn : xn;
-        for (int i = k + 1; i < n; ++i) v[i] = A[(size_t)i * n + k];
+        ready[k] = 1;
+        if (xn == 0.0) { t.e[k] = 0.0; skip[k] = 1; return; }
+        const double alpha = x[k + 1] >= 0.0 ? -xn : xn;
+        double *v = &t.vs[(size_t)k * n];
+        for (int i = k + 1; i < n; ++i) v[i] = x[i];
         v[k + 1] -= alpha;
         double vv = 0.0;
         for (int i = k + 1; i < n; ++i) vv += v[i] * v[i];
         t.e[k] = alpha;
-        if (vv == 0.0) continue;
-        const double bk = 2.0 / vv;
-        t.beta[k] = bk;
-        for (int i = k + 1; i < n; ++i) t.vs[(size_t)k * n + i] = v[i];
-        // p = bk A22 v, w = p - (bk/2)(p.v) v, A22 -= v w^T + w v^T; rows in
-        // parallel on the host cores for the large projected problems
-        const bool par = n - k > 256;
-#pragma omp parallel for schedule(static) if (par)
-        for (int i = k + 1; i < n; ++i) {
-            const double *row = &A[(size_t)i * n];
-            double acc = 0.0;
-            for (int j = k + 1; j < n; ++j) acc += row[j] * v[j];
-            p[i] = bk * acc;
+        if (vv == 0.0) { skip[k] = 1; return; }
+        t.beta[k] = 2.0 / vv;
+    };
+    // One parallel region for the whole reduction on the large projected
+    // matrices.  Step k: p = beta A22 v, w = p - (beta/2)(p.v) v,
+    // A22 -= v w^T + w v^T.  The update of column k+1 is formed first (O(n)),
+    // which gives reflector k+1, so one pass over the trailing block both
+    // applies step k and computes the product A22 v of step k+1 (the look-ahead
+    // column uses the same expression as the pass, so the values agree).
+#pragma omp parallel if (n > 192)
+    for (int k = 0; k + 2 < n; ++k) {
+#pragma omp single
+        {
+            if (!ready[k]) {
+                for (int i = k + 1; i < n; ++i) col[i] = A[(size_t)i * n + k];
+                reflector(k, col.data());
+            }
         }
-        double pv = 0.0;
-        for (int i = k + 1; i < n; ++i) pv += p[i] * v[i];
-        for (int i = k + 1; i < n; ++i) wv[i] = p[i] - 0.5 * bk * pv * v[i];
-#pragma omp parallel for schedule(static) if (par)
+        if (skip[k]) {
+#pragma omp single
+            have_p = 0;
+            continue;
+        }
+        const double *v = &t.vs[(size_t)k * n];
+        const double bk = t.beta[k];
+        if (!have_p) {
+#pragma omp for schedule(static)
+            for (int i = k + 1; i < n; ++i) {
+                const double *row = &A[(size_t)i * n];
+                double acc = 0.0;
+                for (int j = k + 1; j < n; ++j) acc += row[j] * v[j];
+                p[i] = bk * acc;
+            }
+        }
+#pragma omp single
+        {
+            double pv = 0.0;
+            for (int i = k + 1; i < n; ++i) pv += p[i] * v[i];
+            for (int i = k + 1; i < n; ++i) wv[i] = p[i] - 0.5 * bk * pv * v[i];
+            // look-ahead: column k+1 after this step's update, and its reflector
+            if (k + 3 < n) {
+                const int c = k + 1;
+                for (int i = c + 1; i < n; ++i) col[i] = A[(size_t)i * n + c] - (v[i] * wv[c] + wv[i] * v[c]);
+                reflector(c, col.data());
+            }
+        }
+        const int nx = k + 1;
+        const bool next = k + 3 < n && !skip[nx];
+        const double *vn = &t.vs[(size_t)nx * n];
+        const double bn = t.beta[nx];
+#pragma omp for schedule(static)
         for (int i = k + 1; i < n; ++i) {
             double *row = &A[(size_t)i * n];
             const double vi = v[i], wi = wv[i];
-            for (int j = k + 1; j < n; ++j) row[j] -= vi * wv[j] + wi * v[j];
+            double acc = 0.0;
+            if (next && i > nx) {
+                row[nx] -= vi * wv[nx] + wi * v[nx];
+                for (int j = nx + 1; j < n; ++j) {
+                    row[j] -= vi * wv[j] + wi * v[j];
+                    acc += row[j] * vn[j];
+                }
+                pn[i] = bn * acc;
+            } else {
+                for (int j = k + 1; j < n; ++j) row[j] -= vi * wv[j] + wi * v[j];
+            }
+        }
+#pragma omp single
+        {
+            have_p = next ? 1 : 0;
+            if (next) p.swap(pn);
         }
     }
     for (int i = 0; i < n; ++i) t.d[i] = A[(size_t)i * n + i];
@@ -424,6 +498,51 @@ std::vector<double> tridiag_eigenvalues(const Tridiag &t) {
     return a;
 }
 
+// The nvec lowest eigenvalues of T by bisection on Sturm counts (Golub & Van
+// Loan, Sec. 8.4.1): the number of eigenvalues below x is the number of
+// negative pivots of the LDL^T factorisation of T - x I.  Each eigenvalue is
+// bracketed from the Gershgorin interval independently, so they are found in
+// parallel, to a width of a few units in the last place.
+std::vector<double> tridiag_lowest(const Tridiag &t, int nvec) {
+    const int n = (int)t.d.size();
+    double lo = 0.0, hi = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? std::fabs(t.e[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(t.e[i]) : 0.0);
+        lo = i ? std::min(lo, t.d[i] - r) : t.d[i] - r;
+        hi = i ? std::max(hi, t.d[i] + r) : t.d[i] + r;
+    }
+    const double pad = 2.2e-16 * std::max(std::fabs(lo), std::fabs(hi)) + 1e-300;
+    lo -= pad;
+    hi += pad;
+    std::vector<double> e2(n > 1 ? n - 1 : 0);
+    for (int i = 0; i + 1 < n; ++i) e2[i] = t.e[i] * t.e[i];
+    const double tiny = 1e-300 + 2.2e-16 * std::max(std::fabs(lo), std::fabs(hi)) * 1e-10;
+    auto below = [&](double x) {
+        int c = 0;
+        double q = t.d[0] - x;
+        if (q < 0.0) ++c;
+        for (int i = 1; i < n; ++i) {
+            if (q == 0.0) q = -tiny;
+            q = t.d[i] - x - e2[i - 1] / q;
+            if (q < 0.0) ++c;
+        }
+        return c;
+    };
+    std::vector<double> w(nvec);
+#pragma omp parallel for schedule(dynamic, 4) if ((int64_t)nvec * n > 20000)
+    for (int j = 0; j < nvec; ++j) {
+        double a = lo, b = hi;
+        for (int it = 0; it < 2100; ++it) {
+            const double mid = 0.5 * (a + b);
+            if (mid <= a || mid >= b || b - a <= 2.0 * 2.2e-16 * std::max(std::fabs(a), std::fabs(b))) break;
+            if (below(mid) > j) b = mid;
+            else a = mid;
+        }
+        w[j] = 0.5 * (a + b);
+    }
+    return w;
+}
+
 // eigenvector of T for the eigenvalue lam by inverse iteration; the vectors
 // in `cluster` (unit, orthogonal) are projected out after every solve
 void tridiag_vector(const Tridiag &t, double lam, double tnorm, int seed, const std::vector<const double *> &cluster,
@@ -471,12 +590,18 @@ void tridiag_vector(const Tridiag &t, double lam, double tnorm, int seed, const 
         r ^= r >> 12; r ^= r << 25; r ^= r >> 27;
         y[i] = 0.5 + (double)((r * 2685821657736338717ull) >> 11) * (1.0 / 9007199254740992.0);
     }
+    // Two Gram-Schmidt passes: in a large cluster of nearly equal eigenvalues
+    // the solve returns y almost inside the span of the earlier vectors, and
+    // one pass leaves the rounding of that large part in the small remainder
+    // (with fused multiply-adds that reached 1e-9 of orthogonality on the Gram
+    // matrices of the block orthonormalisation); the second pass removes it.
     auto orth_normalise = [&]() {
-        for (const double *q : cluster) {
-            double dot = 0.0;
-            for (int i = 0; i < n; ++i) dot += q[i] * y[i];
-            for (int i = 0; i < n; ++i) y[i] -= dot * q[i];
-        }
+        for (int pass = 0; pass < 2; ++pass)
+            for (const double *q : cluster) {
+                double dot = 0.0;
+                for (int i = 0; i < n; ++i) dot += q[i] * y[i];
+                for (int i = 0; i < n; ++i) y[i] -= dot * q[i];
+            }
         double nrm = 0.0;
         for (int i = 0; i < n; ++i) nrm += y[i] * y[i];
         nrm = std::sqrt(nrm);
@@ -515,14 +640,32 @@ void hb::small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::v
         const double r = (i > 0 ? std::fabs(t.e[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(t.e[i]) : 0.0);
         tnorm = std::max(tnorm, std::fabs(t.d[i]) + r);
     }
-    w = tridiag_eigenvalues(t);
-    // vectors of the nvec lowest, clusters kept orthogonal
+    if (n >= 256 && 2 * nvec < n) {
+        // the wanted lowest by bisection (cheaper than all of them by QR on
+        // the large projected matrices); w then holds those nvec
+        const std::vector<double> low = tridiag_lowest(t, nvec);
+        std::copy(low.begin(), low.end(), w.begin());
+        w.resize(nvec);
+    } else {
+        w = tridiag_eigenvalues(t);
+    }
+    // vectors of the nvec lowest, each orthogonalised against the earlier
+    // vectors whose eigenvalues lie within gap; runs of eigenvalues whose
+    // neighbours are closer than gap are independent and run in parallel
     const double gap = 1e-3 * std::max(tnorm, 1e-300);
+    std::vector<int> first;
+    for (int c = 0; c < nvec; ++c)
+        if (c == 0 || w[c] - w[c - 1] > gap) first.push_back(c);
+    first.push_back(nvec);
     std::vector<double> Y((size_t)std::max(nvec, 1) * n);
-    for (int c = 0; c < nvec; ++c) {
-        std::vector<const double *> cluster;
-        for (int c2 = c - 1; c2 >= 0 && w[c] - w[c2] <= gap; --c2) cluster.push_back(&Y[(size_t)c2 * n]);
-        tridiag_vector(t, w[c], tnorm, c, cluster, &Y[(size_t)c * n]);
+    const int n_runs = (int)first.size() - 1;
+#pragma omp parallel for schedule(dynamic, 1) if ((int64_t)nvec * n > 65536)
+    for (int cl = 0; cl < n_runs; ++cl) {
+        for (int c = first[cl]; c < first[cl + 1]; ++c) {
+            std::vector<const double *> cluster;
+            for (int c2 = c - 1; c2 >= first[cl] && w[c] - w[c2] <= gap; --c2) cluster.push_back(&Y[(size_t)c2 * n]);
+            tridiag_vector(t, w[c], tnorm, c, cluster, &Y[(size_t)c * n]);
+        }
     }
     // back-transformation x = H_0 H_1 ... y (reflectors applied last to first)
 #pragma omp parallel for schedule(static) if ((int64_t)nvec * n > 65536)
@@ -540,11 +683,12 @@ void hb::small_eigh(int n, std::vector<double> A, std::vector<double> &w, std::v
     }
 }
 
-extern "C" int hb_test_symeig(int n, const double *A, double *w, double *V) {
+// test entry: the nvec lowest eigenpairs (w [nvec], V [n][nvec])
+extern "C" int hb_test_symeig(int n, const double *A, int nvec, double *w, double *V) {
     std::vector<double> a(A, A + (size_t)n * n), ww, vv;
-    hb::small_eigh(n, a, ww, vv, n);
-    std::memcpy(w, ww.data(), sizeof(double) * n);
-    std::memcpy(V, vv.data(), sizeof(double) * (size_t)n * n);
+    hb::small_eigh(n, a, ww, vv, nvec);
+    std::memcpy(w, ww.data(), sizeof(double) * nvec);
+    std::memcpy(V, vv.data(), sizeof(double) * (size_t)n * nvec);
     return 0;
 }
 
@@ -560,6 +704,7 @@ struct Ops {
     bool force_fp64 = false;   // products in FP64 even when the tensor-core slices exist
     int launches = 0;
     double ms_gram = 0.0, ms_combine = 0.0, ms_eigh = 0.0;
+    double proj_flops = 0.0;   // FP64 flops of gram, norms2, combine and project_out
     static double now_ms() {
         return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
     }
@@ -625,8 +770,23 @@ struct Ops {
         gram_partial_kernel<<<g, 256, 0, s>>>(X, ld, p, Y, ld, q, n, w->partial);
         reduce_kernel<<<(p * q + 255) / 256, 256, 0, s>>>(w->partial, chunks, p * q, w->small);
         launches += 2;
+        proj_flops += 2.0 * p * q * (double)n;
         G.resize((size_t)p * q);
         cudaMemcpyAsync(G.data(), w->small, sizeof(double) * p * q, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        ms_gram += now_ms() - t0;
+    }
+
+    // r2[a] = |X[a]|^2 on the host (p values)
+    void norms2(const double *X, int p, int64_t ld, std::vector<double> &r2) {
+        const double t0 = now_ms();
+        const int chunks = (int)((n + kGramChunk - 1) / kGramChunk);
+        norms_partial_kernel<<<dim3(chunks, p), 256, 0, s>>>(X, ld, p, n, w->partial);
+        reduce_kernel<<<(p + 255) / 256, 256, 0, s>>>(w->partial, chunks, p, w->small);
+        launches += 2;
+        proj_flops += 2.0 * p * (double)n;
+        r2.resize((size_t)p);
+        cudaMemcpyAsync(r2.data(), w->small, sizeof(double) * p, cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
         ms_gram += now_ms() - t0;
     }
@@ -644,6 +804,7 @@ struct Ops {
         dim3 g((unsigned)((n + 255) / 256), (q + 15) / 16);
         combine_kernel<<<g, 256, 0, s>>>(X, ld, p, w->small, q, n, Y, ld, beta, 1.0);
         ++launches;
+        proj_flops += 2.0 * p * q * (double)n;
         // no wait: the next upload into w->small is ordered after this kernel
         // on the stream, and the pageable source is staged before the copy call returns
         ms_combine += now_ms() - t0;
@@ -660,6 +821,7 @@ struct Ops {
         dim3 g2((unsigned)((n + 255) / 256), (q + 15) / 16);
         combine_kernel<<<g2, 256, 0, s>>>(X, ld, p, w->proj, q, n, Y, ld, 1.0, -1.0);
         launches += 3;
+        proj_flops += 4.0 * p * q * (double)n;
         ms_gram += now_ms() - t0;
     }
 };
@@ -725,7 +887,7 @@ int64_t hb::diag_workspace_bytes(const hb_ctx *ctx, int k, int precond) {
     const int64_t n = ctx->dim, Dc = ctx->Dc, nl = ctx->n_l2;
     if (n < 1 || k < 1) return 0;
     const int b = (int)std::min<int64_t>(n, k + std::max(4, std::min(16, k / 2)));
-    const int mmax = (int)std::min<int64_t>(n, std::max(5 * b, k + 4 * b));
+    const int mmax = (int)std::min<int64_t>(n, (int64_t)ctx->diag_basis * b);
     const int64_t chunks = (n + kGramChunk - 1) / kGramChunk;
     int64_t t = 5 * r(8.0 * mmax * n) + r(8.0 * n) + r(8.0 * chunks * mmax * mmax) + 2 * r(8.0 * mmax * mmax) +
                 r(8.0 * mmax) + r(4.0 * mmax);
@@ -812,7 +974,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         return diag_fail(ctx, HB_ERR_INVALID_ARG, "HB_PRECOND_MLP without weights (hb_mlp_set)");
     cudaStream_t s = (cudaStream_t)stream;
     const int b = (int)std::min<int64_t>(n, k + std::max(4, std::min(16, k / 2)));
-    const int mmax = (int)std::min<int64_t>(n, std::max(5 * b, k + 4 * b));
+    const int mmax = (int)std::min<int64_t>(n, (int64_t)ctx->diag_basis * b);
     int rc = ensure_diag_work(ctx, H, mmax, s);
     if (rc != HB_OK) return rc;
     DiagWork *w = (DiagWork *)ctx->diag;
@@ -862,6 +1024,46 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         ops.gram(blk, q, blk, q, ld, G);
         for (int a = 0; a < q; ++a)
             for (int c = 0; c < a; ++c) G[(size_t)a * q + c] = G[(size_t)c * q + a] = 0.5 * (G[(size_t)a * q + c] + G[(size_t)c * q + a]);
+        // A block that is already nearly orthonormal (the second pass: every
+        // |G - I| below 0.1, so cond(G) < 1.3) is finished by Cholesky,
+        // G = L L^T and C = L^-T, whose orthogonality error is a few units of
+        // rounding; the eigenvalues of such a G form one large cluster, which
+        // the eigensolver would treat vector by vector.
+        {
+            double dev = 0.0;
+            for (int a = 0; a < q; ++a)
+                for (int c = 0; c < q; ++c) dev = std::max(dev, std::fabs(G[(size_t)a * q + c] - (a == c ? 1.0 : 0.0)));
+            if (dev < 0.1) {
+                std::vector<double> L(G);
+                bool ok = true;
+                for (int j = 0; j < q && ok; ++j) {
+                    double d = L[(size_t)j * q + j];
+                    for (int t2 = 0; t2 < j; ++t2) d -= L[(size_t)j * q + t2] * L[(size_t)j * q + t2];
+                    if (!(d > 0.5)) { ok = false; break; }
+                    const double ljj = std::sqrt(d);
+                    L[(size_t)j * q + j] = ljj;
+                    for (int i = j + 1; i < q; ++i) {
+                        double v = L[(size_t)i * q + j];
+                        for (int t2 = 0; t2 < j; ++t2) v -= L[(size_t)i * q + t2] * L[(size_t)j * q + t2];
+                        L[(size_t)i * q + j] = v / ljj;
+                    }
+                }
+                if (ok) {
+                    // C = L^-T: upper triangular, column c solves L^T C[:, c] = e_c
+                    std::vector<double> C((size_t)q * q, 0.0);
+                    for (int c = 0; c < q; ++c)
+                        for (int a = c; a >= 0; --a) {
+                            double v = (a == c) ? 1.0 : 0.0;
+                            for (int t2 = a + 1; t2 <= c; ++t2) v -= L[(size_t)t2 * q + a] * C[(size_t)t2 * q + c];
+                            C[(size_t)a * q + c] = v / L[(size_t)a * q + a];
+                        }
+                    kept = q;
+                    ops.combine(blk, q, C, q, w->X, ld, 0.0);
+                    cudaMemcpyAsync(blk, w->X, sizeof(double) * (size_t)q * ld, cudaMemcpyDeviceToDevice, s);
+                    return;
+                }
+            }
+        }
         ops.eigh(q, G, lam, U, q);
         const double lmax = lam.empty() ? 0.0 : lam.back();
         std::vector<int> keep;
@@ -889,6 +1091,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
     float *wts = nullptr;
     int fallbacks = 0;
     const int kStall = ctx->stall_iters;
+    constexpr int kTcStall = 10;
     const double stall_fall = std::ldexp(1.0, -ctx->stall_log2);
     int refreshes = 0, fp64_iters = 0;
     std::vector<double> res_hist;
@@ -903,7 +1106,8 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         std::vector<double> T(Tp), S;
         for (int a = 0; a < m; ++a)
             for (int c = 0; c < a; ++c) T[(size_t)a * m + c] = T[(size_t)c * m + a] = 0.5 * (T[(size_t)a * m + c] + T[(size_t)c * m + a]);
-        const int nv = std::min(m, 2 * b);      // Ritz vectors needed: b, or 2b at a restart
+        // Ritz vectors needed: b, and 2b when this iteration may restart
+        const int nv = std::min(m, m + b > mmax ? 2 * b : b);
         ops.eigh(m, T, theta, S, nv);
         const int nr = std::min(m, b);
         std::vector<double> Sk((size_t)m * nr);
@@ -919,18 +1123,27 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
             ++ops.launches;
         }
         std::vector<double> RR;
-        ops.gram(w->AX, nr, w->AX, nr, ld, RR);
+        ops.norms2(w->AX, nr, ld, RR);
         std::vector<int32_t> which;
         maxres = 0.0;
         for (int j = 0; j < nr; ++j) {
-            const double r = std::sqrt(std::max(0.0, RR[(size_t)j * nr + j]));
+            const double r = std::sqrt(std::max(0.0, RR[(size_t)j]));
             if (j < k) maxres = std::max(maxres, r);
             if (r > tol) which.push_back(j);
         }
         bool done = true;
         for (int j = 0; j < k; ++j)
-            if (std::sqrt(std::max(0.0, RR[(size_t)j * nr + j])) > tol) done = false;
-        if (done) {
+            if (std::sqrt(std::max(0.0, RR[(size_t)j])) > tol) done = false;
+        // With tensor-core products the residuals carry a floor of their own:
+        // the product errors E give the Ritz residual a component inside the
+        // basis, (V^T E - sym(V^T E)) s, that no correction (orthogonal to
+        // the basis) removes, and it grows with the basis.  When the largest
+        // wanted residual, already within 1e4 tol, has not halved over
+        // kTcStall iterations, the solve goes on from fresh FP64 products, as
+        // after a converged check.
+        const bool tc_stalled = w->tc && !ops.force_fp64 && (int)res_hist.size() >= kTcStall &&
+                                maxres <= 1e4 * tol && maxres > 0.5 * res_hist[res_hist.size() - kTcStall];
+        if (done || tc_stalled) {
             // The residuals above come from products carried through the
             // restarts (A X = (A V) S): the Rayleigh-Ritz step fits the errors
             // of those products, so they measure the residual of a perturbed
@@ -951,17 +1164,17 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
                 residual_kernel<<<g, 256, 0, s>>>(w->AX, w->X, ld, w->theta, nr, n, w->AX);
                 ++ops.launches;
             }
-            ops.gram(w->AX, nr, w->AX, nr, ld, RR);
+            ops.norms2(w->AX, nr, ld, RR);
             which.clear();
             maxres = 0.0;
             for (int j = 0; j < nr; ++j) {
-                const double r = std::sqrt(std::max(0.0, RR[(size_t)j * nr + j]));
+                const double r = std::sqrt(std::max(0.0, RR[(size_t)j]));
                 if (j < k) maxres = std::max(maxres, r);
                 if (r > tol) which.push_back(j);
             }
             done = true;
             for (int j = 0; j < k; ++j)
-                if (std::sqrt(std::max(0.0, RR[(size_t)j * nr + j])) > tol) done = false;
+                if (std::sqrt(std::max(0.0, RR[(size_t)j])) > tol) done = false;
             ++refreshes;
             if (done) { converged = true; break; }
         }
@@ -1079,6 +1292,7 @@ extern "C" int hb_diag(hb_ctx *ctx, const hb_blocks *H, int32_t k, double tol, i
         st->fp64_iterations = fp64_iters;
         st->kernel_launches = ops.launches;
         st->mlp_fallbacks = fallbacks;
+        st->proj_gflop = (int32_t)std::min(2.0e9, ops.proj_flops / 1e9 + 0.5);
     }
     if (!converged) return diag_fail(ctx, HB_ERR_NOT_CONVERGED, "Davidson did not converge in max_iter iterations");
     return HB_OK;

@@ -71,3 +71,35 @@ def test_davidson_not_converged_status():
     w, st, ok = H.diag(b, 8, 1e-12, 2, allow_not_converged=True)
     assert not ok and st.iterations == 2
     H.close()
+
+
+@pytest.mark.parametrize("tensor", [False, True])
+@pytest.mark.parametrize("basis", [3, 10])
+def test_davidson_basis_limit(basis, tensor):
+    """hb_options.diag_basis: a basis of 3 or 10 blocks of b vectors before
+    each thick restart gives the same eigenpairs (within 1e-8 of the oracle's
+    eigh, residuals checked with its matrix), with FP64 or tensor-core block
+    products (whose residual floor grows with the basis: a solve that stalls
+    near it goes on with FP64 products); out-of-range values are refused."""
+    import torch
+    from paper_1709_03005_gb300 import hb
+    P = synth.make_config("mid")
+    H = hb.Hamiltonian(P, diag_basis=basis)
+    b, _ = H.build(0)
+    k = 12
+    evecs = torch.zeros((P.dim, k), dtype=torch.float64, device="cuda")
+    flags = hb.HB_DIAG_TENSOR if tensor else 0
+    w, st, _ = H.diag(b, k, 1e-8, 500, precond=hb.HB_PRECOND_DIAG | flags, evecs=evecs)
+    torch.cuda.synchronize()
+    X = evecs.cpu().numpy()
+    H.close()
+    o = coracle.Oracle(P)
+    R = o.dense()
+    ref = np.linalg.eigvalsh(R)[:k]
+    print(f"basis {basis} blocks, tensor {tensor}: {st.iterations} iterations ({st.fp64_iterations} with FP64 "
+          f"products)")
+    np.testing.assert_allclose(w, ref, atol=1e-8)
+    assert np.linalg.norm(R @ X - X * w, axis=0).max() <= 1e-8 * 1.01
+    for bad in (1, 2, 11, -1):
+        with pytest.raises(hb.HBError):
+            hb.Hamiltonian(P, diag_basis=bad)
