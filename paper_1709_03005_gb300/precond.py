@@ -220,7 +220,8 @@ def main():
             print(f"{name:5s} k={args.k}: {dst.iterations} iterations, {time.perf_counter() - t0:.1f} s, "
                   f"converged {ok}, max residual {dst.max_residual:.2e}, products {dst.ms_matvec / 1e3:.1f} s, "
                   f"small eigenproblems {dst.ms_rr / 1e3:.1f} s, projections {dst.ms_gram / 1e3:.1f} s, "
-                  f"lowest {w[0]:.10f} highest wanted {w[-1]:.10f}", flush=True)
+                  f"lowest {w[0]:.10f} highest wanted {w[-1]:.10f}, learned-factor fallbacks {dst.mlp_fallbacks}",
+                  flush=True)
         H.close()
         return
     if args.cmd == "evaluate":

@@ -129,8 +129,25 @@ def sampled_checks(P, o, cc, b, rng, precision, n_cc=400, n_rows=12, what=""):
     _, _, n_canc, worst = check_elements(got, ref, cond, rel, MIXED_CC_FALLBACK if mixed else FP64_FALLBACK,
                                          f"{what} cc sampled", blockmax=bm)
     strict10 = float(np.mean(np.abs(got - ref) <= 1e-10 * np.abs(ref)))
-    print(f"{what}: {100 * strict10:.2f} % of sampled continuum elements within 1e-10 of their magnitude, "
-          f"{n_canc} by the cancellation clause, worst |d|/cond {worst:.2e}")
+    # The mixed error stays below 3e-11 of the element's condition scale
+    # (the fallback clause; measured at most 2.0e-11, on the L2-heavy
+    # workload), so an element whose terms cancel by at most a factor of 3
+    # meets the relative bound itself: every such element is held to it.
+    d = np.abs(got - ref)
+    ratio = cond / np.maximum(np.abs(ref), 1e-300)
+    plain = ratio <= 3.0
+    off = plain & (d > rel * np.abs(ref))
+    assert not off.any(), (f"{what}: {int(off.sum())} of {int(plain.sum())} continuum elements with condition scale "
+                           f"within 3 of their magnitude beyond {rel:g} relative")
+    stats = []
+    for lim in (3, 10, 100):
+        sel = ratio <= lim
+        if sel.any():
+            stats.append(f"cond <= {lim}|ref|: {int(sel.sum())}, max rel {float((d[sel] / np.abs(ref[sel])).max()):.1e}")
+    print(f"{what}: {100 * strict10:.2f} % of sampled continuum elements within 1e-10 of their magnitude; "
+          f"{n_canc} by the cancellation clause; |d|/cond max {worst:.1e}, median "
+          f"{float(np.median(d / np.maximum(cond, 1e-300))):.1e}; cond/|ref| median {float(np.median(ratio)):.0f}; "
+          + "; ".join(stats))
     rows = np.sort(rng.choice(P.n_l2, n_rows, replace=False))
     ref4 = np.stack([o.class4_row(int(l)) for l in rows])
     cond4 = np.stack([o.class4_rows_abs(int(l), int(l) + 1)[0] for l in rows])

@@ -30,7 +30,7 @@ def test_l2_heavy_build_and_davidson():
     b, st = H.build(hb.HB_MIXED)
     torch.cuda.synchronize()
     print(f"h3po4 shape: L2 nnz {H.layout.l2_nnz:.3e}, mixed build {st.ms_total:.2f} ms")
-    sampled_checks(P, o, cc, b, np.random.default_rng(7), 1, n_cc=300, n_rows=8, what="h3po4 mixed")
+    sampled_checks(P, o, cc, b, np.random.default_rng(7), 1, n_cc=1000, n_rows=8, what="h3po4 mixed")
 
     # the oracle's matrix, block by block (its dense form would be 15e9 entries)
     nl, Dc = P.n_l2, o.Dc

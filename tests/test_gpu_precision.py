@@ -27,11 +27,11 @@ def test_precision_workload_sampled():
     bm, stm = H.build(hb.HB_MIXED)
     torch.cuda.synchronize()
     rng = np.random.default_rng(3)
-    sampled_checks(P, o, cc, bm, rng, 1, what="c3 mixed")
+    sampled_checks(P, o, cc, bm, rng, 1, n_cc=2000, what="c3 mixed")
     mixed_cc = bm["Hcc"]
     b64, st64 = H.build(hb.HB_FP64)
     torch.cuda.synchronize()
-    sampled_checks(P, o, cc, b64, np.random.default_rng(3), 0, what="c3 FP64")
+    sampled_checks(P, o, cc, b64, np.random.default_rng(3), 0, n_cc=2000, what="c3 FP64")
     # whole-block comparison of the two GPU paths
     d = (mixed_cc - b64["Hcc"]).abs()
     ref = b64["Hcc"].abs()
@@ -55,5 +55,5 @@ def test_learned_workload_sampled():
     b, st = H.build(hb.HB_MIXED)
     torch.cuda.synchronize()
     assert H.dim == 60000
-    sampled_checks(P, o, cc, b, np.random.default_rng(5), 1, n_cc=300, n_rows=8, what="c5 mixed")
+    sampled_checks(P, o, cc, b, np.random.default_rng(5), 1, n_cc=1000, n_rows=8, what="c5 mixed")
     H.close()
