@@ -21,7 +21,9 @@ H3PO4 run (dimension 122815, 122103 L2 functions) under "l2_heavy"; the
 
 Prints one JSON line (rank 0).  Under torchrun every rank builds its own
 replica (independent problem, no data-path collective) and the time is the
-maximum over ranks.
+maximum over ranks.  With --sharded the ranks also build one matrix together
+(contraction shares, an NCCL all-reduce of the partial coefficient rows,
+expansion shares) and the line gains a "sharded" key (strong scaling).
 """
 from __future__ import annotations
 
@@ -323,6 +325,48 @@ def run_ours(args, rank, world, local_rank):
     gemm_ms = float(np.mean([x.ms_expand_gemm for x in sts]))
     exp_ms = float(np.mean([x.ms_expand for x in sts]))
 
+    # the sharded build (Section 3.1), with --sharded: every rank contracts its
+    # share of the bra determinants, an all-reduce (NCCL under torchrun) sums
+    # the partial coefficient rows, and every rank expands its share of the
+    # tiles and L2 rows.  The total work is one build for any number of ranks
+    # (strong scaling): the value is one build's positions over the slowest
+    # rank's time per step.
+    sharded = None
+    if args.sharded:
+        import torch.distributed as dist
+        part = torch.empty(max(H.shard_coef_len(), 1), dtype=torch.float64, device="cuda")
+        sb = H.allocate()
+
+        def sharded_step():
+            partial, _ = H.build_contract(precision, rank, world, part)
+            if world > 1:
+                dist.all_reduce(partial, op=dist.ReduceOp.SUM)
+            H.build_expand(precision, rank, world, partial, sb)
+
+        for _ in range(args.warmup):
+            sharded_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sharded_step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = torch.tensor([float(np.mean(ts))], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+        ms = float(ms.item())
+        sharded = {"ranks": world, "scaling": "strong", "ms_per_step": ms, "value": positions(dim) / (ms / 1e3),
+                   "unit": "H elements/s",
+                   "exchange_bytes_per_step": 8 * H.shard_coef_len() if world > 1 else 0}
+        del sb, part
+        torch.cuda.empty_cache()
+
     # the plain FP64 GPU build of the same instance, after the timed steps
     fp64 = None
     if precision == hb.HB_MIXED and args.fp64_steps > 0:
@@ -538,7 +582,7 @@ def run_ours(args, rank, world, local_rank):
                "config": {"workload": workload_text(args), "dim": dim,
                           "positions": positions(dim), "l2_flush": "256 MB write between timed steps",
                           "parallelism": f"replicas x{world}", "precision": args.precision},
-               "fp64": fp64, "speedup_vs_fp64": fp64["ms_per_step"] / (total_ms / args.steps) if fp64 else None,
+               "sharded": sharded, "fp64": fp64, "speedup_vs_fp64": fp64["ms_per_step"] / (total_ms / args.steps) if fp64 else None,
                "init_ms": float(np.mean(init_ms)),
                "roofline": roof, "cpu_baseline": cb,
                "e2e": {"value": e2e_value, "unit": "H elements/s", "h2d_bytes_per_step": int(h2d),
@@ -567,6 +611,8 @@ def main():
     ap.add_argument("--no-l2-heavy", dest="l2_heavy", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--sharded", action="store_true",
+                    help="also time the sharded build (contraction share, all-reduce, expansion share per rank)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
