@@ -128,6 +128,15 @@ typedef struct {
     int32_t n_l2;
     const uint64_t *l2_dets;  /* host, [n_l2][2*n_words], N+1 electrons */
     double e_core;            /* constant added to the Hamiltonian (0 if none) */
+    const int32_t *orb_irrep; /* host, [n_to + n_co], or NULL: the spatial symmetry of every orbital
+                                 (irreducible representation 0..7 of an abelian point group whose
+                                 product is XOR, as for D2h and its subgroups).  With it the
+                                 integrals must vanish unless the XOR of their four orbitals' irreps
+                                 is 0 (checked on the device when validating), and every group's
+                                 continuum range must lie within one irrep.  The expansion panel
+                                 then keeps, for each continuum pair, only the labels of its
+                                 symmetry (about an eighth of them): less memory and work, the
+                                 same results up to the order of the sums. */
 } hb_problem;
 
 typedef struct {

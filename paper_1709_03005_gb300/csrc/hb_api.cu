@@ -357,6 +357,81 @@ extern "C" int hb_init_shared(hb_ctx **out, const hb_problem *p, const hb_option
     return HB_OK;
 }
 
+// The class of every panel label: the irrep of its target pair (r, s) for
+// (jj'|rs) and of (p, q) for (jq|pj'); h and delta in class 0.
+static std::vector<int32_t> label_classes(const hb_ctx *ctx, const hb_problem *p) {
+    const int n_to = p->n_to, nt2 = n_to * n_to;
+    const int64_t Pt = ctx->Pt;
+    const int32_t *ir = p->orb_irrep;
+    std::vector<int32_t> lc(ctx->K, 0);
+    for (int64_t k = 0; k < Pt; ++k) {
+        int r = (int)((std::sqrt(8.0 * (double)k + 1.0) - 1.0) / 2.0);
+        while ((int64_t)r * (r + 1) / 2 > k) --r;
+        while ((int64_t)(r + 1) * (r + 2) / 2 <= k) ++r;
+        const int q = (int)(k - (int64_t)r * (r + 1) / 2);
+        lc[k] = ir[r] ^ ir[q];
+    }
+    for (int pq = 0; pq < nt2; ++pq) lc[Pt + pq] = ir[pq / n_to] ^ ir[pq % n_to];
+    return lc;
+}
+
+// Panel label classes: one class of every label without orbital symmetry;
+// with it, the labels of each irrep of the target pair in ascending order,
+// Kc (the largest class, padded to 64) columns per class.  A context that
+// borrows its integrals borrows these.
+static int setup_label_classes(hb_ctx *ctx, const hb_problem *p, cudaStream_t s) {
+    const int delta_label = (int)(ctx->Pt + (int64_t)p->n_to * p->n_to + 1);
+    if (ctx->base) {
+        const hb_ctx *B = ctx->base;
+        if ((p->orb_irrep != nullptr) != (B->n_cls > 1))
+            return fail(ctx, HB_ERR_INVALID_ARG, "orb_irrep must be given for the base context and this one alike");
+        ctx->n_cls = B->n_cls; ctx->Kc = B->Kc; ctx->cls_labels = B->cls_labels; ctx->cls_labels_h = B->cls_labels_h;
+        ctx->co_irrep = B->co_irrep; ctx->co_irrep_d = B->co_irrep_d; ctx->delta_pos = B->delta_pos;
+    } else if (!p->orb_irrep) {
+        ctx->n_cls = 1;
+        ctx->Kc = ctx->Kpad;
+        ctx->delta_pos = delta_label;
+    } else {
+        const int n_orb = p->n_to + p->n_co;
+        for (int i = 0; i < n_orb; ++i)
+            if (p->orb_irrep[i] < 0 || p->orb_irrep[i] > 7)
+                return fail(ctx, HB_ERR_INVALID_ARG, "orb_irrep values must be 0..7");
+        const std::vector<int32_t> lc = label_classes(ctx, p);
+        std::vector<std::vector<int32_t>> lists(8);
+        for (int k = 0; k < ctx->K; ++k) lists[lc[k]].push_back(k);
+        size_t most = 1;
+        for (auto &l : lists) most = std::max(most, l.size());
+        ctx->n_cls = 8;
+        ctx->Kc = (int)((most + 63) / 64 * 64);
+        ctx->cls_labels_h.assign((size_t)8 * ctx->Kc, -1);
+        for (int x = 0; x < 8; ++x)
+            for (size_t i = 0; i < lists[x].size(); ++i) {
+                ctx->cls_labels_h[(size_t)x * ctx->Kc + i] = lists[x][i];
+                if (lists[x][i] == delta_label) ctx->delta_pos = (int)i;
+            }
+        ctx->co_irrep.assign(p->orb_irrep + p->n_to, p->orb_irrep + n_orb);
+        DALLOC(ctx->cls_labels, (size_t)8 * ctx->Kc);
+        DALLOC(ctx->co_irrep_d, std::max(p->n_co, 1));
+        CK(cudaMemcpyAsync(ctx->cls_labels, ctx->cls_labels_h.data(), sizeof(int32_t) * ctx->cls_labels_h.size(),
+                           cudaMemcpyHostToDevice, s));
+        if (p->n_co > 0)
+            CK(cudaMemcpyAsync(ctx->co_irrep_d, ctx->co_irrep.data(), sizeof(int32_t) * p->n_co,
+                               cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));   // the host tables are staged from (pageable) vectors
+    }
+    if (ctx->n_cls > 1)
+        for (int g = 0; g < p->n_groups; ++g) {
+            const hb_group &G = p->groups[g];
+            if (G.cont_count < 0 || G.cont_first < 0 || (int64_t)G.cont_first + G.cont_count > p->n_co)
+                return fail(ctx, HB_ERR_INVALID_ARG, "group " + std::to_string(g) + ": continuum range");
+            for (int j = G.cont_first; j < G.cont_first + G.cont_count; ++j)
+                if (ctx->co_irrep[j] != ctx->co_irrep[G.cont_first])
+                    return fail(ctx, HB_ERR_INVALID_ARG,
+                                "group " + std::to_string(g) + ": its continuum range spans several irreps");
+        }
+    return HB_OK;
+}
+
 int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStream_t s) {
     CK(cudaGetDevice(&ctx->device));
     ctx->n_to = p->n_to; ctx->n_co = p->n_co; ctx->n_orb = p->n_to + p->n_co;
@@ -377,6 +452,12 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
     ctx->K = (int)(ctx->Pt + (int64_t)p->n_to * p->n_to + 2);
     ctx->Kpad = (ctx->K + 63) / 64 * 64;
     const int W = ctx->W, nw = 2 * W;
+    const bool validate = !o || o->validate;
+    // the expansion panel's label classes (orbital symmetry)
+    {
+        int rc = setup_label_classes(ctx, p, s);
+        if (rc != HB_OK) return rc;
+    }
     // groups and offsets
     int64_t det_off = 0, ci_off = 0, row_off = 0, e_off = 0;
     for (int g = 0; g < p->n_groups; ++g) {
@@ -431,7 +512,7 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
     if (!shared) build_jk(I, ctx->jk, s);
     // --- the expansion panel (classes 1,3,5,6,7)
     if (p->n_groups > 0 && !shared) {
-        DALLOC(ctx->panel, ncc * ctx->Kpad);
+        DALLOC(ctx->panel, ncc * ctx->Kc);
         double *t_ttcc = nullptr, *t_tctc = nullptr;
         CK(cudaMalloc(&t_ttcc, sizeof(double) * Pt * ncc));
         cudaError_t e2 = cudaMalloc(&t_tctc, sizeof(double) * ntc * ntc);
@@ -439,13 +520,37 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
         cudaError_t e3 = cudaMemcpyAsync(t_ttcc, p->eri_ttcc, sizeof(double) * Pt * ncc, cudaMemcpyHostToDevice, s);
         if (e3 == cudaSuccess)
             e3 = cudaMemcpyAsync(t_tctc, p->eri_tctc, sizeof(double) * ntc * ntc, cudaMemcpyHostToDevice, s);
+        int sym_bad = 0;
         if (e3 == cudaSuccess) {
-            build_panel(t_ttcc, t_tctc, ctx->h, p->n_to, p->n_co, ctx->Kpad, ctx->panel, s);
-            e3 = cudaStreamSynchronize(s);
+            build_panel(t_ttcc, t_tctc, ctx->h, p->n_to, p->n_co, ctx->Kc, ctx->n_cls > 1 ? ctx->cls_labels : nullptr,
+                        ctx->co_irrep_d, ctx->panel, s);
+            if (ctx->n_cls > 1 && validate) {
+                // every panel value outside its row's class must vanish
+                int32_t *lcls = nullptr;
+                int *flag = nullptr;
+                e3 = cudaMalloc(&lcls, sizeof(int32_t) * ctx->K);
+                if (e3 == cudaSuccess) e3 = cudaMalloc(&flag, sizeof(int));
+                std::vector<int32_t> lc = label_classes(ctx, p);
+                if (e3 == cudaSuccess)
+                    e3 = cudaMemcpyAsync(lcls, lc.data(), sizeof(int32_t) * ctx->K, cudaMemcpyHostToDevice, s);
+                if (e3 == cudaSuccess) e3 = cudaMemsetAsync(flag, 0, sizeof(int), s);
+                if (e3 == cudaSuccess) {
+                    check_panel_symmetry(t_ttcc, t_tctc, ctx->h, p->n_to, p->n_co, ctx->K, lcls, ctx->co_irrep_d,
+                                         flag, s);
+                    e3 = cudaMemcpyAsync(&sym_bad, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+                }
+                if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(s);
+                cudaFree(lcls);
+                cudaFree(flag);
+            }
+            if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(s);
         }
         cudaFree(t_ttcc);
         cudaFree(t_tctc);
         if (e3 != cudaSuccess) return cuda_fail(ctx, e3, "panel staging");
+        if (sym_bad)
+            return fail(ctx, HB_ERR_INVALID_ARG,
+                        "orb_irrep: an integral of the continuum classes breaks the declared symmetry");
     }
     // --- classification counts (structure of every class)
     for (int g = 0; g < p->n_groups; ++g)
@@ -931,6 +1036,8 @@ extern "C" int hb_dump(const hb_ctx *ctx, const char *path) {
     fprintf(f, "dimension %lld = contracted %lld + L2 %d\n", (long long)ctx->dim, (long long)ctx->Dc, ctx->n_l2);
     fprintf(f, "labels K %d (padded %d), e_core %.17g, split slices %d\n", ctx->K, ctx->Kpad, ctx->e_core,
             ctx->split_slices);
+    fprintf(f, "expansion panel: %d label class%s of %d columns%s\n", ctx->n_cls, ctx->n_cls > 1 ? "es" : "",
+            ctx->Kc, ctx->n_cls > 1 ? " (orbital symmetry)" : "");
     for (int g = 0; g < ctx->n_groups; ++g) {
         const GroupInfo &G = ctx->groups[g];
         fprintf(f, "group %d: %d determinants, %d states, continuum [%d, %d), rows from %lld\n", g, G.ndet, G.ns, G.cf,

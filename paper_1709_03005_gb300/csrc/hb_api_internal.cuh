@@ -114,6 +114,24 @@ struct hb_ctx {
     int c4_path = 0;         // mixed class 4: 0 tensor cores for 32..64 states, 1 double-float only, 2 tensor cores for 1..64
     int64_t Pt = 0;
     int K = 0, Kpad = 0;
+    // expansion panel columns: without orbital symmetry every label (n_cls 1,
+    // Kc = Kpad); with it, 8 label classes (the irrep of the label's target
+    // pair; h and delta in class 0) and Kc columns per class, padded to 64
+    int n_cls = 1, Kc = 0;
+    int32_t *cls_labels = nullptr;          // device [n_cls][Kc]: the labels of each class (-1 padding)
+    std::vector<int32_t> cls_labels_h;
+    std::vector<int32_t> co_irrep;          // irrep of every continuum orbital (empty without symmetry)
+    int32_t *co_irrep_d = nullptr;
+    int delta_pos = 0;                      // panel column of the delta label (in class 0)
+    // the panel column list of the rectangle whose first continuum orbitals
+    // are cf and cfp (null without symmetry)
+    int class_of(int cf, int cfp) const {
+        const int n = (int)co_irrep.size();
+        return (n_cls > 1 && cf >= 0 && cf < n && cfp >= 0 && cfp < n) ? (co_irrep[cf] ^ co_irrep[cfp]) : 0;
+    }
+    const int32_t *class_labels(int cf, int cfp) const {
+        return n_cls > 1 ? cls_labels + (int64_t)class_of(cf, cfp) * Kc : nullptr;
+    }
     int64_t Dc = 0, dim = 0;
     std::vector<hb::GroupInfo> groups;
     std::vector<hb::GroupPair> gps;

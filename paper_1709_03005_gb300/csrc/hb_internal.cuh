@@ -107,12 +107,12 @@ void assemble_coefficients(const double *gamma, const double *S, const double *E
                            cudaStream_t s);
 
 // K3 expansion (k_expand.cu)
-void build_panel(const double *ttcc, const double *tctc, const double *h, int n_to, int n_co, int Kpad,
-                 double *P, cudaStream_t s);
-void expand_fp64(const double *P, const double *A, const int32_t *nn, int n_nn, int Kpad, int n_co, int cf,
-                 int cn, int cfp, int cnp, int64_t row_off, int64_t col_off, int same_group, int64_t ld,
-                 double *H, cudaStream_t s);
-
+void build_panel(const double *ttcc, const double *tctc, const double *h, int n_to, int n_co, int Kc,
+                 const int32_t *cls_labels, const int32_t *co_irrep, double *P, cudaStream_t s);
+// with orbital symmetry: *flag |= 1 if a panel value breaks it (label_cls[k]
+// is the class of label k, co_irrep the continuum orbitals' irreps)
+void check_panel_symmetry(const double *ttcc, const double *tctc, const double *h, int n_to, int n_co, int K,
+                          const int32_t *label_cls, const int32_t *co_irrep, int *flag, cudaStream_t s);
 // K4 class 4 (k_class4.cu)
 // dfloat = 0: FP64 accumulation; 1: FP32 double-float accumulation (mixed path)
 void class4_build(const Ints &I, const hb_pair *pairs, const int64_t *row_ptr, int n_l2, const uint64_t *dets,

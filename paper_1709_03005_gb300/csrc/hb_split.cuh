@@ -21,12 +21,17 @@ int64_t blocks_split(int cn, int cnp, int N, int lg);
 int split_ntn(int N);
 int split_jpt(int cnp, int lg);
 int split_tile_heuristic(int cn, int cnp);
-int g_slice(const hb::Grouped<hb::SliceTask> &g, int64_t R, int Kpad, int S, int skip_col, void *out,
-            cudaStream_t s);
-// lg: tile arrangement (3..5, see SplitTask); every task of g must use it
+// coefficient rows of Kin labels into slices of Kout columns, column k being
+// label perm[k] (null: label k)
+int g_slice(const hb::Grouped<hb::SliceTask> &g, int64_t R, int Kin, int Kout, const int32_t *perm, int S,
+            int skip_col, void *out, cudaStream_t s);
+// lg: tile arrangement (3..5, see SplitTask); every task of g must use it.
+// kblocks: 64-wide K blocks of the panel rows; coef_planes: K blocks per
+// slice of the coefficient slices (the task's kc0 selects its label class)
 // shard_r, shard_n: the launch takes tiles shard_r, shard_r + shard_n, ... only
 int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const hb::Grouped<hb::SplitTask> &g,
-            int kblocks, const hb::ExpCol *cols, int *err, cudaStream_t s, int shard_r = 0, int shard_n = 1);
+            int kblocks, int coef_planes, const hb::ExpCol *cols, int *err, cudaStream_t s, int shard_r = 0,
+            int shard_n = 1);
 int64_t blocks_diag_rows(int j_lo, int j_hi, int n_nn);
 int diag_rows_ny(int n_nn);
 int g_diag_rows(const hb::Grouped<hb::DRTask> &g, cudaStream_t s);

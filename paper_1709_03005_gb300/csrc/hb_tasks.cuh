@@ -151,8 +151,9 @@ struct ExpCol {
 
 struct XTask {          // FP64 expansion of one merged block (Eq. 7)
     const double *P;
-    int Kpad, n_co, cf, cn, cfp, cnp, mtiles, N;
+    int Kpad, n_co, cf, cn, cfp, cnp, mtiles, N;   // Kpad: panel columns (labels of the block's class)
     int64_t col0;             // first column in the ExpCol table
+    const int32_t *perm;      // label of each panel column (orbital symmetry; -1 padding), or null: column = label
 };
 
 struct SliceTask {      // rows of X into bf16 slices at destination rows [row0, row0 + rows)
@@ -164,15 +165,17 @@ struct SplitTask {      // one merged block on the tensor cores
     int cf, cn, cfp, cnp;     // the continuum rectangle (same for every column)
     int jpt_tiles, ntn, N;    // tiles along j', tiles along the columns, columns
     int bjp_log2;             // tile of (128 >> bjp_log2) j x (1 << bjp_log2) j' continuum pairs (3..5)
+    int kc0;                  // first 64-wide K block of the block's label class in the coefficient slices
     int64_t coef_row0;        // first row of the block in the coefficient slices
     int64_t col0;             // first column in the ExpCol table
 };
 
 struct DRTask {         // rows with j == j' of one group pair, in double-float
     const float2 *Pd;         // panel rows (j, j) as float pairs [n_co][Kpad]
-    const float2 *A;          // coefficient rows as float pairs [n_nn][Kpad]
+    const float2 *A;          // coefficient rows as float pairs [n_nn][Ka]
     const int32_t *nn;
-    int n_nn, Kpad, n_co, j_lo, j_hi, cf, cn, cfp, cnp, same, ny;
+    const int32_t *perm;      // label of each panel column of class 0 (orbital symmetry), or null
+    int n_nn, Kpad, Ka, n_co, j_lo, j_hi, cf, cn, cfp, cnp, same, ny;
     int64_t row_off, col_off, ld;
     double *H;
 };

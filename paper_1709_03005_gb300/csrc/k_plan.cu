@@ -41,6 +41,16 @@ struct Stage {
     }
 };
 
+// Labels of the class of the rectangle whose first continuum orbitals are cf,
+// cfp (every label without orbital symmetry): the K of its Eq. 7 sums.
+static int class_label_count(const hb_ctx *ctx, int cf, int cfp) {
+    if (ctx->n_cls <= 1) return ctx->K;
+    const int x = ctx->class_of(cf, cfp);
+    int c = 0;
+    for (int i = 0; i < ctx->Kc; ++i) c += ctx->cls_labels_h[(size_t)x * ctx->Kc + i] >= 0;
+    return c;
+}
+
 struct SplitGroup {
     const hb_ctx *panel_ctx = nullptr;
     int lg = 4;                        // tile arrangement of every task of the launch
@@ -73,6 +83,11 @@ struct Plan {
     std::vector<hb_blocks> outs;
     int precision = HB_FP64;
     int W = 1, Kpad = 0, n_to = 0, S = 0, delta_col = 0;
+    // panel columns per label class (Kc) and the coefficient slices' width
+    // (Kw = every class); perm: the labels of the coefficient slice columns
+    // (null without orbital symmetry)
+    int Kc = 0, Kw = 0;
+    const int32_t *perm = nullptr;
     Stage<ClsTask> cls_tt, cls_tl2;
     Stage<PVTask> pv;
     Stage<PVTask> pvd;                 // the diagonal records of same-group pairs
@@ -308,7 +323,7 @@ void fill_tasks(Plan &p) {
                              ctx->e_core, P.A, p.precision == HB_MIXED ? P.A_df : nullptr,
                              ctx->energy ? ctx->energy + A.e_off : nullptr, ctx->energy && p.shard_r != 0},
                        P.n_nn);
-            p.flops += 2.0 * (double)A.cn * B.cn * P.n_nn * ctx->K;
+            p.flops += 2.0 * (double)A.cn * B.cn * P.n_nn * class_label_count(ctx, A.cf, B.cf);
             ++p.n_expand_tasks;
             // the pair joins the expansion block of its continuum rectangle
             const BlockKey key{(const void *)ctx->panel, A.cf, A.cn, B.cf, B.cn};
@@ -322,7 +337,9 @@ void fill_tasks(Plan &p) {
             blocks[it->second].members.push_back(Member{ctx, &P, &out});
             if (p.precision == HB_MIXED && p.shard_r == 0) {     // the j == j' rows: the first shard
                 const int j_lo = std::max(A.cf, B.cf), j_hi = std::min(A.cf + A.cn, B.cf + B.cn);
-                p.drows.add(DRTask{mixed_panel_diag(ctx), P.A_df, P.nn, P.n_nn, ctx->Kpad, ctx->n_co, j_lo, j_hi, A.cf, A.cn,
+                // rows j == j' are of class 0 (irrep(j) ^ irrep(j) = 0)
+                p.drows.add(DRTask{mixed_panel_diag(ctx), P.A_df, P.nn, ctx->n_cls > 1 ? ctx->cls_labels : nullptr,
+                                   P.n_nn, ctx->Kc, ctx->Kpad, ctx->n_co, j_lo, j_hi, A.cf, A.cn,
                                    B.cf, B.cn, P.same, diag_rows_ny(P.n_nn), A.row_off, B.row_off, ctx->Dc, out.Hcc},
                             blocks_diag_rows(j_lo, j_hi, P.n_nn));
             }
@@ -440,12 +457,13 @@ void fill_tasks(Plan &p) {
             t.N = N;
             t.coef_row0 = coef_row;
             t.col0 = col0;
+            t.kc0 = B.ctx->class_of(k.cf, k.cfp) * (p.Kc / 64);
             p.split[gi].st.add(t, blocks_split(k.cn, k.cnp, N, lg));
             p.tune_split.push_back(TuneSplit{B.ctx, t});
             coef_row += N;
         } else {
-            p.x64.add(XTask{B.ctx->panel, B.ctx->Kpad, B.ctx->n_co, k.cf, k.cn, k.cfp, k.cnp,
-                            expand_fp64_mtiles(k.cn, k.cnp), N, col0},
+            p.x64.add(XTask{B.ctx->panel, B.ctx->Kc, B.ctx->n_co, k.cf, k.cn, k.cfp, k.cnp,
+                            expand_fp64_mtiles(k.cn, k.cnp), N, col0, B.ctx->class_labels(k.cf, k.cfp)},
                       blocks_expand_fp64(k.cn, k.cnp, N));
         }
     }
@@ -537,12 +555,21 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
     p->W = ctxs[0]->W;
     p->Kpad = ctxs[0]->Kpad;
     p->n_to = ctxs[0]->n_to;
-    for (int i = 1; i < n; ++i)
+    p->Kc = ctxs[0]->Kc;
+    p->Kw = ctxs[0]->n_cls * ctxs[0]->Kc;
+    p->perm = ctxs[0]->n_cls > 1 ? ctxs[0]->cls_labels : nullptr;
+    for (int i = 1; i < n; ++i) {
         if (ctxs[i]->W != p->W || ctxs[i]->Kpad != p->Kpad || ctxs[i]->n_to != p->n_to) {
             delete p;
             *err = "contexts of one plan must share the target orbital space (n_words, n_to)";
             return HB_ERR_INVALID_ARG;
         }
+        if (ctxs[i]->n_cls != ctxs[0]->n_cls || ctxs[i]->cls_labels_h != ctxs[0]->cls_labels_h) {
+            delete p;
+            *err = "contexts of one plan must share the orbital symmetry (orb_irrep of the target orbitals)";
+            return HB_ERR_INVALID_ARG;
+        }
+    }
     int rc = HB_OK;
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreate(&p->ev[i]);
@@ -578,7 +605,7 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
             else if (S != p->S) { rc = HB_ERR_INVALID_ARG; *err = "contexts of one plan use different split_slices"; }
         }
         if (rc != HB_OK) { plan_destroy(p); return rc; }
-        p->delta_col = (int)(ctxs[0]->Pt + (int64_t)ctxs[0]->n_to * ctxs[0]->n_to + 1);
+        p->delta_col = ctxs[0]->delta_pos;   // the delta label's column (class 0 comes first)
     }
     if (precision == HB_MIXED && p->S == 0) p->S = mixed_slices(ctxs[0]);
     // class 4 on the tensor cores: integral and CI slices, term-list sizes
@@ -614,7 +641,7 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
     }
     fill_tasks(*p);
     if (precision == HB_MIXED && p->coef_rows > 0) {
-        rc = split_coef_alloc(ctxs[0], p->S, p->coef_rows, p->Kpad, &p->coef, &p->tm_coef, err);
+        rc = split_coef_alloc(ctxs[0], p->S, p->coef_rows, p->Kw, &p->coef, &p->tm_coef, err);
         if (rc != HB_OK) { plan_destroy(p); return rc; }
         ensure_split_events(*p);
     }
@@ -720,7 +747,7 @@ int plan_autotune(Plan *p, cudaStream_t s, std::string *err) {
                     nb.push_back(blocks_split(cn, cnp, u.N, lg));
                 }
                 const float ms = time_tasks(p->ctxs[0], ts, nb, [&](const Grouped<SplitTask> &g) {
-                    g_split(pc, lg, &p->tm_coef, g, p->Kpad / 64, p->d_cols, p->err, s);
+                    g_split(pc, lg, &p->tm_coef, g, p->Kc / 64, p->Kw / 64, p->d_cols, p->err, s);
                 }, s);
                 if (best_lg < 0) { best = def_ms = ms; best_lg = lg; }
                 else if (ms < best && ms < kGain * def_ms) { best = ms; best_lg = lg; }
@@ -934,10 +961,11 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
         if (p->c4t.g.blocks > 0) cudaStreamWaitEvent(s, p->c4_done, 0);
         if (p->coef_rows > 0) {
             cudaMemsetAsync(p->err, 0, sizeof(int), s);
-            L += g_slice(p->slc.g, p->coef_rows, p->Kpad, p->S, p->delta_col, p->coef, s);
+            L += g_slice(p->slc.g, p->coef_rows, p->Kpad, p->Kw, p->perm, p->S, p->delta_col, p->coef, s);
             for (size_t i = 0; i < p->split.size(); ++i) {
                 rec(p->ev_split[2 * i]);
-                LX += g_split(p->split[i].panel_ctx, p->split[i].lg, &p->tm_coef, p->split[i].st.g, p->Kpad / 64, p->d_cols, p->err, s,
+                LX += g_split(p->split[i].panel_ctx, p->split[i].lg, &p->tm_coef, p->split[i].st.g, p->Kc / 64, p->Kw / 64,
+                              p->d_cols, p->err, s,
                               p->shard_r, p->shard_n);
                 rec(p->ev_split[2 * i + 1]);
             }

@@ -222,7 +222,8 @@ template <int S>
 __global__ void __launch_bounds__(NTHREADS, 1)
 split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_constant__ CUtensorMap tm_coef,
                     const SplitTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks, int n_tiles,
-                    int kblocks, const ExpCol *__restrict__ cols, int *err, int shard_r, int shard_n) {
+                    int kblocks, int coef_planes, const ExpCol *__restrict__ cols, int *err, int shard_r,
+                    int shard_n) {
     // this launch's tiles: shard_r, shard_r + shard_n, ... (all of them unless
     // sharded), numbered t = 0, 1, ... so that every role walks the same list
     const int n_local = n_tiles > shard_r ? (n_tiles - shard_r + shard_n - 1) / shard_n : 0;
@@ -274,6 +275,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
                 const TilePos p = tile_pos(tasks, blk, n_tasks, tile);
                 const int cx = tasks[p.ti].cfp + p.jjp0, cy = tasks[p.ti].cf + p.jj0;
                 const int crow = (int)(tasks[p.ti].coef_row0 + p.n0);
+                const int kc0 = tasks[p.ti].kc0;      // the block's label class in the coefficient slices
                 for (int kb = 0; kb < kblocks && ok; ++kb, ++G) {
                     for (int t = 0; t < S && ok; ++t) {
                         const int sl = (G & 1) ? slot_of<S>(1, t) : t;
@@ -284,7 +286,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
                         mbar_expect_tx(&full_bar[sl], (uint32_t)SLOT);
                         const int plane = t * kblocks + kb;
                         tma_load_4d(sA, &tm_panel, &full_bar[sl], 0, cx, cy, plane);
-                        tma_load_3d(sA + A_TILE, &tm_coef, &full_bar[sl], 0, crow, plane);
+                        tma_load_3d(sA + A_TILE, &tm_coef, &full_bar[sl], 0, crow, t * coef_planes + kc0 + kb);
                     }
                 }
             }
@@ -652,21 +654,34 @@ __device__ __forceinline__ void slice_row(const double *__restrict__ x, int64_t 
     }
 }
 
+// Panel rows (j n_co + j') into slices; column skip_col (the delta label) is
+// zeroed on the rows with j == j' (elsewhere that label is zero, or, with
+// orbital symmetry, the column holds another label).
 __global__ void slice_rows_kernel(const double *__restrict__ X, int64_t rows, int Kpad, int S, int skip_col,
-                                  __nv_bfloat16 *__restrict__ out) {
+                                  int n_co, __nv_bfloat16 *__restrict__ out) {
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= rows) return;
-    slice_row(X + row * Kpad, row, rows, Kpad, S, skip_col, out, threadIdx.x & 31);
+    const bool diag = row / n_co == row % n_co;
+    slice_row(X + row * Kpad, row, rows, Kpad, S, diag ? skip_col : -1, out, threadIdx.x & 31);
 }
 
+// Coefficient rows (Kin entries each) into slices of Kout columns: column k
+// holds label perm[k] (the labels class by class, with orbital symmetry; -1
+// padding), or label k without a permutation; column skip_col (the delta
+// label) is zero.
 __global__ void __launch_bounds__(256)
 slice_rows_grouped(const SliceTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks, int64_t R,
-                   int Kpad, int S, int skip_col, __nv_bfloat16 *__restrict__ out) {
+                   int Kin, int Kout, const int32_t *__restrict__ perm, int S, int skip_col,
+                   __nv_bfloat16 *__restrict__ out) {
     const int ti = task_of(blk, n_tasks, blockIdx.x);
     const SliceTask &T = tasks[ti];
     const int64_t row = blockIdx.x - blk[ti];
-    const double *x = T.X + row * Kpad;
-    slice_row_block([&](int k) -> double { return k == skip_col ? 0.0 : __ldg(x + k); }, T.row0 + row, R, Kpad, S, out);
+    const double *x = T.X + row * Kin;
+    slice_row_block([&](int k) -> double {
+        if (k == skip_col) return 0.0;
+        const int lab = perm ? __ldg(perm + k) : k;
+        return (lab >= 0 && lab < Kin) ? __ldg(x + lab) : 0.0;
+    }, T.row0 + row, R, Kout, S, out);
 }
 
 // Rows with j == j' (both ranges): H[(n,j),(n',j)] over all K, incl. delta,
@@ -692,9 +707,10 @@ diag_rows_kernel(const DRTask *__restrict__ tasks, const int64_t *__restrict__ b
     const int j0 = T.j_lo + (lb / T.ny) * kDRj, t0 = (lb % T.ny) * kDRt;
     const int tl = threadIdx.x % kDRt, jl = threadIdx.x / kDRt;
     const int j = j0 + jl, t = t0 + tl;
-    const int Kpad = T.Kpad, j_hi = T.j_hi, n_nn = T.n_nn;
+    const int Kpad = T.Kpad, Ka = T.Ka, j_hi = T.j_hi, n_nn = T.n_nn;
     const float2 *__restrict__ Pd = T.Pd;
     const float2 *__restrict__ A = T.A;
+    const int32_t *__restrict__ perm = T.perm;
     float2 rp[kDRper], ra[kDRper];
     auto fetch = [&](int k0) {
 #pragma unroll
@@ -703,7 +719,9 @@ diag_rows_kernel(const DRTask *__restrict__ tasks, const int64_t *__restrict__ b
             const int r = i / kDRk, k = k0 + i % kDRk;
             const bool kin = k < Kpad;
             rp[u] = (kin && j0 + r < j_hi) ? __ldg(Pd + (int64_t)(j0 + r) * Kpad + k) : make_float2(0.0f, 0.0f);
-            ra[u] = (kin && t0 + r < n_nn) ? __ldg(A + (int64_t)(t0 + r) * Kpad + k) : make_float2(0.0f, 0.0f);
+            const int lab = (kin && perm) ? __ldg(perm + k) : k;   // the label of panel column k
+            ra[u] = (kin && lab >= 0 && t0 + r < n_nn) ? __ldg(A + (int64_t)(t0 + r) * Ka + lab)
+                                                        : make_float2(0.0f, 0.0f);
         }
     };
     float h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, l[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -828,18 +846,20 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
     if (!encode_fn()) return mixed_fail(ctx, HB_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     const int64_t rows = (int64_t)ctx->n_co * ctx->n_co;
     M.panel_rows = rows;
-    cudaError_t e = dmalloc(ctx, (void **)&M.panel_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * rows * ctx->Kpad);
+    // the panel's columns: every label, or with orbital symmetry the Kc labels
+    // of each row's class
+    const int Kc = ctx->Kc;
+    cudaError_t e = dmalloc(ctx, (void **)&M.panel_slices, sizeof(__nv_bfloat16) * (size_t)M.slices * rows * Kc);
     if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("panel slices: ") + cudaGetErrorString(e));
-    ctx->dev_bytes += sizeof(__nv_bfloat16) * (size_t)M.slices * rows * ctx->Kpad;
-    e = dmalloc_n(ctx, &M.pdiag, (size_t)ctx->n_co * ctx->Kpad);
+    ctx->dev_bytes += sizeof(__nv_bfloat16) * (size_t)M.slices * rows * Kc;
+    e = dmalloc_n(ctx, &M.pdiag, (size_t)ctx->n_co * Kc);
     if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_OOM, std::string("panel rows: ") + cudaGetErrorString(e));
-    ctx->dev_bytes += sizeof(float2) * (size_t)ctx->n_co * ctx->Kpad;
-    panel_diag_df_kernel<<<ctx->n_co, 256, 0, s>>>(ctx->panel, ctx->n_co, ctx->Kpad, M.pdiag);
-    const int delta_col = (int)(ctx->Pt + (int64_t)ctx->n_to * ctx->n_to + 1);
-    slice_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(ctx->panel, rows, ctx->Kpad, M.slices, delta_col,
-                                                                 M.panel_slices);
+    ctx->dev_bytes += sizeof(float2) * (size_t)ctx->n_co * Kc;
+    panel_diag_df_kernel<<<ctx->n_co, 256, 0, s>>>(ctx->panel, ctx->n_co, Kc, M.pdiag);
+    slice_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(ctx->panel, rows, Kc, M.slices, ctx->delta_pos,
+                                                                 ctx->n_co, M.panel_slices);
     // 4D map over the panel slices [S*KB][j][j'][64]: coordinates (kk, j', j, plane)
-    const int KB = ctx->Kpad / BKB;
+    const int KB = Kc / BKB;
     cuuint64_t dims[4] = {(cuuint64_t)BKB, (cuuint64_t)ctx->n_co, (cuuint64_t)ctx->n_co,
                           (cuuint64_t)M.slices * KB};
     cuuint64_t strides[3] = {(cuuint64_t)BKB * 2, (cuuint64_t)ctx->n_co * BKB * 2, (cuuint64_t)rows * BKB * 2};
@@ -908,15 +928,16 @@ int split_tile_heuristic(int cn, int cnp) {
     return best;
 }
 
-int g_slice(const Grouped<SliceTask> &g, int64_t R, int Kpad, int S, int skip_col, void *out, cudaStream_t s) {
+int g_slice(const Grouped<SliceTask> &g, int64_t R, int Kin, int Kout, const int32_t *perm, int S, int skip_col,
+            void *out, cudaStream_t s) {
     if (g.blocks <= 0) return 0;
-    slice_rows_grouped<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n, R, Kpad, S, skip_col,
+    slice_rows_grouped<<<(unsigned)g.blocks, 256, 0, s>>>(g.tasks, g.blk, g.n, R, Kin, Kout, perm, S, skip_col,
                                                           (__nv_bfloat16 *)out);
     return 1;
 }
 
 int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const Grouped<SplitTask> &g, int kblocks,
-            const ExpCol *cols, int *err, cudaStream_t s, int shard_r, int shard_n) {
+            int coef_planes, const ExpCol *cols, int *err, cudaStream_t s, int shard_r, int shard_n) {
     if (g.blocks <= 0) return 0;
     const MixedState &M = *panel_ctx->mixed;
     const CUtensorMap &tm_panel = M.tm_panel[lg - 3];
@@ -928,7 +949,7 @@ int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const G
     const unsigned grid = (unsigned)std::min(n_local, sm_count());
 #define HB_SPLIT(SS) \
     split_expand_kernel<SS><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, n_tiles, kblocks, \
-                                                        cols, err, shard_r, shard_n)
+                                                        coef_planes, cols, err, shard_r, shard_n)
     switch (M.slices) {
         case 2: HB_SPLIT(2); break;
         case 3: HB_SPLIT(3); break;

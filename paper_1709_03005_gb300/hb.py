@@ -33,7 +33,7 @@ class hb_problem(C.Structure):
                 ("cont_spin", C.c_int32), ("h", C.c_void_p), ("eri_tttt", C.c_void_p),
                 ("eri_tttc", C.c_void_p), ("eri_ttcc", C.c_void_p), ("eri_tctc", C.c_void_p),
                 ("n_groups", C.c_int32), ("groups", C.c_void_p), ("n_l2", C.c_int32),
-                ("l2_dets", C.c_void_p), ("e_core", C.c_double)]
+                ("l2_dets", C.c_void_p), ("e_core", C.c_double), ("orb_irrep", C.c_void_p)]
 
 
 class hb_options(C.Structure):
@@ -169,7 +169,8 @@ def _marshal_problem(p, keep):
                       ptr(arr(p.h, np.float64)), ptr(arr(p.eri_tttt, np.float64)),
                       ptr(arr(p.eri_tttc, np.float64)), ptr(arr(p.eri_ttcc, np.float64)),
                       ptr(arr(p.eri_tctc, np.float64)), len(p.groups), C.addressof(gs),
-                      p.l2_dets.shape[0], ptr(l2) if l2 is not None else None, float(p.e_core))
+                      p.l2_dets.shape[0], ptr(l2) if l2 is not None else None, float(p.e_core),
+                      ptr(arr(p.orb_irrep, np.int32)) if getattr(p, "orb_irrep", None) is not None else None)
     keep.append(gs)
     return prob, gs
 

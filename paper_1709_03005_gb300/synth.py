@@ -75,6 +75,7 @@ class Problem:
     e_core: float = 0.0
     chol: np.ndarray | None = None   # packed-pair Cholesky factor (small problems)
     meta: dict = field(default_factory=dict)
+    orb_irrep: np.ndarray | None = None   # spatial symmetry of every orbital (0..7, product XOR), or None
 
     @property
     def n_orb(self) -> int:
@@ -387,7 +388,7 @@ def _irrep_of(occ_a, occ_b, orb_irrep):
     return x
 
 
-def make_batched_family(seed=4, n_hams=16, n_to=40, cont_per_irrep=(50, 150), n_elec=8, rank=32,
+def make_batched_family(seed=4, n_hams=16, n_to=40, cont_per_irrep=(50, 400), n_elec=8, rank=32,
                         dim_range=(500, 20000), max_det=600, max_states=16):
     """16 Hamiltonians of one D2h-like molecule: total symmetry Gamma in 0..7
     times two spin couplings (Ms = 0 targets + alpha continuum electron, and
@@ -474,7 +475,7 @@ def make_batched_family(seed=4, n_hams=16, n_to=40, cont_per_irrep=(50, 150), n_
                                 cont_spin=spin, h=h, eri_tttt=eri[0], eri_tttc=eri[1], eri_ttcc=eri[2],
                                 eri_tctc=eri[3], groups=groups, l2_dets=np.ascontiguousarray(l2),
                                 meta=dict(seed=seed, gamma=gam, spin=spin, target_dim=target,
-                                          orb_irrep=orb_irrep)))
+                                          orb_irrep=orb_irrep), orb_irrep=orb_irrep))
     return problems
 
 

@@ -84,7 +84,7 @@ def test_invalid_shape_options_rejected():
 
 def test_batch_reports_its_choices():
     from paper_1709_03005_gb300 import hb
-    fam = synth.make_batched_family()
+    fam = synth.make_batched_family(cont_per_irrep=(20, 60))
     members = [fam[i] for i in np.argsort([P.dim for P in fam])[:3]]
     B = hb.Batch(members, hb.HB_MIXED)
     rep = B.report()
