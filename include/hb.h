@@ -157,7 +157,7 @@ typedef struct {
     int32_t mlp_stall_log2;   /* 0 = 1, i.e. halved (1..60) */
     int32_t diag_basis;       /* hb_diag: the basis holds at most diag_basis blocks of b vectors
                                  (b = k + min(16, max(4, k / 2))) before a thick restart to 2b;
-                                 0 = 5 (3..10) */
+                                 0 = 6 (3..10) */
     int32_t reserved[6];
 } hb_options;
 
