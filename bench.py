@@ -537,7 +537,8 @@ def run_ours(args, rank, world, local_rank):
     batched = None
     if args.batched:
         try:
-            fam = synth.make_batched_family()
+            lo, hi = (int(x) for x in args.batched_cont.split(","))
+            fam = synth.make_batched_family(cont_per_irrep=(lo, hi))
             res = {}
             for name, prec in (("mixed", hb.HB_MIXED), ("fp64", hb.HB_FP64)):
                 B = hb.Batch(fam, prec)
@@ -611,6 +612,8 @@ def main():
     ap.add_argument("--no-l2-heavy", dest="l2_heavy", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--batched-cont", default="50,400", metavar="LO,HI",
+                    help="continuum orbitals per irrep of the batched workload (smaller for profiling)")
     ap.add_argument("--sharded", action="store_true",
                     help="also time the sharded build (contraction share, all-reduce, expansion share per rank)")
     args = ap.parse_args()
