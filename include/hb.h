@@ -158,7 +158,10 @@ typedef struct {
     int32_t diag_basis;       /* hb_diag: the basis holds at most diag_basis blocks of b vectors
                                  (b = k + min(16, max(4, k / 2))) before a thick restart to 2b;
                                  0 = 6 (3..10) */
-    int32_t reserved[6];
+    int32_t split_cols;       /* 0 = chosen per merged block from its columns (state pairs n, n'):
+                                 32 up to 32, 64 up to 64, else 128; 32, 64, 128 force that width of
+                                 the tensor-core tiles (results are bit-identical for every width) */
+    int32_t reserved[5];
 } hb_options;
 
 typedef struct {

@@ -108,6 +108,7 @@ struct hb_ctx {
     int split_slices = 5;
     int autotune = 0;
     int force_tile = 0, force_c4_states = 0, force_c4_threads = 0;   // 0: chosen by the plan
+    int force_cols = 0;      // tensor-core expansion tile width (32, 64, 128); 0: chosen by the plan
     int diag_basis = 6;      // Davidson basis limit, in blocks of b vectors
     int stall_iters = 10;    // learned-factor stall check: window and required fall (2^stall_log2)
     int stall_log2 = 1;

@@ -15,21 +15,25 @@ const void *mixed_panel_key(const hb_ctx *ctx);
 int mixed_slices(const hb_ctx *ctx);
 // Diagonal panel rows (j, j) as float pairs [n_co][Kpad].
 const float2 *mixed_panel_diag(const hb_ctx *ctx);
-// Coefficient slices [S][Kpad/64][rows][64] bf16 and their tensor map.
+// Coefficient slices [S][Kpad/64][rows][64] bf16 and their tensor maps
+// tm[0..2], one per tile width 32, 64, 128.
 int split_coef_alloc(hb_ctx *mem, int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err);
-int64_t blocks_split(int cn, int cnp, int N, int lg);
-int split_ntn(int N);
+int64_t blocks_split(int cn, int cnp, int N, int lg, int bn);
+int split_ntn(int N, int bn);
+// tile width (32, 64, 128) for a merged block of N columns; force: 0 or a width
+int split_cols_choice(int N, int force);
 int split_jpt(int cnp, int lg);
 int split_tile_heuristic(int cn, int cnp);
 // coefficient rows of Kin labels into slices of Kout columns, column k being
 // label perm[k] (null: label k)
 int g_slice(const hb::Grouped<hb::SliceTask> &g, int64_t R, int Kin, int Kout, const int32_t *perm, int S,
             int skip_col, void *out, cudaStream_t s);
-// lg: tile arrangement (3..5, see SplitTask); every task of g must use it.
+// lg: tile arrangement (3..5, see SplitTask) and bn: tile width (32, 64,
+// 128); every task of g must use both.  tm_coef: the three coefficient maps.
 // kblocks: 64-wide K blocks of the panel rows; coef_planes: K blocks per
 // slice of the coefficient slices (the task's kc0 selects its label class)
 // shard_r, shard_n: the launch takes tiles shard_r, shard_r + shard_n, ... only
-int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const hb::Grouped<hb::SplitTask> &g,
+int g_split(const hb_ctx *panel_ctx, int lg, int bn, const CUtensorMap *tm_coef, const hb::Grouped<hb::SplitTask> &g,
             int kblocks, int coef_planes, const hb::ExpCol *cols, int *err, cudaStream_t s, int shard_r = 0,
             int shard_n = 1);
 int64_t blocks_diag_rows(int j_lo, int j_hi, int n_nn);

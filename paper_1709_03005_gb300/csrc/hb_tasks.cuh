@@ -165,6 +165,7 @@ struct SplitTask {      // one merged block on the tensor cores
     int cf, cn, cfp, cnp;     // the continuum rectangle (same for every column)
     int jpt_tiles, ntn, N;    // tiles along j', tiles along the columns, columns
     int bjp_log2;             // tile of (128 >> bjp_log2) j x (1 << bjp_log2) j' continuum pairs (3..5)
+    int bn;                   // columns per tile (32, 64, 128): the launch's tile width
     int kc0;                  // first 64-wide K block of the block's label class in the coefficient slices
     int64_t coef_row0;        // first row of the block in the coefficient slices
     int64_t col0;             // first column in the ExpCol table

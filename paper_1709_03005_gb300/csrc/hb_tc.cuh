@@ -64,6 +64,16 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     return d;
 }
 
+// K-major operand, 64-byte swizzle: rows of 64 B, 8-row atoms of 512 B.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)((512 >> 4) & 0x3FFF) << 32;      // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
+    d |= (uint64_t)4 << 61;                          // layout: 64-byte swizzle
+    return d;
+}
+
 // kind::f16 instruction descriptor: bf16 x bf16 -> f32, K-major A and B.
 __host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
     return (1u << 4)                    // D format f32

@@ -54,6 +54,7 @@ static int class_label_count(const hb_ctx *ctx, int cf, int cfp) {
 struct SplitGroup {
     const hb_ctx *panel_ctx = nullptr;
     int lg = 4;                        // tile arrangement of every task of the launch
+    int bn = 128;                      // tile width (columns) of every task of the launch
     Stage<SplitTask> st;
 };
 
@@ -132,7 +133,7 @@ struct Plan {
     bool upload_pending = false;
     // tensor-core operands
     void *coef = nullptr;
-    CUtensorMap tm_coef;
+    CUtensorMap tm_coef[3];            // coefficient slices, one map per tile width 32, 64, 128
     int64_t coef_rows = 0;
     int *err = nullptr;
     // classes 4, 2 and 8 run on a second stream beside the target side and
@@ -439,26 +440,30 @@ void fill_tasks(Plan &p) {
             auto tc = p.choice.tile.find({k.cn, k.cnp});
             if (tc != p.choice.tile.end()) lg = tc->second;
             if (B.ctx->force_tile) lg = B.ctx->force_tile;
+            const int bn = split_cols_choice(N, B.ctx->force_cols);
             const void *pkey = mixed_panel_key(B.ctx);
             int gi = -1;
             for (size_t i = 0; i < p.split.size(); ++i)
-                if (mixed_panel_key(p.split[i].panel_ctx) == pkey && p.split[i].lg == lg) gi = (int)i;
+                if (mixed_panel_key(p.split[i].panel_ctx) == pkey && p.split[i].lg == lg && p.split[i].bn == bn)
+                    gi = (int)i;
             if (gi < 0) {
                 p.split.emplace_back();
                 p.split.back().panel_ctx = B.ctx;
                 p.split.back().lg = lg;
+                p.split.back().bn = bn;
                 gi = (int)p.split.size() - 1;
             }
             SplitTask t;
             t.cf = k.cf; t.cn = k.cn; t.cfp = k.cfp; t.cnp = k.cnp;
             t.bjp_log2 = lg;
             t.jpt_tiles = split_jpt(k.cnp, lg);
-            t.ntn = split_ntn(N);
+            t.bn = bn;
+            t.ntn = split_ntn(N, bn);
             t.N = N;
             t.coef_row0 = coef_row;
             t.col0 = col0;
             t.kc0 = B.ctx->class_of(k.cf, k.cfp) * (p.Kc / 64);
-            p.split[gi].st.add(t, blocks_split(k.cn, k.cnp, N, lg));
+            p.split[gi].st.add(t, blocks_split(k.cn, k.cnp, N, lg, bn));
             p.tune_split.push_back(TuneSplit{B.ctx, t});
             coef_row += N;
         } else {
@@ -641,7 +646,7 @@ int plan_create(hb_ctx *const *ctxs, int n, const hb_blocks *outs, int precision
     }
     fill_tasks(*p);
     if (precision == HB_MIXED && p->coef_rows > 0) {
-        rc = split_coef_alloc(ctxs[0], p->S, p->coef_rows, p->Kw, &p->coef, &p->tm_coef, err);
+        rc = split_coef_alloc(ctxs[0], p->S, p->coef_rows, p->Kw, &p->coef, p->tm_coef, err);
         if (rc != HB_OK) { plan_destroy(p); return rc; }
         ensure_split_events(*p);
     }
@@ -737,18 +742,24 @@ int plan_autotune(Plan *p, cudaStream_t s, std::string *err) {
             int best_lg = -1;
             for (int lg : {def_lg, 3, 4, 5}) {
                 if (best_lg >= 0 && lg == def_lg) continue;
-                std::vector<SplitTask> ts;
-                std::vector<int64_t> nb;
-                for (auto *t : kv.second) {
-                    SplitTask u = t->t;
-                    u.bjp_log2 = lg;
-                    u.jpt_tiles = split_jpt(cnp, lg);
-                    ts.push_back(u);
-                    nb.push_back(blocks_split(cn, cnp, u.N, lg));
+                // the rectangle's blocks, one launch per tile width as in the build
+                float ms = 0.0f;
+                for (int bn : {32, 64, 128}) {
+                    std::vector<SplitTask> ts;
+                    std::vector<int64_t> nb;
+                    for (auto *t : kv.second) {
+                        if (t->t.bn != bn) continue;
+                        SplitTask u = t->t;
+                        u.bjp_log2 = lg;
+                        u.jpt_tiles = split_jpt(cnp, lg);
+                        ts.push_back(u);
+                        nb.push_back(blocks_split(cn, cnp, u.N, lg, bn));
+                    }
+                    if (ts.empty()) continue;
+                    ms += time_tasks(p->ctxs[0], ts, nb, [&](const Grouped<SplitTask> &g) {
+                        g_split(pc, lg, bn, p->tm_coef, g, p->Kc / 64, p->Kw / 64, p->d_cols, p->err, s);
+                    }, s);
                 }
-                const float ms = time_tasks(p->ctxs[0], ts, nb, [&](const Grouped<SplitTask> &g) {
-                    g_split(pc, lg, &p->tm_coef, g, p->Kc / 64, p->Kw / 64, p->d_cols, p->err, s);
-                }, s);
                 if (best_lg < 0) { best = def_ms = ms; best_lg = lg; }
                 else if (ms < best && ms < kGain * def_ms) { best = ms; best_lg = lg; }
             }
@@ -964,7 +975,7 @@ int plan_run(Plan *p, cudaStream_t s, bool timing, bool capture, int *launches, 
             L += g_slice(p->slc.g, p->coef_rows, p->Kpad, p->Kw, p->perm, p->S, p->delta_col, p->coef, s);
             for (size_t i = 0; i < p->split.size(); ++i) {
                 rec(p->ev_split[2 * i]);
-                LX += g_split(p->split[i].panel_ctx, p->split[i].lg, &p->tm_coef, p->split[i].st.g, p->Kc / 64, p->Kw / 64,
+                LX += g_split(p->split[i].panel_ctx, p->split[i].lg, p->split[i].bn, p->tm_coef, p->split[i].st.g, p->Kc / 64, p->Kw / 64,
                               p->d_cols, p->err, s,
                               p->shard_r, p->shard_n);
                 rec(p->ev_split[2 * i + 1]);

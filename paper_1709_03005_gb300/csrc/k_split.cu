@@ -21,10 +21,12 @@
 // (TwoSum for s <= 2), and at the end write it as FP64.  Pairs with i + l >= S are dropped (below 2^-7S relative).
 //
 // Kernel structure (one CTA per 128 x 128 output tile, 10 warps):
-//   warp 0  TMA producer: per 64-wide K block and slice, one panel tile
-//           (128 x 64) and one coefficient tile (128 x 64), 128-byte swizzle,
+//   warp 0  TMA producer: per 32-wide K stage and slice, one panel tile
+//           (128 x 32) and one coefficient tile (128 x 32), 64-byte swizzle,
 //           each slice in its own shared-memory slot with full/empty mbarriers
-//           so the MMAs start as slices land and slots refill as they free
+//           so the MMAs start as slices land and slots refill as they free;
+//           two full sets of slots (six slices), so a stage loads while the
+//           one before it is multiplied
 //   warp 1  MMA issuer (one elected thread), TMEM allocation owner
 //   warps 2-9 epilogue: TMEM -> registers, double-float accumulation, FP64 out
 //           (two warps per TMEM lane quadrant, 64 columns each)
@@ -75,6 +77,26 @@ constexpr int EPI_WARPS = 8;                 // 2 per TMEM lane quadrant
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int EPI_COLS = BN / 2;             // columns per epilogue thread
 constexpr int NTHREADS = 64 + EPI_THREADS;
+
+// The expansion kernel's K pipeline: stages of 32 K (64-byte operand rows,
+// 64-byte swizzle), and as many full sets of S slots as fit 192 KB, so the
+// copies of the next stages are in flight while the stages before them are
+// multiplied.  Its tile is 128 continuum pairs x TBN columns (state pairs),
+// TBN = 32, 64 or 128 chosen per merged block from its column count; with
+// TBN <= 64 the four accumulators are double-buffered in tensor memory, so the
+// MMAs of the next chunk run while the epilogue drains the last one.
+constexpr int XBK = 32;
+constexpr int XA_TILE = BM * XBK * 2;        // 8 KB
+constexpr int XBUDGET = 192 * 1024;          // shared memory of the slots
+constexpr int XBARS = 24;                    // full and empty barriers: slots at most
+constexpr int XSTAGES_PER_CHUNK = KCHUNK / XBK;
+// one slice of one stage: panel tile, then coefficient tile (multiples of 1 KB)
+__host__ __device__ constexpr int xslot(int tbn) { return XA_TILE + tbn * XBK * 2; }
+__host__ __device__ constexpr int xsets(int S, int tbn) {
+    return XBUDGET / (S * xslot(tbn)) < 4 ? XBUDGET / (S * xslot(tbn)) : 4;
+}
+__host__ __device__ constexpr int xacc_bufs(int tbn) { return 8 * tbn <= 512 ? 2 : 1; }
+__host__ __device__ constexpr int xtmem_cols(int tbn) { return xacc_bufs(tbn) * 4 * tbn; }
 
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *tm, uint64_t *bar, int c0, int c1, int c2,
                                             int c3) {
@@ -158,15 +180,55 @@ __device__ __forceinline__ bool mma_block(uint64_t *full_bar, uint64_t *empty_ba
     return true;
 }
 
-// Fold one chunk's accumulators (EPI_COLS columns of this thread's TMEM lane,
+// One K stage of the expansion kernel from slot set `set` (slots set*S ..
+// set*S + S-1, slice t in slot set*S + t), accumulators at TMEM column tacc:
+// for each arriving slice t the pairs (i, l) with max(i, l) = t and i + l < S,
+// then the commits that free the slots read for the last time.
+template <int S, int TBN>
+__device__ __forceinline__ bool mma_stage(uint64_t *full_bar, uint64_t *empty_bar, int set, uint32_t par,
+                                          uint32_t tacc, uint64_t desc0, uint32_t idesc, uint32_t &fresh, int *err) {
+    constexpr int XS = xslot(TBN);
+    const int sb = set * S;
+    const uint64_t dset = desc0 + (uint64_t)((uint32_t)(sb * XS) >> 4);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        if (!mbar_wait(&full_bar[sb + t], par, err, 4)) return false;
+        tc_fence_after();
+#pragma unroll
+        for (int i = 0; i <= t; ++i) {
+#pragma unroll
+            for (int l = 0; l <= t; ++l) {
+                if ((i == t || l == t) && i + l < S) {
+                    const int s = i + l < 3 ? i + l : 3;
+                    const uint32_t offA = (uint32_t)(i * XS);
+                    const uint32_t offB = (uint32_t)(l * XS + XA_TILE);
+#pragma unroll
+                    for (int k = 0; k < XBK / 16; ++k) {
+                        const uint32_t acc = (fresh >> s) & 1u ? 0u : 1u;
+                        mma_bf16(tacc + s * TBN, dset + ((offA + k * 32) >> 4), dset + ((offB + k * 32) >> 4), idesc,
+                                 acc);
+                        fresh &= ~(1u << s);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+            if (release_step<S>(i) == t) mma_commit(&empty_bar[sb + i]);
+    }
+    return true;
+}
+
+// Fold one chunk's accumulators (NC columns of this thread's TMEM lane,
 // accumulator s at column offset s * stride) into the double-float sums:
 // s = 0, 1, 2 by TwoSum (2^-14 of the result for s = 2 still needs it to keep
 // the low word below an ulp of the high one), s >= 3 (2^-21) into the low word.
-template <int S>
-__device__ __forceinline__ void drain_chunk(uint32_t tbase, int stride, float (&hi)[EPI_COLS], float (&lo)[EPI_COLS]) {
+template <int S, int NC>
+__device__ __forceinline__ void drain_chunk(uint32_t tbase, int stride, float (&hi)[NC], float (&lo)[NC]) {
     constexpr int n_acc = S < 4 ? S : 4;       // accumulators written by the MMAs
+    static_assert(NC % 16 == 0, "columns are loaded 16 at a time");
 #pragma unroll
-    for (int c0 = 0; c0 < EPI_COLS; c0 += 16) {
+    for (int c0 = 0; c0 < NC; c0 += 16) {
         // two accumulators' 16 columns in flight together, one wait each pair
         uint32_t v[16], w[16];
         tmem_ld16_async(tbase + c0, v);
@@ -200,6 +262,7 @@ struct TilePos {
     int ti, jj0, jjp0, n0;
 };
 
+template <int TBN>
 __device__ __forceinline__ TilePos tile_pos(const SplitTask *__restrict__ tasks, const int64_t *__restrict__ blk,
                                             int n_tasks, int tile) {
     TilePos p;
@@ -210,7 +273,7 @@ __device__ __forceinline__ TilePos tile_pos(const SplitTask *__restrict__ tasks,
     const int tile_n = lb % ntn, tile_m = lb / ntn;   // N fastest: CTAs sharing a panel tile run together
     p.jj0 = (tile_m / jpt_tiles) * (BM >> lg);        // tile of (128 >> lg) j x (1 << lg) j'
     p.jjp0 = (tile_m % jpt_tiles) << lg;
-    p.n0 = tile_n * BN;
+    p.n0 = tile_n * TBN;
     return p;
 }
 
@@ -218,7 +281,7 @@ __device__ __forceinline__ TilePos tile_pos(const SplitTask *__restrict__ tasks,
 // The slot ring, the accumulator hand-over and their barrier phases run on
 // across tiles, so the loads and MMAs of the next tile start while the
 // epilogue warps still write the last one out from registers.
-template <int S>
+template <int S, int TBN>
 __global__ void __launch_bounds__(NTHREADS, 1)
 split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_constant__ CUtensorMap tm_coef,
                     const SplitTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks, int n_tiles,
@@ -227,36 +290,41 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     // this launch's tiles: shard_r, shard_r + shard_n, ... (all of them unless
     // sharded), numbered t = 0, 1, ... so that every role walks the same list
     const int n_local = n_tiles > shard_r ? (n_tiles - shard_r + shard_n - 1) / shard_n : 0;
+    constexpr int XS = xslot(TBN);
+    constexpr int NSET = xsets(S, TBN);
+    constexpr int NACC = xacc_bufs(TBN);      // accumulator sets in tensor memory
+    constexpr int TCOLS = xtmem_cols(TBN);
+    constexpr int ECOLS = TBN / 2;            // columns per epilogue thread
+    static_assert(NSET >= 2 && NSET * S <= XBARS, "slot sets");
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *slots = base;                                  // [S][SLOT]
-    uint64_t *full_bar = (uint64_t *)(base + S * SLOT);    // [MAXS]
-    uint64_t *empty_bar = full_bar + MAXS;                  // [MAXS]
-    uint64_t *acc_full = empty_bar + MAXS;                  // [1]
-    uint64_t *acc_empty = acc_full + 1;                     // [1]
-    uint64_t *final_bar = acc_empty + 1;                    // [1]
+    uint8_t *slots = base;                                         // [NSET][S][XS]
+    uint64_t *full_bar = (uint64_t *)(base + NSET * S * XS);      // [XBARS]
+    uint64_t *empty_bar = full_bar + XBARS;                        // [XBARS]
+    uint64_t *acc_full = empty_bar + XBARS;                        // [2]
+    uint64_t *acc_empty = acc_full + 2;                            // [2]
+    uint64_t *final_bar = acc_empty + 2;                           // [1]
     uint32_t *tmem_slot = (uint32_t *)(final_bar + 1);
     // the epilogue's tile: arguments and column destinations, double-buffered
     __shared__ SplitTask ta[2];
     __shared__ TilePos tp[2];
-    __shared__ ExpCol colmeta[2][BN];
+    __shared__ ExpCol colmeta[2][TBN];
     __shared__ int epi_fail;                 // an epilogue wait gave up (read only after a barrier)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int kb_per_chunk = KCHUNK / BKB;
-    const int nchunks = (kblocks + kb_per_chunk - 1) / kb_per_chunk;
+    const int nst = 2 * kblocks;             // K stages of 32 per tile
+    const int nchunks = (nst + XSTAGES_PER_CHUNK - 1) / XSTAGES_PER_CHUNK;
 
     if (threadIdx.x == 0) {
         epi_fail = 0;
-        for (int i = 0; i < MAXS; ++i) { mbar_init(&full_bar[i], 1); mbar_init(&empty_bar[i], 1); }
-        mbar_init(acc_full, 1);
-        mbar_init(acc_empty, EPI_THREADS);
+        for (int i = 0; i < XBARS; ++i) { mbar_init(&full_bar[i], 1); mbar_init(&empty_bar[i], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], EPI_THREADS); }
         mbar_init(final_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
+                     "r"(TCOLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -268,51 +336,55 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
         if (lane == 0) {
-            int G = 0;                            // K blocks issued by this CTA over all its tiles
+            int G = 0;                            // K stages issued by this CTA over all its tiles
             bool ok = true;
             for (int t = blockIdx.x; t < n_local && ok; t += gridDim.x) {
                 const int tile = shard_r + shard_n * t;
-                const TilePos p = tile_pos(tasks, blk, n_tasks, tile);
+                const TilePos p = tile_pos<TBN>(tasks, blk, n_tasks, tile);
                 const int cx = tasks[p.ti].cfp + p.jjp0, cy = tasks[p.ti].cf + p.jj0;
                 const int crow = (int)(tasks[p.ti].coef_row0 + p.n0);
                 const int kc0 = tasks[p.ti].kc0;      // the block's label class in the coefficient slices
-                for (int kb = 0; kb < kblocks && ok; ++kb, ++G) {
+                for (int ks = 0; ks < nst && ok; ++ks, ++G) {
+                    // stage G uses slot set G mod NSET for the (G / NSET)-th time
+                    const int sb = (G % NSET) * S, round = G / NSET;
+                    const int kx = (ks & 1) * XBK, kb = ks >> 1;   // half of 64-wide K block kb
                     for (int t = 0; t < S && ok; ++t) {
-                        const int sl = (G & 1) ? slot_of<S>(1, t) : t;
-                        // each slot is filled once per K block: wait for its release in block G-1
-                        if (G > 0) ok = mbar_wait(&empty_bar[sl], (G - 1) & 1, err, 1);
+                        const int sl = sb + t;
+                        // wait for the slot's release by the stage NSET before this one
+                        if (round > 0) ok = mbar_wait(&empty_bar[sl], (round - 1) & 1, err, 1);
                         if (!ok) break;
-                        uint8_t *sA = slots + sl * SLOT;
-                        mbar_expect_tx(&full_bar[sl], (uint32_t)SLOT);
-                        const int plane = t * kblocks + kb;
-                        tma_load_4d(sA, &tm_panel, &full_bar[sl], 0, cx, cy, plane);
-                        tma_load_3d(sA + A_TILE, &tm_coef, &full_bar[sl], 0, crow, t * coef_planes + kc0 + kb);
+                        uint8_t *sA = slots + sl * XS;
+                        mbar_expect_tx(&full_bar[sl], (uint32_t)XS);
+                        tma_load_4d(sA, &tm_panel, &full_bar[sl], kx, cx, cy, t * kblocks + kb);
+                        tma_load_3d(sA + XA_TILE, &tm_coef, &full_bar[sl], kx, crow, t * coef_planes + kc0 + kb);
                     }
                 }
             }
-            // wait until this producer's copies of the last block have landed
-            if (G > 0)
-                for (int sl = 0; sl < S; ++sl) mbar_wait(&full_bar[sl], (G - 1) & 1, err, 2);
+            // wait until this producer's copies of the last stage of every set have landed
+            for (int g = G > NSET ? G - NSET : 0; g < G; ++g)
+                for (int t = 0; t < S; ++t) mbar_wait(&full_bar[(g % NSET) * S + t], (g / NSET) & 1, err, 2);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = instr_desc_bf16(BM, BN);
-            const uint64_t desc0 = smem_desc_sw128(smem_u32(slots));   // + (offset >> 4) per operand tile
+            const uint32_t idesc = instr_desc_bf16(BM, TBN);
+            const uint64_t desc0 = smem_desc_sw64(smem_u32(slots));    // + (offset >> 4) per operand tile
             bool ok = true;
-            int G = 0, C = 0;                     // K blocks and chunks over all tiles
+            int G = 0, C = 0;                     // K stages and chunks over all tiles
             for (int t = blockIdx.x; t < n_local && ok; t += gridDim.x) {
                 for (int c = 0; c < nchunks && ok; ++c, ++C) {
-                    if (C > 0) ok = mbar_wait(acc_empty, (C - 1) & 1, err, 3);
+                    // chunk C fills accumulator set C mod NACC, drained after chunk C - NACC
+                    const int b = C % NACC;
+                    if (C >= NACC) ok = mbar_wait(&acc_empty[b], (C / NACC - 1) & 1, err, 3);
                     if (!ok) break;
                     tc_fence_after();
-                    const int kb_end = min(kblocks, (c + 1) * kb_per_chunk);
+                    const uint32_t tacc = tmem + (uint32_t)(b * 4 * TBN);
+                    const int ks_end = min(nst, (c + 1) * XSTAGES_PER_CHUNK);
                     uint32_t fresh = 0xFu;        // accumulators not yet written in this chunk
-                    for (int kb = c * kb_per_chunk; kb < kb_end && ok; ++kb, ++G) {
-                        if (G & 1) ok = mma_block<S, 1>(full_bar, empty_bar, 1u, tmem, desc0, idesc, fresh, err);
-                        else ok = mma_block<S, 0>(full_bar, empty_bar, 0u, tmem, desc0, idesc, fresh, err);
-                    }
-                    if (ok) mma_commit(acc_full);         // accumulators of chunk C complete
+                    for (int ks = c * XSTAGES_PER_CHUNK; ks < ks_end && ok; ++ks, ++G)
+                        ok = mma_stage<S, TBN>(full_bar, empty_bar, G % NSET, (uint32_t)((G / NSET) & 1), tacc,
+                                               desc0, idesc, fresh, err);
+                    if (ok) mma_commit(&acc_full[b]);     // accumulators of chunk C complete
                 }
             }
             mma_commit(final_bar);
@@ -323,7 +395,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
         const int e = threadIdx.x - 64;          // 0 .. EPI_THREADS-1
         const int ew = warp - 2;
         const int q = warp & 3;                  // TMEM lane quadrant this warp may access
-        const int col0 = (ew >> 2) * EPI_COLS;
+        const int col0 = (ew >> 2) * ECOLS;
         const int row = q * 32 + lane;           // tile row = TMEM lane
         int C = 0, it = 0;
         for (int t = blockIdx.x; t < n_local; t += gridDim.x, ++it) {
@@ -332,7 +404,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
             // the buffer was last read by the stores of tile it-2, which every
             // epilogue warp finished before the barriers of tile it-1
             if (e == 0) {
-                tp[buf] = tile_pos(tasks, blk, n_tasks, tile);
+                tp[buf] = tile_pos<TBN>(tasks, blk, n_tasks, tile);
                 ta[buf] = tasks[tp[buf].ti];
             }
             // every epilogue thread reaches both barriers of a tile, so the
@@ -340,7 +412,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
             named_bar_sync(1, EPI_THREADS);
             if (epi_fail) break;
             const SplitTask &a = ta[buf];
-            if (e < BN) {
+            if (e < TBN) {
                 const int t = tp[buf].n0 + e;
                 ExpCol cm;
                 if (t < a.N) cm = cols[a.col0 + t];
@@ -348,17 +420,18 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
                 colmeta[buf][e] = cm;
             }
             named_bar_sync(1, EPI_THREADS);
-            float hi[EPI_COLS], lo[EPI_COLS];
+            float hi[ECOLS], lo[ECOLS];
 #pragma unroll
-            for (int c = 0; c < EPI_COLS; ++c) { hi[c] = 0.0f; lo[c] = 0.0f; }
+            for (int c = 0; c < ECOLS; ++c) { hi[c] = 0.0f; lo[c] = 0.0f; }
             bool ok = true;
             for (int c = 0; c < nchunks; ++c, ++C) {
-                if (ok) ok = mbar_wait(acc_full, C & 1, err, 6);
+                const int b = C % NACC;
+                if (ok) ok = mbar_wait(&acc_full[b], (C / NACC) & 1, err, 6);
                 if (!ok) continue;
                 tc_fence_after();
-                drain_chunk<S>(tmem + ((uint32_t)(q * 32) << 16) + col0, BN, hi, lo);
+                drain_chunk<S>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 4 * TBN + col0), TBN, hi, lo);
                 tc_fence_before();
-                mbar_arrive(acc_empty);
+                mbar_arrive(&acc_empty[b]);
             }
             if (!ok) {
                 epi_fail = 1;
@@ -370,7 +443,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
             const int jj = tp[buf].jj0 + (row >> lg), jjp = tp[buf].jjp0 + (row & ((1 << lg) - 1));
             if (jj < a.cn && jjp < a.cnp && (a.cf + jj) != (a.cfp + jjp)) {
 #pragma unroll
-                for (int c = 0; c < EPI_COLS; ++c) {
+                for (int c = 0; c < ECOLS; ++c) {
                     const ExpCol &m = colmeta[buf][col0 + c];
                     if (m.H) {
                         const int64_t r = m.rbase + jj;
@@ -389,7 +462,7 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
     }
 }
 
@@ -791,7 +864,7 @@ EncodeTiled encode_fn() {
 
 // dynamic shared memory of the expansion kernel: the operand slots, the
 // barriers and the 1 KB alignment
-static int split_smem_bytes(int S) { return S * SLOT + 2048; }
+static int split_smem_bytes(int S, int bn) { return xsets(S, bn) * S * xslot(bn) + 2048; }
 
 static int sm_count() {
     static int n = 0;
@@ -806,14 +879,26 @@ static int sm_count() {
     return n;
 }
 
+template <int S>
+static cudaError_t set_smem_attr_s() {
+    cudaError_t e = cudaFuncSetAttribute(split_expand_kernel<S, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         split_smem_bytes(S, 32));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(split_expand_kernel<S, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 split_smem_bytes(S, 64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(split_expand_kernel<S, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 split_smem_bytes(S, 128));
+    return e;
+}
+
 static cudaError_t set_smem_attr(int S) {
-    const int bytes = split_smem_bytes(S);
     switch (S) {
-        case 2: return cudaFuncSetAttribute(split_expand_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        case 3: return cudaFuncSetAttribute(split_expand_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        case 4: return cudaFuncSetAttribute(split_expand_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        case 5: return cudaFuncSetAttribute(split_expand_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        default: return cudaFuncSetAttribute(split_expand_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        case 2: return set_smem_attr_s<2>();
+        case 3: return set_smem_attr_s<3>();
+        case 4: return set_smem_attr_s<4>();
+        case 5: return set_smem_attr_s<5>();
+        default: return set_smem_attr_s<6>();
     }
 }
 
@@ -867,9 +952,10 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
     CUresult r = CUDA_SUCCESS;
     for (int i = 0; i < 3 && r == CUDA_SUCCESS; ++i) {
         const int lg = 3 + i;
-        cuuint32_t box[4] = {BKB, (cuuint32_t)(1 << lg), (cuuint32_t)(BM >> lg), 1};
+        // half a 64-wide K block per copy (x = 0 or 32: 64-byte aligned)
+        cuuint32_t box[4] = {XBK, (cuuint32_t)(1 << lg), (cuuint32_t)(BM >> lg), 1};
         r = encode_fn()(&M.tm_panel[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, M.panel_slices, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     if (r != CUDA_SUCCESS) return mixed_fail(ctx, HB_ERR_CUDA, "panel tensor map: error " + std::to_string((int)r));
@@ -884,7 +970,8 @@ const float2 *mixed_panel_diag(const hb_ctx *ctx) { return ctx->mixed ? ctx->mix
 int mixed_slices(const hb_ctx *ctx) { return ctx->mixed ? ctx->mixed->slices : ctx->split_slices; }
 
 // Coefficient slices of `rows` rows in all: [S][Kpad/64][rows][64] bf16 and
-// the 3D map whose box is one 128 x 64 tile of one slice plane.
+// three 3D maps, one per tile width bn = 32, 64, 128, whose box is one bn x 32
+// tile (rows x half a K block) of one slice plane.
 int split_coef_alloc(hb_ctx *mem, int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err) {
     *buf = nullptr;
     if (!encode_fn()) { *err = "cuTensorMapEncodeTiled is not available"; return HB_ERR_CUDA; }
@@ -894,11 +981,14 @@ int split_coef_alloc(hb_ctx *mem, int S, int64_t rows, int Kpad, void **buf, CUt
     const int KB = Kpad / BKB;
     cuuint64_t dims[3] = {(cuuint64_t)BKB, (cuuint64_t)rows, (cuuint64_t)S * KB};
     cuuint64_t strides[2] = {(cuuint64_t)BKB * 2, (cuuint64_t)rows * BKB * 2};
-    cuuint32_t box[3] = {BKB, BN, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode_fn()(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, *buf, dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = CUDA_SUCCESS;
+    for (int i = 0; i < 3 && r == CUDA_SUCCESS; ++i) {
+        cuuint32_t box[3] = {XBK, (cuuint32_t)(32 << i), 1};   // half a 64-wide K block per copy, as the panel's
+        r = encode_fn()(&tm[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, *buf, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (r != CUDA_SUCCESS) {
         dfree(mem, *buf);
         *buf = nullptr;
@@ -908,12 +998,20 @@ int split_coef_alloc(hb_ctx *mem, int S, int64_t rows, int Kpad, void **buf, CUt
     return HB_OK;
 }
 
-int64_t blocks_split(int cn, int cnp, int N, int lg) {
+int64_t blocks_split(int cn, int cnp, int N, int lg, int bn) {
     if (cn <= 0 || cnp <= 0 || N <= 0) return 0;
     const int bj = BM >> lg, bjp = 1 << lg;
-    return (int64_t)((N + BN - 1) / BN) * ((cn + bj - 1) / bj) * ((cnp + bjp - 1) / bjp);
+    return (int64_t)((N + bn - 1) / bn) * ((cn + bj - 1) / bj) * ((cnp + bjp - 1) / bjp);
 }
-int split_ntn(int N) { return (N + BN - 1) / BN; }
+int split_ntn(int N, int bn) { return (N + bn - 1) / bn; }
+
+// Tile width for a merged block of N columns: the narrowest of 32 and 64 that
+// holds them, else 128 (whose MMAs read the least shared memory per flop);
+// `force` (32, 64, 128) overrides.
+int split_cols_choice(int N, int force) {
+    if (force == 32 || force == 64 || force == 128) return force;
+    return N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+}
 int split_jpt(int cnp, int lg) { return (cnp + (1 << lg) - 1) >> lg; }
 
 // Tile arrangement with the least padding of the cn x cnp rectangle (ties: 8 x 16).
@@ -936,27 +1034,36 @@ int g_slice(const Grouped<SliceTask> &g, int64_t R, int Kin, int Kout, const int
     return 1;
 }
 
-int g_split(const hb_ctx *panel_ctx, int lg, const CUtensorMap *tm_coef, const Grouped<SplitTask> &g, int kblocks,
-            int coef_planes, const ExpCol *cols, int *err, cudaStream_t s, int shard_r, int shard_n) {
+int g_split(const hb_ctx *panel_ctx, int lg, int bn, const CUtensorMap *tm_coef, const Grouped<SplitTask> &g,
+            int kblocks, int coef_planes, const ExpCol *cols, int *err, cudaStream_t s, int shard_r, int shard_n) {
     if (g.blocks <= 0) return 0;
+    if (bn != 32 && bn != 64 && bn != 128) return 0;
     const MixedState &M = *panel_ctx->mixed;
     const CUtensorMap &tm_panel = M.tm_panel[lg - 3];
-    const size_t smem = split_smem_bytes(M.slices);
-    // persistent: one CTA per SM at most (each holds all of its SM's tensor memory)
+    const CUtensorMap &tm_c = tm_coef[bn == 32 ? 0 : (bn == 64 ? 1 : 2)];
+    const size_t smem = split_smem_bytes(M.slices, bn);
+    // persistent: one CTA per SM at most (each holds its SM's tensor memory or half of it)
     const int n_tiles = (int)g.blocks;
     const int n_local = n_tiles > shard_r ? (n_tiles - shard_r + shard_n - 1) / shard_n : 0;
     if (n_local <= 0) return 0;
     const unsigned grid = (unsigned)std::min(n_local, sm_count());
-#define HB_SPLIT(SS) \
-    split_expand_kernel<SS><<<grid, NTHREADS, smem, s>>>(tm_panel, *tm_coef, g.tasks, g.blk, g.n, n_tiles, kblocks, \
-                                                        coef_planes, cols, err, shard_r, shard_n)
+#define HB_SPLIT(SS, BB)                                                                                      \
+    split_expand_kernel<SS, BB><<<grid, NTHREADS, smem, s>>>(tm_panel, tm_c, g.tasks, g.blk, g.n, n_tiles, kblocks, \
+                                                            coef_planes, cols, err, shard_r, shard_n)
+#define HB_SPLIT_S(SS)                           \
+    do {                                         \
+        if (bn == 32) HB_SPLIT(SS, 32);          \
+        else if (bn == 64) HB_SPLIT(SS, 64);     \
+        else HB_SPLIT(SS, 128);                  \
+    } while (0)
     switch (M.slices) {
-        case 2: HB_SPLIT(2); break;
-        case 3: HB_SPLIT(3); break;
-        case 4: HB_SPLIT(4); break;
-        case 5: HB_SPLIT(5); break;
-        default: HB_SPLIT(6); break;
+        case 2: HB_SPLIT_S(2); break;
+        case 3: HB_SPLIT_S(3); break;
+        case 4: HB_SPLIT_S(4); break;
+        case 5: HB_SPLIT_S(5); break;
+        default: HB_SPLIT_S(6); break;
     }
+#undef HB_SPLIT_S
 #undef HB_SPLIT
     return 1;
 }

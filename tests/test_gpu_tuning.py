@@ -1,6 +1,6 @@
-"""Launch shapes of the build plan: every tensor-core tile arrangement and every
-class-4 shape gives the same bits, each matches the oracle, and the autotuner
-(which only chooses among these) never changes the output."""
+"""Launch shapes of the build plan: every tensor-core tile arrangement and width
+and every class-4 shape gives the same bits, each matches the oracle, and the
+autotuner (which only chooses among these) never changes the output."""
 import numpy as np
 import pytest
 
@@ -25,17 +25,21 @@ def _problems():
         synth.make_tiny(11, n_to=6, n_co=14, n_det=12, n_l2=20, n_groups=3, n_state=[1, 3, 2],
                         cont_ranges=[(0, 7), (3, 9), (5, 4)]),
         synth.make_config("mid"),
+        # merged blocks of 78, 63 and 45 columns: several column tiles at width 32
+        synth.make_tiny(12, n_to=6, n_co=16, n_det=14, n_l2=10, n_groups=3, n_state=[12, 7, 9],
+                        cont_ranges=[(0, 16), (2, 11), (0, 9)]),
     ]
 
 
-SHAPES = [dict(split_tile=3, class4_states=8, class4_threads=32),
-          dict(split_tile=4, class4_states=16, class4_threads=64),
-          dict(split_tile=5, class4_states=32, class4_threads=128),
-          dict(split_tile=4, class4_states=4, class4_threads=32),
-          dict(split_tile=3, class4_states=20, class4_threads=64)]
+SHAPES = [dict(split_tile=3, split_cols=32, class4_states=8, class4_threads=32),
+          dict(split_tile=4, split_cols=64, class4_states=16, class4_threads=64),
+          dict(split_tile=5, split_cols=128, class4_states=32, class4_threads=128),
+          dict(split_tile=4, split_cols=32, class4_states=4, class4_threads=32),
+          dict(split_tile=3, split_cols=64, class4_states=20, class4_threads=64),
+          dict(split_tile=5, split_cols=32)]
 
 
-@pytest.mark.parametrize("idx", [0, 1])
+@pytest.mark.parametrize("idx", [0, 1, 2])
 def test_forced_shapes_identical_and_match_oracle(idx):
     P = _problems()[idx]
     ref, _, _ = gpu_dense(P, precision=1)
@@ -75,7 +79,7 @@ def test_autotune_is_bit_identical():
 def test_invalid_shape_options_rejected():
     from paper_1709_03005_gb300 import hb
     P = _problems()[0]
-    for kw in (dict(split_tile=6), dict(class4_states=14), dict(class4_states=36), dict(class4_threads=96),
+    for kw in (dict(split_tile=6), dict(split_cols=48), dict(split_cols=256), dict(class4_states=14), dict(class4_states=36), dict(class4_threads=96),
                dict(class4_path=3),
                dict(class4_path=-1)):
         with pytest.raises(hb.HBError):
