@@ -217,6 +217,8 @@ static int validate_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *
         return fail(ctx, HB_ERR_INVALID_ARG, "diag_basis must be 0 or 3..10");
     if (o && o->split_cols != 0 && o->split_cols != 32 && o->split_cols != 64 && o->split_cols != 128)
         return fail(ctx, HB_ERR_INVALID_ARG, "split_cols must be 0, 32, 64 or 128");
+    if (o && o->split_kstage != 0 && o->split_kstage != 32 && o->split_kstage != 64)
+        return fail(ctx, HB_ERR_INVALID_ARG, "split_kstage must be 0, 32 or 64");
     const int W = p->n_words, nw = 2 * W;
     // electron counts: every target determinant has the same alpha/beta split,
     // the continuum electron sets the L2 split
@@ -444,6 +446,7 @@ int stage_problem(hb_ctx *ctx, const hb_problem *p, const hb_options *o, cudaStr
     if (o) {
         ctx->force_tile = o->split_tile;
         ctx->force_cols = o->split_cols;
+        ctx->force_kstage = o->split_kstage;
         ctx->force_c4_states = o->class4_states;
         ctx->force_c4_threads = o->class4_threads;
         ctx->c4_path = o->class4_path;

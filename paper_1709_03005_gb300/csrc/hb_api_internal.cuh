@@ -109,6 +109,7 @@ struct hb_ctx {
     int autotune = 0;
     int force_tile = 0, force_c4_states = 0, force_c4_threads = 0;   // 0: chosen by the plan
     int force_cols = 0;      // tensor-core expansion tile width (32, 64, 128); 0: chosen by the plan
+    int force_kstage = 0;    // K stage of its 128-column tiles (32, 64); 0: chosen by the plan
     int diag_basis = 6;      // Davidson basis limit, in blocks of b vectors
     int stall_iters = 10;    // learned-factor stall check: window and required fall (2^stall_log2)
     int stall_log2 = 1;

@@ -16,12 +16,14 @@ int mixed_slices(const hb_ctx *ctx);
 // Diagonal panel rows (j, j) as float pairs [n_co][Kpad].
 const float2 *mixed_panel_diag(const hb_ctx *ctx);
 // Coefficient slices [S][Kpad/64][rows][64] bf16 and their tensor maps
-// tm[0..2], one per tile width 32, 64, 128.
+// tm[0..3]: 32-K stages at tile widths 32, 64, 128, and 64-K stages at 128.
 int split_coef_alloc(hb_ctx *mem, int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err);
 int64_t blocks_split(int cn, int cnp, int N, int lg, int bn);
 int split_ntn(int N, int bn);
 // tile width (32, 64, 128) for a merged block of N columns; force: 0 or a width
 int split_cols_choice(int N, int force);
+// K stage (32, 64) of a launch of tile width bn over kblocks 64-wide K blocks
+int split_kstage_choice(int bn, int kblocks, int force);
 int split_jpt(int cnp, int lg);
 int split_tile_heuristic(int cn, int cnp);
 // coefficient rows of Kin labels into slices of Kout columns, column k being
@@ -29,7 +31,7 @@ int split_tile_heuristic(int cn, int cnp);
 int g_slice(const hb::Grouped<hb::SliceTask> &g, int64_t R, int Kin, int Kout, const int32_t *perm, int S,
             int skip_col, void *out, cudaStream_t s);
 // lg: tile arrangement (3..5, see SplitTask) and bn: tile width (32, 64,
-// 128); every task of g must use both.  tm_coef: the three coefficient maps.
+// 128); every task of g must use both.  tm_coef: the four coefficient maps.
 // kblocks: 64-wide K blocks of the panel rows; coef_planes: K blocks per
 // slice of the coefficient slices (the task's kc0 selects its label class)
 // shard_r, shard_n: the launch takes tiles shard_r, shard_r + shard_n, ... only

@@ -133,7 +133,7 @@ struct Plan {
     bool upload_pending = false;
     // tensor-core operands
     void *coef = nullptr;
-    CUtensorMap tm_coef[3];            // coefficient slices, one map per tile width 32, 64, 128
+    CUtensorMap tm_coef[4];            // coefficient slices: 32-K stages at widths 32, 64, 128; 64-K at 128
     int64_t coef_rows = 0;
     int *err = nullptr;
     // classes 4, 2 and 8 run on a second stream beside the target side and

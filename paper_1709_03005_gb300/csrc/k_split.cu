@@ -54,7 +54,8 @@ struct MixedState {
     __nv_bfloat16 *panel_slices = nullptr;   // [S][Kpad/64][n_co*n_co][64]
     bool panel_ready = false;
     bool borrowed_panel = false;
-    CUtensorMap tm_panel[3];                  // boxes of 8 x 16, 16 x 8, 32 x 4 continuum pairs (j' x j)
+    // [stage width 32, 64][box of 8 x 16, 16 x 8, 32 x 4 continuum pairs (j' x j)]
+    CUtensorMap tm_panel[2][3];
     float2 *pdiag = nullptr;                  // diagonal panel rows (j, j) as float pairs [n_co][Kpad]
 };
 
@@ -78,22 +79,25 @@ constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int EPI_COLS = BN / 2;             // columns per epilogue thread
 constexpr int NTHREADS = 64 + EPI_THREADS;
 
-// The expansion kernel's K pipeline: stages of 32 K (64-byte operand rows,
-// 64-byte swizzle), and as many full sets of S slots as fit 192 KB, so the
-// copies of the next stages are in flight while the stages before them are
-// multiplied.  Its tile is 128 continuum pairs x TBN columns (state pairs),
-// TBN = 32, 64 or 128 chosen per merged block from its column count; with
-// TBN <= 64 the four accumulators are double-buffered in tensor memory, so the
-// MMAs of the next chunk run while the epilogue drains the last one.
-constexpr int XBK = 32;
-constexpr int XA_TILE = BM * XBK * 2;        // 8 KB
+// The expansion kernel's K pipeline: stages of KS = 32 K (64-byte operand
+// rows, 64-byte swizzle) or 64 K (128-byte rows and swizzle), and as many full
+// sets of S slots as fit 192 KB, so the copies of the next stages are in
+// flight while the stages before them are multiplied.  With one set (64-K
+// stages and 128 columns) odd stages use the slots in the order in which the
+// even ones free them (slot_of).  Its tile is 128 continuum pairs x TBN
+// columns (state pairs), TBN = 32, 64 or 128 chosen per merged block from its
+// column count; with TBN <= 64 the four accumulators are double-buffered in
+// tensor memory, so the MMAs of the next chunk run while the epilogue drains
+// the last one.  64-K stages serve 128-column tiles over long K (fewer waits
+// and copies per K), 32-K stages the rest (deeper prefetch).
 constexpr int XBUDGET = 192 * 1024;          // shared memory of the slots
 constexpr int XBARS = 24;                    // full and empty barriers: slots at most
-constexpr int XSTAGES_PER_CHUNK = KCHUNK / XBK;
+constexpr int kK64Blocks = 32;               // 64-K stages from this many 64-wide K blocks up
+__host__ __device__ constexpr int xa_tile(int ks) { return BM * ks * 2; }
 // one slice of one stage: panel tile, then coefficient tile (multiples of 1 KB)
-__host__ __device__ constexpr int xslot(int tbn) { return XA_TILE + tbn * XBK * 2; }
-__host__ __device__ constexpr int xsets(int S, int tbn) {
-    return XBUDGET / (S * xslot(tbn)) < 4 ? XBUDGET / (S * xslot(tbn)) : 4;
+__host__ __device__ constexpr int xslot(int tbn, int ks) { return (BM + tbn) * ks * 2; }
+__host__ __device__ constexpr int xsets(int S, int tbn, int ks) {
+    return XBUDGET / (S * xslot(tbn, ks)) < 4 ? XBUDGET / (S * xslot(tbn, ks)) : 4;
 }
 __host__ __device__ constexpr int xacc_bufs(int tbn) { return 8 * tbn <= 512 ? 2 : 1; }
 __host__ __device__ constexpr int xtmem_cols(int tbn) { return xacc_bufs(tbn) * 4 * tbn; }
@@ -180,19 +184,26 @@ __device__ __forceinline__ bool mma_block(uint64_t *full_bar, uint64_t *empty_ba
     return true;
 }
 
-// One K stage of the expansion kernel from slot set `set` (slots set*S ..
-// set*S + S-1, slice t in slot set*S + t), accumulators at TMEM column tacc:
-// for each arriving slice t the pairs (i, l) with max(i, l) = t and i + l < S,
-// then the commits that free the slots read for the last time.
-template <int S, int TBN>
-__device__ __forceinline__ bool mma_stage(uint64_t *full_bar, uint64_t *empty_bar, int set, uint32_t par,
-                                          uint32_t tacc, uint64_t desc0, uint32_t idesc, uint32_t &fresh, int *err) {
-    constexpr int XS = xslot(TBN);
-    const int sb = set * S;
-    const uint64_t dset = desc0 + (uint64_t)((uint32_t)(sb * XS) >> 4);
+// Slot of slice t in stage G: slot set G mod NSET, or with a single set the
+// release-ordered slots of odd stages.
+template <int S, int NSET>
+__device__ __forceinline__ int xslot_index(int G, int t) {
+    if (NSET >= 2) return (G % NSET) * S + t;
+    return (G & 1) ? slot_of<S>(1, t) : t;
+}
+
+// One K stage of the expansion kernel (stage G, slots xslot_index), with
+// accumulators at TMEM column tacc: for each arriving slice t the pairs (i, l)
+// with max(i, l) = t and i + l < S, then the commits that free the slots read
+// for the last time.
+template <int S, int TBN, int KS, int NSET>
+__device__ __forceinline__ bool mma_stage(uint64_t *full_bar, uint64_t *empty_bar, int G, uint32_t tacc,
+                                          uint64_t desc0, uint32_t idesc, uint32_t &fresh, int *err) {
+    constexpr int XS = xslot(TBN, KS);
+    const uint32_t par = (uint32_t)((G / NSET) & 1);
 #pragma unroll
     for (int t = 0; t < S; ++t) {
-        if (!mbar_wait(&full_bar[sb + t], par, err, 4)) return false;
+        if (!mbar_wait(&full_bar[xslot_index<S, NSET>(G, t)], par, err, 4)) return false;
         tc_fence_after();
 #pragma unroll
         for (int i = 0; i <= t; ++i) {
@@ -200,13 +211,13 @@ __device__ __forceinline__ bool mma_stage(uint64_t *full_bar, uint64_t *empty_ba
             for (int l = 0; l <= t; ++l) {
                 if ((i == t || l == t) && i + l < S) {
                     const int s = i + l < 3 ? i + l : 3;
-                    const uint32_t offA = (uint32_t)(i * XS);
-                    const uint32_t offB = (uint32_t)(l * XS + XA_TILE);
+                    const uint32_t offA = (uint32_t)(xslot_index<S, NSET>(G, i) * XS);
+                    const uint32_t offB = (uint32_t)(xslot_index<S, NSET>(G, l) * XS + xa_tile(KS));
 #pragma unroll
-                    for (int k = 0; k < XBK / 16; ++k) {
+                    for (int k = 0; k < KS / 16; ++k) {
                         const uint32_t acc = (fresh >> s) & 1u ? 0u : 1u;
-                        mma_bf16(tacc + s * TBN, dset + ((offA + k * 32) >> 4), dset + ((offB + k * 32) >> 4), idesc,
-                                 acc);
+                        mma_bf16(tacc + s * TBN, desc0 + ((offA + k * 32) >> 4), desc0 + ((offB + k * 32) >> 4),
+                                 idesc, acc);
                         fresh &= ~(1u << s);
                     }
                 }
@@ -214,7 +225,7 @@ __device__ __forceinline__ bool mma_stage(uint64_t *full_bar, uint64_t *empty_ba
         }
 #pragma unroll
         for (int i = 0; i < S; ++i)
-            if (release_step<S>(i) == t) mma_commit(&empty_bar[sb + i]);
+            if (release_step<S>(i) == t) mma_commit(&empty_bar[xslot_index<S, NSET>(G, i)]);
     }
     return true;
 }
@@ -281,7 +292,7 @@ __device__ __forceinline__ TilePos tile_pos(const SplitTask *__restrict__ tasks,
 // The slot ring, the accumulator hand-over and their barrier phases run on
 // across tiles, so the loads and MMAs of the next tile start while the
 // epilogue warps still write the last one out from registers.
-template <int S, int TBN>
+template <int S, int TBN, int KS>
 __global__ void __launch_bounds__(NTHREADS, 1)
 split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_constant__ CUtensorMap tm_coef,
                     const SplitTask *__restrict__ tasks, const int64_t *__restrict__ blk, int n_tasks, int n_tiles,
@@ -290,12 +301,14 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     // this launch's tiles: shard_r, shard_r + shard_n, ... (all of them unless
     // sharded), numbered t = 0, 1, ... so that every role walks the same list
     const int n_local = n_tiles > shard_r ? (n_tiles - shard_r + shard_n - 1) / shard_n : 0;
-    constexpr int XS = xslot(TBN);
-    constexpr int NSET = xsets(S, TBN);
+    constexpr int XS = xslot(TBN, KS);
+    constexpr int NSET = xsets(S, TBN, KS);
     constexpr int NACC = xacc_bufs(TBN);      // accumulator sets in tensor memory
     constexpr int TCOLS = xtmem_cols(TBN);
     constexpr int ECOLS = TBN / 2;            // columns per epilogue thread
-    static_assert(NSET >= 2 && NSET * S <= XBARS, "slot sets");
+    constexpr int SPC = KCHUNK / KS;          // stages per exact chunk
+    static_assert(KS == 32 || KS == 64, "stage width");
+    static_assert(NSET >= 1 && NSET * S <= XBARS, "slot sets");
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *slots = base;                                         // [NSET][S][XS]
@@ -312,8 +325,8 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
     __shared__ int epi_fail;                 // an epilogue wait gave up (read only after a barrier)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nst = 2 * kblocks;             // K stages of 32 per tile
-    const int nchunks = (nst + XSTAGES_PER_CHUNK - 1) / XSTAGES_PER_CHUNK;
+    const int nst = kblocks * (64 / KS);     // K stages per tile
+    const int nchunks = (nst + SPC - 1) / SPC;
 
     if (threadIdx.x == 0) {
         epi_fail = 0;
@@ -345,30 +358,34 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
                 const int crow = (int)(tasks[p.ti].coef_row0 + p.n0);
                 const int kc0 = tasks[p.ti].kc0;      // the block's label class in the coefficient slices
                 for (int ks = 0; ks < nst && ok; ++ks, ++G) {
-                    // stage G uses slot set G mod NSET for the (G / NSET)-th time
-                    const int sb = (G % NSET) * S, round = G / NSET;
-                    const int kx = (ks & 1) * XBK, kb = ks >> 1;   // half of 64-wide K block kb
+                    // stage G uses its slots for the (G / NSET)-th time
+                    const int round = G / NSET;
+                    const int kx = KS == 64 ? 0 : (ks & 1) * 32;   // part of 64-wide K block kb
+                    const int kb = KS == 64 ? ks : ks >> 1;
                     for (int t = 0; t < S && ok; ++t) {
-                        const int sl = sb + t;
+                        const int sl = xslot_index<S, NSET>(G, t);
                         // wait for the slot's release by the stage NSET before this one
                         if (round > 0) ok = mbar_wait(&empty_bar[sl], (round - 1) & 1, err, 1);
                         if (!ok) break;
                         uint8_t *sA = slots + sl * XS;
                         mbar_expect_tx(&full_bar[sl], (uint32_t)XS);
                         tma_load_4d(sA, &tm_panel, &full_bar[sl], kx, cx, cy, t * kblocks + kb);
-                        tma_load_3d(sA + XA_TILE, &tm_coef, &full_bar[sl], kx, crow, t * coef_planes + kc0 + kb);
+                        tma_load_3d(sA + xa_tile(KS), &tm_coef, &full_bar[sl], kx, crow,
+                                    t * coef_planes + kc0 + kb);
                     }
                 }
             }
             // wait until this producer's copies of the last stage of every set have landed
             for (int g = G > NSET ? G - NSET : 0; g < G; ++g)
-                for (int t = 0; t < S; ++t) mbar_wait(&full_bar[(g % NSET) * S + t], (g / NSET) & 1, err, 2);
+                for (int t = 0; t < S; ++t)
+                    mbar_wait(&full_bar[xslot_index<S, NSET>(g, t)], (g / NSET) & 1, err, 2);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = instr_desc_bf16(BM, TBN);
-            const uint64_t desc0 = smem_desc_sw64(smem_u32(slots));    // + (offset >> 4) per operand tile
+            // + (offset >> 4) per operand tile
+            const uint64_t desc0 = KS == 64 ? smem_desc_sw128(smem_u32(slots)) : smem_desc_sw64(smem_u32(slots));
             bool ok = true;
             int G = 0, C = 0;                     // K stages and chunks over all tiles
             for (int t = blockIdx.x; t < n_local && ok; t += gridDim.x) {
@@ -379,11 +396,10 @@ split_expand_kernel(const __grid_constant__ CUtensorMap tm_panel, const __grid_c
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t tacc = tmem + (uint32_t)(b * 4 * TBN);
-                    const int ks_end = min(nst, (c + 1) * XSTAGES_PER_CHUNK);
+                    const int ks_end = min(nst, (c + 1) * SPC);
                     uint32_t fresh = 0xFu;        // accumulators not yet written in this chunk
-                    for (int ks = c * XSTAGES_PER_CHUNK; ks < ks_end && ok; ++ks, ++G)
-                        ok = mma_stage<S, TBN>(full_bar, empty_bar, G % NSET, (uint32_t)((G / NSET) & 1), tacc,
-                                               desc0, idesc, fresh, err);
+                    for (int ks = c * SPC; ks < ks_end && ok; ++ks, ++G)
+                        ok = mma_stage<S, TBN, KS, NSET>(full_bar, empty_bar, G, tacc, desc0, idesc, fresh, err);
                     if (ok) mma_commit(&acc_full[b]);     // accumulators of chunk C complete
                 }
             }
@@ -864,7 +880,7 @@ EncodeTiled encode_fn() {
 
 // dynamic shared memory of the expansion kernel: the operand slots, the
 // barriers and the 1 KB alignment
-static int split_smem_bytes(int S, int bn) { return xsets(S, bn) * S * xslot(bn) + 2048; }
+static int split_smem_bytes(int S, int bn, int ks) { return xsets(S, bn, ks) * S * xslot(bn, ks) + 2048; }
 
 static int sm_count() {
     static int n = 0;
@@ -881,14 +897,14 @@ static int sm_count() {
 
 template <int S>
 static cudaError_t set_smem_attr_s() {
-    cudaError_t e = cudaFuncSetAttribute(split_expand_kernel<S, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         split_smem_bytes(S, 32));
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(split_expand_kernel<S, 32, 32>, attr, split_smem_bytes(S, 32, 32));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(split_expand_kernel<S, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 split_smem_bytes(S, 64));
+        e = cudaFuncSetAttribute(split_expand_kernel<S, 64, 32>, attr, split_smem_bytes(S, 64, 32));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(split_expand_kernel<S, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 split_smem_bytes(S, 128));
+        e = cudaFuncSetAttribute(split_expand_kernel<S, 128, 32>, attr, split_smem_bytes(S, 128, 32));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(split_expand_kernel<S, 128, 64>, attr, split_smem_bytes(S, 128, 64));
     return e;
 }
 
@@ -920,7 +936,8 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
         M.slices = B.slices;
         M.panel_rows = B.panel_rows;
         M.panel_slices = B.panel_slices;
-        for (int i = 0; i < 3; ++i) M.tm_panel[i] = B.tm_panel[i];
+        for (int w = 0; w < 2; ++w)
+            for (int i = 0; i < 3; ++i) M.tm_panel[w][i] = B.tm_panel[w][i];
         M.pdiag = B.pdiag;
         M.borrowed_panel = true;
         M.panel_ready = true;
@@ -950,14 +967,17 @@ int mixed_prepare(hb_ctx *ctx, cudaStream_t s) {
     cuuint64_t strides[3] = {(cuuint64_t)BKB * 2, (cuuint64_t)ctx->n_co * BKB * 2, (cuuint64_t)rows * BKB * 2};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = CUDA_SUCCESS;
-    for (int i = 0; i < 3 && r == CUDA_SUCCESS; ++i) {
-        const int lg = 3 + i;
-        // half a 64-wide K block per copy (x = 0 or 32: 64-byte aligned)
-        cuuint32_t box[4] = {XBK, (cuuint32_t)(1 << lg), (cuuint32_t)(BM >> lg), 1};
-        r = encode_fn()(&M.tm_panel[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, M.panel_slices, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    }
+    for (int w = 0; w < 2 && r == CUDA_SUCCESS; ++w)
+        for (int i = 0; i < 3 && r == CUDA_SUCCESS; ++i) {
+            const int lg = 3 + i;
+            // a 32-K stage copies half a 64-wide K block (x = 0 or 32: 64-byte
+            // aligned, 64-byte swizzle), a 64-K stage all of it (128-byte swizzle)
+            cuuint32_t box[4] = {w ? 64u : 32u, (cuuint32_t)(1 << lg), (cuuint32_t)(BM >> lg), 1};
+            r = encode_fn()(&M.tm_panel[w][i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, M.panel_slices, dims, strides,
+                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            w ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
     if (r != CUDA_SUCCESS) return mixed_fail(ctx, HB_ERR_CUDA, "panel tensor map: error " + std::to_string((int)r));
     e = set_smem_attr(M.slices);
     if (e != cudaSuccess) return mixed_fail(ctx, HB_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
@@ -970,8 +990,9 @@ const float2 *mixed_panel_diag(const hb_ctx *ctx) { return ctx->mixed ? ctx->mix
 int mixed_slices(const hb_ctx *ctx) { return ctx->mixed ? ctx->mixed->slices : ctx->split_slices; }
 
 // Coefficient slices of `rows` rows in all: [S][Kpad/64][rows][64] bf16 and
-// three 3D maps, one per tile width bn = 32, 64, 128, whose box is one bn x 32
-// tile (rows x half a K block) of one slice plane.
+// four 3D maps: for 32-K stages one per tile width bn = 32, 64, 128 (box: bn
+// rows x half a K block of one slice plane, 64-byte swizzle), and for 64-K
+// stages one of 128 rows x a whole K block (128-byte swizzle).
 int split_coef_alloc(hb_ctx *mem, int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err) {
     *buf = nullptr;
     if (!encode_fn()) { *err = "cuTensorMapEncodeTiled is not available"; return HB_ERR_CUDA; }
@@ -983,11 +1004,11 @@ int split_coef_alloc(hb_ctx *mem, int S, int64_t rows, int Kpad, void **buf, CUt
     cuuint64_t strides[2] = {(cuuint64_t)BKB * 2, (cuuint64_t)rows * BKB * 2};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = CUDA_SUCCESS;
-    for (int i = 0; i < 3 && r == CUDA_SUCCESS; ++i) {
-        cuuint32_t box[3] = {XBK, (cuuint32_t)(32 << i), 1};   // half a 64-wide K block per copy, as the panel's
+    for (int i = 0; i < 4 && r == CUDA_SUCCESS; ++i) {
+        cuuint32_t box[3] = {i < 3 ? 32u : 64u, (cuuint32_t)(i < 3 ? 32 << i : 128), 1};
         r = encode_fn()(&tm[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, *buf, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, i < 3 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     if (r != CUDA_SUCCESS) {
         dfree(mem, *buf);
@@ -1034,27 +1055,35 @@ int g_slice(const Grouped<SliceTask> &g, int64_t R, int Kin, int Kout, const int
     return 1;
 }
 
+int split_kstage_choice(int bn, int kblocks, int force) {
+    if (bn != 128) return 32;
+    if (force == 32 || force == 64) return force;
+    return kblocks >= kK64Blocks ? 64 : 32;
+}
+
 int g_split(const hb_ctx *panel_ctx, int lg, int bn, const CUtensorMap *tm_coef, const Grouped<SplitTask> &g,
             int kblocks, int coef_planes, const ExpCol *cols, int *err, cudaStream_t s, int shard_r, int shard_n) {
     if (g.blocks <= 0) return 0;
     if (bn != 32 && bn != 64 && bn != 128) return 0;
     const MixedState &M = *panel_ctx->mixed;
-    const CUtensorMap &tm_panel = M.tm_panel[lg - 3];
-    const CUtensorMap &tm_c = tm_coef[bn == 32 ? 0 : (bn == 64 ? 1 : 2)];
-    const size_t smem = split_smem_bytes(M.slices, bn);
+    const int ks = split_kstage_choice(bn, kblocks, panel_ctx->force_kstage);
+    const CUtensorMap &tm_panel = M.tm_panel[ks == 64 ? 1 : 0][lg - 3];
+    const CUtensorMap &tm_c = tm_coef[ks == 64 ? 3 : (bn == 32 ? 0 : (bn == 64 ? 1 : 2))];
+    const size_t smem = split_smem_bytes(M.slices, bn, ks);
     // persistent: one CTA per SM at most (each holds its SM's tensor memory or half of it)
     const int n_tiles = (int)g.blocks;
     const int n_local = n_tiles > shard_r ? (n_tiles - shard_r + shard_n - 1) / shard_n : 0;
     if (n_local <= 0) return 0;
     const unsigned grid = (unsigned)std::min(n_local, sm_count());
-#define HB_SPLIT(SS, BB)                                                                                      \
-    split_expand_kernel<SS, BB><<<grid, NTHREADS, smem, s>>>(tm_panel, tm_c, g.tasks, g.blk, g.n, n_tiles, kblocks, \
-                                                            coef_planes, cols, err, shard_r, shard_n)
-#define HB_SPLIT_S(SS)                           \
-    do {                                         \
-        if (bn == 32) HB_SPLIT(SS, 32);          \
-        else if (bn == 64) HB_SPLIT(SS, 64);     \
-        else HB_SPLIT(SS, 128);                  \
+#define HB_SPLIT(SS, BB, KK)                                                                                    \
+    split_expand_kernel<SS, BB, KK><<<grid, NTHREADS, smem, s>>>(tm_panel, tm_c, g.tasks, g.blk, g.n, n_tiles, \
+                                                                kblocks, coef_planes, cols, err, shard_r, shard_n)
+#define HB_SPLIT_S(SS)                                 \
+    do {                                               \
+        if (bn == 32) HB_SPLIT(SS, 32, 32);            \
+        else if (bn == 64) HB_SPLIT(SS, 64, 32);       \
+        else if (ks == 32) HB_SPLIT(SS, 128, 32);      \
+        else HB_SPLIT(SS, 128, 64);                    \
     } while (0)
     switch (M.slices) {
         case 2: HB_SPLIT_S(2); break;

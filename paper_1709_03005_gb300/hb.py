@@ -40,7 +40,8 @@ class hb_options(C.Structure):
     _fields_ = [("split_slices", C.c_int32), ("validate", C.c_int32), ("autotune", C.c_int32),
                 ("split_tile", C.c_int32), ("class4_states", C.c_int32), ("class4_threads", C.c_int32),
                 ("class4_path", C.c_int32), ("mlp_stall_iters", C.c_int32), ("mlp_stall_log2", C.c_int32),
-                ("diag_basis", C.c_int32), ("split_cols", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("diag_basis", C.c_int32), ("split_cols", C.c_int32),
+                ("split_kstage", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class hb_layout(C.Structure):
@@ -207,7 +208,7 @@ class Hamiltonian:
 
     def __init__(self, problem, split_slices=0, validate=True, stream=None, base=None, autotune=False,
                  split_tile=0, class4_states=0, class4_threads=0, class4_path=0, mlp_stall_iters=0,
-                 mlp_stall_log2=0, diag_basis=0, split_cols=0):
+                 mlp_stall_log2=0, diag_basis=0, split_cols=0, split_kstage=0):
         import torch
         self.lib = load()
         self.base = base        # keeps a borrowed-integral base context alive
@@ -215,7 +216,8 @@ class Hamiltonian:
         keep = []
         self._problem, gs = _marshal_problem(p, keep)
         opts = hb_options(split_slices, 1 if validate else 0, 1 if autotune else 0, split_tile, class4_states,
-                          class4_threads, class4_path, mlp_stall_iters, mlp_stall_log2, diag_basis, split_cols)
+                          class4_threads, class4_path, mlp_stall_iters, mlp_stall_log2, diag_basis, split_cols,
+                          split_kstage)
         self.ctx = C.c_void_p()
         torch.cuda.init()
         if base is None:

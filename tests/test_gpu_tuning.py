@@ -1,6 +1,11 @@
 """Launch shapes of the build plan: every tensor-core tile arrangement and width
 and every class-4 shape gives the same bits, each matches the oracle, and the
-autotuner (which only chooses among these) never changes the output."""
+autotuner (which only chooses among these) never changes the output.  The K
+stage of the tensor-core expansion (32 or 64) orders the slice products
+differently, which rounds their one inexact accumulator (slice pairs
+i + l >= 3) differently: the two agree within the continuum tolerance of the
+mixed path (3e-11 of each element's condition scale), and to the bit outside
+the continuum block."""
 import numpy as np
 import pytest
 
@@ -36,7 +41,9 @@ SHAPES = [dict(split_tile=3, split_cols=32, class4_states=8, class4_threads=32),
           dict(split_tile=5, split_cols=128, class4_states=32, class4_threads=128),
           dict(split_tile=4, split_cols=32, class4_states=4, class4_threads=32),
           dict(split_tile=3, split_cols=64, class4_states=20, class4_threads=64),
-          dict(split_tile=5, split_cols=32)]
+          dict(split_tile=5, split_cols=32),
+          dict(split_tile=3, split_kstage=32)]
+KSTAGE_SHAPES = [dict(split_tile=4, split_cols=128, split_kstage=64), dict(split_kstage=64)]
 
 
 @pytest.mark.parametrize("idx", [0, 1, 2])
@@ -47,9 +54,13 @@ def test_forced_shapes_identical_and_match_oracle(idx):
     R = o.dense()
     cond = o.cc_condition()
     Dc = o.Dc
-    for kw in SHAPES:
+    for kw in SHAPES + KSTAGE_SHAPES:
         G, _, _ = gpu_dense(P, precision=1, **kw)
-        assert np.array_equal(G, ref), kw
+        if kw in SHAPES:
+            assert np.array_equal(G, ref), kw
+        else:
+            assert np.array_equal(G[Dc:, :], ref[Dc:, :]) and np.array_equal(G[:, Dc:], ref[:, Dc:]), kw
+            assert np.all(np.abs(G[:Dc, :Dc] - ref[:Dc, :Dc]) <= 3e-11 * cond), kw
         d = np.abs(G[:Dc, :Dc] - R[:Dc, :Dc])
         assert np.all(d <= 1e-10 * cond), kw
         for blk in (np.s_[Dc:, :Dc], np.s_[Dc:, Dc:]):
@@ -79,7 +90,8 @@ def test_autotune_is_bit_identical():
 def test_invalid_shape_options_rejected():
     from paper_1709_03005_gb300 import hb
     P = _problems()[0]
-    for kw in (dict(split_tile=6), dict(split_cols=48), dict(split_cols=256), dict(class4_states=14), dict(class4_states=36), dict(class4_threads=96),
+    for kw in (dict(split_tile=6), dict(split_cols=48), dict(split_cols=256), dict(split_kstage=16),
+               dict(class4_states=14), dict(class4_states=36), dict(class4_threads=96),
                dict(class4_path=3),
                dict(class4_path=-1)):
         with pytest.raises(hb.HBError):
