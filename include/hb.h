@@ -158,16 +158,18 @@ typedef struct {
     int32_t diag_basis;       /* hb_diag: the basis holds at most diag_basis blocks of b vectors
                                  (b = k + min(16, max(4, k / 2))) before a thick restart to 2b;
                                  0 = 6 (3..10) */
-    int32_t split_cols;       /* 0 = chosen per merged block from its columns (state pairs n, n'):
-                                 32 up to 32, 64 up to 64, else 128; 32, 64, 128 force that width of
-                                 the tensor-core tiles (results are bit-identical for every width) */
-    int32_t split_kstage;     /* 0 = chosen: K stages of 64 for 128-column tiles over at least 2048
-                                 labels, of 32 otherwise; 32 or 64 forces it for 128-column tiles
-                                 (narrower tiles always use 32).  The two orders of the products
-                                 round the FP32 accumulator of the slice pairs i + l >= 3 (terms
-                                 below 2^-21 of the largest products) differently, so results agree
-                                 within the mixed path's error bound, not bit for bit; every other
-                                 shape option keeps the bits */
+    int32_t split_cols;       /* 0 = chosen: below 2048 labels per merged block from its columns
+                                 (state pairs n, n'): 32 up to 32, 64 up to 64, else 128; from 2048
+                                 labels on, 128.  32, 64, 128 force that width of the tensor-core
+                                 tiles.  Results are bit-identical for every width that keeps the
+                                 K stage (below) */
+    int32_t split_kstage;     /* 0 = chosen: K stages of 64 for 128-column tiles from 2048 labels on,
+                                 of 32 otherwise; 32 or 64 forces it for 128-column tiles (narrower
+                                 tiles always use 32).  The two orders of the products round the
+                                 FP32 accumulator of the slice pairs i + l >= 3 (terms below 2^-21
+                                 of the largest products) differently, so results agree within the
+                                 mixed path's error bound, not bit for bit; every other shape
+                                 option keeps the bits */
     int32_t reserved[4];
 } hb_options;
 

@@ -20,8 +20,9 @@ const float2 *mixed_panel_diag(const hb_ctx *ctx);
 int split_coef_alloc(hb_ctx *mem, int S, int64_t rows, int Kpad, void **buf, CUtensorMap *tm, std::string *err);
 int64_t blocks_split(int cn, int cnp, int N, int lg, int bn);
 int split_ntn(int N, int bn);
-// tile width (32, 64, 128) for a merged block of N columns; force: 0 or a width
-int split_cols_choice(int N, int force);
+// tile width (32, 64, 128) for a merged block of N columns over kblocks 64-wide
+// K blocks; force: 0 or a width
+int split_cols_choice(int N, int kblocks, int force);
 // K stage (32, 64) of a launch of tile width bn over kblocks 64-wide K blocks
 int split_kstage_choice(int bn, int kblocks, int force);
 int split_jpt(int cnp, int lg);

@@ -440,7 +440,7 @@ void fill_tasks(Plan &p) {
             auto tc = p.choice.tile.find({k.cn, k.cnp});
             if (tc != p.choice.tile.end()) lg = tc->second;
             if (B.ctx->force_tile) lg = B.ctx->force_tile;
-            const int bn = split_cols_choice(N, B.ctx->force_cols);
+            const int bn = split_cols_choice(N, p.Kc / 64, B.ctx->force_cols);
             const void *pkey = mixed_panel_key(B.ctx);
             int gi = -1;
             for (size_t i = 0; i < p.split.size(); ++i)

@@ -1026,11 +1026,14 @@ int64_t blocks_split(int cn, int cnp, int N, int lg, int bn) {
 }
 int split_ntn(int N, int bn) { return (N + bn - 1) / bn; }
 
-// Tile width for a merged block of N columns: the narrowest of 32 and 64 that
-// holds them, else 128 (whose MMAs read the least shared memory per flop);
-// `force` (32, 64, 128) overrides.
-int split_cols_choice(int N, int force) {
+// Tile width for a merged block of N columns over kblocks 64-wide K blocks:
+// the narrowest of 32 and 64 that holds them, else 128 (whose MMAs read the
+// least shared memory per flop).  Over long K every tile is 128 wide, so that
+// every tile of the plan takes the same K stage (64) and a block's bits do not
+// depend on the columns it is merged with.  `force` (32, 64, 128) overrides.
+int split_cols_choice(int N, int kblocks, int force) {
     if (force == 32 || force == 64 || force == 128) return force;
+    if (kblocks >= kK64Blocks) return 128;
     return N <= 32 ? 32 : (N <= 64 ? 64 : 128);
 }
 int split_jpt(int cnp, int lg) { return (cnp + (1 << lg) - 1) >> lg; }
