@@ -1078,3 +1078,13 @@ void plan_destroy(Plan *p) {
     if (p->pinned) cudaFreeHost(p->pinned);
     delete p;
 }
+
+// Test hook (host only, not part of the interface): the tile width and K stage
+// the plan gives a merged block of n_cols columns over kblocks 64-wide K blocks.
+extern "C" int hb_test_split_shape(int n_cols, int kblocks, int force_cols, int force_kstage, int *cols,
+                                   int *kstage) {
+    if (!cols || !kstage || n_cols < 1 || kblocks < 1) return HB_ERR_INVALID_ARG;
+    *cols = split_cols_choice(n_cols, kblocks, force_cols);
+    *kstage = split_kstage_choice(*cols, kblocks, force_kstage);
+    return HB_OK;
+}
